@@ -1,0 +1,207 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module holds no arithmetic of the homogenisation method: it only draws
+random numbers and voxelises simple geometries.  Everything that the method
+computes (tensor-train algebra, rounding, Fourier operators, Green operator,
+fixed-point iteration) lives elsewhere.
+
+Conventions
+-----------
+* A voxel grid has N = 2**n points per side; voxel (i, j, k) has its centre at
+  ((i + 1/2)/N, (j + 1/2)/N, (k + 1/2)/N) in the unit cell.  Points exactly on
+  an inclusion boundary count as inside.
+* Phase indicators are float64 arrays of shape (N, N, N) holding 0.0 (matrix,
+  phase 1) or 1.0 (inclusion / second phase, phase 2).
+* Random tensor-train cores have shape (r_{k-1}, p, r_k) with r_0 = r_d = 1 and
+  bond caps r_k <= min(r, p**k, p**(d-k)).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+# ---------------------------------------------------------------- geometry --
+
+def voxel_centres(N: int) -> np.ndarray:
+    return (np.arange(N, dtype=np.float64) + 0.5) / N
+
+
+def laminate_indicator(N: int, axis: int = 0, fraction: float = 0.5) -> np.ndarray:
+    """Two-phase laminate, layers normal to `axis`; phase 2 where coordinate < fraction."""
+    c = voxel_centres(N)
+    ind1d = (c < fraction).astype(np.float64)
+    shape = [1, 1, 1]
+    shape[axis] = N
+    return np.broadcast_to(ind1d.reshape(shape), (N, N, N)).copy()
+
+
+def sphere_radius(volume_fraction: float) -> float:
+    """Radius of a sphere of the given volume fraction in the unit cell."""
+    return (3.0 * volume_fraction / (4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def sphere_indicator(N: int, volume_fraction: float = 0.2,
+                     centre=(0.5, 0.5, 0.5)) -> np.ndarray:
+    """Single centred spherical inclusion of the given (continuum) volume fraction."""
+    R = sphere_radius(volume_fraction)
+    c = voxel_centres(N)
+    dx = (c - centre[0])[:, None, None]
+    dy = (c - centre[1])[None, :, None]
+    dz = (c - centre[2])[None, None, :]
+    return ((dx * dx + dy * dy + dz * dz) <= R * R).astype(np.float64)
+
+
+def _random_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniform random rotation from a uniform unit quaternion."""
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def _periodic_delta(c: np.ndarray, centre: float) -> np.ndarray:
+    d = c - centre
+    return d - np.round(d)
+
+
+def ellipsoid_rve(N: int, rng: np.random.Generator, max_tries: int = 200):
+    """Random RVE of 1..8 non-overlapping, randomly oriented ellipsoids.
+
+    Semi-axes are drawn from U[0.05, 0.2] (units of the cell), the count from
+    1..8, the orientation from a uniform quaternion.  A draw whose ellipsoid
+    overlaps an earlier one (tested on the voxel grid, periodic) is rejected.
+    The whole RVE is redrawn until the voxel phase fraction lies in
+    [0.1, 0.3].  Returns (indicator, contrast) with the contrast log-uniform in
+    [5, 100].
+    """
+    c = voxel_centres(N)
+    for _ in range(max_tries):
+        count = int(rng.integers(1, 9))
+        ind = np.zeros((N, N, N), dtype=bool)
+        placed = 0
+        for _ in range(50 * count):
+            if placed == count:
+                break
+            axes = rng.uniform(0.05, 0.2, size=3)
+            rot = _random_rotation(rng)
+            ctr = rng.uniform(0.0, 1.0, size=3)
+            dx = _periodic_delta(c, ctr[0])[:, None, None]
+            dy = _periodic_delta(c, ctr[1])[None, :, None]
+            dz = _periodic_delta(c, ctr[2])[None, None, :]
+            # body-frame coordinates u = rot^T (x - c)
+            u0 = rot[0, 0] * dx + rot[1, 0] * dy + rot[2, 0] * dz
+            u1 = rot[0, 1] * dx + rot[1, 1] * dy + rot[2, 1] * dz
+            u2 = rot[0, 2] * dx + rot[1, 2] * dy + rot[2, 2] * dz
+            inside = (u0 / axes[0]) ** 2 + (u1 / axes[1]) ** 2 + (u2 / axes[2]) ** 2 <= 1.0
+            if np.any(inside & ind):
+                continue
+            ind |= inside
+            placed += 1
+        frac = ind.mean()
+        if placed >= 1 and 0.1 <= frac <= 0.3:
+            contrast = float(np.exp(rng.uniform(np.log(5.0), np.log(100.0))))
+            return ind.astype(np.float64), contrast
+    raise RuntimeError("ellipsoid_rve: no admissible draw")
+
+
+def fibre_rve(N: int, rng: np.random.Generator, count: int = 32,
+              fibre_fraction: float = 0.3, max_tries: int = 100000) -> np.ndarray:
+    """Aligned cylindrical fibres (axis parallel to z), non-overlapping under the
+    periodic minimum-image distance, radius chosen so that `count` fibres fill
+    `fibre_fraction` of the cell."""
+    radius = math.sqrt(fibre_fraction / (count * math.pi))
+    centres = []
+    for _ in range(max_tries):
+        if len(centres) == count:
+            break
+        p = rng.uniform(0.0, 1.0, size=2)
+        ok = True
+        for q in centres:
+            d = p - q
+            d -= np.round(d)
+            if d @ d < (2.0 * radius) ** 2:
+                ok = False
+                break
+        if ok:
+            centres.append(p)
+    if len(centres) < count:
+        raise RuntimeError("fibre_rve: could not place all fibres")
+    c = voxel_centres(N)
+    ind2 = np.zeros((N, N), dtype=bool)
+    for p in centres:
+        dx = _periodic_delta(c, p[0])[:, None]
+        dy = _periodic_delta(c, p[1])[None, :]
+        ind2 |= dx * dx + dy * dy <= radius * radius
+    return np.broadcast_to(ind2[:, :, None], (N, N, N)).astype(np.float64)
+
+
+def batched_rve_set(count: int = 64, seed: int = 4, log2_min: int = 6, log2_max: int = 9):
+    """The mixed-resolution ellipsoid RVE batch: side 2**u with u uniform in
+    [log2_min, log2_max]; RVE i uses the i-th child generator spawned from
+    `default_rng(seed)`.  Returns a list of (n_bits, child_rng) pairs; the
+    indicator itself is drawn lazily with `ellipsoid_rve(2**n, rng)`."""
+    master = np.random.default_rng(seed)
+    children = master.spawn(count)
+    sizes = master.integers(log2_min, log2_max + 1, size=count)
+    return [(int(s), ch) for s, ch in zip(sizes, children)]
+
+
+# ------------------------------------------------------ isotropic moduli --
+
+def lame_from_young(E: float, nu: float):
+    """(lambda, mu) of an isotropic material from Young's modulus and Poisson ratio."""
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    return lam, mu
+
+
+# ------------------------------------------------------ random TT cores --
+
+def capped_ranks(d: int, p: int, r: int) -> list[int]:
+    """Bond ranks r_0..r_d for a uniform target rank r with boundary caps."""
+    ranks = [1]
+    for k in range(1, d):
+        ranks.append(int(min(r, p ** min(k, 30), p ** min(d - k, 30))))
+    ranks.append(1)
+    return ranks
+
+
+def random_tt_cores(d: int, p: int, r: int, seed: int, dtype=np.float64,
+                    ranks: list[int] | None = None) -> list[np.ndarray]:
+    """Gaussian cores N(0,1)/sqrt(r) with shapes (r_{k-1}, p, r_k).
+
+    For complex dtypes the real and imaginary parts are drawn independently
+    and scaled by 1/sqrt(2) so that E|z|^2 matches the real case."""
+    rng = np.random.default_rng(seed)
+    if ranks is None:
+        ranks = capped_ranks(d, p, r)
+    cores = []
+    scale = 1.0 / math.sqrt(r)
+    cplx = np.issubdtype(np.dtype(dtype), np.complexfloating)
+    for k in range(d):
+        shape = (ranks[k], p, ranks[k + 1])
+        if cplx:
+            a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+            a *= scale / math.sqrt(2.0)
+        else:
+            a = rng.standard_normal(shape) * scale
+        cores.append(a.astype(dtype))
+    return cores
+
+
+def random_mpo_cores(d: int, p: int, chi: int, seed: int, dtype=np.complex128) -> list[np.ndarray]:
+    """Gaussian operator cores of shape (chi_{k-1}, p_out, p_in, chi_k)."""
+    rng = np.random.default_rng(seed)
+    ranks = capped_ranks(d, p * p, chi)
+    cores = []
+    for k in range(d):
+        shape = (ranks[k], p, p, ranks[k + 1])
+        a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        cores.append((a / math.sqrt(2.0 * chi)).astype(dtype))
+    return cores
