@@ -1,0 +1,227 @@
+/*
+ * qtt.h - C-ABI of the GB300 library for the quantized-tensor-train (QTT)
+ * Moulinec-Suquet hot path of arXiv 2512.07811 ("Performance Benchmarking of
+ * Tensor Trains for Quantum-Inspired Homogenization on TPU, GPU, and CPU
+ * Architectures").
+ *
+ * General conventions
+ *  - Every call returns QTT_OK (0) or a negative status (see below); no C++
+ *    exception crosses this boundary.  qtt_status_string() names a status.
+ *  - A tensor train (TT) with d cores stores core k as a row-major array of
+ *    shape (r_{k-1}, n_k, r_k), r_0 = r_d = 1 (Sec. 2, Eq. tt_format; the
+ *    paper writes (r_k x p x r_{k-1}), the index order is immaterial).
+ *    Elements are interleaved complex numbers: QTT_C128 = two doubles
+ *    (C99 double _Complex), QTT_C64 = two floats.
+ *  - An operator train (TTO / MPO) stores core k as (g_{k-1}, m_k, n_k, g_k):
+ *    output mode m_k, input mode n_k (Sec. 2, Eq. tto_format).
+ *  - Combined bonds put the first operand's bond index first (major):
+ *    Hadamard (alpha_x, alpha_y), operator application (gamma, alpha),
+ *    addition [x block | y block].
+ *  - Trains and operators are library-owned device memory on the device of
+ *    the context; callers release them with qtt_tt_destroy / qtt_mpo_destroy.
+ *    Inputs are never modified and never aliased into outputs; outputs are
+ *    freshly allocated and owned by the caller.
+ *  - All work is enqueued on the context's stream.  Calls that return host
+ *    scalars (tt_dot, tt_norm, ranks chosen by rounding, ms_homogenize)
+ *    synchronise that stream.
+ *  - The library has no CPU fallback: every operation runs in its CUDA
+ *    kernels on an sm_103a device; creating a context fails without one.
+ */
+#ifndef QTT_H
+#define QTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QTT_API __attribute__((visibility("default")))
+#else
+#define QTT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ statuses */
+#define QTT_OK 0
+#define QTT_ERR_ARG -1           /* invalid argument, shape or dtype mismatch   */
+#define QTT_ERR_OOM -2           /* device allocation failed                    */
+#define QTT_ERR_RANK -3          /* a rank exceeds a fixed workspace limit      */
+#define QTT_ERR_TIMEOUT -4       /* a bounded device wait gave up               */
+#define QTT_ERR_NOT_CONVERGED -5 /* iteration limit reached before the tolerance */
+#define QTT_ERR_NAN -6           /* non-finite values detected in a result      */
+#define QTT_ERR_CUDA -7          /* a CUDA runtime call failed                  */
+#define QTT_ERR_UNSUPPORTED -8   /* combination not implemented                 */
+
+typedef struct qtt_ctx qtt_ctx;
+typedef struct qtt_tt qtt_tt;
+typedef struct qtt_mpo qtt_mpo;
+
+typedef enum { QTT_C128 = 0, QTT_C64 = 1 } qtt_dtype;
+
+/* Arithmetic used inside an operation.  QTT_PREC_F64 needs QTT_C128 storage
+ * and computes everything in double.  QTT_PREC_F32 (QTT_C64 storage) runs the
+ * core contractions and the small factorisations in float, norms, rounding
+ * thresholds and residuals in double. */
+typedef enum { QTT_PREC_F64 = 0, QTT_PREC_F32 = 1 } qtt_prec;
+
+typedef struct {
+  double re, im;
+} qtt_complex;
+
+/* Outcome of one rounding (Sec. 2.2, Compression via SVD). */
+typedef struct {
+  double norm;      /* ||x||_F of the (possibly structured) input train          */
+  double delta;     /* per-bond threshold eps ||x||_F / sqrt(d - 1)             */
+  double tail;      /* sqrt(sum over bonds of squared discarded singular values) */
+  double err;       /* exact relative error ||x - y|| / ||x|| when computed, else -1 */
+  int32_t capped;   /* 1 if max_rank cut a rank that the tolerance asked for    */
+  int32_t max_rank_out;
+} qtt_round_info;
+
+/* ------------------------------------------------------------- context */
+/* Bind a context to CUDA device `device` and stream `cuda_stream` (a
+ * cudaStream_t, or NULL for a new non-blocking stream owned by the context).
+ * Fails with QTT_ERR_CUDA if the device is absent or is not sm_103. */
+QTT_API int qtt_ctx_create(int device, void* cuda_stream, qtt_ctx** out);
+QTT_API void qtt_ctx_destroy(qtt_ctx* ctx);
+QTT_API int qtt_ctx_sync(qtt_ctx* ctx);
+/* Number of kernels this library has launched on the context so far. */
+QTT_API int64_t qtt_ctx_launch_count(const qtt_ctx* ctx);
+
+/* --------------------------------------------------------------- trains */
+/* New train with the given modes (d entries) and ranks (d + 1 entries,
+ * ranks[0] = ranks[d] = 1), zero-filled. */
+QTT_API int qtt_tt_create(qtt_ctx* ctx, int ncores, const int32_t* modes, const int32_t* ranks, qtt_dtype dtype,
+                  qtt_tt** out);
+QTT_API void qtt_tt_destroy(qtt_tt* x);
+QTT_API int qtt_tt_ncores(const qtt_tt* x);
+QTT_API int qtt_tt_ranks(const qtt_tt* x, int32_t* ranks /* ncores + 1 */);
+QTT_API int qtt_tt_modes(const qtt_tt* x, int32_t* modes /* ncores */);
+QTT_API int qtt_tt_dtype(const qtt_tt* x);
+/* Device address of core k (valid until the train is destroyed). */
+QTT_API void* qtt_tt_core_ptr(const qtt_tt* x, int core);
+/* Copy core k from / to host memory (r_{k-1} * n_k * r_k complex elements). */
+QTT_API int qtt_tt_from_host(qtt_tt* x, int core, const void* buf);
+QTT_API int qtt_tt_to_host(const qtt_tt* x, int core, void* buf);
+/* Copy core k from device memory of the same device (stream-ordered). */
+QTT_API int qtt_tt_from_device(qtt_tt* x, int core, const void* dev_buf);
+/* y = x stored in another dtype (rounds to nearest when narrowing). */
+QTT_API int qtt_tt_convert(qtt_ctx* ctx, const qtt_tt* x, qtt_dtype dtype, qtt_tt** y);
+
+/* ------------------------------------------------------------ operators */
+QTT_API int qtt_mpo_create(qtt_ctx* ctx, int ncores, const int32_t* modes_out, const int32_t* modes_in,
+                   const int32_t* ranks, qtt_dtype dtype, qtt_mpo** out);
+QTT_API void qtt_mpo_destroy(qtt_mpo* A);
+QTT_API int qtt_mpo_ranks(const qtt_mpo* A, int32_t* ranks /* ncores + 1 */);
+QTT_API int qtt_mpo_from_host(qtt_mpo* A, int core, const void* buf);
+QTT_API int qtt_mpo_to_host(const qtt_mpo* A, int core, void* buf);
+
+/* --------------------------------------------------------- TT algebra */
+/* z = a x + b y by block placement (Sec. 2.1, Addition; constant
+ * multiplication rescales the first cores, Eq. tt_const_multiplication).
+ * Ranks add.  x and y need equal modes and dtypes. */
+QTT_API int tt_add(qtt_ctx* ctx, qtt_complex a, const qtt_tt* x, qtt_complex b, const qtt_tt* y, qtt_tt** z);
+
+/* z = x (elementwise) y: C_k(i) = A_k(i) (kron) B_k(i) (Sec. 2.1, Hadamard
+ * product).  Ranks multiply. */
+QTT_API int tt_hadamard(qtt_ctx* ctx, const qtt_tt* x, const qtt_tt* y, qtt_tt** z);
+
+/* y = A x: B_k(i) = sum_j D_k(i, j) (kron) A_k(j) (Sec. 2.1, TT-TTO
+ * contraction).  Ranks multiply. */
+QTT_API int tt_mpo_apply(qtt_ctx* ctx, const qtt_mpo* A, const qtt_tt* x, qtt_tt** y);
+
+/* SVD-based rounding (Sec. 2.2, Orthogonalization and Compression via SVD):
+ * a left-to-right QR sweep, ||x|| from the orthogonality centre, the
+ * threshold delta = eps ||x|| / sqrt(d - 1) (Eq. optimal_delta, read with
+ * sqrt(d-1)), then a right-to-left sweep of truncated SVDs keeping the
+ * smallest rank whose discarded tail is <= delta, capped at max_rank (<= 0:
+ * no cap).  The output's cores 2..d are right-orthonormal.  `prec` must
+ * match the dtype (F64 for C128, F32 for C64).  `info` may be NULL. */
+QTT_API int tt_round(qtt_ctx* ctx, const qtt_tt* x, double eps, int max_rank, qtt_prec prec, qtt_round_info* info,
+             qtt_tt** y);
+
+/* Randomize-then-orthogonalize rounding of a structured sum
+ *     s = sum_t coef[t] * A_t x_t     (A_t = NULL means the identity)
+ * without forming s: with the Gaussian sketch train `sketch` (modes = the
+ * output modes, ranks l_k) the right partial contractions of s with the
+ * sketch are built term by term, then a left-to-right sweep of QR
+ * factorisations of the sketched cores projects s onto rank l_k, and a
+ * deterministic rounding (tt_round) of that projection applies eps and
+ * max_rank.  A builder addition with no counterpart in the paper (Al Daas et
+ * al., SIAM J. Sci. Comput. 45, 2023).  All trains share one dtype. */
+QTT_API int tt_round_sketched(qtt_ctx* ctx, int nterms, const qtt_complex* coef, const qtt_mpo* const* ops,
+                      const qtt_tt* const* xs, const qtt_tt* sketch, double eps, int max_rank, qtt_prec prec,
+                      qtt_round_info* info, qtt_tt** y);
+
+/* out = <x, y> = sum_i conj(x(i)) y(i) through the transfer-matrix chain
+ * W_k = sum_i A_k(i)^H W_{k-1} B_k(i); out[0] = real, out[1] = imaginary
+ * part.  Accumulates in the storage precision; returns a double. */
+QTT_API int tt_dot(qtt_ctx* ctx, const qtt_tt* x, const qtt_tt* y, double out[2]);
+
+/* ||x||_F as the norm of the orthogonality centre after the QR sweep
+ * (Sec. 2.2), which avoids the cancellation of <x, x> for differences. */
+QTT_API int tt_norm(qtt_ctx* ctx, const qtt_tt* x, double* out);
+
+/* Dense tensor (device memory, modes[0] slowest) to a train by sequential
+ * truncated SVDs of the unfoldings (TT-SVD, Oseledets 2011), threshold
+ * eps ||A|| / sqrt(d - 1) per bond, computed in double (QTT_C128 output). */
+QTT_API int tt_from_dense(qtt_ctx* ctx, int ncores, const int32_t* modes, const void* dense_c128, double eps,
+                  int max_rank, qtt_tt** out);
+
+/* Q_n of QFT_n = R_n Q_n (Sec. 3.2, Fig. 1): the unitary DFT with sign
+ * `sign` (-1: exp(-2 pi i jk/N)) whose output bits are left in reversed
+ * order, as an operator train of `nbits` sites (site a: output bit of weight
+ * 2^(a-1), input bit of weight 2^(nbits-a)), rounded at `tol`. */
+QTT_API int qtt_qft_mpo(qtt_ctx* ctx, int nbits, int sign, double tol, qtt_mpo** out);
+
+/* ---------------------------------------------------- homogenisation */
+typedef struct {
+  int32_t ncomp;        /* 3: scalar conductivity, 6: elasticity (Voigt 11,22,33,23,13,12) */
+  int32_t nbits;        /* N = 2^nbits voxels per side                                     */
+  const double* indicator; /* host, N^3 values 0/1 (1 = phase 2), x slowest                 */
+  double k1, k2;        /* scalar: phase conductivities                                    */
+  double lam1, mu1, lam2, mu2; /* elasticity: Lame constants of phases 1 and 2             */
+  int32_t interleaved;  /* site order: 1 = x1 y1 z1 x2 ..., 0 = grouped by dimension      */
+} qtt_rve;
+
+typedef struct {
+  qtt_prec prec;        /* arithmetic of the iteration                                    */
+  double eps;           /* rounding tolerance of every step                               */
+  double op_tol;        /* tolerance of the operator trains (phase, Green)               */
+  int32_t max_iter;
+  int32_t oversample;   /* sketch width = max_rank + oversample                           */
+  int32_t load_mask;    /* bit k set: solve load case E = e_k (column k of C_eff)        */
+  int32_t min_iter;
+  uint64_t seed;        /* counter-based generator seed for the sketches                 */
+} ms_opts;
+
+typedef struct {
+  int32_t iterations[6];
+  double residual[6];      /* last relative change ||eps_{m+1} - eps_m|| / ||E 1||       */
+  double sigma_imag_max;   /* max |Im sigma_eff| (diagnostic)                             */
+  int32_t max_rank_seen;
+  double setup_ms, iterate_ms;
+  int64_t kernel_launches;
+} ms_report;
+
+/* Moulinec-Suquet homogenisation in QTT form (Sec. 3.2, Algorithm 2):
+ *   tau = round((C - C0) eps_m);  tau^ = S tau;  eps^ = round(Gamma0 tau^);
+ *   eps_{m+1} = round(E - S^{-1} eps^);  stop when
+ *   ||eps_{m+1} - eps_m||_F / ||E 1||_F < tol (Algorithm 2; Appendix A for the
+ * effective tensor, sigma_eff = <C eps>).  C0 is the isotropic reference
+ * (3x3 k0*I or Voigt 6x6, row-major).  Each rounding uses the sketched
+ * rounding with width max_rank + oversample.  C_eff (ncomp x ncomp,
+ * row-major, real part) receives the columns of the load cases in
+ * opts->load_mask; `report` may be NULL. */
+QTT_API int ms_homogenize(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, double tol, int max_rank,
+                  const ms_opts* opts, double* C_eff, ms_report* report);
+
+QTT_API const char* qtt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTT_H */

@@ -1,0 +1,861 @@
+// The C-ABI of include/qtt.h: argument checking, dtype dispatch, and the
+// Moulinec-Suquet driver (Algorithm 2 of arXiv 2512.07811) composed from the
+// device algorithms in engine.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "../../include/qtt.h"
+#include "common.cuh"
+#include "engine.h"
+#include "kernels.h"
+
+#define TRY(expr)                 \
+  do {                            \
+    int _st = (expr);             \
+    if (_st != QTT_OK) return _st; \
+  } while (0)
+
+namespace {
+
+bool same_modes(const qtt_tt* x, const qtt_tt* y) { return x->d == y->d && x->n == y->n; }
+
+bool valid_tt(const qtt_tt* x) {
+  if (!x || x->d < 1 || (int)x->r.size() != x->d + 1 || x->r[0] != 1 || x->r[x->d] != 1) return false;
+  return true;
+}
+
+template <class R>
+int add_dev(qtt_ctx* c, cplx<R> a, const qtt_tt* x, cplx<R> b, const qtt_tt* y, qtt_tt** out) {
+  const int d = x->d;
+  std::vector<int> r(d + 1, 1);
+  for (int k = 1; k < d; ++k) r[k] = x->r[k] + y->r[k];
+  int st;
+  qtt_tt* z = tt_alloc(c, d, x->n, r, x->dtype, &st);
+  if (!z) return st;
+  cudaMemsetAsync(z->data, 0, z->bytes, c->stream);
+  typedef cplx<R> C;
+  const C one(1, 0);
+  for (int k = 0; k < d; ++k) {
+    const int64_t n = x->n[k];
+    const int64_t xa = x->r[k], xb = x->r[k + 1], ya = y->r[k], yb = y->r[k + 1];
+    C* Z = core_ptr<C>(z, k);
+    const int64_t zb = r[k + 1];
+    if (d == 1) {
+      // z = a x + b y elementwise (single core)
+      c->launches += 2;
+      int s1 = qtt_place_block<R>(core_ptr<C>(x, 0), 1, n, 1, Z, 1, 0, 0, a, c->stream);
+      if (s1) {
+        tt_free(z);
+        return s1;
+      }
+      // accumulate b*y with a rank-1 GEMM: Z (1 x n) += b * [1] (1 x 1) * y (1 x n)
+      void* onep;
+      if (dalloc(c, &onep, sizeof(C))) {
+        tt_free(z);
+        return QTT_ERR_OOM;
+      }
+      cudaMemcpyAsync(onep, &one, sizeof(C), cudaMemcpyHostToDevice, c->stream);
+      GemmDesc g;
+      g.bA = g.bB = g.bC = MIdx{1, 1, 0, 0};
+      g.M = 1;
+      g.N = n;
+      g.K = 1;
+      g.batch = 1;
+      g.mA = MIdx{1, 1, 1, 0};
+      g.kA = MIdx{1, 1, 1, 0};
+      g.kB = MIdx{1, 1, n, 0};
+      g.nB = MIdx{n, 1, 1, 0};
+      g.mC = MIdx{1, 1, n, 0};
+      g.nC = MIdx{n, 1, 1, 0};
+      g.conjA = g.conjB = 0;
+      int s2 = qtt_gemm<R>(g, b, one, reinterpret_cast<C*>(onep), core_ptr<C>(y, 0), Z, c->stream);
+      dfree(c, onep);
+      if (s2) {
+        tt_free(z);
+        return s2;
+      }
+      break;
+    }
+    const int64_t xoff0 = 0, xoff1 = 0;
+    const int64_t yoff0 = (k == 0) ? 0 : xa;
+    const int64_t yoff1 = (k == d - 1) ? 0 : xb;
+    c->launches += 2;
+    int s1 = qtt_place_block<R>(core_ptr<C>(x, k), xa, n, xb, Z, zb, xoff0, xoff1, k == 0 ? a : one, c->stream);
+    int s2 = qtt_place_block<R>(core_ptr<C>(y, k), ya, n, yb, Z, zb, yoff0, yoff1, k == 0 ? b : one, c->stream);
+    if (s1 || s2) {
+      tt_free(z);
+      return s1 ? s1 : s2;
+    }
+  }
+  *out = z;
+  return QTT_OK;
+}
+
+template <class R>
+int hadamard_dev(qtt_ctx* c, const qtt_tt* x, const qtt_tt* y, qtt_tt** out) {
+  const int d = x->d;
+  std::vector<int> r(d + 1);
+  for (int k = 0; k <= d; ++k) r[k] = x->r[k] * y->r[k];
+  int st;
+  qtt_tt* z = tt_alloc(c, d, x->n, r, x->dtype, &st);
+  if (!z) return st;
+  typedef cplx<R> C;
+  for (int k = 0; k < d; ++k) {
+    c->launches++;
+    int s = qtt_hadamard_core<R>(core_ptr<C>(x, k), x->r[k], x->r[k + 1], core_ptr<C>(y, k), y->r[k], y->r[k + 1],
+                                 x->n[k], core_ptr<C>(z, k), c->stream);
+    if (s) {
+      tt_free(z);
+      return s;
+    }
+  }
+  *out = z;
+  return QTT_OK;
+}
+
+template <class R>
+int mpo_apply_dev(qtt_ctx* c, const qtt_mpo* A, const qtt_tt* x, qtt_tt** out) {
+  const int d = x->d;
+  std::vector<int> r(d + 1);
+  for (int k = 0; k <= d; ++k) r[k] = A->g[k] * x->r[k];
+  int st;
+  qtt_tt* z = tt_alloc(c, d, A->no, r, x->dtype, &st);
+  if (!z) return st;
+  typedef cplx<R> C;
+  for (int k = 0; k < d; ++k) {
+    c->launches++;
+    int s = qtt_mpo_core<R>(core_ptr<C>(A, k), A->g[k], A->no[k], A->ni[k], A->g[k + 1], core_ptr<C>(x, k), x->r[k],
+                            x->r[k + 1], core_ptr<C>(z, k), c->stream);
+    if (s) {
+      tt_free(z);
+      return s;
+    }
+  }
+  *out = z;
+  return QTT_OK;
+}
+
+int check_prec(qtt_dtype dt, qtt_prec p) {
+  if (dt == QTT_C128 && p == QTT_PREC_F64) return QTT_OK;
+  if (dt == QTT_C64 && p == QTT_PREC_F32) return QTT_OK;
+  return QTT_ERR_ARG;
+}
+
+// sketch train: real Gaussian cores N(0, 1/(n_k l_k)), ranks min(l, prod left, prod right)
+int make_sketch(qtt_ctx* c, const std::vector<int>& modes, int ell, qtt_dtype dt, uint64_t seed, uint64_t stream_id,
+                qtt_tt** out) {
+  const int d = (int)modes.size();
+  std::vector<int> r(d + 1, 1);
+  double left = 1;
+  for (int k = 1; k < d; ++k) {
+    left *= modes[k - 1];
+    double right = 1;
+    for (int j = k; j < d; ++j) right *= modes[j];
+    r[k] = (int)std::min<double>(ell, std::min(left, right));
+  }
+  int st;
+  qtt_tt* S = tt_alloc(c, d, modes, r, dt, &st);
+  if (!S) return st;
+  for (int k = 0; k < d; ++k) {
+    int64_t cnt = (int64_t)r[k] * modes[k] * r[k + 1];
+    double scale = 1.0 / sqrt((double)modes[k] * r[k + 1]);
+    c->launches++;
+    int s = dt == QTT_C128
+                ? qtt_fill_gaussian<double>(core_ptr<zc>(S, k), cnt, seed, (stream_id << 8) + k, scale, c->stream)
+                : qtt_fill_gaussian<float>(core_ptr<cc>(S, k), cnt, seed, (stream_id << 8) + k, scale, c->stream);
+    if (s) {
+      tt_free(S);
+      return s;
+    }
+  }
+  *out = S;
+  return QTT_OK;
+}
+
+int convert_tt(qtt_ctx* c, const qtt_tt* x, qtt_dtype dt, qtt_tt** out) {
+  int st;
+  qtt_tt* y = tt_alloc(c, x->d, x->n, x->r, dt, &st);
+  if (!y) return st;
+  for (int k = 0; k < x->d; ++k) {
+    int64_t cnt = (int64_t)x->r[k] * x->n[k] * x->r[k + 1];
+    if (x->dtype == dt) {
+      cudaMemcpyAsync(core_ptr<char>(y, k), core_ptr<char>(x, k), cnt * dtype_size(dt), cudaMemcpyDeviceToDevice,
+                      c->stream);
+    } else if (dt == QTT_C64) {
+      c->launches++;
+      qtt_convert_z2c(core_ptr<zc>(x, k), core_ptr<cc>(y, k), cnt, c->stream);
+    } else {
+      c->launches++;
+      qtt_convert_c2z(core_ptr<cc>(x, k), core_ptr<zc>(y, k), cnt, c->stream);
+    }
+  }
+  *out = y;
+  return QTT_OK;
+}
+
+int convert_mpo(qtt_ctx* c, const qtt_mpo* A, qtt_dtype dt, qtt_mpo** out) {
+  int st;
+  qtt_mpo* B = mpo_alloc(c, A->d, A->no, A->ni, A->g, dt, &st);
+  if (!B) return st;
+  for (int k = 0; k < A->d; ++k) {
+    int64_t cnt = (int64_t)A->g[k] * A->no[k] * A->ni[k] * A->g[k + 1];
+    if (A->dtype == dt) {
+      cudaMemcpyAsync(core_ptr<char>(B, k), core_ptr<char>(A, k), cnt * dtype_size(dt), cudaMemcpyDeviceToDevice,
+                      c->stream);
+    } else if (dt == QTT_C64) {
+      c->launches++;
+      qtt_convert_z2c(core_ptr<zc>(A, k), core_ptr<cc>(B, k), cnt, c->stream);
+    } else {
+      c->launches++;
+      qtt_convert_c2z(core_ptr<cc>(A, k), core_ptr<zc>(B, k), cnt, c->stream);
+    }
+  }
+  *out = B;
+  return QTT_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char* qtt_status_string(int s) {
+  switch (s) {
+    case QTT_OK: return "ok";
+    case QTT_ERR_ARG: return "invalid argument";
+    case QTT_ERR_OOM: return "device allocation failed";
+    case QTT_ERR_RANK: return "rank exceeds workspace limit";
+    case QTT_ERR_TIMEOUT: return "bounded device wait gave up";
+    case QTT_ERR_NOT_CONVERGED: return "not converged";
+    case QTT_ERR_NAN: return "non-finite values";
+    case QTT_ERR_CUDA: return "CUDA runtime error";
+    case QTT_ERR_UNSUPPORTED: return "unsupported combination";
+    default: return "unknown status";
+  }
+}
+
+int qtt_ctx_create(int device, void* stream, qtt_ctx** out) {
+  if (!out) return QTT_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return QTT_ERR_CUDA;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return QTT_ERR_CUDA;
+  if (!(prop.major == 10 && prop.minor == 3)) return QTT_ERR_UNSUPPORTED;  // built for sm_103a only
+  if (cudaSetDevice(device) != cudaSuccess) return QTT_ERR_CUDA;
+  qtt_ctx* c = new (std::nothrow) qtt_ctx();
+  if (!c) return QTT_ERR_OOM;
+  c->device = device;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return QTT_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return QTT_OK;
+}
+
+void qtt_ctx_destroy(qtt_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int qtt_ctx_sync(qtt_ctx* c) {
+  if (!c) return QTT_ERR_ARG;
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+int64_t qtt_ctx_launch_count(const qtt_ctx* c) { return c ? c->launches : -1; }
+
+int qtt_tt_create(qtt_ctx* c, int d, const int32_t* modes, const int32_t* ranks, qtt_dtype dt, qtt_tt** out) {
+  if (!c || !out || d < 1 || !modes || !ranks || (dt != QTT_C128 && dt != QTT_C64)) return QTT_ERR_ARG;
+  if (ranks[0] != 1 || ranks[d] != 1) return QTT_ERR_ARG;
+  for (int k = 0; k < d; ++k)
+    if (modes[k] < 1 || ranks[k + 1] < 1) return QTT_ERR_ARG;
+  std::vector<int> n(modes, modes + d), r(ranks, ranks + d + 1);
+  int st;
+  qtt_tt* x = tt_alloc(c, d, n, r, dt, &st);
+  if (!x) return st;
+  cudaMemsetAsync(x->data, 0, x->bytes, c->stream);
+  *out = x;
+  return QTT_OK;
+}
+
+void qtt_tt_destroy(qtt_tt* x) { tt_free(x); }
+int qtt_tt_ncores(const qtt_tt* x) { return x ? x->d : QTT_ERR_ARG; }
+int qtt_tt_ranks(const qtt_tt* x, int32_t* r) {
+  if (!x || !r) return QTT_ERR_ARG;
+  for (int k = 0; k <= x->d; ++k) r[k] = x->r[k];
+  return QTT_OK;
+}
+int qtt_tt_modes(const qtt_tt* x, int32_t* n) {
+  if (!x || !n) return QTT_ERR_ARG;
+  for (int k = 0; k < x->d; ++k) n[k] = x->n[k];
+  return QTT_OK;
+}
+int qtt_tt_dtype(const qtt_tt* x) { return x ? (int)x->dtype : QTT_ERR_ARG; }
+void* qtt_tt_core_ptr(const qtt_tt* x, int k) {
+  if (!x || k < 0 || k >= x->d) return nullptr;
+  return core_ptr<char>(x, k);
+}
+
+static size_t core_bytes(const qtt_tt* x, int k) {
+  return (size_t)x->r[k] * x->n[k] * x->r[k + 1] * dtype_size(x->dtype);
+}
+
+int qtt_tt_from_host(qtt_tt* x, int k, const void* buf) {
+  if (!x || !buf || k < 0 || k >= x->d) return QTT_ERR_ARG;
+  if (cudaMemcpyAsync(core_ptr<char>(x, k), buf, core_bytes(x, k), cudaMemcpyHostToDevice, x->ctx->stream) !=
+      cudaSuccess)
+    return QTT_ERR_CUDA;
+  return cudaStreamSynchronize(x->ctx->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+int qtt_tt_to_host(const qtt_tt* x, int k, void* buf) {
+  if (!x || !buf || k < 0 || k >= x->d) return QTT_ERR_ARG;
+  return sync_read(x->ctx, buf, core_ptr<char>(x, k), core_bytes(x, k));
+}
+int qtt_tt_from_device(qtt_tt* x, int k, const void* buf) {
+  if (!x || !buf || k < 0 || k >= x->d) return QTT_ERR_ARG;
+  return cudaMemcpyAsync(core_ptr<char>(x, k), buf, core_bytes(x, k), cudaMemcpyDeviceToDevice, x->ctx->stream) ==
+                 cudaSuccess
+             ? QTT_OK
+             : QTT_ERR_CUDA;
+}
+int qtt_tt_convert(qtt_ctx* c, const qtt_tt* x, qtt_dtype dt, qtt_tt** y) {
+  if (!c || !valid_tt(x) || !y || (dt != QTT_C128 && dt != QTT_C64)) return QTT_ERR_ARG;
+  return convert_tt(c, x, dt, y);
+}
+
+int qtt_mpo_create(qtt_ctx* c, int d, const int32_t* mo, const int32_t* mi, const int32_t* ranks, qtt_dtype dt,
+                   qtt_mpo** out) {
+  if (!c || !out || d < 1 || !mo || !mi || !ranks || (dt != QTT_C128 && dt != QTT_C64)) return QTT_ERR_ARG;
+  if (ranks[0] != 1 || ranks[d] != 1) return QTT_ERR_ARG;
+  for (int k = 0; k < d; ++k)
+    if (mo[k] < 1 || mi[k] < 1 || ranks[k + 1] < 1) return QTT_ERR_ARG;
+  std::vector<int> no(mo, mo + d), ni(mi, mi + d), g(ranks, ranks + d + 1);
+  int st;
+  qtt_mpo* A = mpo_alloc(c, d, no, ni, g, dt, &st);
+  if (!A) return st;
+  cudaMemsetAsync(A->data, 0, A->bytes, c->stream);
+  *out = A;
+  return QTT_OK;
+}
+void qtt_mpo_destroy(qtt_mpo* A) { mpo_free(A); }
+int qtt_mpo_ranks(const qtt_mpo* A, int32_t* r) {
+  if (!A || !r) return QTT_ERR_ARG;
+  for (int k = 0; k <= A->d; ++k) r[k] = A->g[k];
+  return QTT_OK;
+}
+static size_t mpo_core_bytes(const qtt_mpo* A, int k) {
+  return (size_t)A->g[k] * A->no[k] * A->ni[k] * A->g[k + 1] * dtype_size(A->dtype);
+}
+int qtt_mpo_from_host(qtt_mpo* A, int k, const void* buf) {
+  if (!A || !buf || k < 0 || k >= A->d) return QTT_ERR_ARG;
+  if (cudaMemcpyAsync(core_ptr<char>(A, k), buf, mpo_core_bytes(A, k), cudaMemcpyHostToDevice, A->ctx->stream) !=
+      cudaSuccess)
+    return QTT_ERR_CUDA;
+  return cudaStreamSynchronize(A->ctx->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+int qtt_mpo_to_host(const qtt_mpo* A, int k, void* buf) {
+  if (!A || !buf || k < 0 || k >= A->d) return QTT_ERR_ARG;
+  return sync_read(A->ctx, buf, core_ptr<char>(A, k), mpo_core_bytes(A, k));
+}
+
+int tt_add(qtt_ctx* c, qtt_complex a, const qtt_tt* x, qtt_complex b, const qtt_tt* y, qtt_tt** z) {
+  if (!c || !valid_tt(x) || !valid_tt(y) || !z || !same_modes(x, y) || x->dtype != y->dtype) return QTT_ERR_ARG;
+  if (x->dtype == QTT_C128) return add_dev<double>(c, zc(a.re, a.im), x, zc(b.re, b.im), y, z);
+  return add_dev<float>(c, cc((float)a.re, (float)a.im), x, cc((float)b.re, (float)b.im), y, z);
+}
+
+int tt_hadamard(qtt_ctx* c, const qtt_tt* x, const qtt_tt* y, qtt_tt** z) {
+  if (!c || !valid_tt(x) || !valid_tt(y) || !z || !same_modes(x, y) || x->dtype != y->dtype) return QTT_ERR_ARG;
+  return x->dtype == QTT_C128 ? hadamard_dev<double>(c, x, y, z) : hadamard_dev<float>(c, x, y, z);
+}
+
+int tt_mpo_apply(qtt_ctx* c, const qtt_mpo* A, const qtt_tt* x, qtt_tt** y) {
+  if (!c || !A || !valid_tt(x) || !y || A->d != x->d || A->dtype != x->dtype) return QTT_ERR_ARG;
+  for (int k = 0; k < x->d; ++k)
+    if (A->ni[k] != x->n[k]) return QTT_ERR_ARG;
+  return x->dtype == QTT_C128 ? mpo_apply_dev<double>(c, A, x, y) : mpo_apply_dev<float>(c, A, x, y);
+}
+
+int tt_round(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, qtt_prec p, qtt_round_info* info, qtt_tt** y) {
+  if (!c || !valid_tt(x) || !y || !(eps >= 0)) return QTT_ERR_ARG;
+  TRY(check_prec(x->dtype, p));
+  return x->dtype == QTT_C128 ? round_det<double>(c, x, eps, max_rank, nullptr, info, y)
+                              : round_det<float>(c, x, eps, max_rank, nullptr, info, y);
+}
+
+int tt_round_sketched(qtt_ctx* c, int nterms, const qtt_complex* coef, const qtt_mpo* const* ops,
+                      const qtt_tt* const* xs, const qtt_tt* sketch, double eps, int max_rank, qtt_prec p,
+                      qtt_round_info* info, qtt_tt** y) {
+  if (!c || nterms < 1 || !coef || !xs || !valid_tt(sketch) || !y || !(eps >= 0)) return QTT_ERR_ARG;
+  for (int t = 0; t < nterms; ++t) {
+    if (!valid_tt(xs[t]) || xs[t]->dtype != sketch->dtype) return QTT_ERR_ARG;
+    if (ops && ops[t] && ops[t]->dtype != sketch->dtype) return QTT_ERR_ARG;
+  }
+  TRY(check_prec(sketch->dtype, p));
+  return sketch->dtype == QTT_C128
+             ? round_sketched<double>(c, nterms, coef, ops, xs, sketch, eps, max_rank, info, y)
+             : round_sketched<float>(c, nterms, coef, ops, xs, sketch, eps, max_rank, info, y);
+}
+
+int tt_dot(qtt_ctx* c, const qtt_tt* x, const qtt_tt* y, double out[2]) {
+  if (!c || !valid_tt(x) || !valid_tt(y) || !out || !same_modes(x, y) || x->dtype != y->dtype) return QTT_ERR_ARG;
+  return x->dtype == QTT_C128 ? dot_dev<double>(c, x, y, out) : dot_dev<float>(c, x, y, out);
+}
+
+int tt_norm(qtt_ctx* c, const qtt_tt* x, double* out) {
+  if (!c || !valid_tt(x) || !out) return QTT_ERR_ARG;
+  return x->dtype == QTT_C128 ? norm_dev<double>(c, x, out) : norm_dev<float>(c, x, out);
+}
+
+int tt_from_dense(qtt_ctx* c, int d, const int32_t* modes, const void* dense, double eps, int max_rank,
+                  qtt_tt** out) {
+  if (!c || d < 1 || !modes || !dense || !out || !(eps >= 0)) return QTT_ERR_ARG;
+  std::vector<int> m(modes, modes + d);
+  for (int v : m)
+    if (v < 1) return QTT_ERR_ARG;
+  return tt_svd_dev<double>(c, d, m, reinterpret_cast<const zc*>(dense), eps, max_rank, QTT_C128, out);
+}
+
+int qtt_qft_mpo(qtt_ctx* c, int nbits, int sign, double tol, qtt_mpo** out) {
+  if (!c || nbits < 1 || nbits > 13 || (sign != 1 && sign != -1) || !out || !(tol >= 0)) return QTT_ERR_ARG;
+  const int64_t total = (int64_t)1 << (2 * nbits);
+  void* dense;
+  TRY(dalloc(c, &dense, total * sizeof(zc)));
+  c->launches++;
+  int s = qtt_fill_qft_dense<double>(reinterpret_cast<zc*>(dense), nbits, (double)sign, c->stream);
+  qtt_tt* t = nullptr;
+  if (!s) s = tt_svd_dev<double>(c, nbits, std::vector<int>(nbits, 4), reinterpret_cast<zc*>(dense), tol, 0,
+                                 QTT_C128, &t);
+  dfree(c, dense);
+  if (s) return s;
+  std::vector<int> two(nbits, 2);
+  qtt_mpo* A = mpo_alloc(c, nbits, two, two, t->r, QTT_C128, &s);
+  if (!A) {
+    tt_free(t);
+    return s;
+  }
+  for (int k = 0; k < nbits; ++k)
+    cudaMemcpyAsync(core_ptr<char>(A, k), core_ptr<char>(t, k), (size_t)t->r[k] * 4 * t->r[k + 1] * sizeof(zc),
+                    cudaMemcpyDeviceToDevice, c->stream);
+  tt_free(t);
+  *out = A;
+  return QTT_OK;
+}
+
+}  // extern "C"
+
+// ========================================================= homogenisation
+
+namespace {
+
+struct Ops {
+  qtt_mpo* dCa = nullptr;    // (C1 - C0) (x) I
+  qtt_mpo* dCb = nullptr;    // (C2 - C1) (x) diag(chi)
+  qtt_mpo* gamma = nullptr;  // Green operator, momentum convention
+  qtt_mpo* q[3] = {nullptr, nullptr, nullptr};
+  qtt_mpo* qi[3] = {nullptr, nullptr, nullptr};
+  qtt_tt* chi = nullptr;     // spatial sites only
+  void release() {
+    mpo_free(dCa);
+    mpo_free(dCb);
+    mpo_free(gamma);
+    for (int i = 0; i < 3; ++i) {
+      mpo_free(q[i]);
+      mpo_free(qi[i]);
+    }
+    tt_free(chi);
+    *this = Ops();
+  }
+};
+
+int upload(qtt_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return QTT_ERR_CUDA;
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+// control-site operator core (1, nc, nc, 1) from a host matrix
+int ctrl_core(qtt_ctx* c, const double* Mh, int nc, zc* dst) {
+  std::vector<zc> h(nc * nc);
+  for (int i = 0; i < nc * nc; ++i) h[i] = zc(Mh[i], 0.0);
+  return upload(c, dst, h.data(), h.size() * sizeof(zc));
+}
+
+// site p (0-based, spatial) -> (dimension, bit position)
+void site_of(int p, int nbits, int interleaved, int* dim, int* pos) {
+  if (interleaved) {
+    *dim = p % 3;
+    *pos = p / 3;
+  } else {
+    *dim = p / nbits;
+    *pos = p % nbits;
+  }
+}
+
+int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2, const double* C0, double op_tol,
+              double k0, double lam0, double mu0, Ops* ops) {
+  const int nc = rve->ncomp, nb = rve->nbits, dsp = 3 * nb, d = dsp + 1;
+  const int64_t Nv = (int64_t)1 << dsp;
+  // phase indicator train
+  void *ind = nullptr, *dense = nullptr;
+  TRY(dalloc(c, &ind, Nv * sizeof(double)));
+  int s = upload(c, ind, rve->indicator, Nv * sizeof(double));
+  if (!s) s = dalloc(c, &dense, (size_t)Nv * nc * nc * sizeof(zc));
+  if (s) {
+    dfree(c, ind);
+    return s;
+  }
+  c->launches++;
+  s = qtt_fill_indicator_sites<double>(reinterpret_cast<double*>(ind), nb, rve->interleaved,
+                                       reinterpret_cast<zc*>(dense), c->stream);
+  if (!s) s = tt_svd_dev<double>(c, dsp, std::vector<int>(dsp, 2), reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128,
+                                 &ops->chi);
+  dfree(c, ind);
+  if (s) {
+    dfree(c, dense);
+    return s;
+  }
+  // Green operator train
+  c->launches++;
+  s = qtt_fill_green_dense<double>(reinterpret_cast<zc*>(dense), nb, nc, rve->interleaved, k0, lam0, mu0, c->stream);
+  qtt_tt* g = nullptr;
+  if (!s) {
+    std::vector<int> modes(d, 2);
+    modes[0] = nc * nc;
+    s = tt_svd_dev<double>(c, d, modes, reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128, &g);
+  }
+  dfree(c, dense);
+  if (s) return s;
+  std::vector<int> mo(d, 2), g1(d + 1, 1);
+  mo[0] = nc;
+  // Gamma: control core reshaped, spatial cores diagonal
+  ops->gamma = mpo_alloc(c, d, mo, mo, g->r, QTT_C128, &s);
+  if (!ops->gamma) {
+    tt_free(g);
+    return s;
+  }
+  cudaMemcpyAsync(core_ptr<char>(ops->gamma, 0), core_ptr<char>(g, 0), (size_t)nc * nc * g->r[1] * sizeof(zc),
+                  cudaMemcpyDeviceToDevice, c->stream);
+  for (int k = 1; k < d; ++k) {
+    c->launches++;
+    TRY(qtt_diag_mpo_core<double>(core_ptr<zc>(g, k), g->r[k], 2, g->r[k + 1], core_ptr<zc>(ops->gamma, k), c->stream));
+  }
+  tt_free(g);
+  // stiffness contrast operators
+  std::vector<double> A(nc * nc), B(nc * nc);
+  for (int i = 0; i < nc * nc; ++i) {
+    A[i] = C1[i] - C0[i];
+    B[i] = C2[i] - C1[i];
+  }
+  ops->dCa = mpo_alloc(c, d, mo, mo, g1, QTT_C128, &s);
+  if (!ops->dCa) return s;
+  TRY(ctrl_core(c, A.data(), nc, core_ptr<zc>(ops->dCa, 0)));
+  for (int k = 1; k < d; ++k) {
+    c->launches++;
+    TRY(qtt_identity_core<double>(1, 2, core_ptr<zc>(ops->dCa, k), c->stream));
+  }
+  // bond k of the full operator sits between site k-1 and site k; spatial
+  // site k holds phase core k-1, so bond k equals the phase train's bond k-1
+  std::vector<int> gb(d + 1, 1);
+  for (int k = 1; k <= d; ++k) gb[k] = ops->chi->r[k - 1];
+  ops->dCb = mpo_alloc(c, d, mo, mo, gb, QTT_C128, &s);
+  if (!ops->dCb) return s;
+  TRY(ctrl_core(c, B.data(), nc, core_ptr<zc>(ops->dCb, 0)));
+  for (int k = 1; k < d; ++k) {
+    c->launches++;
+    TRY(qtt_diag_mpo_core<double>(core_ptr<zc>(ops->chi, k - 1), ops->chi->r[k - 1], 2, ops->chi->r[k],
+                                  core_ptr<zc>(ops->dCb, k), c->stream));
+  }
+  // superfast Fourier transform, one dimension at a time
+  qtt_mpo* q1 = nullptr;
+  TRY(qtt_qft_mpo(c, nb, -1, 1e-12, &q1));
+  for (int dim = 0; dim < 3; ++dim) {
+    // the bond of the one-dimensional train is carried unchanged through the
+    // sites of the other dimensions (identity cores)
+    std::vector<int> gq(d + 1, 1);
+    int cur = 1;
+    for (int p = 0; p < dsp; ++p) {
+      int dm, pos;
+      site_of(p, nb, rve->interleaved, &dm, &pos);
+      if (dm == dim) cur = q1->g[pos + 1];
+      gq[p + 2] = cur;
+    }
+    qtt_mpo* Q = mpo_alloc(c, d, mo, mo, gq, QTT_C128, &s);
+    qtt_mpo* Qi = Q ? mpo_alloc(c, d, mo, mo, gq, QTT_C128, &s) : nullptr;
+    if (!Q || !Qi) {
+      mpo_free(Q);
+      mpo_free(q1);
+      return s;
+    }
+    c->launches++;
+    qtt_identity_core<double>(1, nc, core_ptr<zc>(Q, 0), c->stream);
+    for (int p = 0; p < dsp; ++p) {
+      int dm, pos;
+      site_of(p, nb, rve->interleaved, &dm, &pos);
+      const int k = p + 1;
+      if (dm == dim) {
+        cudaMemcpyAsync(core_ptr<char>(Q, k), core_ptr<char>(q1, pos),
+                        (size_t)q1->g[pos] * 4 * q1->g[pos + 1] * sizeof(zc), cudaMemcpyDeviceToDevice, c->stream);
+      } else {
+        c->launches++;
+        qtt_identity_core<double>(gq[k], 2, core_ptr<zc>(Q, k), c->stream);
+      }
+    }
+    for (int k = 0; k < d; ++k) {
+      c->launches++;
+      qtt_adjoint_core<double>(core_ptr<zc>(Q, k), gq[k], mo[k], mo[k], gq[k + 1], core_ptr<zc>(Qi, k), c->stream);
+    }
+    ops->q[dim] = Q;
+    ops->qi[dim] = Qi;
+  }
+  mpo_free(q1);
+  return QTT_OK;
+}
+
+template <class R>
+int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2h, Ops& O, double tol, int max_rank,
+             const ms_opts& o, qtt_dtype dt, double* C_eff, ms_report* rep) {
+  typedef cplx<R> C;
+  const int nc = rve->ncomp, nb = rve->nbits, dsp = 3 * nb, d = dsp + 1;
+  std::vector<int> modes(d, 2);
+  modes[0] = nc;
+  const int ell = max_rank + std::max(0, (int)o.oversample);
+  const double Nvox = ldexp(1.0, dsp);
+  uint64_t call = 1;
+  int st;
+  // unit E trains, probe trains e_I (x) ones, e_I (x) chi
+  auto make_rank1 = [&](const std::vector<double>& ctrl, const qtt_tt* spatial, qtt_tt** out) -> int {
+    std::vector<int> r(d + 1, 1);
+    if (spatial)
+      for (int k = 1; k <= d; ++k) r[k] = spatial->r[k - 1];
+    qtt_tt* x = tt_alloc(c, d, modes, r, dt, &st);
+    if (!x) return st;
+    std::vector<C> h(nc);
+    for (int i = 0; i < nc; ++i) h[i] = C((R)ctrl[i], 0);
+    TRY(upload(c, core_ptr<char>(x, 0), h.data(), nc * sizeof(C)));
+    for (int k = 1; k < d; ++k) {
+      if (spatial) {
+        int64_t cnt = (int64_t)spatial->r[k - 1] * 2 * spatial->r[k];
+        if (dt == QTT_C128) {
+          cudaMemcpyAsync(core_ptr<char>(x, k), core_ptr<char>(spatial, k - 1), cnt * sizeof(zc),
+                          cudaMemcpyDeviceToDevice, c->stream);
+        } else {
+          c->launches++;
+          qtt_convert_z2c(core_ptr<zc>(spatial, k - 1), core_ptr<cc>(x, k), cnt, c->stream);
+        }
+      } else {
+        C two[2] = {C(1, 0), C(1, 0)};
+        TRY(upload(c, core_ptr<char>(x, k), two, sizeof(two)));
+      }
+    }
+    *out = x;
+    return QTT_OK;
+  };
+  // operators in the working dtype
+  qtt_mpo *dCa, *dCb, *G, *Q[3], *Qi[3];
+  TRY(convert_mpo(c, O.dCa, dt, &dCa));
+  TRY(convert_mpo(c, O.dCb, dt, &dCb));
+  TRY(convert_mpo(c, O.gamma, dt, &G));
+  for (int i = 0; i < 3; ++i) {
+    TRY(convert_mpo(c, O.q[i], dt, &Q[i]));
+    TRY(convert_mpo(c, O.qi[i], dt, &Qi[i]));
+  }
+  struct Free {
+    std::vector<qtt_mpo*> m;
+    ~Free() {
+      for (auto* p : m) mpo_free(p);
+    }
+  } fr{{dCa, dCb, G, Q[0], Q[1], Q[2], Qi[0], Qi[1], Qi[2]}};
+
+  auto sk_round = [&](int T, const qtt_complex* cf, const qtt_mpo* const* A, const qtt_tt* const* X,
+                      qtt_tt** out) -> int {
+    qtt_tt* S = nullptr;
+    TRY(make_sketch(c, modes, ell, dt, o.seed, call++, &S));
+    qtt_round_info info;
+    int s = round_sketched<R>(c, T, cf, A, X, S, o.eps, max_rank, &info, out);
+    tt_free(S);
+    if (!s && rep) rep->max_rank_seen = std::max(rep->max_rank_seen, info.max_rank_out);
+    return s;
+  };
+  double sig_im = 0;
+  for (int lc = 0; lc < nc; ++lc) {
+    if (!(o.load_mask & (1 << lc))) continue;
+    std::vector<double> e(nc, 0.0);
+    e[lc] = 1.0;
+    qtt_tt* E = nullptr;
+    TRY(make_rank1(e, nullptr, &E));
+    const double normE = sqrt(Nvox);
+    qtt_tt* x = nullptr;
+    TRY(convert_tt(c, E, dt, &x));
+    int it = 0;
+    double res = 1.0;
+    const qtt_complex one = {1.0, 0.0};
+    for (it = 1; it <= o.max_iter; ++it) {
+      qtt_tt* tau = nullptr;
+      {
+        qtt_complex cf[2] = {one, one};
+        const qtt_mpo* A[2] = {dCa, dCb};
+        const qtt_tt* X[2] = {x, x};
+        TRY(sk_round(2, cf, A, X, &tau));
+      }
+      qtt_tt* h = tau;
+      for (int dim = 0; dim < 3; ++dim) {
+        qtt_tt* hn = nullptr;
+        const qtt_mpo* A[1] = {Q[dim]};
+        const qtt_tt* X[1] = {h};
+        int s = sk_round(1, &one, A, X, &hn);
+        tt_free(h);
+        if (s) return s;
+        h = hn;
+      }
+      {
+        qtt_tt* hn = nullptr;
+        const qtt_mpo* A[1] = {G};
+        const qtt_tt* X[1] = {h};
+        int s = sk_round(1, &one, A, X, &hn);
+        tt_free(h);
+        if (s) return s;
+        h = hn;
+      }
+      for (int dim = 2; dim >= 0; --dim) {
+        qtt_tt* hn = nullptr;
+        const qtt_mpo* A[1] = {Qi[dim]};
+        const qtt_tt* X[1] = {h};
+        int s = sk_round(1, &one, A, X, &hn);
+        tt_free(h);
+        if (s) return s;
+        h = hn;
+      }
+      // eps_{m+1} = round(E - S^{-1} eps^)
+      qtt_tt *sum = nullptr, *xn = nullptr;
+      int s = add_dev<R>(c, C(1, 0), E, C(-1, 0), h, &sum);
+      tt_free(h);
+      if (s) return s;
+      s = round_det<R>(c, sum, o.eps, max_rank, nullptr, nullptr, &xn);
+      tt_free(sum);
+      if (s) return s;
+      // relative change, on the difference train (orthogonalisation, no cancellation)
+      qtt_tt* diff = nullptr;
+      TRY(add_dev<R>(c, C(1, 0), xn, C(-1, 0), x, &diff));
+      double dn = 0;
+      s = norm_dev<R>(c, diff, &dn);
+      tt_free(diff);
+      if (s) return s;
+      res = dn / normE;
+      tt_free(x);
+      x = xn;
+      if (res < tol && it >= std::max(1, (int)o.min_iter)) break;
+    }
+    if (it > o.max_iter) it = o.max_iter;
+    // sigma = C1 <eps> + (C2 - C1) <chi eps>
+    std::vector<double> m1(2 * nc), m2(2 * nc);
+    for (int I = 0; I < nc; ++I) {
+      std::vector<double> eI(nc, 0.0);
+      eI[I] = 1.0;
+      qtt_tt *u = nullptr, *v = nullptr;
+      TRY(make_rank1(eI, nullptr, &u));
+      TRY(make_rank1(eI, O.chi, &v));
+      double a[2], b[2];
+      int s = dot_dev<R>(c, u, x, a);
+      if (!s) s = dot_dev<R>(c, v, x, b);
+      tt_free(u);
+      tt_free(v);
+      if (s) return s;
+      m1[2 * I] = a[0] / Nvox;
+      m1[2 * I + 1] = a[1] / Nvox;
+      m2[2 * I] = b[0] / Nvox;
+      m2[2 * I + 1] = b[1] / Nvox;
+    }
+    for (int I = 0; I < nc; ++I) {
+      double sr = 0, si = 0;
+      for (int J = 0; J < nc; ++J) {
+        sr += C1h[I * nc + J] * m1[2 * J] + (C2h[I * nc + J] - C1h[I * nc + J]) * m2[2 * J];
+        si += C1h[I * nc + J] * m1[2 * J + 1] + (C2h[I * nc + J] - C1h[I * nc + J]) * m2[2 * J + 1];
+      }
+      C_eff[I * nc + lc] = sr;
+      sig_im = std::max(sig_im, fabs(si));
+    }
+    if (rep) {
+      rep->iterations[lc] = it;
+      rep->residual[lc] = res;
+    }
+    tt_free(x);
+    tt_free(E);
+  }
+  if (rep) rep->sigma_imag_max = sig_im;
+  return QTT_OK;
+}
+
+}  // namespace
+
+extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, double tol, int max_rank,
+                             const ms_opts* o, double* C_eff, ms_report* rep) {
+  if (!c || !rve || !C0 || !o || !C_eff || max_rank < 1) return QTT_ERR_ARG;
+  if ((rve->ncomp != 3 && rve->ncomp != 6) || rve->nbits < 1 || rve->nbits > 10 || !rve->indicator)
+    return QTT_ERR_ARG;
+  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32) return QTT_ERR_ARG;
+  const int nc = rve->ncomp;
+  std::vector<double> C1(nc * nc, 0.0), C2(nc * nc, 0.0);
+  double k0 = 0, lam0 = 0, mu0 = 0;
+  if (nc == 3) {
+    for (int i = 0; i < 3; ++i) {
+      C1[i * 3 + i] = rve->k1;
+      C2[i * 3 + i] = rve->k2;
+    }
+    k0 = C0[0];
+    if (!(k0 > 0)) return QTT_ERR_ARG;
+  } else {
+    auto iso = [](double lam, double mu, double* M) {
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i * 6 + j] = lam + (i == j ? 2 * mu : 0.0);
+      for (int i = 3; i < 6; ++i) M[i * 6 + i] = mu;
+    };
+    iso(rve->lam1, rve->mu1, C1.data());
+    iso(rve->lam2, rve->mu2, C2.data());
+    lam0 = C0[1];
+    mu0 = C0[3 * 6 + 3];
+    if (!(mu0 > 0)) return QTT_ERR_ARG;
+  }
+  if (rep) memset(rep, 0, sizeof(*rep));
+  for (int i = 0; i < nc * nc; ++i) C_eff[i] = 0.0;
+  const int64_t l0 = c->launches;
+  auto t0 = std::chrono::steady_clock::now();
+  Ops O;
+  int s = build_ops(c, rve, C1.data(), C2.data(), C0, o->op_tol > 0 ? o->op_tol : 1e-10, k0, lam0, mu0, &O);
+  if (s) {
+    O.release();
+    return s;
+  }
+  cudaStreamSynchronize(c->stream);
+  auto t1 = std::chrono::steady_clock::now();
+  if (o->prec == QTT_PREC_F64)
+    s = ms_solve<double>(c, rve, C1.data(), C2.data(), O, tol, max_rank, *o, QTT_C128, C_eff, rep);
+  else
+    s = ms_solve<float>(c, rve, C1.data(), C2.data(), O, tol, max_rank, *o, QTT_C64, C_eff, rep);
+  cudaStreamSynchronize(c->stream);
+  auto t2 = std::chrono::steady_clock::now();
+  O.release();
+  if (rep) {
+    rep->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    rep->iterate_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    rep->kernel_launches = c->launches - l0;
+  }
+  if (cudaGetLastError() != cudaSuccess) return QTT_ERR_CUDA;
+  return s;
+}

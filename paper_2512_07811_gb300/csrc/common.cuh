@@ -1,0 +1,81 @@
+// Shared device helpers for the QTT kernels: complex arithmetic over double and
+// float, launch-error plumbing.  Complex numbers are stored interleaved
+// (re, im), 8- or 16-byte aligned, exactly like C99 `double _Complex` /
+// `float _Complex`.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define QTT_HD __host__ __device__ __forceinline__
+
+template <class R>
+struct alignas(2 * sizeof(R)) cplx {
+  R re, im;
+  QTT_HD cplx() {}
+  QTT_HD cplx(R r, R i = R(0)) : re(r), im(i) {}
+};
+
+typedef cplx<double> zc;   // complex double
+typedef cplx<float> cc;    // complex float
+
+template <class R> QTT_HD cplx<R> operator+(cplx<R> a, cplx<R> b) { return cplx<R>(a.re + b.re, a.im + b.im); }
+template <class R> QTT_HD cplx<R> operator-(cplx<R> a, cplx<R> b) { return cplx<R>(a.re - b.re, a.im - b.im); }
+template <class R> QTT_HD cplx<R> operator-(cplx<R> a) { return cplx<R>(-a.re, -a.im); }
+template <class R> QTT_HD cplx<R> operator*(cplx<R> a, cplx<R> b) {
+  return cplx<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class R> QTT_HD cplx<R> operator*(R s, cplx<R> a) { return cplx<R>(s * a.re, s * a.im); }
+template <class R> QTT_HD cplx<R> conjg(cplx<R> a) { return cplx<R>(a.re, -a.im); }
+template <class R> QTT_HD R abs2(cplx<R> a) { return a.re * a.re + a.im * a.im; }
+// a += b * c   (fused where the hardware fuses)
+template <class R> QTT_HD void cfma(cplx<R>& a, cplx<R> b, cplx<R> c) {
+  a.re = fma(b.re, c.re, a.re);
+  a.re = fma(-b.im, c.im, a.re);
+  a.im = fma(b.re, c.im, a.im);
+  a.im = fma(b.im, c.re, a.im);
+}
+// a += conj(b) * c
+template <class R> QTT_HD void cfma_conj(cplx<R>& a, cplx<R> b, cplx<R> c) {
+  a.re = fma(b.re, c.re, a.re);
+  a.re = fma(b.im, c.im, a.re);
+  a.im = fma(b.re, c.im, a.im);
+  a.im = fma(-b.im, c.re, a.im);
+}
+
+// Status codes shared with the C-ABI (qtt.h).
+#define QTT_OK 0
+#define QTT_ERR_ARG -1
+#define QTT_ERR_OOM -2
+#define QTT_ERR_RANK -3
+#define QTT_ERR_TIMEOUT -4
+#define QTT_ERR_NOT_CONVERGED -5
+#define QTT_ERR_NAN -6
+#define QTT_ERR_CUDA -7
+#define QTT_ERR_UNSUPPORTED -8
+
+// Multi-index GEMM descriptor.  Every logical index of a contraction is a
+// pair of sub-indices (outer, inner) with sizes (n1, n2) and element strides
+// (s1, s2): logical value v maps to offset (v / n2) * s1 + (v % n2) * s2.
+struct MIdx {
+  int64_t n1, n2;   // sizes
+  int64_t s1, s2;   // strides (elements)
+};
+
+QTT_HD int64_t midx_off(const MIdx& m, int64_t v) {
+  if (m.n2 == 1) return v * m.s1;
+  int64_t a = v / m.n2;
+  int64_t b = v - a * m.n2;
+  return a * m.s1 + b * m.s2;
+}
+QTT_HD int64_t midx_size(const MIdx& m) { return m.n1 * m.n2; }
+
+// C[b][m][n] = alpha * sum_k opA(A)[b][m][k] * opB(B)[b][k][n] + beta * C[b][m][n]
+// with every one of b, m, n, k a two-level multi-index per operand.
+struct GemmDesc {
+  MIdx bA, mA, kA;   // A strides for batch, m, k
+  MIdx bB, kB, nB;   // B strides for batch, k, n
+  MIdx bC, mC, nC;   // C strides for batch, m, n
+  int64_t M, N, K, batch;
+  int conjA, conjB;  // conjugate A / B elements
+};

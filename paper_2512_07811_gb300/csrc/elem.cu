@@ -1,0 +1,498 @@
+// Elementwise and placement kernels of the tensor-train path, plus the dense
+// operator fills used when building the Fourier and Green trains on the device.
+//
+// Core layout: (r_{k-1}, n_k, r_k) row-major.  Combined bonds put the first
+// operand's index first (major).
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned nblocks(int64_t count) {
+  int64_t b = (count + TPB - 1) / TPB;
+  if (b > (int64_t)1 << 30) b = (int64_t)1 << 30;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// complex product with separately rounded terms (no contraction to FMA), so
+// that scaling by exactly representable factors reproduces the host result.
+__device__ __forceinline__ zc mul_rn(zc a, zc b) {
+  return zc(__dsub_rn(__dmul_rn(a.re, b.re), __dmul_rn(a.im, b.im)),
+            __dadd_rn(__dmul_rn(a.re, b.im), __dmul_rn(a.im, b.re)));
+}
+__device__ __forceinline__ cc mul_rn(cc a, cc b) {
+  return cc(__fsub_rn(__fmul_rn(a.re, b.re), __fmul_rn(a.im, b.im)),
+            __fadd_rn(__fmul_rn(a.re, b.im), __fmul_rn(a.im, b.re)));
+}
+
+// dst[(off0 + a), j, (off1 + c)] = scale * src[a, j, c];  dst row length n*d1
+template <class R>
+__global__ void place_block_kernel(const cplx<R>* __restrict__ src, int64_t s0, int64_t n, int64_t s1,
+                                   cplx<R>* __restrict__ dst, int64_t d1, int64_t off0, int64_t off1,
+                                   cplx<R> scale, int unit) {
+  const int64_t total = s0 * n * s1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = e % s1;
+    int64_t t = e / s1;
+    int64_t j = t % n;
+    int64_t a = t / n;
+    cplx<R> v = src[e];
+    if (!unit) v = mul_rn(scale, v);
+    dst[((off0 + a) * n + j) * d1 + off1 + c] = v;
+  }
+}
+
+// out[(a0i, b0i), i, (a1i, b1i)] = x[a0i, i, a1i] * y[b0i, i, b1i]
+template <class R>
+__global__ void hadamard_kernel(const cplx<R>* __restrict__ x, int64_t a0, int64_t a1,
+                                const cplx<R>* __restrict__ y, int64_t b0, int64_t b1, int64_t n,
+                                cplx<R>* __restrict__ out) {
+  const int64_t o1 = a1 * b1;
+  const int64_t total = a0 * b0 * n * o1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = e % o1;
+    int64_t t = e / o1;
+    int64_t i = t % n;
+    int64_t r = t / n;
+    int64_t ra = r / b0, rb = r - ra * b0;
+    int64_t ca = c / b1, cb = c - ca * b1;
+    out[e] = mul_rn(x[(ra * n + i) * a1 + ca], y[(rb * n + i) * b1 + cb]);
+  }
+}
+
+// out[(g0i, a0i), i, (g1i, a1i)] = sum_j D[g0i, i, j, g1i] * X[a0i, j, a1i]
+template <class R>
+__global__ void mpo_core_kernel(const cplx<R>* __restrict__ D, int64_t g0, int64_t no, int64_t ni,
+                                int64_t g1, const cplx<R>* __restrict__ X, int64_t a0, int64_t a1,
+                                cplx<R>* __restrict__ out) {
+  const int64_t o1 = g1 * a1;
+  const int64_t total = g0 * a0 * no * o1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = e % o1;
+    int64_t t = e / o1;
+    int64_t i = t % no;
+    int64_t r = t / no;
+    int64_t gr = r / a0, ar = r - gr * a0;
+    int64_t gc = c / a1, ac = c - gc * a1;
+    cplx<R> acc(0, 0);
+    for (int64_t j = 0; j < ni; ++j)
+      cfma(acc, D[((gr * no + i) * ni + j) * g1 + gc], X[(ar * ni + j) * a1 + ac]);
+    out[e] = acc;
+  }
+}
+
+template <class R>
+__global__ void scale_kernel(cplx<R>* x, int64_t count, cplx<R> s) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    x[e] = mul_rn(s, x[e]);
+}
+
+// single-block sum of squared moduli in double (deterministic order per launch shape)
+template <class R>
+__global__ void sumsq_kernel(const cplx<R>* __restrict__ x, int64_t count, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < count; e += blockDim.x) {
+    double re = (double)x[e].re, im = (double)x[e].im;
+    acc = fma(re, re, acc);
+    acc = fma(im, im, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    *out = s;
+  }
+}
+
+__global__ void z2c_kernel(const zc* __restrict__ in, cc* __restrict__ out, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = cc((float)in[e].re, (float)in[e].im);
+}
+__global__ void c2z_kernel(const cc* __restrict__ in, zc* __restrict__ out, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = zc((double)in[e].re, (double)in[e].im);
+}
+
+template <class R>
+__global__ void copy_strided_kernel(const cplx<R>* __restrict__ in, MIdx rows, MIdx cols, int64_t nrows,
+                                    int64_t ncols, int conj_in, cplx<R>* __restrict__ out, int64_t ldo) {
+  const int64_t total = nrows * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / ncols, c = e - i * ncols;
+    cplx<R> v = in[midx_off(rows, i) + midx_off(cols, c)];
+    if (conj_in) v.im = -v.im;
+    out[i * ldo + c] = v;
+  }
+}
+
+// x[i, :] *= sv[i]  (or /= sv[i] when invert; rows with sv[i] == 0 are zeroed)
+template <class R>
+__global__ void scale_rows_kernel(cplx<R>* x, int64_t rows, int64_t cols, int64_t ld, const R* sv, int invert) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / cols, c = e - i * cols;
+    R s = sv[i];
+    R f = invert ? (s > R(0) ? R(1) / s : R(0)) : s;
+    cplx<R>& v = x[i * ld + c];
+    v = cplx<R>(v.re * f, v.im * f);
+  }
+}
+
+template <class R>
+__global__ void isfinite_kernel(const cplx<R>* __restrict__ x, int64_t count, int* flag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (!isfinite(x[e].re) || !isfinite(x[e].im)) atomicExch(flag, 1);
+  }
+}
+
+// Q_n of the superfast Fourier transform in site order: entry index
+// s = sum_a (m_a*2 + j_a) 4^(n-1-a), value exp(sign 2 pi i sum_{b<=a} j_a m_b 2^(b-a-1)) / sqrt(2^n).
+template <class R>
+__global__ void qft_dense_kernel(cplx<R>* out, int n, double sign) {
+  const int64_t total = (int64_t)1 << (2 * n);
+  const double norm = pow(2.0, -0.5 * n);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double phase = 0.0;  // in units of full turns
+    for (int a = 0; a < n; ++a) {
+      int ja = (int)((e >> (2 * (n - 1 - a))) & 1);
+      if (!ja) continue;
+      for (int b = 0; b <= a; ++b) {
+        int mb = (int)((e >> (2 * (n - 1 - b) + 1)) & 1);
+        if (mb) phase += ldexp(1.0, b - a - 1);
+      }
+    }
+    phase -= floor(phase);
+    double sn, cs;
+    sincospi(2.0 * sign * phase, &sn, &cs);
+    out[e] = cplx<R>((R)(cs * norm), (R)(sn * norm));
+  }
+}
+
+// weight of spatial site p (0-based) and its dimension, for the given ordering
+__device__ __forceinline__ void site_info(int p, int nbits, int interleaved, int* dim, int* pos) {
+  if (interleaved) {
+    *dim = p % 3;
+    *pos = p / 3;
+  } else {
+    *dim = p / nbits;
+    *pos = p % nbits;
+  }
+}
+
+// Dense Green operator in momentum site order: out[IJ * 2^(3n) + s], s the
+// site multi-index (site 0 slowest).  In momentum space site (dim, pos)
+// carries the bit of weight 2^pos of the frequency index k_dim (Sec. 3.2:
+// bits reversed per dimension).  Frequencies xi = k for k < N/2 else k - N.
+template <class R>
+__global__ void green_dense_kernel(cplx<R>* out, int nbits, int ncomp, int interleaved, double k0,
+                                   double lam0, double mu0) {
+  const int d = 3 * nbits;
+  const int64_t total = (int64_t)1 << d;
+  const int64_t N = (int64_t)1 << nbits;
+  const int vi[6] = {0, 1, 2, 1, 0, 0};
+  const int vj[6] = {0, 1, 2, 2, 2, 1};
+  const double vw[6] = {1, 1, 1, 2, 2, 2};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k[3] = {0, 0, 0};
+    for (int p = 0; p < d; ++p) {
+      int bit = (int)((s >> (d - 1 - p)) & 1);
+      int dim, pos;
+      site_info(p, nbits, interleaved, &dim, &pos);
+      k[dim] |= (int64_t)bit << pos;
+    }
+    double xi[3];
+    for (int a = 0; a < 3; ++a) xi[a] = (double)(k[a] < N / 2 ? k[a] : k[a] - N);
+    double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    if (ncomp == 3) {
+      for (int I = 0; I < 3; ++I)
+        for (int J = 0; J < 3; ++J) {
+          double g = q2 > 0 ? xi[I] * xi[J] / (k0 * q2) : 0.0;
+          out[(int64_t)(I * 3 + J) * total + s] = cplx<R>((R)g, R(0));
+        }
+    } else {
+      double coef = (lam0 + mu0) / (mu0 * (lam0 + 2 * mu0));
+      for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) {
+          double g = 0.0;
+          if (q2 > 0) {
+            int i = vi[I], j = vj[I], kk = vi[J], h = vj[J];
+            double t = 0.0;
+            if (kk == i) t += xi[h] * xi[j];
+            if (h == i) t += xi[kk] * xi[j];
+            if (kk == j) t += xi[h] * xi[i];
+            if (h == j) t += xi[kk] * xi[i];
+            g = t / (4.0 * mu0 * q2) - coef * xi[i] * xi[j] * xi[kk] * xi[h] / (q2 * q2);
+            g *= vw[I] * vw[J];
+          }
+          out[(int64_t)(I * 6 + J) * total + s] = cplx<R>((R)g, R(0));
+        }
+    }
+  }
+}
+
+// Phase indicator (N^3 doubles, x slowest, MSB-first bits) to site order.
+template <class R>
+__global__ void indicator_sites_kernel(const double* __restrict__ ind, int nbits, int interleaved,
+                                       cplx<R>* __restrict__ out) {
+  const int d = 3 * nbits;
+  const int64_t total = (int64_t)1 << d;
+  const int64_t N = (int64_t)1 << nbits;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t x[3] = {0, 0, 0};
+    for (int p = 0; p < d; ++p) {
+      int bit = (int)((s >> (d - 1 - p)) & 1);
+      int dim, pos;
+      site_info(p, nbits, interleaved, &dim, &pos);
+      x[dim] |= (int64_t)bit << (nbits - 1 - pos);
+    }
+    out[s] = cplx<R>((R)ind[(x[0] * N + x[1]) * N + x[2]], R(0));
+  }
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): counter-based generator, 10 rounds with the published
+// multipliers and Weyl key increments.
+__device__ __forceinline__ void philox4x32_10(uint32_t ctr[4], uint32_t key[2]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(M0, ctr[0]), lo0 = M0 * ctr[0];
+    uint32_t hi1 = __umulhi(M1, ctr[2]), lo1 = M1 * ctr[2];
+    uint32_t n0 = hi1 ^ ctr[1] ^ key[0];
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ ctr[3] ^ key[1];
+    uint32_t n3 = lo0;
+    ctr[0] = n0; ctr[1] = n1; ctr[2] = n2; ctr[3] = n3;
+    key[0] += W0;
+    key[1] += W1;
+  }
+}
+
+// Real Gaussian entries N(0, scale^2) stored as complex with zero imaginary
+// part: Box-Muller on two 32-bit uniforms per entry; counter = (index, stream).
+template <class R>
+__global__ void gaussian_kernel(cplx<R>* out, int64_t count, uint64_t seed, uint64_t stream, double scale) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t ctr[4] = {(uint32_t)e, (uint32_t)((uint64_t)e >> 32), (uint32_t)stream, (uint32_t)(stream >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    philox4x32_10(ctr, key);
+    double u1 = ((double)ctr[0] + 0.5) * 2.3283064365386963e-10;   // (0, 1)
+    double u2 = ((double)ctr[1] + 0.5) * 2.3283064365386963e-10;
+    double rad = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    out[e] = cplx<R>((R)(scale * rad * cs), R(0));
+  }
+}
+
+// D[a, i, i, b] = X[a, i, b], zero elsewhere (Sec. 2.1, Eq. tt_to_tto)
+template <class R>
+__global__ void diag_mpo_kernel(const cplx<R>* __restrict__ X, int64_t r0, int64_t n, int64_t r1,
+                                cplx<R>* __restrict__ D) {
+  const int64_t total = r0 * n * n * r1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = e % r1;
+    int64_t t = e / r1;
+    int64_t j = t % n;
+    t /= n;
+    int64_t i = t % n;
+    int64_t a = t / n;
+    D[e] = (i == j) ? X[(a * n + i) * r1 + b] : cplx<R>(0, 0);
+  }
+}
+
+// identity operator core carrying a bond of size g: D[c, i, j, c'] = delta_ij delta_cc'
+template <class R>
+__global__ void identity_core_kernel(int64_t g, int64_t n, cplx<R>* __restrict__ D) {
+  const int64_t total = g * n * n * g;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c2 = e % g;
+    int64_t t = e / g;
+    int64_t j = t % n;
+    t /= n;
+    int64_t i = t % n;
+    int64_t c = t / n;
+    D[e] = cplx<R>((i == j && c == c2) ? R(1) : R(0), R(0));
+  }
+}
+
+// adjoint operator core: out[c, j, i, c'] = conj(D[c, i, j, c'])
+template <class R>
+__global__ void adjoint_core_kernel(const cplx<R>* __restrict__ D, int64_t g0, int64_t no, int64_t ni,
+                                    int64_t g1, cplx<R>* __restrict__ out) {
+  const int64_t total = g0 * no * ni * g1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c2 = e % g1;
+    int64_t t = e / g1;
+    int64_t j = t % ni;
+    t /= ni;
+    int64_t i = t % no;
+    int64_t c = t / no;
+    out[((c * ni + j) * no + i) * g1 + c2] = conjg(D[e]);
+  }
+}
+
+}  // namespace
+
+#define CHECK_LAUNCH() return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA
+
+template <class R>
+int qtt_place_block(const cplx<R>* src, int64_t s0, int64_t n, int64_t s1, cplx<R>* dst, int64_t d1,
+                    int64_t off0, int64_t off1, cplx<R> scale, cudaStream_t s) {
+  int64_t total = s0 * n * s1;
+  if (total <= 0) return QTT_OK;
+  int unit = (scale.re == R(1) && scale.im == R(0));
+  place_block_kernel<R><<<nblocks(total), TPB, 0, s>>>(src, s0, n, s1, dst, d1, off0, off1, scale, unit);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_hadamard_core(const cplx<R>* x, int64_t a0, int64_t a1, const cplx<R>* y, int64_t b0, int64_t b1,
+                      int64_t n, cplx<R>* out, cudaStream_t s) {
+  int64_t total = a0 * b0 * n * a1 * b1;
+  if (total <= 0) return QTT_OK;
+  hadamard_kernel<R><<<nblocks(total), TPB, 0, s>>>(x, a0, a1, y, b0, b1, n, out);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_mpo_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64_t g1, const cplx<R>* X,
+                 int64_t a0, int64_t a1, cplx<R>* out, cudaStream_t s) {
+  int64_t total = g0 * a0 * no * g1 * a1;
+  if (total <= 0) return QTT_OK;
+  mpo_core_kernel<R><<<nblocks(total), TPB, 0, s>>>(D, g0, no, ni, g1, X, a0, a1, out);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_scale(cplx<R>* x, int64_t count, cplx<R> sc, cudaStream_t s) {
+  if (count <= 0) return QTT_OK;
+  scale_kernel<R><<<nblocks(count), TPB, 0, s>>>(x, count, sc);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_sumsq(const cplx<R>* x, int64_t count, double* out, cudaStream_t s) {
+  sumsq_kernel<R><<<1, 1024, 0, s>>>(x, count, out);
+  CHECK_LAUNCH();
+}
+int qtt_convert_z2c(const zc* in, cc* out, int64_t count, cudaStream_t s) {
+  if (count <= 0) return QTT_OK;
+  z2c_kernel<<<nblocks(count), TPB, 0, s>>>(in, out, count);
+  CHECK_LAUNCH();
+}
+int qtt_convert_c2z(const cc* in, zc* out, int64_t count, cudaStream_t s) {
+  if (count <= 0) return QTT_OK;
+  c2z_kernel<<<nblocks(count), TPB, 0, s>>>(in, out, count);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_copy_strided(const cplx<R>* in, MIdx rows, MIdx cols, int64_t nrows, int64_t ncols, int conj_in,
+                     cplx<R>* out, int64_t ldo, cudaStream_t s) {
+  int64_t total = nrows * ncols;
+  if (total <= 0) return QTT_OK;
+  copy_strided_kernel<R><<<nblocks(total), TPB, 0, s>>>(in, rows, cols, nrows, ncols, conj_in, out, ldo);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_scale_rows(cplx<R>* x, int64_t rows, int64_t cols, int64_t ld, const R* sv, int invert, cudaStream_t s) {
+  int64_t total = rows * cols;
+  if (total <= 0) return QTT_OK;
+  scale_rows_kernel<R><<<nblocks(total), TPB, 0, s>>>(x, rows, cols, ld, sv, invert);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_isfinite(const cplx<R>* x, int64_t count, int* flag, cudaStream_t s) {
+  if (count <= 0) return QTT_OK;
+  isfinite_kernel<R><<<nblocks(count), TPB, 0, s>>>(x, count, flag);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_fill_qft_dense(cplx<R>* out, int n, double sign, cudaStream_t s) {
+  int64_t total = (int64_t)1 << (2 * n);
+  qft_dense_kernel<R><<<nblocks(total), TPB, 0, s>>>(out, n, sign);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_fill_green_dense(cplx<R>* out, int nbits, int ncomp, int interleaved, double k0, double lam0,
+                         double mu0, cudaStream_t s) {
+  int64_t total = (int64_t)1 << (3 * nbits);
+  green_dense_kernel<R><<<nblocks(total), TPB, 0, s>>>(out, nbits, ncomp, interleaved, k0, lam0, mu0);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_fill_indicator_sites(const double* ind, int nbits, int interleaved, cplx<R>* out, cudaStream_t s) {
+  int64_t total = (int64_t)1 << (3 * nbits);
+  indicator_sites_kernel<R><<<nblocks(total), TPB, 0, s>>>(ind, nbits, interleaved, out);
+  CHECK_LAUNCH();
+}
+
+template <class R>
+int qtt_fill_gaussian(cplx<R>* out, int64_t count, uint64_t seed, uint64_t stream, double scale, cudaStream_t s) {
+  if (count <= 0) return QTT_OK;
+  gaussian_kernel<R><<<nblocks(count), TPB, 0, s>>>(out, count, seed, stream, scale);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_diag_mpo_core(const cplx<R>* X, int64_t r0, int64_t n, int64_t r1, cplx<R>* D, cudaStream_t s) {
+  int64_t total = r0 * n * n * r1;
+  if (total <= 0) return QTT_OK;
+  diag_mpo_kernel<R><<<nblocks(total), TPB, 0, s>>>(X, r0, n, r1, D);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_identity_core(int64_t g, int64_t n, cplx<R>* D, cudaStream_t s) {
+  int64_t total = g * n * n * g;
+  if (total <= 0) return QTT_OK;
+  identity_core_kernel<R><<<nblocks(total), TPB, 0, s>>>(g, n, D);
+  CHECK_LAUNCH();
+}
+template <class R>
+int qtt_adjoint_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64_t g1, cplx<R>* out,
+                     cudaStream_t s) {
+  int64_t total = g0 * no * ni * g1;
+  if (total <= 0) return QTT_OK;
+  adjoint_core_kernel<R><<<nblocks(total), TPB, 0, s>>>(D, g0, no, ni, g1, out);
+  CHECK_LAUNCH();
+}
+
+#define INST(R)                                                                                          \
+  template int qtt_place_block<R>(const cplx<R>*, int64_t, int64_t, int64_t, cplx<R>*, int64_t, int64_t,  \
+                                  int64_t, cplx<R>, cudaStream_t);                                        \
+  template int qtt_hadamard_core<R>(const cplx<R>*, int64_t, int64_t, const cplx<R>*, int64_t, int64_t,  \
+                                    int64_t, cplx<R>*, cudaStream_t);                                    \
+  template int qtt_mpo_core<R>(const cplx<R>*, int64_t, int64_t, int64_t, int64_t, const cplx<R>*,        \
+                               int64_t, int64_t, cplx<R>*, cudaStream_t);                                \
+  template int qtt_scale<R>(cplx<R>*, int64_t, cplx<R>, cudaStream_t);                                   \
+  template int qtt_sumsq<R>(const cplx<R>*, int64_t, double*, cudaStream_t);                             \
+  template int qtt_copy_strided<R>(const cplx<R>*, MIdx, MIdx, int64_t, int64_t, int, cplx<R>*, int64_t, \
+                                   cudaStream_t);                                                        \
+  template int qtt_scale_rows<R>(cplx<R>*, int64_t, int64_t, int64_t, const R*, int, cudaStream_t);       \
+  template int qtt_isfinite<R>(const cplx<R>*, int64_t, int*, cudaStream_t);                             \
+  template int qtt_fill_qft_dense<R>(cplx<R>*, int, double, cudaStream_t);                               \
+  template int qtt_fill_green_dense<R>(cplx<R>*, int, int, int, double, double, double, cudaStream_t);   \
+  template int qtt_fill_indicator_sites<R>(const double*, int, int, cplx<R>*, cudaStream_t);                \
+  template int qtt_fill_gaussian<R>(cplx<R>*, int64_t, uint64_t, uint64_t, double, cudaStream_t);          \
+  template int qtt_diag_mpo_core<R>(const cplx<R>*, int64_t, int64_t, int64_t, cplx<R>*, cudaStream_t);    \
+  template int qtt_identity_core<R>(int64_t, int64_t, cplx<R>*, cudaStream_t);                             \
+  template int qtt_adjoint_core<R>(const cplx<R>*, int64_t, int64_t, int64_t, int64_t, cplx<R>*, cudaStream_t);
+INST(double)
+INST(float)

@@ -1,0 +1,752 @@
+// Host side of the library: contexts, train handles, and the tensor-train
+// algorithms (rounding, sketched rounding, TT-SVD, inner products) composed
+// from the device kernels.  Everything numeric runs in kernels on the
+// context's stream; the host only sizes buffers and reads back the ranks that
+// the truncations choose.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "../../include/qtt.h"
+#include "common.cuh"
+#include "engine.h"
+#include "kernels.h"
+
+// ------------------------------------------------------------------ basics
+
+size_t dtype_size(qtt_dtype t) { return t == QTT_C128 ? 16 : 8; }
+
+int dalloc(qtt_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return QTT_OK;
+  if (cudaMallocAsync(p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return QTT_ERR_OOM;
+  }
+  return QTT_OK;
+}
+void dfree(qtt_ctx* c, void* p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+
+int sync_read(qtt_ctx* c, void* host, const void* dev, size_t bytes) {
+  if (cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return QTT_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return QTT_ERR_CUDA;
+  return QTT_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+qtt_tt* tt_alloc(qtt_ctx* c, int d, const std::vector<int>& n, const std::vector<int>& r, qtt_dtype dt, int* st) {
+  qtt_tt* x = new (std::nothrow) qtt_tt();
+  if (!x) {
+    *st = QTT_ERR_OOM;
+    return nullptr;
+  }
+  x->ctx = c;
+  x->d = d;
+  x->n = n;
+  x->r = r;
+  x->dtype = dt;
+  x->off.resize(d);
+  size_t tot = 0;
+  for (int k = 0; k < d; ++k) {
+    x->off[k] = tot;
+    tot += align256((size_t)r[k] * n[k] * r[k + 1] * dtype_size(dt));
+  }
+  x->bytes = tot;
+  *st = dalloc(c, &x->data, tot ? tot : 256);
+  if (*st) {
+    delete x;
+    return nullptr;
+  }
+  return x;
+}
+
+void tt_free(qtt_tt* x) {
+  if (!x) return;
+  dfree(x->ctx, x->data);
+  delete x;
+}
+
+qtt_mpo* mpo_alloc(qtt_ctx* c, int d, const std::vector<int>& no, const std::vector<int>& ni,
+                   const std::vector<int>& g, qtt_dtype dt, int* st) {
+  qtt_mpo* A = new (std::nothrow) qtt_mpo();
+  if (!A) {
+    *st = QTT_ERR_OOM;
+    return nullptr;
+  }
+  A->ctx = c;
+  A->d = d;
+  A->no = no;
+  A->ni = ni;
+  A->g = g;
+  A->dtype = dt;
+  A->off.resize(d);
+  size_t tot = 0;
+  for (int k = 0; k < d; ++k) {
+    A->off[k] = tot;
+    tot += align256((size_t)g[k] * no[k] * ni[k] * g[k + 1] * dtype_size(dt));
+  }
+  A->bytes = tot;
+  *st = dalloc(c, &A->data, tot ? tot : 256);
+  if (*st) {
+    delete A;
+    return nullptr;
+  }
+  return A;
+}
+
+void mpo_free(qtt_mpo* A) {
+  if (!A) return;
+  dfree(A->ctx, A->data);
+  delete A;
+}
+
+static inline MIdx L1(int64_t n, int64_t s) { return MIdx{n, 1, s, 0}; }
+static inline MIdx L2(int64_t n1, int64_t s1, int64_t n2, int64_t s2) { return MIdx{n1, n2, s1, s2}; }
+static inline MIdx B0() { return MIdx{1, 1, 0, 0}; }
+
+// C (M x N) = alpha op(A) op(B) + beta C, single batch, general strides
+template <class R>
+int mm(qtt_ctx* c, int64_t M, int64_t N, int64_t K, const cplx<R>* A, int64_t sAm, int64_t sAk, int conjA,
+       const cplx<R>* B, int64_t sBk, int64_t sBn, int conjB, cplx<R>* C, int64_t sCm, int64_t sCn,
+       cplx<R> alpha = cplx<R>(1, 0), cplx<R> beta = cplx<R>(0, 0)) {
+  GemmDesc g;
+  g.bA = B0();
+  g.bB = B0();
+  g.bC = B0();
+  g.mA = L1(M, sAm);
+  g.kA = L1(K, sAk);
+  g.kB = L1(K, sBk);
+  g.nB = L1(N, sBn);
+  g.mC = L1(M, sCm);
+  g.nC = L1(N, sCn);
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = 1;
+  g.conjA = conjA;
+  g.conjB = conjB;
+  if (K == 0) {
+    // C = beta C (only used with beta = 0 here): zero the output
+    if (sCn == 1 && sCm == N) return cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(cplx<R>), c->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+  }
+  c->launches++;
+  return qtt_gemm<R>(g, alpha, beta, A, B, C, c->stream);
+}
+
+template <class R>
+int gemm(qtt_ctx* c, const GemmDesc& g, const cplx<R>* A, const cplx<R>* B, cplx<R>* C) {
+  c->launches++;
+  return qtt_gemm<R>(g, cplx<R>(1, 0), cplx<R>(0, 0), A, B, C, c->stream);
+}
+
+#define TRY(expr)                 \
+  do {                            \
+    int _st = (expr);             \
+    if (_st != QTT_OK) return _st; \
+  } while (0)
+
+// RAII device buffer on the context stream
+struct DBuf {
+  qtt_ctx* c = nullptr;
+  void* p = nullptr;
+  DBuf() {}
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : c(o.c), p(o.p) { o.p = nullptr; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      dfree(c, p);
+      c = o.c;
+      p = o.p;
+      o.p = nullptr;
+    }
+    return *this;
+  }
+  ~DBuf() { dfree(c, p); }
+  int alloc(qtt_ctx* ctx, size_t bytes) {
+    dfree(c, p);
+    c = ctx;
+    return dalloc(ctx, &p, bytes);
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------ TSQR (R only)
+// R factor of an m x n matrix whose element (i, c) is in[rowI(i) + colI(c)]
+// (conjugated if conj_in): row blocks of max(2n, 256) rows are factored in
+// parallel (one CTA each), their R factors stacked and factored again until
+// one block remains.  Output: min(m, n) x n, row-major, leading dimension n.
+template <class R>
+int tsqr_r(qtt_ctx* c, const cplx<R>* in, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n, cplx<R>* Rout,
+           int64_t* rows_out) {
+  const int64_t chunk = std::max<int64_t>(2 * n, 256);
+  if (m <= chunk) {
+    DBuf W;
+    TRY(W.alloc(c, (size_t)m * n * sizeof(cplx<R>)));
+    c->launches++;
+    TRY(qtt_qr_r<R>(in, B0(), rowI, colI, conj_in, m, n, m, m, 1, W.as<cplx<R>>(), Rout, 0, n, c->stream));
+    *rows_out = std::min(m, n);
+    return QTT_OK;
+  }
+  const int64_t nch = (m + chunk - 1) / chunk;
+  DBuf W, Rs;
+  TRY(W.alloc(c, (size_t)nch * chunk * n * sizeof(cplx<R>)));
+  TRY(Rs.alloc(c, (size_t)nch * n * n * sizeof(cplx<R>)));
+  // batch b reads rows [b*chunk, (b+1)*chunk): the batch stride is chunk rows
+  MIdx inB = L1(nch, rowI.n2 == 1 ? chunk * rowI.s1 : 0);
+  if (rowI.n2 != 1) return QTT_ERR_UNSUPPORTED;
+  MIdx rows = L1(chunk, rowI.s1);
+  c->launches++;
+  TRY(qtt_qr_r<R>(in, inB, rows, colI, conj_in, chunk, n, m, chunk, nch, W.as<cplx<R>>(), Rs.as<cplx<R>>(),
+                  n * n, n, c->stream));
+  return tsqr_r<R>(c, Rs.as<cplx<R>>(), L1(nch * n, n), L1(n, 1), 0, nch * n, n, Rout, rows_out);
+}
+
+// SVD pieces of an (rows x cols) matrix given through a view: the left
+// singular vectors U (rows x rows, columns sorted by decreasing singular
+// value) and the singular values, via QR of the conjugate transpose followed
+// by one-sided Jacobi on the triangular factor.
+template <class R>
+int left_svd(qtt_ctx* c, const cplx<R>* Cm, int64_t rows, int64_t cols, int64_t ld, cplx<R>* U, R* sigma) {
+  // C^H is cols x rows: element (i, j) = conj(C[j, i]) -> row stride 1, column stride ld
+  const int64_t p = std::min(rows, cols);
+  DBuf Rc, V;
+  TRY(Rc.alloc(c, (size_t)std::max<int64_t>(p, 1) * rows * sizeof(cplx<R>)));
+  TRY(V.alloc(c, (size_t)rows * rows * sizeof(cplx<R>)));
+  int64_t got = 0;
+  TRY(tsqr_r<R>(c, Cm, L1(cols, 1), L1(rows, ld), 1, cols, rows, Rc.as<cplx<R>>(), &got));
+  // Jacobi on Rc (got x rows): Rc V = U_R S  =>  C = V S U_R^H Q^H, left vectors of C = V
+  c->launches++;
+  TRY(qtt_jacobi<R>(Rc.as<cplx<R>>(), V.as<cplx<R>>(), sigma, U, (int)got, (int)rows, 1, 60, nullptr, c->stream));
+  if (got < rows) {
+    // trailing singular values are exactly zero (rank <= got): sigma entries
+    // beyond `got` come out as zero column norms already.
+  }
+  return QTT_OK;
+}
+
+// ------------------------------------------------------- deterministic round
+// R-only variant of the QR-then-SVD rounding (Sec. 2.2): the left sweep keeps
+// only the triangular factors R_k of R_{k-1} A_k; the right sweep factors
+// C_k = R_{k-1} T_k with T_k = A_k (T_{k+1} V_{k+1}), keeps V_k^H as core k and
+// never needs the Q factors.  In exact arithmetic this equals keeping Q_k and
+// absorbing U_k S_k into it.
+template <class R>
+int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* forced, qtt_round_info* info,
+              qtt_tt** yout) {
+  const int d = x->d;
+  std::vector<int> n = x->n, r = x->r;
+  auto A = [&](int k) { return reinterpret_cast<const cplx<R>*>(static_cast<const char*>(x->data) + x->off[k]); };
+  if (d == 1) {
+    int st;
+    qtt_tt* y = tt_alloc(c, 1, n, r, x->dtype, &st);
+    if (!y) return st;
+    cudaMemcpyAsync(y->data, x->data, (size_t)n[0] * sizeof(cplx<R>), cudaMemcpyDeviceToDevice, c->stream);
+    double s2 = 0;
+    DBuf db;
+    TRY(db.alloc(c, sizeof(double)));
+    c->launches++;
+    TRY(qtt_sumsq<R>(A(0), n[0], db.as<double>(), c->stream));
+    TRY(sync_read(c, &s2, db.p, sizeof(double)));
+    if (info) {
+      info->norm = sqrt(s2);
+      info->delta = 0;
+      info->tail = 0;
+      info->err = 0;
+      info->capped = 0;
+      info->max_rank_out = 1;
+    }
+    *yout = y;
+    return QTT_OK;
+  }
+  // ---- sweep 1: R factors
+  std::vector<DBuf> Rf(d);
+  std::vector<int64_t> rp(d + 1, 1);
+  for (int k = 0; k < d - 1; ++k) {
+    const int64_t a0 = r[k], nk = n[k], a1 = r[k + 1];
+    DBuf Mb;
+    const cplx<R>* M = A(k);
+    if (k > 0) {
+      TRY(Mb.alloc(c, (size_t)rp[k] * nk * a1 * sizeof(cplx<R>)));
+      TRY(mm<R>(c, rp[k], nk * a1, a0, Rf[k - 1].as<cplx<R>>(), a0, 1, 0, A(k), nk * a1, 1, 0, Mb.as<cplx<R>>(),
+                nk * a1, 1));
+      M = Mb.as<cplx<R>>();
+    }
+    const int64_t m = rp[k] * nk;
+    rp[k + 1] = std::min(m, a1);
+    TRY(Rf[k].alloc(c, (size_t)rp[k + 1] * a1 * sizeof(cplx<R>)));
+    int64_t got = 0;
+    TRY(tsqr_r<R>(c, M, L1(m, a1), L1(a1, 1), 0, m, a1, Rf[k].as<cplx<R>>(), &got));
+  }
+  // ---- norm from the orthogonality centre R_{d-2} A_{d-1}
+  DBuf scal;
+  TRY(scal.alloc(c, 64));
+  double* dscal = scal.as<double>();
+  int* dint = reinterpret_cast<int*>(dscal + 4);
+  {
+    const int64_t a0 = r[d - 1], nk = n[d - 1];
+    DBuf Cb;
+    TRY(Cb.alloc(c, (size_t)rp[d - 1] * nk * sizeof(cplx<R>)));
+    TRY(mm<R>(c, rp[d - 1], nk, a0, Rf[d - 2].as<cplx<R>>(), a0, 1, 0, A(d - 1), nk, 1, 0, Cb.as<cplx<R>>(), nk, 1));
+    c->launches++;
+    TRY(qtt_sumsq<R>(Cb.as<cplx<R>>(), rp[d - 1] * nk, dscal, c->stream));
+  }
+  double nrm2 = 0;
+  TRY(sync_read(c, &nrm2, dscal, sizeof(double)));
+  const double nrm = sqrt(nrm2);
+  const double delta = d > 1 ? eps * nrm / sqrt((double)(d - 1)) : 0.0;
+  // ---- sweep 2
+  std::vector<DBuf> newc(d);
+  std::vector<int> nr(d + 1, 1);
+  DBuf Tb;
+  const cplx<R>* T = A(d - 1);
+  int64_t Trows = r[d - 1];
+  double tail2 = 0;
+  int capped = 0;
+  for (int k = d - 1; k >= 1; --k) {
+    const int64_t nk = n[k], tk = nr[k + 1], Tcols = nk * tk;
+    const int64_t rk = rp[k];  // rows of R_{k-1}
+    const int64_t a0 = r[k];
+    DBuf Cb, U, sig;
+    TRY(Cb.alloc(c, (size_t)rk * Tcols * sizeof(cplx<R>)));
+    TRY(mm<R>(c, rk, Tcols, a0, Rf[k - 1].as<cplx<R>>(), a0, 1, 0, T, Tcols, 1, 0, Cb.as<cplx<R>>(), Tcols, 1));
+    TRY(U.alloc(c, (size_t)rk * rk * sizeof(cplx<R>)));
+    TRY(sig.alloc(c, (size_t)rk * sizeof(R)));
+    TRY(left_svd<R>(c, Cb.as<cplx<R>>(), rk, Tcols, Tcols, U.as<cplx<R>>(), sig.as<R>()));
+    int t;
+    if (forced) {
+      t = (int)std::min<int64_t>(forced[k], rk);
+      c->launches++;
+      TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)rk, -1.0, t, dint, dscal + 1, c->stream));
+      // trunc with delta < 0 keeps everything then caps at t
+    } else {
+      c->launches++;
+      TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)rk, delta, max_rank, dint, dscal + 1, c->stream));
+    }
+    int hv[2];
+    double tl = 0;
+    TRY(sync_read(c, hv, dint, sizeof(hv)));
+    TRY(sync_read(c, &tl, dscal + 1, sizeof(double)));
+    t = hv[0];
+    if (!forced) capped |= hv[1];
+    tail2 += tl * tl;
+    nr[k] = t;
+    // new core k = S_t^{-1} U_t^H C  (t x Tcols)
+    TRY(newc[k].alloc(c, (size_t)t * Tcols * sizeof(cplx<R>)));
+    cplx<R>* core = newc[k].as<cplx<R>>();
+    TRY(mm<R>(c, t, Tcols, rk, U.as<cplx<R>>(), 1, rk, 1, Cb.as<cplx<R>>(), Tcols, 1, 0, core, Tcols, 1));
+    c->launches++;
+    TRY(qtt_scale_rows<R>(core, t, Tcols, Tcols, sig.as<R>(), 1, c->stream));
+    // P = T core^H (a0 x t); T_{k-1} = A_{k-1} P (r_{k-2} n_{k-1} x t)
+    DBuf P, Tn;
+    TRY(P.alloc(c, (size_t)a0 * t * sizeof(cplx<R>)));
+    TRY(mm<R>(c, a0, t, Tcols, T, Tcols, 1, 0, core, 1, Tcols, 1, P.as<cplx<R>>(), t, 1));
+    const int64_t pr = (int64_t)r[k - 1] * n[k - 1];
+    TRY(Tn.alloc(c, (size_t)pr * t * sizeof(cplx<R>)));
+    TRY(mm<R>(c, pr, t, a0, A(k - 1), a0, 1, 0, P.as<cplx<R>>(), t, 1, 0, Tn.as<cplx<R>>(), t, 1));
+    Tb = std::move(Tn);
+    T = Tb.as<cplx<R>>();
+    Trows = r[k - 1];
+  }
+  // core 0 = T_0 (1 x n_0 x t_1)
+  int st;
+  qtt_tt* y = tt_alloc(c, d, n, nr, x->dtype, &st);
+  if (!y) return st;
+  for (int k = 0; k < d; ++k) {
+    const void* src = (k == 0) ? (const void*)T : newc[k].p;
+    size_t bytes = (size_t)nr[k] * n[k] * nr[k + 1] * sizeof(cplx<R>);
+    if (cudaMemcpyAsync(static_cast<char*>(y->data) + y->off[k], src, bytes, cudaMemcpyDeviceToDevice, c->stream) !=
+        cudaSuccess) {
+      tt_free(y);
+      return QTT_ERR_CUDA;
+    }
+  }
+  (void)Trows;
+  if (info) {
+    info->norm = nrm;
+    info->delta = delta;
+    info->tail = sqrt(tail2);
+    info->err = -1;
+    info->capped = capped;
+    info->max_rank_out = *std::max_element(nr.begin(), nr.end());
+  }
+  *yout = y;
+  return QTT_OK;
+}
+
+template int round_det<double>(qtt_ctx*, const qtt_tt*, double, int, const int*, qtt_round_info*, qtt_tt**);
+template int round_det<float>(qtt_ctx*, const qtt_tt*, double, int, const int*, qtt_round_info*, qtt_tt**);
+
+// ------------------------------------------------------------------- TT-SVD
+template <class R>
+int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* dense, double eps, int max_rank,
+               qtt_dtype dt, qtt_tt** out) {
+  int64_t total = 1;
+  for (int k = 0; k < d; ++k) total *= modes[k];
+  DBuf scal;
+  TRY(scal.alloc(c, 64));
+  double* dscal = scal.as<double>();
+  int* dint = reinterpret_cast<int*>(dscal + 4);
+  c->launches++;
+  TRY(qtt_sumsq<R>(dense, total, dscal, c->stream));
+  double n2 = 0;
+  TRY(sync_read(c, &n2, dscal, sizeof(double)));
+  const double delta = d > 1 ? eps * sqrt(n2) / sqrt((double)(d - 1)) : 0.0;
+  std::vector<DBuf> cores(d);
+  std::vector<int> ranks(d + 1, 1);
+  DBuf Cown;
+  const cplx<R>* C = dense;
+  int64_t rest = total;
+  int64_t rprev = 1;
+  for (int k = 0; k < d - 1; ++k) {
+    const int64_t m = rprev * modes[k];
+    rest /= modes[k];
+    // C viewed as m x rest (row-major)
+    DBuf U, sig;
+    TRY(U.alloc(c, (size_t)m * m * sizeof(cplx<R>)));
+    TRY(sig.alloc(c, (size_t)m * sizeof(R)));
+    TRY(left_svd<R>(c, C, m, rest, rest, U.as<cplx<R>>(), sig.as<R>()));
+    c->launches++;
+    TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)m, delta, max_rank, dint, dscal + 1, c->stream));
+    int hv[2];
+    TRY(sync_read(c, hv, dint, sizeof(hv)));
+    const int t = hv[0];
+    ranks[k + 1] = t;
+    // core k = U[:, :t] as (rprev, n_k, t)
+    TRY(cores[k].alloc(c, (size_t)m * t * sizeof(cplx<R>)));
+    c->launches++;
+    TRY(qtt_copy_strided<R>(U.as<cplx<R>>(), L1(m, m), L1(t, 1), m, t, 0, cores[k].as<cplx<R>>(), t, c->stream));
+    // next C = U_t^H C  (t x rest)
+    DBuf Cn;
+    TRY(Cn.alloc(c, (size_t)t * rest * sizeof(cplx<R>)));
+    TRY(mm<R>(c, t, rest, m, U.as<cplx<R>>(), 1, m, 1, C, rest, 1, 0, Cn.as<cplx<R>>(), rest, 1));
+    Cown = std::move(Cn);
+    C = Cown.as<cplx<R>>();
+    rprev = t;
+  }
+  int st;
+  std::vector<int> md(modes.begin(), modes.begin() + d);
+  qtt_tt* y = tt_alloc(c, d, md, ranks, dt, &st);
+  if (!y) return st;
+  for (int k = 0; k < d; ++k) {
+    const void* src = (k == d - 1) ? (const void*)C : cores[k].p;
+    size_t bytes = (size_t)ranks[k] * modes[k] * ranks[k + 1] * sizeof(cplx<R>);
+    cudaMemcpyAsync(static_cast<char*>(y->data) + y->off[k], src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  *out = y;
+  return QTT_OK;
+}
+
+template int tt_svd_dev<double>(qtt_ctx*, int, const std::vector<int>&, const zc*, double, int, qtt_dtype, qtt_tt**);
+
+// ----------------------------------------------------------- inner product
+template <class R>
+int dot_dev(qtt_ctx* c, const qtt_tt* x, const qtt_tt* y, double out[2]) {
+  const int d = x->d;
+  DBuf W, T;
+  // W_0 = [1]
+  int64_t wa = 1, wb = 1;
+  TRY(W.alloc(c, sizeof(cplx<R>)));
+  cplx<R> one(1, 0);
+  cudaMemcpyAsync(W.p, &one, sizeof(one), cudaMemcpyHostToDevice, c->stream);
+  for (int k = 0; k < d; ++k) {
+    const int64_t a0 = x->r[k], a1 = x->r[k + 1], b0 = y->r[k], b1 = y->r[k + 1], nk = x->n[k];
+    const cplx<R>* Ak = reinterpret_cast<const cplx<R>*>(static_cast<const char*>(x->data) + x->off[k]);
+    const cplx<R>* Bk = reinterpret_cast<const cplx<R>*>(static_cast<const char*>(y->data) + y->off[k]);
+    // T[a0, (i, b1)] = W[a0, b0] B[b0, (i, b1)]
+    DBuf Tn;
+    TRY(Tn.alloc(c, (size_t)a0 * nk * b1 * sizeof(cplx<R>)));
+    TRY(mm<R>(c, a0, nk * b1, b0, W.as<cplx<R>>(), wb, 1, 0, Bk, nk * b1, 1, 0, Tn.as<cplx<R>>(), nk * b1, 1));
+    // W'[a1, b1] = sum_{(a0, i)} conj(A[(a0, i), a1]) T[(a0, i), b1]
+    DBuf Wn;
+    TRY(Wn.alloc(c, (size_t)a1 * b1 * sizeof(cplx<R>)));
+    TRY(mm<R>(c, a1, b1, a0 * nk, Ak, 1, a1, 1, Tn.as<cplx<R>>(), b1, 1, 0, Wn.as<cplx<R>>(), b1, 1));
+    W = std::move(Wn);
+    wa = a1;
+    wb = b1;
+  }
+  (void)wa;
+  cplx<R> h;
+  TRY(sync_read(c, &h, W.p, sizeof(h)));
+  out[0] = (double)h.re;
+  out[1] = (double)h.im;
+  return QTT_OK;
+}
+
+template int dot_dev<double>(qtt_ctx*, const qtt_tt*, const qtt_tt*, double*);
+template int dot_dev<float>(qtt_ctx*, const qtt_tt*, const qtt_tt*, double*);
+
+// Frobenius norm: R factor sweep, then the norm of the centre.
+template <class R>
+int norm_dev(qtt_ctx* c, const qtt_tt* x, double* out) {
+  const int d = x->d;
+  auto A = [&](int k) { return reinterpret_cast<const cplx<R>*>(static_cast<const char*>(x->data) + x->off[k]); };
+  DBuf Rprev;
+  int64_t rp = 1;
+  DBuf scal;
+  TRY(scal.alloc(c, 64));
+  for (int k = 0; k < d; ++k) {
+    const int64_t a0 = x->r[k], nk = x->n[k], a1 = x->r[k + 1];
+    DBuf Mb;
+    const cplx<R>* M = A(k);
+    if (k > 0) {
+      TRY(Mb.alloc(c, (size_t)rp * nk * a1 * sizeof(cplx<R>)));
+      TRY(mm<R>(c, rp, nk * a1, a0, Rprev.as<cplx<R>>(), a0, 1, 0, A(k), nk * a1, 1, 0, Mb.as<cplx<R>>(), nk * a1, 1));
+      M = Mb.as<cplx<R>>();
+    }
+    const int64_t m = rp * nk;
+    if (k == d - 1) {
+      c->launches++;
+      TRY(qtt_sumsq<R>(M, m * a1, scal.as<double>(), c->stream));
+      break;
+    }
+    DBuf Rn;
+    const int64_t rn = std::min(m, a1);
+    TRY(Rn.alloc(c, (size_t)rn * a1 * sizeof(cplx<R>)));
+    int64_t got;
+    TRY(tsqr_r<R>(c, M, L1(m, a1), L1(a1, 1), 0, m, a1, Rn.as<cplx<R>>(), &got));
+    Rprev = std::move(Rn);
+    rp = rn;
+  }
+  double s2;
+  TRY(sync_read(c, &s2, scal.p, sizeof(double)));
+  *out = sqrt(s2);
+  return QTT_OK;
+}
+
+template int norm_dev<double>(qtt_ctx*, const qtt_tt*, double*);
+template int norm_dev<float>(qtt_ctx*, const qtt_tt*, double*);
+
+// ------------------------------------------------------- sketched rounding
+// Randomize-then-orthogonalize for s = sum_t coef_t A_t x_t (A_t may be NULL).
+template <class R>
+int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* const* ops, const qtt_tt* const* xs,
+                   const qtt_tt* S, double eps, int max_rank, qtt_round_info* info, qtt_tt** yout) {
+  const int d = S->d;
+  typedef cplx<R> C;
+  // identity operators for terms without one
+  std::vector<qtt_mpo*> own(T, nullptr);
+  std::vector<const qtt_mpo*> A(T);
+  struct Cleanup {
+    std::vector<qtt_mpo*>& v;
+    ~Cleanup() {
+      for (auto* p : v) mpo_free(p);
+    }
+  } cleanup{own};
+  for (int t = 0; t < T; ++t) {
+    if (xs[t]->d != d) return QTT_ERR_ARG;
+    if (ops && ops[t]) {
+      if (ops[t]->d != d) return QTT_ERR_ARG;
+      A[t] = ops[t];
+    } else {
+      int st;
+      std::vector<int> g(d + 1, 1);
+      own[t] = mpo_alloc(c, d, xs[t]->n, xs[t]->n, g, S->dtype, &st);
+      if (!own[t]) return st;
+      for (int k = 0; k < d; ++k) {
+        c->launches++;
+        TRY(qtt_identity_core<R>(1, xs[t]->n[k],
+                                 reinterpret_cast<C*>(static_cast<char*>(own[t]->data) + own[t]->off[k]), c->stream));
+      }
+      A[t] = own[t];
+    }
+    for (int k = 0; k < d; ++k) {
+      if (A[t]->ni[k] != xs[t]->n[k] || A[t]->no[k] != S->n[k]) return QTT_ERR_ARG;
+    }
+  }
+  auto Dk = [&](int t, int k) {
+    return reinterpret_cast<const C*>(static_cast<const char*>(A[t]->data) + A[t]->off[k]);
+  };
+  auto Xk = [&](int t, int k) {
+    return reinterpret_cast<const C*>(static_cast<const char*>(xs[t]->data) + xs[t]->off[k]);
+  };
+  auto Sk = [&](int k) { return reinterpret_cast<const C*>(static_cast<const char*>(S->data) + S->off[k]); };
+  // stacked bond sizes and offsets
+  std::vector<std::vector<int64_t>> boff(d + 1, std::vector<int64_t>(T + 1, 0));
+  for (int k = 0; k <= d; ++k)
+    for (int t = 0; t < T; ++t) boff[k][t + 1] = boff[k][t] + (int64_t)A[t]->g[k] * xs[t]->r[k];
+  auto Bt = [&](int k) { return boff[k][T]; };
+  // ---- right partial contractions W_k (Bt_k x l_k), k = 1..d
+  std::vector<DBuf> W(d + 1);
+  {
+    TRY(W[d].alloc(c, (size_t)T * sizeof(C)));
+    std::vector<C> ones(T, C(1, 0));
+    cudaMemcpyAsync(W[d].p, ones.data(), T * sizeof(C), cudaMemcpyHostToDevice, c->stream);
+  }
+  for (int k = d - 1; k >= 1; --k) {
+    const int64_t l0 = S->r[k], l1 = S->r[k + 1], no = S->n[k];
+    TRY(W[k].alloc(c, (size_t)Bt(k) * l0 * sizeof(C)));
+    for (int t = 0; t < T; ++t) {
+      const int64_t g0 = A[t]->g[k], g1 = A[t]->g[k + 1], ni = A[t]->ni[k];
+      const int64_t a0 = xs[t]->r[k], a1 = xs[t]->r[k + 1];
+      const C* Wn = W[k + 1].as<C>() + boff[k + 1][t] * l1;  // (g1 a1) x l1
+      // U1[g1, a1, i, l0] = sum_l1 Wn[(g1 a1), l1] S[l0, i, l1]
+      DBuf U1, U2;
+      TRY(U1.alloc(c, (size_t)g1 * a1 * no * l0 * sizeof(C)));
+      {
+        GemmDesc g;
+        g.bA = g.bB = g.bC = B0();
+        g.M = g1 * a1;
+        g.N = no * l0;
+        g.K = l1;
+        g.batch = 1;
+        g.mA = L1(g.M, l1);
+        g.kA = L1(l1, 1);
+        g.kB = L1(l1, 1);
+        g.nB = L2(no, l1, l0, no * l1);
+        g.mC = L1(g.M, no * l0);
+        g.nC = L1(g.N, 1);
+        g.conjA = g.conjB = 0;
+        TRY(gemm<R>(c, g, Wn, Sk(k), U1.as<C>()));
+      }
+      // U2[a1, g0, j, l0] = sum_{i, g1} D[g0, i, j, g1] U1[g1, a1, i, l0]   (batch a1)
+      TRY(U2.alloc(c, (size_t)a1 * g0 * ni * l0 * sizeof(C)));
+      {
+        GemmDesc g;
+        g.M = g0 * ni;
+        g.N = l0;
+        g.K = no * g1;
+        g.batch = a1;
+        g.bA = L1(a1, 0);
+        g.mA = L2(g0, no * ni * g1, ni, g1);
+        g.kA = L2(no, ni * g1, g1, 1);
+        g.bB = L1(a1, no * l0);
+        g.kB = L2(no, l0, g1, a1 * no * l0);
+        g.nB = L1(l0, 1);
+        g.bC = L1(a1, g0 * ni * l0);
+        g.mC = L1(g.M, l0);
+        g.nC = L1(l0, 1);
+        g.conjA = g.conjB = 0;
+        TRY(gemm<R>(c, g, Dk(t, k), U1.as<C>(), U2.as<C>()));
+      }
+      // W_k[g0, a0, l0] = sum_{j, a1} X[a0, j, a1] U2[a1, g0, j, l0]   (batch g0)
+      {
+        GemmDesc g;
+        g.M = a0;
+        g.N = l0;
+        g.K = ni * a1;
+        g.batch = g0;
+        g.bA = L1(g0, 0);
+        g.mA = L1(a0, ni * a1);
+        g.kA = L1(g.K, 1);
+        g.bB = L1(g0, ni * l0);
+        g.kB = L2(ni, l0, a1, g0 * ni * l0);
+        g.nB = L1(l0, 1);
+        g.bC = L1(g0, a0 * l0);
+        g.mC = L1(a0, l0);
+        g.nC = L1(l0, 1);
+        g.conjA = g.conjB = 0;
+        TRY(gemm<R>(c, g, Xk(t, k), U2.as<C>(), W[k].as<C>() + boff[k][t] * l0));
+      }
+    }
+  }
+  // ---- left-to-right projection
+  std::vector<DBuf> outc(d);
+  std::vector<int> orank(d + 1, 1);
+  DBuf M;  // l_k x Bt_k
+  {
+    TRY(M.alloc(c, (size_t)T * sizeof(C)));
+    std::vector<C> cf(T);
+    for (int t = 0; t < T; ++t) cf[t] = C((R)coef[t].re, (R)coef[t].im);
+    cudaMemcpyAsync(M.p, cf.data(), T * sizeof(C), cudaMemcpyHostToDevice, c->stream);
+  }
+  int64_t lk = 1;
+  for (int k = 0; k < d; ++k) {
+    const int64_t no = S->n[k];
+    const int64_t Bn = Bt(k + 1);
+    DBuf Y;
+    TRY(Y.alloc(c, (size_t)lk * no * Bn * sizeof(C)));
+    for (int t = 0; t < T; ++t) {
+      const int64_t g0 = A[t]->g[k], g1 = A[t]->g[k + 1], ni = A[t]->ni[k];
+      const int64_t a0 = xs[t]->r[k], a1 = xs[t]->r[k + 1];
+      // T1[l, g0, j, a1] = sum_a0 M[l, off + g0 a0 + a0] X[a0, j, a1]
+      DBuf T1;
+      TRY(T1.alloc(c, (size_t)lk * g0 * ni * a1 * sizeof(C)));
+      {
+        GemmDesc g;
+        g.bA = g.bB = g.bC = B0();
+        g.M = lk * g0;
+        g.N = ni * a1;
+        g.K = a0;
+        g.batch = 1;
+        g.mA = L2(lk, Bt(k), g0, a0);
+        g.kA = L1(a0, 1);
+        g.kB = L1(a0, ni * a1);
+        g.nB = L1(g.N, 1);
+        g.mC = L1(g.M, ni * a1);
+        g.nC = L1(g.N, 1);
+        g.conjA = g.conjB = 0;
+        TRY(gemm<R>(c, g, M.as<C>() + boff[k][t], Xk(t, k), T1.as<C>()));
+      }
+      // Y[l, i, off' + g1 a1 + a1] = sum_{g0, j} D[g0, i, j, g1] T1[l, g0, j, a1]  (batch l)
+      {
+        GemmDesc g;
+        g.M = no * g1;
+        g.N = a1;
+        g.K = g0 * ni;
+        g.batch = lk;
+        g.bA = L1(lk, 0);
+        g.mA = L2(no, ni * g1, g1, 1);
+        g.kA = L2(g0, no * ni * g1, ni, g1);
+        g.bB = L1(lk, g0 * ni * a1);
+        g.kB = L1(g.K, a1);
+        g.nB = L1(a1, 1);
+        g.bC = L1(lk, no * Bn);
+        g.mC = L2(no, Bn, g1, a1);
+        g.nC = L1(a1, 1);
+        g.conjA = g.conjB = 0;
+        TRY(gemm<R>(c, g, Dk(t, k), T1.as<C>(), Y.as<C>() + boff[k + 1][t]));
+      }
+    }
+    const int64_t l1 = S->r[k + 1];
+    // Z = Y (lk no x Bn) W_{k+1} (Bn x l1)
+    DBuf Z;
+    TRY(Z.alloc(c, (size_t)lk * no * l1 * sizeof(C)));
+    TRY(mm<R>(c, lk * no, l1, Bn, Y.as<C>(), Bn, 1, 0, W[k + 1].as<C>(), l1, 1, 0, Z.as<C>(), l1, 1));
+    if (k == d - 1) {
+      outc[k] = std::move(Z);
+      break;
+    }
+    // Q of Z (lk no x l1): new core (lk, no, q)
+    const int64_t m = lk * no, q = std::min(m, l1);
+    DBuf Wq, tau;
+    TRY(outc[k].alloc(c, (size_t)m * q * sizeof(C)));
+    TRY(Wq.alloc(c, (size_t)m * l1 * sizeof(C)));
+    TRY(tau.alloc(c, (size_t)2 * l1 * sizeof(C)));
+    c->launches++;
+    TRY(qtt_qr_r<R>(Z.as<C>(), B0(), L1(m, l1), L1(l1, 1), 0, m, l1, m, m, 1, Wq.as<C>(), nullptr, 0, 0, c->stream,
+                    tau.as<C>(), outc[k].as<C>(), 0, q));
+    orank[k + 1] = (int)q;
+    // M_{k+1} = Q^H Y  (q x Bn)
+    DBuf Mn;
+    TRY(Mn.alloc(c, (size_t)q * Bn * sizeof(C)));
+    TRY(mm<R>(c, q, Bn, m, outc[k].as<C>(), 1, q, 1, Y.as<C>(), Bn, 1, 0, Mn.as<C>(), Bn, 1));
+    M = std::move(Mn);
+    lk = q;
+  }
+  // assemble the projected train, then round it deterministically
+  int st;
+  qtt_tt* P = tt_alloc(c, d, S->n, orank, S->dtype, &st);
+  if (!P) return st;
+  for (int k = 0; k < d; ++k) {
+    size_t bytes = (size_t)orank[k] * S->n[k] * orank[k + 1] * sizeof(C);
+    cudaMemcpyAsync(static_cast<char*>(P->data) + P->off[k], outc[k].p, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  int rs = round_det<R>(c, P, eps, max_rank, nullptr, info, yout);
+  tt_free(P);
+  return rs;
+}
+
+template int round_sketched<double>(qtt_ctx*, int, const qtt_complex*, const qtt_mpo* const*, const qtt_tt* const*,
+                                    const qtt_tt*, double, int, qtt_round_info*, qtt_tt**);
+template int round_sketched<float>(qtt_ctx*, int, const qtt_complex*, const qtt_mpo* const*, const qtt_tt* const*,
+                                   const qtt_tt*, double, int, qtt_round_info*, qtt_tt**);

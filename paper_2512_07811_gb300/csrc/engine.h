@@ -1,0 +1,69 @@
+// Internal structures shared by the host-side translation units.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/qtt.h"
+#include "common.cuh"
+
+struct qtt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t launches = 0;
+};
+
+struct qtt_tt {
+  qtt_ctx* ctx = nullptr;
+  int d = 0;
+  std::vector<int> n, r;          // modes (d), ranks (d + 1)
+  qtt_dtype dtype = QTT_C128;
+  void* data = nullptr;           // one allocation holding every core
+  std::vector<size_t> off;        // byte offset of each core
+  size_t bytes = 0;
+};
+
+struct qtt_mpo {
+  qtt_ctx* ctx = nullptr;
+  int d = 0;
+  std::vector<int> no, ni, g;     // output modes, input modes, bond ranks (d + 1)
+  qtt_dtype dtype = QTT_C128;
+  void* data = nullptr;
+  std::vector<size_t> off;
+  size_t bytes = 0;
+};
+
+size_t dtype_size(qtt_dtype t);
+int dalloc(qtt_ctx* c, void** p, size_t bytes);
+void dfree(qtt_ctx* c, void* p);
+int sync_read(qtt_ctx* c, void* host, const void* dev, size_t bytes);
+qtt_tt* tt_alloc(qtt_ctx* c, int d, const std::vector<int>& n, const std::vector<int>& r, qtt_dtype dt, int* st);
+void tt_free(qtt_tt* x);
+qtt_mpo* mpo_alloc(qtt_ctx* c, int d, const std::vector<int>& no, const std::vector<int>& ni,
+                   const std::vector<int>& g, qtt_dtype dt, int* st);
+void mpo_free(qtt_mpo* A);
+
+template <class R>
+int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* forced, qtt_round_info* info,
+              qtt_tt** yout);
+template <class R>
+int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* const* ops, const qtt_tt* const* xs,
+                   const qtt_tt* S, double eps, int max_rank, qtt_round_info* info, qtt_tt** yout);
+template <class R>
+int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* dense, double eps, int max_rank,
+               qtt_dtype dt, qtt_tt** out);
+template <class R>
+int dot_dev(qtt_ctx* c, const qtt_tt* x, const qtt_tt* y, double out[2]);
+template <class R>
+int norm_dev(qtt_ctx* c, const qtt_tt* x, double* out);
+
+template <class T>
+inline T* core_ptr(const qtt_tt* x, int k) {
+  return reinterpret_cast<T*>(static_cast<char*>(x->data) + x->off[k]);
+}
+template <class T>
+inline T* core_ptr(const qtt_mpo* A, int k) {
+  return reinterpret_cast<T*>(static_cast<char*>(A->data) + A->off[k]);
+}

@@ -1,0 +1,65 @@
+// Internal kernel launchers (C++ linkage; not part of the C-ABI).
+#pragma once
+
+#include "common.cuh"
+
+template <class R>
+int qtt_gemm(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B,
+             cplx<R>* C, cudaStream_t s);
+
+template <class R>
+int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
+             int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
+             int64_t out_bstride, int64_t ldr, cudaStream_t s, cplx<R>* tauws = nullptr,
+             cplx<R>* Qout = nullptr, int64_t q_bstride = 0, int64_t ldq = 0);
+
+template <class R>
+int qtt_jacobi(cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, int q, int batch,
+               int max_sweeps, int* sweeps, cudaStream_t s);
+
+template <class R>
+int qtt_trunc_rank(const R* sigma, int q, double delta, int max_rank, int* out, double* tail,
+                   cudaStream_t s);
+
+// ---- elementwise / placement kernels (elem.cu)
+template <class R>
+int qtt_place_block(const cplx<R>* src, int64_t s0, int64_t n, int64_t s1, cplx<R>* dst, int64_t d1,
+                    int64_t off0, int64_t off1, cplx<R> scale, cudaStream_t s);
+template <class R>
+int qtt_hadamard_core(const cplx<R>* x, int64_t a0, int64_t a1, const cplx<R>* y, int64_t b0,
+                      int64_t b1, int64_t n, cplx<R>* out, cudaStream_t s);
+template <class R>
+int qtt_mpo_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64_t g1, const cplx<R>* X,
+                 int64_t a0, int64_t a1, cplx<R>* out, cudaStream_t s);
+template <class R>
+int qtt_scale(cplx<R>* x, int64_t count, cplx<R> scale, cudaStream_t s);
+template <class R>
+int qtt_sumsq(const cplx<R>* x, int64_t count, double* out, cudaStream_t s);
+int qtt_convert_z2c(const zc* in, cc* out, int64_t count, cudaStream_t s);
+int qtt_convert_c2z(const cc* in, zc* out, int64_t count, cudaStream_t s);
+template <class R>
+int qtt_copy_strided(const cplx<R>* in, MIdx rows, MIdx cols, int64_t nrows, int64_t ncols, int conj_in,
+                     cplx<R>* out, int64_t ldo, cudaStream_t s);
+template <class R>
+int qtt_scale_rows(cplx<R>* x, int64_t rows, int64_t cols, int64_t ld, const R* sv, int invert,
+                   cudaStream_t s);
+template <class R>
+int qtt_isfinite(const cplx<R>* x, int64_t count, int* flag, cudaStream_t s);
+
+// ---- operator construction on the device (elem.cu)
+template <class R>
+int qtt_fill_qft_dense(cplx<R>* out, int n, double sign, cudaStream_t s);
+template <class R>
+int qtt_fill_green_dense(cplx<R>* out, int nbits, int ncomp, int interleaved, double k0, double lam0,
+                         double mu0, cudaStream_t s);
+template <class R>
+int qtt_fill_indicator_sites(const double* ind, int nbits, int interleaved, cplx<R>* out, cudaStream_t s);
+template <class R>
+int qtt_fill_gaussian(cplx<R>* out, int64_t count, uint64_t seed, uint64_t stream, double scale, cudaStream_t s);
+template <class R>
+int qtt_diag_mpo_core(const cplx<R>* X, int64_t r0, int64_t n, int64_t r1, cplx<R>* D, cudaStream_t s);
+template <class R>
+int qtt_identity_core(int64_t g, int64_t n, cplx<R>* D, cudaStream_t s);
+template <class R>
+int qtt_adjoint_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64_t g1, cplx<R>* out,
+                     cudaStream_t s);

@@ -1,0 +1,318 @@
+// Small dense factorisations on the device, one CTA per matrix, batched over
+// blockIdx.x:
+//   * Householder QR returning only R (the orthogonalisation sweep of TT
+//     rounding needs only the triangular factor; TSQR trees stack R factors);
+//   * one-sided (Hestenes) Jacobi SVD with accumulated right rotations;
+//   * the truncation-rank rule on sorted singular values.
+// Arithmetic is in the storage precision R (double or float); reductions of
+// the truncation tail are always in double.
+#include <float.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+template <class R>
+__device__ R block_sum(R v, R* red) {
+  // red: shared scratch of blockDim.x/32 entries
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  R s = R(0);
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+// --------------------------------------------------------------- QR (R only)
+// Input element (i, c) of batch b sits at in[in_b + rowI(i) + colI(c)] (optionally
+// conjugated); rows at or beyond rows_valid(b) read as zero.  W is a per-batch
+// workspace of m*n elements (row-major, ld = n).  Output R_b is min(m, n) x n,
+// upper trapezoidal, row-major with leading dimension ldr, at out + b*out_bstride.
+template <class R>
+__global__ void __launch_bounds__(256)
+qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int conj_in,
+            int64_t m, int64_t n, int64_t rows_total, int64_t rows_per_batch,
+            cplx<R>* __restrict__ Wbase, cplx<R>* __restrict__ out, int64_t out_bstride, int64_t ldr,
+            cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout, int64_t q_bstride, int64_t ldq) {
+  __shared__ R red[32];
+  __shared__ cplx<R> s_v0;
+  __shared__ R s_tau;
+  const int64_t b = blockIdx.x;
+  cplx<R>* W = Wbase + b * m * n;
+  const int64_t row0 = b * rows_per_batch;
+  int64_t valid = rows_total - row0;
+  if (valid > m) valid = m;
+  const int64_t ib = midx_off(inB, b);
+  for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) {
+    int64_t i = e / n, c = e - i * n;
+    cplx<R> v(0, 0);
+    if (i < valid) {
+      v = in[ib + midx_off(rowI, i) + midx_off(colI, c)];
+      if (conj_in) v.im = -v.im;
+    }
+    W[e] = v;
+  }
+  __syncthreads();
+  const int64_t kmax = m < n ? m : n;
+  for (int64_t j = 0; j < kmax; ++j) {
+    // squared norm of column j below (and at) the diagonal
+    R part = R(0);
+    for (int64_t i = j + threadIdx.x; i < m; i += blockDim.x) part += abs2(W[i * n + j]);
+    R nrm2 = block_sum(part, red);
+    if (threadIdx.x == 0) {
+      cplx<R> x0 = W[j * n + j];
+      R ax0 = sqrt(abs2(x0));
+      R nrm = sqrt(nrm2);
+      if (nrm2 == R(0) || (nrm2 - ax0 * ax0) <= R(0) * nrm2) {
+        // already triangular in this column (covers nrm2 == 0)
+        s_tau = R(0);
+        s_v0 = cplx<R>(0, 0);
+      } else {
+        cplx<R> ph = ax0 > R(0) ? cplx<R>(x0.re / ax0, x0.im / ax0) : cplx<R>(1, 0);
+        cplx<R> alpha = cplx<R>(-ph.re * nrm, -ph.im * nrm);
+        cplx<R> v0 = x0 - alpha;
+        R vn2 = nrm2 - ax0 * ax0 + abs2(v0);
+        s_tau = R(2) / vn2;
+        s_v0 = v0;
+        W[j * n + j] = alpha;
+      }
+      if (tauws) {
+        tauws[b * 2 * n + 2 * j] = s_v0;
+        tauws[b * 2 * n + 2 * j + 1] = cplx<R>(s_tau, R(0));
+      }
+    }
+    __syncthreads();
+    const R tau = s_tau;
+    if (tau != R(0)) {
+      const cplx<R> v0 = s_v0;
+      for (int64_t c = j + 1 + threadIdx.x; c < n; c += blockDim.x) {
+        cplx<R> w = cplx<R>(0, 0);
+        cfma_conj(w, v0, W[j * n + c]);
+        for (int64_t i = j + 1; i < m; ++i) cfma_conj(w, W[i * n + j], W[i * n + c]);
+        w = tau * w;
+        W[j * n + c] = W[j * n + c] - v0 * w;
+        for (int64_t i = j + 1; i < m; ++i) W[i * n + c] = W[i * n + c] - W[i * n + j] * w;
+      }
+    }
+    __syncthreads();
+  }
+  if (out) {
+    cplx<R>* Rb = out + b * out_bstride;
+    for (int64_t e = threadIdx.x; e < kmax * n; e += blockDim.x) {
+      int64_t i = e / n, c = e - i * n;
+      Rb[i * ldr + c] = (c >= i) ? W[i * n + c] : cplx<R>(0, 0);
+    }
+  }
+  if (Qout) {
+    // Q = H_0 H_1 ... H_{kmax-1} [I; 0], accumulated from the last reflector.
+    cplx<R>* Q = Qout + b * q_bstride;
+    for (int64_t e = threadIdx.x; e < m * kmax; e += blockDim.x) {
+      int64_t i = e / kmax, c = e - i * kmax;
+      Q[i * ldq + c] = cplx<R>(i == c ? R(1) : R(0), R(0));
+    }
+    __syncthreads();
+    for (int64_t j = kmax - 1; j >= 0; --j) {
+      const cplx<R> v0 = tauws[b * 2 * n + 2 * j];
+      const R tau = tauws[b * 2 * n + 2 * j + 1].re;
+      if (tau != R(0)) {
+        for (int64_t c = j + threadIdx.x; c < kmax; c += blockDim.x) {
+          cplx<R> w = cplx<R>(0, 0);
+          cfma_conj(w, v0, Q[j * ldq + c]);
+          for (int64_t i = j + 1; i < m; ++i) cfma_conj(w, W[i * n + j], Q[i * ldq + c]);
+          w = tau * w;
+          Q[j * ldq + c] = Q[j * ldq + c] - v0 * w;
+          for (int64_t i = j + 1; i < m; ++i) Q[i * ldq + c] = Q[i * ldq + c] - W[i * n + j] * w;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------- one-sided Jacobi
+// G (p x q, row-major ld = q, per batch at G + b*p*q) is rotated in place so
+// that its columns become mutually orthogonal; V (q x q, row-major, per batch
+// at V + b*q*q) accumulates the rotations (G_in V = G_out).  On exit the
+// columns are sorted by decreasing norm: sigma[b*q + j] = ||G_out[:, j]||,
+// V columns permuted alike; G columns are left unsorted (callers use V).
+template <class R>
+__global__ void __launch_bounds__(256)
+jacobi_kernel(cplx<R>* __restrict__ Gbase, cplx<R>* __restrict__ Vbase, R* __restrict__ sigma_out,
+              cplx<R>* __restrict__ Vsorted_base, int p, int q, int max_sweeps, int* __restrict__ sweeps_out) {
+  extern __shared__ unsigned char smem_raw[];
+  const int64_t b = blockIdx.x;
+  cplx<R>* G = Gbase + b * (int64_t)p * q;
+  cplx<R>* V = Vbase + b * (int64_t)q * q;
+  const int qe = q + (q & 1);            // even number of players (one virtual)
+  int* order = reinterpret_cast<int*>(smem_raw);          // qe entries
+  R* norms = reinterpret_cast<R*>(order + qe + (qe & 1)); // q entries (aligned for double)
+  __shared__ int s_rot;
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+    int i = e / q, c = e - i * q;
+    V[e] = cplx<R>(i == c ? R(1) : R(0), R(0));
+  }
+  for (int e = threadIdx.x; e < qe; e += blockDim.x) order[e] = e;
+  __syncthreads();
+  const R tol = (sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON)) * sqrt(R(p > 1 ? p : 1));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < qe - 1; ++round) {
+      for (int pr = warp; pr < qe / 2; pr += nwarps) {
+        int a = order[pr], c = order[qe - 1 - pr];
+        if (a >= q || c >= q) continue;
+        if (a > c) { int t = a; a = c; c = t; }
+        R al = 0, be = 0;
+        cplx<R> ga(0, 0);
+        for (int i = lane; i < p; i += 32) {
+          cplx<R> x = G[(int64_t)i * q + a], y = G[(int64_t)i * q + c];
+          al += abs2(x);
+          be += abs2(y);
+          cfma_conj(ga, x, y);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
+          ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
+        }
+        R ag = sqrt(abs2(ga));
+        if (!(ag > tol * sqrt(al * be)) || ag == R(0)) continue;
+        // rotation making columns a, c orthogonal (complex Hestenes step)
+        cplx<R> ph(ga.re / ag, ga.im / ag);       // e^{i phi}
+        R zeta = (be - al) / (R(2) * ag);
+        R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+        R cs = R(1) / sqrt(R(1) + t * t);
+        R sn = cs * t;
+        // new_a = cs*a - sn*conj(ph)*c ; new_c = sn*ph*a + cs*c
+        cplx<R> f1 = sn * conjg(ph);
+        cplx<R> f2 = sn * ph;
+        for (int i = lane; i < p; i += 32) {
+          cplx<R> x = G[(int64_t)i * q + a], y = G[(int64_t)i * q + c];
+          G[(int64_t)i * q + a] = cs * x - f1 * y;
+          G[(int64_t)i * q + c] = f2 * x + cs * y;
+        }
+        for (int i = lane; i < q; i += 32) {
+          cplx<R> x = V[(int64_t)i * q + a], y = V[(int64_t)i * q + c];
+          V[(int64_t)i * q + a] = cs * x - f1 * y;
+          V[(int64_t)i * q + c] = f2 * x + cs * y;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+      // rotate the tournament: keep order[0], cycle the rest
+      if (threadIdx.x == 0) {
+        int last = order[qe - 1];
+        for (int i = qe - 1; i > 1; --i) order[i] = order[i - 1];
+        order[1] = last;
+      }
+      __syncthreads();
+    }
+    int any = s_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (threadIdx.x == 0 && sweeps_out) sweeps_out[b] = sweep;
+  // column norms
+  for (int c = warp; c < q; c += nwarps) {
+    R s = 0;
+    for (int i = lane; i < p; i += 32) s += abs2(G[(int64_t)i * q + c]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) norms[c] = sqrt(s);
+  }
+  __syncthreads();
+  // rank of each column by decreasing norm (ties by index) and scatter
+  cplx<R>* Vs = Vsorted_base + b * (int64_t)q * q;
+  for (int c = threadIdx.x; c < q; c += blockDim.x) {
+    R v = norms[c];
+    int rk = 0;
+    for (int i = 0; i < q; ++i) {
+      R u = norms[i];
+      rk += (u > v) || (u == v && i < c);
+    }
+    sigma_out[b * (int64_t)q + rk] = v;
+    for (int i = 0; i < q; ++i) Vs[(int64_t)i * q + rk] = V[(int64_t)i * q + c];
+  }
+}
+
+// Truncation rule on sorted singular values: smallest t >= 1 with
+// sqrt(sum_{j >= t} s_j^2) <= delta, then capped at max_rank.  Writes t and
+// whether the cap cut a rank the tolerance asked for, plus the discarded tail.
+template <class R>
+__global__ void trunc_rank_kernel(const R* __restrict__ s, int q, double delta, int max_rank,
+                                  int* __restrict__ out /* [t, capped] */, double* __restrict__ tail_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double tail2 = 0.0;
+  int t = q;
+  // walk from the end: tail2 after including s[j] is sum_{i >= j} s_i^2
+  for (int j = q - 1; j >= 1; --j) {
+    double v = (double)s[j];
+    double nt = tail2 + v * v;
+    if (sqrt(nt) <= delta) {
+      tail2 = nt;
+      t = j;
+    } else {
+      break;
+    }
+  }
+  if (q == 0) t = 0;
+  int capped = 0;
+  if (max_rank > 0 && t > max_rank) {
+    t = max_rank;
+    capped = 1;
+  }
+  double tl = 0.0;
+  for (int j = t; j < q; ++j) tl += (double)s[j] * (double)s[j];
+  out[0] = t;
+  out[1] = capped;
+  if (tail_out) *tail_out = sqrt(tl);
+}
+
+}  // namespace
+
+template <class R>
+int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
+             int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
+             int64_t out_bstride, int64_t ldr, cudaStream_t s, cplx<R>* tauws, cplx<R>* Qout,
+             int64_t q_bstride, int64_t ldq) {
+  if (batch <= 0 || m <= 0 || n <= 0) return QTT_OK;
+  if (Qout && !tauws) return QTT_ERR_ARG;
+  qr_r_kernel<R><<<(unsigned)batch, 256, 0, s>>>(in, inB, rowI, colI, conj_in, m, n, rows_total,
+                                                 rows_per_batch, W, out, out_bstride, ldr, tauws, Qout,
+                                                 q_bstride, ldq);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template <class R>
+int qtt_jacobi(cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, int q, int batch,
+               int max_sweeps, int* sweeps, cudaStream_t s) {
+  if (batch <= 0 || q <= 0) return QTT_OK;
+  int qe = q + (q & 1);
+  size_t sm = (size_t)(qe + (qe & 1)) * sizeof(int) + (size_t)q * sizeof(R) + 16;
+  if (sm > 48 * 1024) {
+    if (cudaFuncSetAttribute(jacobi_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      return QTT_ERR_CUDA;
+  }
+  jacobi_kernel<R><<<(unsigned)batch, 256, sm, s>>>(G, Vwork, sigma, Vsorted, p, q, max_sweeps, sweeps);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template <class R>
+int qtt_trunc_rank(const R* sigma, int q, double delta, int max_rank, int* out, double* tail, cudaStream_t s) {
+  trunc_rank_kernel<R><<<1, 32, 0, s>>>(sigma, q, delta, max_rank, out, tail);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template int qtt_qr_r<double>(const zc*, MIdx, MIdx, MIdx, int, int64_t, int64_t, int64_t, int64_t, int64_t,
+                              zc*, zc*, int64_t, int64_t, cudaStream_t, zc*, zc*, int64_t, int64_t);
+template int qtt_qr_r<float>(const cc*, MIdx, MIdx, MIdx, int, int64_t, int64_t, int64_t, int64_t, int64_t,
+                             cc*, cc*, int64_t, int64_t, cudaStream_t, cc*, cc*, int64_t, int64_t);
+template int qtt_jacobi<double>(zc*, zc*, double*, zc*, int, int, int, int, int*, cudaStream_t);
+template int qtt_jacobi<float>(cc*, cc*, float*, cc*, int, int, int, int, int*, cudaStream_t);
+template int qtt_trunc_rank<double>(const double*, int, double, int, int*, double*, cudaStream_t);
+template int qtt_trunc_rank<float>(const float*, int, double, int, int*, double*, cudaStream_t);

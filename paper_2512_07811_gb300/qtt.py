@@ -1,0 +1,384 @@
+"""Thin ctypes binding of include/qtt.h (argument marshalling only).
+
+Every operation runs in the CUDA kernels of libqtt.so; this module converts
+NumPy arrays / torch tensors to the plain pointers and sizes of the C-ABI and
+raises `QTTError` on a negative status.  There is no fallback: importing it
+fails loudly when the shared library has not been built, and creating a
+context fails without an sm_103 device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqtt.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libqtt.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = C.CDLL(LIB_PATH)
+
+C128, C64 = 0, 1
+PREC_F64, PREC_F32 = 0, 1
+_NP = {C128: np.complex128, C64: np.complex64}
+
+
+class QTTError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        msg = _lib.qtt_status_string(status).decode()
+        super().__init__("%s failed: %s (%d)" % (what, msg, status))
+
+
+class Complex(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class RoundInfo(C.Structure):
+    _fields_ = [("norm", C.c_double), ("delta", C.c_double), ("tail", C.c_double), ("err", C.c_double),
+                ("capped", C.c_int32), ("max_rank_out", C.c_int32)]
+
+
+class RVE(C.Structure):
+    _fields_ = [("ncomp", C.c_int32), ("nbits", C.c_int32), ("indicator", C.POINTER(C.c_double)),
+                ("k1", C.c_double), ("k2", C.c_double), ("lam1", C.c_double), ("mu1", C.c_double),
+                ("lam2", C.c_double), ("mu2", C.c_double), ("interleaved", C.c_int32)]
+
+
+class MSOpts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("eps", C.c_double), ("op_tol", C.c_double), ("max_iter", C.c_int32),
+                ("oversample", C.c_int32), ("load_mask", C.c_int32), ("min_iter", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class MSReport(C.Structure):
+    _fields_ = [("iterations", C.c_int32 * 6), ("residual", C.c_double * 6), ("sigma_imag_max", C.c_double),
+                ("max_rank_seen", C.c_int32), ("setup_ms", C.c_double), ("iterate_ms", C.c_double),
+                ("kernel_launches", C.c_int64)]
+
+
+_P = C.c_void_p
+_I32P = C.POINTER(C.c_int32)
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("qtt_status_string", C.c_char_p, [C.c_int])
+_sig("qtt_ctx_create", C.c_int, [C.c_int, _P, C.POINTER(_P)])
+_sig("qtt_ctx_destroy", None, [_P])
+_sig("qtt_ctx_sync", C.c_int, [_P])
+_sig("qtt_ctx_launch_count", C.c_int64, [_P])
+_sig("qtt_tt_create", C.c_int, [_P, C.c_int, _I32P, _I32P, C.c_int, C.POINTER(_P)])
+_sig("qtt_tt_destroy", None, [_P])
+_sig("qtt_tt_ncores", C.c_int, [_P])
+_sig("qtt_tt_ranks", C.c_int, [_P, _I32P])
+_sig("qtt_tt_modes", C.c_int, [_P, _I32P])
+_sig("qtt_tt_dtype", C.c_int, [_P])
+_sig("qtt_tt_core_ptr", _P, [_P, C.c_int])
+_sig("qtt_tt_from_host", C.c_int, [_P, C.c_int, _P])
+_sig("qtt_tt_to_host", C.c_int, [_P, C.c_int, _P])
+_sig("qtt_tt_from_device", C.c_int, [_P, C.c_int, _P])
+_sig("qtt_tt_convert", C.c_int, [_P, _P, C.c_int, C.POINTER(_P)])
+_sig("qtt_mpo_create", C.c_int, [_P, C.c_int, _I32P, _I32P, _I32P, C.c_int, C.POINTER(_P)])
+_sig("qtt_mpo_destroy", None, [_P])
+_sig("qtt_mpo_ranks", C.c_int, [_P, _I32P])
+_sig("qtt_mpo_from_host", C.c_int, [_P, C.c_int, _P])
+_sig("qtt_mpo_to_host", C.c_int, [_P, C.c_int, _P])
+_sig("tt_add", C.c_int, [_P, Complex, _P, Complex, _P, C.POINTER(_P)])
+_sig("tt_hadamard", C.c_int, [_P, _P, _P, C.POINTER(_P)])
+_sig("tt_mpo_apply", C.c_int, [_P, _P, _P, C.POINTER(_P)])
+_sig("tt_round", C.c_int, [_P, _P, C.c_double, C.c_int, C.c_int, C.POINTER(RoundInfo), C.POINTER(_P)])
+_sig("tt_round_sketched", C.c_int, [_P, C.c_int, C.POINTER(Complex), C.POINTER(_P), C.POINTER(_P), _P,
+                                    C.c_double, C.c_int, C.c_int, C.POINTER(RoundInfo), C.POINTER(_P)])
+_sig("tt_dot", C.c_int, [_P, _P, _P, C.POINTER(C.c_double)])
+_sig("tt_norm", C.c_int, [_P, _P, C.POINTER(C.c_double)])
+_sig("tt_from_dense", C.c_int, [_P, C.c_int, _I32P, _P, C.c_double, C.c_int, C.POINTER(_P)])
+_sig("qtt_qft_mpo", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(_P)])
+_sig("ms_homogenize", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
+                                C.POINTER(MSOpts), C.POINTER(C.c_double), C.POINTER(MSReport)])
+
+EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_sync", "qtt_ctx_launch_count",
+            "qtt_tt_create", "qtt_tt_destroy", "qtt_tt_ncores", "qtt_tt_ranks", "qtt_tt_modes", "qtt_tt_dtype",
+            "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
+            "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
+            "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_sketched", "tt_dot", "tt_norm",
+            "tt_from_dense", "qtt_qft_mpo", "ms_homogenize"]
+
+
+def _check(st, what):
+    if st != 0:
+        raise QTTError(st, what)
+
+
+def _i32(seq):
+    a = (C.c_int32 * len(seq))(*[int(v) for v in seq])
+    return a
+
+
+class Context:
+    """A device context bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = _P()
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:  # torch is optional plumbing
+                stream = None
+        _check(_lib.qtt_ctx_create(int(device), _P(stream) if stream else None, C.byref(h)), "qtt_ctx_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.qtt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def sync(self):
+        _check(_lib.qtt_ctx_sync(self.h), "qtt_ctx_sync")
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.qtt_ctx_launch_count(self.h))
+
+
+class TT:
+    """Handle of a library-owned tensor train."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    @classmethod
+    def from_cores(cls, ctx: Context, cores, dtype=C128):
+        cores = [np.ascontiguousarray(c, dtype=_NP[dtype]) for c in cores]
+        d = len(cores)
+        modes = [c.shape[1] for c in cores]
+        ranks = [cores[0].shape[0]] + [c.shape[2] for c in cores]
+        h = _P()
+        _check(_lib.qtt_tt_create(ctx.h, d, _i32(modes), _i32(ranks), dtype, C.byref(h)), "qtt_tt_create")
+        t = cls(ctx, h)
+        for k, c in enumerate(cores):
+            _check(_lib.qtt_tt_from_host(h, k, c.ctypes.data), "qtt_tt_from_host")
+        return t
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.qtt_tt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def ncores(self) -> int:
+        return int(_lib.qtt_tt_ncores(self.h))
+
+    @property
+    def ranks(self):
+        r = (C.c_int32 * (self.ncores + 1))()
+        _check(_lib.qtt_tt_ranks(self.h, r), "qtt_tt_ranks")
+        return list(r)
+
+    @property
+    def modes(self):
+        m = (C.c_int32 * self.ncores)()
+        _check(_lib.qtt_tt_modes(self.h, m), "qtt_tt_modes")
+        return list(m)
+
+    @property
+    def dtype(self) -> int:
+        return int(_lib.qtt_tt_dtype(self.h))
+
+    def cores(self):
+        out = []
+        r, m = self.ranks, self.modes
+        for k in range(self.ncores):
+            a = np.empty((r[k], m[k], r[k + 1]), dtype=_NP[self.dtype])
+            _check(_lib.qtt_tt_to_host(self.h, k, a.ctypes.data), "qtt_tt_to_host")
+            out.append(a)
+        return out
+
+    def core_ptr(self, k: int) -> int:
+        return int(_lib.qtt_tt_core_ptr(self.h, k))
+
+    def convert(self, dtype):
+        h = _P()
+        _check(_lib.qtt_tt_convert(self.ctx.h, self.h, dtype, C.byref(h)), "qtt_tt_convert")
+        return TT(self.ctx, h)
+
+
+class MPO:
+    def __init__(self, ctx: Context, handle, d: int):
+        self.ctx = ctx
+        self.h = handle
+        self.d = d
+
+    @classmethod
+    def from_cores(cls, ctx: Context, cores, dtype=C128):
+        cores = [np.ascontiguousarray(c, dtype=_NP[dtype]) for c in cores]
+        d = len(cores)
+        mo = [c.shape[1] for c in cores]
+        mi = [c.shape[2] for c in cores]
+        g = [cores[0].shape[0]] + [c.shape[3] for c in cores]
+        h = _P()
+        _check(_lib.qtt_mpo_create(ctx.h, d, _i32(mo), _i32(mi), _i32(g), dtype, C.byref(h)), "qtt_mpo_create")
+        A = cls(ctx, h, d)
+        for k, c in enumerate(cores):
+            _check(_lib.qtt_mpo_from_host(h, k, c.ctypes.data), "qtt_mpo_from_host")
+        A._shapes = [c.shape for c in cores]
+        A._dtype = dtype
+        return A
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.qtt_mpo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def ranks(self):
+        r = (C.c_int32 * (self.d + 1))()
+        _check(_lib.qtt_mpo_ranks(self.h, r), "qtt_mpo_ranks")
+        return list(r)
+
+    def cores(self, shapes=None, dtype=C128):
+        shapes = shapes or self._shapes
+        out = []
+        for k, s in enumerate(shapes):
+            a = np.empty(s, dtype=_NP[dtype])
+            _check(_lib.qtt_mpo_to_host(self.h, k, a.ctypes.data), "qtt_mpo_to_host")
+            out.append(a)
+        return out
+
+
+def _cx(v) -> Complex:
+    v = complex(v)
+    return Complex(v.real, v.imag)
+
+
+def tt_add(ctx: Context, a, x: TT, b, y: TT) -> TT:
+    h = _P()
+    _check(_lib.tt_add(ctx.h, _cx(a), x.h, _cx(b), y.h, C.byref(h)), "tt_add")
+    return TT(ctx, h)
+
+
+def tt_hadamard(ctx: Context, x: TT, y: TT) -> TT:
+    h = _P()
+    _check(_lib.tt_hadamard(ctx.h, x.h, y.h, C.byref(h)), "tt_hadamard")
+    return TT(ctx, h)
+
+
+def tt_mpo_apply(ctx: Context, A: MPO, x: TT) -> TT:
+    h = _P()
+    _check(_lib.tt_mpo_apply(ctx.h, A.h, x.h, C.byref(h)), "tt_mpo_apply")
+    return TT(ctx, h)
+
+
+def tt_round(ctx: Context, x: TT, eps: float, max_rank: int = 0, prec=None):
+    if prec is None:
+        prec = PREC_F64 if x.dtype == C128 else PREC_F32
+    h = _P()
+    info = RoundInfo()
+    _check(_lib.tt_round(ctx.h, x.h, float(eps), int(max_rank), int(prec), C.byref(info), C.byref(h)), "tt_round")
+    return TT(ctx, h), info
+
+
+def tt_round_sketched(ctx: Context, terms, sketch: TT, eps: float, max_rank: int = 0, prec=None):
+    """terms: list of (coef, MPO or None, TT)."""
+    if prec is None:
+        prec = PREC_F64 if sketch.dtype == C128 else PREC_F32
+    T = len(terms)
+    coefs = (Complex * T)(*[_cx(c) for c, _, _ in terms])
+    ops = (_P * T)(*[(A.h if A is not None else None) for _, A, _ in terms])
+    xs = (_P * T)(*[x.h for _, _, x in terms])
+    h = _P()
+    info = RoundInfo()
+    _check(_lib.tt_round_sketched(ctx.h, T, coefs, ops, xs, sketch.h, float(eps), int(max_rank), int(prec),
+                                  C.byref(info), C.byref(h)), "tt_round_sketched")
+    return TT(ctx, h), info
+
+
+def tt_dot(ctx: Context, x: TT, y: TT) -> complex:
+    out = (C.c_double * 2)()
+    _check(_lib.tt_dot(ctx.h, x.h, y.h, out), "tt_dot")
+    return complex(out[0], out[1])
+
+
+def tt_norm(ctx: Context, x: TT) -> float:
+    out = C.c_double()
+    _check(_lib.tt_norm(ctx.h, x.h, C.byref(out)), "tt_norm")
+    return float(out.value)
+
+
+def tt_from_dense(ctx: Context, dense_device_ptr: int, modes, eps: float, max_rank: int = 0) -> TT:
+    """TT-SVD of a complex128 dense tensor already in device memory (e.g. a torch tensor's data_ptr())."""
+    h = _P()
+    _check(_lib.tt_from_dense(ctx.h, len(modes), _i32(modes), _P(dense_device_ptr), float(eps), int(max_rank),
+                              C.byref(h)), "tt_from_dense")
+    return TT(ctx, h)
+
+
+def qtt_qft_mpo(ctx: Context, nbits: int, sign: int = -1, tol: float = 1e-12) -> MPO:
+    h = _P()
+    _check(_lib.qtt_qft_mpo(ctx.h, int(nbits), int(sign), float(tol), C.byref(h)), "qtt_qft_mpo")
+    A = MPO(ctx, h, nbits)
+    g = A.ranks
+    A._shapes = [(g[k], 2, 2, g[k + 1]) for k in range(nbits)]
+    A._dtype = C128
+    return A
+
+
+def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, tol: float, max_rank: int,
+                  eps: float = 1e-6, op_tol: float = 1e-10, prec: int = PREC_F64, max_iter: int = 100,
+                  oversample: int = 8, load_mask: int | None = None, interleaved: bool = True,
+                  min_iter: int = 1, seed: int = 12345):
+    """Effective tensor of a two-phase RVE (phase 2 where indicator == 1).
+
+    kind "scalar": moduli = (k1, k2), C0 = 3x3; kind "elastic": moduli =
+    (lam1, mu1, lam2, mu2), C0 = Voigt 6x6.  Returns (C_eff, report)."""
+    ind = np.ascontiguousarray(indicator, dtype=np.float64)
+    N = ind.shape[0]
+    nbits = int(round(np.log2(N)))
+    assert ind.shape == (N, N, N) and (1 << nbits) == N
+    rve = RVE()
+    rve.nbits = nbits
+    rve.indicator = ind.ctypes.data_as(C.POINTER(C.c_double))
+    rve.interleaved = 1 if interleaved else 0
+    if kind == "scalar":
+        rve.ncomp = 3
+        rve.k1, rve.k2 = map(float, moduli)
+    else:
+        rve.ncomp = 6
+        rve.lam1, rve.mu1, rve.lam2, rve.mu2 = map(float, moduli)
+    nc = rve.ncomp
+    C0a = np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(nc, nc))
+    o = MSOpts()
+    o.prec = int(prec)
+    o.eps = float(eps)
+    o.op_tol = float(op_tol)
+    o.max_iter = int(max_iter)
+    o.oversample = int(oversample)
+    o.load_mask = int(load_mask if load_mask is not None else (1 << nc) - 1)
+    o.min_iter = int(min_iter)
+    o.seed = int(seed)
+    out = np.zeros((nc, nc), dtype=np.float64)
+    rep = MSReport()
+    _check(_lib.ms_homogenize(ctx.h, C.byref(rve), C0a.ctypes.data_as(C.POINTER(C.c_double)), float(tol),
+                              int(max_rank), C.byref(o), out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep)),
+           "ms_homogenize")
+    return out, rep

@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Tolerances: placement work (tt_add with exactly representable scales) is
+bit-exact; FP64 arithmetic is compared at 1e-12 relative on gauge-invariant
+quantities (contracted tensors, norms of difference trains computed by the
+oracle, inner products, singular-value ranks); FP32 storage at 1e-5.
+Sizes span several 64-wide GEMM tiles and ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ms as MS
+from oracle import qft as QF
+from oracle import randround as RR
+from oracle import tt as T
+from paper_2512_07811_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2512_07811_gb300 import qtt
+    return qtt
+
+
+@pytest.fixture(scope="module")
+def ctx(Q):
+    return Q.Context(0)
+
+
+def cplx_tt(dims, ranks, seed):
+    rng = np.random.default_rng(seed)
+    return [(rng.standard_normal((ranks[k], n, ranks[k + 1]))
+             + 1j * rng.standard_normal((ranks[k], n, ranks[k + 1]))) / math.sqrt(2 * max(ranks))
+            for k, n in enumerate(dims)]
+
+
+def rel_diff(a, b):
+    """||a - b|| / ||b|| computed by the oracle on the difference train."""
+    nb = T.tt_norm(b)
+    return T.tt_norm(T.tt_add(a, b, 1.0, -1.0)) / (nb if nb > 0 else 1.0)
+
+
+DIMS = [2, 3, 2, 2, 5, 2, 2, 3]
+RA = [1, 2, 6, 12, 70, 9, 6, 3, 1]
+RB = [1, 3, 5, 65, 8, 10, 4, 3, 1]
+
+
+@pytest.mark.parametrize("a,b", [(1.0, 1.0), (1.0, -1.0), (2.0, 0.5), (0.5j, -4.0)])
+def test_tt_add_bit_exact(Q, ctx, a, b):
+    x, y = cplx_tt(DIMS, RA, 1), cplx_tt(DIMS, RB, 2)
+    z = Q.tt_add(ctx, a, Q.TT.from_cores(ctx, x), b, Q.TT.from_cores(ctx, y))
+    ref = T.tt_add(x, y, a, b)
+    assert z.ranks == T.tt_ranks(ref)
+    for g, r in zip(z.cores(), ref):
+        assert np.array_equal(g, r)
+
+
+def test_tt_hadamard(Q, ctx):
+    x, y = cplx_tt(DIMS, RA, 3), cplx_tt(DIMS, RB, 4)
+    z = Q.tt_hadamard(ctx, Q.TT.from_cores(ctx, x), Q.TT.from_cores(ctx, y))
+    ref = T.tt_hadamard(x, y)
+    assert z.ranks == T.tt_ranks(ref)
+    for g, r in zip(z.cores(), ref):
+        np.testing.assert_allclose(g, r, rtol=0, atol=4e-16 * np.abs(r).max())
+
+
+def test_tt_mpo_apply(Q, ctx):
+    rng = np.random.default_rng(5)
+    gr = [1, 2, 3, 4, 2, 3, 2, 2, 1]
+    mpo = [(rng.standard_normal((gr[k], n + (k % 2), n, gr[k + 1]))
+            + 1j * rng.standard_normal((gr[k], n + (k % 2), n, gr[k + 1]))) for k, n in enumerate(DIMS)]
+    x = cplx_tt(DIMS, RA, 6)
+    z = Q.tt_mpo_apply(ctx, Q.MPO.from_cores(ctx, mpo), Q.TT.from_cores(ctx, x))
+    ref = T.tt_mpo_apply(mpo, x)
+    assert z.ranks == T.tt_ranks(ref)
+    for g, r in zip(z.cores(), ref):
+        np.testing.assert_allclose(g, r, rtol=0, atol=1e-14 * np.abs(r).max())
+
+
+def test_tt_dot_and_norm(Q, ctx):
+    x, y = cplx_tt(DIMS, RA, 7), cplx_tt(DIMS, RB, 8)
+    gx, gy = Q.TT.from_cores(ctx, x), Q.TT.from_cores(ctx, y)
+    v = Q.tt_dot(ctx, gx, gy)
+    ref = T.tt_dot(x, y)
+    assert abs(v - ref) <= 1e-12 * T.tt_norm(x) * T.tt_norm(y)
+    assert math.isclose(Q.tt_norm(ctx, gx), T.tt_norm(x), rel_tol=1e-12)
+
+
+def test_round_gapped_spectrum_matches_oracle(Q, ctx):
+    """A rank-k train written at rank 2k: unique truncation ranks, 1e-12 parity."""
+    base = I.random_tt_cores(16, 2, 24, seed=11, dtype=np.complex128)
+    x = T.tt_add(base, base, 1.0, 0.75)
+    g = Q.TT.from_cores(ctx, x)
+    y, info = Q.tt_round(ctx, g, 1e-10)
+    ref, rinfo = T.tt_round(x, 1e-10)
+    assert y.ranks == T.tt_ranks(ref) == T.tt_ranks(base)
+    assert math.isclose(info.norm, rinfo["norm"], rel_tol=1e-12)
+    assert rel_diff(y.cores(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-3, 1e-6])
+def test_round_bound_and_oracle_agreement(Q, ctx, eps):
+    rng = np.random.default_rng(12)
+    dims = [2] * 14
+    low = I.random_tt_cores(14, 2, 40, seed=13, dtype=np.complex128)
+    noise = I.random_tt_cores(14, 2, 20, seed=14, dtype=np.complex128)
+    x = T.tt_add(low, noise, 1.0, 1e-3)
+    y, info = Q.tt_round(ctx, Q.TT.from_cores(ctx, x), eps)
+    yc = y.cores()
+    err = rel_diff(yc, x)
+    assert err <= eps * (1 + 1e-9)
+    ref, _ = T.tt_round(x, eps)
+    # where the oracle and the GPU chose the same ranks, the results agree
+    if y.ranks == T.tt_ranks(ref):
+        assert rel_diff(yc, ref) < 1e-10
+    # right-orthonormal cores 2..d
+    for c in yc[1:]:
+        M = c.reshape(c.shape[0], -1)
+        np.testing.assert_allclose(M @ M.conj().T, np.eye(c.shape[0]), atol=1e-12)
+
+
+def test_round_forced_by_max_rank(Q, ctx):
+    x = I.random_tt_cores(12, 2, 32, seed=15, dtype=np.complex128)
+    y, info = Q.tt_round(ctx, Q.TT.from_cores(ctx, x), 1e-12, max_rank=9)
+    ref, rinfo = T.tt_round(x, 1e-12, max_rank=9)
+    assert info.capped == 1 and rinfo["capped"]
+    assert y.ranks == T.tt_ranks(ref)
+    assert rel_diff(y.cores(), ref) < 1e-10
+
+
+def test_round_fp32(Q, ctx):
+    base = I.random_tt_cores(14, 2, 20, seed=16, dtype=np.complex128)
+    x = T.tt_add(base, base, 1.0, 1.0)
+    g = Q.TT.from_cores(ctx, x, dtype=Q.C64)
+    y, info = Q.tt_round(ctx, g, 1e-4)
+    assert y.ranks == T.tt_ranks(base)
+    assert rel_diff([c.astype(np.complex128) for c in y.cores()], T.tt_scale(2.0, base)) < 1e-5
+
+
+def test_round_edge_cases(Q, ctx):
+    # one core
+    x = [np.arange(5, dtype=np.complex128).reshape(1, 5, 1)]
+    y, info = Q.tt_round(ctx, Q.TT.from_cores(ctx, x), 1e-8)
+    np.testing.assert_array_equal(y.cores()[0], x[0])
+    # zero train rounds to rank 1 zero
+    z = [np.zeros((1, 2, 3)), np.zeros((3, 2, 3)), np.zeros((3, 2, 1))]
+    y, info = Q.tt_round(ctx, Q.TT.from_cores(ctx, z), 1e-8)
+    assert y.ranks == [1, 1, 1, 1] and info.norm == 0.0
+    assert all(np.count_nonzero(c) == 0 for c in y.cores()[:1])
+    # ranks limited by mode products (rank-deficient R factors)
+    w = I.random_tt_cores(6, 3, 50, seed=17, dtype=np.complex128, ranks=[1, 3, 9, 27, 9, 3, 1])
+    y, _ = Q.tt_round(ctx, Q.TT.from_cores(ctx, w), 1e-13)
+    assert rel_diff(y.cores(), w) < 1e-12
+
+
+def test_sketched_rounding_matches_oracle(Q, ctx):
+    """Same Gaussian sketch on both sides: the projected trains agree to 1e-11."""
+    dims = [2] * 12
+    x = I.random_tt_cores(12, 2, 16, seed=21, dtype=np.complex128)
+    rng = np.random.default_rng(22)
+    gr = [1] + [3] * 11 + [1]
+    mpo = [(rng.standard_normal((gr[k], 2, 2, gr[k + 1])) + 1j * rng.standard_normal((gr[k], 2, 2, gr[k + 1])))
+           / 2.0 for k in range(12)]
+    y = I.random_tt_cores(12, 2, 5, seed=23, dtype=np.complex128)
+    ell = 30
+    sr = RR.sketch_ranks(12, dims, ell)
+    S = [rng.standard_normal((sr[k], 2, sr[k + 1])).astype(np.complex128) for k in range(12)]
+    s_full = T.tt_add(T.tt_mpo_apply(mpo, x), y, 1.5, -0.5)
+    P = RR.rand_orth(s_full, S)
+    ref, _ = T.tt_round(P, 1e-12)
+    g, info = Q.tt_round_sketched(ctx, [(1.5, Q.MPO.from_cores(ctx, mpo), Q.TT.from_cores(ctx, x)),
+                                        (-0.5, None, Q.TT.from_cores(ctx, y))],
+                                  Q.TT.from_cores(ctx, S), 1e-12)
+    assert rel_diff(g.cores(), ref) < 1e-11
+    # and the result is close to the exact sum (the sketch width covers rank 16*3+5)
+    assert rel_diff(g.cores(), s_full) < 0.5
+
+
+def test_sketched_exact_for_low_rank_sum(Q, ctx):
+    x = I.random_tt_cores(10, 2, 6, seed=24, dtype=np.complex128)
+    rng = np.random.default_rng(25)
+    sr = RR.sketch_ranks(10, [2] * 10, 14)
+    S = [rng.standard_normal((sr[k], 2, sr[k + 1])).astype(np.complex128) for k in range(10)]
+    g, info = Q.tt_round_sketched(ctx, [(1.0, None, Q.TT.from_cores(ctx, x)), (2.0, None, Q.TT.from_cores(ctx, x))],
+                                  Q.TT.from_cores(ctx, S), 1e-12)
+    assert rel_diff(g.cores(), T.tt_scale(3.0, x)) < 1e-12
+    assert g.ranks == T.tt_ranks(x)
+
+
+def test_tt_from_dense_matches_tt_svd(Q, ctx):
+    import torch
+    rng = np.random.default_rng(26)
+    low = cplx_tt([4, 2, 3, 2, 2, 4, 2], [1, 3, 5, 7, 6, 4, 2, 1], 27)
+    F = T.tt_full(low) + 1e-9 * (rng.standard_normal(T.tt_full(low).shape))
+    dev = torch.from_numpy(np.ascontiguousarray(F.astype(np.complex128))).cuda()
+    g = Q.tt_from_dense(ctx, dev.data_ptr(), list(F.shape), 1e-6)
+    ref = T.tt_svd(F, 1e-6)
+    assert g.ranks == T.tt_ranks(ref)
+    np.testing.assert_allclose(T.tt_full(g.cores()), F, atol=1e-6 * np.linalg.norm(F))
+
+
+@pytest.mark.parametrize("n", [1, 3, 6, 9])
+def test_qft_mpo_is_bitreversed_dft(Q, ctx, n):
+    A = Q.qtt_qft_mpo(ctx, n, -1, 1e-12)
+    M = T.mpo_full(A.cores())
+    N = 1 << n
+    F = np.fft.fft(np.eye(N), norm="ortho", axis=0)
+    np.testing.assert_allclose(M, F[QF.bit_reverse_indices(n)], atol=1e-10)
+    assert max(A.ranks) <= 16
+
+
+def test_ms_scalar_laminate_config1_shape(Q, ctx):
+    """32^3 laminate, 15 interleaved bit sites: the exact 20/11 and 11/2."""
+    ind = I.laminate_indicator(32)
+    C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), tol=1e-12, max_rank=64,
+                             eps=1e-8, max_iter=50, prec=Q.PREC_F64)
+    np.testing.assert_allclose(C, MS.scalar_laminate_keff(1.0, 10.0, 0.5), atol=1e-10)
+    assert max(rep.iterations[:3]) <= 3
+    assert rep.sigma_imag_max < 1e-10
+
+
+def test_ms_elastic_laminate_backus(Q, ctx):
+    lam1, mu1 = I.lame_from_young(1.0, 0.3)
+    lam2, mu2 = I.lame_from_young(10.0, 0.3)
+    ind = I.laminate_indicator(8)
+    C0 = MS.iso_voigt(0.5 * (lam1 + lam2), 0.5 * (mu1 + mu2))
+    C, rep = Q.ms_homogenize(ctx, ind, "elastic", (lam1, mu1, lam2, mu2), C0, tol=1e-13, max_rank=32,
+                             eps=1e-12, max_iter=200, prec=Q.PREC_F64)
+    Cx = MS.elastic_laminate_ceff([lam2, lam1], [mu2, mu1], [0.5, 0.5])
+    np.testing.assert_allclose(C, Cx, atol=1e-9 * np.abs(Cx).max())
+
+
+def test_ms_scalar_sphere_matches_dense_oracle(Q, ctx):
+    pb = MS.scalar_problem(I.sphere_indicator(8, 0.2), 1.0, 10.0)
+    Cd, _ = MS.effective_tensor_dense(pb, tol=1e-10, max_iter=500)
+    C, rep = Q.ms_homogenize(ctx, pb.indicator, "scalar", (1.0, 10.0), pb.C0, tol=1e-10, max_rank=200,
+                             eps=1e-10, max_iter=200, oversample=16, prec=Q.PREC_F64)
+    assert np.linalg.norm(C - Cd.real) / np.linalg.norm(Cd.real) < 1e-7
+
+
+def test_ms_fp32_laminate(Q, ctx):
+    ind = I.laminate_indicator(16)
+    C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), tol=1e-6, max_rank=32,
+                             eps=1e-6, max_iter=20, prec=Q.PREC_F32)
+    Cx = MS.scalar_laminate_keff(1.0, 10.0, 0.5)
+    assert np.abs(C - Cx).max() / np.abs(Cx).max() < 1e-5
