@@ -2,6 +2,8 @@
 // Moulinec-Suquet driver (Algorithm 2 of arXiv 2512.07811) composed from the
 // device algorithms in engine.cu.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -137,6 +139,35 @@ int mpo_apply_dev(qtt_ctx* c, const qtt_mpo* A, const qtt_tt* x, qtt_tt** out) {
   }
   *out = z;
   return QTT_OK;
+}
+
+// Non-finite scan of every core of a train (one flag word, one sync).
+int tt_finite(qtt_ctx* c, const qtt_tt* x, int* finite) {
+  void* flag;
+  TRY(dalloc(c, &flag, sizeof(int)));
+  cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+  for (int k = 0; k < x->d; ++k) {
+    int64_t cnt = (int64_t)x->r[k] * x->n[k] * x->r[k + 1];
+    c->launches++;
+    if (x->dtype == QTT_C128)
+      qtt_isfinite<double>(core_ptr<zc>(x, k), cnt, reinterpret_cast<int*>(flag), c->stream);
+    else
+      qtt_isfinite<float>(core_ptr<cc>(x, k), cnt, reinterpret_cast<int*>(flag), c->stream);
+  }
+  int h = 0;
+  int s = sync_read(c, &h, flag, sizeof(int));
+  dfree(c, flag);
+  *finite = !h;
+  return s;
+}
+
+bool debug_checks() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("QTT_DEBUG_CHECKS");
+    v = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return v == 1;
 }
 
 int check_prec(qtt_dtype dt, qtt_prec p) {
@@ -683,6 +714,19 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     }
   } fr{{dCa, dCb, G, Q[0], Q[1], Q[2], Qi[0], Qi[1], Qi[2]}};
 
+  const char* stage = "";
+  int cur_it = 0, cur_lc = 0;
+  auto finite_or_fail = [&](const qtt_tt* t, const char* tag) -> int {
+    if (!debug_checks()) return QTT_OK;
+    int ok = 1;
+    TRY(tt_finite(c, t, &ok));
+    if (!ok) {
+      fprintf(stderr, "qtt: non-finite values after %s (%s), load case %d, iteration %d\n", tag, stage, cur_lc,
+              cur_it);
+      return QTT_ERR_NAN;
+    }
+    return QTT_OK;
+  };
   auto sk_round = [&](int T, const qtt_complex* cf, const qtt_mpo* const* A, const qtt_tt* const* X,
                       qtt_tt** out) -> int {
     qtt_tt* S = nullptr;
@@ -691,6 +735,10 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     int s = round_sketched<R>(c, T, cf, A, X, S, o.eps, max_rank, &info, out);
     tt_free(S);
     if (!s && rep) rep->max_rank_seen = std::max(rep->max_rank_seen, info.max_rank_out);
+    if (!s) s = finite_or_fail(*out, "sketched rounding");
+    if (!s && debug_checks())
+      fprintf(stderr, "qtt: lc %d it %d %s norm %.3e delta %.3e tail %.3e rank %d\n", cur_lc, cur_it, stage,
+              info.norm, info.delta, info.tail, info.max_rank_out);
     return s;
   };
   double sig_im = 0;
@@ -706,7 +754,10 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     int it = 0;
     double res = 1.0;
     const qtt_complex one = {1.0, 0.0};
+    cur_lc = lc;
     for (it = 1; it <= o.max_iter; ++it) {
+      cur_it = it;
+      stage = "tau";
       qtt_tt* tau = nullptr;
       {
         qtt_complex cf[2] = {one, one};
@@ -715,7 +766,10 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         TRY(sk_round(2, cf, A, X, &tau));
       }
       qtt_tt* h = tau;
+      static const char* fwd[3] = {"S0", "S1", "S2"};
+      static const char* inv[3] = {"Si0", "Si1", "Si2"};
       for (int dim = 0; dim < 3; ++dim) {
+        stage = fwd[dim];
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {Q[dim]};
         const qtt_tt* X[1] = {h};
@@ -725,6 +779,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         h = hn;
       }
       {
+        stage = "Gamma";
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {G};
         const qtt_tt* X[1] = {h};
@@ -734,6 +789,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         h = hn;
       }
       for (int dim = 2; dim >= 0; --dim) {
+        stage = inv[dim];
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {Qi[dim]};
         const qtt_tt* X[1] = {h};
@@ -747,9 +803,20 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
       int s = add_dev<R>(c, C(1, 0), E, C(-1, 0), h, &sum);
       tt_free(h);
       if (s) return s;
+      stage = "update";
       s = round_det<R>(c, sum, o.eps, max_rank, nullptr, nullptr, &xn);
       tt_free(sum);
       if (s) return s;
+      // the new iterate is always scanned: a non-finite strain ends the solve with QTT_ERR_NAN
+      {
+        int ok = 1;
+        TRY(tt_finite(c, xn, &ok));
+        if (!ok) {
+          if (debug_checks()) fprintf(stderr, "qtt: non-finite iterate, load case %d iteration %d\n", lc, it);
+          tt_free(xn);
+          return QTT_ERR_NAN;
+        }
+      }
       // relative change, on the difference train (orthogonalisation, no cancellation)
       qtt_tt* diff = nullptr;
       TRY(add_dev<R>(c, C(1, 0), xn, C(-1, 0), x, &diff));

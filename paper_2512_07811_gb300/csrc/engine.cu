@@ -4,6 +4,8 @@
 // context's stream; the host only sizes buffers and reads back the ranks that
 // the truncations choose.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -153,6 +155,34 @@ int gemm(qtt_ctx* c, const GemmDesc& g, const cplx<R>* A, const cplx<R>* B, cplx
     if (_st != QTT_OK) return _st; \
   } while (0)
 
+static bool dbg_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("QTT_DEBUG_CHECKS");
+    v = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+// Debug-only non-finite scan of an intermediate buffer (QTT_DEBUG_CHECKS=1).
+template <class R>
+static int dbg_finite(qtt_ctx* c, const cplx<R>* p, int64_t count, const char* tag, int k) {
+  if (!dbg_enabled() || count <= 0) return QTT_OK;
+  void* flag;
+  if (dalloc(c, &flag, sizeof(int))) return QTT_ERR_OOM;
+  cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+  qtt_isfinite<R>(p, count, reinterpret_cast<int*>(flag), c->stream);
+  int h = 0;
+  int s = sync_read(c, &h, flag, sizeof(int));
+  dfree(c, flag);
+  if (s) return s;
+  if (h) {
+    fprintf(stderr, "qtt-debug: non-finite in %s (core %d, %lld elements)\n", tag, k, (long long)count);
+    return QTT_ERR_NAN;
+  }
+  return QTT_OK;
+}
+
 // RAII device buffer on the context stream
 struct DBuf {
   qtt_ctx* c = nullptr;
@@ -286,6 +316,8 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     TRY(Rf[k].alloc(c, (size_t)rp[k + 1] * a1 * sizeof(cplx<R>)));
     int64_t got = 0;
     TRY(tsqr_r<R>(c, M, L1(m, a1), L1(a1, 1), 0, m, a1, Rf[k].as<cplx<R>>(), &got));
+    TRY(dbg_finite<R>(c, M, m * a1, "round sweep1 M", k));
+    TRY(dbg_finite<R>(c, Rf[k].as<cplx<R>>(), rp[k + 1] * a1, "round sweep1 R", k));
   }
   // ---- norm from the orthogonality centre R_{d-2} A_{d-1}
   DBuf scal;
@@ -316,12 +348,32 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     const int64_t nk = n[k], tk = nr[k + 1], Tcols = nk * tk;
     const int64_t rk = rp[k];  // rows of R_{k-1}
     const int64_t a0 = r[k];
-    DBuf Cb, U, sig;
+    DBuf Cb, U, UG, sig, Rc, Qc, Wq, tau, Vw;
     TRY(Cb.alloc(c, (size_t)rk * Tcols * sizeof(cplx<R>)));
     TRY(mm<R>(c, rk, Tcols, a0, Rf[k - 1].as<cplx<R>>(), a0, 1, 0, T, Tcols, 1, 0, Cb.as<cplx<R>>(), Tcols, 1));
+    // SVD of C (rk x Tcols): C^H = Q_c R_c (Householder, explicit Q_c), then
+    // one-sided Jacobi R_c V = U_G S.  Left vectors of C: V; right: Q_c U_G.
+    const int64_t pq = std::min(rk, Tcols);
+    TRY(Rc.alloc(c, (size_t)pq * rk * sizeof(cplx<R>)));
+    TRY(Qc.alloc(c, (size_t)Tcols * pq * sizeof(cplx<R>)));
+    TRY(Wq.alloc(c, (size_t)Tcols * rk * sizeof(cplx<R>)));
+    TRY(tau.alloc(c, (size_t)2 * rk * sizeof(cplx<R>)));
+    c->launches++;
+    TRY(qtt_qr_r<R>(Cb.as<cplx<R>>(), B0(), L1(Tcols, 1), L1(rk, Tcols), 1, Tcols, rk, Tcols, Tcols, 1,
+                    Wq.as<cplx<R>>(), Rc.as<cplx<R>>(), 0, rk, c->stream, tau.as<cplx<R>>(), Qc.as<cplx<R>>(), 0,
+                    pq));
     TRY(U.alloc(c, (size_t)rk * rk * sizeof(cplx<R>)));
+    TRY(UG.alloc(c, (size_t)pq * rk * sizeof(cplx<R>)));
+    TRY(Vw.alloc(c, (size_t)rk * rk * sizeof(cplx<R>)));
     TRY(sig.alloc(c, (size_t)rk * sizeof(R)));
-    TRY(left_svd<R>(c, Cb.as<cplx<R>>(), rk, Tcols, Tcols, U.as<cplx<R>>(), sig.as<R>()));
+    c->launches++;
+    TRY(dbg_finite<R>(c, Cb.as<cplx<R>>(), rk * Tcols, "round sweep2 C", k));
+    TRY(dbg_finite<R>(c, Rc.as<cplx<R>>(), pq * rk, "round sweep2 Rc", k));
+    TRY(dbg_finite<R>(c, Qc.as<cplx<R>>(), Tcols * pq, "round sweep2 Qc", k));
+    TRY(qtt_jacobi<R>(Rc.as<cplx<R>>(), Vw.as<cplx<R>>(), sig.as<R>(), U.as<cplx<R>>(), (int)pq, (int)rk, 1, 60,
+                      nullptr, c->stream, UG.as<cplx<R>>()));
+    TRY(dbg_finite<R>(c, U.as<cplx<R>>(), rk * rk, "round sweep2 U", k));
+    TRY(dbg_finite<R>(c, UG.as<cplx<R>>(), pq * rk, "round sweep2 UG", k));
     int t;
     if (forced) {
       t = (int)std::min<int64_t>(forced[k], rk);
@@ -340,12 +392,11 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     if (!forced) capped |= hv[1];
     tail2 += tl * tl;
     nr[k] = t;
-    // new core k = S_t^{-1} U_t^H C  (t x Tcols)
+    // new core k = (Q_c U_G[:, :t])^H = U_G[:, :t]^H Q_c^H  (t x Tcols)
     TRY(newc[k].alloc(c, (size_t)t * Tcols * sizeof(cplx<R>)));
     cplx<R>* core = newc[k].as<cplx<R>>();
-    TRY(mm<R>(c, t, Tcols, rk, U.as<cplx<R>>(), 1, rk, 1, Cb.as<cplx<R>>(), Tcols, 1, 0, core, Tcols, 1));
-    c->launches++;
-    TRY(qtt_scale_rows<R>(core, t, Tcols, Tcols, sig.as<R>(), 1, c->stream));
+    TRY(mm<R>(c, t, Tcols, pq, UG.as<cplx<R>>(), 1, rk, 1, Qc.as<cplx<R>>(), 1, pq, 1, core, Tcols, 1));
+    TRY(dbg_finite<R>(c, core, t * Tcols, "round sweep2 core", k));
     // P = T core^H (a0 x t); T_{k-1} = A_{k-1} P (r_{k-2} n_{k-1} x t)
     DBuf P, Tn;
     TRY(P.alloc(c, (size_t)a0 * t * sizeof(cplx<R>)));
@@ -608,6 +659,7 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
         g.conjA = g.conjB = 0;
         TRY(gemm<R>(c, g, Wn, Sk(k), U1.as<C>()));
       }
+      TRY(dbg_finite<R>(c, U1.as<C>(), g1 * a1 * no * l0, "sketch U1", k));
       // U2[a1, g0, j, l0] = sum_{i, g1} D[g0, i, j, g1] U1[g1, a1, i, l0]   (batch a1)
       TRY(U2.alloc(c, (size_t)a1 * g0 * ni * l0 * sizeof(C)));
       {
@@ -628,6 +680,7 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
         g.conjA = g.conjB = 0;
         TRY(gemm<R>(c, g, Dk(t, k), U1.as<C>(), U2.as<C>()));
       }
+      TRY(dbg_finite<R>(c, U2.as<C>(), a1 * g0 * ni * l0, "sketch U2", k));
       // W_k[g0, a0, l0] = sum_{j, a1} X[a0, j, a1] U2[a1, g0, j, l0]   (batch g0)
       {
         GemmDesc g;
@@ -648,6 +701,7 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
         TRY(gemm<R>(c, g, Xk(t, k), U2.as<C>(), W[k].as<C>() + boff[k][t] * l0));
       }
     }
+    TRY(dbg_finite<R>(c, W[k].as<C>(), Bt(k) * l0, "sketch W", k));
   }
   // ---- left-to-right projection
   std::vector<DBuf> outc(d);
@@ -687,6 +741,7 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
         g.conjA = g.conjB = 0;
         TRY(gemm<R>(c, g, M.as<C>() + boff[k][t], Xk(t, k), T1.as<C>()));
       }
+      TRY(dbg_finite<R>(c, T1.as<C>(), lk * g0 * ni * a1, "left T1", k));
       // Y[l, i, off' + g1 a1 + a1] = sum_{g0, j} D[g0, i, j, g1] T1[l, g0, j, a1]  (batch l)
       {
         GemmDesc g;
@@ -711,7 +766,9 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
     // Z = Y (lk no x Bn) W_{k+1} (Bn x l1)
     DBuf Z;
     TRY(Z.alloc(c, (size_t)lk * no * l1 * sizeof(C)));
+    TRY(dbg_finite<R>(c, Y.as<C>(), lk * no * Bn, "left Y", k));
     TRY(mm<R>(c, lk * no, l1, Bn, Y.as<C>(), Bn, 1, 0, W[k + 1].as<C>(), l1, 1, 0, Z.as<C>(), l1, 1));
+    TRY(dbg_finite<R>(c, Z.as<C>(), lk * no * l1, "left Z", k));
     if (k == d - 1) {
       outc[k] = std::move(Z);
       break;
@@ -725,6 +782,7 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
     c->launches++;
     TRY(qtt_qr_r<R>(Z.as<C>(), B0(), L1(m, l1), L1(l1, 1), 0, m, l1, m, m, 1, Wq.as<C>(), nullptr, 0, 0, c->stream,
                     tau.as<C>(), outc[k].as<C>(), 0, q));
+    TRY(dbg_finite<R>(c, outc[k].as<C>(), m * q, "left Q", k));
     orank[k + 1] = (int)q;
     // M_{k+1} = Q^H Y  (q x Bn)
     DBuf Mn;

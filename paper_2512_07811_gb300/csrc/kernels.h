@@ -15,7 +15,7 @@ int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int
 
 template <class R>
 int qtt_jacobi(cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, int q, int batch,
-               int max_sweeps, int* sweeps, cudaStream_t s);
+               int max_sweeps, int* sweeps, cudaStream_t s, cplx<R>* Usorted = nullptr);
 
 template <class R>
 int qtt_trunc_rank(const R* sigma, int q, double delta, int max_rank, int* out, double* tail,

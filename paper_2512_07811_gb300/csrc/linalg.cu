@@ -37,15 +37,17 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
             int64_t m, int64_t n, int64_t rows_total, int64_t rows_per_batch,
             cplx<R>* __restrict__ Wbase, cplx<R>* __restrict__ out, int64_t out_bstride, int64_t ldr,
             cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout, int64_t q_bstride, int64_t ldq) {
-  __shared__ R red[32];
-  __shared__ cplx<R> s_v0;
+  __shared__ double red[32];
+  __shared__ cplx<R> s_inv_v0;
   __shared__ R s_tau;
+  __shared__ int s_zero;
   const int64_t b = blockIdx.x;
   cplx<R>* W = Wbase + b * m * n;
   const int64_t row0 = b * rows_per_batch;
   int64_t valid = rows_total - row0;
   if (valid > m) valid = m;
   const int64_t ib = midx_off(inB, b);
+  double part = 0.0;
   for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) {
     int64_t i = e / n, c = e - i * n;
     cplx<R> v(0, 0);
@@ -54,46 +56,63 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
       if (conj_in) v.im = -v.im;
     }
     W[e] = v;
+    part += (double)v.re * v.re + (double)v.im * v.im;
   }
-  __syncthreads();
+  // columns whose remaining norm is below eps * ||A||_F are numerically zero:
+  // they are cleared instead of reflected (a perturbation within the
+  // backward error of the factorisation), which keeps every reflector
+  // away from underflow
+  const double anorm2 = block_sum(part, red);
+  const double eps = sizeof(R) == 8 ? (double)DBL_EPSILON : (double)FLT_EPSILON;
+  const double zero_thresh2 = eps * eps * anorm2;
   const int64_t kmax = m < n ? m : n;
   for (int64_t j = 0; j < kmax; ++j) {
-    // squared norm of column j below (and at) the diagonal
-    R part = R(0);
-    for (int64_t i = j + threadIdx.x; i < m; i += blockDim.x) part += abs2(W[i * n + j]);
-    R nrm2 = block_sum(part, red);
+    double p2 = 0.0;
+    for (int64_t i = j + threadIdx.x; i < m; i += blockDim.x) {
+      cplx<R> v = W[i * n + j];
+      p2 += (double)v.re * v.re + (double)v.im * v.im;
+    }
+    const double nrm2 = block_sum(p2, red);
     if (threadIdx.x == 0) {
       cplx<R> x0 = W[j * n + j];
-      R ax0 = sqrt(abs2(x0));
-      R nrm = sqrt(nrm2);
-      if (nrm2 == R(0) || (nrm2 - ax0 * ax0) <= R(0) * nrm2) {
-        // already triangular in this column (covers nrm2 == 0)
+      double ax2 = (double)x0.re * x0.re + (double)x0.im * x0.im;
+      double below = nrm2 - ax2;
+      if (nrm2 <= zero_thresh2 || below <= zero_thresh2) {
+        // nothing to eliminate below the diagonal (or numerically zero column)
         s_tau = R(0);
-        s_v0 = cplx<R>(0, 0);
+        s_zero = 1;
+        if (nrm2 <= zero_thresh2) W[j * n + j] = cplx<R>(0, 0);
       } else {
-        cplx<R> ph = ax0 > R(0) ? cplx<R>(x0.re / ax0, x0.im / ax0) : cplx<R>(1, 0);
-        cplx<R> alpha = cplx<R>(-ph.re * nrm, -ph.im * nrm);
-        cplx<R> v0 = x0 - alpha;
-        R vn2 = nrm2 - ax0 * ax0 + abs2(v0);
-        s_tau = R(2) / vn2;
-        s_v0 = v0;
-        W[j * n + j] = alpha;
+        // H = I - tau v v^H with v = (1, x_1/v0, ...), v0 = x0 - alpha,
+        // alpha = -e^{i arg x0} ||x||, tau = 2 |v0|^2 / ||x - alpha e1||^2 in [1, 2]
+        double ax0 = sqrt(ax2), nrm = sqrt(nrm2);
+        double phr = ax0 > 0 ? x0.re / ax0 : 1.0, phi = ax0 > 0 ? x0.im / ax0 : 0.0;
+        double alr = -phr * nrm, ali = -phi * nrm;
+        double v0r = x0.re - alr, v0i = x0.im - ali;
+        double v02 = v0r * v0r + v0i * v0i;
+        double vn2 = below + v02;
+        s_tau = (R)(2.0 * v02 / vn2);
+        s_inv_v0 = cplx<R>((R)(v0r / v02), (R)(-v0i / v02));
+        s_zero = 0;
+        W[j * n + j] = cplx<R>((R)alr, (R)ali);
       }
-      if (tauws) {
-        tauws[b * 2 * n + 2 * j] = s_v0;
-        tauws[b * 2 * n + 2 * j + 1] = cplx<R>(s_tau, R(0));
-      }
+      if (tauws) tauws[b * 2 * n + 2 * j + 1] = cplx<R>(s_tau, R(0));
     }
     __syncthreads();
     const R tau = s_tau;
     if (tau != R(0)) {
-      const cplx<R> v0 = s_v0;
+      const cplx<R> iv = s_inv_v0;
+      for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) W[i * n + j] = W[i * n + j] * iv;
+    } else if (s_zero) {
+      for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) W[i * n + j] = cplx<R>(0, 0);
+    }
+    __syncthreads();
+    if (tau != R(0)) {
       for (int64_t c = j + 1 + threadIdx.x; c < n; c += blockDim.x) {
-        cplx<R> w = cplx<R>(0, 0);
-        cfma_conj(w, v0, W[j * n + c]);
+        cplx<R> w = W[j * n + c];
         for (int64_t i = j + 1; i < m; ++i) cfma_conj(w, W[i * n + j], W[i * n + c]);
         w = tau * w;
-        W[j * n + c] = W[j * n + c] - v0 * w;
+        W[j * n + c] = W[j * n + c] - w;
         for (int64_t i = j + 1; i < m; ++i) W[i * n + c] = W[i * n + c] - W[i * n + j] * w;
       }
     }
@@ -107,7 +126,7 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
     }
   }
   if (Qout) {
-    // Q = H_0 H_1 ... H_{kmax-1} [I; 0], accumulated from the last reflector.
+    // Q = H_0 H_1 ... H_{kmax-1} [I; 0], accumulated from the last reflector
     cplx<R>* Q = Qout + b * q_bstride;
     for (int64_t e = threadIdx.x; e < m * kmax; e += blockDim.x) {
       int64_t i = e / kmax, c = e - i * kmax;
@@ -115,15 +134,13 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
     }
     __syncthreads();
     for (int64_t j = kmax - 1; j >= 0; --j) {
-      const cplx<R> v0 = tauws[b * 2 * n + 2 * j];
       const R tau = tauws[b * 2 * n + 2 * j + 1].re;
       if (tau != R(0)) {
         for (int64_t c = j + threadIdx.x; c < kmax; c += blockDim.x) {
-          cplx<R> w = cplx<R>(0, 0);
-          cfma_conj(w, v0, Q[j * ldq + c]);
+          cplx<R> w = Q[j * ldq + c];
           for (int64_t i = j + 1; i < m; ++i) cfma_conj(w, W[i * n + j], Q[i * ldq + c]);
           w = tau * w;
-          Q[j * ldq + c] = Q[j * ldq + c] - v0 * w;
+          Q[j * ldq + c] = Q[j * ldq + c] - w;
           for (int64_t i = j + 1; i < m; ++i) Q[i * ldq + c] = Q[i * ldq + c] - W[i * n + j] * w;
         }
       }
@@ -141,7 +158,8 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
 template <class R>
 __global__ void __launch_bounds__(256)
 jacobi_kernel(cplx<R>* __restrict__ Gbase, cplx<R>* __restrict__ Vbase, R* __restrict__ sigma_out,
-              cplx<R>* __restrict__ Vsorted_base, int p, int q, int max_sweeps, int* __restrict__ sweeps_out) {
+              cplx<R>* __restrict__ Vsorted_base, cplx<R>* __restrict__ Usorted_base, int p, int q, int max_sweeps,
+              int* __restrict__ sweeps_out) {
   extern __shared__ unsigned char smem_raw[];
   const int64_t b = blockIdx.x;
   cplx<R>* G = Gbase + b * (int64_t)p * q;
@@ -156,6 +174,7 @@ jacobi_kernel(cplx<R>* __restrict__ Gbase, cplx<R>* __restrict__ Vbase, R* __res
   }
   for (int e = threadIdx.x; e < qe; e += blockDim.x) order[e] = e;
   __syncthreads();
+  // stop when every column pair has |cos| <= sqrt(p) eps; the sweep count is bounded by max_sweeps
   const R tol = (sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON)) * sqrt(R(p > 1 ? p : 1));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int sweep = 0;
@@ -182,7 +201,7 @@ jacobi_kernel(cplx<R>* __restrict__ Gbase, cplx<R>* __restrict__ Vbase, R* __res
           ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
         }
         R ag = sqrt(abs2(ga));
-        if (!(ag > tol * sqrt(al * be)) || ag == R(0)) continue;
+        if (!(al > R(0) && be > R(0)) || !(ag > tol * sqrt(al) * sqrt(be))) continue;
         // rotation making columns a, c orthogonal (complex Hestenes step)
         cplx<R> ph(ga.re / ag, ga.im / ag);       // e^{i phi}
         R zeta = (be - al) / (R(2) * ag);
@@ -237,6 +256,16 @@ jacobi_kernel(cplx<R>* __restrict__ Gbase, cplx<R>* __restrict__ Vbase, R* __res
     }
     sigma_out[b * (int64_t)q + rk] = v;
     for (int i = 0; i < q; ++i) Vs[(int64_t)i * q + rk] = V[(int64_t)i * q + c];
+    if (Usorted_base) {
+      // normalised rotated column: G_in V = U S, so U[:, rk] = G_out[:, c] / sigma
+      cplx<R>* Us = Usorted_base + b * (int64_t)p * q;
+      // columns with a subnormal norm carry no usable direction
+      R f = v > (sizeof(R) == 8 ? R(DBL_MIN) : R(FLT_MIN)) * R(4) ? R(1) / v : R(0);
+      for (int i = 0; i < p; ++i) {
+        cplx<R> g = G[(int64_t)i * q + c];
+        Us[(int64_t)i * q + rk] = cplx<R>(g.re * f, g.im * f);
+      }
+    }
   }
 }
 
@@ -290,7 +319,7 @@ int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int
 
 template <class R>
 int qtt_jacobi(cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, int q, int batch,
-               int max_sweeps, int* sweeps, cudaStream_t s) {
+               int max_sweeps, int* sweeps, cudaStream_t s, cplx<R>* Usorted) {
   if (batch <= 0 || q <= 0) return QTT_OK;
   int qe = q + (q & 1);
   size_t sm = (size_t)(qe + (qe & 1)) * sizeof(int) + (size_t)q * sizeof(R) + 16;
@@ -298,7 +327,7 @@ int qtt_jacobi(cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, in
     if (cudaFuncSetAttribute(jacobi_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
       return QTT_ERR_CUDA;
   }
-  jacobi_kernel<R><<<(unsigned)batch, 256, sm, s>>>(G, Vwork, sigma, Vsorted, p, q, max_sweeps, sweeps);
+  jacobi_kernel<R><<<(unsigned)batch, 256, sm, s>>>(G, Vwork, sigma, Vsorted, Usorted, p, q, max_sweeps, sweeps);
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
 
@@ -312,7 +341,7 @@ template int qtt_qr_r<double>(const zc*, MIdx, MIdx, MIdx, int, int64_t, int64_t
                               zc*, zc*, int64_t, int64_t, cudaStream_t, zc*, zc*, int64_t, int64_t);
 template int qtt_qr_r<float>(const cc*, MIdx, MIdx, MIdx, int, int64_t, int64_t, int64_t, int64_t, int64_t,
                              cc*, cc*, int64_t, int64_t, cudaStream_t, cc*, cc*, int64_t, int64_t);
-template int qtt_jacobi<double>(zc*, zc*, double*, zc*, int, int, int, int, int*, cudaStream_t);
-template int qtt_jacobi<float>(cc*, cc*, float*, cc*, int, int, int, int, int*, cudaStream_t);
+template int qtt_jacobi<double>(zc*, zc*, double*, zc*, int, int, int, int, int*, cudaStream_t, zc*);
+template int qtt_jacobi<float>(cc*, cc*, float*, cc*, int, int, int, int, int*, cudaStream_t, cc*);
 template int qtt_trunc_rank<double>(const double*, int, double, int, int*, double*, cudaStream_t);
 template int qtt_trunc_rank<float>(const float*, int, double, int, int*, double*, cudaStream_t);

@@ -8,6 +8,7 @@ context fails without an sm_103 device.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 
@@ -20,6 +21,12 @@ if not os.path.exists(LIB_PATH):
     raise ImportError("libqtt.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
 
 _lib = C.CDLL(LIB_PATH)
+
+# Handles still alive when the interpreter shuts down are left to the
+# process exit: destroying them after the CUDA runtime has torn down its
+# contexts would touch freed driver state.
+_ALIVE = [True]
+atexit.register(lambda: _ALIVE.__setitem__(0, False))
 
 C128, C64 = 0, 1
 PREC_F64, PREC_F32 = 0, 1
@@ -139,9 +146,9 @@ class Context:
         self.h = h
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and _ALIVE[0]:
             _lib.qtt_ctx_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         self.close()
@@ -175,9 +182,9 @@ class TT:
         return t
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and _ALIVE[0]:
             _lib.qtt_tt_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         self.close()
@@ -243,9 +250,9 @@ class MPO:
         return A
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and _ALIVE[0]:
             _lib.qtt_mpo_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         self.close()
