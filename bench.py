@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark of the QTT hot path on GB300.
+
+One step = one pass over the TT-op workload of random quantized trains
+(d = 30 mode-2 cores, uniform bond rank r, Gaussian cores N(0,1)/sqrt(r)):
+  1. z = x + y, then SVD rounding of z at eps = 1e-6 (rank 2r in and out:
+     random trains have flat spectra, so nothing is truncated);
+  2. the Hadamard product x * y rounded by the sketched rounding (width
+     r + 8, capped at rank r) without forming the rank-r^2 product;
+  3. the 30-bit superfast Fourier transform applied to x, rounded the same
+     way (bond <= 16 operator);
+  4. <x, y>.
+The metric is the flop model of every SVD rounding in the step (shared with
+the CPU oracle, paper_2512_07811_gb300/flops.py) divided by the step time:
+"tt_round TFLOP/s".  The fast path stores complex64 and runs float kernels;
+the FP64 path runs the same step in complex128 and is reported beside it.
+A secondary object times the Moulinec-Suquet iteration on the 32^3 scalar
+laminate (15 interleaved bit sites + one control site).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2512_07811_gb300 import inputs as I  # noqa: E402
+from paper_2512_07811_gb300.flops import round_flops  # noqa: E402
+
+D = 30
+EPS = 1e-6
+OVERSAMPLE = 8
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--rank", type=int, default=64)
+    p.add_argument("--no-ms", action="store_true")
+    p.add_argument("--fp64-steps", type=int, default=3)
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def sketch_cores(rng, d, modes, ell):
+    ranks = [1]
+    left = 1
+    for k in range(1, d):
+        left *= modes[k - 1]
+        right = int(np.prod(modes[k:], dtype=np.float64)) if d - k < 60 else 1 << 60
+        ranks.append(int(min(ell, left, right)))
+    ranks.append(1)
+    return [rng.standard_normal((ranks[k], modes[k], ranks[k + 1])) / math.sqrt(modes[k] * ranks[k + 1])
+            for k in range(d)], ranks
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.splitlines():
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ our path
+class Step:
+    """Device-resident inputs and one pass of the workload on one context."""
+
+    def __init__(self, Q, ctx, r, dtype, qft_c128):
+        self.Q, self.ctx, self.r, self.dtype = Q, ctx, r, dtype
+        self.xc = I.random_tt_cores(D, 2, r, seed=1000 + r, dtype=np.complex128)
+        self.yc = I.random_tt_cores(D, 2, r, seed=1001 + r, dtype=np.complex128)
+        rng = np.random.default_rng(2000 + r)
+        sk, self.sk_ranks = sketch_cores(rng, D, [2] * D, r + OVERSAMPLE)
+        self.X = Q.TT.from_cores(ctx, self.xc, dtype)
+        self.Y = Q.TT.from_cores(ctx, self.yc, dtype)
+        self.S = Q.TT.from_cores(ctx, sk, dtype)
+        self.DX = Q.qtt_mpo_diag(ctx, self.X)
+        self.F = qft_c128 if dtype == Q.C128 else Q.qtt_mpo_convert(ctx, qft_c128, dtype)
+        self.modes = [2] * D
+
+    def run(self, X=None, Y=None):
+        Q, ctx, r = self.Q, self.ctx, self.r
+        X = X or self.X
+        Y = Y or self.Y
+        DX = self.DX if X is self.X else Q.qtt_mpo_diag(ctx, X)
+        z = Q.tt_add(ctx, 1.0, X, 1.0, Y)
+        zr, _ = Q.tt_round(ctx, z, EPS)
+        h, _ = Q.tt_round_sketched(ctx, [(1.0, DX, Y)], self.S, EPS, r)
+        q, _ = Q.tt_round_sketched(ctx, [(1.0, self.F, X)], self.S, EPS, r)
+        v = Q.tt_dot(ctx, X, Y)
+        flops = (round_flops(self.modes, z.ranks, zr.ranks)
+                 + round_flops(self.modes, self.sk_ranks, h.ranks)
+                 + round_flops(self.modes, self.sk_ranks, q.ranks))
+        return flops, (zr, h, q, v)
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)
+
+
+def time_steps(torch, stream, step, steps, flush):
+    """Per-step device time with CUDA events on the library's stream; the L2
+    flush between steps sits outside the timed intervals."""
+    total_ms, flops = 0.0, 0.0
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush_l2(torch, flush)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f, _ = step.run()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        flops += f
+    return total_ms, flops
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2512_07811_gb300 import qtt as Q
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream(device=local_rank)
+    ctx = Q.Context(local_rank, stream.cuda_stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    r = args.rank
+    qft = Q.qtt_qft_mpo(ctx, D, -1, 1e-12)
+    fast = Step(Q, ctx, r, Q.C64, qft)
+    for _ in range(args.warmup):
+        fast.run()
+    ctx.sync()
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    l0 = ctx.launches
+    ctx.profile(True)
+    ms, flops = time_steps(torch, stream, fast, args.steps, flush)
+    prof = {k: ctx.profile_read(k) for k in ["gemm", "qr", "jacobi", "elem"]}
+    ctx.profile(False)
+    launches = ctx.launches - l0
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    # e2e: the same step with the inputs uploaded from pinned host memory and
+    # every result read back, host<->device copies inside the timed region
+    pin_x = [torch.from_numpy(c.astype(np.complex64)).pin_memory() for c in fast.xc]
+    pin_y = [torch.from_numpy(c.astype(np.complex64)).pin_memory() for c in fast.yc]
+    h2d = sum(t.numel() * 8 for t in pin_x + pin_y)
+    e2e_ms, e2e_flops, d2h = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush_l2(torch, flush)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        X = Q.TT.from_cores(ctx, [t.numpy() for t in pin_x], Q.C64)
+        Y = Q.TT.from_cores(ctx, [t.numpy() for t in pin_y], Q.C64)
+        f, outs = fast.run(X, Y)
+        d2h = 0
+        for tt in outs[:3]:
+            for c in tt.cores():
+                d2h += c.nbytes
+        d2h += 16
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_flops += f
+
+    # FP64 path, same step in complex128
+    slow = Step(Q, ctx, r, Q.C128, qft)
+    slow.run()
+    ctx.sync()
+    ms64, flops64 = time_steps(torch, stream, slow, args.fp64_steps, flush)
+
+    ms_part = None
+    if not args.no_ms:
+        ms_part = ms_laminate(Q, ctx)
+    return dict(ms=ms, flops=flops, prof=prof, launches=launches, clocks=clk, e2e_ms=e2e_ms,
+                e2e_flops=e2e_flops, h2d=h2d, d2h=d2h, ms64=ms64, flops64=flops64, ms_part=ms_part)
+
+
+def ms_laminate(Q, ctx):
+    """Moulinec-Suquet iterations on the 32^3 scalar laminate, load case E = e_x,
+    three iterations each for the fast and the FP64 path."""
+    ind = I.laminate_indicator(32)
+    out = {"workload": "32^3 scalar laminate, 15 interleaved bit sites + control, contrast 10, "
+                       "eps 1e-8, max rank 64, E = e_x, 3 iterations"}
+    for name, prec in [("fast", Q.PREC_F32), ("fp64", Q.PREC_F64)]:
+        C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), tol=0.0, max_rank=64, eps=1e-8,
+                                 max_iter=3, min_iter=3, prec=prec, load_mask=1)
+        it = rep.iterations[0]
+        out[name] = {"iters_per_s": it / (rep.iterate_ms * 1e-3) if rep.iterate_ms > 0 else None,
+                     "setup_ms": rep.setup_ms, "k_eff_xx": C[0, 0], "iterations": it}
+    out["k_eff_xx_exact"] = 20.0 / 11.0
+    if out["fast"]["iters_per_s"] and out["fp64"]["iters_per_s"]:
+        out["speedup_fast_vs_fp64"] = out["fast"]["iters_per_s"] / out["fp64"]["iters_per_s"]
+    return out
+
+
+# ------------------------------------------------------- CPU oracle arm
+def oracle_sample(r, repeats=1):
+    """The oracle's tt_add + SVD rounding of the step's first rounding, on the
+    host cores: returns (seconds, model flops)."""
+    from oracle import tt as T
+    x = I.random_tt_cores(D, 2, r, seed=1000 + r, dtype=np.complex128)
+    y = I.random_tt_cores(D, 2, r, seed=1001 + r, dtype=np.complex128)
+    t0 = time.perf_counter()
+    fl = 0.0
+    for _ in range(repeats):
+        z = T.tt_add(x, y)
+        zr, _ = T.tt_round(z, EPS)
+        fl += round_flops([2] * D, T.tt_ranks(z), T.tt_ranks(zr))
+    return time.perf_counter() - t0, fl
+
+
+def cpu_baseline(r):
+    sec, fl = oracle_sample(r)
+    return {"value": fl / sec / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one tt_add + SVD rounding of the d=30, r=%d pair (the first of the step's three roundings), "
+                      "NumPy FP64 with its threaded BLAS" % r, "seconds": sec}
+
+
+def config_dict(args, world):
+    return {"workload": "tt_ops_d30_r%d: random QTT d=30, mode 2, rank %d, complex; add+round, "
+                        "hadamard+sketched round, 30-bit SFFT apply+sketched round, dot" % (args.rank, args.rank),
+            "d": D, "rank": args.rank, "eps": EPS, "sketch_oversample": OVERSAMPLE,
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas x%d" % world}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    metric = "tt_round TFLOP/s (flop model), fast path"
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        t_total, f_total = 0.0, 0.0
+        for _ in range(args.warmup if args.warmup < 1 else 1):
+            oracle_sample(args.rank)
+        for _ in range(args.steps):
+            sec, fl = oracle_sample(args.rank)
+            t_total += sec
+            f_total += fl
+        val = f_total / t_total / 1e12
+        line = {"impl": "reference", "metric": metric, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic", "config": config_dict(args, 1),
+                "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": "per step: one tt_add + SVD rounding of the d=30 pair (NumPy FP64)"},
+                "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank != 0:
+        return 0
+    peaks, peak_src = load_peaks()
+    value = world * res["flops"] / (res["ms"] * 1e-3) / 1e12
+    # dominant kernel class and its roofline (ALU-bound: float CUDA cores)
+    prof = res["prof"]
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[dom]
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    if dom == "elem":
+        roof = {"bound": "hbm", "achieved": p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] else 0.0,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        roof = {"bound": "alu", "achieved": p["flops"] / (p["ms"] * 1e-3) / 1e12 if p["ms"] else 0.0,
+                "peak": fp32_peak, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+    roof["traffic"] = None
+    roof["kernel"] = {"gemm": "gemm_midx_kernel", "qr": "qr_r_kernel", "jacobi": "jacobi_kernel",
+                      "elem": "elementwise kernels"}[dom]
+    roof["peak_source"] = ("FP32 CUDA-core peak 152 SMs x 128 FMA/clk x %.0f MHz (%s clock)" %
+                           (sm_mhz, peak_src)) if roof["bound"] == "alu" else "MEASURED_PEAKS hbm_gbs"
+    roof["launches"] = p["launches"]
+    roof["kernel_ms_total"] = p["ms"]
+    line = {
+        "metric": metric, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": config_dict(args, world),
+        "roofline": roof,
+        "kernel_classes": {k: {"ms": v["ms"], "launches": v["launches"], "model_flops": v["flops"]}
+                           for k, v in prof.items()},
+        "cpu_baseline": cpu_baseline(args.rank),
+        "e2e": {"value": world * res["e2e_flops"] / (res["e2e_ms"] * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+        "fp64_path": {"value": world * res["flops64"] / (res["ms64"] * 1e-3) / 1e12, "unit": "TFLOP/s",
+                      "ms_per_step": res["ms64"] / args.fp64_steps, "steps": args.fp64_steps, "dtype": "c128"},
+    }
+    line["fast_vs_fp64"] = line["value"] / line["fp64_path"]["value"] if line["fp64_path"]["value"] else None
+    if res["ms_part"] is not None:
+        line["ms_iteration"] = res["ms_part"]
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

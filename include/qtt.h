@@ -89,6 +89,16 @@ QTT_API void qtt_ctx_destroy(qtt_ctx* ctx);
 QTT_API int qtt_ctx_sync(qtt_ctx* ctx);
 /* Number of kernels this library has launched on the context so far. */
 QTT_API int64_t qtt_ctx_launch_count(const qtt_ctx* ctx);
+/* Built-in profiler: with `enable` != 0 every launch of the GEMM (class 0),
+ * Householder QR (1), one-sided Jacobi (2) and elementwise (3) kernels is
+ * bracketed by CUDA events on the context stream and its model flops and
+ * bytes are recorded; enabling or disabling clears the records. */
+QTT_API int qtt_ctx_profile(qtt_ctx* ctx, int enable);
+/* Totals of one kernel class since profiling was enabled: summed event time
+ * (ms), launches, model flops (Jacobi: per-sweep model times the sweeps the
+ * kernel ran) and model bytes.  Synchronises the stream. */
+QTT_API int qtt_ctx_profile_read(qtt_ctx* ctx, int kclass, double* total_ms, int64_t* launches, double* flops,
+                                 double* bytes);
 
 /* --------------------------------------------------------------- trains */
 /* New train with the given modes (d entries) and ranks (d + 1 entries,
@@ -173,8 +183,18 @@ QTT_API int tt_from_dense(qtt_ctx* ctx, int ncores, const int32_t* modes, const 
 /* Q_n of QFT_n = R_n Q_n (Sec. 3.2, Fig. 1): the unitary DFT with sign
  * `sign` (-1: exp(-2 pi i jk/N)) whose output bits are left in reversed
  * order, as an operator train of `nbits` sites (site a: output bit of weight
- * 2^(a-1), input bit of weight 2^(nbits-a)), rounded at `tol`. */
+ * 2^(a-1), input bit of weight 2^(nbits-a)), rounded at `tol`, QTT_C128.
+ * Up to 12 bits: TT-SVD of the closed-form matrix; beyond: product of the
+ * circuit's layers (Hadamard, then the controlled phases of one qubit),
+ * rounded after every layer. */
 QTT_API int qtt_qft_mpo(qtt_ctx* ctx, int nbits, int sign, double tol, qtt_mpo** out);
+
+/* The train x lifted to the operator D(i, j) = x(i) delta(i, j) (Sec. 2.1,
+ * Eq. tt_to_tto): applying it is the Hadamard product with x, which lets
+ * tt_round_sketched round x (elementwise) y without forming it. */
+QTT_API int qtt_mpo_diag(qtt_ctx* ctx, const qtt_tt* x, qtt_mpo** out);
+/* B = A stored in another dtype. */
+QTT_API int qtt_mpo_convert(qtt_ctx* ctx, const qtt_mpo* A, qtt_dtype dtype, qtt_mpo** out);
 
 /* ---------------------------------------------------- homogenisation */
 typedef struct {

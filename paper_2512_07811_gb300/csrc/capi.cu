@@ -253,6 +253,16 @@ int convert_mpo(qtt_ctx* c, const qtt_mpo* A, qtt_dtype dt, qtt_mpo** out) {
 
 // ===================================================================== ABI
 
+static void prof_clear(qtt_ctx* c) {
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  c->recs.clear();
+  c->sweeps_used = 0;
+}
+
+
 extern "C" {
 
 const char* qtt_status_string(int s) {
@@ -301,6 +311,8 @@ int qtt_ctx_create(int device, void* stream, qtt_ctx** out) {
 void qtt_ctx_destroy(qtt_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  prof_clear(c);
+  if (c->d_sweeps) cudaFree(c->d_sweeps);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -311,6 +323,47 @@ int qtt_ctx_sync(qtt_ctx* c) {
 }
 
 int64_t qtt_ctx_launch_count(const qtt_ctx* c) { return c ? c->launches : -1; }
+
+int qtt_ctx_profile(qtt_ctx* c, int enable) {
+  if (!c) return QTT_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  prof_clear(c);
+  if (enable && !c->d_sweeps) {
+    c->sweeps_cap = 1 << 20;
+    if (cudaMalloc(&c->d_sweeps, c->sweeps_cap * sizeof(int)) != cudaSuccess) {
+      c->d_sweeps = nullptr;
+      c->sweeps_cap = 0;
+      return QTT_ERR_OOM;
+    }
+  }
+  c->prof = enable != 0;
+  return QTT_OK;
+}
+
+int qtt_ctx_profile_read(qtt_ctx* c, int kclass, double* total_ms, int64_t* launches, double* flops, double* bytes) {
+  if (!c || kclass < 0 || kclass >= PK_N) return QTT_ERR_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return QTT_ERR_CUDA;
+  std::vector<int> sw(c->sweeps_used, 0);
+  if (c->sweeps_used)
+    cudaMemcpy(sw.data(), c->d_sweeps, c->sweeps_used * sizeof(int), cudaMemcpyDeviceToHost);
+  double ms = 0, fl = 0, by = 0;
+  int64_t n = 0;
+  for (auto& r : c->recs) {
+    if (r.cls != kclass) continue;
+    float e = 0;
+    cudaEventElapsedTime(&e, r.a, r.b);
+    ms += e;
+    ++n;
+    by += r.bytes;
+    fl += r.flops;
+    if (r.sweep_idx >= 0) fl += r.per_sweep * std::max(1, sw[r.sweep_idx]);
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = n;
+  if (flops) *flops = fl;
+  if (bytes) *bytes = by;
+  return QTT_OK;
+}
 
 int qtt_tt_create(qtt_ctx* c, int d, const int32_t* modes, const int32_t* ranks, qtt_dtype dt, qtt_tt** out) {
   if (!c || !out || d < 1 || !modes || !ranks || (dt != QTT_C128 && dt != QTT_C64)) return QTT_ERR_ARG;
@@ -464,8 +517,8 @@ int tt_from_dense(qtt_ctx* c, int d, const int32_t* modes, const void* dense, do
   return tt_svd_dev<double>(c, d, m, reinterpret_cast<const zc*>(dense), eps, max_rank, QTT_C128, out);
 }
 
-int qtt_qft_mpo(qtt_ctx* c, int nbits, int sign, double tol, qtt_mpo** out) {
-  if (!c || nbits < 1 || nbits > 13 || (sign != 1 && sign != -1) || !out || !(tol >= 0)) return QTT_ERR_ARG;
+// Dense route for nbits <= 13: TT-SVD of the closed-form matrix in site order.
+static int qft_dense_route(qtt_ctx* c, int nbits, int sign, double tol, qtt_mpo** out) {
   const int64_t total = (int64_t)1 << (2 * nbits);
   void* dense;
   TRY(dalloc(c, &dense, total * sizeof(zc)));
@@ -488,6 +541,130 @@ int qtt_qft_mpo(qtt_ctx* c, int nbits, int sign, double tol, qtt_mpo** out) {
   tt_free(t);
   *out = A;
   return QTT_OK;
+}
+
+// Circuit route (any nbits): the QFT circuit without its final swaps, one
+// layer per qubit b (a Hadamard on b, then the phase gates controlled by b on
+// every later qubit a with angle sign*2*pi*2^(b-a-1)), multiplied into the
+// running operator layer by layer and rounded at `tol` after each layer.
+// The running operator is stored as a train with mode 4 = (out, in); a layer
+// acts on it as the operator L (x) I_in, built on the host (bond 2).
+static int qft_layer_route(qtt_ctx* c, int nbits, int sign, double tol, qtt_mpo** out) {
+  const int n = nbits;
+  int st;
+  std::vector<int> m4(n, 4), r1(n + 1, 1);
+  qtt_tt* Q = tt_alloc(c, n, m4, r1, QTT_C128, &st);
+  if (!Q) return st;
+  {
+    zc id[4] = {zc(1, 0), zc(0, 0), zc(0, 0), zc(1, 0)};  // (out, in) = identity
+    for (int k = 0; k < n; ++k) {
+      if (cudaMemcpyAsync(core_ptr<char>(Q, k), id, sizeof(id), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+        tt_free(Q);
+        return QTT_ERR_CUDA;
+      }
+    }
+    cudaStreamSynchronize(c->stream);
+  }
+  const double PI = 3.14159265358979323846;
+  for (int b = 0; b < n; ++b) {
+    // layer cores L_a(i, k) with bonds; lifted to (i j', k j) with j' = j
+    std::vector<int> g(n + 1, 1);
+    for (int a = b; a < n - 1; ++a) g[a + 1] = 2;
+    std::vector<int> m4o(n, 4), m4i(n, 4);
+    qtt_mpo* L = mpo_alloc(c, n, m4o, m4i, g, QTT_C128, &st);
+    if (!L) {
+      tt_free(Q);
+      return st;
+    }
+    for (int a = 0; a < n; ++a) {
+      const int g0 = g[a], g1 = g[a + 1];
+      std::vector<zc> core((size_t)g0 * 4 * 4 * g1, zc(0, 0));
+      auto at = [&](int c0, int i, int k, int c1) -> zc& {
+        return core[(((size_t)c0 * 4 + i) * 4 + k) * g1 + c1];
+      };
+      for (int j = 0; j < 2; ++j) {          // the untouched input index of the operator being built
+        for (int i = 0; i < 2; ++i)
+          for (int k = 0; k < 2; ++k) {
+            const int I = i * 2 + j, K = k * 2 + j;
+            if (a < b) {
+              if (i == k) at(0, I, K, 0) = zc(1, 0);
+            } else if (a == b) {
+              // Hadamard, output bit i becomes the control carried on the bond
+              double h = ((i * k) & 1 ? -1.0 : 1.0) / sqrt(2.0);
+              at(0, I, K, g1 == 1 ? 0 : i) = zc(h, 0);
+            } else {
+              // phase on qubit a controlled by the bond value (the output bit of b)
+              if (i != k) continue;
+              for (int cb = 0; cb < 2; ++cb) {
+                double th = sign * 2.0 * PI * ldexp(1.0, b - a - 1) * cb * k;
+                at(cb, I, K, g1 == 1 ? 0 : cb) = zc(cos(th), sin(th));
+              }
+            }
+          }
+      }
+      if (cudaMemcpyAsync(core_ptr<char>(L, a), core.data(), core.size() * sizeof(zc), cudaMemcpyHostToDevice,
+                          c->stream) != cudaSuccess) {
+        mpo_free(L);
+        tt_free(Q);
+        return QTT_ERR_CUDA;
+      }
+    }
+    cudaStreamSynchronize(c->stream);
+    qtt_tt* LQ = nullptr;
+    st = tt_mpo_apply(c, L, Q, &LQ);
+    mpo_free(L);
+    tt_free(Q);
+    if (st) return st;
+    qtt_tt* Qr = nullptr;
+    st = round_det<double>(c, LQ, tol, 0, nullptr, nullptr, &Qr);
+    tt_free(LQ);
+    if (st) return st;
+    Q = Qr;
+  }
+  std::vector<int> two(n, 2);
+  qtt_mpo* A = mpo_alloc(c, n, two, two, Q->r, QTT_C128, &st);
+  if (!A) {
+    tt_free(Q);
+    return st;
+  }
+  for (int k = 0; k < n; ++k)
+    cudaMemcpyAsync(core_ptr<char>(A, k), core_ptr<char>(Q, k), (size_t)Q->r[k] * 4 * Q->r[k + 1] * sizeof(zc),
+                    cudaMemcpyDeviceToDevice, c->stream);
+  tt_free(Q);
+  *out = A;
+  return QTT_OK;
+}
+
+int qtt_qft_mpo(qtt_ctx* c, int nbits, int sign, double tol, qtt_mpo** out) {
+  if (!c || nbits < 1 || nbits > 62 || (sign != 1 && sign != -1) || !out || !(tol >= 0)) return QTT_ERR_ARG;
+  if (nbits <= 12) return qft_dense_route(c, nbits, sign, tol, out);
+  return qft_layer_route(c, nbits, sign, tol, out);
+}
+
+int qtt_mpo_diag(qtt_ctx* c, const qtt_tt* x, qtt_mpo** out) {
+  if (!c || !valid_tt(x) || !out) return QTT_ERR_ARG;
+  int st;
+  qtt_mpo* A = mpo_alloc(c, x->d, x->n, x->n, x->r, x->dtype, &st);
+  if (!A) return st;
+  for (int k = 0; k < x->d; ++k) {
+    c->launches++;
+    int s = x->dtype == QTT_C128
+                ? qtt_diag_mpo_core<double>(core_ptr<zc>(x, k), x->r[k], x->n[k], x->r[k + 1], core_ptr<zc>(A, k),
+                                            c->stream)
+                : qtt_diag_mpo_core<float>(core_ptr<cc>(x, k), x->r[k], x->n[k], x->r[k + 1], core_ptr<cc>(A, k),
+                                           c->stream);
+    if (s) {
+      mpo_free(A);
+      return s;
+    }
+  }
+  *out = A;
+  return QTT_OK;
+}
+
+int qtt_mpo_convert(qtt_ctx* c, const qtt_mpo* A, qtt_dtype dt, qtt_mpo** out) {
+  if (!c || !A || !out || (dt != QTT_C128 && dt != QTT_C64)) return QTT_ERR_ARG;
+  return convert_mpo(c, A, dt, out);
 }
 
 }  // extern "C"

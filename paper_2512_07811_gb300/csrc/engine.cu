@@ -140,13 +140,20 @@ int mm(qtt_ctx* c, int64_t M, int64_t N, int64_t K, const cplx<R>* A, int64_t sA
     if (sCn == 1 && sCm == N) return cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(cplx<R>), c->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
   }
   c->launches++;
-  return qtt_gemm<R>(g, alpha, beta, A, B, C, c->stream);
+  cudaEvent_t ev = prof_begin(c);
+  int st = qtt_gemm<R>(g, alpha, beta, A, B, C, c->stream);
+  prof_end(c, ev, PK_GEMM, 8.0 * M * N * K, (double)(M * K + K * N + M * N) * sizeof(cplx<R>));
+  return st;
 }
 
 template <class R>
 int gemm(qtt_ctx* c, const GemmDesc& g, const cplx<R>* A, const cplx<R>* B, cplx<R>* C) {
   c->launches++;
-  return qtt_gemm<R>(g, cplx<R>(1, 0), cplx<R>(0, 0), A, B, C, c->stream);
+  cudaEvent_t ev = prof_begin(c);
+  int st = qtt_gemm<R>(g, cplx<R>(1, 0), cplx<R>(0, 0), A, B, C, c->stream);
+  prof_end(c, ev, PK_GEMM, 8.0 * g.M * g.N * g.K * g.batch,
+           (double)(g.M * g.K + g.K * g.N + g.M * g.N) * g.batch * sizeof(cplx<R>));
+  return st;
 }
 
 #define TRY(expr)                 \
@@ -210,6 +217,62 @@ struct DBuf {
   T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// model flops of a complex Householder QR of an m x n panel (R only, or R and Q)
+static double qr_flops(double m, double n, bool with_q) {
+  double k = m < n ? m : n;
+  double f = 8.0 * (2.0 * m * n * k - (m + n) * k * k + 2.0 * k * k * k / 3.0);
+  return with_q ? 2.0 * f : f;
+}
+// one sweep of one-sided Jacobi on p x q: q(q-1)/2 pairs, each three complex
+// dot products of length p and two rotations of p- and q-long column pairs
+static double jacobi_sweep_flops(double p, double q) { return 0.5 * q * (q - 1) * (40.0 * p + 24.0 * q); }
+
+template <class R>
+static int qr_launch(qtt_ctx* c, const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m,
+                     int64_t n, int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
+                     int64_t out_bstride, int64_t ldr, cplx<R>* tauws = nullptr, cplx<R>* Qout = nullptr,
+                     int64_t q_bstride = 0, int64_t ldq = 0) {
+  c->launches++;
+  cudaEvent_t ev = prof_begin(c);
+  int st = qtt_qr_r<R>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out, out_bstride,
+                       ldr, c->stream, tauws, Qout, q_bstride, ldq);
+  prof_end(c, ev, PK_QR, batch * qr_flops((double)m, (double)n, Qout != nullptr),
+           (double)batch * m * n * sizeof(cplx<R>) * 2.0);
+  return st;
+}
+
+template <class R>
+static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, int q,
+                         int max_sweeps, cplx<R>* Usorted = nullptr) {
+  // FP64 runs at a few flops per clock per SM on this part: spread every
+  // sizeable FP64 factorisation over all SMs; FP32 stays in one CTA up to
+  // q = 256, where one SM's FP32 rate beats a launch per round.
+  const bool wide = (sizeof(R) == 8 && q >= 32) || q > 256;
+  if (wide) {
+    void* buf = nullptr;
+    size_t gb = (size_t)p * q * sizeof(cplx<R>), vb = (size_t)q * q * sizeof(cplx<R>);
+    TRY(dalloc(c, &buf, gb + vb + 256));
+    cplx<R>* Gw = reinterpret_cast<cplx<R>*>(buf);
+    cplx<R>* Vw = reinterpret_cast<cplx<R>*>(static_cast<char*>(buf) + gb);
+    int* flag = reinterpret_cast<int*>(static_cast<char*>(buf) + gb + vb);
+    int sweeps = 0;
+    cudaEvent_t ev = prof_begin(c);
+    int st = qtt_jacobi_wide<R>(G, Gw, Vw, sigma, Vsorted, Usorted, p, q, max_sweeps, flag, &sweeps, &c->launches,
+                                c->stream);
+    prof_end(c, ev, PK_JACOBI, jacobi_sweep_flops(p, q) * std::max(1, sweeps), (double)(p + 2.0 * q) * q * sizeof(cplx<R>));
+    dfree(c, buf);
+    (void)Vwork;
+    return st;
+  }
+  c->launches++;
+  int idx;
+  int* slot = prof_sweep_slot(c, &idx);
+  cudaEvent_t ev = prof_begin(c);
+  int st = qtt_jacobi<R>(G, Vwork, sigma, Vsorted, p, q, 1, max_sweeps, slot, c->stream, Usorted);
+  prof_end(c, ev, PK_JACOBI, 0.0, (double)(p + 2.0 * q) * q * sizeof(cplx<R>), idx, jacobi_sweep_flops(p, q));
+  return st;
+}
+
 // ------------------------------------------------------------ TSQR (R only)
 // R factor of an m x n matrix whose element (i, c) is in[rowI(i) + colI(c)]
 // (conjugated if conj_in): row blocks of max(2n, 256) rows are factored in
@@ -222,8 +285,7 @@ int tsqr_r(qtt_ctx* c, const cplx<R>* in, MIdx rowI, MIdx colI, int conj_in, int
   if (m <= chunk) {
     DBuf W;
     TRY(W.alloc(c, (size_t)m * n * sizeof(cplx<R>)));
-    c->launches++;
-    TRY(qtt_qr_r<R>(in, B0(), rowI, colI, conj_in, m, n, m, m, 1, W.as<cplx<R>>(), Rout, 0, n, c->stream));
+    TRY(qr_launch<R>(c, in, B0(), rowI, colI, conj_in, m, n, m, m, 1, W.as<cplx<R>>(), Rout, 0, n));
     *rows_out = std::min(m, n);
     return QTT_OK;
   }
@@ -235,9 +297,8 @@ int tsqr_r(qtt_ctx* c, const cplx<R>* in, MIdx rowI, MIdx colI, int conj_in, int
   MIdx inB = L1(nch, rowI.n2 == 1 ? chunk * rowI.s1 : 0);
   if (rowI.n2 != 1) return QTT_ERR_UNSUPPORTED;
   MIdx rows = L1(chunk, rowI.s1);
-  c->launches++;
-  TRY(qtt_qr_r<R>(in, inB, rows, colI, conj_in, chunk, n, m, chunk, nch, W.as<cplx<R>>(), Rs.as<cplx<R>>(),
-                  n * n, n, c->stream));
+  TRY(qr_launch<R>(c, in, inB, rows, colI, conj_in, chunk, n, m, chunk, nch, W.as<cplx<R>>(), Rs.as<cplx<R>>(),
+                   n * n, n));
   return tsqr_r<R>(c, Rs.as<cplx<R>>(), L1(nch * n, n), L1(n, 1), 0, nch * n, n, Rout, rows_out);
 }
 
@@ -255,8 +316,7 @@ int left_svd(qtt_ctx* c, const cplx<R>* Cm, int64_t rows, int64_t cols, int64_t 
   int64_t got = 0;
   TRY(tsqr_r<R>(c, Cm, L1(cols, 1), L1(rows, ld), 1, cols, rows, Rc.as<cplx<R>>(), &got));
   // Jacobi on Rc (got x rows): Rc V = U_R S  =>  C = V S U_R^H Q^H, left vectors of C = V
-  c->launches++;
-  TRY(qtt_jacobi<R>(Rc.as<cplx<R>>(), V.as<cplx<R>>(), sigma, U, (int)got, (int)rows, 1, 60, nullptr, c->stream));
+  TRY(jacobi_launch<R>(c, Rc.as<cplx<R>>(), V.as<cplx<R>>(), sigma, U, (int)got, (int)rows, 60));
   if (got < rows) {
     // trailing singular values are exactly zero (rank <= got): sigma entries
     // beyond `got` come out as zero column norms already.
@@ -358,10 +418,8 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     TRY(Qc.alloc(c, (size_t)Tcols * pq * sizeof(cplx<R>)));
     TRY(Wq.alloc(c, (size_t)Tcols * rk * sizeof(cplx<R>)));
     TRY(tau.alloc(c, (size_t)2 * rk * sizeof(cplx<R>)));
-    c->launches++;
-    TRY(qtt_qr_r<R>(Cb.as<cplx<R>>(), B0(), L1(Tcols, 1), L1(rk, Tcols), 1, Tcols, rk, Tcols, Tcols, 1,
-                    Wq.as<cplx<R>>(), Rc.as<cplx<R>>(), 0, rk, c->stream, tau.as<cplx<R>>(), Qc.as<cplx<R>>(), 0,
-                    pq));
+    TRY(qr_launch<R>(c, Cb.as<cplx<R>>(), B0(), L1(Tcols, 1), L1(rk, Tcols), 1, Tcols, rk, Tcols, Tcols, 1,
+                     Wq.as<cplx<R>>(), Rc.as<cplx<R>>(), 0, rk, tau.as<cplx<R>>(), Qc.as<cplx<R>>(), 0, pq));
     TRY(U.alloc(c, (size_t)rk * rk * sizeof(cplx<R>)));
     TRY(UG.alloc(c, (size_t)pq * rk * sizeof(cplx<R>)));
     TRY(Vw.alloc(c, (size_t)rk * rk * sizeof(cplx<R>)));
@@ -370,8 +428,8 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     TRY(dbg_finite<R>(c, Cb.as<cplx<R>>(), rk * Tcols, "round sweep2 C", k));
     TRY(dbg_finite<R>(c, Rc.as<cplx<R>>(), pq * rk, "round sweep2 Rc", k));
     TRY(dbg_finite<R>(c, Qc.as<cplx<R>>(), Tcols * pq, "round sweep2 Qc", k));
-    TRY(qtt_jacobi<R>(Rc.as<cplx<R>>(), Vw.as<cplx<R>>(), sig.as<R>(), U.as<cplx<R>>(), (int)pq, (int)rk, 1, 60,
-                      nullptr, c->stream, UG.as<cplx<R>>()));
+    TRY(jacobi_launch<R>(c, Rc.as<cplx<R>>(), Vw.as<cplx<R>>(), sig.as<R>(), U.as<cplx<R>>(), (int)pq, (int)rk, 60,
+                         UG.as<cplx<R>>()));
     TRY(dbg_finite<R>(c, U.as<cplx<R>>(), rk * rk, "round sweep2 U", k));
     TRY(dbg_finite<R>(c, UG.as<cplx<R>>(), pq * rk, "round sweep2 UG", k));
     int t;
@@ -779,9 +837,8 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
     TRY(outc[k].alloc(c, (size_t)m * q * sizeof(C)));
     TRY(Wq.alloc(c, (size_t)m * l1 * sizeof(C)));
     TRY(tau.alloc(c, (size_t)2 * l1 * sizeof(C)));
-    c->launches++;
-    TRY(qtt_qr_r<R>(Z.as<C>(), B0(), L1(m, l1), L1(l1, 1), 0, m, l1, m, m, 1, Wq.as<C>(), nullptr, 0, 0, c->stream,
-                    tau.as<C>(), outc[k].as<C>(), 0, q));
+    TRY(qr_launch<R>(c, Z.as<C>(), B0(), L1(m, l1), L1(l1, 1), 0, m, l1, m, m, 1, Wq.as<C>(), nullptr, 0, 0,
+                     tau.as<C>(), outc[k].as<C>(), 0, q));
     TRY(dbg_finite<R>(c, outc[k].as<C>(), m * q, "left Q", k));
     orank[k + 1] = (int)q;
     // M_{k+1} = Q^H Y  (q x Bn)

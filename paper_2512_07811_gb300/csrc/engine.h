@@ -8,12 +8,49 @@
 #include "../../include/qtt.h"
 #include "common.cuh"
 
+// Kernel classes for the built-in profiler (qtt_ctx_profile*).
+enum { PK_GEMM = 0, PK_QR = 1, PK_JACOBI = 2, PK_ELEM = 3, PK_N = 4 };
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+  double flops, bytes;
+  int sweep_idx;         // Jacobi: index of the device sweep counter, else -1
+  double per_sweep;      // Jacobi: model flops of one sweep
+};
+
 struct qtt_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int64_t launches = 0;
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  int* d_sweeps = nullptr;   // device counters written by profiled Jacobi launches
+  int sweeps_cap = 0, sweeps_used = 0;
 };
+
+inline cudaEvent_t prof_begin(qtt_ctx* c) {
+  if (!c->prof) return nullptr;
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, c->stream);
+  return e;
+}
+inline void prof_end(qtt_ctx* c, cudaEvent_t a, int cls, double flops, double bytes, int sweep_idx = -1,
+                     double per_sweep = 0.0) {
+  if (!c->prof || !a) return;
+  cudaEvent_t b;
+  cudaEventCreate(&b);
+  cudaEventRecord(b, c->stream);
+  c->recs.push_back(ProfRec{cls, a, b, flops, bytes, sweep_idx, per_sweep});
+}
+inline int* prof_sweep_slot(qtt_ctx* c, int* idx) {
+  *idx = -1;
+  if (!c->prof || !c->d_sweeps || c->sweeps_used >= c->sweeps_cap) return nullptr;
+  *idx = c->sweeps_used++;
+  return c->d_sweeps + *idx;
+}
 
 struct qtt_tt {
   qtt_ctx* ctx = nullptr;

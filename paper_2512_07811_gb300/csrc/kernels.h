@@ -18,6 +18,10 @@ int qtt_jacobi(cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, in
                int max_sweeps, int* sweeps, cudaStream_t s, cplx<R>* Usorted = nullptr);
 
 template <class R>
+int qtt_jacobi_wide(const cplx<R>* G, cplx<R>* Gwork, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, cplx<R>* Usorted,
+                    int p, int q, int max_sweeps, int* dflag, int* sweeps_done, int64_t* launches, cudaStream_t s);
+
+template <class R>
 int qtt_trunc_rank(const R* sigma, int q, double delta, int max_rank, int* out, double* tail,
                    cudaStream_t s);
 

@@ -8,6 +8,8 @@
 // the truncation tail are always in double.
 #include <float.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -302,6 +304,116 @@ __global__ void trunc_rank_kernel(const R* __restrict__ s, int q, double delta, 
   if (tail_out) *tail_out = sqrt(tl);
 }
 
+// ------------------------------------------- one-sided Jacobi over many CTAs
+// Same rotations as jacobi_kernel, one launch per round of the round-robin
+// tournament (q/2 disjoint column pairs, one warp per pair, all SMs), on a
+// column-major copy Gc (q columns of length p) and Vc (q columns of length q).
+// Round r pairs position i with position qe-1-i of the order
+// [0, 1 + (r mod (qe-1)), ...]: order[0] = 0, order[i] = 1 + (i - 1 + r) mod (qe - 1).
+template <class R>
+__global__ void __launch_bounds__(256)
+jacobi_round_kernel(cplx<R>* __restrict__ Gc, cplx<R>* __restrict__ Vc, int p, int q, int round,
+                    int* __restrict__ rotated) {
+  const int qe = q + (q & 1);
+  const int lane = threadIdx.x & 31;
+  const int pr = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (pr >= qe / 2) return;
+  auto ord = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + round) % (qe - 1); };
+  int a = ord(pr), c = ord(qe - 1 - pr);
+  if (a >= q || c >= q) return;
+  if (a > c) { int t = a; a = c; c = t; }
+  cplx<R>* ga = Gc + (int64_t)a * p;
+  cplx<R>* gc = Gc + (int64_t)c * p;
+  R al = 0, be = 0;
+  cplx<R> g(0, 0);
+  for (int i = lane; i < p; i += 32) {
+    cplx<R> x = ga[i], y = gc[i];
+    al += abs2(x);
+    be += abs2(y);
+    cfma_conj(g, x, y);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    g.re += __shfl_xor_sync(0xffffffffu, g.re, o);
+    g.im += __shfl_xor_sync(0xffffffffu, g.im, o);
+  }
+  const R tol = (sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON)) * sqrt(R(p > 1 ? p : 1));
+  R ag = sqrt(abs2(g));
+  if (!(al > R(0) && be > R(0)) || !(ag > tol * sqrt(al) * sqrt(be))) return;
+  cplx<R> ph(g.re / ag, g.im / ag);
+  R zeta = (be - al) / (R(2) * ag);
+  R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+  R cs = R(1) / sqrt(R(1) + t * t);
+  R sn = cs * t;
+  cplx<R> f1 = sn * conjg(ph), f2 = sn * ph;
+  for (int i = lane; i < p; i += 32) {
+    cplx<R> x = ga[i], y = gc[i];
+    ga[i] = cs * x - f1 * y;
+    gc[i] = f2 * x + cs * y;
+  }
+  cplx<R>* va = Vc + (int64_t)a * q;
+  cplx<R>* vc = Vc + (int64_t)c * q;
+  for (int i = lane; i < q; i += 32) {
+    cplx<R> x = va[i], y = vc[i];
+    va[i] = cs * x - f1 * y;
+    vc[i] = f2 * x + cs * y;
+  }
+  if (lane == 0) *rotated = 1;
+}
+
+// column norms of Gc, then the sorted outputs in the row-major layout of jacobi_kernel
+template <class R>
+__global__ void __launch_bounds__(256)
+jacobi_finish_kernel(const cplx<R>* __restrict__ Gc, const cplx<R>* __restrict__ Vc, int p, int q,
+                     R* __restrict__ sigma_out, cplx<R>* __restrict__ Vs, cplx<R>* __restrict__ Us) {
+  extern __shared__ unsigned char smem_raw[];
+  R* norms = reinterpret_cast<R*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int c = warp; c < q; c += nwarps) {
+    R s = 0;
+    for (int i = lane; i < p; i += 32) s += abs2(Gc[(int64_t)c * p + i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) norms[c] = sqrt(s);
+  }
+  __syncthreads();
+  for (int c = warp; c < q; c += nwarps) {
+    R v = norms[c];
+    int rk = 0;
+    for (int i = 0; i < q; ++i) {
+      R u = norms[i];
+      rk += (u > v) || (u == v && i < c);
+    }
+    if (lane == 0) sigma_out[rk] = v;
+    for (int i = lane; i < q; i += 32) Vs[(int64_t)i * q + rk] = Vc[(int64_t)c * q + i];
+    if (Us) {
+      R f = v > (sizeof(R) == 8 ? R(DBL_MIN) : R(FLT_MIN)) * R(4) ? R(1) / v : R(0);
+      for (int i = lane; i < p; i += 32) {
+        cplx<R> g = Gc[(int64_t)c * p + i];
+        Us[(int64_t)i * q + rk] = cplx<R>(g.re * f, g.im * f);
+      }
+    }
+  }
+}
+
+// G (p x q row-major) -> Gc column-major; Vc = identity (column-major)
+template <class R>
+__global__ void jacobi_setup_kernel(const cplx<R>* __restrict__ G, int p, int q, cplx<R>* __restrict__ Gc,
+                                    cplx<R>* __restrict__ Vc) {
+  const int64_t tg = (int64_t)p * q, tv = (int64_t)q * q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tg + tv;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < tg) {
+      int64_t c = e / p, i = e - c * p;
+      Gc[e] = G[i * q + c];
+    } else {
+      int64_t f = e - tg;
+      int64_t c = f / q, i = f - c * q;
+      Vc[f] = cplx<R>(i == c ? R(1) : R(0), R(0));
+    }
+  }
+}
+
 }  // namespace
 
 template <class R>
@@ -345,3 +457,47 @@ template int qtt_jacobi<double>(zc*, zc*, double*, zc*, int, int, int, int, int*
 template int qtt_jacobi<float>(cc*, cc*, float*, cc*, int, int, int, int, int*, cudaStream_t, cc*);
 template int qtt_trunc_rank<double>(const double*, int, double, int, int*, double*, cudaStream_t);
 template int qtt_trunc_rank<float>(const float*, int, double, int, int*, double*, cudaStream_t);
+
+// Multi-CTA one-sided Jacobi (batch 1): one launch per round, a device flag
+// per sweep read by the host (one synchronisation per sweep, at most
+// max_sweeps sweeps).  Gwork needs p*q elements, Vwork q*q.
+template <class R>
+int qtt_jacobi_wide(const cplx<R>* G, cplx<R>* Gwork, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, cplx<R>* Usorted,
+                    int p, int q, int max_sweeps, int* dflag, int* sweeps_done, int64_t* launches, cudaStream_t s) {
+  if (q <= 0) return QTT_OK;
+  const int64_t tot = (int64_t)p * q + (int64_t)q * q;
+  jacobi_setup_kernel<R><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 65535), 256, 0, s>>>(G, p, q, Gwork, Vwork);
+  *launches += 1;
+  const int qe = q + (q & 1);
+  const int pairs = qe / 2;
+  const unsigned blocks = (unsigned)((pairs * 32 + 255) / 256);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (cudaMemsetAsync(dflag, 0, sizeof(int), s) != cudaSuccess) return QTT_ERR_CUDA;
+    for (int r = 0; r < qe - 1; ++r)
+      jacobi_round_kernel<R><<<blocks, 256, 0, s>>>(Gwork, Vwork, p, q, r, dflag);
+    *launches += qe - 1;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return QTT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return QTT_ERR_CUDA;
+    if (!h) {
+      ++sweep;
+      break;
+    }
+  }
+  if (sweeps_done) *sweeps_done = sweep;
+  size_t sm = (size_t)q * sizeof(R);
+  if (sm > 48 * 1024) {
+    if (cudaFuncSetAttribute(jacobi_finish_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return QTT_ERR_CUDA;
+  }
+  jacobi_finish_kernel<R><<<1, 256, sm, s>>>(Gwork, Vwork, p, q, sigma, Vsorted, Usorted);
+  *launches += 1;
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template int qtt_jacobi_wide<double>(const zc*, zc*, zc*, double*, zc*, zc*, int, int, int, int*, int*, int64_t*,
+                                     cudaStream_t);
+template int qtt_jacobi_wide<float>(const cc*, cc*, cc*, float*, cc*, cc*, int, int, int, int*, int*, int64_t*,
+                                    cudaStream_t);

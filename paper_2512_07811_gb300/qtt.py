@@ -83,6 +83,9 @@ _sig("qtt_ctx_create", C.c_int, [C.c_int, _P, C.POINTER(_P)])
 _sig("qtt_ctx_destroy", None, [_P])
 _sig("qtt_ctx_sync", C.c_int, [_P])
 _sig("qtt_ctx_launch_count", C.c_int64, [_P])
+_sig("qtt_ctx_profile", C.c_int, [_P, C.c_int])
+_sig("qtt_ctx_profile_read", C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double)])
 _sig("qtt_tt_create", C.c_int, [_P, C.c_int, _I32P, _I32P, C.c_int, C.POINTER(_P)])
 _sig("qtt_tt_destroy", None, [_P])
 _sig("qtt_tt_ncores", C.c_int, [_P])
@@ -109,15 +112,18 @@ _sig("tt_dot", C.c_int, [_P, _P, _P, C.POINTER(C.c_double)])
 _sig("tt_norm", C.c_int, [_P, _P, C.POINTER(C.c_double)])
 _sig("tt_from_dense", C.c_int, [_P, C.c_int, _I32P, _P, C.c_double, C.c_int, C.POINTER(_P)])
 _sig("qtt_qft_mpo", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(_P)])
+_sig("qtt_mpo_diag", C.c_int, [_P, _P, C.POINTER(_P)])
+_sig("qtt_mpo_convert", C.c_int, [_P, _P, C.c_int, C.POINTER(_P)])
 _sig("ms_homogenize", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
                                 C.POINTER(MSOpts), C.POINTER(C.c_double), C.POINTER(MSReport)])
 
 EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_sync", "qtt_ctx_launch_count",
+            "qtt_ctx_profile", "qtt_ctx_profile_read",
             "qtt_tt_create", "qtt_tt_destroy", "qtt_tt_ncores", "qtt_tt_ranks", "qtt_tt_modes", "qtt_tt_dtype",
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_sketched", "tt_dot", "tt_norm",
-            "tt_from_dense", "qtt_qft_mpo", "ms_homogenize"]
+            "tt_from_dense", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize"]
 
 
 def _check(st, what):
@@ -159,6 +165,18 @@ class Context:
     @property
     def launches(self) -> int:
         return int(_lib.qtt_ctx_launch_count(self.h))
+
+    KERNEL_CLASSES = {"gemm": 0, "qr": 1, "jacobi": 2, "elem": 3}
+
+    def profile(self, enable: bool):
+        _check(_lib.qtt_ctx_profile(self.h, 1 if enable else 0), "qtt_ctx_profile")
+
+    def profile_read(self, kclass: str):
+        ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+        n = C.c_int64()
+        _check(_lib.qtt_ctx_profile_read(self.h, self.KERNEL_CLASSES[kclass], C.byref(ms), C.byref(n), C.byref(fl),
+                                         C.byref(by)), "qtt_ctx_profile_read")
+        return {"ms": ms.value, "launches": int(n.value), "flops": fl.value, "bytes": by.value}
 
 
 class TT:
@@ -348,6 +366,25 @@ def qtt_qft_mpo(ctx: Context, nbits: int, sign: int = -1, tol: float = 1e-12) ->
     A._shapes = [(g[k], 2, 2, g[k + 1]) for k in range(nbits)]
     A._dtype = C128
     return A
+
+
+def qtt_mpo_diag(ctx: Context, x: TT) -> MPO:
+    h = _P()
+    _check(_lib.qtt_mpo_diag(ctx.h, x.h, C.byref(h)), "qtt_mpo_diag")
+    A = MPO(ctx, h, x.ncores)
+    r, m = x.ranks, x.modes
+    A._shapes = [(r[k], m[k], m[k], r[k + 1]) for k in range(x.ncores)]
+    A._dtype = x.dtype
+    return A
+
+
+def qtt_mpo_convert(ctx: Context, A: MPO, dtype) -> MPO:
+    h = _P()
+    _check(_lib.qtt_mpo_convert(ctx.h, A.h, int(dtype), C.byref(h)), "qtt_mpo_convert")
+    B = MPO(ctx, h, A.d)
+    B._shapes = getattr(A, "_shapes", None)
+    B._dtype = dtype
+    return B
 
 
 def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, tol: float, max_rank: int,

@@ -248,3 +248,26 @@ def test_ms_fp32_laminate(Q, ctx):
                              eps=1e-6, max_iter=20, prec=Q.PREC_F32)
     Cx = MS.scalar_laminate_keff(1.0, 10.0, 0.5)
     assert np.abs(C - Cx).max() / np.abs(Cx).max() < 1e-5
+
+
+@pytest.mark.parametrize("n", [13, 20])
+def test_qft_layer_route_matches_fft(Q, ctx, n):
+    """Beyond 12 bits the transform is built from circuit layers; applied to a
+    random rank-3 train it must equal numpy's unitary FFT with bit-reversed output."""
+    A = Q.qtt_qft_mpo(ctx, n, -1, 1e-12)
+    assert max(A.ranks) <= 24
+    rng = np.random.default_rng(40 + n)
+    ranks = [1] + [3] * (n - 1) + [1]
+    x = [rng.standard_normal((ranks[k], 2, ranks[k + 1])) + 0j for k in range(n)]
+    y = Q.tt_mpo_apply(ctx, A, Q.TT.from_cores(ctx, x))
+    v = T.tt_full(x).reshape(-1)
+    got = T.tt_full(y.cores()).reshape(-1)
+    want = np.fft.fft(v, norm="ortho")[QF.bit_reverse_indices(n)]
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+
+
+def test_mpo_diag_is_hadamard(Q, ctx):
+    x, y = cplx_tt(DIMS, RA, 30), cplx_tt(DIMS, RB, 31)
+    gx, gy = Q.TT.from_cores(ctx, x), Q.TT.from_cores(ctx, y)
+    z = Q.tt_mpo_apply(ctx, Q.qtt_mpo_diag(ctx, gx), gy)
+    assert rel_diff(z.cores(), T.tt_hadamard(x, y)) < 1e-13
