@@ -233,9 +233,12 @@ static int qr_launch(qtt_ctx* c, const cplx<R>* in, MIdx inB, MIdx rowI, MIdx co
                      int64_t out_bstride, int64_t ldr, cplx<R>* tauws = nullptr, cplx<R>* Qout = nullptr,
                      int64_t q_bstride = 0, int64_t ldq = 0) {
   c->launches++;
+  void* qws = nullptr;
+  if (Qout) TRY(dalloc(c, &qws, (size_t)batch * m * std::min(m, n) * sizeof(cplx<R>)));
   cudaEvent_t ev = prof_begin(c);
   int st = qtt_qr_r<R>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out, out_bstride,
-                       ldr, c->stream, tauws, Qout, q_bstride, ldq);
+                       ldr, c->stream, tauws, Qout, q_bstride, ldq, reinterpret_cast<cplx<R>*>(qws));
+  dfree(c, qws);
   prof_end(c, ev, PK_QR, batch * qr_flops((double)m, (double)n, Qout != nullptr),
            (double)batch * m * n * sizeof(cplx<R>) * 2.0);
   return st;
@@ -248,6 +251,16 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
   // sizeable FP64 factorisation over all SMs; FP32 stays in one CTA up to
   // q = 256, where one SM's FP32 rate beats a launch per round.
   const bool wide = (sizeof(R) == 8 && q >= 32) || q > 256;
+  const bool smem = !wide && qtt_jacobi_smem_bytes<R>(p, q) <= 200 * 1024;
+  if (smem) {
+    int idx;
+    int* slot = prof_sweep_slot(c, &idx);
+    c->launches++;
+    cudaEvent_t ev = prof_begin(c);
+    int st = qtt_jacobi_smem<R>(G, Vwork, sigma, Vsorted, Usorted, p, q, max_sweeps, slot, c->stream);
+    prof_end(c, ev, PK_JACOBI, 0.0, (double)(p + 2.0 * q) * q * sizeof(cplx<R>), idx, jacobi_sweep_flops(p, q));
+    return st;
+  }
   if (wide) {
     void* buf = nullptr;
     size_t gb = (size_t)p * q * sizeof(cplx<R>), vb = (size_t)q * q * sizeof(cplx<R>);

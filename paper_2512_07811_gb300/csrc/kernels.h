@@ -11,7 +11,13 @@ template <class R>
 int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
              int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
              int64_t out_bstride, int64_t ldr, cudaStream_t s, cplx<R>* tauws = nullptr,
-             cplx<R>* Qout = nullptr, int64_t q_bstride = 0, int64_t ldq = 0);
+             cplx<R>* Qout = nullptr, int64_t q_bstride = 0, int64_t ldq = 0, cplx<R>* Qws = nullptr);
+
+template <class R>
+size_t qtt_jacobi_smem_bytes(int p, int q);
+template <class R>
+int qtt_jacobi_smem(const cplx<R>* G, cplx<R>* Vws, R* sigma, cplx<R>* Vsorted, cplx<R>* Usorted, int p, int q,
+                    int max_sweeps, int* sweeps, cudaStream_t s);
 
 template <class R>
 int qtt_jacobi(cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, int q, int batch,

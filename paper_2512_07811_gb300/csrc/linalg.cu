@@ -34,11 +34,23 @@ __device__ R block_sum(R v, R* red) {
 // workspace of m*n elements (row-major, ld = n).  Output R_b is min(m, n) x n,
 // upper trapezoidal, row-major with leading dimension ldr, at out + b*out_bstride.
 template <class R>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ R warp_sum(R v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Householder QR, one CTA of 1024 threads per matrix.  The matrix is copied
+// into a column-major workspace (W + c*m + i holds element (i, c)) so that a
+// warp streams a column with consecutive lanes on consecutive rows; every
+// trailing column is handled by one warp (dot product with the reflector by
+// shuffles, then the rank-1 update).
+template <class R>
+__global__ void __launch_bounds__(1024)
 qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int conj_in,
             int64_t m, int64_t n, int64_t rows_total, int64_t rows_per_batch,
             cplx<R>* __restrict__ Wbase, cplx<R>* __restrict__ out, int64_t out_bstride, int64_t ldr,
-            cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout, int64_t q_bstride, int64_t ldq) {
+            cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout, int64_t q_bstride, int64_t ldq,
+            cplx<R>* __restrict__ Qws) {
   __shared__ double red[32];
   __shared__ cplx<R> s_inv_v0;
   __shared__ R s_tau;
@@ -49,15 +61,17 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
   int64_t valid = rows_total - row0;
   if (valid > m) valid = m;
   const int64_t ib = midx_off(inB, b);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   double part = 0.0;
   for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) {
+    // e enumerates the input row-major-ish: consecutive threads on consecutive columns
     int64_t i = e / n, c = e - i * n;
     cplx<R> v(0, 0);
     if (i < valid) {
       v = in[ib + midx_off(rowI, i) + midx_off(colI, c)];
       if (conj_in) v.im = -v.im;
     }
-    W[e] = v;
+    W[c * m + i] = v;
     part += (double)v.re * v.re + (double)v.im * v.im;
   }
   // columns whose remaining norm is below eps * ||A||_F are numerically zero:
@@ -69,21 +83,21 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
   const double zero_thresh2 = eps * eps * anorm2;
   const int64_t kmax = m < n ? m : n;
   for (int64_t j = 0; j < kmax; ++j) {
+    cplx<R>* colj = W + j * m;
     double p2 = 0.0;
     for (int64_t i = j + threadIdx.x; i < m; i += blockDim.x) {
-      cplx<R> v = W[i * n + j];
+      cplx<R> v = colj[i];
       p2 += (double)v.re * v.re + (double)v.im * v.im;
     }
     const double nrm2 = block_sum(p2, red);
     if (threadIdx.x == 0) {
-      cplx<R> x0 = W[j * n + j];
+      cplx<R> x0 = colj[j];
       double ax2 = (double)x0.re * x0.re + (double)x0.im * x0.im;
       double below = nrm2 - ax2;
       if (nrm2 <= zero_thresh2 || below <= zero_thresh2) {
-        // nothing to eliminate below the diagonal (or numerically zero column)
         s_tau = R(0);
         s_zero = 1;
-        if (nrm2 <= zero_thresh2) W[j * n + j] = cplx<R>(0, 0);
+        if (nrm2 <= zero_thresh2) colj[j] = cplx<R>(0, 0);
       } else {
         // H = I - tau v v^H with v = (1, x_1/v0, ...), v0 = x0 - alpha,
         // alpha = -e^{i arg x0} ||x||, tau = 2 |v0|^2 / ||x - alpha e1||^2 in [1, 2]
@@ -96,7 +110,7 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
         s_tau = (R)(2.0 * v02 / vn2);
         s_inv_v0 = cplx<R>((R)(v0r / v02), (R)(-v0i / v02));
         s_zero = 0;
-        W[j * n + j] = cplx<R>((R)alr, (R)ali);
+        colj[j] = cplx<R>((R)alr, (R)ali);
       }
       if (tauws) tauws[b * 2 * n + 2 * j + 1] = cplx<R>(s_tau, R(0));
     }
@@ -104,18 +118,22 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
     const R tau = s_tau;
     if (tau != R(0)) {
       const cplx<R> iv = s_inv_v0;
-      for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) W[i * n + j] = W[i * n + j] * iv;
+      for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) colj[i] = colj[i] * iv;
     } else if (s_zero) {
-      for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) W[i * n + j] = cplx<R>(0, 0);
+      for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) colj[i] = cplx<R>(0, 0);
     }
     __syncthreads();
     if (tau != R(0)) {
-      for (int64_t c = j + 1 + threadIdx.x; c < n; c += blockDim.x) {
-        cplx<R> w = W[j * n + c];
-        for (int64_t i = j + 1; i < m; ++i) cfma_conj(w, W[i * n + j], W[i * n + c]);
+      for (int64_t c = j + 1 + warp; c < n; c += nwarps) {
+        cplx<R>* colc = W + c * m;
+        cplx<R> w(0, 0);
+        if (lane == 0) w = colc[j];
+        for (int64_t i = j + 1 + lane; i < m; i += 32) cfma_conj(w, colj[i], colc[i]);
+        w.re = warp_sum(w.re);
+        w.im = warp_sum(w.im);
         w = tau * w;
-        W[j * n + c] = W[j * n + c] - w;
-        for (int64_t i = j + 1; i < m; ++i) W[i * n + c] = W[i * n + c] - W[i * n + j] * w;
+        if (lane == 0) colc[j] = colc[j] - w;
+        for (int64_t i = j + 1 + lane; i < m; i += 32) colc[i] = colc[i] - colj[i] * w;
       }
     }
     __syncthreads();
@@ -124,29 +142,41 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
     cplx<R>* Rb = out + b * out_bstride;
     for (int64_t e = threadIdx.x; e < kmax * n; e += blockDim.x) {
       int64_t i = e / n, c = e - i * n;
-      Rb[i * ldr + c] = (c >= i) ? W[i * n + c] : cplx<R>(0, 0);
+      Rb[i * ldr + c] = (c >= i) ? W[c * m + i] : cplx<R>(0, 0);
     }
   }
   if (Qout) {
     // Q = H_0 H_1 ... H_{kmax-1} [I; 0], accumulated from the last reflector
-    cplx<R>* Q = Qout + b * q_bstride;
+    // in the column-major workspace Qws (one warp per column of Q, rows on
+    // the lanes), then written out row-major
+    cplx<R>* Qc = Qws + b * m * kmax;
     for (int64_t e = threadIdx.x; e < m * kmax; e += blockDim.x) {
-      int64_t i = e / kmax, c = e - i * kmax;
-      Q[i * ldq + c] = cplx<R>(i == c ? R(1) : R(0), R(0));
+      int64_t c = e / m, i = e - c * m;
+      Qc[e] = cplx<R>(i == c ? R(1) : R(0), R(0));
     }
     __syncthreads();
     for (int64_t j = kmax - 1; j >= 0; --j) {
       const R tau = tauws[b * 2 * n + 2 * j + 1].re;
+      const cplx<R>* colj = W + j * m;
       if (tau != R(0)) {
-        for (int64_t c = j + threadIdx.x; c < kmax; c += blockDim.x) {
-          cplx<R> w = Q[j * ldq + c];
-          for (int64_t i = j + 1; i < m; ++i) cfma_conj(w, W[i * n + j], Q[i * ldq + c]);
+        for (int64_t c = j + warp; c < kmax; c += nwarps) {
+          cplx<R>* qc = Qc + c * m;
+          cplx<R> w(0, 0);
+          if (lane == 0) w = qc[j];
+          for (int64_t i = j + 1 + lane; i < m; i += 32) cfma_conj(w, colj[i], qc[i]);
+          w.re = warp_sum(w.re);
+          w.im = warp_sum(w.im);
           w = tau * w;
-          Q[j * ldq + c] = Q[j * ldq + c] - w;
-          for (int64_t i = j + 1; i < m; ++i) Q[i * ldq + c] = Q[i * ldq + c] - W[i * n + j] * w;
+          if (lane == 0) qc[j] = qc[j] - w;
+          for (int64_t i = j + 1 + lane; i < m; i += 32) qc[i] = qc[i] - colj[i] * w;
         }
       }
       __syncthreads();
+    }
+    cplx<R>* Q = Qout + b * q_bstride;
+    for (int64_t e = threadIdx.x; e < m * kmax; e += blockDim.x) {
+      int64_t i = e / kmax, c = e - i * kmax;
+      Q[i * ldq + c] = Qc[c * m + i];
     }
   }
 }
@@ -414,18 +444,131 @@ __global__ void jacobi_setup_kernel(const cplx<R>* __restrict__ G, int p, int q,
   }
 }
 
+// ------------------------------------------- one-sided Jacobi in shared memory
+// One CTA of 1024 threads.  G (p x q, row-major input, ld q) is held
+// column-major in shared memory; the rotations accumulate in the
+// column-major workspace Vws (q x q, global).  Each round of the round-robin
+// tournament pairs order[i] with order[qe-1-i] (order[0] = 0, order[i] =
+// 1 + (i - 1 + r) mod (qe - 1)); warps take the pairs of a round, lanes the
+// rows.  Outputs as in jacobi_kernel: sigma sorted decreasingly, V columns
+// (row-major q x q) and normalised columns of the rotated G (row-major p x q)
+// in the same order.
+template <class R>
+__global__ void __launch_bounds__(1024)
+jacobi_smem_kernel(const cplx<R>* __restrict__ Gin, cplx<R>* __restrict__ Vws, R* __restrict__ sigma_out,
+                   cplx<R>* __restrict__ Vs, cplx<R>* __restrict__ Us, int p, int q, int max_sweeps,
+                   int* __restrict__ sweeps_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* Gs = reinterpret_cast<cplx<R>*>(smem_raw);
+  R* norms = reinterpret_cast<R*>(Gs + (size_t)p * q);
+  __shared__ int s_rot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+    int i = e / q, c = e - i * q;
+    Gs[c * p + i] = Gin[e];
+  }
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+    int c = e / q, i = e - c * q;
+    Vws[e] = cplx<R>(i == c ? R(1) : R(0), R(0));
+  }
+  __syncthreads();
+  const int qe = q + (q & 1);
+  const R tol = (sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON)) * sqrt(R(p > 1 ? p : 1));
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < qe - 1; ++round) {
+      for (int pr = warp; pr < qe / 2; pr += nwarps) {
+        int a = pr == 0 ? 0 : 1 + (pr - 1 + round) % (qe - 1);
+        int qi = qe - 1 - pr;
+        int c = qi == 0 ? 0 : 1 + (qi - 1 + round) % (qe - 1);
+        if (a >= q || c >= q) continue;
+        if (a > c) { int t = a; a = c; c = t; }
+        cplx<R>* ga = Gs + (size_t)a * p;
+        cplx<R>* gc = Gs + (size_t)c * p;
+        R al = 0, be = 0;
+        cplx<R> g(0, 0);
+        for (int i = lane; i < p; i += 32) {
+          cplx<R> x = ga[i], y = gc[i];
+          al += abs2(x);
+          be += abs2(y);
+          cfma_conj(g, x, y);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        g.re = warp_sum(g.re);
+        g.im = warp_sum(g.im);
+        R ag = sqrt(abs2(g));
+        if (!(al > R(0) && be > R(0)) || !(ag > tol * sqrt(al) * sqrt(be))) continue;
+        cplx<R> ph(g.re / ag, g.im / ag);
+        R zeta = (be - al) / (R(2) * ag);
+        R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+        R cs = R(1) / sqrt(R(1) + t * t);
+        R sn = cs * t;
+        cplx<R> f1 = sn * conjg(ph), f2 = sn * ph;
+        for (int i = lane; i < p; i += 32) {
+          cplx<R> x = ga[i], y = gc[i];
+          ga[i] = cs * x - f1 * y;
+          gc[i] = f2 * x + cs * y;
+        }
+        cplx<R>* va = Vws + (size_t)a * q;
+        cplx<R>* vc = Vws + (size_t)c * q;
+        for (int i = lane; i < q; i += 32) {
+          cplx<R> x = va[i], y = vc[i];
+          va[i] = cs * x - f1 * y;
+          vc[i] = f2 * x + cs * y;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    int any = s_rot;
+    __syncthreads();
+    if (!any) {
+      ++sweep;
+      break;
+    }
+  }
+  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+  for (int c = warp; c < q; c += nwarps) {
+    R sacc = 0;
+    for (int i = lane; i < p; i += 32) sacc += abs2(Gs[(size_t)c * p + i]);
+    sacc = warp_sum(sacc);
+    if (lane == 0) norms[c] = sqrt(sacc);
+  }
+  __syncthreads();
+  for (int c = warp; c < q; c += nwarps) {
+    R v = norms[c];
+    int rk = 0;
+    for (int i = 0; i < q; ++i) {
+      R u = norms[i];
+      rk += (u > v) || (u == v && i < c);
+    }
+    if (lane == 0) sigma_out[rk] = v;
+    for (int i = lane; i < q; i += 32) Vs[(size_t)i * q + rk] = Vws[(size_t)c * q + i];
+    if (Us) {
+      R f = v > (sizeof(R) == 8 ? R(DBL_MIN) : R(FLT_MIN)) * R(4) ? R(1) / v : R(0);
+      for (int i = lane; i < p; i += 32) {
+        cplx<R> g = Gs[(size_t)c * p + i];
+        Us[(size_t)i * q + rk] = cplx<R>(g.re * f, g.im * f);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 template <class R>
 int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
              int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
              int64_t out_bstride, int64_t ldr, cudaStream_t s, cplx<R>* tauws, cplx<R>* Qout,
-             int64_t q_bstride, int64_t ldq) {
+             int64_t q_bstride, int64_t ldq, cplx<R>* Qws) {
   if (batch <= 0 || m <= 0 || n <= 0) return QTT_OK;
-  if (Qout && !tauws) return QTT_ERR_ARG;
-  qr_r_kernel<R><<<(unsigned)batch, 256, 0, s>>>(in, inB, rowI, colI, conj_in, m, n, rows_total,
+  if (Qout && (!tauws || !Qws)) return QTT_ERR_ARG;
+  qr_r_kernel<R><<<(unsigned)batch, 1024, 0, s>>>(in, inB, rowI, colI, conj_in, m, n, rows_total,
                                                  rows_per_batch, W, out, out_bstride, ldr, tauws, Qout,
-                                                 q_bstride, ldq);
+                                                 q_bstride, ldq, Qws);
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
 
@@ -450,9 +593,9 @@ int qtt_trunc_rank(const R* sigma, int q, double delta, int max_rank, int* out, 
 }
 
 template int qtt_qr_r<double>(const zc*, MIdx, MIdx, MIdx, int, int64_t, int64_t, int64_t, int64_t, int64_t,
-                              zc*, zc*, int64_t, int64_t, cudaStream_t, zc*, zc*, int64_t, int64_t);
+                              zc*, zc*, int64_t, int64_t, cudaStream_t, zc*, zc*, int64_t, int64_t, zc*);
 template int qtt_qr_r<float>(const cc*, MIdx, MIdx, MIdx, int, int64_t, int64_t, int64_t, int64_t, int64_t,
-                             cc*, cc*, int64_t, int64_t, cudaStream_t, cc*, cc*, int64_t, int64_t);
+                             cc*, cc*, int64_t, int64_t, cudaStream_t, cc*, cc*, int64_t, int64_t, cc*);
 template int qtt_jacobi<double>(zc*, zc*, double*, zc*, int, int, int, int, int*, cudaStream_t, zc*);
 template int qtt_jacobi<float>(cc*, cc*, float*, cc*, int, int, int, int, int*, cudaStream_t, cc*);
 template int qtt_trunc_rank<double>(const double*, int, double, int, int*, double*, cudaStream_t);
@@ -501,3 +644,23 @@ template int qtt_jacobi_wide<double>(const zc*, zc*, zc*, double*, zc*, zc*, int
                                      cudaStream_t);
 template int qtt_jacobi_wide<float>(const cc*, cc*, cc*, float*, cc*, cc*, int, int, int, int*, int*, int64_t*,
                                     cudaStream_t);
+
+template <class R>
+size_t qtt_jacobi_smem_bytes(int p, int q) { return (size_t)p * q * sizeof(cplx<R>) + (size_t)q * sizeof(R) + 16; }
+
+template <class R>
+int qtt_jacobi_smem(const cplx<R>* G, cplx<R>* Vws, R* sigma, cplx<R>* Vsorted, cplx<R>* Usorted, int p, int q,
+                    int max_sweeps, int* sweeps, cudaStream_t s) {
+  if (q <= 0) return QTT_OK;
+  size_t sm = qtt_jacobi_smem_bytes<R>(p, q);
+  if (sm > 227 * 1024) return QTT_ERR_RANK;
+  if (cudaFuncSetAttribute(jacobi_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return QTT_ERR_CUDA;
+  jacobi_smem_kernel<R><<<1, 1024, sm, s>>>(G, Vws, sigma, Vsorted, Usorted, p, q, max_sweeps, sweeps);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template size_t qtt_jacobi_smem_bytes<double>(int, int);
+template size_t qtt_jacobi_smem_bytes<float>(int, int);
+template int qtt_jacobi_smem<double>(const zc*, zc*, double*, zc*, zc*, int, int, int, int*, cudaStream_t);
+template int qtt_jacobi_smem<float>(const cc*, cc*, float*, cc*, cc*, int, int, int, int*, cudaStream_t);
