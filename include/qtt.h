@@ -57,6 +57,7 @@ extern "C" {
 typedef struct qtt_ctx qtt_ctx;
 typedef struct qtt_tt qtt_tt;
 typedef struct qtt_mpo qtt_mpo;
+typedef struct qtt_mlp qtt_mlp;
 
 typedef enum { QTT_C128 = 0, QTT_C64 = 1 } qtt_dtype;
 
@@ -206,6 +207,18 @@ typedef struct {
   int32_t interleaved;  /* site order: 1 = x1 y1 z1 x2 ..., 0 = grouped by dimension      */
 } qtt_rve;
 
+/* Per-bond rank features of one rounding inside ms_homogenize (the rank
+ * predictor's input), QTT_MLP_FEATURES floats per bond k = 1..d-1:
+ *  0 k/d                      1 log2(1 + structured input rank at bond k)/10
+ *  2 log2(1 + previous output rank at k, same step)/10 (0 on the first iteration)
+ *  3, 4 the same at k-1 and k+1       5 -log10(eps)/10
+ *  6 log2(1 + max_rank)/10            7 step id/8 (0 contrast, 1-3 SFFT x,y,z,
+ *                                       4 Green, 5-7 inverse SFFT z,y,x)
+ *  8 min(iteration, 20)/20            9 log2 of the smaller mode product on
+ *                                       either side of the bond / 20
+ * target: log2(output rank at bond k). */
+#define QTT_MLP_FEATURES 10
+
 typedef struct {
   qtt_prec prec;        /* arithmetic of the iteration                                    */
   double eps;           /* rounding tolerance of every step                               */
@@ -215,6 +228,12 @@ typedef struct {
   int32_t load_mask;    /* bit k set: solve load case E = e_k (column k of C_eff)        */
   int32_t min_iter;
   uint64_t seed;        /* counter-based generator seed for the sketches                 */
+  const qtt_mlp* predictor; /* NULL: every sketch has width max_rank + oversample; else the
+                            per-bond widths are 1.25 * predicted rank + oversample, with a
+                            fallback to the full width when a bond's rank saturates its sketch */
+  float* trace;          /* NULL or host buffer receiving (features, target) rows of every
+                            sketched rounding: QTT_MLP_FEATURES + 1 floats per bond          */
+  int64_t trace_cap;     /* capacity of `trace` in rows                                     */
 } ms_opts;
 
 typedef struct {
@@ -224,6 +243,9 @@ typedef struct {
   int32_t max_rank_seen;
   double setup_ms, iterate_ms;
   int64_t kernel_launches;
+  int64_t trace_len;       /* rows written to opts->trace                                 */
+  int64_t sketch_width_sum;/* sum over roundings and bonds of the sketch ranks used      */
+  int32_t fallbacks;       /* sketched roundings redone at the full width                */
 } ms_report;
 
 /* Moulinec-Suquet homogenisation in QTT form (Sec. 3.2, Algorithm 2):
@@ -237,6 +259,32 @@ typedef struct {
  * opts->load_mask; `report` may be NULL. */
 QTT_API int ms_homogenize(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, double tol, int max_rank,
                   const ms_opts* opts, double* C_eff, ms_report* report);
+
+QTT_API /* ------------------------------------------------ rank predictor (MLP) */
+/* A multilayer perceptron with three hidden layers of width 64 and ReLU, FP16
+ * weights, FP32 accumulation, FP32 master weights and Adam moments; it maps
+ * QTT_MLP_FEATURES (or any n_features <= 32) per-bond features to a predicted
+ * log2 rank.  A builder addition with no counterpart in the paper (nearest
+ * relative: the coarse-grained ranks of Sec. 5.1).  Packed parameter order:
+ * W0 (64 x F), b0 (64), W1 (64 x 64), b1, W2 (64 x 64), b2, W3 (64), b3 (1),
+ * weights row-major (out, in).  Host buffers throughout; every call
+ * synchronises the context stream. */
+QTT_API int qtt_mlp_create(qtt_ctx* ctx, int n_features, uint64_t seed, qtt_mlp** out);
+QTT_API void qtt_mlp_destroy(qtt_mlp* m);
+QTT_API int64_t qtt_mlp_param_count(const qtt_mlp* m);
+/* Replace the FP32 master parameters (the FP16 weights are rounded from them)
+ * and reset the Adam moments. */
+QTT_API int qtt_mlp_set_params(qtt_mlp* m, const float* params, int64_t count);
+QTT_API int qtt_mlp_get_params(const qtt_mlp* m, float* params, int64_t count);
+/* y[b] for the B rows of X (B x F, row-major). */
+QTT_API int qtt_mlp_forward(qtt_mlp* m, const float* X, int64_t B, float* y);
+/* One training step on the batch: the asymmetric loss
+ * (1/B) sum w_b (y_b - t_b)^2, w_b = alpha where y_b < t_b, else 1; its
+ * gradient by the hand-written backward kernel; one Adam update with rate lr.
+ * Returns the loss before the update; `grads` (nullable) receives the packed
+ * gradient. */
+QTT_API int qtt_mlp_train_step(qtt_mlp* m, const float* X, const float* t, int64_t B, float alpha, float lr,
+                               double* loss, float* grads);
 
 QTT_API const char* qtt_status_string(int status);
 

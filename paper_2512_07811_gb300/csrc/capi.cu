@@ -15,6 +15,30 @@
 #include "engine.h"
 #include "kernels.h"
 
+#include <cuda_fp16.h>
+
+#include <random>
+
+int64_t qtt_mlp_param_count_f(int F);
+int qtt_mlp_sync_half(const float* P, __half* Wh, int64_t n, cudaStream_t s);
+int qtt_mlp_forward_dev(const __half* Wh, const float* P, int F, const float* X, int64_t B, float* Y, cudaStream_t s);
+int qtt_mlp_backward_dev(const __half* Wh, const float* P, int F, const float* X, const float* T, int64_t B,
+                         float alpha, float* G, float* loss_acc, cudaStream_t s);
+int qtt_mlp_adam_dev(float* P, __half* Wh, const float* G, float* M, float* V, int64_t n, float lr, int t,
+                     cudaStream_t s);
+
+struct qtt_mlp {
+  qtt_ctx* ctx = nullptr;
+  int F = 0;
+  int64_t n = 0;
+  float* P = nullptr;   // FP32 master parameters (packed)
+  __half* Wh = nullptr; // FP16 copy used by the kernels for the weights
+  float* M = nullptr;   // Adam moments
+  float* V = nullptr;
+  float* G = nullptr;   // gradient (+1 slot)
+  int t = 0;
+};
+
 #define TRY(expr)                 \
   do {                            \
     int _st = (expr);             \
@@ -177,8 +201,8 @@ int check_prec(qtt_dtype dt, qtt_prec p) {
 }
 
 // sketch train: real Gaussian cores N(0, 1/(n_k l_k)), ranks min(l, prod left, prod right)
-int make_sketch(qtt_ctx* c, const std::vector<int>& modes, int ell, qtt_dtype dt, uint64_t seed, uint64_t stream_id,
-                qtt_tt** out) {
+int make_sketch(qtt_ctx* c, const std::vector<int>& modes, const std::vector<int>& ell, qtt_dtype dt, uint64_t seed,
+                uint64_t stream_id, qtt_tt** out) {
   const int d = (int)modes.size();
   std::vector<int> r(d + 1, 1);
   double left = 1;
@@ -186,7 +210,7 @@ int make_sketch(qtt_ctx* c, const std::vector<int>& modes, int ell, qtt_dtype dt
     left *= modes[k - 1];
     double right = 1;
     for (int j = k; j < d; ++j) right *= modes[j];
-    r[k] = (int)std::min<double>(ell, std::min(left, right));
+    r[k] = (int)std::max<double>(1.0, std::min<double>(ell[k], std::min(left, right)));
   }
   int st;
   qtt_tt* S = tt_alloc(c, d, modes, r, dt, &st);
@@ -667,6 +691,116 @@ int qtt_mpo_convert(qtt_ctx* c, const qtt_mpo* A, qtt_dtype dt, qtt_mpo** out) {
   return convert_mpo(c, A, dt, out);
 }
 
+
+// ------------------------------------------------------------ rank predictor
+int qtt_mlp_create(qtt_ctx* c, int F, uint64_t seed, qtt_mlp** out) {
+  if (!c || !out || F < 1 || F > 32) return QTT_ERR_ARG;
+  qtt_mlp* m = new (std::nothrow) qtt_mlp();
+  if (!m) return QTT_ERR_OOM;
+  m->ctx = c;
+  m->F = F;
+  m->n = qtt_mlp_param_count_f(F);
+  size_t fb = (size_t)m->n * sizeof(float);
+  if (cudaMalloc(&m->P, fb) != cudaSuccess || cudaMalloc(&m->Wh, (size_t)m->n * sizeof(__half)) != cudaSuccess ||
+      cudaMalloc(&m->M, fb) != cudaSuccess || cudaMalloc(&m->V, fb) != cudaSuccess ||
+      cudaMalloc(&m->G, fb + sizeof(float)) != cudaSuccess) {
+    qtt_mlp_destroy(m);
+    return QTT_ERR_OOM;
+  }
+  // He-normal weights, zero biases (host generator, seeded)
+  std::vector<float> h(m->n, 0.f);
+  std::mt19937_64 gen(seed);
+  const int sizes[5] = {F, 64, 64, 64, 1};
+  int64_t off = 0;
+  for (int l = 0; l < 4; ++l) {
+    std::normal_distribution<float> nd(0.f, sqrtf(2.f / sizes[l]));
+    for (int64_t i = 0; i < (int64_t)sizes[l + 1] * sizes[l]; ++i) h[off + i] = nd(gen);
+    off += (int64_t)sizes[l + 1] * sizes[l] + sizes[l + 1];
+  }
+  int st = qtt_mlp_set_params(m, h.data(), m->n);
+  if (st) {
+    qtt_mlp_destroy(m);
+    return st;
+  }
+  *out = m;
+  return QTT_OK;
+}
+
+void qtt_mlp_destroy(qtt_mlp* m) {
+  if (!m) return;
+  cudaFree(m->P);
+  cudaFree(m->Wh);
+  cudaFree(m->M);
+  cudaFree(m->V);
+  cudaFree(m->G);
+  delete m;
+}
+
+int64_t qtt_mlp_param_count(const qtt_mlp* m) { return m ? m->n : QTT_ERR_ARG; }
+
+int qtt_mlp_set_params(qtt_mlp* m, const float* p, int64_t n) {
+  if (!m || !p || n != m->n) return QTT_ERR_ARG;
+  cudaStream_t s = m->ctx->stream;
+  if (cudaMemcpyAsync(m->P, p, n * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess) return QTT_ERR_CUDA;
+  cudaMemsetAsync(m->M, 0, n * sizeof(float), s);
+  cudaMemsetAsync(m->V, 0, n * sizeof(float), s);
+  m->t = 0;
+  m->ctx->launches++;
+  TRY(qtt_mlp_sync_half(m->P, m->Wh, n, s));
+  return cudaStreamSynchronize(s) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+int qtt_mlp_get_params(const qtt_mlp* m, float* p, int64_t n) {
+  if (!m || !p || n != m->n) return QTT_ERR_ARG;
+  return sync_read(m->ctx, p, m->P, n * sizeof(float));
+}
+
+static int mlp_forward_host(qtt_mlp* m, const float* X, int64_t B, float* y) {
+  qtt_ctx* c = m->ctx;
+  void* buf;
+  TRY(dalloc(c, &buf, (size_t)B * (m->F + 1) * sizeof(float) + 16));
+  float* dX = reinterpret_cast<float*>(buf);
+  float* dY = dX + B * m->F;
+  cudaMemcpyAsync(dX, X, (size_t)B * m->F * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  c->launches++;
+  int st = qtt_mlp_forward_dev(m->Wh, m->P, m->F, dX, B, dY, c->stream);
+  if (!st) st = sync_read(c, y, dY, (size_t)B * sizeof(float));
+  dfree(c, buf);
+  return st;
+}
+
+int qtt_mlp_forward(qtt_mlp* m, const float* X, int64_t B, float* y) {
+  if (!m || !X || !y || B < 0) return QTT_ERR_ARG;
+  if (B == 0) return QTT_OK;
+  return mlp_forward_host(m, X, B, y);
+}
+
+int qtt_mlp_train_step(qtt_mlp* m, const float* X, const float* T, int64_t B, float alpha, float lr, double* loss,
+                       float* grads) {
+  if (!m || !X || !T || B <= 0) return QTT_ERR_ARG;
+  qtt_ctx* c = m->ctx;
+  void* buf;
+  TRY(dalloc(c, &buf, (size_t)B * (m->F + 1) * sizeof(float) + 16));
+  float* dX = reinterpret_cast<float*>(buf);
+  float* dT = dX + B * m->F;
+  cudaMemcpyAsync(dX, X, (size_t)B * m->F * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(dT, T, (size_t)B * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  cudaMemsetAsync(m->G, 0, (size_t)(m->n + 1) * sizeof(float), c->stream);
+  c->launches += 2;
+  int st = qtt_mlp_backward_dev(m->Wh, m->P, m->F, dX, dT, B, alpha, m->G, m->G + m->n, c->stream);
+  float lsum = 0.f;
+  if (!st) st = sync_read(c, &lsum, m->G + m->n, sizeof(float));
+  if (!st && grads) st = sync_read(c, grads, m->G, (size_t)m->n * sizeof(float));
+  if (!st) {
+    m->t += 1;
+    st = qtt_mlp_adam_dev(m->P, m->Wh, m->G, m->M, m->V, m->n, lr, m->t, c->stream);
+  }
+  if (!st) st = cudaStreamSynchronize(c->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+  dfree(c, buf);
+  if (loss) *loss = (double)lsum / (double)B;
+  return st;
+}
+
 }  // extern "C"
 
 // ========================================================= homogenisation
@@ -893,6 +1027,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
 
   const char* stage = "";
   int cur_it = 0, cur_lc = 0;
+  int cur_it_global = 0;
   auto finite_or_fail = [&](const qtt_tt* t, const char* tag) -> int {
     if (!debug_checks()) return QTT_OK;
     int ok = 1;
@@ -904,15 +1039,93 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     }
     return QTT_OK;
   };
-  auto sk_round = [&](int T, const qtt_complex* cf, const qtt_mpo* const* A, const qtt_tt* const* X,
+  // ---- sketch widths: learned per-bond prediction or the full width
+  const int NF = QTT_MLP_FEATURES;
+  std::vector<std::vector<int>> prev(9, std::vector<int>(d + 1, 0));  // last output ranks per step id
+  std::vector<double> side(d + 1, 0.0);  // log2 of the smaller mode product on either side of bond k
+  {
+    double lft = 0;
+    for (int k = 1; k < d; ++k) {
+      lft += log2((double)modes[k - 1]);
+      double rgt = 0;
+      for (int j = k; j < d; ++j) rgt += log2((double)modes[j]);
+      side[k] = std::min(lft, rgt);
+    }
+  }
+  qtt_mlp* pred = const_cast<qtt_mlp*>(o.predictor);
+  if (pred && pred->F != NF) return QTT_ERR_ARG;
+  auto features = [&](int T, const qtt_mpo* const* A, const qtt_tt* const* X, int opid, std::vector<float>& F) {
+    F.assign((size_t)(d - 1) * NF, 0.f);
+    for (int k = 1; k < d; ++k) {
+      double rin = 0;
+      for (int t = 0; t < T; ++t) rin += (double)(A && A[t] ? A[t]->g[k] : 1) * X[t]->r[k];
+      float* f = &F[(size_t)(k - 1) * NF];
+      f[0] = (float)k / d;
+      f[1] = (float)(log2(1.0 + rin) / 10.0);
+      f[2] = (float)(log2(1.0 + prev[opid][k]) / 10.0);
+      f[3] = (float)(log2(1.0 + prev[opid][k - 1]) / 10.0);
+      f[4] = (float)(log2(1.0 + prev[opid][k + 1]) / 10.0);
+      f[5] = (float)(-log10(o.eps > 0 ? o.eps : 1e-16) / 10.0);
+      f[6] = (float)(log2(1.0 + max_rank) / 10.0);
+      f[7] = (float)opid / 8.f;
+      f[8] = (float)std::min(cur_it_global, 20) / 20.f;
+      f[9] = (float)(side[k] / 20.0);
+    }
+  };
+  auto sk_round = [&](int T, const qtt_complex* cf, const qtt_mpo* const* A, const qtt_tt* const* X, int opid,
                       qtt_tt** out) -> int {
-    qtt_tt* S = nullptr;
-    TRY(make_sketch(c, modes, ell, dt, o.seed, call++, &S));
+    std::vector<float> F;
+    features(T, A, X, opid, F);
+    std::vector<int> full(d + 1, ell), w(d + 1, ell);
+    if (pred) {
+      std::vector<float> y(d - 1);
+      TRY(mlp_forward_host(pred, F.data(), d - 1, y.data()));
+      for (int k = 1; k < d; ++k) {
+        double r = exp2((double)std::min(std::max(y[k - 1], 0.f), 20.f));
+        w[k] = std::min(ell, (int)ceil(1.25 * r) + std::max(1, (int)o.oversample));
+      }
+    }
     qtt_round_info info;
-    int s = round_sketched<R>(c, T, cf, A, X, S, o.eps, max_rank, &info, out);
-    tt_free(S);
-    if (!s && rep) rep->max_rank_seen = std::max(rep->max_rank_seen, info.max_rank_out);
-    if (!s) s = finite_or_fail(*out, "sketched rounding");
+    int s = QTT_OK;
+    std::vector<int> width = w;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      qtt_tt* S = nullptr;
+      TRY(make_sketch(c, modes, width, dt, o.seed, call++, &S));
+      if (rep)
+        for (int k = 1; k < d; ++k) rep->sketch_width_sum += S->r[k];
+      s = round_sketched<R>(c, T, cf, A, X, S, o.eps, max_rank, &info, out);
+      std::vector<int> sr = S->r;
+      tt_free(S);
+      if (s) return s;
+      if (!pred || attempt == 1) break;
+      // a bond whose rank reaches its narrowed sketch width may have been cut
+      // by the sketch rather than by the tolerance: widen those bonds to the
+      // full width (mode-product caps apply to both) and redo the rounding
+      bool saturated = false;
+      for (int k = 1; k < d; ++k) {
+        const int cap = (int)std::min<double>(full[k], exp2(side[k]));
+        if (sr[k] < cap && (*out)->r[k] >= sr[k]) {
+          saturated = true;
+          width[k] = full[k];
+        }
+      }
+      if (!saturated) break;
+      if (rep) rep->fallbacks++;
+      tt_free(*out);
+      *out = nullptr;
+    }
+    if (rep) rep->max_rank_seen = std::max(rep->max_rank_seen, info.max_rank_out);
+    // rank trace: (features, log2 output rank) per bond
+    if (o.trace && rep) {
+      for (int k = 1; k < d && rep->trace_len < o.trace_cap; ++k) {
+        float* row = o.trace + rep->trace_len * (NF + 1);
+        for (int j = 0; j < NF; ++j) row[j] = F[(size_t)(k - 1) * NF + j];
+        row[NF] = (float)log2((double)(*out)->r[k]);
+        rep->trace_len++;
+      }
+    }
+    for (int k = 0; k <= d; ++k) prev[opid][k] = (*out)->r[k];
+    s = finite_or_fail(*out, "sketched rounding");
     if (!s && debug_checks())
       fprintf(stderr, "qtt: lc %d it %d %s norm %.3e delta %.3e tail %.3e rank %d\n", cur_lc, cur_it, stage,
               info.norm, info.delta, info.tail, info.max_rank_out);
@@ -932,15 +1145,17 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     double res = 1.0;
     const qtt_complex one = {1.0, 0.0};
     cur_lc = lc;
+    for (auto& v : prev) std::fill(v.begin(), v.end(), 0);
     for (it = 1; it <= o.max_iter; ++it) {
       cur_it = it;
+      cur_it_global = it;
       stage = "tau";
       qtt_tt* tau = nullptr;
       {
         qtt_complex cf[2] = {one, one};
         const qtt_mpo* A[2] = {dCa, dCb};
         const qtt_tt* X[2] = {x, x};
-        TRY(sk_round(2, cf, A, X, &tau));
+        TRY(sk_round(2, cf, A, X, 0, &tau));
       }
       qtt_tt* h = tau;
       static const char* fwd[3] = {"S0", "S1", "S2"};
@@ -950,7 +1165,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {Q[dim]};
         const qtt_tt* X[1] = {h};
-        int s = sk_round(1, &one, A, X, &hn);
+        int s = sk_round(1, &one, A, X, 1 + dim, &hn);
         tt_free(h);
         if (s) return s;
         h = hn;
@@ -960,7 +1175,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {G};
         const qtt_tt* X[1] = {h};
-        int s = sk_round(1, &one, A, X, &hn);
+        int s = sk_round(1, &one, A, X, 4, &hn);
         tt_free(h);
         if (s) return s;
         h = hn;
@@ -970,7 +1185,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {Qi[dim]};
         const qtt_tt* X[1] = {h};
-        int s = sk_round(1, &one, A, X, &hn);
+        int s = sk_round(1, &one, A, X, 7 - dim, &hn);
         tt_free(h);
         if (s) return s;
         h = hn;

@@ -37,6 +37,17 @@ def laminate_indicator(N: int, axis: int = 0, fraction: float = 0.5) -> np.ndarr
     return np.broadcast_to(ind1d.reshape(shape), (N, N, N)).copy()
 
 
+def box_indicator(N: int, volume_fraction: float = 0.2, centre=(0.5, 0.5, 0.5)) -> np.ndarray:
+    """Axis-aligned cubic inclusion of the given volume fraction (the 3D
+    counterpart of the box geometry of the paper's Fig. 4)."""
+    h = 0.5 * volume_fraction ** (1.0 / 3.0)
+    c = voxel_centres(N)
+    inx = (np.abs(c - centre[0]) <= h)[:, None, None]
+    iny = (np.abs(c - centre[1]) <= h)[None, :, None]
+    inz = (np.abs(c - centre[2]) <= h)[None, None, :]
+    return (inx & iny & inz).astype(np.float64)
+
+
 def sphere_radius(volume_fraction: float) -> float:
     """Radius of a sphere of the given volume fraction in the unit cell."""
     return (3.0 * volume_fraction / (4.0 * math.pi)) ** (1.0 / 3.0)

@@ -58,13 +58,18 @@ class RVE(C.Structure):
 class MSOpts(C.Structure):
     _fields_ = [("prec", C.c_int), ("eps", C.c_double), ("op_tol", C.c_double), ("max_iter", C.c_int32),
                 ("oversample", C.c_int32), ("load_mask", C.c_int32), ("min_iter", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("predictor", C.c_void_p), ("trace", C.POINTER(C.c_float)),
+                ("trace_cap", C.c_int64)]
 
 
 class MSReport(C.Structure):
     _fields_ = [("iterations", C.c_int32 * 6), ("residual", C.c_double * 6), ("sigma_imag_max", C.c_double),
                 ("max_rank_seen", C.c_int32), ("setup_ms", C.c_double), ("iterate_ms", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("trace_len", C.c_int64), ("sketch_width_sum", C.c_int64),
+                ("fallbacks", C.c_int32)]
+
+
+MLP_FEATURES = 10
 
 
 _P = C.c_void_p
@@ -114,6 +119,14 @@ _sig("tt_from_dense", C.c_int, [_P, C.c_int, _I32P, _P, C.c_double, C.c_int, C.P
 _sig("qtt_qft_mpo", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(_P)])
 _sig("qtt_mpo_diag", C.c_int, [_P, _P, C.POINTER(_P)])
 _sig("qtt_mpo_convert", C.c_int, [_P, _P, C.c_int, C.POINTER(_P)])
+_sig("qtt_mlp_create", C.c_int, [_P, C.c_int, C.c_uint64, C.POINTER(_P)])
+_sig("qtt_mlp_destroy", None, [_P])
+_sig("qtt_mlp_param_count", C.c_int64, [_P])
+_sig("qtt_mlp_set_params", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64])
+_sig("qtt_mlp_get_params", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64])
+_sig("qtt_mlp_forward", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_float)])
+_sig("qtt_mlp_train_step", C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64, C.c_float,
+                                     C.c_float, C.POINTER(C.c_double), C.POINTER(C.c_float)])
 _sig("ms_homogenize", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
                                 C.POINTER(MSOpts), C.POINTER(C.c_double), C.POINTER(MSReport)])
 
@@ -123,7 +136,9 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_sketched", "tt_dot", "tt_norm",
-            "tt_from_dense", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize"]
+            "tt_from_dense", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
+            "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
+            "qtt_mlp_get_params", "qtt_mlp_forward", "qtt_mlp_train_step"]
 
 
 def _check(st, what):
@@ -387,10 +402,61 @@ def qtt_mpo_convert(ctx: Context, A: MPO, dtype) -> MPO:
     return B
 
 
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class MLP:
+    """The per-bond rank predictor (3 hidden layers of 64, FP16 weights) on the device."""
+
+    def __init__(self, ctx: Context, n_features: int = MLP_FEATURES, seed: int = 0):
+        self.ctx = ctx
+        h = _P()
+        _check(_lib.qtt_mlp_create(ctx.h, int(n_features), int(seed), C.byref(h)), "qtt_mlp_create")
+        self.h = h
+        self.n_features = n_features
+
+    def close(self):
+        if getattr(self, "h", None) and _ALIVE[0]:
+            _lib.qtt_mlp_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def param_count(self) -> int:
+        return int(_lib.qtt_mlp_param_count(self.h))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.param_count, dtype=np.float32)
+        _check(_lib.qtt_mlp_get_params(self.h, _fptr(p), p.size), "qtt_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(_lib.qtt_mlp_set_params(self.h, _fptr(p), p.size), "qtt_mlp_set_params")
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.empty(X.shape[0], dtype=np.float32)
+        _check(_lib.qtt_mlp_forward(self.h, _fptr(X), X.shape[0], _fptr(y)), "qtt_mlp_forward")
+        return y
+
+    def train_step(self, X, t, alpha: float = 4.0, lr: float = 1e-3, want_grads: bool = False):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = C.c_double()
+        g = np.empty(self.param_count, dtype=np.float32) if want_grads else None
+        _check(_lib.qtt_mlp_train_step(self.h, _fptr(X), _fptr(t), X.shape[0], float(alpha), float(lr),
+                                       C.byref(loss), _fptr(g) if g is not None else None), "qtt_mlp_train_step")
+        return (loss.value, g) if want_grads else loss.value
+
+
 def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, tol: float, max_rank: int,
                   eps: float = 1e-6, op_tol: float = 1e-10, prec: int = PREC_F64, max_iter: int = 100,
                   oversample: int = 8, load_mask: int | None = None, interleaved: bool = True,
-                  min_iter: int = 1, seed: int = 12345):
+                  min_iter: int = 1, seed: int = 12345, predictor: "MLP | None" = None, trace_cap: int = 0):
     """Effective tensor of a two-phase RVE (phase 2 where indicator == 1).
 
     kind "scalar": moduli = (k1, k2), C0 = 3x3; kind "elastic": moduli =
@@ -420,9 +486,15 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
     o.load_mask = int(load_mask if load_mask is not None else (1 << nc) - 1)
     o.min_iter = int(min_iter)
     o.seed = int(seed)
+    o.predictor = predictor.h if predictor is not None else None
+    trace = np.zeros((max(trace_cap, 1), MLP_FEATURES + 1), dtype=np.float32)
+    o.trace = _fptr(trace) if trace_cap > 0 else None
+    o.trace_cap = int(trace_cap)
     out = np.zeros((nc, nc), dtype=np.float64)
     rep = MSReport()
     _check(_lib.ms_homogenize(ctx.h, C.byref(rve), C0a.ctypes.data_as(C.POINTER(C.c_double)), float(tol),
                               int(max_rank), C.byref(o), out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep)),
            "ms_homogenize")
+    if trace_cap > 0:
+        rep.trace_rows = trace[:rep.trace_len].copy()
     return out, rep

@@ -1,0 +1,114 @@
+"""The rank predictor's device kernels against the FP64 oracle network, and
+what the trained predictor gains over the fixed-width sketched rounding."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from oracle import ms as MS
+from paper_2512_07811_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2512_07811_gb300 import qtt
+    return qtt
+
+
+@pytest.fixture(scope="module")
+def ctx(Q):
+    return Q.Context(0)
+
+
+def to_oracle(p, F):
+    """Packed device parameters -> oracle layers, with the weights rounded to
+    FP16 exactly as the device kernels read them (biases stay FP32)."""
+    sizes = [F, 64, 64, 64, 1]
+    out, off = [], 0
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        W = p[off:off + a * b].reshape(b, a).astype(np.float16).astype(np.float64)
+        off += a * b
+        bias = p[off:off + b].astype(np.float64)
+        off += b
+        out.append([W, bias])
+    return out
+
+
+def pack(grads):
+    return np.concatenate([np.concatenate([g[0].reshape(-1), g[1].reshape(-1)]) for g in grads])
+
+
+def test_forward_and_gradients_match_oracle(Q, ctx):
+    F = Q.MLP_FEATURES
+    net = Q.MLP(ctx, F, seed=3)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((300, F)).astype(np.float32)
+    t = (rng.standard_normal(300) * 2 + 3).astype(np.float32)
+    p = net.get_params()
+    params = to_oracle(p, F)
+    y_ref, cache = M.forward(params, X.astype(np.float64))
+    y = net.forward(X)
+    np.testing.assert_allclose(y, y_ref, rtol=2e-5, atol=2e-5 * np.abs(y_ref).max())
+    loss, g = net.train_step(X, t, alpha=4.0, lr=1e-3, want_grads=True)
+    g_ref = pack(M.backward(params, cache, y_ref, t.astype(np.float64), 4.0))
+    assert abs(loss - M.loss(y_ref, t.astype(np.float64), 4.0)) < 1e-4 * max(1.0, loss)
+    scale = np.abs(g_ref).max()
+    np.testing.assert_allclose(g, g_ref, rtol=0, atol=2e-4 * scale)
+    # the Adam update of the master weights equals the oracle's with the device gradient
+    state = {}
+    ref_layers = [[lay[0].copy(), lay[1].copy()] for lay in to_oracle(p, F)]
+    # oracle Adam acts on the FP32 master values, not the FP16-rounded weights
+    master = []
+    off = 0
+    for a, b in zip([F, 64, 64, 64], [64, 64, 64, 1]):
+        master.append([p[off:off + a * b].reshape(b, a).astype(np.float64), p[off + a * b:off + a * b + b].astype(np.float64)])
+        off += a * b + b
+    gl, off = [], 0
+    for a, b in zip([F, 64, 64, 64], [64, 64, 64, 1]):
+        gl.append([g[off:off + a * b].reshape(b, a).astype(np.float64), g[off + a * b:off + a * b + b].astype(np.float64)])
+        off += a * b + b
+    M.adam_step(master, gl, state, lr=1e-3)
+    np.testing.assert_allclose(net.get_params(), pack(master), rtol=0, atol=2e-6)
+    del ref_layers
+
+
+def test_training_reduces_loss(Q, ctx):
+    F = Q.MLP_FEATURES
+    net = Q.MLP(ctx, F, seed=5)
+    rng = np.random.default_rng(6)
+    X = rng.uniform(0, 1, size=(2000, F)).astype(np.float32)
+    t = (3.0 * X[:, 1] + 2.0 * X[:, 2] - X[:, 7] + 2.0).astype(np.float32)
+    from paper_2512_07811_gb300 import predictor as P
+    hist = P.train(net, X, t, epochs=60, batch=256, lr=3e-3)
+    assert hist[-1] < 0.05 * hist[0]
+
+
+def test_predictor_gain_over_fixed_width(Q, ctx):
+    """Trained on the rank traces of 8^3 and 16^3 solves, the predictor sizes
+    the sketches of the 32^3 laminate (config 1 shape, ranks far below the
+    cap, where the fixed width max_rank + oversample is wasted): much less
+    sketch width, less time, the same effective conductivity (the exact
+    20/11 to 1e-5 in FP32)."""
+    from paper_2512_07811_gb300 import predictor as P
+    common = dict(kind="scalar", moduli=(1.0, 10.0), max_rank=64, max_iter=4, min_iter=4, tol=0.0,
+                  prec=Q.PREC_F32, load_mask=1)
+    train = []
+    for ind in [I.laminate_indicator(8), I.laminate_indicator(16), I.box_indicator(8, 0.2)]:
+        pb = MS.scalar_problem(ind, 1.0, 10.0)
+        for eps in [1e-6, 1e-4]:
+            train.append(dict(indicator=pb.indicator, C0=pb.C0, eps=eps, **common))
+    X, t = P.collect_traces(ctx, train)
+    assert X.shape[0] > 500
+    net = Q.MLP(ctx, Q.MLP_FEATURES, seed=7)
+    P.train(net, X, t, epochs=150, batch=512, lr=3e-3, alpha=4.0)
+    test_pb = MS.scalar_problem(I.laminate_indicator(32), 1.0, 10.0)
+    C_full, rep_full = Q.ms_homogenize(ctx, test_pb.indicator, C0=test_pb.C0, eps=1e-6, **common)
+    C_pred, rep_pred = Q.ms_homogenize(ctx, test_pb.indicator, C0=test_pb.C0, eps=1e-6, predictor=net, **common)
+    print("\nlaminate 32^3: widths full %d predicted %d, fallbacks %d, iterate ms %.1f vs %.1f, C %.8f %.8f"
+          % (rep_full.sketch_width_sum, rep_pred.sketch_width_sum, rep_pred.fallbacks, rep_full.iterate_ms,
+             rep_pred.iterate_ms, C_full[0, 0], C_pred[0, 0]))
+    assert rep_pred.sketch_width_sum < 0.3 * rep_full.sketch_width_sum
+    assert rep_pred.iterate_ms < 0.7 * rep_full.iterate_ms
+    assert abs(C_pred[0, 0] - 20.0 / 11.0) < 1e-5 * 20.0 / 11.0
+    assert abs(C_full[0, 0] - 20.0 / 11.0) < 1e-5 * 20.0 / 11.0
