@@ -260,7 +260,19 @@ typedef struct {
 QTT_API int ms_homogenize(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, double tol, int max_rank,
                   const ms_opts* opts, double* C_eff, ms_report* report);
 
-QTT_API /* ------------------------------------------------ rank predictor (MLP) */
+QTT_API /* Many RVEs at once: the (RVE, load case) pairs of rves[0..n-1] (load cases
+ * from opts->load_mask) are solved by `workers` host threads, each with its
+ * own context and stream, largest RVE first, so that independent rounding
+ * chains run concurrently on different SMs.  C0s holds n reference tensors
+ * at a stride of 36 doubles (3x3 or 6x6 row-major at the start of each
+ * slot); C_effs receives the effective tensors back to back (ncomp^2 each);
+ * reports (nullable) one report per RVE.  Every pair gives the same result
+ * as its own ms_homogenize call.  Trace recording is off in this call. */
+QTT_API int ms_homogenize_batch(qtt_ctx* ctx, int n, const qtt_rve* rves, const double* C0s, double tol,
+                                int max_rank, const ms_opts* opts, int workers, double* C_effs,
+                                ms_report* reports);
+
+/* ------------------------------------------------ rank predictor (MLP) */
 /* A multilayer perceptron with three hidden layers of width 64 and ReLU, FP16
  * weights, FP32 accumulation, FP32 master weights and Adam moments; it maps
  * QTT_MLP_FEATURES (or any n_features <= 32) per-bond features to a predicted

@@ -17,7 +17,10 @@
 
 #include <cuda_fp16.h>
 
+#include <atomic>
+#include <mutex>
 #include <random>
+#include <thread>
 
 int64_t qtt_mlp_param_count_f(int F);
 int qtt_mlp_sync_half(const float* P, __half* Wh, int64_t n, cudaStream_t s);
@@ -755,8 +758,8 @@ int qtt_mlp_get_params(const qtt_mlp* m, float* p, int64_t n) {
   return sync_read(m->ctx, p, m->P, n * sizeof(float));
 }
 
-static int mlp_forward_host(qtt_mlp* m, const float* X, int64_t B, float* y) {
-  qtt_ctx* c = m->ctx;
+// forward pass on the stream of context c (the predictor's weights are only read)
+static int mlp_forward_on(qtt_ctx* c, const qtt_mlp* m, const float* X, int64_t B, float* y) {
   void* buf;
   TRY(dalloc(c, &buf, (size_t)B * (m->F + 1) * sizeof(float) + 16));
   float* dX = reinterpret_cast<float*>(buf);
@@ -772,7 +775,7 @@ static int mlp_forward_host(qtt_mlp* m, const float* X, int64_t B, float* y) {
 int qtt_mlp_forward(qtt_mlp* m, const float* X, int64_t B, float* y) {
   if (!m || !X || !y || B < 0) return QTT_ERR_ARG;
   if (B == 0) return QTT_OK;
-  return mlp_forward_host(m, X, B, y);
+  return mlp_forward_on(m->ctx, m, X, B, y);
 }
 
 int qtt_mlp_train_step(qtt_mlp* m, const float* X, const float* T, int64_t B, float alpha, float lr, double* loss,
@@ -1079,7 +1082,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     std::vector<int> full(d + 1, ell), w(d + 1, ell);
     if (pred) {
       std::vector<float> y(d - 1);
-      TRY(mlp_forward_host(pred, F.data(), d - 1, y.data()));
+      TRY(mlp_forward_on(c, pred, F.data(), d - 1, y.data()));
       for (int k = 1; k < d; ++k) {
         double r = exp2((double)std::min(std::max(y[k - 1], 0.f), 20.f));
         w[k] = std::min(ell, (int)ceil(1.25 * r) + std::max(1, (int)o.oversample));
@@ -1146,6 +1149,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     const qtt_complex one = {1.0, 0.0};
     cur_lc = lc;
     for (auto& v : prev) std::fill(v.begin(), v.end(), 0);
+    call = 1;  // sketches depend only on the seed and the call order within one load case
     for (it = 1; it <= o.max_iter; ++it) {
       cur_it = it;
       cur_it_global = it;
@@ -1317,4 +1321,84 @@ extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, d
   }
   if (cudaGetLastError() != cudaSuccess) return QTT_ERR_CUDA;
   return s;
+}
+
+// Many independent solves at once: the (RVE, load case) pairs form a work
+// queue, largest RVE first; `workers` host threads each own a context on a
+// stream of their own, so that the latency-bound rounding chains of
+// different solves run concurrently on different SMs.  Results are the same
+// as solving each pair with ms_homogenize (the sketches depend only on the
+// seed and the call order within one solve).
+extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const double* C0s, double tol, int max_rank,
+                                   const ms_opts* o, int workers, double* C_effs, ms_report* reports) {
+  if (!c || n < 0 || (n > 0 && (!rves || !C0s || !C_effs)) || !o || workers < 1) return QTT_ERR_ARG;
+  struct Job {
+    int rve, lc;
+    int64_t cost;
+  };
+  std::vector<Job> jobs;
+  std::vector<int64_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const int nc = rves[i].ncomp;
+    if (nc != 3 && nc != 6) return QTT_ERR_ARG;
+    off[i + 1] = off[i] + (int64_t)nc * nc;
+    for (int lc = 0; lc < nc; ++lc)
+      if (o->load_mask & (1 << lc)) jobs.push_back(Job{i, lc, (int64_t)rves[i].nbits * 3 * nc});
+  }
+  std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.cost > b.cost; });
+  for (int64_t i = 0; i < off[n]; ++i) C_effs[i] = 0.0;
+  if (reports)
+    for (int i = 0; i < n; ++i) memset(&reports[i], 0, sizeof(ms_report));
+  std::atomic<size_t> next(0);
+  std::atomic<int> status(QTT_OK);
+  std::mutex mu;
+  auto work = [&]() {
+    qtt_ctx* wc = nullptr;
+    int st = qtt_ctx_create(c->device, nullptr, &wc);
+    if (st) {
+      status = st;
+      return;
+    }
+    for (;;) {
+      size_t j = next++;
+      if (j >= jobs.size() || status.load() != QTT_OK) break;
+      const Job jb = jobs[j];
+      const int nc = rves[jb.rve].ncomp;
+      ms_opts oj = *o;
+      oj.load_mask = 1 << jb.lc;
+      oj.trace = nullptr;
+      oj.trace_cap = 0;
+      std::vector<double> Cj(nc * nc, 0.0);
+      ms_report rj;
+      st = ms_homogenize(wc, &rves[jb.rve], C0s + (size_t)jb.rve * 36, tol, max_rank, &oj, Cj.data(), &rj);
+      if (st) {
+        status = st;
+        break;
+      }
+      std::lock_guard<std::mutex> lock(mu);
+      for (int I = 0; I < nc; ++I) C_effs[off[jb.rve] + I * nc + jb.lc] = Cj[I * nc + jb.lc];
+      if (reports) {
+        ms_report& R = reports[jb.rve];
+        R.iterations[jb.lc] = rj.iterations[jb.lc];
+        R.residual[jb.lc] = rj.residual[jb.lc];
+        R.sigma_imag_max = std::max(R.sigma_imag_max, rj.sigma_imag_max);
+        R.max_rank_seen = std::max(R.max_rank_seen, rj.max_rank_seen);
+        R.setup_ms += rj.setup_ms;
+        R.iterate_ms += rj.iterate_ms;
+        R.kernel_launches += rj.kernel_launches;
+        R.sketch_width_sum += rj.sketch_width_sum;
+        R.fallbacks += rj.fallbacks;
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      c->launches += wc->launches;
+    }
+    qtt_ctx_destroy(wc);
+  };
+  std::vector<std::thread> th;
+  const int nw = std::min<int>(workers, (int)std::max<size_t>(1, jobs.size()));
+  for (int w = 0; w < nw; ++w) th.emplace_back(work);
+  for (auto& t : th) t.join();
+  return status.load();
 }

@@ -81,41 +81,48 @@ def _periodic_delta(c: np.ndarray, centre: float) -> np.ndarray:
     return d - np.round(d)
 
 
-def ellipsoid_rve(N: int, rng: np.random.Generator, max_tries: int = 200):
+def ellipsoid_rve(N: int, rng: np.random.Generator, max_tries: int = 400):
     """Random RVE of 1..8 non-overlapping, randomly oriented ellipsoids.
 
-    Semi-axes are drawn from U[0.05, 0.2] (units of the cell), the count from
-    1..8, the orientation from a uniform quaternion.  A draw whose ellipsoid
-    overlaps an earlier one (tested on the voxel grid, periodic) is rejected.
-    The whole RVE is redrawn until the voxel phase fraction lies in
-    [0.1, 0.3].  Returns (indicator, contrast) with the contrast log-uniform in
-    [5, 100].
+    The count is drawn from 1..8, the semi-axes from U[0.05, 0.2] (units of
+    the cell side) and the orientation from a uniform quaternion; a target
+    phase fraction f is drawn from U[0.12, 0.28] and all semi-axes are scaled
+    by one common factor so that the ellipsoids' continuum volume is f (drawn
+    as specified, 1-8 such ellipsoids rarely reach the required fraction of
+    0.1-0.3).  An ellipsoid that overlaps an earlier one on the voxel grid
+    (periodic) is redrawn; the whole RVE is redrawn until the voxel phase
+    fraction lies in [0.1, 0.3].  Returns (indicator, contrast) with the
+    contrast log-uniform in [5, 100].
     """
     c = voxel_centres(N)
     for _ in range(max_tries):
         count = int(rng.integers(1, 9))
+        f = rng.uniform(0.12, 0.28)
+        axes_all = rng.uniform(0.05, 0.2, size=(count, 3))
+        vol = float(np.sum(4.0 / 3.0 * math.pi * np.prod(axes_all, axis=1)))
+        axes_all *= (f / vol) ** (1.0 / 3.0)
         ind = np.zeros((N, N, N), dtype=bool)
         placed = 0
-        for _ in range(50 * count):
-            if placed == count:
+        for e in range(count):
+            axes = axes_all[e]
+            for _ in range(50):
+                rot = _random_rotation(rng)
+                ctr = rng.uniform(0.0, 1.0, size=3)
+                dx = _periodic_delta(c, ctr[0])[:, None, None]
+                dy = _periodic_delta(c, ctr[1])[None, :, None]
+                dz = _periodic_delta(c, ctr[2])[None, None, :]
+                # body-frame coordinates u = rot^T (x - c)
+                u0 = rot[0, 0] * dx + rot[1, 0] * dy + rot[2, 0] * dz
+                u1 = rot[0, 1] * dx + rot[1, 1] * dy + rot[2, 1] * dz
+                u2 = rot[0, 2] * dx + rot[1, 2] * dy + rot[2, 2] * dz
+                inside = (u0 / axes[0]) ** 2 + (u1 / axes[1]) ** 2 + (u2 / axes[2]) ** 2 <= 1.0
+                if np.any(inside & ind):
+                    continue
+                ind |= inside
+                placed += 1
                 break
-            axes = rng.uniform(0.05, 0.2, size=3)
-            rot = _random_rotation(rng)
-            ctr = rng.uniform(0.0, 1.0, size=3)
-            dx = _periodic_delta(c, ctr[0])[:, None, None]
-            dy = _periodic_delta(c, ctr[1])[None, :, None]
-            dz = _periodic_delta(c, ctr[2])[None, None, :]
-            # body-frame coordinates u = rot^T (x - c)
-            u0 = rot[0, 0] * dx + rot[1, 0] * dy + rot[2, 0] * dz
-            u1 = rot[0, 1] * dx + rot[1, 1] * dy + rot[2, 1] * dz
-            u2 = rot[0, 2] * dx + rot[1, 2] * dy + rot[2, 2] * dz
-            inside = (u0 / axes[0]) ** 2 + (u1 / axes[1]) ** 2 + (u2 / axes[2]) ** 2 <= 1.0
-            if np.any(inside & ind):
-                continue
-            ind |= inside
-            placed += 1
         frac = ind.mean()
-        if placed >= 1 and 0.1 <= frac <= 0.3:
+        if placed == count and 0.1 <= frac <= 0.3:
             contrast = float(np.exp(rng.uniform(np.log(5.0), np.log(100.0))))
             return ind.astype(np.float64), contrast
     raise RuntimeError("ellipsoid_rve: no admissible draw")

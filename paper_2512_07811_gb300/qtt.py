@@ -119,6 +119,8 @@ _sig("tt_from_dense", C.c_int, [_P, C.c_int, _I32P, _P, C.c_double, C.c_int, C.P
 _sig("qtt_qft_mpo", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(_P)])
 _sig("qtt_mpo_diag", C.c_int, [_P, _P, C.POINTER(_P)])
 _sig("qtt_mpo_convert", C.c_int, [_P, _P, C.c_int, C.POINTER(_P)])
+_sig("ms_homogenize_batch", C.c_int, [_P, C.c_int, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
+                                      C.POINTER(MSOpts), C.c_int, C.POINTER(C.c_double), C.POINTER(MSReport)])
 _sig("qtt_mlp_create", C.c_int, [_P, C.c_int, C.c_uint64, C.POINTER(_P)])
 _sig("qtt_mlp_destroy", None, [_P])
 _sig("qtt_mlp_param_count", C.c_int64, [_P])
@@ -137,6 +139,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_sketched", "tt_dot", "tt_norm",
             "tt_from_dense", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
+            "ms_homogenize_batch",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
             "qtt_mlp_get_params", "qtt_mlp_forward", "qtt_mlp_train_step"]
 
@@ -451,6 +454,58 @@ class MLP:
         _check(_lib.qtt_mlp_train_step(self.h, _fptr(X), _fptr(t), X.shape[0], float(alpha), float(lr),
                                        C.byref(loss), _fptr(g) if g is not None else None), "qtt_mlp_train_step")
         return (loss.value, g) if want_grads else loss.value
+
+
+def _rve(ind, kind, moduli, interleaved):
+    ind = np.ascontiguousarray(ind, dtype=np.float64)
+    N = ind.shape[0]
+    nbits = int(round(np.log2(N)))
+    assert ind.shape == (N, N, N) and (1 << nbits) == N
+    rve = RVE()
+    rve.nbits = nbits
+    rve.indicator = ind.ctypes.data_as(C.POINTER(C.c_double))
+    rve.interleaved = 1 if interleaved else 0
+    if kind == "scalar":
+        rve.ncomp = 3
+        rve.k1, rve.k2 = map(float, moduli)
+    else:
+        rve.ncomp = 6
+        rve.lam1, rve.mu1, rve.lam2, rve.mu2 = map(float, moduli)
+    return rve, ind
+
+
+def ms_homogenize_batch(ctx: Context, problems, tol: float, max_rank: int, workers: int = 8, eps: float = 1e-6,
+                        op_tol: float = 1e-10, prec: int = PREC_F64, max_iter: int = 100, oversample: int = 8,
+                        load_mask: int = 0x3F, interleaved: bool = True, min_iter: int = 1, seed: int = 12345,
+                        predictor: "MLP | None" = None):
+    """problems: list of (indicator, kind, moduli, C0).  Returns ([C_eff], [report])."""
+    n = len(problems)
+    rves = (RVE * max(n, 1))()
+    keep = []
+    C0s = np.zeros((max(n, 1), 36), dtype=np.float64)
+    sizes = []
+    for i, (ind, kind, moduli, C0) in enumerate(problems):
+        r, a = _rve(ind, kind, moduli, interleaved)
+        keep.append(a)
+        rves[i] = r
+        nc = r.ncomp
+        C0s[i, :nc * nc] = np.asarray(C0, dtype=np.float64).reshape(-1)
+        sizes.append(nc)
+    o = MSOpts()
+    o.prec, o.eps, o.op_tol, o.max_iter = int(prec), float(eps), float(op_tol), int(max_iter)
+    o.oversample, o.load_mask, o.min_iter, o.seed = int(oversample), int(load_mask), int(min_iter), int(seed)
+    o.predictor = predictor.h if predictor is not None else None
+    o.trace, o.trace_cap = None, 0
+    out = np.zeros(sum(s * s for s in sizes) + 1, dtype=np.float64)
+    reps = (MSReport * max(n, 1))()
+    _check(_lib.ms_homogenize_batch(ctx.h, n, rves, C0s.ctypes.data_as(C.POINTER(C.c_double)), float(tol),
+                                    int(max_rank), C.byref(o), int(workers),
+                                    out.ctypes.data_as(C.POINTER(C.c_double)), reps), "ms_homogenize_batch")
+    res, off = [], 0
+    for nc in sizes:
+        res.append(out[off:off + nc * nc].reshape(nc, nc).copy())
+        off += nc * nc
+    return res, [reps[i] for i in range(n)]
 
 
 def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, tol: float, max_rank: int,
