@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--rank", type=int, default=64)
     p.add_argument("--no-ms", action="store_true")
     p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--prec", choices=["f32", "tc32"], default="f32",
+                   help="fast path arithmetic: float CUDA cores, or tensor cores for the large contractions")
     return p.parse_args()
 
 
@@ -128,8 +130,9 @@ class ClockSampler:
 class Step:
     """Device-resident inputs and one pass of the workload on one context."""
 
-    def __init__(self, Q, ctx, r, dtype, qft_c128):
+    def __init__(self, Q, ctx, r, dtype, qft_c128, prec=None):
         self.Q, self.ctx, self.r, self.dtype = Q, ctx, r, dtype
+        self.prec = prec
         self.xc = I.random_tt_cores(D, 2, r, seed=1000 + r, dtype=np.complex128)
         self.yc = I.random_tt_cores(D, 2, r, seed=1001 + r, dtype=np.complex128)
         rng = np.random.default_rng(2000 + r)
@@ -147,9 +150,9 @@ class Step:
         Y = Y or self.Y
         DX = self.DX if X is self.X else Q.qtt_mpo_diag(ctx, X)
         z = Q.tt_add(ctx, 1.0, X, 1.0, Y)
-        zr, _ = Q.tt_round(ctx, z, EPS)
-        h, _ = Q.tt_round_sketched(ctx, [(1.0, DX, Y)], self.S, EPS, r)
-        q, _ = Q.tt_round_sketched(ctx, [(1.0, self.F, X)], self.S, EPS, r)
+        zr, _ = Q.tt_round(ctx, z, EPS, prec=self.prec)
+        h, _ = Q.tt_round_sketched(ctx, [(1.0, DX, Y)], self.S, EPS, r, prec=self.prec)
+        q, _ = Q.tt_round_sketched(ctx, [(1.0, self.F, X)], self.S, EPS, r, prec=self.prec)
         v = Q.tt_dot(ctx, X, Y)
         flops = (round_flops(self.modes, z.ranks, zr.ranks)
                  + round_flops(self.modes, self.sk_ranks, h.ranks)
@@ -190,7 +193,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     r = args.rank
     qft = Q.qtt_qft_mpo(ctx, D, -1, 1e-12)
-    fast = Step(Q, ctx, r, Q.C64, qft)
+    fast = Step(Q, ctx, r, Q.C64, qft, Q.PREC_TC32 if args.prec == "tc32" else Q.PREC_F32)
     for _ in range(args.warmup):
         fast.run()
     ctx.sync()
@@ -239,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_flops += f
 
     # FP64 path, same step in complex128
-    slow = Step(Q, ctx, r, Q.C128, qft)
+    slow = Step(Q, ctx, r, Q.C128, qft, Q.PREC_F64)
     slow.run()
     ctx.sync()
     ms64, flops64 = time_steps(torch, stream, slow, args.fp64_steps, flush)
@@ -359,7 +362,7 @@ def main():
     line = {
         "metric": metric, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "fast_path_arithmetic": args.prec, "data": "synthetic",
         "config": config_dict(args, world),
         "roofline": roof,
         "kernel_classes": {k: {"ms": v["ms"], "launches": v["launches"], "model_flops": v["flops"]}

@@ -64,8 +64,11 @@ typedef enum { QTT_C128 = 0, QTT_C64 = 1 } qtt_dtype;
 /* Arithmetic used inside an operation.  QTT_PREC_F64 needs QTT_C128 storage
  * and computes everything in double.  QTT_PREC_F32 (QTT_C64 storage) runs the
  * core contractions and the small factorisations in float, norms, rounding
- * thresholds and residuals in double. */
-typedef enum { QTT_PREC_F64 = 0, QTT_PREC_F32 = 1 } qtt_prec;
+ * thresholds and residuals in double.  QTT_PREC_TC32 (QTT_C64 storage) is
+ * QTT_PREC_F32 with the larger core contractions on the tensor cores
+ * (tcgen05.mma kind::tf32, three-term TF32 split, FP32 accumulation in
+ * tensor memory): about 1e-5 relative per contraction at K ~ 10^3. */
+typedef enum { QTT_PREC_F64 = 0, QTT_PREC_F32 = 1, QTT_PREC_TC32 = 2 } qtt_prec;
 
 typedef struct {
   double re, im;
@@ -189,6 +192,14 @@ QTT_API int tt_from_dense(qtt_ctx* ctx, int ncores, const int32_t* modes, const 
  * circuit's layers (Hadamard, then the controlled phases of one qubit),
  * rounded after every layer. */
 QTT_API int qtt_qft_mpo(qtt_ctx* ctx, int nbits, int sign, double tol, qtt_mpo** out);
+
+/* C = A B for row-major complex64 device matrices A (M x K), B (K x N),
+ * C (M x N): engine 0 on the CUDA cores (float FMA), engine 1 on the tensor
+ * cores (tcgen05.mma kind::tf32 with the three-term TF32 split, which keeps
+ * FP32-level accuracy).  The same routines serve every core contraction of
+ * the float path.  QTT_ERR_TIMEOUT if a bounded device wait gave up. */
+QTT_API int qtt_cgemm(qtt_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, const void* B, void* C,
+                      int engine);
 
 /* The train x lifted to the operator D(i, j) = x(i) delta(i, j) (Sec. 2.1,
  * Eq. tt_to_tto): applying it is the Hadamard product with x, which lets

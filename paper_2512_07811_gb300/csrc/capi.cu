@@ -199,7 +199,7 @@ bool debug_checks() {
 
 int check_prec(qtt_dtype dt, qtt_prec p) {
   if (dt == QTT_C128 && p == QTT_PREC_F64) return QTT_OK;
-  if (dt == QTT_C64 && p == QTT_PREC_F32) return QTT_OK;
+  if (dt == QTT_C64 && (p == QTT_PREC_F32 || p == QTT_PREC_TC32)) return QTT_OK;
   return QTT_ERR_ARG;
 }
 
@@ -340,6 +340,7 @@ void qtt_ctx_destroy(qtt_ctx* c) {
   cudaStreamSynchronize(c->stream);
   prof_clear(c);
   if (c->d_sweeps) cudaFree(c->d_sweeps);
+  if (c->d_tcerr) cudaFree(c->d_tcerr);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -507,6 +508,7 @@ int tt_mpo_apply(qtt_ctx* c, const qtt_mpo* A, const qtt_tt* x, qtt_tt** y) {
 int tt_round(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, qtt_prec p, qtt_round_info* info, qtt_tt** y) {
   if (!c || !valid_tt(x) || !y || !(eps >= 0)) return QTT_ERR_ARG;
   TRY(check_prec(x->dtype, p));
+  TcScope tc(c, p == QTT_PREC_TC32);
   return x->dtype == QTT_C128 ? round_det<double>(c, x, eps, max_rank, nullptr, info, y)
                               : round_det<float>(c, x, eps, max_rank, nullptr, info, y);
 }
@@ -520,6 +522,7 @@ int tt_round_sketched(qtt_ctx* c, int nterms, const qtt_complex* coef, const qtt
     if (ops && ops[t] && ops[t]->dtype != sketch->dtype) return QTT_ERR_ARG;
   }
   TRY(check_prec(sketch->dtype, p));
+  TcScope tc(c, p == QTT_PREC_TC32);
   return sketch->dtype == QTT_C128
              ? round_sketched<double>(c, nterms, coef, ops, xs, sketch, eps, max_rank, info, y)
              : round_sketched<float>(c, nterms, coef, ops, xs, sketch, eps, max_rank, info, y);
@@ -666,6 +669,42 @@ int qtt_qft_mpo(qtt_ctx* c, int nbits, int sign, double tol, qtt_mpo** out) {
   if (!c || nbits < 1 || nbits > 62 || (sign != 1 && sign != -1) || !out || !(tol >= 0)) return QTT_ERR_ARG;
   if (nbits <= 12) return qft_dense_route(c, nbits, sign, tol, out);
   return qft_layer_route(c, nbits, sign, tol, out);
+}
+
+int qtt_cgemm(qtt_ctx* c, int64_t M, int64_t N, int64_t K, const void* A, const void* B, void* C, int engine) {
+  if (!c || M < 1 || N < 1 || K < 1 || !A || !B || !C || (engine != 0 && engine != 1)) return QTT_ERR_ARG;
+  GemmDesc g;
+  g.bA = g.bB = g.bC = MIdx{1, 1, 0, 0};
+  g.mA = MIdx{M, 1, K, 0};
+  g.kA = MIdx{K, 1, 1, 0};
+  g.kB = MIdx{K, 1, N, 0};
+  g.nB = MIdx{N, 1, 1, 0};
+  g.mC = MIdx{M, 1, N, 0};
+  g.nC = MIdx{N, 1, 1, 0};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = 1;
+  g.conjA = g.conjB = 0;
+  const cc one(1.f, 0.f), zero(0.f, 0.f);
+  if (engine == 0) {
+    c->launches++;
+    TRY(qtt_gemm<float>(g, one, zero, reinterpret_cast<const cc*>(A), reinterpret_cast<const cc*>(B),
+                        reinterpret_cast<cc*>(C), c->stream));
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+  }
+  void* ws = nullptr;
+  TRY(dalloc(c, &ws, qtt_tc_gemm_workspace(M, N, K) + 256));
+  int* err = reinterpret_cast<int*>(static_cast<char*>(ws) + qtt_tc_gemm_workspace(M, N, K));
+  cudaMemsetAsync(err, 0, sizeof(int), c->stream);
+  c->launches += 4;
+  int st = qtt_tc_gemm(g, one, zero, reinterpret_cast<const cc*>(A), reinterpret_cast<const cc*>(B),
+                       reinterpret_cast<cc*>(C), ws, err, c->stream);
+  int h = 0;
+  if (!st) st = sync_read(c, &h, err, sizeof(int));
+  dfree(c, ws);
+  if (!st && h) st = QTT_ERR_TIMEOUT;
+  return st;
 }
 
 int qtt_mpo_diag(qtt_ctx* c, const qtt_tt* x, qtt_mpo** out) {
@@ -1272,7 +1311,7 @@ extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, d
   if (!c || !rve || !C0 || !o || !C_eff || max_rank < 1) return QTT_ERR_ARG;
   if ((rve->ncomp != 3 && rve->ncomp != 6) || rve->nbits < 1 || rve->nbits > 10 || !rve->indicator)
     return QTT_ERR_ARG;
-  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32) return QTT_ERR_ARG;
+  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32) return QTT_ERR_ARG;
   const int nc = rve->ncomp;
   std::vector<double> C1(nc * nc, 0.0), C2(nc * nc, 0.0);
   double k0 = 0, lam0 = 0, mu0 = 0;
@@ -1307,10 +1346,17 @@ extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, d
   }
   cudaStreamSynchronize(c->stream);
   auto t1 = std::chrono::steady_clock::now();
-  if (o->prec == QTT_PREC_F64)
+  if (o->prec == QTT_PREC_F64) {
     s = ms_solve<double>(c, rve, C1.data(), C2.data(), O, tol, max_rank, *o, QTT_C128, C_eff, rep);
-  else
+  } else {
+    TcScope tc(c, o->prec == QTT_PREC_TC32);
     s = ms_solve<float>(c, rve, C1.data(), C2.data(), O, tol, max_rank, *o, QTT_C64, C_eff, rep);
+  }
+  if (!s && c->d_tcerr) {
+    int h = 0;
+    sync_read(c, &h, c->d_tcerr, sizeof(int));
+    if (h) s = QTT_ERR_TIMEOUT;
+  }
   cudaStreamSynchronize(c->stream);
   auto t2 = std::chrono::steady_clock::now();
   O.release();

@@ -114,6 +114,32 @@ static inline MIdx L1(int64_t n, int64_t s) { return MIdx{n, 1, s, 0}; }
 static inline MIdx L2(int64_t n1, int64_t s1, int64_t n2, int64_t s2) { return MIdx{n1, n2, s1, s2}; }
 static inline MIdx B0() { return MIdx{1, 1, 0, 0}; }
 
+// Tensor-core route for one float contraction (batch handled by a loop);
+// returns QTT_ERR_UNSUPPORTED when the contraction is too small to pay for
+// the packing, so that the caller falls back to the CUDA-core kernel.
+static int tc_route(qtt_ctx* c, const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C) {
+  if (!c->tc || g.M < 64 || g.N < 16 || g.K < 32 || (double)g.M * g.N * g.K < 2.0e5) return QTT_ERR_UNSUPPORTED;
+  if (!c->d_tcerr) {
+    if (cudaMalloc(&c->d_tcerr, sizeof(int)) != cudaSuccess) return QTT_ERR_OOM;
+    cudaMemsetAsync(c->d_tcerr, 0, sizeof(int), c->stream);
+  }
+  void* ws = nullptr;
+  if (dalloc(c, &ws, qtt_tc_gemm_workspace(g.M, g.N, g.K))) return QTT_ERR_OOM;
+  GemmDesc one = g;
+  one.batch = 1;
+  one.bA = one.bB = one.bC = MIdx{1, 1, 0, 0};
+  int st = QTT_OK;
+  for (int64_t b = 0; b < g.batch && !st; ++b) {
+    c->launches += 4;
+    cudaEvent_t ev = prof_begin(c);
+    st = qtt_tc_gemm(one, alpha, beta, A + midx_off(g.bA, b), B + midx_off(g.bB, b), C + midx_off(g.bC, b), ws,
+                     c->d_tcerr, c->stream);
+    prof_end(c, ev, PK_GEMM, 8.0 * g.M * g.N * g.K, (double)(g.M * g.K + g.K * g.N + g.M * g.N) * sizeof(cc));
+  }
+  dfree(c, ws);
+  return st;
+}
+
 // C (M x N) = alpha op(A) op(B) + beta C, single batch, general strides
 template <class R>
 int mm(qtt_ctx* c, int64_t M, int64_t N, int64_t K, const cplx<R>* A, int64_t sAm, int64_t sAk, int conjA,
@@ -139,6 +165,11 @@ int mm(qtt_ctx* c, int64_t M, int64_t N, int64_t K, const cplx<R>* A, int64_t sA
     // C = beta C (only used with beta = 0 here): zero the output
     if (sCn == 1 && sCm == N) return cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(cplx<R>), c->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
   }
+  if (sizeof(R) == 4) {
+    int st = tc_route(c, g, cc((float)alpha.re, (float)alpha.im), cc((float)beta.re, (float)beta.im),
+                      reinterpret_cast<const cc*>(A), reinterpret_cast<const cc*>(B), reinterpret_cast<cc*>(C));
+    if (st != QTT_ERR_UNSUPPORTED) return st;
+  }
   c->launches++;
   cudaEvent_t ev = prof_begin(c);
   int st = qtt_gemm<R>(g, alpha, beta, A, B, C, c->stream);
@@ -148,6 +179,11 @@ int mm(qtt_ctx* c, int64_t M, int64_t N, int64_t K, const cplx<R>* A, int64_t sA
 
 template <class R>
 int gemm(qtt_ctx* c, const GemmDesc& g, const cplx<R>* A, const cplx<R>* B, cplx<R>* C) {
+  if (sizeof(R) == 4) {
+    int st = tc_route(c, g, cc(1, 0), cc(0, 0), reinterpret_cast<const cc*>(A), reinterpret_cast<const cc*>(B),
+                      reinterpret_cast<cc*>(C));
+    if (st != QTT_ERR_UNSUPPORTED) return st;
+  }
   c->launches++;
   cudaEvent_t ev = prof_begin(c);
   int st = qtt_gemm<R>(g, cplx<R>(1, 0), cplx<R>(0, 0), A, B, C, c->stream);

@@ -28,6 +28,16 @@ struct qtt_ctx {
   std::vector<ProfRec> recs;
   int* d_sweeps = nullptr;   // device counters written by profiled Jacobi launches
   int sweeps_cap = 0, sweeps_used = 0;
+  bool tc = false;           // route large float contractions to the tensor cores
+  int* d_tcerr = nullptr;    // bounded-wait failure flag of the tensor-core GEMM
+};
+
+// Scoped switch of the tensor-core route for one ABI call.
+struct TcScope {
+  qtt_ctx* c;
+  bool old;
+  TcScope(qtt_ctx* ctx, bool on) : c(ctx), old(ctx->tc) { ctx->tc = on; }
+  ~TcScope() { c->tc = old; }
 };
 
 inline cudaEvent_t prof_begin(qtt_ctx* c) {

@@ -73,3 +73,8 @@ int qtt_identity_core(int64_t g, int64_t n, cplx<R>* D, cudaStream_t s);
 template <class R>
 int qtt_adjoint_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64_t g1, cplx<R>* out,
                      cudaStream_t s);
+
+// tensor-core complex64 GEMM (tc_gemm.cu), batch 1
+size_t qtt_tc_gemm_workspace(int64_t M, int64_t N, int64_t K);
+int qtt_tc_gemm(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C, void* ws, int* err,
+                cudaStream_t s);

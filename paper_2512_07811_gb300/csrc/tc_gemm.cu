@@ -1,0 +1,351 @@
+// Complex GEMM on the 5th-generation tensor cores (tcgen05, kind::tf32) for
+// the FP32 path.
+//
+// C = alpha op(A) op(B) + beta C with complex64 operands given through
+// two-level strided views (any contraction of the tensor-train path) is
+// computed as ONE real GEMM C3 = A3 B3^T on packed operands:
+//   A2 = [Ar | Ai]                       (M x 2K, K contiguous)
+//   B2 = [[Br^T | -Bi^T]; [Bi^T | Br^T]] (2N x 2K)   =>  A2 B2^T = [Cr | Ci]
+// and, for FP32-level accuracy, the split x = hi + lo with hi = tf32(x),
+// lo = tf32(x - hi): A3 = [A2hi | A2hi | A2lo], B3 = [B2hi | B2lo | B2hi]
+// (K3 = 6K, padded to 32), so A3 B3^T = A2hi B2hi^T + A2hi B2lo^T + A2lo B2hi^T.
+//
+// The tensor-core kernel: one CTA (128 threads) per 128 x 128 tile of C3;
+// TMA (128-byte swizzle, 32 fp32 of K per row) fills a 4-stage ring of A and
+// B tiles guarded by mbarriers; one thread issues tcgen05.mma (M = 128,
+// N = 128, K = 8 per instruction) into a 128-column FP32 accumulator in
+// tensor memory and commits each stage back to the producer; after the last
+// stage the four warps read their 32 accumulator lanes with tcgen05.ld and
+// store C3.  Every mbarrier wait is bounded: on timeout the kernel records
+// the failure in `err`, stops issuing work, still frees its tensor memory and
+// returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr int TBM = 128, TBN = 128, TBK = 32, STAGES = 4;
+constexpr int TILE_A_BYTES = TBM * TBK * 4;   // 16 KB
+constexpr int TILE_B_BYTES = TBN * TBK * 4;   // 16 KB
+constexpr int STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
+constexpr uint32_t WAIT_LIMIT = 1u << 26;     // bounded spin (~ seconds), then give up
+
+// ----------------------------------------------------------- packing kernels
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// A3 row m (m < Mp): columns [part*2K + c], c < 2K: c < K -> Re A[m, c], else Im A[m, c-K]
+template <int PART_LO>
+__device__ __forceinline__ float split_part(float x) {
+  float hi = to_tf32(x);
+  return PART_LO ? to_tf32(x - hi) : hi;
+}
+
+__global__ void pack_a_kernel(const cc* __restrict__ A, GemmDesc g, int64_t K3p, float* __restrict__ A3, int64_t Mp) {
+  const int64_t K = g.K;
+  const int64_t total = Mp * K3p;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t m = e / K3p, col = e - m * K3p;
+    float v = 0.f;
+    if (m < g.M && col < 6 * K) {
+      int part = (int)(col / (2 * K));
+      int64_t c = col - part * 2 * K;
+      int64_t k = c < K ? c : c - K;
+      cc a = A[midx_off(g.mA, m) + midx_off(g.kA, k)];
+      if (g.conjA) a.im = -a.im;
+      float x = c < K ? a.re : a.im;
+      v = part == 2 ? split_part<1>(x) : split_part<0>(x);
+    }
+    A3[e] = v;
+  }
+}
+
+// B3 row j (j < Np): n = j mod N, half = j / N; K-columns as for A with parts (hi, lo, hi)
+__global__ void pack_b_kernel(const cc* __restrict__ B, GemmDesc g, int64_t K3p, float* __restrict__ B3, int64_t Np) {
+  const int64_t K = g.K, N = g.N;
+  const int64_t total = Np * K3p;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = e / K3p, col = e - j * K3p;
+    float v = 0.f;
+    if (j < 2 * N && col < 6 * K) {
+      int part = (int)(col / (2 * K));
+      int64_t c = col - part * 2 * K;
+      int64_t n = j < N ? j : j - N;
+      int64_t k = c < K ? c : c - K;
+      cc b = B[midx_off(g.kB, k) + midx_off(g.nB, n)];
+      if (g.conjB) b.im = -b.im;
+      float x;
+      if (j < N) x = c < K ? b.re : -b.im;  // row n:   [Br | -Bi]
+      else x = c < K ? b.im : b.re;         // row N+n: [Bi |  Br]
+      v = part == 1 ? split_part<1>(x) : split_part<0>(x);
+    }
+    B3[e] = v;
+  }
+}
+
+// C[m, n] = alpha (C3[m, n] + i C3[m, N + n]) + beta C[m, n]
+__global__ void unpack_c_kernel(const float* __restrict__ C3, int64_t ldc3, GemmDesc g, cc alpha, cc beta,
+                                cc* __restrict__ C) {
+  const int64_t total = g.M * g.N;
+  const bool use_beta = beta.re != 0.f || beta.im != 0.f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t m = e / g.N, n = e - m * g.N;
+    cc v(C3[m * ldc3 + n], C3[m * ldc3 + g.N + n]);
+    int64_t o = midx_off(g.mC, m) + midx_off(g.nC, n);
+    cc r = alpha * v;
+    if (use_beta) r = r + beta * C[o];
+    C[o] = r;
+  }
+}
+
+// ------------------------------------------------------- PTX helper wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes));
+}
+// bounded wait on the phase with the given parity; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+// shared-memory matrix descriptor (K-major, 128-byte swizzle): start >> 4,
+// leading byte offset 16 (unused with swizzling), stride byte offset 1024
+// (eight 128-byte rows), descriptor version 1, swizzle mode 2 (128 B)
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(16 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, N, M
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4)                       // D format F32
+         | (2u << 7)                     // A format TF32
+         | (2u << 10)                    // B format TF32
+         | ((uint32_t)(N >> 3) << 17)    // N / 8
+         | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+__global__ void __launch_bounds__(128, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float* __restrict__ C3,
+               int64_t ldc3, int k_tiles, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled tiles
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    // 128 columns of FP32 accumulator for the 128 x 128 tile
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(TBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA loads into the ring
+    for (int kt = 0; kt < k_tiles; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t round = kt / STAGES;
+      if (kt >= STAGES) {
+        if (!mbar_wait(&empty_bar[s], (round - 1) & 1)) {
+          atomicExch(err, 1);
+          abort_sh = 1;
+          break;
+        }
+      }
+      if (abort_sh) break;
+      unsigned char* a = smem + s * STAGE_BYTES;
+      unsigned char* b = a + TILE_A_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      tma_load_2d(&mapA, &full_bar[s], a, kt * TBK, m0);
+      tma_load_2d(&mapB, &full_bar[s], b, kt * TBK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = idesc_tf32(TBM, TBN);
+    for (int kt = 0; kt < k_tiles; ++kt) {
+      const int s = kt % STAGES;
+      if (!mbar_wait(&full_bar[s], (kt / STAGES) & 1)) {
+        atomicExch(err, 2);
+        abort_sh = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t b = a + TILE_A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < TBK / 8; ++kk) {
+        // K advances 8 tf32 = 32 bytes inside the 128-byte swizzle atom
+        const uint64_t da = smem_desc_sw128(a + kk * 32);
+        const uint64_t db = smem_desc_sw128(b + kk * 32);
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+      }
+      // free the stage once these MMAs have read it
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&empty_bar[s])));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(&done_bar)));
+  }
+  // epilogue: every warp waits for the accumulator, then reads its 32 lanes
+  __syncwarp();
+  bool ok = mbar_wait(&done_bar, 0);
+  if (!ok && lane == 0) atomicExch(err, 3);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    float* crow = C3 + (int64_t)row * ldc3 + n0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TBN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) crow[c0 + j] = __uint_as_float(v[j]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+  }
+}
+
+// ------------------------------------------------------ tensor-map encoding
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// rows x cols fp32, row-major (cols contiguous), box 32 (cols) x 128 (rows), 128-byte swizzle
+bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)TBM};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline unsigned grid1d(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 65535 * 8); }
+
+}  // namespace
+
+// Workspace bytes for one call with the given sizes.
+size_t qtt_tc_gemm_workspace(int64_t M, int64_t N, int64_t K) {
+  const int64_t Mp = (M + TBM - 1) / TBM * TBM;
+  const int64_t Np = (2 * N + TBN - 1) / TBN * TBN;
+  const int64_t K3p = (6 * K + TBK - 1) / TBK * TBK;
+  return (size_t)(Mp * K3p + Np * K3p + Mp * Np) * sizeof(float) + 3 * 1024 + 16;
+}
+
+// Single-batch complex64 GEMM through the tensor cores.  `ws` needs
+// qtt_tc_gemm_workspace(M, N, K) bytes (device), `err` one device int
+// (set non-zero when a bounded wait gave up).
+int qtt_tc_gemm(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C, void* ws, int* err,
+                cudaStream_t s) {
+  if (g.batch != 1) return QTT_ERR_UNSUPPORTED;
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return QTT_ERR_ARG;
+  const int64_t Mp = (g.M + TBM - 1) / TBM * TBM;
+  const int64_t Np = (2 * g.N + TBN - 1) / TBN * TBN;
+  const int64_t K3p = (6 * g.K + TBK - 1) / TBK * TBK;
+  uintptr_t p = (reinterpret_cast<uintptr_t>(ws) + 1023) & ~(uintptr_t)1023;
+  float* A3 = reinterpret_cast<float*>(p);
+  p = (reinterpret_cast<uintptr_t>(A3 + Mp * K3p) + 1023) & ~(uintptr_t)1023;
+  float* B3 = reinterpret_cast<float*>(p);
+  p = (reinterpret_cast<uintptr_t>(B3 + Np * K3p) + 1023) & ~(uintptr_t)1023;
+  float* C3 = reinterpret_cast<float*>(p);
+  pack_a_kernel<<<grid1d(Mp * K3p), 256, 0, s>>>(A, g, K3p, A3, Mp);
+  pack_b_kernel<<<grid1d(Np * K3p), 256, 0, s>>>(B, g, K3p, B3, Np);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A3, Mp, K3p) || !make_map(&mb, B3, Np, K3p)) return QTT_ERR_CUDA;
+  const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] {
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr_err != cudaSuccess) return QTT_ERR_CUDA;
+  dim3 grid((unsigned)(Np / TBN), (unsigned)(Mp / TBM), 1);
+  tc_gemm_kernel<<<grid, 128, smem, s>>>(ma, mb, C3, Np, (int)(K3p / TBK), err);
+  unpack_c_kernel<<<grid1d(g.M * g.N), 256, 0, s>>>(C3, Np, g, alpha, beta, C);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}

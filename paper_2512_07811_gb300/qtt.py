@@ -29,7 +29,7 @@ _ALIVE = [True]
 atexit.register(lambda: _ALIVE.__setitem__(0, False))
 
 C128, C64 = 0, 1
-PREC_F64, PREC_F32 = 0, 1
+PREC_F64, PREC_F32, PREC_TC32 = 0, 1, 2
 _NP = {C128: np.complex128, C64: np.complex64}
 
 
@@ -118,6 +118,7 @@ _sig("tt_norm", C.c_int, [_P, _P, C.POINTER(C.c_double)])
 _sig("tt_from_dense", C.c_int, [_P, C.c_int, _I32P, _P, C.c_double, C.c_int, C.POINTER(_P)])
 _sig("qtt_qft_mpo", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(_P)])
 _sig("qtt_mpo_diag", C.c_int, [_P, _P, C.POINTER(_P)])
+_sig("qtt_cgemm", C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, C.c_int])
 _sig("qtt_mpo_convert", C.c_int, [_P, _P, C.c_int, C.POINTER(_P)])
 _sig("ms_homogenize_batch", C.c_int, [_P, C.c_int, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
                                       C.POINTER(MSOpts), C.c_int, C.POINTER(C.c_double), C.POINTER(MSReport)])
@@ -139,7 +140,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_sketched", "tt_dot", "tt_norm",
             "tt_from_dense", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
-            "ms_homogenize_batch",
+            "ms_homogenize_batch", "qtt_cgemm",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
             "qtt_mlp_get_params", "qtt_mlp_forward", "qtt_mlp_train_step"]
 
@@ -384,6 +385,11 @@ def qtt_qft_mpo(ctx: Context, nbits: int, sign: int = -1, tol: float = 1e-12) ->
     A._shapes = [(g[k], 2, 2, g[k + 1]) for k in range(nbits)]
     A._dtype = C128
     return A
+
+
+def qtt_cgemm(ctx: Context, M: int, N: int, K: int, A_ptr: int, B_ptr: int, C_ptr: int, engine: int = 1):
+    """C = A B for row-major complex64 device buffers (e.g. torch tensors' data_ptr())."""
+    _check(_lib.qtt_cgemm(ctx.h, int(M), int(N), int(K), _P(A_ptr), _P(B_ptr), _P(C_ptr), int(engine)), "qtt_cgemm")
 
 
 def qtt_mpo_diag(ctx: Context, x: TT) -> MPO:
