@@ -3,6 +3,9 @@
 
 #include "common.cuh"
 
+// raise a kernel's dynamic shared-memory limit to the maximum once per device (linalg.cu)
+int qtt_allow_max_smem(const void* func);
+
 template <class R>
 int qtt_gemm(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B,
              cplx<R>* C, cudaStream_t s);

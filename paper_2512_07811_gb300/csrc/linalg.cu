@@ -9,6 +9,9 @@
 #include <float.h>
 
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -559,6 +562,29 @@ jacobi_smem_kernel(const cplx<R>* __restrict__ Gin, cplx<R>* __restrict__ Vws, R
 
 }  // namespace
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum
+// (minus its static shared memory), once per (kernel, device).  The limit is
+// never lowered afterwards, so launches from several host threads with
+// different dynamic sizes cannot invalidate one another.
+int qtt_allow_max_smem(const void* func) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QTT_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({func, dev})) return QTT_OK;
+  int optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, func) != cudaSuccess)
+    return QTT_ERR_CUDA;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes) !=
+      cudaSuccess)
+    return QTT_ERR_CUDA;
+  done.insert({func, dev});
+  return QTT_OK;
+}
+
 template <class R>
 int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
              int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
@@ -578,10 +604,7 @@ int qtt_jacobi(cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, in
   if (batch <= 0 || q <= 0) return QTT_OK;
   int qe = q + (q & 1);
   size_t sm = (size_t)(qe + (qe & 1)) * sizeof(int) + (size_t)q * sizeof(R) + 16;
-  if (sm > 48 * 1024) {
-    if (cudaFuncSetAttribute(jacobi_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-      return QTT_ERR_CUDA;
-  }
+  if (sm > 48 * 1024 && qtt_allow_max_smem((const void*)jacobi_kernel<R>) != QTT_OK) return QTT_ERR_CUDA;
   jacobi_kernel<R><<<(unsigned)batch, 256, sm, s>>>(G, Vwork, sigma, Vsorted, Usorted, p, q, max_sweeps, sweeps);
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
@@ -630,11 +653,7 @@ int qtt_jacobi_wide(const cplx<R>* G, cplx<R>* Gwork, cplx<R>* Vwork, R* sigma, 
   }
   if (sweeps_done) *sweeps_done = sweep;
   size_t sm = (size_t)q * sizeof(R);
-  if (sm > 48 * 1024) {
-    if (cudaFuncSetAttribute(jacobi_finish_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-        cudaSuccess)
-      return QTT_ERR_CUDA;
-  }
+  if (sm > 48 * 1024 && qtt_allow_max_smem((const void*)jacobi_finish_kernel<R>) != QTT_OK) return QTT_ERR_CUDA;
   jacobi_finish_kernel<R><<<1, 256, sm, s>>>(Gwork, Vwork, p, q, sigma, Vsorted, Usorted);
   *launches += 1;
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
@@ -654,8 +673,7 @@ int qtt_jacobi_smem(const cplx<R>* G, cplx<R>* Vws, R* sigma, cplx<R>* Vsorted, 
   if (q <= 0) return QTT_OK;
   size_t sm = qtt_jacobi_smem_bytes<R>(p, q);
   if (sm > 227 * 1024) return QTT_ERR_RANK;
-  if (cudaFuncSetAttribute(jacobi_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-    return QTT_ERR_CUDA;
+  if (qtt_allow_max_smem((const void*)jacobi_smem_kernel<R>) != QTT_OK) return QTT_ERR_CUDA;
   jacobi_smem_kernel<R><<<1, 1024, sm, s>>>(G, Vws, sigma, Vsorted, Usorted, p, q, max_sweeps, sweeps);
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }

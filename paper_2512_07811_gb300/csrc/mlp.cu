@@ -266,8 +266,7 @@ int qtt_mlp_backward_dev(const __half* Wh, const float* P, int F, const float* X
   int64_t blocks = (B + WARPS - 1) / WARPS;
   if (blocks > 256) blocks = 256;
   size_t sm = (size_t)(offsets(F).total + 1) * sizeof(float);
-  if (cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-    return QTT_ERR_CUDA;
+  if (qtt_allow_max_smem((const void*)mlp_backward_kernel) != QTT_OK) return QTT_ERR_CUDA;
   mlp_backward_kernel<<<(unsigned)blocks, WARPS * 32, sm, s>>>(Wh, P, F, X, T, B, alpha, G, loss_acc);
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }

@@ -338,12 +338,7 @@ int qtt_tc_gemm(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, 
   CUtensorMap ma, mb;
   if (!make_map(&ma, A3, Mp, K3p) || !make_map(&mb, B3, Np, K3p)) return QTT_ERR_CUDA;
   const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [&] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  if (attr_err != cudaSuccess) return QTT_ERR_CUDA;
+  if (qtt_allow_max_smem((const void*)tc_gemm_kernel) != QTT_OK) return QTT_ERR_CUDA;
   dim3 grid((unsigned)(Np / TBN), (unsigned)(Mp / TBM), 1);
   tc_gemm_kernel<<<grid, 128, smem, s>>>(ma, mb, C3, Np, (int)(K3p / TBK), err);
   unpack_c_kernel<<<grid1d(g.M * g.N), 256, 0, s>>>(C3, Np, g, alpha, beta, C);
