@@ -201,6 +201,31 @@ QTT_API int qtt_qft_mpo(qtt_ctx* ctx, int nbits, int sign, double tol, qtt_mpo**
 QTT_API int qtt_cgemm(qtt_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, const void* B, void* C,
                       int engine);
 
+/* The same product as qtt_cgemm with engine 1 (tensor cores), for callers
+ * that may not allocate device memory: for example a host application that
+ * reserves the whole device memory for itself at start-up and forbids its
+ * libraries to call cudaMalloc afterwards, or code that must not block on
+ * the allocator while it runs.  This call allocates nothing: its working
+ * space is a fixed 16 MiB array that the library reserves on every device
+ * it is loaded on, kept until the process exits.  The paper has no
+ * counterpart; it is a service of this library.
+ *  - A, B, C: row-major complex64 device matrices (M x K, K x N, M x N);
+ *    `stream` is a cudaStream_t (NULL: the legacy default stream).
+ *  - Sizes whose packed operands do not fit the array are rejected with
+ *    QTT_ERR_RANK before any GPU work (the working space is
+ *    4 (Mp K3 + Np K3 + Mp Np) bytes plus alignment, Mp = M rounded up to
+ *    128, Np = 2N rounded up to 128, K3 = 6K rounded up to 32; M = N = K = 384
+ *    fits).
+ *  - The first call on a device looks up the array's device address (and
+ *    checks the device is sm_103); make that first call before any stream
+ *    capture.  Every call synchronises `stream`.
+ *  - All calls share the one array, which keeps the last call's contents:
+ *    calls whose GPU work overlaps (other streams, other host threads) race
+ *    on it, so serialise them.
+ *  - QTT_ERR_TIMEOUT if a bounded device wait gave up. */
+QTT_API int qtt_cgemm_noalloc(void* stream, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
+                              void* C);
+
 /* The train x lifted to the operator D(i, j) = x(i) delta(i, j) (Sec. 2.1,
  * Eq. tt_to_tto): applying it is the Hadamard product with x, which lets
  * tt_round_sketched round x (elementwise) y without forming it. */

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "../../include/qtt.h"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -343,4 +344,74 @@ int qtt_tc_gemm(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, 
   tc_gemm_kernel<<<grid, 128, smem, s>>>(ma, mb, C3, Np, (int)(K3p / TBK), err);
   unpack_c_kernel<<<grid1d(g.M * g.N), 256, 0, s>>>(C3, Np, g, alpha, beta, C);
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+// --------------------------------------------- allocation-free entry point
+// Scratch of qtt_cgemm_noalloc: the packed operands, the real product and the
+// wait-failure flag of one call live in this file-scope device array, so the
+// call itself never allocates.  Every device that loads the library holds it
+// (16 MiB) until the process exits.  Calls share it: a call overwrites what
+// the previous one left, and two calls in flight on the GPU at the same time
+// (different streams, or different host threads) would race on it.
+#define QTT_NOALLOC_SCRATCH_BYTES (16u << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QTT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[128] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the array's name as a device address).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return QTT_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return QTT_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return QTT_ERR_UNSUPPORTED;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return QTT_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return QTT_OK;
+}
+}  // namespace
+
+extern "C" int qtt_cgemm_noalloc(void* stream, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
+                                 void* C) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return QTT_ERR_ARG;
+  const size_t need = qtt_tc_gemm_workspace(M, N, K);
+  if (need + 256 > QTT_NOALLOC_SCRATCH_BYTES) return QTT_ERR_RANK;
+  void* base = nullptr;
+  int st = noalloc_scratch(&base);
+  if (st) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the flag must start at zero; everything else is overwritten by the call
+  int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(base) + QTT_NOALLOC_SCRATCH_BYTES - 256);
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return QTT_ERR_CUDA;
+  GemmDesc g;
+  g.bA = g.bB = g.bC = MIdx{1, 1, 0, 0};
+  g.mA = MIdx{M, 1, K, 0};
+  g.kA = MIdx{K, 1, 1, 0};
+  g.kB = MIdx{K, 1, N, 0};
+  g.nB = MIdx{N, 1, 1, 0};
+  g.mC = MIdx{M, 1, N, 0};
+  g.nC = MIdx{N, 1, 1, 0};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = 1;
+  g.conjA = g.conjB = 0;
+  st = qtt_tc_gemm(g, cc(1.f, 0.f), cc(0.f, 0.f), reinterpret_cast<const cc*>(A), reinterpret_cast<const cc*>(B),
+                   reinterpret_cast<cc*>(C), base, err, s);
+  if (st) return st;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return QTT_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return QTT_ERR_CUDA;
+  return h ? QTT_ERR_TIMEOUT : QTT_OK;
 }

@@ -119,6 +119,7 @@ _sig("tt_from_dense", C.c_int, [_P, C.c_int, _I32P, _P, C.c_double, C.c_int, C.P
 _sig("qtt_qft_mpo", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(_P)])
 _sig("qtt_mpo_diag", C.c_int, [_P, _P, C.POINTER(_P)])
 _sig("qtt_cgemm", C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, C.c_int])
+_sig("qtt_cgemm_noalloc", C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, _P, _P, _P])
 _sig("qtt_mpo_convert", C.c_int, [_P, _P, C.c_int, C.POINTER(_P)])
 _sig("ms_homogenize_batch", C.c_int, [_P, C.c_int, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
                                       C.POINTER(MSOpts), C.c_int, C.POINTER(C.c_double), C.POINTER(MSReport)])
@@ -140,7 +141,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_sketched", "tt_dot", "tt_norm",
             "tt_from_dense", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
-            "ms_homogenize_batch", "qtt_cgemm",
+            "ms_homogenize_batch", "qtt_cgemm", "qtt_cgemm_noalloc",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
             "qtt_mlp_get_params", "qtt_mlp_forward", "qtt_mlp_train_step"]
 
@@ -390,6 +391,13 @@ def qtt_qft_mpo(ctx: Context, nbits: int, sign: int = -1, tol: float = 1e-12) ->
 def qtt_cgemm(ctx: Context, M: int, N: int, K: int, A_ptr: int, B_ptr: int, C_ptr: int, engine: int = 1):
     """C = A B for row-major complex64 device buffers (e.g. torch tensors' data_ptr())."""
     _check(_lib.qtt_cgemm(ctx.h, int(M), int(N), int(K), _P(A_ptr), _P(B_ptr), _P(C_ptr), int(engine)), "qtt_cgemm")
+
+
+def qtt_cgemm_noalloc(stream: int, M: int, N: int, K: int, A_ptr: int, B_ptr: int, C_ptr: int):
+    """Tensor-core C = A B that allocates no device memory (fixed 16 MiB library
+    array); for callers that may not allocate.  `stream` is a cudaStream_t value."""
+    _check(_lib.qtt_cgemm_noalloc(_P(stream) if stream else None, int(M), int(N), int(K), _P(A_ptr), _P(B_ptr),
+                                  _P(C_ptr)), "qtt_cgemm_noalloc")
 
 
 def qtt_mpo_diag(ctx: Context, x: TT) -> MPO:
