@@ -14,8 +14,10 @@ The metric is the flop model of every SVD rounding in the step (shared with
 the CPU oracle, paper_2512_07811_gb300/flops.py) divided by the step time:
 "tt_round TFLOP/s".  The fast path stores complex64 and runs float kernels;
 the FP64 path runs the same step in complex128 and is reported beside it.
-A secondary object times the Moulinec-Suquet iteration on the 32^3 scalar
-laminate (15 interleaved bit sites + one control site).
+The three roundings of a step are independent and run concurrently on three
+streams (one host thread each).  A secondary object times the
+Moulinec-Suquet iteration on the 32^3 scalar laminate (15 interleaved bit
+sites + one control site).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -128,11 +130,17 @@ class ClockSampler:
 
 # ------------------------------------------------------------ our path
 class Step:
-    """Device-resident inputs and one pass of the workload on one context."""
+    """Device-resident inputs and one pass of the workload.  The step's three
+    roundings are independent: each runs on its own context (stream) from its
+    own host thread, so that their latency-bound factorisation chains occupy
+    different SMs at the same time; `run` returns when all three are done."""
 
-    def __init__(self, Q, ctx, r, dtype, qft_c128, prec=None):
-        self.Q, self.ctx, self.r, self.dtype = Q, ctx, r, dtype
+    def __init__(self, Q, torch, ctxs, streams, r, dtype, qft_c128, prec=None):
+        import concurrent.futures as cf
+        self.Q, self.torch, self.r, self.dtype = Q, torch, r, dtype
+        self.ctxs, self.streams = ctxs, streams
         self.prec = prec
+        ctx = ctxs[0]
         self.xc = I.random_tt_cores(D, 2, r, seed=1000 + r, dtype=np.complex128)
         self.yc = I.random_tt_cores(D, 2, r, seed=1001 + r, dtype=np.complex128)
         rng = np.random.default_rng(2000 + r)
@@ -143,18 +151,40 @@ class Step:
         self.DX = Q.qtt_mpo_diag(ctx, self.X)
         self.F = qft_c128 if dtype == Q.C128 else Q.qtt_mpo_convert(ctx, qft_c128, dtype)
         self.modes = [2] * D
+        ctx.sync()
+        self.pool = cf.ThreadPoolExecutor(max_workers=3)
 
     def run(self, X=None, Y=None):
-        Q, ctx, r = self.Q, self.ctx, self.r
+        Q, r, torch = self.Q, self.r, self.torch
+        c0, c1, c2 = self.ctxs
         X = X or self.X
         Y = Y or self.Y
-        DX = self.DX if X is self.X else Q.qtt_mpo_diag(ctx, X)
-        z = Q.tt_add(ctx, 1.0, X, 1.0, Y)
-        zr, _ = Q.tt_round(ctx, z, EPS, prec=self.prec)
-        h, _ = Q.tt_round_sketched(ctx, [(1.0, DX, Y)], self.S, EPS, r, prec=self.prec)
-        q, _ = Q.tt_round_sketched(ctx, [(1.0, self.F, X)], self.S, EPS, r, prec=self.prec)
-        v = Q.tt_dot(ctx, X, Y)
-        flops = (round_flops(self.modes, z.ranks, zr.ranks)
+        DX = self.DX if X is self.X else Q.qtt_mpo_diag(c0, X)
+        # the worker streams start after everything already queued on the first
+        start = torch.cuda.Event()
+        start.record(self.streams[0])
+        for st in self.streams[1:]:
+            st.wait_event(start)
+
+        def add_round():
+            z = Q.tt_add(c0, 1.0, X, 1.0, Y)
+            zr, _ = Q.tt_round(c0, z, EPS, prec=self.prec)
+            return z.ranks, zr, Q.tt_dot(c0, X, Y)
+
+        def had_round():
+            return Q.tt_round_sketched(c1, [(1.0, DX, Y)], self.S, EPS, r, prec=self.prec)[0]
+
+        def qft_round():
+            return Q.tt_round_sketched(c2, [(1.0, self.F, X)], self.S, EPS, r, prec=self.prec)[0]
+
+        fa, fh, fq = self.pool.submit(add_round), self.pool.submit(had_round), self.pool.submit(qft_round)
+        zranks, zr, v = fa.result()
+        h, q = fh.result(), fq.result()
+        for st in self.streams[1:]:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            self.streams[0].wait_event(ev)
+        flops = (round_flops(self.modes, zranks, zr.ranks)
                  + round_flops(self.modes, self.sk_ranks, h.ranks)
                  + round_flops(self.modes, self.sk_ranks, q.ranks))
         return flops, (zr, h, q, v)
@@ -188,12 +218,14 @@ def run_ours(args, rank, world, local_rank):
     from paper_2512_07811_gb300 import qtt as Q
 
     torch.cuda.set_device(local_rank)
-    stream = torch.cuda.Stream(device=local_rank)
-    ctx = Q.Context(local_rank, stream.cuda_stream)
+    streams = [torch.cuda.Stream(device=local_rank) for _ in range(3)]
+    stream = streams[0]
+    ctxs = [Q.Context(local_rank, st.cuda_stream) for st in streams]
+    ctx = ctxs[0]
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     r = args.rank
     qft = Q.qtt_qft_mpo(ctx, D, -1, 1e-12)
-    fast = Step(Q, ctx, r, Q.C64, qft, Q.PREC_TC32 if args.prec == "tc32" else Q.PREC_F32)
+    fast = Step(Q, torch, ctxs, streams, r, Q.C64, qft, Q.PREC_TC32 if args.prec == "tc32" else Q.PREC_F32)
     for _ in range(args.warmup):
         fast.run()
     ctx.sync()
@@ -204,12 +236,17 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank)
     clocks.start()
-    l0 = ctx.launches
-    ctx.profile(True)
+    l0 = sum(c.launches for c in ctxs)
+    for c in ctxs:
+        c.profile(True)
     ms, flops = time_steps(torch, stream, fast, args.steps, flush)
-    prof = {k: ctx.profile_read(k) for k in ["gemm", "qr", "jacobi", "elem"]}
-    ctx.profile(False)
-    launches = ctx.launches - l0
+    prof = {}
+    for k in ["gemm", "qr", "jacobi", "elem"]:
+        parts = [c.profile_read(k) for c in ctxs]
+        prof[k] = {f: sum(p[f] for p in parts) for f in ["ms", "launches", "flops", "bytes"]}
+    for c in ctxs:
+        c.profile(False)
+    launches = sum(c.launches for c in ctxs) - l0
     clk = clocks.stop()
     torch.cuda.synchronize()
     if world > 1:
@@ -242,7 +279,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_flops += f
 
     # FP64 path, same step in complex128
-    slow = Step(Q, ctx, r, Q.C128, qft, Q.PREC_F64)
+    slow = Step(Q, torch, ctxs, streams, r, Q.C128, qft, Q.PREC_F64)
     slow.run()
     ctx.sync()
     ms64, flops64 = time_steps(torch, stream, slow, args.fp64_steps, flush)

@@ -46,7 +46,11 @@ __device__ __forceinline__ R warp_sum(R v) {
 // into a column-major workspace (W + c*m + i holds element (i, c)) so that a
 // warp streams a column with consecutive lanes on consecutive rows; every
 // trailing column is handled by one warp (dot product with the reflector by
-// shuffles, then the rank-1 update).
+// shuffles, then the rank-1 update).  Two barriers per column: thread 0 forms
+// reflector j from the norm that the warp owning column j computed while it
+// applied reflector j-1, then all warps apply reflector j.  Reflectors are
+// stored unscaled below the diagonal, v = (1, x_{j+1} / v0, ...), with 1/v0
+// kept per column, and scaled on the fly.
 template <class R>
 __global__ void __launch_bounds__(1024)
 qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int conj_in,
@@ -55,7 +59,8 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
             cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout, int64_t q_bstride, int64_t ldq,
             cplx<R>* __restrict__ Qws) {
   __shared__ double red[32];
-  __shared__ cplx<R> s_inv_v0;
+  __shared__ double s_nrm2[2];
+  __shared__ cplx<R> s_iv;
   __shared__ R s_tau;
   __shared__ int s_zero;
   const int64_t b = blockIdx.x;
@@ -65,9 +70,8 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
   if (valid > m) valid = m;
   const int64_t ib = midx_off(inB, b);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  double part = 0.0;
+  double part = 0.0, part0 = 0.0;
   for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) {
-    // e enumerates the input row-major-ish: consecutive threads on consecutive columns
     int64_t i = e / n, c = e - i * n;
     cplx<R> v(0, 0);
     if (i < valid) {
@@ -75,68 +79,80 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
       if (conj_in) v.im = -v.im;
     }
     W[c * m + i] = v;
-    part += (double)v.re * v.re + (double)v.im * v.im;
+    const double a2 = (double)v.re * v.re + (double)v.im * v.im;
+    part += a2;
+    if (c == 0) part0 += a2;
   }
   // columns whose remaining norm is below eps * ||A||_F are numerically zero:
   // they are cleared instead of reflected (a perturbation within the
   // backward error of the factorisation), which keeps every reflector
   // away from underflow
   const double anorm2 = block_sum(part, red);
+  const double col0 = block_sum(part0, red);
+  if (threadIdx.x == 0) s_nrm2[0] = col0;
   const double eps = sizeof(R) == 8 ? (double)DBL_EPSILON : (double)FLT_EPSILON;
   const double zero_thresh2 = eps * eps * anorm2;
   const int64_t kmax = m < n ? m : n;
+  __syncthreads();
   for (int64_t j = 0; j < kmax; ++j) {
     cplx<R>* colj = W + j * m;
-    double p2 = 0.0;
-    for (int64_t i = j + threadIdx.x; i < m; i += blockDim.x) {
-      cplx<R> v = colj[i];
-      p2 += (double)v.re * v.re + (double)v.im * v.im;
-    }
-    const double nrm2 = block_sum(p2, red);
     if (threadIdx.x == 0) {
+      const double nrm2 = s_nrm2[j & 1];
       cplx<R> x0 = colj[j];
       double ax2 = (double)x0.re * x0.re + (double)x0.im * x0.im;
       double below = nrm2 - ax2;
+      cplx<R> iv(0, 0);
       if (nrm2 <= zero_thresh2 || below <= zero_thresh2) {
         s_tau = R(0);
         s_zero = 1;
         if (nrm2 <= zero_thresh2) colj[j] = cplx<R>(0, 0);
       } else {
-        // H = I - tau v v^H with v = (1, x_1/v0, ...), v0 = x0 - alpha,
-        // alpha = -e^{i arg x0} ||x||, tau = 2 |v0|^2 / ||x - alpha e1||^2 in [1, 2]
+        // H = I - tau v v^H, v0 = x0 - alpha, alpha = -e^{i arg x0} ||x||,
+        // tau = 2 |v0|^2 / ||x - alpha e1||^2 in [1, 2]
         double ax0 = sqrt(ax2), nrm = sqrt(nrm2);
         double phr = ax0 > 0 ? x0.re / ax0 : 1.0, phi = ax0 > 0 ? x0.im / ax0 : 0.0;
         double alr = -phr * nrm, ali = -phi * nrm;
         double v0r = x0.re - alr, v0i = x0.im - ali;
         double v02 = v0r * v0r + v0i * v0i;
-        double vn2 = below + v02;
-        s_tau = (R)(2.0 * v02 / vn2);
-        s_inv_v0 = cplx<R>((R)(v0r / v02), (R)(-v0i / v02));
+        s_tau = (R)(2.0 * v02 / (below + v02));
+        iv = cplx<R>((R)(v0r / v02), (R)(-v0i / v02));
         s_zero = 0;
         colj[j] = cplx<R>((R)alr, (R)ali);
       }
-      if (tauws) tauws[b * 2 * n + 2 * j + 1] = cplx<R>(s_tau, R(0));
+      s_iv = iv;
+      if (tauws) {
+        tauws[b * 2 * n + 2 * j] = iv;
+        tauws[b * 2 * n + 2 * j + 1] = cplx<R>(s_tau, R(0));
+      }
     }
     __syncthreads();
     const R tau = s_tau;
-    if (tau != R(0)) {
-      const cplx<R> iv = s_inv_v0;
-      for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) colj[i] = colj[i] * iv;
-    } else if (s_zero) {
+    const cplx<R> iv = s_iv;
+    if (s_zero) {
       for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) colj[i] = cplx<R>(0, 0);
     }
-    __syncthreads();
-    if (tau != R(0)) {
-      for (int64_t c = j + 1 + warp; c < n; c += nwarps) {
-        cplx<R>* colc = W + c * m;
+    for (int64_t c = j + 1 + warp; c < n; c += nwarps) {
+      cplx<R>* colc = W + c * m;
+      if (tau != R(0)) {
         cplx<R> w(0, 0);
         if (lane == 0) w = colc[j];
-        for (int64_t i = j + 1 + lane; i < m; i += 32) cfma_conj(w, colj[i], colc[i]);
+        for (int64_t i = j + 1 + lane; i < m; i += 32) cfma_conj(w, colj[i] * iv, colc[i]);
         w.re = warp_sum(w.re);
         w.im = warp_sum(w.im);
         w = tau * w;
         if (lane == 0) colc[j] = colc[j] - w;
-        for (int64_t i = j + 1 + lane; i < m; i += 32) colc[i] = colc[i] - colj[i] * w;
+        for (int64_t i = j + 1 + lane; i < m; i += 32) colc[i] = colc[i] - (colj[i] * iv) * w;
+      }
+      if (c == j + 1) {
+        // norm of the next column below (and at) the next diagonal, for the next step
+        __syncwarp();
+        double p2 = 0.0;
+        for (int64_t i = j + 1 + lane; i < m; i += 32) {
+          cplx<R> v = colc[i];
+          p2 += (double)v.re * v.re + (double)v.im * v.im;
+        }
+        for (int o = 16; o > 0; o >>= 1) p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+        if (lane == 0) s_nrm2[(j + 1) & 1] = p2;
       }
     }
     __syncthreads();
@@ -160,18 +176,19 @@ qr_r_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int 
     __syncthreads();
     for (int64_t j = kmax - 1; j >= 0; --j) {
       const R tau = tauws[b * 2 * n + 2 * j + 1].re;
+      const cplx<R> iv = tauws[b * 2 * n + 2 * j];
       const cplx<R>* colj = W + j * m;
       if (tau != R(0)) {
         for (int64_t c = j + warp; c < kmax; c += nwarps) {
           cplx<R>* qc = Qc + c * m;
           cplx<R> w(0, 0);
           if (lane == 0) w = qc[j];
-          for (int64_t i = j + 1 + lane; i < m; i += 32) cfma_conj(w, colj[i], qc[i]);
+          for (int64_t i = j + 1 + lane; i < m; i += 32) cfma_conj(w, colj[i] * iv, qc[i]);
           w.re = warp_sum(w.re);
           w.im = warp_sum(w.im);
           w = tau * w;
           if (lane == 0) qc[j] = qc[j] - w;
-          for (int64_t i = j + 1 + lane; i < m; i += 32) qc[i] = qc[i] - colj[i] * w;
+          for (int64_t i = j + 1 + lane; i < m; i += 32) qc[i] = qc[i] - (colj[i] * iv) * w;
         }
       }
       __syncthreads();
