@@ -251,9 +251,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms, flops = aggregate(ms, flops)
         dist.barrier()
 
     # e2e: the same step with the inputs uploaded from pinned host memory and
@@ -332,6 +330,21 @@ def cpu_baseline(r):
                       "NumPy FP64 with its threaded BLAS" % r, "seconds": sec}
 
 
+def aggregate(ms: float, flops: float):
+    """Whole-job figures across ranks: the slowest rank's time (max) and the
+    work of all ranks (sum).  Works on NCCL (CUDA tensors) and gloo (CPU)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return ms, flops
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    f = torch.tensor([flops], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(f.item())
+
+
 def config_dict(args, world):
     return {"workload": "tt_ops_d30_r%d: random QTT d=30, mode 2, rank %d, complex; add+round, "
                         "hadamard+sketched round, 30-bit SFFT apply+sketched round, dot" % (args.rank, args.rank),
@@ -375,7 +388,7 @@ def main():
     if rank != 0:
         return 0
     peaks, peak_src = load_peaks()
-    value = world * res["flops"] / (res["ms"] * 1e-3) / 1e12
+    value = res["flops"] / (res["ms"] * 1e-3) / 1e12   # all ranks' work over the slowest rank's time
     # dominant kernel class and its roofline (ALU-bound: float CUDA cores)
     prof = res["prof"]
     dom = max(prof, key=lambda k: prof[k]["ms"])

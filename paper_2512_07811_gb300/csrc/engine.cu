@@ -286,6 +286,22 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
   // FP64 runs at a few flops per clock per SM on this part: spread every
   // sizeable FP64 factorisation over all SMs; FP32 stays in one CTA up to
   // q = 256, where one SM's FP32 rate beats a launch per round.
+  // FP32 matrices too large for one CTA's shared memory: a cluster of 4 or 8
+  // CTAs splitting the rows (a cluster barrier per round costs more than one
+  // SM's compute at the sizes that fit one CTA, so those stay single-CTA)
+  if (sizeof(R) == 4 && q >= 48 && qtt_jacobi_smem_bytes<R>(p, q) > 200 * 1024) {
+    const int nc = q <= 160 ? 4 : 8;
+    if (qtt_jacobi_cluster_bytes<R>(p, q, nc) <= 200 * 1024) {
+      int idx;
+      int* slot = prof_sweep_slot(c, &idx);
+      c->launches++;
+      cudaEvent_t ev = prof_begin(c);
+      int st = qtt_jacobi_cluster<R>(G, sigma, Vsorted, Usorted, p, q, nc, max_sweeps, slot, c->stream);
+      prof_end(c, ev, PK_JACOBI, 0.0, (double)(p + 2.0 * q) * q * sizeof(cplx<R>), idx, jacobi_sweep_flops(p, q));
+      (void)Vwork;
+      return st;
+    }
+  }
   const bool wide = (sizeof(R) == 8 && q >= 32) || q > 256;
   const bool smem = !wide && qtt_jacobi_smem_bytes<R>(p, q) <= 200 * 1024;
   if (smem) {

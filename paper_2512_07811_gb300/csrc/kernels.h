@@ -81,3 +81,10 @@ int qtt_adjoint_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64
 size_t qtt_tc_gemm_workspace(int64_t M, int64_t N, int64_t K);
 int qtt_tc_gemm(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C, void* ws, int* err,
                 cudaStream_t s);
+
+// one-sided Jacobi over a thread-block cluster of nc CTAs (4 or 8), rows split over the CTAs (linalg.cu)
+template <class R>
+size_t qtt_jacobi_cluster_bytes(int p, int q, int nc);
+template <class R>
+int qtt_jacobi_cluster(const cplx<R>* G, R* sigma, cplx<R>* Vsorted, cplx<R>* Usorted, int p, int q, int nc,
+                       int max_sweeps, int* sweeps, cudaStream_t s);

@@ -6,6 +6,7 @@
 //   * the truncation-rank rule on sorted singular values.
 // Arithmetic is in the storage precision R (double or float); reductions of
 // the truncation tail are always in double.
+#include <cooperative_groups.h>
 #include <float.h>
 
 #include <algorithm>
@@ -577,6 +578,174 @@ jacobi_smem_kernel(const cplx<R>* __restrict__ Gin, cplx<R>* __restrict__ Vws, R
   }
 }
 
+// ----------------------------------------- one-sided Jacobi over a CTA cluster
+// The rows of G (p x q) and of the rotation matrix V (q x q) are split over the
+// NC CTAs of one thread-block cluster; each CTA keeps its rows of every
+// column in shared memory.  A round of the round-robin tournament (order[0] =
+// 0, order[i] = 1 + (i - 1 + r) mod (qe - 1), pairs (order[i], order[qe-1-i]))
+// runs in three steps: every CTA computes its partial inner products of the
+// round's column pairs (||g_a||^2, ||g_c||^2, g_a^H g_c over its rows) and
+// writes them into slot [its rank] of every CTA's exchange buffer (distributed
+// shared memory, double-buffered by round parity); one cluster barrier; every
+// CTA sums the NC slots in rank order -- identical totals, hence identical
+// rotation decisions in all CTAs -- and rotates its own rows of G and V.
+template <class R, int NC>
+__global__ void __launch_bounds__(1024)
+jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out, cplx<R>* __restrict__ Vs_out,
+                      cplx<R>* __restrict__ Us_out, int p, int q, int max_sweeps, int* __restrict__ sweeps_out) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int qe = q + (q & 1);
+  const int npairs = qe / 2;
+  const int chunk = (p + NC - 1) / NC;         // G rows per CTA
+  const int chunkv = (q + NC - 1) / NC;        // V rows per CTA
+  const int r0 = rank * chunk, r1 = min(p, r0 + chunk);
+  const int v0 = rank * chunkv, v1 = min(q, v0 + chunkv);
+  const int nr = max(r1 - r0, 0), nv = max(v1 - v0, 0);
+  // layout: slots[2][NC][npairs] x 4 R | nsum[NC][q] R | norms[q] R | G[q][chunk] | V[q][chunkv]
+  R* slots = reinterpret_cast<R*>(smem_raw);
+  R* nsum = slots + 2 * NC * npairs * 4;
+  R* norms = nsum + NC * q;
+  size_t off = (size_t)(2 * NC * npairs * 4 + NC * q + q) * sizeof(R);
+  off = (off + 15) & ~(size_t)15;
+  cplx<R>* G = reinterpret_cast<cplx<R>*>(smem_raw + off);
+  cplx<R>* V = G + (size_t)q * chunk;
+  __shared__ int s_rot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < q * chunk; e += blockDim.x) {
+    int c = e / chunk, i = e - c * chunk;
+    G[e] = (r0 + i < p) ? Gin[(int64_t)(r0 + i) * q + c] : cplx<R>(0, 0);
+  }
+  for (int e = threadIdx.x; e < q * chunkv; e += blockDim.x) {
+    int c = e / chunkv, i = e - c * chunkv;
+    V[e] = cplx<R>((v0 + i == c) ? R(1) : R(0), R(0));
+  }
+  cluster.sync();
+  const R tol = (sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON)) * sqrt(R(p > 1 ? p : 1));
+  int sweep = 0, round_count = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < qe - 1; ++round, ++round_count) {
+      const int buf = round_count & 1;
+      // 1. partial inner products of this round's pairs over the local rows
+      for (int pr = warp; pr < npairs; pr += nwarps) {
+        int a = pr == 0 ? 0 : 1 + (pr - 1 + round) % (qe - 1);
+        int qi = qe - 1 - pr;
+        int c = qi == 0 ? 0 : 1 + (qi - 1 + round) % (qe - 1);
+        R al = 0, be = 0;
+        cplx<R> g(0, 0);
+        if (a < q && c < q) {
+          if (a > c) { int t = a; a = c; c = t; }
+          const cplx<R>* ga = G + (size_t)a * chunk;
+          const cplx<R>* gc = G + (size_t)c * chunk;
+          for (int i = lane; i < nr; i += 32) {
+            cplx<R> x = ga[i], y = gc[i];
+            al += abs2(x);
+            be += abs2(y);
+            cfma_conj(g, x, y);
+          }
+          al = warp_sum(al);
+          be = warp_sum(be);
+          g.re = warp_sum(g.re);
+          g.im = warp_sum(g.im);
+        }
+        if (lane < NC) {
+          R* dst = cluster.map_shared_rank(slots, lane) + ((size_t)(buf * NC + rank) * npairs + pr) * 4;
+          dst[0] = al;
+          dst[1] = be;
+          dst[2] = g.re;
+          dst[3] = g.im;
+        }
+      }
+      cluster.sync();
+      // 2. totals (same order in every CTA) and the rotation of the local rows
+      for (int pr = warp; pr < npairs; pr += nwarps) {
+        int a = pr == 0 ? 0 : 1 + (pr - 1 + round) % (qe - 1);
+        int qi = qe - 1 - pr;
+        int c = qi == 0 ? 0 : 1 + (qi - 1 + round) % (qe - 1);
+        if (a >= q || c >= q) continue;
+        if (a > c) { int t = a; a = c; c = t; }
+        R al = 0, be = 0;
+        cplx<R> g(0, 0);
+        for (int rr = 0; rr < NC; ++rr) {
+          const R* src = slots + ((size_t)(buf * NC + rr) * npairs + pr) * 4;
+          al += src[0];
+          be += src[1];
+          g.re += src[2];
+          g.im += src[3];
+        }
+        R ag = sqrt(abs2(g));
+        if (!(al > R(0) && be > R(0)) || !(ag > tol * sqrt(al) * sqrt(be))) continue;
+        cplx<R> ph(g.re / ag, g.im / ag);
+        R zeta = (be - al) / (R(2) * ag);
+        R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+        R cs = R(1) / sqrt(R(1) + t * t);
+        R sn = cs * t;
+        cplx<R> f1 = sn * conjg(ph), f2 = sn * ph;
+        cplx<R>* ga = G + (size_t)a * chunk;
+        cplx<R>* gc = G + (size_t)c * chunk;
+        for (int i = lane; i < nr; i += 32) {
+          cplx<R> x = ga[i], y = gc[i];
+          ga[i] = cs * x - f1 * y;
+          gc[i] = f2 * x + cs * y;
+        }
+        cplx<R>* va = V + (size_t)a * chunkv;
+        cplx<R>* vc = V + (size_t)c * chunkv;
+        for (int i = lane; i < nv; i += 32) {
+          cplx<R> x = va[i], y = vc[i];
+          va[i] = cs * x - f1 * y;
+          vc[i] = f2 * x + cs * y;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    const int any = s_rot;  // identical in every CTA: the decisions come from identical totals
+    __syncthreads();
+    if (!any) {
+      ++sweep;
+      break;
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+  // column norms: local partial sums exchanged, then summed in rank order
+  for (int c = warp; c < q; c += nwarps) {
+    R sacc = 0;
+    for (int i = lane; i < nr; i += 32) sacc += abs2(G[(size_t)c * chunk + i]);
+    sacc = warp_sum(sacc);
+    if (lane < NC) cluster.map_shared_rank(nsum, lane)[rank * q + c] = sacc;
+  }
+  cluster.sync();
+  for (int c = threadIdx.x; c < q; c += blockDim.x) {
+    R sacc = 0;
+    for (int rr = 0; rr < NC; ++rr) sacc += nsum[rr * q + c];
+    norms[c] = sqrt(sacc);
+  }
+  __syncthreads();
+  for (int c = warp; c < q; c += nwarps) {
+    R v = norms[c];
+    int rk = 0;
+    for (int i = 0; i < q; ++i) {
+      R u = norms[i];
+      rk += (u > v) || (u == v && i < c);
+    }
+    if (rank == 0 && lane == 0) sigma_out[rk] = v;
+    for (int i = lane; i < nv; i += 32) Vs_out[(size_t)(v0 + i) * q + rk] = V[(size_t)c * chunkv + i];
+    if (Us_out) {
+      R f = v > (sizeof(R) == 8 ? R(DBL_MIN) : R(FLT_MIN)) * R(4) ? R(1) / v : R(0);
+      for (int i = lane; i < nr; i += 32) {
+        cplx<R> g = G[(size_t)c * chunk + i];
+        Us_out[(size_t)(r0 + i) * q + rk] = cplx<R>(g.re * f, g.im * f);
+      }
+    }
+  }
+  // keep every CTA's shared memory alive until all remote writes are done
+  cluster.sync();
+}
+
 }  // namespace
 
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum
@@ -699,3 +868,65 @@ template size_t qtt_jacobi_smem_bytes<double>(int, int);
 template size_t qtt_jacobi_smem_bytes<float>(int, int);
 template int qtt_jacobi_smem<double>(const zc*, zc*, double*, zc*, zc*, int, int, int, int*, cudaStream_t);
 template int qtt_jacobi_smem<float>(const cc*, cc*, float*, cc*, cc*, int, int, int, int*, cudaStream_t);
+
+template <class R, int NC>
+static size_t jacobi_cluster_bytes(int p, int q) {
+  const int qe = q + (q & 1);
+  const int chunk = (p + NC - 1) / NC, chunkv = (q + NC - 1) / NC;
+  size_t off = (size_t)(2 * NC * (qe / 2) * 4 + NC * q + q) * sizeof(R);
+  off = (off + 15) & ~(size_t)15;
+  return off + (size_t)q * (chunk + chunkv) * sizeof(cplx<R>);
+}
+
+template <class R, int NC>
+static int launch_jacobi_cluster(const cplx<R>* G, R* sigma, cplx<R>* Vs, cplx<R>* Us, int p, int q, int max_sweeps,
+                                 int* sweeps, cudaStream_t s) {
+  const size_t sm = jacobi_cluster_bytes<R, NC>(p, q);
+  if (qtt_allow_max_smem((const void*)jacobi_cluster_kernel<R, NC>) != QTT_OK) return QTT_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC, 1, 1);
+  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = NC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<R, NC>, G, sigma, Vs, Us, p, q, max_sweeps, sweeps) !=
+      cudaSuccess)
+    return QTT_ERR_CUDA;
+  return QTT_OK;
+}
+
+// Shared-memory bytes per CTA of the cluster Jacobi for the given cluster size
+// (0 if that size is not compiled).
+template <class R>
+size_t qtt_jacobi_cluster_bytes(int p, int q, int nc) {
+  switch (nc) {
+    case 4: return jacobi_cluster_bytes<R, 4>(p, q);
+    case 8: return jacobi_cluster_bytes<R, 8>(p, q);
+    default: return 0;
+  }
+}
+
+template <class R>
+int qtt_jacobi_cluster(const cplx<R>* G, R* sigma, cplx<R>* Vsorted, cplx<R>* Usorted, int p, int q, int nc,
+                       int max_sweeps, int* sweeps, cudaStream_t s) {
+  if (q <= 0) return QTT_OK;
+  int st;
+  switch (nc) {
+    case 4: st = launch_jacobi_cluster<R, 4>(G, sigma, Vsorted, Usorted, p, q, max_sweeps, sweeps, s); break;
+    case 8: st = launch_jacobi_cluster<R, 8>(G, sigma, Vsorted, Usorted, p, q, max_sweeps, sweeps, s); break;
+    default: return QTT_ERR_ARG;
+  }
+  if (st) return st;
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template size_t qtt_jacobi_cluster_bytes<double>(int, int, int);
+template size_t qtt_jacobi_cluster_bytes<float>(int, int, int);
+template int qtt_jacobi_cluster<double>(const zc*, double*, zc*, zc*, int, int, int, int, int*, cudaStream_t);
+template int qtt_jacobi_cluster<float>(const cc*, float*, cc*, cc*, int, int, int, int, int*, cudaStream_t);
