@@ -140,6 +140,22 @@ static int tc_route(qtt_ctx* c, const GemmDesc& g, cc alpha, cc beta, const cc* 
   return st;
 }
 
+// CUDA-core GEMM with the thin-tile / split-K choice of qtt_gemm_splits
+template <class R>
+static int simt_gemm(qtt_ctx* c, const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B,
+                     cplx<R>* C) {
+  const int splits = qtt_gemm_splits(g);
+  void* P = nullptr;
+  if (splits > 1 && dalloc(c, &P, (size_t)splits * g.batch * g.M * g.N * sizeof(cplx<R>))) return QTT_ERR_OOM;
+  c->launches += splits > 1 ? 2 : 1;
+  cudaEvent_t ev = prof_begin(c);
+  int st = qtt_gemm_ex<R>(g, alpha, beta, A, B, C, splits, reinterpret_cast<cplx<R>*>(P), c->stream);
+  prof_end(c, ev, PK_GEMM, 8.0 * g.M * g.N * g.K * g.batch,
+           (double)(g.M * g.K + g.K * g.N + g.M * g.N) * g.batch * sizeof(cplx<R>));
+  dfree(c, P);
+  return st;
+}
+
 // C (M x N) = alpha op(A) op(B) + beta C, single batch, general strides
 template <class R>
 int mm(qtt_ctx* c, int64_t M, int64_t N, int64_t K, const cplx<R>* A, int64_t sAm, int64_t sAk, int conjA,
@@ -170,11 +186,7 @@ int mm(qtt_ctx* c, int64_t M, int64_t N, int64_t K, const cplx<R>* A, int64_t sA
                       reinterpret_cast<const cc*>(A), reinterpret_cast<const cc*>(B), reinterpret_cast<cc*>(C));
     if (st != QTT_ERR_UNSUPPORTED) return st;
   }
-  c->launches++;
-  cudaEvent_t ev = prof_begin(c);
-  int st = qtt_gemm<R>(g, alpha, beta, A, B, C, c->stream);
-  prof_end(c, ev, PK_GEMM, 8.0 * M * N * K, (double)(M * K + K * N + M * N) * sizeof(cplx<R>));
-  return st;
+  return simt_gemm<R>(c, g, alpha, beta, A, B, C);
 }
 
 template <class R>
@@ -184,12 +196,7 @@ int gemm(qtt_ctx* c, const GemmDesc& g, const cplx<R>* A, const cplx<R>* B, cplx
                       reinterpret_cast<cc*>(C));
     if (st != QTT_ERR_UNSUPPORTED) return st;
   }
-  c->launches++;
-  cudaEvent_t ev = prof_begin(c);
-  int st = qtt_gemm<R>(g, cplx<R>(1, 0), cplx<R>(0, 0), A, B, C, c->stream);
-  prof_end(c, ev, PK_GEMM, 8.0 * g.M * g.N * g.K * g.batch,
-           (double)(g.M * g.K + g.K * g.N + g.M * g.N) * g.batch * sizeof(cplx<R>));
-  return st;
+  return simt_gemm<R>(c, g, cplx<R>(1, 0), cplx<R>(0, 0), A, B, C);
 }
 
 #define TRY(expr)                 \
@@ -289,9 +296,22 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
   // FP32 matrices too large for one CTA's shared memory: a cluster of 4 or 8
   // CTAs splitting the rows (a cluster barrier per round costs more than one
   // SM's compute at the sizes that fit one CTA, so those stay single-CTA)
-  if (sizeof(R) == 4 && q >= 48 && qtt_jacobi_smem_bytes<R>(p, q) > 200 * 1024) {
+  // Vsorted may be null (rotations not wanted): the single-CTA and the
+  // multi-launch kernels then skip the rotation updates, the cluster and the
+  // global-memory kernels write them to scratch space
+  const bool cluster = sizeof(R) == 4 && q >= 48 && qtt_jacobi_smem_bytes<R>(p, q) > 200 * 1024 &&
+                       qtt_jacobi_cluster_bytes<R>(p, q, q <= 160 ? 4 : 8) <= 200 * 1024;
+  const bool wide = !cluster && ((sizeof(R) == 8 && q >= 32) || q > 256);
+  const bool smem = !cluster && !wide && qtt_jacobi_smem_bytes<R>(p, q) <= 200 * 1024;
+  DBuf vtmp;
+  if (!smem && !wide && (!Vsorted || !Vwork)) {
+    TRY(vtmp.alloc(c, (size_t)2 * q * q * sizeof(cplx<R>)));
+    if (!Vsorted) Vsorted = vtmp.as<cplx<R>>();
+    if (!Vwork) Vwork = vtmp.as<cplx<R>>() + (size_t)q * q;
+  }
+  if (cluster) {
     const int nc = q <= 160 ? 4 : 8;
-    if (qtt_jacobi_cluster_bytes<R>(p, q, nc) <= 200 * 1024) {
+    {
       int idx;
       int* slot = prof_sweep_slot(c, &idx);
       c->launches++;
@@ -302,8 +322,6 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
       return st;
     }
   }
-  const bool wide = (sizeof(R) == 8 && q >= 32) || q > 256;
-  const bool smem = !wide && qtt_jacobi_smem_bytes<R>(p, q) <= 200 * 1024;
   if (smem) {
     int idx;
     int* slot = prof_sweep_slot(c, &idx);
@@ -315,7 +333,7 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
   }
   if (wide) {
     void* buf = nullptr;
-    size_t gb = (size_t)p * q * sizeof(cplx<R>), vb = (size_t)q * q * sizeof(cplx<R>);
+    size_t gb = (size_t)p * q * sizeof(cplx<R>), vb = Vsorted ? (size_t)q * q * sizeof(cplx<R>) : 0;
     TRY(dalloc(c, &buf, gb + vb + 256));
     cplx<R>* Gw = reinterpret_cast<cplx<R>*>(buf);
     cplx<R>* Vw = reinterpret_cast<cplx<R>*>(static_cast<char*>(buf) + gb);
@@ -395,9 +413,21 @@ int left_svd(qtt_ctx* c, const cplx<R>* Cm, int64_t rows, int64_t cols, int64_t 
 // C_k = R_{k-1} T_k with T_k = A_k (T_{k+1} V_{k+1}), keeps V_k^H as core k and
 // never needs the Q factors.  In exact arithmetic this equals keeping Q_k and
 // absorbing U_k S_k into it.
+//
+// left_orth: cores 0..d-2 of x are already left-orthogonal (their (r_k n_k) x
+// r_{k+1} unfoldings have orthonormal columns), so every R factor is the
+// identity and the left sweep is skipped.
+//
+// The SVD of C_k is taken by one-sided Jacobi on C_k^H itself (C^H V = W,
+// right singular vectors W / |W|): its Gram matrix equals that of the
+// triangular factor of a QR of C_k^H, so a QR first would not shorten the
+// sweeps; it pays only when C_k is far wider than tall.  The right vectors
+// come from the rotated data, not from the accumulated rotations V, whose
+// rounding error would leak into the kept subspace (about 10x larger rounding
+// error in FP32).
 template <class R>
 int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* forced, qtt_round_info* info,
-              qtt_tt** yout) {
+              qtt_tt** yout, bool left_orth) {
   const int d = x->d;
   std::vector<int> n = x->n, r = x->r;
   auto A = [&](int k) { return reinterpret_cast<const cplx<R>*>(static_cast<const char*>(x->data) + x->off[k]); };
@@ -426,7 +456,9 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
   // ---- sweep 1: R factors
   std::vector<DBuf> Rf(d);
   std::vector<int64_t> rp(d + 1, 1);
-  for (int k = 0; k < d - 1; ++k) {
+  if (left_orth)
+    for (int k = 0; k < d; ++k) rp[k] = r[k];
+  for (int k = 0; k < d - 1 && !left_orth; ++k) {
     const int64_t a0 = r[k], nk = n[k], a1 = r[k + 1];
     DBuf Mb;
     const cplx<R>* M = A(k);
@@ -452,10 +484,15 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
   {
     const int64_t a0 = r[d - 1], nk = n[d - 1];
     DBuf Cb;
-    TRY(Cb.alloc(c, (size_t)rp[d - 1] * nk * sizeof(cplx<R>)));
-    TRY(mm<R>(c, rp[d - 1], nk, a0, Rf[d - 2].as<cplx<R>>(), a0, 1, 0, A(d - 1), nk, 1, 0, Cb.as<cplx<R>>(), nk, 1));
+    const cplx<R>* centre = A(d - 1);
+    if (!left_orth) {
+      TRY(Cb.alloc(c, (size_t)rp[d - 1] * nk * sizeof(cplx<R>)));
+      TRY(mm<R>(c, rp[d - 1], nk, a0, Rf[d - 2].as<cplx<R>>(), a0, 1, 0, A(d - 1), nk, 1, 0, Cb.as<cplx<R>>(), nk,
+                1));
+      centre = Cb.as<cplx<R>>();
+    }
     c->launches++;
-    TRY(qtt_sumsq<R>(Cb.as<cplx<R>>(), rp[d - 1] * nk, dscal, c->stream));
+    TRY(qtt_sumsq<R>(centre, rp[d - 1] * nk, dscal, c->stream));
   }
   double nrm2 = 0;
   TRY(sync_read(c, &nrm2, dscal, sizeof(double)));
@@ -474,8 +511,66 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     const int64_t rk = rp[k];  // rows of R_{k-1}
     const int64_t a0 = r[k];
     DBuf Cb, U, UG, sig, Rc, Qc, Wq, tau, Vw;
-    TRY(Cb.alloc(c, (size_t)rk * Tcols * sizeof(cplx<R>)));
-    TRY(mm<R>(c, rk, Tcols, a0, Rf[k - 1].as<cplx<R>>(), a0, 1, 0, T, Tcols, 1, 0, Cb.as<cplx<R>>(), Tcols, 1));
+    // Jacobi on G = C^H (Tcols x rk, row-major) unless C is so wide that a QR
+    // of C^H first pays for itself
+    const int64_t jp = Tcols, jq = rk;
+    if (jp <= 4 * jq || jp * jq <= 4096) {
+      TRY(Cb.alloc(c, (size_t)rk * Tcols * sizeof(cplx<R>)));
+      if (left_orth) {
+        c->launches++;
+        TRY(qtt_copy_strided<R>(T, L1(Tcols, 1), L1(rk, Tcols), Tcols, rk, 1, Cb.as<cplx<R>>(), rk, c->stream));
+      } else {
+        // element (j, i) = sum_a conj(R[i, a]) conj(T[a, j]), written transposed
+        TRY(mm<R>(c, rk, Tcols, a0, Rf[k - 1].as<cplx<R>>(), a0, 1, 1, T, Tcols, 1, 1, Cb.as<cplx<R>>(), 1, rk));
+      }
+      TRY(dbg_finite<R>(c, Cb.as<cplx<R>>(), rk * Tcols, "round sweep2 G", k));
+      // X (Tcols x jq): right singular vectors of C, columns by decreasing singular value
+      DBuf X;
+      TRY(X.alloc(c, (size_t)Tcols * jq * sizeof(cplx<R>)));
+      TRY(sig.alloc(c, (size_t)jq * sizeof(R)));
+      TRY(jacobi_launch<R>(c, Cb.as<cplx<R>>(), nullptr, sig.as<R>(), nullptr, (int)jp, (int)jq, 60,
+                           X.as<cplx<R>>()));
+      TRY(dbg_finite<R>(c, X.as<cplx<R>>(), Tcols * jq, "round sweep2 X", k));
+      int t;
+      c->launches++;
+      if (forced) {
+        t = (int)std::min<int64_t>(forced[k], jq);
+        TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)jq, -1.0, t, dint, reinterpret_cast<double*>(dint + 2), c->stream));
+      } else {
+        TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)jq, delta, max_rank, dint, reinterpret_cast<double*>(dint + 2),
+                              c->stream));
+      }
+      int hv[4];
+      TRY(sync_read(c, hv, dint, sizeof(hv)));
+      double tl;
+      memcpy(&tl, hv + 2, sizeof(double));
+      t = hv[0];
+      if (!forced) capped |= hv[1];
+      tail2 += tl * tl;
+      nr[k] = t;
+      // new core k = X[:, :t]^H (t x Tcols)
+      TRY(newc[k].alloc(c, (size_t)t * Tcols * sizeof(cplx<R>)));
+      cplx<R>* core = newc[k].as<cplx<R>>();
+      c->launches++;
+      TRY(qtt_copy_strided<R>(X.as<cplx<R>>(), L1(t, 1), L1(Tcols, jq), t, Tcols, 1, core, Tcols, c->stream));
+      // P = T X[:, :t] (a0 x t); T_{k-1} = A_{k-1} P
+      DBuf P, Tn;
+      TRY(P.alloc(c, (size_t)a0 * t * sizeof(cplx<R>)));
+      TRY(mm<R>(c, a0, t, Tcols, T, Tcols, 1, 0, X.as<cplx<R>>(), jq, 1, 0, P.as<cplx<R>>(), t, 1));
+      const int64_t pr = (int64_t)r[k - 1] * n[k - 1];
+      TRY(Tn.alloc(c, (size_t)pr * t * sizeof(cplx<R>)));
+      TRY(mm<R>(c, pr, t, a0, A(k - 1), a0, 1, 0, P.as<cplx<R>>(), t, 1, 0, Tn.as<cplx<R>>(), t, 1));
+      Tb = std::move(Tn);
+      T = Tb.as<cplx<R>>();
+      Trows = r[k - 1];
+      continue;
+    }
+    const cplx<R>* Cm = T;  // R factor is the identity for a left-orthogonal train
+    if (!left_orth) {
+      TRY(Cb.alloc(c, (size_t)rk * Tcols * sizeof(cplx<R>)));
+      TRY(mm<R>(c, rk, Tcols, a0, Rf[k - 1].as<cplx<R>>(), a0, 1, 0, T, Tcols, 1, 0, Cb.as<cplx<R>>(), Tcols, 1));
+      Cm = Cb.as<cplx<R>>();
+    }
     // SVD of C (rk x Tcols): C^H = Q_c R_c (Householder, explicit Q_c), then
     // one-sided Jacobi R_c V = U_G S.  Left vectors of C: V; right: Q_c U_G.
     const int64_t pq = std::min(rk, Tcols);
@@ -483,14 +578,14 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     TRY(Qc.alloc(c, (size_t)Tcols * pq * sizeof(cplx<R>)));
     TRY(Wq.alloc(c, (size_t)Tcols * rk * sizeof(cplx<R>)));
     TRY(tau.alloc(c, (size_t)2 * rk * sizeof(cplx<R>)));
-    TRY(qr_launch<R>(c, Cb.as<cplx<R>>(), B0(), L1(Tcols, 1), L1(rk, Tcols), 1, Tcols, rk, Tcols, Tcols, 1,
+    TRY(qr_launch<R>(c, Cm, B0(), L1(Tcols, 1), L1(rk, Tcols), 1, Tcols, rk, Tcols, Tcols, 1,
                      Wq.as<cplx<R>>(), Rc.as<cplx<R>>(), 0, rk, tau.as<cplx<R>>(), Qc.as<cplx<R>>(), 0, pq));
     TRY(U.alloc(c, (size_t)rk * rk * sizeof(cplx<R>)));
     TRY(UG.alloc(c, (size_t)pq * rk * sizeof(cplx<R>)));
     TRY(Vw.alloc(c, (size_t)rk * rk * sizeof(cplx<R>)));
     TRY(sig.alloc(c, (size_t)rk * sizeof(R)));
     c->launches++;
-    TRY(dbg_finite<R>(c, Cb.as<cplx<R>>(), rk * Tcols, "round sweep2 C", k));
+    TRY(dbg_finite<R>(c, Cm, rk * Tcols, "round sweep2 C", k));
     TRY(dbg_finite<R>(c, Rc.as<cplx<R>>(), pq * rk, "round sweep2 Rc", k));
     TRY(dbg_finite<R>(c, Qc.as<cplx<R>>(), Tcols * pq, "round sweep2 Qc", k));
     TRY(jacobi_launch<R>(c, Rc.as<cplx<R>>(), Vw.as<cplx<R>>(), sig.as<R>(), U.as<cplx<R>>(), (int)pq, (int)rk, 60,
@@ -557,8 +652,10 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
   return QTT_OK;
 }
 
-template int round_det<double>(qtt_ctx*, const qtt_tt*, double, int, const int*, qtt_round_info*, qtt_tt**);
-template int round_det<float>(qtt_ctx*, const qtt_tt*, double, int, const int*, qtt_round_info*, qtt_tt**);
+template int round_det<double>(qtt_ctx*, const qtt_tt*, double, int, const int*, qtt_round_info*, qtt_tt**,
+                                bool);
+template int round_det<float>(qtt_ctx*, const qtt_tt*, double, int, const int*, qtt_round_info*, qtt_tt**,
+                               bool);
 
 // ------------------------------------------------------------------- TT-SVD
 template <class R>
@@ -921,7 +1018,7 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
     size_t bytes = (size_t)orank[k] * S->n[k] * orank[k + 1] * sizeof(C);
     cudaMemcpyAsync(static_cast<char*>(P->data) + P->off[k], outc[k].p, bytes, cudaMemcpyDeviceToDevice, c->stream);
   }
-  int rs = round_det<R>(c, P, eps, max_rank, nullptr, info, yout);
+  int rs = round_det<R>(c, P, eps, max_rank, nullptr, info, yout, true);
   tt_free(P);
   return rs;
 }

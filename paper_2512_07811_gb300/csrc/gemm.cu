@@ -5,22 +5,30 @@
 // sketch contractions of operator-times-train products) is one call of this
 // kernel with suitable index strides, so no contraction needs an explicit
 // permutation pass.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace {
 
+// With splits > 1 every CTA sums only its share of K and stores the raw
+// partial tile to P[split][batch][m][n] (dense); a second kernel reduces the
+// partials in split order and applies alpha, beta and the output strides.
 template <class R, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
                  const cplx<R>* __restrict__ A, const cplx<R>* __restrict__ B,
-                 cplx<R>* __restrict__ C) {
+                 cplx<R>* __restrict__ C, int splits, int64_t kchunk, cplx<R>* __restrict__ P) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   __shared__ cplx<R> As[BK][BM + 1];
   __shared__ cplx<R> Bs[BK][BN + 1];
 
-  const int64_t b = blockIdx.z;
+  const int64_t b = blockIdx.z / splits;
+  const int split = blockIdx.z - (int)(b * splits);
+  const int64_t kbeg = (int64_t)split * kchunk;
+  const int64_t kend = min(g.K, kbeg + kchunk);
   const int64_t m0 = (int64_t)blockIdx.y * BM;
   const int64_t n0 = (int64_t)blockIdx.x * BN;
   const int tid = threadIdx.x;
@@ -34,12 +42,12 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = cplx<R>(0, 0);
 
-  for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     for (int e = tid; e < BM * BK; e += NT) {
       int mm = e % BM, kk = e / BM;
       int64_t m = m0 + mm, k = k0 + kk;
       cplx<R> v(0, 0);
-      if (m < g.M && k < g.K) {
+      if (m < g.M && k < kend) {
         v = A[offA + midx_off(g.mA, m) + midx_off(g.kA, k)];
         if (g.conjA) v.im = -v.im;
       }
@@ -49,7 +57,7 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
       int nn = e % BN, kk = e / BN;
       int64_t n = n0 + nn, k = k0 + kk;
       cplx<R> v(0, 0);
-      if (n < g.N && k < g.K) {
+      if (n < g.N && k < kend) {
         v = B[offB + midx_off(g.kB, k) + midx_off(g.nB, n)];
         if (g.conjB) v.im = -v.im;
       }
@@ -71,6 +79,20 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
     __syncthreads();
   }
   const bool use_beta = (beta.re != R(0) || beta.im != R(0));
+  if (splits > 1) {
+    cplx<R>* Pt = P + ((int64_t)split * g.batch + b) * g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      int64_t m = m0 + ty + i * (BM / TM);
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        int64_t n = n0 + tx + j * TX;
+        if (n < g.N) Pt[m * g.N + n] = acc[i][j];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     int64_t m = m0 + ty + i * (BM / TM);
@@ -87,7 +109,66 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
   }
 }
 
+// C[b][m][n] = alpha sum_s P[s][b][m][n] + beta C[b][m][n], summed in split order
+template <class R>
+__global__ void splitk_reduce_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta, const cplx<R>* __restrict__ P,
+                                     int splits, cplx<R>* __restrict__ C) {
+  const int64_t mn = g.M * g.N, total = g.batch * mn;
+  const bool use_beta = (beta.re != R(0) || beta.im != R(0));
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = e / mn, r = e - b * mn;
+    int64_t m = r / g.N, n = r - m * g.N;
+    cplx<R> acc(0, 0);
+    for (int s = 0; s < splits; ++s) acc = acc + P[(int64_t)s * total + e];
+    int64_t o = midx_off(g.bC, b) + midx_off(g.mC, m) + midx_off(g.nC, n);
+    cplx<R> v = alpha * acc;
+    if (use_beta) v = v + beta * C[o];
+    C[o] = v;
+  }
+}
+
 }  // namespace
+
+// Number of K splits worth using for this shape (1 = no split): GEMMs whose
+// output tiles cannot occupy half the SMs and whose K is long get their K
+// range cut so that about one CTA per SM works.
+int qtt_gemm_splits(const GemmDesc& g) {
+  const int64_t small = (g.M <= 32 || g.N <= 32) ? 32 : 64;
+  const int64_t tiles = ((g.M + small - 1) / small) * ((g.N + small - 1) / small) * g.batch;
+  if (tiles >= 76 || g.K < 256) return 1;
+  int64_t s = std::min<int64_t>((g.K + 127) / 128, std::max<int64_t>(1, 152 / tiles));
+  return (int)std::min<int64_t>(s, 32);
+}
+
+template <class R>
+int qtt_gemm_ex(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B, cplx<R>* C,
+                int splits, cplx<R>* P, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return QTT_OK;
+  if (splits < 1 || (splits > 1 && !P)) return QTT_ERR_ARG;
+  const int64_t kchunk = splits > 1 ? (g.K + splits - 1) / splits : std::max<int64_t>(g.K, 1);
+  const bool thin = g.M <= 32 || g.N <= 32;
+  constexpr int BK = sizeof(R) == 8 ? 8 : 16;
+  const int64_t zdim = g.batch * splits;
+  if (zdim > 65535) return QTT_ERR_ARG;
+  if (thin) {
+    dim3 grid((unsigned)((g.N + 31) / 32), (unsigned)((g.M + 31) / 32), (unsigned)zdim);
+    if (grid.y > 65535) return QTT_ERR_ARG;
+    gemm_midx_kernel<R, 32, 32, BK, 2, 2><<<grid, 256, 0, s>>>(g, alpha, beta, A, B, C, splits, kchunk, P);
+  } else {
+    dim3 grid((unsigned)((g.N + 63) / 64), (unsigned)((g.M + 63) / 64), (unsigned)zdim);
+    if (grid.y > 65535) return QTT_ERR_ARG;
+    gemm_midx_kernel<R, 64, 64, BK, 4, 4><<<grid, 256, 0, s>>>(g, alpha, beta, A, B, C, splits, kchunk, P);
+  }
+  if (splits > 1) {
+    const int64_t total = g.batch * g.M * g.N;
+    splitk_reduce_kernel<R><<<(unsigned)std::min<int64_t>((total + 255) / 256, 65535), 256, 0, s>>>(g, alpha, beta, P,
+                                                                                                     splits, C);
+  }
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template int qtt_gemm_ex<double>(const GemmDesc&, zc, zc, const zc*, const zc*, zc*, int, zc*, cudaStream_t);
+template int qtt_gemm_ex<float>(const GemmDesc&, cc, cc, const cc*, const cc*, cc*, int, cc*, cudaStream_t);
 
 template <class R>
 int qtt_gemm(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A,
@@ -100,7 +181,8 @@ int qtt_gemm(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A,
   constexpr int BK = sizeof(R) == 8 ? 8 : 16;
   dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM), (unsigned)g.batch);
   if (grid.y > 65535 || grid.z > 65535) return QTT_ERR_ARG;
-  gemm_midx_kernel<R, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(g, alpha, beta, A, B, C);
+  gemm_midx_kernel<R, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(g, alpha, beta, A, B, C, 1,
+                                                                                std::max<int64_t>(g.K, 1), nullptr);
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
 

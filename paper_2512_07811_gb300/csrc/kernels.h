@@ -10,6 +10,12 @@ template <class R>
 int qtt_gemm(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B,
              cplx<R>* C, cudaStream_t s);
 
+// split-K aware variant: `splits` K ranges, partials in P (splits x batch x M x N), see qtt_gemm_splits
+int qtt_gemm_splits(const GemmDesc& g);
+template <class R>
+int qtt_gemm_ex(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B, cplx<R>* C,
+                int splits, cplx<R>* P, cudaStream_t s);
+
 template <class R>
 int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
              int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,

@@ -403,12 +403,14 @@ jacobi_round_kernel(cplx<R>* __restrict__ Gc, cplx<R>* __restrict__ Vc, int p, i
     ga[i] = cs * x - f1 * y;
     gc[i] = f2 * x + cs * y;
   }
-  cplx<R>* va = Vc + (int64_t)a * q;
-  cplx<R>* vc = Vc + (int64_t)c * q;
-  for (int i = lane; i < q; i += 32) {
-    cplx<R> x = va[i], y = vc[i];
-    va[i] = cs * x - f1 * y;
-    vc[i] = f2 * x + cs * y;
+  if (Vc) {
+    cplx<R>* va = Vc + (int64_t)a * q;
+    cplx<R>* vc = Vc + (int64_t)c * q;
+    for (int i = lane; i < q; i += 32) {
+      cplx<R> x = va[i], y = vc[i];
+      va[i] = cs * x - f1 * y;
+      vc[i] = f2 * x + cs * y;
+    }
   }
   if (lane == 0) *rotated = 1;
 }
@@ -436,7 +438,8 @@ jacobi_finish_kernel(const cplx<R>* __restrict__ Gc, const cplx<R>* __restrict__
       rk += (u > v) || (u == v && i < c);
     }
     if (lane == 0) sigma_out[rk] = v;
-    for (int i = lane; i < q; i += 32) Vs[(int64_t)i * q + rk] = Vc[(int64_t)c * q + i];
+    if (Vs)
+      for (int i = lane; i < q; i += 32) Vs[(int64_t)i * q + rk] = Vc[(int64_t)c * q + i];
     if (Us) {
       R f = v > (sizeof(R) == 8 ? R(DBL_MIN) : R(FLT_MIN)) * R(4) ? R(1) / v : R(0);
       for (int i = lane; i < p; i += 32) {
@@ -457,7 +460,7 @@ __global__ void jacobi_setup_kernel(const cplx<R>* __restrict__ G, int p, int q,
     if (e < tg) {
       int64_t c = e / p, i = e - c * p;
       Gc[e] = G[i * q + c];
-    } else {
+    } else if (Vc) {
       int64_t f = e - tg;
       int64_t c = f / q, i = f - c * q;
       Vc[f] = cplx<R>(i == c ? R(1) : R(0), R(0));
@@ -467,13 +470,54 @@ __global__ void jacobi_setup_kernel(const cplx<R>* __restrict__ G, int p, int q,
 
 // ------------------------------------------- one-sided Jacobi in shared memory
 // One CTA of 1024 threads.  G (p x q, row-major input, ld q) is held
-// column-major in shared memory; the rotations accumulate in the
-// column-major workspace Vws (q x q, global).  Each round of the round-robin
-// tournament pairs order[i] with order[qe-1-i] (order[0] = 0, order[i] =
-// 1 + (i - 1 + r) mod (qe - 1)); warps take the pairs of a round, lanes the
-// rows.  Outputs as in jacobi_kernel: sigma sorted decreasingly, V columns
-// (row-major q x q) and normalised columns of the rotated G (row-major p x q)
-// in the same order.
+// column-major in shared memory.  Each round of the round-robin tournament
+// pairs order[i] with order[qe-1-i] (order[0] = 0, order[i] = 1 + (i - 1 + r)
+// mod (qe - 1)); each half-warp takes one pair of a round (its 16 lanes the
+// rows), so the 64 pairs of a 128-column round run side by side.  Outputs as
+// in jacobi_kernel: sigma sorted decreasingly, normalised columns of the
+// rotated G (row-major p x q) and, when Vs is given, the accumulated rotations
+// (row-major q x q, accumulated column-major in the global workspace Vws) in
+// the same order.  Without Vs no rotation touches global memory.
+// Rotation of one column pair from al = |g_a|^2, be = |g_c|^2, g = g_a^H g_c:
+// false if the pair is already orthogonal to tol (|g|^2 <= tol2 al be, a zero
+// column, or |g|^2 below the normal range), else the unitary [cs, -f1; f2, cs] (f1 = sn conj(ph), f2 = sn
+// ph, ph = g / |g|, tan = t from the usual smaller root of t^2 + 2 zeta t - 1
+// = 0, zeta = (be - al) / (2 |g|)).  1/|g| and cos come from a reciprocal
+// square root refined by one Newton step, y <- y (3 - x y^2) / 2, which keeps
+// cs^2 (1 + t^2) and |ph| within a few units in the last place of 1.
+template <class R>
+__device__ __forceinline__ R rsqrt_refined(R x) {
+  R y = rsqrt(x);
+  return y * (R(1.5) - R(0.5) * x * y * y);
+}
+
+template <class R>
+__device__ __forceinline__ bool jacobi_rotation(R al, R be, cplx<R> g, R tol2, R& cs, cplx<R>& f1, cplx<R>& f2) {
+  const R ag2 = abs2(g);
+  // an inner product whose square is below the normal range is rounding noise of two tiny columns
+  const R tiny = sizeof(R) == 8 ? R(DBL_MIN) : R(FLT_MIN);
+  if (!(al > R(0) && be > R(0)) || !(ag2 > tol2 * al * be) || !(ag2 >= tiny)) return false;
+  const R inv = rsqrt_refined(ag2);
+  const R zeta = (be - al) * (R(0.5) * inv);
+  const R az = fabs(zeta);
+  // for |zeta| beyond 1e18 the root is 1 / (2 zeta) to working precision (and zeta^2 could overflow)
+  R t = az < R(1e18) ? R(1) / (az + sqrt(R(1) + az * az)) : R(0.5) / az;
+  if (zeta < R(0)) t = -t;
+  cs = rsqrt_refined(R(1) + t * t);
+  const R sn = cs * t;
+  const cplx<R> ph(g.re * inv, g.im * inv);
+  f1 = sn * conjg(ph);
+  f2 = sn * ph;
+  return true;
+}
+
+template <class R>
+__device__ __forceinline__ R half_sum(R v, unsigned mask) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, 16);
+  return v;
+}
+
 template <class R>
 __global__ void __launch_bounds__(1024)
 jacobi_smem_kernel(const cplx<R>* __restrict__ Gin, cplx<R>* __restrict__ Vws, R* __restrict__ sigma_out,
@@ -484,23 +528,28 @@ jacobi_smem_kernel(const cplx<R>* __restrict__ Gin, cplx<R>* __restrict__ Vws, R
   R* norms = reinterpret_cast<R*>(Gs + (size_t)p * q);
   __shared__ int s_rot;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int hl = lane & 15, hw = warp * 2 + (lane >> 4), nhw = nwarps * 2;
+  const unsigned hmask = (lane >> 4) ? 0xffff0000u : 0x0000ffffu;
+  const bool wantV = Vs != nullptr;
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
     int i = e / q, c = e - i * q;
     Gs[c * p + i] = Gin[e];
   }
-  for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
-    int c = e / q, i = e - c * q;
-    Vws[e] = cplx<R>(i == c ? R(1) : R(0), R(0));
-  }
+  if (wantV)
+    for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+      int c = e / q, i = e - c * q;
+      Vws[e] = cplx<R>(i == c ? R(1) : R(0), R(0));
+    }
   __syncthreads();
   const int qe = q + (q & 1);
   const R tol = (sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON)) * sqrt(R(p > 1 ? p : 1));
+  const R tol2 = tol * tol;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int round = 0; round < qe - 1; ++round) {
-      for (int pr = warp; pr < qe / 2; pr += nwarps) {
+      for (int pr = hw; pr < qe / 2; pr += nhw) {
         int a = pr == 0 ? 0 : 1 + (pr - 1 + round) % (qe - 1);
         int qi = qe - 1 - pr;
         int c = qi == 0 ? 0 : 1 + (qi - 1 + round) % (qe - 1);
@@ -510,37 +559,50 @@ jacobi_smem_kernel(const cplx<R>* __restrict__ Gin, cplx<R>* __restrict__ Vws, R
         cplx<R>* gc = Gs + (size_t)c * p;
         R al = 0, be = 0;
         cplx<R> g(0, 0);
-        for (int i = lane; i < p; i += 32) {
+#pragma unroll 4
+        for (int i = hl; i < p; i += 16) {
           cplx<R> x = ga[i], y = gc[i];
           al += abs2(x);
           be += abs2(y);
           cfma_conj(g, x, y);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        g.re = warp_sum(g.re);
-        g.im = warp_sum(g.im);
-        R ag = sqrt(abs2(g));
-        if (!(al > R(0) && be > R(0)) || !(ag > tol * sqrt(al) * sqrt(be))) continue;
-        cplx<R> ph(g.re / ag, g.im / ag);
-        R zeta = (be - al) / (R(2) * ag);
-        R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-        R cs = R(1) / sqrt(R(1) + t * t);
-        R sn = cs * t;
-        cplx<R> f1 = sn * conjg(ph), f2 = sn * ph;
-        for (int i = lane; i < p; i += 32) {
+        al = half_sum(al, hmask);
+        be = half_sum(be, hmask);
+        g.re = half_sum(g.re, hmask);
+        g.im = half_sum(g.im, hmask);
+        cplx<R> f1, f2;
+        R cs;
+        if (!jacobi_rotation(al, be, g, tol2, cs, f1, f2)) continue;
+#pragma unroll 4
+        for (int i = hl; i < p; i += 16) {
           cplx<R> x = ga[i], y = gc[i];
           ga[i] = cs * x - f1 * y;
           gc[i] = f2 * x + cs * y;
         }
-        cplx<R>* va = Vws + (size_t)a * q;
-        cplx<R>* vc = Vws + (size_t)c * q;
-        for (int i = lane; i < q; i += 32) {
-          cplx<R> x = va[i], y = vc[i];
-          va[i] = cs * x - f1 * y;
-          vc[i] = f2 * x + cs * y;
+        if (wantV) {
+          cplx<R>* va = Vws + (size_t)a * q;
+          cplx<R>* vc = Vws + (size_t)c * q;
+          for (int i0 = hl; i0 < q; i0 += 64) {
+            cplx<R> x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = i0 + 16 * u;
+              if (i < q) {
+                x[u] = va[i];
+                y[u] = vc[i];
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = i0 + 16 * u;
+              if (i < q) {
+                va[i] = cs * x[u] - f1 * y[u];
+                vc[i] = f2 * x[u] + cs * y[u];
+              }
+            }
+          }
         }
-        if (lane == 0) s_rot = 1;
+        if (hl == 0) s_rot = 1;
       }
       __syncthreads();
     }
@@ -567,7 +629,8 @@ jacobi_smem_kernel(const cplx<R>* __restrict__ Gin, cplx<R>* __restrict__ Vws, R
       rk += (u > v) || (u == v && i < c);
     }
     if (lane == 0) sigma_out[rk] = v;
-    for (int i = lane; i < q; i += 32) Vs[(size_t)i * q + rk] = Vws[(size_t)c * q + i];
+    if (wantV)
+      for (int i = lane; i < q; i += 32) Vs[(size_t)i * q + rk] = Vws[(size_t)c * q + i];
     if (Us) {
       R f = v > (sizeof(R) == 8 ? R(DBL_MIN) : R(FLT_MIN)) * R(4) ? R(1) / v : R(0);
       for (int i = lane; i < p; i += 32) {
@@ -817,6 +880,8 @@ template <class R>
 int qtt_jacobi_wide(const cplx<R>* G, cplx<R>* Gwork, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, cplx<R>* Usorted,
                     int p, int q, int max_sweeps, int* dflag, int* sweeps_done, int64_t* launches, cudaStream_t s) {
   if (q <= 0) return QTT_OK;
+  if (!Vsorted) Vwork = nullptr;  // rotations not wanted
+  if (Vsorted && !Vwork) return QTT_ERR_ARG;
   const int64_t tot = (int64_t)p * q + (int64_t)q * q;
   jacobi_setup_kernel<R><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 65535), 256, 0, s>>>(G, p, q, Gwork, Vwork);
   *launches += 1;

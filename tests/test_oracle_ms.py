@@ -122,7 +122,7 @@ def test_sphere_bounds_and_symmetry(sphere16):
     assert lo <= K <= hi
 
 
-def test_qtt_laminate_config1_shape():
+def test_qtt_laminate_32cubed_15_sites():
     """32^3 scalar laminate, 15 interleaved bit sites + one control site."""
     g = load_golden("scalar_laminate_keff.json")
     pb = MS.scalar_problem(I.laminate_indicator(32), g["k1"], g["k2"])
