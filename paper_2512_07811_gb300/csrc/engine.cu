@@ -296,15 +296,15 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
   // FP32 matrices too large for one CTA's shared memory: a cluster of 4 or 8
   // CTAs splitting the rows (a cluster barrier per round costs more than one
   // SM's compute at the sizes that fit one CTA, so those stay single-CTA)
-  // Vsorted may be null (rotations not wanted): the single-CTA and the
-  // multi-launch kernels then skip the rotation updates, the cluster and the
-  // global-memory kernels write them to scratch space
+  // Vsorted may be null (rotations not wanted): the single-CTA, cluster and
+  // multi-launch kernels then skip the rotation updates, the global-memory
+  // kernel writes them to scratch space
   const bool cluster = sizeof(R) == 4 && q >= 48 && qtt_jacobi_smem_bytes<R>(p, q) > 200 * 1024 &&
                        qtt_jacobi_cluster_bytes<R>(p, q, q <= 160 ? 4 : 8) <= 200 * 1024;
   const bool wide = !cluster && ((sizeof(R) == 8 && q >= 32) || q > 256);
   const bool smem = !cluster && !wide && qtt_jacobi_smem_bytes<R>(p, q) <= 200 * 1024;
   DBuf vtmp;
-  if (!smem && !wide && (!Vsorted || !Vwork)) {
+  if (!smem && !wide && !cluster && (!Vsorted || !Vwork)) {
     TRY(vtmp.alloc(c, (size_t)2 * q * q * sizeof(cplx<R>)));
     if (!Vsorted) Vsorted = vtmp.as<cplx<R>>();
     if (!Vwork) Vwork = vtmp.as<cplx<R>>() + (size_t)q * q;

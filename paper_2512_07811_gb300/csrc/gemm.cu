@@ -15,6 +15,15 @@ namespace {
 // With splits > 1 every CTA sums only its share of K and stores the raw
 // partial tile to P[split][batch][m][n] (dense); a second kernel reduces the
 // partials in split order and applies alpha, beta and the output strides.
+//
+// Index arithmetic: the element offsets of the tile's BM rows of A and BN
+// columns of B are computed once per CTA, those of each K-tile's BK values
+// once per tile (one tile ahead, double-buffered), so the loads do no
+// division.  Threads walk a tile along whichever index is contiguous in
+// memory (k or m for A, k or n for B) so that neighbouring threads read
+// neighbouring elements.
+QTT_HD bool midx_unit_inner(const MIdx& m) { return (m.n2 == 1 ? m.s1 : m.s2) == 1; }
+
 template <class R, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
@@ -22,8 +31,10 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
                  cplx<R>* __restrict__ C, int splits, int64_t kchunk, cplx<R>* __restrict__ P) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
+  static_assert(2 * BK <= NT, "one thread per K offset");
   __shared__ cplx<R> As[BK][BM + 1];
   __shared__ cplx<R> Bs[BK][BN + 1];
+  __shared__ int64_t rowA[BM], colB[BN], kOffA[2][BK], kOffB[2][BK];
 
   const int64_t b = blockIdx.z / splits;
   const int split = blockIdx.z - (int)(b * splits);
@@ -35,6 +46,18 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
   const int tx = tid % TX, ty = tid / TX;
 
   const int64_t offA = midx_off(g.bA, b), offB = midx_off(g.bB, b), offC = midx_off(g.bC, b);
+  for (int i = tid; i < BM; i += NT) rowA[i] = (m0 + i < g.M) ? offA + midx_off(g.mA, m0 + i) : -1;
+  for (int i = tid; i < BN; i += NT) colB[i] = (n0 + i < g.N) ? offB + midx_off(g.nB, n0 + i) : -1;
+  if (tid < BK) {
+    const int64_t k = kbeg + tid;
+    kOffA[0][tid] = k < kend ? midx_off(g.kA, k) : -1;
+  } else if (tid < 2 * BK) {
+    const int64_t k = kbeg + tid - BK;
+    kOffB[0][tid - BK] = k < kend ? midx_off(g.kB, k) : -1;
+  }
+  const bool a_kfast = midx_unit_inner(g.kA) && !midx_unit_inner(g.mA);
+  const bool b_kfast = midx_unit_inner(g.kB) && !midx_unit_inner(g.nB);
+  __syncthreads();
 
   cplx<R> acc[TM][TN];
 #pragma unroll
@@ -42,28 +65,41 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = cplx<R>(0, 0);
 
-  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+  int cur = 0;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK, cur ^= 1) {
+#pragma unroll
     for (int e = tid; e < BM * BK; e += NT) {
-      int mm = e % BM, kk = e / BM;
-      int64_t m = m0 + mm, k = k0 + kk;
+      const int mm = a_kfast ? e / BK : e % BM;
+      const int kk = a_kfast ? e % BK : e / BM;
+      const int64_t ra = rowA[mm], ka = kOffA[cur][kk];
       cplx<R> v(0, 0);
-      if (m < g.M && k < kend) {
-        v = A[offA + midx_off(g.mA, m) + midx_off(g.kA, k)];
+      if (ra >= 0 && ka >= 0) {
+        v = A[ra + ka];
         if (g.conjA) v.im = -v.im;
       }
       As[kk][mm] = v;
     }
+#pragma unroll
     for (int e = tid; e < BN * BK; e += NT) {
-      int nn = e % BN, kk = e / BN;
-      int64_t n = n0 + nn, k = k0 + kk;
+      const int nn = b_kfast ? e / BK : e % BN;
+      const int kk = b_kfast ? e % BK : e / BN;
+      const int64_t cb = colB[nn], kb = kOffB[cur][kk];
       cplx<R> v(0, 0);
-      if (n < g.N && k < kend) {
-        v = B[offB + midx_off(g.kB, k) + midx_off(g.nB, n)];
+      if (cb >= 0 && kb >= 0) {
+        v = B[cb + kb];
         if (g.conjB) v.im = -v.im;
       }
       Bs[kk][nn] = v;
     }
     __syncthreads();
+    // offsets of the next K-tile into the other buffer (read after the barrier below)
+    if (tid < BK) {
+      const int64_t k = k0 + BK + tid;
+      kOffA[cur ^ 1][tid] = k < kend ? midx_off(g.kA, k) : -1;
+    } else if (tid < 2 * BK) {
+      const int64_t k = k0 + BK + tid - BK;
+      kOffB[cur ^ 1][tid - BK] = k < kend ? midx_off(g.kB, k) : -1;
+    }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       cplx<R> a[TM], bb[TN];

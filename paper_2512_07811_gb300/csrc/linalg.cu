@@ -651,7 +651,8 @@ jacobi_smem_kernel(const cplx<R>* __restrict__ Gin, cplx<R>* __restrict__ Vws, R
 // writes them into slot [its rank] of every CTA's exchange buffer (distributed
 // shared memory, double-buffered by round parity); one cluster barrier; every
 // CTA sums the NC slots in rank order -- identical totals, hence identical
-// rotation decisions in all CTAs -- and rotates its own rows of G and V.
+// rotation decisions in all CTAs -- and rotates its own rows of G and, when
+// Vs_out is given, of V.  A half-warp takes one column pair in both steps.
 template <class R, int NC>
 __global__ void __launch_bounds__(1024)
 jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out, cplx<R>* __restrict__ Vs_out,
@@ -662,8 +663,9 @@ jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int qe = q + (q & 1);
   const int npairs = qe / 2;
-  const int chunk = (p + NC - 1) / NC;         // G rows per CTA
-  const int chunkv = (q + NC - 1) / NC;        // V rows per CTA
+  const bool wantV = Vs_out != nullptr;
+  const int chunk = (p + NC - 1) / NC;                   // G rows per CTA
+  const int chunkv = wantV ? (q + NC - 1) / NC : 0;      // V rows per CTA
   const int r0 = rank * chunk, r1 = min(p, r0 + chunk);
   const int v0 = rank * chunkv, v1 = min(q, v0 + chunkv);
   const int nr = max(r1 - r0, 0), nv = max(v1 - v0, 0);
@@ -677,6 +679,8 @@ jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out
   cplx<R>* V = G + (size_t)q * chunk;
   __shared__ int s_rot;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int hl = lane & 15, hw = warp * 2 + (lane >> 4), nhw = nwarps * 2;
+  const unsigned hmask = (lane >> 4) ? 0xffff0000u : 0x0000ffffu;
   for (int e = threadIdx.x; e < q * chunk; e += blockDim.x) {
     int c = e / chunk, i = e - c * chunk;
     G[e] = (r0 + i < p) ? Gin[(int64_t)(r0 + i) * q + c] : cplx<R>(0, 0);
@@ -687,14 +691,15 @@ jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out
   }
   cluster.sync();
   const R tol = (sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON)) * sqrt(R(p > 1 ? p : 1));
+  const R tol2 = tol * tol;
   int sweep = 0, round_count = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int round = 0; round < qe - 1; ++round, ++round_count) {
       const int buf = round_count & 1;
-      // 1. partial inner products of this round's pairs over the local rows
-      for (int pr = warp; pr < npairs; pr += nwarps) {
+      // 1. partial inner products of this round's pairs over the local rows (a half-warp per pair)
+      for (int pr = hw; pr < npairs; pr += nhw) {
         int a = pr == 0 ? 0 : 1 + (pr - 1 + round) % (qe - 1);
         int qi = qe - 1 - pr;
         int c = qi == 0 ? 0 : 1 + (qi - 1 + round) % (qe - 1);
@@ -704,19 +709,20 @@ jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out
           if (a > c) { int t = a; a = c; c = t; }
           const cplx<R>* ga = G + (size_t)a * chunk;
           const cplx<R>* gc = G + (size_t)c * chunk;
-          for (int i = lane; i < nr; i += 32) {
+#pragma unroll 4
+          for (int i = hl; i < nr; i += 16) {
             cplx<R> x = ga[i], y = gc[i];
             al += abs2(x);
             be += abs2(y);
             cfma_conj(g, x, y);
           }
-          al = warp_sum(al);
-          be = warp_sum(be);
-          g.re = warp_sum(g.re);
-          g.im = warp_sum(g.im);
+          al = half_sum(al, hmask);
+          be = half_sum(be, hmask);
+          g.re = half_sum(g.re, hmask);
+          g.im = half_sum(g.im, hmask);
         }
-        if (lane < NC) {
-          R* dst = cluster.map_shared_rank(slots, lane) + ((size_t)(buf * NC + rank) * npairs + pr) * 4;
+        if (hl < NC) {
+          R* dst = cluster.map_shared_rank(slots, hl) + ((size_t)(buf * NC + rank) * npairs + pr) * 4;
           dst[0] = al;
           dst[1] = be;
           dst[2] = g.re;
@@ -725,7 +731,7 @@ jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out
       }
       cluster.sync();
       // 2. totals (same order in every CTA) and the rotation of the local rows
-      for (int pr = warp; pr < npairs; pr += nwarps) {
+      for (int pr = hw; pr < npairs; pr += nhw) {
         int a = pr == 0 ? 0 : 1 + (pr - 1 + round) % (qe - 1);
         int qi = qe - 1 - pr;
         int c = qi == 0 ? 0 : 1 + (qi - 1 + round) % (qe - 1);
@@ -733,6 +739,7 @@ jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out
         if (a > c) { int t = a; a = c; c = t; }
         R al = 0, be = 0;
         cplx<R> g(0, 0);
+#pragma unroll
         for (int rr = 0; rr < NC; ++rr) {
           const R* src = slots + ((size_t)(buf * NC + rr) * npairs + pr) * 4;
           al += src[0];
@@ -740,29 +747,27 @@ jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out
           g.re += src[2];
           g.im += src[3];
         }
-        R ag = sqrt(abs2(g));
-        if (!(al > R(0) && be > R(0)) || !(ag > tol * sqrt(al) * sqrt(be))) continue;
-        cplx<R> ph(g.re / ag, g.im / ag);
-        R zeta = (be - al) / (R(2) * ag);
-        R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-        R cs = R(1) / sqrt(R(1) + t * t);
-        R sn = cs * t;
-        cplx<R> f1 = sn * conjg(ph), f2 = sn * ph;
+        cplx<R> f1, f2;
+        R cs;
+        if (!jacobi_rotation(al, be, g, tol2, cs, f1, f2)) continue;
         cplx<R>* ga = G + (size_t)a * chunk;
         cplx<R>* gc = G + (size_t)c * chunk;
-        for (int i = lane; i < nr; i += 32) {
+#pragma unroll 4
+        for (int i = hl; i < nr; i += 16) {
           cplx<R> x = ga[i], y = gc[i];
           ga[i] = cs * x - f1 * y;
           gc[i] = f2 * x + cs * y;
         }
-        cplx<R>* va = V + (size_t)a * chunkv;
-        cplx<R>* vc = V + (size_t)c * chunkv;
-        for (int i = lane; i < nv; i += 32) {
-          cplx<R> x = va[i], y = vc[i];
-          va[i] = cs * x - f1 * y;
-          vc[i] = f2 * x + cs * y;
+        if (wantV) {
+          cplx<R>* va = V + (size_t)a * chunkv;
+          cplx<R>* vc = V + (size_t)c * chunkv;
+          for (int i = hl; i < nv; i += 16) {
+            cplx<R> x = va[i], y = vc[i];
+            va[i] = cs * x - f1 * y;
+            vc[i] = f2 * x + cs * y;
+          }
         }
-        if (lane == 0) s_rot = 1;
+        if (hl == 0) s_rot = 1;
       }
       __syncthreads();
     }
@@ -796,7 +801,8 @@ jacobi_cluster_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out
       rk += (u > v) || (u == v && i < c);
     }
     if (rank == 0 && lane == 0) sigma_out[rk] = v;
-    for (int i = lane; i < nv; i += 32) Vs_out[(size_t)(v0 + i) * q + rk] = V[(size_t)c * chunkv + i];
+    if (wantV)
+      for (int i = lane; i < nv; i += 32) Vs_out[(size_t)(v0 + i) * q + rk] = V[(size_t)c * chunkv + i];
     if (Us_out) {
       R f = v > (sizeof(R) == 8 ? R(DBL_MIN) : R(FLT_MIN)) * R(4) ? R(1) / v : R(0);
       for (int i = lane; i < nr; i += 32) {
