@@ -296,6 +296,18 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
   // FP32 matrices too large for one CTA's shared memory: a cluster of 4 or 8
   // CTAs splitting the rows (a cluster barrier per round costs more than one
   // SM's compute at the sizes that fit one CTA, so those stay single-CTA)
+  // Without rotations wanted (Vsorted null) and q >= 32: the block-cyclic
+  // cluster kernel, which needs a cluster barrier only per block exchange
+  int bs = 0;
+  if (!Vsorted && qtt_jacobi_block_plan<R>(p, q, &bs)) {
+    int idx;
+    int* slot = prof_sweep_slot(c, &idx);
+    c->launches++;
+    cudaEvent_t ev = prof_begin(c);
+    int st = qtt_jacobi_block<R>(G, sigma, Usorted, p, q, max_sweeps, slot, c->stream);
+    prof_end(c, ev, PK_JACOBI, 0.0, (double)p * q * sizeof(cplx<R>) * 2.0, idx, jacobi_sweep_flops(p, q));
+    return st;
+  }
   // Vsorted may be null (rotations not wanted): the single-CTA, cluster and
   // multi-launch kernels then skip the rotation updates, the global-memory
   // kernel writes them to scratch space

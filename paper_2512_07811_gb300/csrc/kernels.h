@@ -94,3 +94,10 @@ size_t qtt_jacobi_cluster_bytes(int p, int q, int nc);
 template <class R>
 int qtt_jacobi_cluster(const cplx<R>* G, R* sigma, cplx<R>* Vsorted, cplx<R>* Usorted, int p, int q, int nc,
                        int max_sweeps, int* sweeps, cudaStream_t s);
+
+// block-cyclic one-sided Jacobi over a cluster (columns split into blocks, linalg.cu); no rotations output
+template <class R>
+int qtt_jacobi_block_plan(int p, int q, int* bs_out);
+template <class R>
+int qtt_jacobi_block(const cplx<R>* G, R* sigma, cplx<R>* Usorted, int p, int q, int max_sweeps, int* sweeps,
+                     cudaStream_t s);

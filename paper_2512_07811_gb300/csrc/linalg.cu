@@ -1001,3 +1001,274 @@ template size_t qtt_jacobi_cluster_bytes<double>(int, int, int);
 template size_t qtt_jacobi_cluster_bytes<float>(int, int, int);
 template int qtt_jacobi_cluster<double>(const zc*, double*, zc*, zc*, int, int, int, int, int*, cudaStream_t);
 template int qtt_jacobi_cluster<float>(const cc*, float*, cc*, cc*, int, int, int, int, int*, cudaStream_t);
+
+// ------------------------------------- block-cyclic one-sided Jacobi (cluster)
+// Columns split, not rows: the q columns (padded with zero columns to
+// 2*NC*bs, bs even) form NB = 2*NC blocks of bs whole columns, and CTA i of
+// the cluster holds the blocks at tournament positions i ("top") and NB-1-i
+// ("bottom"); at block-round r of a sweep position j holds block 0 (j = 0) or
+// 1 + (j - 1 + r) mod (NB - 1), the round-robin tournament of the blocks.  In
+// a block-round every CTA rotates all bs*bs cross pairs of its two blocks (bs
+// rounds of bs disjoint pairs: top column w with bottom column (w + s) mod
+// bs, one warp per pair, the top column kept in registers); in the first
+// block-round of a sweep also the pairs inside each block (bs - 1 rounds of
+// the round-robin of bs columns).  A sweep thus rotates every column pair
+// once, like the scalar orderings, but needs a cluster barrier only at the
+// NB - 1 block exchanges (each block moves one position down the tournament,
+// copied into the receiving CTA's spare slots through distributed shared
+// memory), not at every round.  NB - 1 exchanges bring every block back to
+// its starting CTA, so at a sweep boundary CTA i holds blocks i and NB-1-i.
+// Rotation parameters and the stopping rule are those of the other Jacobi
+// kernels; the rotations are not accumulated (callers that need V use the
+// other kernels).  Outputs: sigma sorted decreasingly and the normalised
+// rotated columns (row-major p x q) in the same order.
+template <class R, int RPL>
+__device__ __forceinline__ bool warp_pair_rotate(cplx<R> (&x)[RPL], cplx<R> (&y)[RPL], R tol2) {
+  R al = 0, be = 0;
+  cplx<R> g(0, 0);
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    al += abs2(x[u]);
+    be += abs2(y[u]);
+    cfma_conj(g, x[u], y[u]);
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  g.re = warp_sum(g.re);
+  g.im = warp_sum(g.im);
+  cplx<R> f1, f2;
+  R cs;
+  if (!jacobi_rotation(al, be, g, tol2, cs, f1, f2)) return false;
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    const cplx<R> a = x[u], b = y[u];
+    x[u] = cs * a - f1 * b;
+    y[u] = f2 * a + cs * b;
+  }
+  return true;
+}
+
+template <class R, int RPL>
+__device__ __forceinline__ void col_load(cplx<R> (&x)[RPL], const cplx<R>* col, int p, int lane) {
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    const int i = lane + 32 * u;
+    x[u] = i < p ? col[i] : cplx<R>(0, 0);
+  }
+}
+
+template <class R, int RPL>
+__device__ __forceinline__ void col_store(const cplx<R> (&x)[RPL], cplx<R>* col, int p, int lane) {
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    const int i = lane + 32 * u;
+    if (i < p) col[i] = x[u];
+  }
+}
+
+// shared-memory bytes of jacobi_block_kernel: four block slots, all column norms, the cluster's flags
+template <class R>
+static size_t jacobi_block_bytes(int p, int bs, int nc) {
+  return (size_t)4 * bs * p * sizeof(cplx<R>) + (size_t)2 * nc * bs * sizeof(R) + 2 * nc * sizeof(int) + 16;
+}
+
+template <class R, int NC, int RPL>
+__global__ void __launch_bounds__(512, 1)
+jacobi_block_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out, cplx<R>* __restrict__ Us_out, int p,
+                    int q, int bs, int max_sweeps, int* __restrict__ sweeps_out) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  constexpr int NB = 2 * NC;
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* slots = reinterpret_cast<cplx<R>*>(smem_raw);  // [4][bs][p]
+  R* norms = reinterpret_cast<R*>(slots + (size_t)4 * bs * p);  // [NB * bs]
+  int* flags = reinterpret_cast<int*>(norms + (size_t)NB * bs);  // [2][NC]
+  __shared__ int s_rot;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int top = 0, bot = 1, in_top = 2, in_bot = 3;
+  auto col = [&](int slot, int j) { return slots + ((size_t)slot * bs + j) * p; };
+  // initial blocks: rank (top) and NB-1-rank (bottom)
+  for (int e = threadIdx.x; e < 2 * bs * p; e += blockDim.x) {
+    const int half = e / (bs * p), f = e - half * bs * p;
+    const int j = f / p, i = f - j * p;
+    const int blk = half == 0 ? rank : NB - 1 - rank;
+    const int c = blk * bs + j;
+    col(half == 0 ? top : bot, j)[i] = c < q ? Gin[(int64_t)i * q + c] : cplx<R>(0, 0);
+  }
+  if (threadIdx.x == 0) s_rot = 0;
+  cluster.sync();
+  const R tol = (sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON)) * sqrt(R(p > 1 ? p : 1));
+  const R tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int br = 0; br < NB - 1; ++br) {
+      if (br == 0) {
+        // pairs inside each block: round-robin of bs columns, warps < bs/2 on the top block
+        for (int s = 0; s + 1 < bs; ++s) {
+          const int k = w < bs / 2 ? w : w - bs / 2;
+          const int slot = w < bs / 2 ? top : bot;
+          const int a = k == 0 ? 0 : 1 + (k - 1 + s) % (bs - 1);
+          const int kk = bs - 1 - k;
+          const int c = kk == 0 ? 0 : 1 + (kk - 1 + s) % (bs - 1);
+          cplx<R> x[RPL], y[RPL];
+          col_load(x, col(slot, a), p, lane);
+          col_load(y, col(slot, c), p, lane);
+          if (warp_pair_rotate(x, y, tol2)) {
+            col_store(x, col(slot, a), p, lane);
+            col_store(y, col(slot, c), p, lane);
+            if (lane == 0) s_rot = 1;
+          }
+          __syncthreads();
+        }
+      }
+      // cross pairs: top column w (in registers) with bottom column (w + s) mod bs
+      cplx<R> x[RPL];
+      col_load(x, col(top, w), p, lane);
+      bool xr = false;
+      for (int s = 0; s < bs; ++s) {
+        const int c = (w + s) % bs;
+        cplx<R> y[RPL];
+        col_load(y, col(bot, c), p, lane);
+        if (warp_pair_rotate(x, y, tol2)) {
+          col_store(y, col(bot, c), p, lane);
+          xr = true;
+        }
+        __syncthreads();
+      }
+      if (xr) {
+        col_store(x, col(top, w), p, lane);
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+      // exchange: the block at position j moves to j - 1 (j >= 2), position 1 to NB - 1, position 0 stays
+      const int pos[2] = {rank, NB - 1 - rank};
+      const int src[2] = {top, bot};
+      for (int h = 0; h < 2; ++h) {
+        int np = pos[h] == 0 ? 0 : (pos[h] == 1 ? NB - 1 : pos[h] - 1);
+        const int dcta = np < NC ? np : NB - 1 - np;
+        const int drole = np < NC ? in_top : in_bot;  // slot indices agree in every CTA
+        cplx<R>* dst = cluster.map_shared_rank(col(drole, 0), dcta);
+        const cplx<R>* sp = col(src[h], 0);
+        for (int e = threadIdx.x; e < bs * p; e += blockDim.x) dst[e] = sp[e];
+      }
+      if (br == NB - 2 && threadIdx.x == 0) {
+        const int any = s_rot;
+        for (int rr = 0; rr < NC; ++rr) cluster.map_shared_rank(flags, rr)[(sweep & 1) * NC + rank] = any;
+      }
+      cluster.sync();
+      int t = top;
+      top = in_top;
+      in_top = t;
+      t = bot;
+      bot = in_bot;
+      in_bot = t;
+    }
+    int any = 0;
+    for (int rr = 0; rr < NC; ++rr) any |= flags[(sweep & 1) * NC + rr];
+    __syncthreads();
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    if (!any) {
+      ++sweep;
+      break;
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+  // column norms (whole columns are local), gathered in every CTA
+  for (int j = w; j < 2 * bs; j += blockDim.x >> 5) {
+    const int slot = j < bs ? top : bot;
+    const int blk = j < bs ? rank : NB - 1 - rank;
+    const cplx<R>* cp = col(slot, j < bs ? j : j - bs);
+    R sacc = 0;
+    for (int i = lane; i < p; i += 32) sacc += abs2(cp[i]);
+    sacc = warp_sum(sacc);
+    if (lane < NC) cluster.map_shared_rank(norms, lane)[blk * bs + (j < bs ? j : j - bs)] = sqrt(sacc);
+  }
+  cluster.sync();
+  const int qp = NB * bs;
+  for (int j = w; j < 2 * bs; j += blockDim.x >> 5) {
+    const int blk = j < bs ? rank : NB - 1 - rank;
+    const int c = blk * bs + (j < bs ? j : j - bs);
+    if (c >= q) continue;
+    const R v = norms[c];
+    int rk = 0;
+    for (int i = 0; i < qp; ++i) {
+      const R u = norms[i];
+      rk += (u > v) || (u == v && i < c);
+    }
+    if (lane == 0) sigma_out[rk] = v;
+    if (Us_out) {
+      const cplx<R>* cp = col(j < bs ? top : bot, j < bs ? j : j - bs);
+      const R f = v > (sizeof(R) == 8 ? R(DBL_MIN) : R(FLT_MIN)) * R(4) ? R(1) / v : R(0);
+      for (int i = lane; i < p; i += 32) {
+        const cplx<R> g = cp[i];
+        Us_out[(size_t)i * q + rk] = cplx<R>(g.re * f, g.im * f);
+      }
+    }
+  }
+}
+
+template <class R, int NC, int RPL>
+static int launch_jacobi_block(const cplx<R>* G, R* sigma, cplx<R>* Us, int p, int q, int bs, int max_sweeps,
+                               int* sweeps, cudaStream_t s) {
+  const size_t sm = jacobi_block_bytes<R>(p, bs, NC);
+  if (qtt_allow_max_smem((const void*)jacobi_block_kernel<R, NC, RPL>) != QTT_OK) return QTT_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC, 1, 1);
+  cfg.blockDim = dim3(32 * bs, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = NC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, jacobi_block_kernel<R, NC, RPL>, G, sigma, Us, p, q, bs, max_sweeps, sweeps) !=
+      cudaSuccess)
+    return QTT_ERR_CUDA;
+  return QTT_OK;
+}
+
+// Cluster size and block width of the block-cyclic Jacobi for a p x q matrix,
+// or 0 when it does not apply (q < 32, p > 512, more than 16 columns per block
+// or too much shared memory).
+template <class R>
+int qtt_jacobi_block_plan(int p, int q, int* bs_out) {
+  if (q < 32 || p < 1 || p > (sizeof(R) == 8 ? 256 : 512)) return 0;
+  const int nc = q >= 64 ? 8 : 4;
+  int bs = (q + 2 * nc - 1) / (2 * nc);
+  bs += bs & 1;
+  if (bs > 16 || jacobi_block_bytes<R>(p, bs, nc) > 200 * 1024) return 0;
+  *bs_out = bs;
+  return nc;
+}
+
+template <class R>
+int qtt_jacobi_block(const cplx<R>* G, R* sigma, cplx<R>* Usorted, int p, int q, int max_sweeps, int* sweeps,
+                     cudaStream_t s) {
+  int bs = 0;
+  const int nc = qtt_jacobi_block_plan<R>(p, q, &bs);
+  if (!nc) return QTT_ERR_UNSUPPORTED;
+  const int rpl = p <= 128 ? 4 : (p <= 256 ? 8 : 16);
+  if (sizeof(R) == 8 && rpl > 8) return QTT_ERR_UNSUPPORTED;
+  int st;
+  constexpr int RMAX = sizeof(R) == 8 ? 8 : 16;  // rows per lane: two columns of them live in registers
+  if (nc == 8)
+    st = rpl == 4 ? launch_jacobi_block<R, 8, 4>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s)
+       : rpl == 8 ? launch_jacobi_block<R, 8, 8>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s)
+                  : launch_jacobi_block<R, 8, RMAX>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s);
+  else
+    st = rpl == 4 ? launch_jacobi_block<R, 4, 4>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s)
+       : rpl == 8 ? launch_jacobi_block<R, 4, 8>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s)
+                  : launch_jacobi_block<R, 4, RMAX>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s);
+  if (st != QTT_OK) return st;
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template int qtt_jacobi_block_plan<double>(int, int, int*);
+template int qtt_jacobi_block_plan<float>(int, int, int*);
+template int qtt_jacobi_block<double>(const zc*, double*, zc*, int, int, int, int*, cudaStream_t);
+template int qtt_jacobi_block<float>(const cc*, float*, cc*, int, int, int, int*, cudaStream_t);
