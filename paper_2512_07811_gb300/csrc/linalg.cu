@@ -840,12 +840,326 @@ int qtt_allow_max_smem(const void* func) {
   return QTT_OK;
 }
 
+// Compensated sums in working precision: each partial sum carries its
+// rounding error (Knuth's TwoSum), so a sum of squares over a column is
+// accurate to a few units in the last place however many terms it has,
+// without FP64 arithmetic (slow on this part).
+template <class R>
+__device__ __forceinline__ void two_sum_acc(R& hi, R& lo, R t) {
+  const R s = hi + t;
+  const R bb = s - hi;
+  lo += (hi - (s - bb)) + (t - bb);
+  hi = s;
+}
+
+template <class R>
+__device__ __forceinline__ R warp_sum_compensated(R hi, R lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const R ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+    const R olo = __shfl_xor_sync(0xffffffffu, lo, o);
+    lo += olo;
+    two_sum_acc(hi, lo, ohi);
+  }
+  return hi + lo;
+}
+
+// ------------------------------------------------- left-looking panel QR
+// Householder QR, one CTA per matrix, for m <= 32 * RPL rows.  Columns are
+// taken in panels of NW (= warps per CTA) columns.  For a panel, each warp
+// loads one column into registers (rows on the lanes) and applies every
+// earlier reflector to it on its own -- no barrier, the reflectors read from
+// the workspace W through L1 -- then the panel is factored in shared memory
+// with the same reflectors and look-ahead norms as qr_r_kernel (thread 0
+// forms reflector j, all warps apply it, the warp owning column j + 1 also
+// computes that column's norm) and written back to W.  Earlier reflectors
+// are staged in shared memory one panel at a time.  The explicit Q, when
+// wanted, is formed column by column in registers, one warp per column
+// (Q e_c = H_0 ... H_c e_c).  Same inputs, outputs, zero-column rule and
+// reflector format (v = (1, x_{j+1} / v0, ...) with 1/v0 and tau kept per
+// column) as qr_r_kernel.
+// warps per CTA of qr_panel_kernel: 16 where two register columns would not fit 64 registers
+template <class R, int RPL>
+constexpr int qr_panel_warps() { return sizeof(R) * RPL > 32 ? 16 : 32; }
+
+template <class R, int RPL>
+__global__ void __launch_bounds__(32 * qr_panel_warps<R, RPL>())
+qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int m, int n,
+                int64_t rows_total, int64_t rows_per_batch, cplx<R>* __restrict__ Wbase, cplx<R>* __restrict__ out,
+                int64_t out_bstride, int64_t ldr, cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout,
+                int64_t q_bstride, int64_t ldq) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NW = blockDim.x >> 5;
+  const int kmax = m < n ? m : n;
+  cplx<R>* P = reinterpret_cast<cplx<R>*>(smem_raw);           // panel, NW columns of m
+  cplx<R>* S = P + (size_t)NW * m;                              // staged reflectors of an earlier panel
+  cplx<R>* s_ivs = S + (size_t)NW * m;                          // 1/v0 per reflector
+  R* s_taus = reinterpret_cast<R*>(s_ivs + kmax);               // tau per reflector
+  __shared__ R red[32];
+  __shared__ R s_below[2];  // squared norm strictly below the diagonal of the next column
+  __shared__ int s_zero;
+  const int64_t b = blockIdx.x;
+  cplx<R>* W = Wbase + b * (int64_t)m * n;
+  const int64_t row0 = b * rows_per_batch;
+  int64_t valid = rows_total - row0;
+  if (valid > m) valid = m;
+  const int64_t ib = midx_off(inB, b);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // Frobenius norm of the input, for the numerically-zero threshold
+  R part = 0;
+  for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
+    const int64_t c = e / m, i = e - c * m;
+    if (i < valid) part += abs2(in[ib + midx_off(rowI, i) + midx_off(colI, c)]);
+  }
+  const R anorm2 = block_sum(part, red);
+  const R eps = sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON);
+  const R zero_thresh2 = eps * eps * anorm2;
+  for (int p0 = 0; p0 < n; p0 += NW) {
+    const int pcols = min(NW, n - p0);
+    const int pw = max(0, min(NW, kmax - p0));  // reflectors formed in this panel
+    // 1. column p0 + warp: load, apply reflectors 0 .. p0-1 (staged in shared
+    // memory one earlier panel at a time), store into the panel
+    const int c = p0 + warp;
+    cplx<R> x[RPL];
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      const int i = lane + 32 * u;
+      cplx<R> v(0, 0);
+      if (warp < pcols && i < valid) {
+        v = in[ib + midx_off(rowI, i) + midx_off(colI, c)];
+        if (conj_in) v.im = -v.im;
+      }
+      x[u] = v;
+    }
+    for (int q0 = 0; q0 < p0 && q0 < kmax; q0 += NW) {
+      const int qn = min(NW, kmax - q0);
+      for (int e = threadIdx.x; e < qn * m; e += blockDim.x) S[e] = W[(int64_t)q0 * m + e];
+      __syncthreads();
+      if (warp < pcols) {
+        for (int jj = 0; jj < qn; ++jj) {
+          const int j = q0 + jj;
+          const R tau = s_taus[j];
+          if (tau == R(0)) continue;
+          const cplx<R> iv = s_ivs[j];
+          const cplx<R>* vj = S + (size_t)jj * m;
+          cplx<R> v[RPL];
+          cplx<R> w(0, 0);
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            v[u] = i > j && i < m ? vj[i] * iv : (i == j ? cplx<R>(1, 0) : cplx<R>(0, 0));
+            cfma_conj(w, v[u], x[u]);
+          }
+          w.re = warp_sum(w.re);
+          w.im = warp_sum(w.im);
+          w = tau * w;
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) x[u] = x[u] - v[u] * w;
+        }
+      }
+      __syncthreads();
+    }
+    if (warp < pcols) {
+      cplx<R>* pc = P + (size_t)warp * m;
+      R hi = 0, lo = 0;
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        const int i = lane + 32 * u;
+        if (i < m) {
+          pc[i] = x[u];
+          if (warp == 0 && i > p0) two_sum_acc(hi, lo, abs2(x[u]));
+        }
+      }
+      if (warp == 0) {
+        const R p2 = warp_sum_compensated(hi, lo);
+        if (lane == 0) s_below[0] = p2;
+      }
+    }
+    __syncthreads();
+    // 2. factor the panel in shared memory
+    for (int jj = 0; jj < pw; ++jj) {
+      const int j = p0 + jj;
+      cplx<R>* colj = P + (size_t)jj * m;
+      if (threadIdx.x == 0) {
+        // the part below the diagonal is summed directly (no cancellation in
+        // ||x||^2 - |x0|^2) and with compensation, so tau is accurate to
+        // working precision without FP64
+        const R below = s_below[jj & 1];
+        const cplx<R> x0 = colj[j];
+        const R ax2 = abs2(x0);
+        const R nrm2 = below + ax2;
+        cplx<R> iv(0, 0);
+        R tau = R(0);
+        int zero = 0;
+        if (nrm2 <= zero_thresh2 || below <= zero_thresh2) {
+          zero = 1;
+          if (nrm2 <= zero_thresh2) colj[j] = cplx<R>(0, 0);
+        } else {
+          // alpha = -e^{i arg x0} ||x||, v0 = x0 - alpha = e^{i arg x0} (|x0| + ||x||)
+          const R ax0 = sqrt(ax2), nrm = sqrt(nrm2);
+          const R phr = ax0 > R(0) ? x0.re / ax0 : R(1), phi = ax0 > R(0) ? x0.im / ax0 : R(0);
+          const R s0 = ax0 + nrm;
+          const R v02 = s0 * s0;
+          tau = R(2) * v02 / (below + v02);
+          iv = cplx<R>(phr / s0, -phi / s0);
+          colj[j] = cplx<R>(-phr * nrm, -phi * nrm);
+        }
+        s_taus[j] = tau;
+        s_ivs[j] = iv;
+        s_zero = zero;
+        if (tauws) {
+          tauws[b * 2 * n + 2 * j] = iv;
+          tauws[b * 2 * n + 2 * j + 1] = cplx<R>(tau, R(0));
+        }
+      }
+      __syncthreads();
+      const R tau = s_taus[j];
+      const cplx<R> iv = s_ivs[j];
+      if (s_zero)
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) colj[i] = cplx<R>(0, 0);
+      const int cl = jj + 1 + warp;  // one panel column per warp, rows in registers
+      if (cl < pcols) {
+        cplx<R>* colc = P + (size_t)cl * m;
+        cplx<R> xr[RPL];
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const int i = lane + 32 * u;
+          xr[u] = i < m ? colc[i] : cplx<R>(0, 0);
+        }
+        if (tau != R(0)) {
+          cplx<R> v[RPL];
+          cplx<R> w(0, 0);
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            v[u] = i > j && i < m ? colj[i] * iv : (i == j ? cplx<R>(1, 0) : cplx<R>(0, 0));
+            cfma_conj(w, v[u], xr[u]);
+          }
+          w.re = warp_sum(w.re);
+          w.im = warp_sum(w.im);
+          w = tau * w;
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            xr[u] = xr[u] - v[u] * w;
+            if (i >= j && i < m) colc[i] = xr[u];
+          }
+        }
+        if (cl == jj + 1) {
+          R hi = 0, lo = 0;
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            if (i >= j + 2 && i < m) two_sum_acc(hi, lo, abs2(xr[u]));
+          }
+          const R p2 = warp_sum_compensated(hi, lo);
+          if (lane == 0) s_below[(jj + 1) & 1] = p2;
+        }
+      }
+      __syncthreads();
+    }
+    // 3. panel back to the workspace (R above, reflectors below the diagonal)
+    for (int e = threadIdx.x; e < pcols * m; e += blockDim.x) {
+      const int cc = e / m, i = e - cc * m;
+      W[(int64_t)(p0 + cc) * m + i] = P[(size_t)cc * m + i];
+    }
+    __syncthreads();
+  }
+  if (out) {
+    cplx<R>* Rb = out + b * out_bstride;
+    for (int64_t e = threadIdx.x; e < (int64_t)kmax * n; e += blockDim.x) {
+      const int64_t i = e / n, c = e - i * n;
+      Rb[i * ldr + c] = (c >= i) ? W[c * m + i] : cplx<R>(0, 0);
+    }
+  }
+  if (Qout) {
+    // NW columns of Q at a time, one per warp; the reflectors they need
+    // (j <= c) are staged panel by panel, last panel first
+    cplx<R>* Q = Qout + b * q_bstride;
+    for (int g0 = 0; g0 < kmax; g0 += NW) {
+      const int c = g0 + warp;
+      cplx<R> x[RPL];
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) x[u] = cplx<R>(lane + 32 * u == c ? R(1) : R(0), R(0));
+      const int jmax = min(kmax - 1, g0 + NW - 1);
+      for (int q0 = (jmax / NW) * NW; q0 >= 0; q0 -= NW) {
+        const int qn = min(NW, kmax - q0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < qn * m; e += blockDim.x) S[e] = W[(int64_t)q0 * m + e];
+        __syncthreads();
+        if (c < kmax) {
+          for (int jj = qn - 1; jj >= 0; --jj) {
+            const int j = q0 + jj;
+            const R tau = s_taus[j];
+            if (j > c || tau == R(0)) continue;
+            const cplx<R> iv = s_ivs[j];
+            const cplx<R>* vj = S + (size_t)jj * m;
+            cplx<R> v[RPL];
+            cplx<R> w(0, 0);
+#pragma unroll
+            for (int u = 0; u < RPL; ++u) {
+              const int i = lane + 32 * u;
+              v[u] = i > j && i < m ? vj[i] * iv : (i == j ? cplx<R>(1, 0) : cplx<R>(0, 0));
+              cfma_conj(w, v[u], x[u]);
+            }
+            w.re = warp_sum(w.re);
+            w.im = warp_sum(w.im);
+            w = tau * w;
+#pragma unroll
+            for (int u = 0; u < RPL; ++u) x[u] = x[u] - v[u] * w;
+          }
+        }
+      }
+      if (c < kmax) {
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const int i = lane + 32 * u;
+          if (i < m) Q[(int64_t)i * ldq + c] = x[u];
+        }
+      }
+    }
+  }
+}
+
+template <class R, int RPL>
+static int launch_qr_panel(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
+                           int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
+                           int64_t out_bstride, int64_t ldr, cplx<R>* tauws, cplx<R>* Qout, int64_t q_bstride,
+                           int64_t ldq, cudaStream_t s) {
+  const int nw = qr_panel_warps<R, RPL>();
+  const int64_t kmax = std::min(m, n);
+  const size_t sm = (size_t)2 * nw * m * sizeof(cplx<R>) + (size_t)kmax * (sizeof(cplx<R>) + sizeof(R)) + 16;
+  if (sm > 200 * 1024) return QTT_ERR_UNSUPPORTED;
+  if (qtt_allow_max_smem((const void*)qr_panel_kernel<R, RPL>) != QTT_OK) return QTT_ERR_CUDA;
+  qr_panel_kernel<R, RPL><<<(unsigned)batch, 32 * nw, sm, s>>>(in, inB, rowI, colI, conj_in, (int)m, (int)n,
+                                                                rows_total, rows_per_batch, W, out, out_bstride, ldr,
+                                                                tauws, Qout, q_bstride, ldq);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
 template <class R>
 int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
              int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
              int64_t out_bstride, int64_t ldr, cudaStream_t s, cplx<R>* tauws, cplx<R>* Qout,
              int64_t q_bstride, int64_t ldq, cplx<R>* Qws) {
   if (batch <= 0 || m <= 0 || n <= 0) return QTT_OK;
+  if (batch > 65535 || m > INT32_MAX || n > INT32_MAX) return QTT_ERR_ARG;
+  // panel kernel for up to 512 rows (256 in FP64), else the workspace kernel
+  {
+    int st = QTT_ERR_UNSUPPORTED;
+    if (m <= 128)
+      st = launch_qr_panel<R, 4>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
+                                 out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+    else if (m <= 256)
+      st = launch_qr_panel<R, 8>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
+                                 out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+    else if constexpr (sizeof(R) == 4) {
+      if (m <= 512)
+        st = launch_qr_panel<R, 16>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
+                                    out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+    }
+    if (st != QTT_ERR_UNSUPPORTED) return st;
+  }
   if (Qout && (!tauws || !Qws)) return QTT_ERR_ARG;
   qr_r_kernel<R><<<(unsigned)batch, 1024, 0, s>>>(in, inB, rowI, colI, conj_in, m, n, rows_total,
                                                  rows_per_batch, W, out, out_bstride, ldr, tauws, Qout,
