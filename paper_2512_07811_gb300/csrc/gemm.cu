@@ -165,14 +165,22 @@ __global__ void splitk_reduce_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta, co
 
 }  // namespace
 
+// Tile edge of qtt_gemm_ex: 64, or 32 for thin shapes and for grids of
+// 64 x 64 tiles that would not fill a quarter of the SMs.
+static int64_t gemm_tile(const GemmDesc& g) {
+  if (g.M <= 32 || g.N <= 32) return 32;
+  const int64_t t64 = ((g.M + 63) / 64) * ((g.N + 63) / 64) * g.batch;
+  return t64 < 38 ? 32 : 64;
+}
+
 // Number of K splits worth using for this shape (1 = no split): GEMMs whose
-// output tiles cannot occupy half the SMs and whose K is long get their K
-// range cut so that about one CTA per SM works.
+// output tiles cannot occupy half the SMs and whose K is at least 128 get
+// their K range cut into chunks of 64 or more, about one CTA per SM.
 int qtt_gemm_splits(const GemmDesc& g) {
-  const int64_t small = (g.M <= 32 || g.N <= 32) ? 32 : 64;
-  const int64_t tiles = ((g.M + small - 1) / small) * ((g.N + small - 1) / small) * g.batch;
-  if (tiles >= 76 || g.K < 256) return 1;
-  int64_t s = std::min<int64_t>((g.K + 127) / 128, std::max<int64_t>(1, 152 / tiles));
+  const int64_t tile = gemm_tile(g);
+  const int64_t tiles = ((g.M + tile - 1) / tile) * ((g.N + tile - 1) / tile) * g.batch;
+  if (tiles >= 76 || g.K < 128) return 1;
+  int64_t s = std::min<int64_t>((g.K + 63) / 64, std::max<int64_t>(1, 152 / tiles));
   return (int)std::min<int64_t>(s, 32);
 }
 
@@ -182,7 +190,7 @@ int qtt_gemm_ex(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return QTT_OK;
   if (splits < 1 || (splits > 1 && !P)) return QTT_ERR_ARG;
   const int64_t kchunk = splits > 1 ? (g.K + splits - 1) / splits : std::max<int64_t>(g.K, 1);
-  const bool thin = g.M <= 32 || g.N <= 32;
+  const bool thin = gemm_tile(g) == 32;
   constexpr int BK = sizeof(R) == 8 ? 8 : 16;
   const int64_t zdim = g.batch * splits;
   if (zdim > 65535) return QTT_ERR_ARG;

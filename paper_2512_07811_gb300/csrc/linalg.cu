@@ -864,15 +864,53 @@ __device__ __forceinline__ R warp_sum_compensated(R hi, R lo) {
   return hi + lo;
 }
 
+// Reflector of a shared-memory column whose diagonal is row j, formed by one
+// warp (lane 0 computes, the warp clears a numerically zero column):
+// alpha = -e^{i arg x0} ||x||, v0 = x0 - alpha, stored as 1/v0 and tau.
+template <class R>
+__device__ __forceinline__ void qr_reflector_warp(cplx<R>* col, int j, int m, R below, R zero_thresh2, int lane,
+                                                  R* s_taus, cplx<R>* s_ivs, cplx<R>* tauws) {
+  __syncwarp();
+  int zero = 0;
+  if (lane == 0) {
+    const cplx<R> x0 = col[j];
+    const R ax2 = abs2(x0);
+    const R nrm2 = below + ax2;
+    cplx<R> iv(0, 0);
+    R tau = R(0);
+    if (nrm2 <= zero_thresh2 || below <= zero_thresh2) {
+      zero = 1;
+      if (nrm2 <= zero_thresh2) col[j] = cplx<R>(0, 0);
+    } else {
+      const R ax0 = sqrt(ax2), nrm = sqrt(nrm2);
+      const R phr = ax0 > R(0) ? x0.re / ax0 : R(1), phi = ax0 > R(0) ? x0.im / ax0 : R(0);
+      const R s0 = ax0 + nrm;
+      const R v02 = s0 * s0;
+      tau = R(2) * v02 / (below + v02);
+      iv = cplx<R>(phr / s0, -phi / s0);
+      col[j] = cplx<R>(-phr * nrm, -phi * nrm);
+    }
+    s_taus[j] = tau;
+    s_ivs[j] = iv;
+    if (tauws) {
+      tauws[2 * j] = iv;
+      tauws[2 * j + 1] = cplx<R>(tau, R(0));
+    }
+  }
+  zero = __shfl_sync(0xffffffffu, zero, 0);
+  if (zero)
+    for (int i = j + 1 + lane; i < m; i += 32) col[i] = cplx<R>(0, 0);
+}
+
 // ------------------------------------------------- left-looking panel QR
 // Householder QR, one CTA per matrix, for m <= 32 * RPL rows.  Columns are
 // taken in panels of NW (= warps per CTA) columns.  For a panel, each warp
 // loads one column into registers (rows on the lanes) and applies every
 // earlier reflector to it on its own -- no barrier, the reflectors read from
 // the workspace W through L1 -- then the panel is factored in shared memory
-// with the same reflectors and look-ahead norms as qr_r_kernel (thread 0
-// forms reflector j, all warps apply it, the warp owning column j + 1 also
-// computes that column's norm) and written back to W.  Earlier reflectors
+// (all warps apply reflector j, the warp owning column j + 1 meanwhile
+// computes that column's norm and reflector, one barrier per column) and
+// written back to W.  Earlier reflectors
 // are staged in shared memory one panel at a time.  The explicit Q, when
 // wanted, is formed column by column in registers, one warp per column
 // (Q e_c = H_0 ... H_c e_c).  Same inputs, outputs, zero-column rule and
@@ -896,8 +934,6 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
   cplx<R>* s_ivs = S + (size_t)NW * m;                          // 1/v0 per reflector
   R* s_taus = reinterpret_cast<R*>(s_ivs + kmax);               // tau per reflector
   __shared__ R red[32];
-  __shared__ R s_below[2];  // squared norm strictly below the diagonal of the next column
-  __shared__ int s_zero;
   const int64_t b = blockIdx.x;
   cplx<R>* W = Wbase + b * (int64_t)m * n;
   const int64_t row0 = b * rows_per_batch;
@@ -970,53 +1006,21 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
           if (warp == 0 && i > p0) two_sum_acc(hi, lo, abs2(x[u]));
         }
       }
-      if (warp == 0) {
-        const R p2 = warp_sum_compensated(hi, lo);
-        if (lane == 0) s_below[0] = p2;
+      if (warp == 0 && pw > 0) {
+        const R below = warp_sum_compensated(hi, lo);
+        qr_reflector_warp(pc, p0, m, below, zero_thresh2, lane, s_taus, s_ivs, tauws ? tauws + b * 2 * n : nullptr);
       }
     }
     __syncthreads();
-    // 2. factor the panel in shared memory
+    // 2. factor the panel in shared memory: reflector j is ready; every warp
+    // applies it to one later panel column, and the warp holding column j + 1
+    // also forms reflector j + 1 from that column's fresh norm -- one barrier
+    // per column
     for (int jj = 0; jj < pw; ++jj) {
       const int j = p0 + jj;
-      cplx<R>* colj = P + (size_t)jj * m;
-      if (threadIdx.x == 0) {
-        // the part below the diagonal is summed directly (no cancellation in
-        // ||x||^2 - |x0|^2) and with compensation, so tau is accurate to
-        // working precision without FP64
-        const R below = s_below[jj & 1];
-        const cplx<R> x0 = colj[j];
-        const R ax2 = abs2(x0);
-        const R nrm2 = below + ax2;
-        cplx<R> iv(0, 0);
-        R tau = R(0);
-        int zero = 0;
-        if (nrm2 <= zero_thresh2 || below <= zero_thresh2) {
-          zero = 1;
-          if (nrm2 <= zero_thresh2) colj[j] = cplx<R>(0, 0);
-        } else {
-          // alpha = -e^{i arg x0} ||x||, v0 = x0 - alpha = e^{i arg x0} (|x0| + ||x||)
-          const R ax0 = sqrt(ax2), nrm = sqrt(nrm2);
-          const R phr = ax0 > R(0) ? x0.re / ax0 : R(1), phi = ax0 > R(0) ? x0.im / ax0 : R(0);
-          const R s0 = ax0 + nrm;
-          const R v02 = s0 * s0;
-          tau = R(2) * v02 / (below + v02);
-          iv = cplx<R>(phr / s0, -phi / s0);
-          colj[j] = cplx<R>(-phr * nrm, -phi * nrm);
-        }
-        s_taus[j] = tau;
-        s_ivs[j] = iv;
-        s_zero = zero;
-        if (tauws) {
-          tauws[b * 2 * n + 2 * j] = iv;
-          tauws[b * 2 * n + 2 * j + 1] = cplx<R>(tau, R(0));
-        }
-      }
-      __syncthreads();
+      const cplx<R>* colj = P + (size_t)jj * m;
       const R tau = s_taus[j];
       const cplx<R> iv = s_ivs[j];
-      if (s_zero)
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) colj[i] = cplx<R>(0, 0);
       const int cl = jj + 1 + warp;  // one panel column per warp, rows in registers
       if (cl < pcols) {
         cplx<R>* colc = P + (size_t)cl * m;
@@ -1045,15 +1049,16 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
             if (i >= j && i < m) colc[i] = xr[u];
           }
         }
-        if (cl == jj + 1) {
+        if (cl == jj + 1 && jj + 1 < pw) {
           R hi = 0, lo = 0;
 #pragma unroll
           for (int u = 0; u < RPL; ++u) {
             const int i = lane + 32 * u;
             if (i >= j + 2 && i < m) two_sum_acc(hi, lo, abs2(xr[u]));
           }
-          const R p2 = warp_sum_compensated(hi, lo);
-          if (lane == 0) s_below[(jj + 1) & 1] = p2;
+          const R below = warp_sum_compensated(hi, lo);
+          qr_reflector_warp(colc, j + 1, m, below, zero_thresh2, lane, s_taus, s_ivs,
+                            tauws ? tauws + b * 2 * n : nullptr);
         }
       }
       __syncthreads();
@@ -1338,14 +1343,23 @@ template int qtt_jacobi_cluster<float>(const cc*, float*, cc*, cc*, int, int, in
 // rotated columns (row-major p x q) in the same order.
 template <class R, int RPL>
 __device__ __forceinline__ bool warp_pair_rotate(cplx<R> (&x)[RPL], cplx<R> (&y)[RPL], R tol2) {
-  R al = 0, be = 0;
-  cplx<R> g(0, 0);
+  // two independent accumulator sets (even / odd rows) halve the FMA chains
+  R al = 0, be = 0, al1 = 0, be1 = 0;
+  cplx<R> g(0, 0), g1(0, 0);
 #pragma unroll
-  for (int u = 0; u < RPL; ++u) {
+  for (int u = 0; u < RPL; u += 2) {
     al += abs2(x[u]);
     be += abs2(y[u]);
     cfma_conj(g, x[u], y[u]);
+    if (u + 1 < RPL) {
+      al1 += abs2(x[u + 1]);
+      be1 += abs2(y[u + 1]);
+      cfma_conj(g1, x[u + 1], y[u + 1]);
+    }
   }
+  al += al1;
+  be += be1;
+  g = g + g1;
   al = warp_sum(al);
   be = warp_sum(be);
   g.re = warp_sum(g.re);
@@ -1552,11 +1566,17 @@ static int launch_jacobi_block(const cplx<R>* G, R* sigma, cplx<R>* Us, int p, i
 template <class R>
 int qtt_jacobi_block_plan(int p, int q, int* bs_out) {
   if (q < 32 || p < 1 || p > (sizeof(R) == 8 ? 256 : 512)) return 0;
-  const int nc = q >= 64 ? 8 : 4;
-  int bs = (q + 2 * nc - 1) / (2 * nc);
-  bs += bs & 1;
-  if (bs > 16 || jacobi_block_bytes<R>(p, bs, nc) > 200 * 1024) return 0;
-  *bs_out = bs;
+  // 4 CTAs below q = 64, else 8 (4 CTAs of 16 warps at q = 128 measured 1.4x
+  // slower than 8 of 8: each round's pair chain, not the number of warps,
+  // sets the time)
+  auto width = [&](int nc) {
+    int bs = (q + 2 * nc - 1) / (2 * nc);
+    return bs + (bs & 1);
+  };
+  auto fits = [&](int nc) { return width(nc) <= 16 && jacobi_block_bytes<R>(p, width(nc), nc) <= 200 * 1024; };
+  int nc = q < 64 && fits(4) ? 4 : 8;
+  if (!fits(nc)) return 0;
+  *bs_out = width(nc);
   return nc;
 }
 
