@@ -501,7 +501,17 @@ __device__ __forceinline__ bool jacobi_rotation(R al, R be, cplx<R> g, R tol2, R
   const R zeta = (be - al) * (R(0.5) * inv);
   const R az = fabs(zeta);
   // for |zeta| beyond 1e18 the root is 1 / (2 zeta) to working precision (and zeta^2 could overflow)
-  R t = az < R(1e18) ? R(1) / (az + sqrt(R(1) + az * az)) : R(0.5) / az;
+  R t;
+  if constexpr (sizeof(R) == 4) {
+    // the tangent only steers the rotation (cos and sin below are consistent
+    // with whatever t is, so the rotation stays orthogonal); hardware
+    // approximations of the square root and the quotient leave a residual
+    // inner product of a few ulp, far below the stopping tolerance
+    const R u = R(1) + az * az;
+    t = az < R(1e18) ? __fdividef(R(1), az + u * rsqrtf(u)) : __fdividef(R(0.5), az);
+  } else {
+    t = az < R(1e18) ? R(1) / (az + sqrt(R(1) + az * az)) : R(0.5) / az;
+  }
   if (zeta < R(0)) t = -t;
   cs = rsqrt_refined(R(1) + t * t);
   const R sn = cs * t;
