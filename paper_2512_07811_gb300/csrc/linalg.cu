@@ -876,17 +876,19 @@ __device__ __forceinline__ R warp_sum_compensated(R hi, R lo) {
 
 // Reflector of a shared-memory column whose diagonal is row j, formed by one
 // warp (lane 0 computes, the warp clears a numerically zero column):
-// alpha = -e^{i arg x0} ||x||, v0 = x0 - alpha, stored as 1/v0 and tau.
-template <class R>
+// alpha = -e^{i arg x0} ||x||, v0 = x0 - alpha, stored as 1/v0 and tau; the
+// scaled reflector (0 above row j, 1 at j, x_i / v0 below, 0 in the padding
+// up to MP rows) is also written to vs, so that its users need no scaling.
+template <class R, int MP>
 __device__ __forceinline__ void qr_reflector_warp(cplx<R>* col, int j, int m, R below, R zero_thresh2, int lane,
-                                                  R* s_taus, cplx<R>* s_ivs, cplx<R>* tauws) {
+                                                  R* s_taus, cplx<R>* s_ivs, cplx<R>* tauws, cplx<R>* vs) {
   __syncwarp();
   int zero = 0;
+  cplx<R> iv(0, 0);
   if (lane == 0) {
     const cplx<R> x0 = col[j];
     const R ax2 = abs2(x0);
     const R nrm2 = below + ax2;
-    cplx<R> iv(0, 0);
     R tau = R(0);
     if (nrm2 <= zero_thresh2 || below <= zero_thresh2) {
       zero = 1;
@@ -908,8 +910,12 @@ __device__ __forceinline__ void qr_reflector_warp(cplx<R>* col, int j, int m, R 
     }
   }
   zero = __shfl_sync(0xffffffffu, zero, 0);
+  iv.re = __shfl_sync(0xffffffffu, iv.re, 0);
+  iv.im = __shfl_sync(0xffffffffu, iv.im, 0);
   if (zero)
     for (int i = j + 1 + lane; i < m; i += 32) col[i] = cplx<R>(0, 0);
+  for (int i = lane; i < MP; i += 32)
+    vs[i] = i > j && i < m ? col[i] * iv : cplx<R>(i == j ? R(1) : R(0), R(0));
 }
 
 // ------------------------------------------------- left-looking panel QR
@@ -936,16 +942,19 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
                 int64_t rows_total, int64_t rows_per_batch, cplx<R>* __restrict__ Wbase, cplx<R>* __restrict__ out,
                 int64_t out_bstride, int64_t ldr, cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout,
                 int64_t q_bstride, int64_t ldq) {
+  constexpr int MP = 32 * RPL;  // rows padded to whole warps
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NW = blockDim.x >> 5;
   const int kmax = m < n ? m : n;
   cplx<R>* P = reinterpret_cast<cplx<R>*>(smem_raw);           // panel, NW columns of m
-  cplx<R>* S = P + (size_t)NW * m;                              // staged reflectors of an earlier panel
-  cplx<R>* s_ivs = S + (size_t)NW * m;                          // 1/v0 per reflector
+  cplx<R>* S = P + (size_t)NW * m;                              // NW scaled reflectors of MP rows
+  cplx<R>* Vc = S + (size_t)NW * MP;                            // the current scaled reflector, 2 x MP
+  cplx<R>* s_ivs = Vc + 2 * MP;                                 // 1/v0 per reflector
   R* s_taus = reinterpret_cast<R*>(s_ivs + kmax);               // tau per reflector
   __shared__ R red[32];
   const int64_t b = blockIdx.x;
   cplx<R>* W = Wbase + b * (int64_t)m * n;
+  cplx<R>* tw = tauws ? tauws + b * 2 * n : nullptr;
   const int64_t row0 = b * rows_per_batch;
   int64_t valid = rows_total - row0;
   if (valid > m) valid = m;
@@ -953,18 +962,39 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // Frobenius norm of the input, for the numerically-zero threshold
   R part = 0;
-  for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
-    const int64_t c = e / m, i = e - c * m;
-    if (i < valid) part += abs2(in[ib + midx_off(rowI, i) + midx_off(colI, c)]);
-  }
+  for (int c = warp; c < n; c += NW)
+    for (int i = lane; i < valid; i += 32) part += abs2(in[ib + midx_off(rowI, i) + midx_off(colI, c)]);
   const R anorm2 = block_sum(part, red);
   const R eps = sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON);
   const R zero_thresh2 = eps * eps * anorm2;
+  // stage reflectors q0 .. q0+qn-1 from W into S, scaled
+  auto stage = [&](int q0, int qn) {
+    for (int e = threadIdx.x; e < qn * MP; e += blockDim.x) {
+      const int jj = e / MP, i = e - jj * MP;
+      const int j = q0 + jj;
+      const cplx<R> v = i > j && i < m ? W[(int64_t)j * m + i] * s_ivs[j] : cplx<R>(i == j ? R(1) : R(0), R(0));
+      S[e] = s_taus[j] != R(0) ? v : cplx<R>(0, 0);
+    }
+  };
+  // x <- (I - tau v v^H) x for a register column and a scaled reflector in shared memory
+  auto reflect = [&](cplx<R>(&x)[RPL], const cplx<R>* v, R tau) {
+    cplx<R> w(0, 0), w1(0, 0);
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      if (u & 1) cfma_conj(w1, v[lane + 32 * u], x[u]); else cfma_conj(w, v[lane + 32 * u], x[u]);
+    }
+    w = w + w1;
+    w.re = warp_sum(w.re);
+    w.im = warp_sum(w.im);
+    w = tau * w;
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) x[u] = x[u] - v[lane + 32 * u] * w;
+  };
   for (int p0 = 0; p0 < n; p0 += NW) {
     const int pcols = min(NW, n - p0);
     const int pw = max(0, min(NW, kmax - p0));  // reflectors formed in this panel
-    // 1. column p0 + warp: load, apply reflectors 0 .. p0-1 (staged in shared
-    // memory one earlier panel at a time), store into the panel
+    // 1. column p0 + warp: load, apply reflectors 0 .. p0-1 (staged one
+    // earlier panel at a time), store into the panel
     const int c = p0 + warp;
     cplx<R> x[RPL];
 #pragma unroll
@@ -979,30 +1009,13 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
     }
     for (int q0 = 0; q0 < p0 && q0 < kmax; q0 += NW) {
       const int qn = min(NW, kmax - q0);
-      for (int e = threadIdx.x; e < qn * m; e += blockDim.x) S[e] = W[(int64_t)q0 * m + e];
+      stage(q0, qn);
       __syncthreads();
-      if (warp < pcols) {
+      if (warp < pcols)
         for (int jj = 0; jj < qn; ++jj) {
-          const int j = q0 + jj;
-          const R tau = s_taus[j];
-          if (tau == R(0)) continue;
-          const cplx<R> iv = s_ivs[j];
-          const cplx<R>* vj = S + (size_t)jj * m;
-          cplx<R> v[RPL];
-          cplx<R> w(0, 0);
-#pragma unroll
-          for (int u = 0; u < RPL; ++u) {
-            const int i = lane + 32 * u;
-            v[u] = i > j && i < m ? vj[i] * iv : (i == j ? cplx<R>(1, 0) : cplx<R>(0, 0));
-            cfma_conj(w, v[u], x[u]);
-          }
-          w.re = warp_sum(w.re);
-          w.im = warp_sum(w.im);
-          w = tau * w;
-#pragma unroll
-          for (int u = 0; u < RPL; ++u) x[u] = x[u] - v[u] * w;
+          const R tau = s_taus[q0 + jj];
+          if (tau != R(0)) reflect(x, S + (size_t)jj * MP, tau);
         }
-      }
       __syncthreads();
     }
     if (warp < pcols) {
@@ -1018,7 +1031,7 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
       }
       if (warp == 0 && pw > 0) {
         const R below = warp_sum_compensated(hi, lo);
-        qr_reflector_warp(pc, p0, m, below, zero_thresh2, lane, s_taus, s_ivs, tauws ? tauws + b * 2 * n : nullptr);
+        qr_reflector_warp<R, MP>(pc, p0, m, below, zero_thresh2, lane, s_taus, s_ivs, tw, Vc + (p0 & 1) * MP);
       }
     }
     __syncthreads();
@@ -1028,9 +1041,7 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
     // per column
     for (int jj = 0; jj < pw; ++jj) {
       const int j = p0 + jj;
-      const cplx<R>* colj = P + (size_t)jj * m;
       const R tau = s_taus[j];
-      const cplx<R> iv = s_ivs[j];
       const int cl = jj + 1 + warp;  // one panel column per warp, rows in registers
       if (cl < pcols) {
         cplx<R>* colc = P + (size_t)cl * m;
@@ -1041,21 +1052,10 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
           xr[u] = i < m ? colc[i] : cplx<R>(0, 0);
         }
         if (tau != R(0)) {
-          cplx<R> v[RPL];
-          cplx<R> w(0, 0);
+          reflect(xr, Vc + (j & 1) * MP, tau);
 #pragma unroll
           for (int u = 0; u < RPL; ++u) {
             const int i = lane + 32 * u;
-            v[u] = i > j && i < m ? colj[i] * iv : (i == j ? cplx<R>(1, 0) : cplx<R>(0, 0));
-            cfma_conj(w, v[u], xr[u]);
-          }
-          w.re = warp_sum(w.re);
-          w.im = warp_sum(w.im);
-          w = tau * w;
-#pragma unroll
-          for (int u = 0; u < RPL; ++u) {
-            const int i = lane + 32 * u;
-            xr[u] = xr[u] - v[u] * w;
             if (i >= j && i < m) colc[i] = xr[u];
           }
         }
@@ -1067,8 +1067,8 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
             if (i >= j + 2 && i < m) two_sum_acc(hi, lo, abs2(xr[u]));
           }
           const R below = warp_sum_compensated(hi, lo);
-          qr_reflector_warp(colc, j + 1, m, below, zero_thresh2, lane, s_taus, s_ivs,
-                            tauws ? tauws + b * 2 * n : nullptr);
+          qr_reflector_warp<R, MP>(colc, j + 1, m, below, zero_thresh2, lane, s_taus, s_ivs, tw,
+                                   Vc + ((j + 1) & 1) * MP);
         }
       }
       __syncthreads();
@@ -1100,30 +1100,14 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
       for (int q0 = (jmax / NW) * NW; q0 >= 0; q0 -= NW) {
         const int qn = min(NW, kmax - q0);
         __syncthreads();
-        for (int e = threadIdx.x; e < qn * m; e += blockDim.x) S[e] = W[(int64_t)q0 * m + e];
+        stage(q0, qn);
         __syncthreads();
-        if (c < kmax) {
+        if (c < kmax)
           for (int jj = qn - 1; jj >= 0; --jj) {
             const int j = q0 + jj;
             const R tau = s_taus[j];
-            if (j > c || tau == R(0)) continue;
-            const cplx<R> iv = s_ivs[j];
-            const cplx<R>* vj = S + (size_t)jj * m;
-            cplx<R> v[RPL];
-            cplx<R> w(0, 0);
-#pragma unroll
-            for (int u = 0; u < RPL; ++u) {
-              const int i = lane + 32 * u;
-              v[u] = i > j && i < m ? vj[i] * iv : (i == j ? cplx<R>(1, 0) : cplx<R>(0, 0));
-              cfma_conj(w, v[u], x[u]);
-            }
-            w.re = warp_sum(w.re);
-            w.im = warp_sum(w.im);
-            w = tau * w;
-#pragma unroll
-            for (int u = 0; u < RPL; ++u) x[u] = x[u] - v[u] * w;
+            if (j <= c && tau != R(0)) reflect(x, S + (size_t)jj * MP, tau);
           }
-        }
       }
       if (c < kmax) {
 #pragma unroll
@@ -1143,7 +1127,8 @@ static int launch_qr_panel(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, in
                            int64_t ldq, cudaStream_t s) {
   const int nw = qr_panel_warps<R, RPL>();
   const int64_t kmax = std::min(m, n);
-  const size_t sm = (size_t)2 * nw * m * sizeof(cplx<R>) + (size_t)kmax * (sizeof(cplx<R>) + sizeof(R)) + 16;
+  const size_t sm = ((size_t)nw * m + (size_t)(nw + 2) * 32 * RPL + kmax) * sizeof(cplx<R>) + (size_t)kmax * sizeof(R) +
+                    16;
   if (sm > 200 * 1024) return QTT_ERR_UNSUPPORTED;
   if (qtt_allow_max_smem((const void*)qr_panel_kernel<R, RPL>) != QTT_OK) return QTT_ERR_CUDA;
   qr_panel_kernel<R, RPL><<<(unsigned)batch, 32 * nw, sm, s>>>(in, inB, rowI, colI, conj_in, (int)m, (int)n,

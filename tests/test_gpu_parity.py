@@ -132,6 +132,28 @@ def test_round_forced_by_max_rank(Q, ctx):
     assert rel_diff(y.cores(), ref) < 1e-10
 
 
+@pytest.mark.parametrize("k,n0,n1", [(17, 39, 100), (25, 55, 150), (50, 300, 300), (64, 140, 256), (100, 205, 500)])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_round_factorisation_shapes(Q, ctx, k, n0, n1, fp32):
+    """Two cores (1, n0, 2k) and (2k, n1, 1) holding 1.75 x a rank-k train:
+    the left sweep factors an n0 x 2k matrix, the truncation SVD a
+    (n1 x 2k) C^H, so the cases reach the block-cyclic Jacobi with odd block
+    widths and 4 or 8 CTAs, 8 and 16 rows per lane, the shared-memory limit
+    (2k = 200, 500 rows), and the panel QR beyond 256 rows.  The rank-k
+    truncation is unique: ranks equal, 1e-12 (FP64) / 1e-5 (FP32) parity."""
+    rng = np.random.default_rng(100 + k)
+    a = (rng.standard_normal((1, n0, k)) + 1j * rng.standard_normal((1, n0, k))) / math.sqrt(2 * k)
+    b = (rng.standard_normal((k, n1, 1)) + 1j * rng.standard_normal((k, n1, 1))) / math.sqrt(2 * k)
+    x = T.tt_add([a, b], [a, b], 1.0, 0.75)
+    eps = 1e-5 if fp32 else 1e-10
+    g = Q.TT.from_cores(ctx, x, dtype=Q.C64 if fp32 else Q.C128)
+    y, info = Q.tt_round(ctx, g, eps)
+    ref, _ = T.tt_round(x, eps)
+    assert y.ranks == T.tt_ranks(ref) == [1, k, 1]
+    err = rel_diff([c.astype(np.complex128) for c in y.cores()], ref)
+    assert err < (1e-5 if fp32 else 1e-12)
+
+
 def test_round_fp32(Q, ctx):
     base = I.random_tt_cores(14, 2, 20, seed=16, dtype=np.complex128)
     x = T.tt_add(base, base, 1.0, 1.0)
