@@ -297,17 +297,29 @@ def run_ours(args, rank, world, local_rank):
 
 
 def ms_laminate(Q, ctx):
-    """Moulinec-Suquet iterations on the 32^3 scalar laminate, load case E = e_x,
-    three iterations each for the fast and the FP64 path."""
+    """Moulinec-Suquet iterations on the 32^3 scalar laminate, load case E = e_x:
+    the FP64 path at the workload's rounding tolerance 1e-8, the fast (FP32)
+    path at 1e-6 -- a tolerance below FP32 resolution cannot truncate the
+    rounding noise, so its ranks would run into the cap -- with the fast
+    path's effective-tensor deviation from the FP64 result reported (the
+    accuracy the comparison is held to is 1e-4).  One warm-up solve each, then
+    five timed iterations (setup reported separately)."""
     ind = I.laminate_indicator(32)
-    out = {"workload": "32^3 scalar laminate, 15 interleaved bit sites + control, contrast 10, "
-                       "eps 1e-8, max rank 64, E = e_x, 3 iterations"}
-    for name, prec in [("fast", Q.PREC_F32), ("fp64", Q.PREC_F64)]:
-        C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), tol=0.0, max_rank=64, eps=1e-8,
-                                 max_iter=3, min_iter=3, prec=prec, load_mask=1)
+    out = {"workload": "32^3 scalar laminate, 15 interleaved bit sites + control, contrast 10, max rank 64, "
+                       "E = e_x, 5 iterations; eps 1e-8 (FP64) / 1e-6 (fast)"}
+    C64 = None
+    for name, prec, eps in [("fp64", Q.PREC_F64, 1e-8), ("fast", Q.PREC_F32, 1e-6)]:
+        kw = dict(tol=0.0, max_rank=64, eps=eps, prec=prec, load_mask=1)
+        Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=1, min_iter=1, **kw)
+        C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=5, min_iter=5, **kw)
         it = rep.iterations[0]
-        out[name] = {"iters_per_s": it / (rep.iterate_ms * 1e-3) if rep.iterate_ms > 0 else None,
-                     "setup_ms": rep.setup_ms, "k_eff_xx": C[0, 0], "iterations": it}
+        out[name] = {"iters_per_s": it / (rep.iterate_ms * 1e-3) if rep.iterate_ms > 0 else None, "eps": eps,
+                     "setup_ms": rep.setup_ms, "k_eff_xx": C[0, 0], "iterations": it,
+                     "max_rank": rep.max_rank_seen}
+        if name == "fp64":
+            C64 = C
+        else:
+            out[name]["rel_dev_from_fp64"] = float(abs(C[0, 0] - C64[0, 0]) / abs(C64[0, 0]))
     out["k_eff_xx_exact"] = 20.0 / 11.0
     if out["fast"]["iters_per_s"] and out["fp64"]["iters_per_s"]:
         out["speedup_fast_vs_fp64"] = out["fast"]["iters_per_s"] / out["fp64"]["iters_per_s"]

@@ -397,25 +397,28 @@ int tsqr_r(qtt_ctx* c, const cplx<R>* in, MIdx rowI, MIdx colI, int conj_in, int
   return tsqr_r<R>(c, Rs.as<cplx<R>>(), L1(nch * n, n), L1(n, 1), 0, nch * n, n, Rout, rows_out);
 }
 
-// SVD pieces of an (rows x cols) matrix given through a view: the left
-// singular vectors U (rows x rows, columns sorted by decreasing singular
-// value) and the singular values, via QR of the conjugate transpose followed
-// by one-sided Jacobi on the triangular factor.
+// Left singular vectors and singular values of a (rows x cols) row-major
+// matrix C (leading dimension ld): C^H = Q R by TSQR (R only, got x rows,
+// got = min(rows, cols)), then one-sided Jacobi on R^H (rows x got), whose
+// normalised rotated columns are the left singular vectors of C (no rotation
+// accumulation).  U: rows x got, row-major (leading dimension got), columns
+// by decreasing singular value; sigma: got values; *nsv = got.
 template <class R>
-int left_svd(qtt_ctx* c, const cplx<R>* Cm, int64_t rows, int64_t cols, int64_t ld, cplx<R>* U, R* sigma) {
-  // C^H is cols x rows: element (i, j) = conj(C[j, i]) -> row stride 1, column stride ld
+int left_svd(qtt_ctx* c, const cplx<R>* Cm, int64_t rows, int64_t cols, int64_t ld, cplx<R>* U, R* sigma,
+             int64_t* nsv) {
   const int64_t p = std::min(rows, cols);
-  DBuf Rc, V;
+  DBuf Rc, G;
   TRY(Rc.alloc(c, (size_t)std::max<int64_t>(p, 1) * rows * sizeof(cplx<R>)));
-  TRY(V.alloc(c, (size_t)rows * rows * sizeof(cplx<R>)));
   int64_t got = 0;
+  // C^H is cols x rows: element (i, j) = conj(C[j, i]) -> row stride 1, column stride ld
   TRY(tsqr_r<R>(c, Cm, L1(cols, 1), L1(rows, ld), 1, cols, rows, Rc.as<cplx<R>>(), &got));
-  // Jacobi on Rc (got x rows): Rc V = U_R S  =>  C = V S U_R^H Q^H, left vectors of C = V
-  TRY(jacobi_launch<R>(c, Rc.as<cplx<R>>(), V.as<cplx<R>>(), sigma, U, (int)got, (int)rows, 60));
-  if (got < rows) {
-    // trailing singular values are exactly zero (rank <= got): sigma entries
-    // beyond `got` come out as zero column norms already.
-  }
+  // G = R^H (rows x got): element (i, j) = conj(R[j, i])
+  TRY(G.alloc(c, (size_t)rows * std::max<int64_t>(got, 1) * sizeof(cplx<R>)));
+  c->launches++;
+  TRY(qtt_copy_strided<R>(Rc.as<cplx<R>>(), L1(rows, 1), L1(got, rows), rows, got, 1, G.as<cplx<R>>(), got,
+                          c->stream));
+  TRY(jacobi_launch<R>(c, G.as<cplx<R>>(), nullptr, sigma, nullptr, (int)rows, (int)got, 60, U));
+  *nsv = got;
   return QTT_OK;
 }
 
@@ -525,7 +528,8 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     DBuf Cb, U, UG, sig, Rc, Qc, Wq, tau, Vw;
     // Jacobi on G = C^H (Tcols x rk, row-major) unless C is so wide that a QR
     // of C^H first pays for itself
-    const int64_t jp = Tcols, jq = rk;
+    const int64_t jp = Tcols;
+    int64_t jq = rk;
     if (jp <= 4 * jq || jp * jq <= 4096) {
       TRY(Cb.alloc(c, (size_t)rk * Tcols * sizeof(cplx<R>)));
       if (left_orth) {
@@ -538,10 +542,32 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
       TRY(dbg_finite<R>(c, Cb.as<cplx<R>>(), rk * Tcols, "round sweep2 G", k));
       // X (Tcols x jq): right singular vectors of C, columns by decreasing singular value
       DBuf X;
-      TRY(X.alloc(c, (size_t)Tcols * jq * sizeof(cplx<R>)));
-      TRY(sig.alloc(c, (size_t)jq * sizeof(R)));
-      TRY(jacobi_launch<R>(c, Cb.as<cplx<R>>(), nullptr, sig.as<R>(), nullptr, (int)jp, (int)jq, 60,
-                           X.as<cplx<R>>()));
+      if (Tcols < rk) {
+        // C taller than wide (rank <= Tcols): C = Q_c R_c with R_c square
+        // (R only), and Jacobi on R_c^H (Tcols x Tcols) gives the same right
+        // vectors as normalised rotated columns, in Tcols - 1 rounds a sweep
+        // instead of rk - 1
+        DBuf Rq, Gq;
+        TRY(Rq.alloc(c, (size_t)Tcols * Tcols * sizeof(cplx<R>)));
+        int64_t got = 0;
+        // Cb holds C^H (Tcols x rk, row-major): C (rk x Tcols) is read through the transposed view, conjugated
+        TRY(tsqr_r<R>(c, Cb.as<cplx<R>>(), L1(rk, 1), L1(Tcols, rk), 1, rk, Tcols, Rq.as<cplx<R>>(), &got));
+        TRY(Gq.alloc(c, (size_t)Tcols * Tcols * sizeof(cplx<R>)));
+        c->launches++;
+        // G = R_c^H: element (i, j) = conj(R_c[j, i])
+        TRY(qtt_copy_strided<R>(Rq.as<cplx<R>>(), L1(Tcols, 1), L1(Tcols, Tcols), Tcols, Tcols, 1, Gq.as<cplx<R>>(),
+                                Tcols, c->stream));
+        TRY(X.alloc(c, (size_t)Tcols * Tcols * sizeof(cplx<R>)));
+        TRY(sig.alloc(c, (size_t)Tcols * sizeof(R)));
+        TRY(jacobi_launch<R>(c, Gq.as<cplx<R>>(), nullptr, sig.as<R>(), nullptr, (int)Tcols, (int)Tcols, 60,
+                             X.as<cplx<R>>()));
+        jq = Tcols;
+      } else {
+        TRY(X.alloc(c, (size_t)Tcols * jq * sizeof(cplx<R>)));
+        TRY(sig.alloc(c, (size_t)jq * sizeof(R)));
+        TRY(jacobi_launch<R>(c, Cb.as<cplx<R>>(), nullptr, sig.as<R>(), nullptr, (int)jp, (int)jq, 60,
+                             X.as<cplx<R>>()));
+      }
       TRY(dbg_finite<R>(c, X.as<cplx<R>>(), Tcols * jq, "round sweep2 X", k));
       int t;
       c->launches++;
@@ -697,9 +723,10 @@ int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* 
     DBuf U, sig;
     TRY(U.alloc(c, (size_t)m * m * sizeof(cplx<R>)));
     TRY(sig.alloc(c, (size_t)m * sizeof(R)));
-    TRY(left_svd<R>(c, C, m, rest, rest, U.as<cplx<R>>(), sig.as<R>()));
+    int64_t nsv = 0;
+    TRY(left_svd<R>(c, C, m, rest, rest, U.as<cplx<R>>(), sig.as<R>(), &nsv));
     c->launches++;
-    TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)m, delta, max_rank, dint, dscal + 1, c->stream));
+    TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)nsv, delta, max_rank, dint, dscal + 1, c->stream));
     int hv[2];
     TRY(sync_read(c, hv, dint, sizeof(hv)));
     const int t = hv[0];
@@ -707,11 +734,11 @@ int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* 
     // core k = U[:, :t] as (rprev, n_k, t)
     TRY(cores[k].alloc(c, (size_t)m * t * sizeof(cplx<R>)));
     c->launches++;
-    TRY(qtt_copy_strided<R>(U.as<cplx<R>>(), L1(m, m), L1(t, 1), m, t, 0, cores[k].as<cplx<R>>(), t, c->stream));
+    TRY(qtt_copy_strided<R>(U.as<cplx<R>>(), L1(m, nsv), L1(t, 1), m, t, 0, cores[k].as<cplx<R>>(), t, c->stream));
     // next C = U_t^H C  (t x rest)
     DBuf Cn;
     TRY(Cn.alloc(c, (size_t)t * rest * sizeof(cplx<R>)));
-    TRY(mm<R>(c, t, rest, m, U.as<cplx<R>>(), 1, m, 1, C, rest, 1, 0, Cn.as<cplx<R>>(), rest, 1));
+    TRY(mm<R>(c, t, rest, m, U.as<cplx<R>>(), 1, nsv, 1, C, rest, 1, 0, Cn.as<cplx<R>>(), rest, 1));
     Cown = std::move(Cn);
     C = Cown.as<cplx<R>>();
     rprev = t;

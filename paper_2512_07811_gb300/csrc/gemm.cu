@@ -18,10 +18,12 @@ namespace {
 //
 // Index arithmetic: the element offsets of the tile's BM rows of A and BN
 // columns of B are computed once per CTA, those of each K-tile's BK values
-// once per tile (one tile ahead, double-buffered), so the loads do no
+// once per tile (two tiles ahead, in a ring of three), so the loads do no
 // division.  Threads walk a tile along whichever index is contiguous in
 // memory (k or m for A, k or n for B) so that neighbouring threads read
-// neighbouring elements.
+// neighbouring elements.  The main loop is software-pipelined: the next
+// tile is loaded into registers while the current one is multiplied from
+// shared memory.
 QTT_HD bool midx_unit_inner(const MIdx& m) { return (m.n2 == 1 ? m.s1 : m.s2) == 1; }
 
 template <class R, int BM, int BN, int BK, int TM, int TN>
@@ -31,10 +33,11 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
                  cplx<R>* __restrict__ C, int splits, int64_t kchunk, cplx<R>* __restrict__ P) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
-  static_assert(2 * BK <= NT, "one thread per K offset");
+  constexpr int LA = BM * BK / NT, LB = BN * BK / NT;  // tile elements each thread loads
+  static_assert(2 * BK <= NT && LA * NT == BM * BK && LB * NT == BN * BK, "tile shape");
   __shared__ cplx<R> As[BK][BM + 1];
   __shared__ cplx<R> Bs[BK][BN + 1];
-  __shared__ int64_t rowA[BM], colB[BN], kOffA[2][BK], kOffB[2][BK];
+  __shared__ int64_t rowA[BM], colB[BN], kOffA[3][BK], kOffB[3][BK];
 
   const int64_t b = blockIdx.z / splits;
   const int split = blockIdx.z - (int)(b * splits);
@@ -44,20 +47,59 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
   const int64_t n0 = (int64_t)blockIdx.x * BN;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
+  const int ntiles = kend > kbeg ? (int)((kend - kbeg + BK - 1) / BK) : 0;
 
   const int64_t offA = midx_off(g.bA, b), offB = midx_off(g.bB, b), offC = midx_off(g.bC, b);
   for (int i = tid; i < BM; i += NT) rowA[i] = (m0 + i < g.M) ? offA + midx_off(g.mA, m0 + i) : -1;
   for (int i = tid; i < BN; i += NT) colB[i] = (n0 + i < g.N) ? offB + midx_off(g.nB, n0 + i) : -1;
-  if (tid < BK) {
-    const int64_t k = kbeg + tid;
-    kOffA[0][tid] = k < kend ? midx_off(g.kA, k) : -1;
-  } else if (tid < 2 * BK) {
-    const int64_t k = kbeg + tid - BK;
-    kOffB[0][tid - BK] = k < kend ? midx_off(g.kB, k) : -1;
-  }
+  // K offsets of tile t live in slot t mod 3, computed two tiles ahead
+  auto koffs = [&](int t) {
+    const int sl = t % 3;
+    if (tid < BK) {
+      const int64_t k = kbeg + (int64_t)t * BK + tid;
+      kOffA[sl][tid] = k < kend ? midx_off(g.kA, k) : -1;
+    } else if (tid < 2 * BK) {
+      const int64_t k = kbeg + (int64_t)t * BK + tid - BK;
+      kOffB[sl][tid - BK] = k < kend ? midx_off(g.kB, k) : -1;
+    }
+  };
+  koffs(0);
+  koffs(1);
   const bool a_kfast = midx_unit_inner(g.kA) && !midx_unit_inner(g.mA);
   const bool b_kfast = midx_unit_inner(g.kB) && !midx_unit_inner(g.nB);
   __syncthreads();
+
+  // global -> registers for tile t (this thread's LA + LB elements)
+  cplx<R> ra[LA], rb[LB];
+  auto fetch = [&](int t) {
+    const int sl = t % 3;
+#pragma unroll
+    for (int l = 0; l < LA; ++l) {
+      const int e = tid + l * NT;
+      const int mm = a_kfast ? e / BK : e % BM;
+      const int kk = a_kfast ? e % BK : e / BM;
+      const int64_t r = rowA[mm], k = kOffA[sl][kk];
+      cplx<R> v(0, 0);
+      if (r >= 0 && k >= 0) {
+        v = A[r + k];
+        if (g.conjA) v.im = -v.im;
+      }
+      ra[l] = v;
+    }
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int e = tid + l * NT;
+      const int nn = b_kfast ? e / BK : e % BN;
+      const int kk = b_kfast ? e % BK : e / BN;
+      const int64_t c = colB[nn], k = kOffB[sl][kk];
+      cplx<R> v(0, 0);
+      if (c >= 0 && k >= 0) {
+        v = B[c + k];
+        if (g.conjB) v.im = -v.im;
+      }
+      rb[l] = v;
+    }
+  };
 
   cplx<R> acc[TM][TN];
 #pragma unroll
@@ -65,41 +107,22 @@ gemm_midx_kernel(GemmDesc g, cplx<R> alpha, cplx<R> beta,
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = cplx<R>(0, 0);
 
-  int cur = 0;
-  for (int64_t k0 = kbeg; k0 < kend; k0 += BK, cur ^= 1) {
+  if (ntiles > 0) fetch(0);
+  for (int t = 0; t < ntiles; ++t) {
 #pragma unroll
-    for (int e = tid; e < BM * BK; e += NT) {
-      const int mm = a_kfast ? e / BK : e % BM;
-      const int kk = a_kfast ? e % BK : e / BM;
-      const int64_t ra = rowA[mm], ka = kOffA[cur][kk];
-      cplx<R> v(0, 0);
-      if (ra >= 0 && ka >= 0) {
-        v = A[ra + ka];
-        if (g.conjA) v.im = -v.im;
-      }
-      As[kk][mm] = v;
+    for (int l = 0; l < LA; ++l) {
+      const int e = tid + l * NT;
+      As[a_kfast ? e % BK : e / BM][a_kfast ? e / BK : e % BM] = ra[l];
     }
 #pragma unroll
-    for (int e = tid; e < BN * BK; e += NT) {
-      const int nn = b_kfast ? e / BK : e % BN;
-      const int kk = b_kfast ? e % BK : e / BN;
-      const int64_t cb = colB[nn], kb = kOffB[cur][kk];
-      cplx<R> v(0, 0);
-      if (cb >= 0 && kb >= 0) {
-        v = B[cb + kb];
-        if (g.conjB) v.im = -v.im;
-      }
-      Bs[kk][nn] = v;
+    for (int l = 0; l < LB; ++l) {
+      const int e = tid + l * NT;
+      Bs[b_kfast ? e % BK : e / BN][b_kfast ? e / BK : e % BN] = rb[l];
     }
     __syncthreads();
-    // offsets of the next K-tile into the other buffer (read after the barrier below)
-    if (tid < BK) {
-      const int64_t k = k0 + BK + tid;
-      kOffA[cur ^ 1][tid] = k < kend ? midx_off(g.kA, k) : -1;
-    } else if (tid < 2 * BK) {
-      const int64_t k = k0 + BK + tid - BK;
-      kOffB[cur ^ 1][tid - BK] = k < kend ? midx_off(g.kB, k) : -1;
-    }
+    // the next tile's loads are in flight while this one is multiplied
+    if (t + 1 < ntiles) fetch(t + 1);
+    koffs(t + 2);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       cplx<R> a[TM], bb[TN];
