@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--rank", type=int, default=64)
     p.add_argument("--no-ms", action="store_true")
     p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--batch", type=int, default=32,
+                   help="trains rounded together in the grouped-batching secondary measurement (0: skip)")
     p.add_argument("--prec", choices=["f32", "tc32"], default="f32",
                    help="fast path arithmetic: float CUDA cores, or tensor cores for the large contractions")
     return p.parse_args()
@@ -290,11 +292,46 @@ def run_ours(args, rank, world, local_rank):
     ctx.sync()
     ms64, flops64 = time_steps(torch, stream, slow, args.fp64_steps, flush)
 
+    batched = None
+    if args.batch > 0:
+        batched = batched_rounding(Q, torch, ctx, stream, flush, r, args.batch, 2)
     ms_part = None
     if not args.no_ms:
         ms_part = ms_laminate(Q, ctx)
     return dict(ms=ms, flops=flops, prof=prof, ms_prof=ms_prof, launches=launches, clocks=clk, e2e_ms=e2e_ms,
-                e2e_flops=e2e_flops, h2d=h2d, d2h=d2h, ms64=ms64, flops64=flops64, ms_part=ms_part)
+                e2e_flops=e2e_flops, h2d=h2d, d2h=d2h, ms64=ms64, flops64=flops64, ms_part=ms_part, batched=batched)
+
+
+def batched_rounding(Q, torch, ctx, stream, flush, r, count, steps):
+    """Grouped batching: `count` independent add + SVD roundings of the
+    workload's shape (rank-r pairs, d = D) in lockstep through tt_round_batch,
+    one launch per kernel per core step for the whole batch.  Returns the
+    model-flop rate and the time per batch (CUDA events, L2 flushed before
+    each timed batch)."""
+    xs = []
+    for b in range(count):
+        x = Q.TT.from_cores(ctx, I.random_tt_cores(D, 2, r, seed=3000 + b, dtype=np.complex128), Q.C64)
+        y = Q.TT.from_cores(ctx, I.random_tt_cores(D, 2, r, seed=4000 + b, dtype=np.complex128), Q.C64)
+        xs.append(Q.tt_add(ctx, 1.0, x, 1.0, y))
+    Q.tt_round_batch(ctx, xs, EPS)  # warm-up
+    ctx.sync()
+    ms, flops = 0.0, 0.0
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush_l2(torch, flush)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ys, _ = Q.tt_round_batch(ctx, xs, EPS)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        flops += sum(round_flops([2] * D, x.ranks, y.ranks) for x, y in zip(xs, ys))
+    return {"workload": "%d independent add + SVD roundings of d=%d rank-%d pairs (rank %d sums), tt_round_batch"
+                        % (count, D, r, 2 * r),
+            "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_batch": ms / steps, "steps": steps,
+            "roundings_per_s": count * steps / (ms * 1e-3)}
 
 
 def ms_laminate(Q, ctx):
@@ -463,6 +500,8 @@ def main():
     line["fast_vs_fp64"] = line["value"] / line["fp64_path"]["value"] if line["fp64_path"]["value"] else None
     if res["ms_part"] is not None:
         line["ms_iteration"] = res["ms_part"]
+    if res.get("batched") is not None:
+        line["batched_rounding"] = res["batched"]
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -156,6 +156,20 @@ QTT_API int tt_mpo_apply(qtt_ctx* ctx, const qtt_mpo* A, const qtt_tt* x, qtt_tt
 QTT_API int tt_round(qtt_ctx* ctx, const qtt_tt* x, double eps, int max_rank, qtt_prec prec, qtt_round_info* info,
              qtt_tt** y);
 
+/* Batched SVD-based rounding: count trains of one shape (equal modes, ranks
+ * and dtype), each rounded exactly as tt_round would (its own ||x||, delta,
+ * truncation ranks and cap), in lockstep: each step of either sweep is one
+ * launch per kernel for the whole batch (one QR block and one Jacobi
+ * cluster per train), so many independent roundings share the device instead
+ * of queueing.  A builder addition for many RVEs or load cases (the grouped
+ * batching the paper lists as future work, Sec. 6); results agree with
+ * tt_round to rounding error (the Jacobi sweeps may visit pairs in another
+ * order).  x: count input handles; y: count outputs (new handles owned by
+ * the caller); info: NULL or count entries.  QTT_ERR_ARG if the shapes
+ * differ; trains with a single core are rounded one by one. */
+QTT_API int tt_round_batch(qtt_ctx* ctx, int count, const qtt_tt* const* x, double eps, int max_rank, qtt_prec prec,
+                           qtt_round_info* info, qtt_tt** y);
+
 /* Randomize-then-orthogonalize rounding of a structured sum
  *     s = sum_t coef[t] * A_t x_t     (A_t = NULL means the identity)
  * without forming s: with the Gaussian sketch train `sketch` (modes = the

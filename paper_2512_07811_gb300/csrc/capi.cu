@@ -513,6 +513,33 @@ int tt_round(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, qtt_prec p, 
                               : round_det<float>(c, x, eps, max_rank, nullptr, info, y);
 }
 
+int tt_round_batch(qtt_ctx* c, int count, const qtt_tt* const* x, double eps, int max_rank, qtt_prec p,
+                   qtt_round_info* info, qtt_tt** y) {
+  if (!c || count < 1 || !x || !y || !(eps >= 0)) return QTT_ERR_ARG;
+  for (int b = 0; b < count; ++b) {
+    if (!valid_tt(x[b])) return QTT_ERR_ARG;
+    y[b] = nullptr;
+  }
+  TRY(check_prec(x[0]->dtype, p));
+  TcScope tc(c, p == QTT_PREC_TC32);
+  int st = x[0]->dtype == QTT_C128 ? round_det_batch<double>(c, count, x, eps, max_rank, info, y)
+                                   : round_det_batch<float>(c, count, x, eps, max_rank, info, y);
+  if (st != QTT_ERR_UNSUPPORTED) return st;
+  // shapes the lockstep path does not take: one train at a time
+  for (int b = 0; b < count; ++b) {
+    st = x[b]->dtype == QTT_C128 ? round_det<double>(c, x[b], eps, max_rank, nullptr, info ? info + b : nullptr, y + b)
+                                 : round_det<float>(c, x[b], eps, max_rank, nullptr, info ? info + b : nullptr, y + b);
+    if (st) {
+      for (int e = 0; e < b; ++e) {
+        tt_free(y[e]);
+        y[e] = nullptr;
+      }
+      return st;
+    }
+  }
+  return QTT_OK;
+}
+
 int tt_round_sketched(qtt_ctx* c, int nterms, const qtt_complex* coef, const qtt_mpo* const* ops,
                       const qtt_tt* const* xs, const qtt_tt* sketch, double eps, int max_rank, qtt_prec p,
                       qtt_round_info* info, qtt_tt** y) {

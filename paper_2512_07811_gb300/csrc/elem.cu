@@ -5,6 +5,8 @@
 // operand's index first (major).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -359,6 +361,41 @@ __global__ void adjoint_core_kernel(const cplx<R>* __restrict__ D, int64_t g0, i
 #define CHECK_LAUNCH() return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA
 
 template <class R>
+__global__ void copy_batch_kernel(const cplx<R>* __restrict__ in, int64_t ib, MIdx rows, MIdx cols, int64_t nrows,
+                                  int64_t ncols, int conj_in, cplx<R>* __restrict__ out, int64_t ldo, int64_t ob) {
+  const int64_t b = blockIdx.y, tot = nrows * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncols, j = e - i * ncols;
+    cplx<R> v = in[b * ib + midx_off(rows, i) + midx_off(cols, j)];
+    if (conj_in) v.im = -v.im;
+    out[b * ob + i * ldo + j] = v;
+  }
+}
+
+template <class R>
+__global__ void mask_cols_kernel(cplx<R>* __restrict__ X, int64_t bs, int64_t rows, int64_t cols, int64_t ld,
+                                 const int* __restrict__ t, int tstride) {
+  const int64_t b = blockIdx.y, tot = rows * cols;
+  const int tb = t[b * tstride];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e - i * cols;
+    if (j >= tb) X[b * bs + i * ld + j] = cplx<R>(0, 0);
+  }
+}
+
+template <class R>
+__global__ void crop_kernel(const cplx<R>* __restrict__ src, int64_t sb, int64_t r0, int64_t n, int64_t r1,
+                            cplx<R>* const* __restrict__ dst, const int* __restrict__ t0, const int* __restrict__ t1) {
+  const int64_t b = blockIdx.y;
+  const int64_t a0 = t0[b], a1 = t1[b], tot = a0 * n * a1;
+  cplx<R>* d = dst[b];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / (n * a1), rem = e - i * n * a1, k = rem / a1, j = rem - k * a1;
+    d[e] = src[b * sb + (i * n + k) * r1 + j];
+  }
+}
+
+template <class R>
 int qtt_place_block(const cplx<R>* src, int64_t s0, int64_t n, int64_t s1, cplx<R>* dst, int64_t d1,
                     int64_t off0, int64_t off1, cplx<R> scale, cudaStream_t s) {
   int64_t total = s0 * n * s1;
@@ -496,3 +533,44 @@ int qtt_adjoint_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64
   template int qtt_adjoint_core<R>(const cplx<R>*, int64_t, int64_t, int64_t, int64_t, cplx<R>*, cudaStream_t);
 INST(double)
 INST(float)
+
+static unsigned grid_for(int64_t tot) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 4096)); }
+
+template <class R>
+int qtt_copy_batch(const cplx<R>* in, int64_t ib, MIdx rows, MIdx cols, int64_t nrows, int64_t ncols, int conj_in,
+                   cplx<R>* out, int64_t ldo, int64_t ob, int batch, cudaStream_t s) {
+  if (batch < 1 || nrows * ncols == 0) return QTT_OK;
+  if (batch > 65535) return QTT_ERR_ARG;
+  copy_batch_kernel<R><<<dim3(grid_for(nrows * ncols), batch), 256, 0, s>>>(in, ib, rows, cols, nrows, ncols, conj_in,
+                                                                            out, ldo, ob);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template <class R>
+int qtt_mask_cols_batch(cplx<R>* X, int64_t bs, int64_t rows, int64_t cols, int64_t ld, const int* t, int tstride,
+                        int batch, cudaStream_t s) {
+  if (batch < 1 || rows * cols == 0) return QTT_OK;
+  if (batch > 65535) return QTT_ERR_ARG;
+  mask_cols_kernel<R><<<dim3(grid_for(rows * cols), batch), 256, 0, s>>>(X, bs, rows, cols, ld, t, tstride);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template <class R>
+int qtt_crop_batch(const cplx<R>* src, int64_t sb, int64_t r0, int64_t n, int64_t r1, cplx<R>* const* dst,
+                   const int* t0, const int* t1, int batch, cudaStream_t s) {
+  if (batch < 1) return QTT_OK;
+  if (batch > 65535) return QTT_ERR_ARG;
+  crop_kernel<R><<<dim3(grid_for(r0 * n * r1), batch), 256, 0, s>>>(src, sb, r0, n, r1, dst, t0, t1);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+template int qtt_copy_batch<double>(const zc*, int64_t, MIdx, MIdx, int64_t, int64_t, int, zc*, int64_t, int64_t, int,
+                                    cudaStream_t);
+template int qtt_copy_batch<float>(const cc*, int64_t, MIdx, MIdx, int64_t, int64_t, int, cc*, int64_t, int64_t, int,
+                                   cudaStream_t);
+template int qtt_mask_cols_batch<double>(zc*, int64_t, int64_t, int64_t, int64_t, const int*, int, int, cudaStream_t);
+template int qtt_mask_cols_batch<float>(cc*, int64_t, int64_t, int64_t, int64_t, const int*, int, int, cudaStream_t);
+template int qtt_crop_batch<double>(const zc*, int64_t, int64_t, int64_t, int64_t, zc* const*, const int*,
+                                    const int*, int, cudaStream_t);
+template int qtt_crop_batch<float>(const cc*, int64_t, int64_t, int64_t, int64_t, cc* const*, const int*, const int*,
+                                   int, cudaStream_t);

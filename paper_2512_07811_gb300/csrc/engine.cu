@@ -695,6 +695,247 @@ template int round_det<double>(qtt_ctx*, const qtt_tt*, double, int, const int*,
 template int round_det<float>(qtt_ctx*, const qtt_tt*, double, int, const int*, qtt_round_info*, qtt_tt**,
                                bool);
 
+// ------------------------------------------------ batched deterministic round
+// B trains of one shape (same modes and ranks) rounded in lockstep by the
+// algorithm of round_det: every step of either sweep is one launch per kernel
+// for the whole batch -- batched GEMMs, one QR CTA per train, one Jacobi
+// cluster per train -- and the truncation sweep needs one host
+// synchronisation per core for all trains.  Each train keeps its own
+// truncation: a bond is carried at the largest rank of the batch, the
+// singular vectors beyond a train's own rank are zeroed, so that its padded
+// rows and columns stay exactly zero, and the outputs are cropped to each
+// train's ranks.  QTT_ERR_UNSUPPORTED for shapes it does not take (the
+// caller then rounds the trains one by one).
+template <class R>
+static GemmDesc bgemm(int64_t B, int64_t M, int64_t N, int64_t K, int64_t bA, MIdx mA, MIdx kA, int64_t bB, MIdx kB,
+                      MIdx nB, int64_t bC, MIdx mC, MIdx nC, int conjA = 0, int conjB = 0) {
+  GemmDesc g;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = B;
+  g.bA = L1(B, bA);
+  g.mA = mA;
+  g.kA = kA;
+  g.bB = L1(B, bB);
+  g.kB = kB;
+  g.nB = nB;
+  g.bC = L1(B, bC);
+  g.mC = mC;
+  g.nC = nC;
+  g.conjA = conjA;
+  g.conjB = conjB;
+  return g;
+}
+
+template <class R>
+int round_det_batch(qtt_ctx* c, int B, const qtt_tt* const* xs, double eps, int max_rank, qtt_round_info* infos,
+                    qtt_tt** ys) {
+  typedef cplx<R> C;
+  const qtt_tt* x0 = xs[0];
+  const int d = x0->d;
+  for (int b = 1; b < B; ++b)
+    if (xs[b]->d != d || xs[b]->n != x0->n || xs[b]->r != x0->r || xs[b]->dtype != x0->dtype) return QTT_ERR_ARG;
+  if (d < 2 || B > 65535) return QTT_ERR_UNSUPPORTED;
+  const std::vector<int>& n = x0->n;
+  const std::vector<int>& r = x0->r;
+  // the trains side by side: train b at X + b * xst, core k at offset off[k]
+  const int64_t xst = (int64_t)(x0->bytes / sizeof(C));
+  DBuf Xall;
+  TRY(Xall.alloc(c, (size_t)B * x0->bytes));
+  for (int b = 0; b < B; ++b)
+    if (cudaMemcpyAsync(Xall.as<char>() + (size_t)b * x0->bytes, xs[b]->data, x0->bytes, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+      return QTT_ERR_CUDA;
+  auto A = [&](int k) { return Xall.as<C>() + x0->off[k] / sizeof(C); };
+  // ---- sweep 1: R factors, B per core
+  std::vector<DBuf> Rf(d);
+  std::vector<int64_t> rp(d + 1, 1);
+  for (int k = 0; k < d - 1; ++k) {
+    const int64_t a0 = r[k], nk = n[k], a1 = r[k + 1];
+    const C* M = A(k);
+    int64_t mst = xst;
+    DBuf Mb;
+    if (k > 0) {
+      TRY(Mb.alloc(c, (size_t)B * rp[k] * nk * a1 * sizeof(C)));
+      TRY(gemm<R>(c, bgemm<R>(B, rp[k], nk * a1, a0, rp[k] * a0, L1(rp[k], a0), L1(a0, 1), xst, L1(a0, nk * a1),
+                              L1(nk * a1, 1), rp[k] * nk * a1, L1(rp[k], nk * a1), L1(nk * a1, 1)),
+                  Rf[k - 1].as<C>(), A(k), Mb.as<C>()));
+      M = Mb.as<C>();
+      mst = rp[k] * nk * a1;
+    }
+    const int64_t m = rp[k] * nk;
+    rp[k + 1] = std::min(m, a1);
+    DBuf W;
+    TRY(Rf[k].alloc(c, (size_t)B * rp[k + 1] * a1 * sizeof(C)));
+    TRY(W.alloc(c, (size_t)B * m * a1 * sizeof(C)));
+    TRY(qr_launch<R>(c, M, L1(B, mst), L1(m, a1), L1(a1, 1), 0, m, a1, m, 0, B, W.as<C>(), Rf[k].as<C>(),
+                     rp[k + 1] * a1, a1));
+  }
+  // ---- norms from the orthogonality centres, thresholds per train
+  DBuf scal;
+  TRY(scal.alloc(c, (size_t)B * (sizeof(double) + 4 * sizeof(int))));
+  double* dnorm = scal.as<double>();
+  int* dtr = reinterpret_cast<int*>(dnorm + B);
+  std::vector<double> nrm(B), delta(B);
+  {
+    const int64_t M = rp[d - 1], N = n[d - 1], K = r[d - 1];
+    DBuf Cc;
+    TRY(Cc.alloc(c, (size_t)B * M * N * sizeof(C)));
+    TRY(gemm<R>(c, bgemm<R>(B, M, N, K, M * K, L1(M, K), L1(K, 1), xst, L1(K, N), L1(N, 1), M * N, L1(M, N),
+                            L1(N, 1)),
+                Rf[d - 2].as<C>(), A(d - 1), Cc.as<C>()));
+    for (int b = 0; b < B; ++b) {
+      c->launches++;
+      TRY(qtt_sumsq<R>(Cc.as<C>() + (size_t)b * M * N, M * N, dnorm + b, c->stream));
+    }
+    TRY(sync_read(c, nrm.data(), dnorm, (size_t)B * sizeof(double)));
+    for (int b = 0; b < B; ++b) {
+      nrm[b] = sqrt(nrm[b]);
+      delta[b] = eps * nrm[b] / sqrt((double)(d - 1));
+    }
+    if (cudaMemcpyAsync(dnorm, delta.data(), (size_t)B * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+      return QTT_ERR_CUDA;
+  }
+  // ---- sweep 2
+  std::vector<DBuf> newc(d);
+  std::vector<int> tmax(d + 1, 1);
+  std::vector<std::vector<int>> tb(B, std::vector<int>(d + 1, 1));
+  std::vector<double> tail2(B, 0.0);
+  std::vector<int> capped(B, 0);
+  std::vector<int> hv((size_t)4 * B);
+  DBuf Tb;
+  const C* T = A(d - 1);
+  int64_t tst = xst;
+  for (int k = d - 1; k >= 1; --k) {
+    const int64_t nk = n[k], Tcols = nk * tmax[k + 1], rk = rp[k], a0 = r[k];
+    if (!(Tcols <= 4 * rk || Tcols * rk <= 4096)) return QTT_ERR_UNSUPPORTED;
+    // C_b^H (Tcols x rk) = (R_{k-1,b} T_b)^H, written transposed
+    DBuf Cb, Rq, Gq, W2, X, sig;
+    TRY(Cb.alloc(c, (size_t)B * rk * Tcols * sizeof(C)));
+    TRY(gemm<R>(c, bgemm<R>(B, rk, Tcols, a0, rk * a0, L1(rk, a0), L1(a0, 1), tst, L1(a0, Tcols), L1(Tcols, 1),
+                            rk * Tcols, L1(rk, 1), L1(Tcols, rk), 1, 1),
+                Rf[k - 1].as<C>(), T, Cb.as<C>()));
+    C* G = Cb.as<C>();
+    int64_t gq = rk;
+    if (Tcols < rk) {
+      // C taller than wide: R-only QR of C_b (read conjugated through C_b^H), Jacobi on R_b^H
+      TRY(Rq.alloc(c, (size_t)B * Tcols * Tcols * sizeof(C)));
+      TRY(W2.alloc(c, (size_t)B * rk * Tcols * sizeof(C)));
+      TRY(qr_launch<R>(c, Cb.as<C>(), L1(B, rk * Tcols), L1(rk, 1), L1(Tcols, rk), 1, rk, Tcols, rk, 0, B,
+                       W2.as<C>(), Rq.as<C>(), Tcols * Tcols, Tcols));
+      TRY(Gq.alloc(c, (size_t)B * Tcols * Tcols * sizeof(C)));
+      c->launches++;
+      TRY(qtt_copy_batch<R>(Rq.as<C>(), Tcols * Tcols, L1(Tcols, 1), L1(Tcols, Tcols), Tcols, Tcols, 1, Gq.as<C>(),
+                            Tcols, Tcols * Tcols, B, c->stream));
+      G = Gq.as<C>();
+      gq = Tcols;
+    }
+    const int64_t jq = gq;
+    TRY(X.alloc(c, (size_t)B * Tcols * jq * sizeof(C)));
+    TRY(sig.alloc(c, (size_t)B * jq * sizeof(R)));
+    int bsz = 0;
+    if (qtt_jacobi_block_plan<R>((int)Tcols, (int)jq, &bsz)) {
+      int idx;
+      int* slot = prof_sweep_slot(c, &idx);
+      c->launches++;
+      cudaEvent_t ev = prof_begin(c);
+      TRY(qtt_jacobi_block<R>(G, sig.as<R>(), X.as<C>(), (int)Tcols, (int)jq, 60, slot, c->stream, B));
+      prof_end(c, ev, PK_JACOBI, 0.0, (double)B * Tcols * jq * sizeof(C) * 2.0, idx,
+               B * jacobi_sweep_flops((double)Tcols, (double)jq));
+    } else {
+      for (int b = 0; b < B; ++b)
+        TRY(jacobi_launch<R>(c, G + (size_t)b * Tcols * jq, nullptr, sig.as<R>() + (size_t)b * jq, nullptr,
+                             (int)Tcols, (int)jq, 60, X.as<C>() + (size_t)b * Tcols * jq));
+    }
+    c->launches++;
+    TRY(qtt_trunc_rank_batch<R>(sig.as<R>(), (int)jq, dnorm, max_rank, dtr, B, c->stream));
+    TRY(sync_read(c, hv.data(), dtr, (size_t)4 * B * sizeof(int)));
+    int tm = 1;
+    for (int b = 0; b < B; ++b) {
+      double tl;
+      memcpy(&tl, &hv[(size_t)4 * b + 2], sizeof(double));
+      tb[b][k] = hv[(size_t)4 * b];
+      capped[b] |= hv[(size_t)4 * b + 1];
+      tail2[b] += tl * tl;
+      tm = std::max(tm, tb[b][k]);
+    }
+    tmax[k] = tm;
+    // singular vectors beyond each train's own rank -> 0
+    c->launches++;
+    TRY(qtt_mask_cols_batch<R>(X.as<C>(), Tcols * jq, Tcols, jq, jq, dtr, 4, B, c->stream));
+    // padded core k of train b = X_b[:, :tm]^H (tm x Tcols)
+    TRY(newc[k].alloc(c, (size_t)B * tm * Tcols * sizeof(C)));
+    c->launches++;
+    TRY(qtt_copy_batch<R>(X.as<C>(), Tcols * jq, L1(tm, 1), L1(Tcols, jq), tm, Tcols, 1, newc[k].as<C>(), Tcols,
+                          tm * Tcols, B, c->stream));
+    // P_b = T_b X_b[:, :tm] (a0 x tm); T_{k-1,b} = A_{k-1,b} P_b
+    DBuf P, Tn;
+    TRY(P.alloc(c, (size_t)B * a0 * tm * sizeof(C)));
+    TRY(gemm<R>(c, bgemm<R>(B, a0, tm, Tcols, tst, L1(a0, Tcols), L1(Tcols, 1), Tcols * jq, L1(Tcols, jq),
+                            L1(tm, 1), a0 * tm, L1(a0, tm), L1(tm, 1)),
+                T, X.as<C>(), P.as<C>()));
+    const int64_t pr = (int64_t)r[k - 1] * n[k - 1];
+    TRY(Tn.alloc(c, (size_t)B * pr * tm * sizeof(C)));
+    TRY(gemm<R>(c, bgemm<R>(B, pr, tm, a0, xst, L1(pr, a0), L1(a0, 1), a0 * tm, L1(a0, tm), L1(tm, 1), pr * tm,
+                            L1(pr, tm), L1(tm, 1)),
+                A(k - 1), P.as<C>(), Tn.as<C>()));
+    Tb = std::move(Tn);
+    T = Tb.as<C>();
+    tst = pr * tm;
+  }
+  // ---- outputs cropped to each train's ranks
+  std::vector<C*> ptrs((size_t)d * B);
+  std::vector<int> t01((size_t)2 * d * B);
+  for (int b = 0; b < B; ++b) {
+    std::vector<int> rb(d + 1, 1);
+    for (int k = 1; k < d; ++k) rb[k] = tb[b][k];
+    int st;
+    ys[b] = tt_alloc(c, d, n, rb, x0->dtype, &st);
+    if (!ys[b]) {
+      for (int e = 0; e < b; ++e) {
+        tt_free(ys[e]);
+        ys[e] = nullptr;
+      }
+      return st;
+    }
+    for (int k = 0; k < d; ++k) {
+      ptrs[(size_t)k * B + b] = reinterpret_cast<C*>(static_cast<char*>(ys[b]->data) + ys[b]->off[k]);
+      t01[(size_t)k * B + b] = rb[k];
+      t01[(size_t)d * B + (size_t)k * B + b] = rb[k + 1];
+    }
+    if (infos) {
+      infos[b].norm = nrm[b];
+      infos[b].delta = delta[b];
+      infos[b].tail = sqrt(tail2[b]);
+      infos[b].err = -1;
+      infos[b].capped = capped[b];
+      infos[b].max_rank_out = *std::max_element(rb.begin(), rb.end());
+    }
+  }
+  DBuf meta;
+  TRY(meta.alloc(c, ptrs.size() * sizeof(C*) + t01.size() * sizeof(int)));
+  C** dptrs = meta.as<C*>();
+  int* dt01 = reinterpret_cast<int*>(dptrs + ptrs.size());
+  if (cudaMemcpyAsync(dptrs, ptrs.data(), ptrs.size() * sizeof(C*), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(dt01, t01.data(), t01.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return QTT_ERR_CUDA;
+  tmax[0] = tmax[d] = 1;
+  for (int k = 0; k < d; ++k) {
+    const C* src = k == 0 ? T : newc[k].as<C>();
+    c->launches++;
+    TRY(qtt_crop_batch<R>(src, (int64_t)tmax[k] * n[k] * tmax[k + 1], tmax[k], n[k], tmax[k + 1],
+                          dptrs + (size_t)k * B, dt01 + (size_t)k * B, dt01 + (size_t)d * B + (size_t)k * B, B,
+                          c->stream));
+  }
+  // the host arrays above were copied from pageable memory (staged before return)
+  return QTT_OK;
+}
+
+template int round_det_batch<double>(qtt_ctx*, int, const qtt_tt* const*, double, int, qtt_round_info*, qtt_tt**);
+template int round_det_batch<float>(qtt_ctx*, int, const qtt_tt* const*, double, int, qtt_round_info*, qtt_tt**);
+
 // ------------------------------------------------------------------- TT-SVD
 template <class R>
 int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* dense, double eps, int max_rank,

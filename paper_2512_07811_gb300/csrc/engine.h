@@ -96,6 +96,9 @@ template <class R>
 int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* forced, qtt_round_info* info,
               qtt_tt** yout, bool left_orth = false);
 template <class R>
+int round_det_batch(qtt_ctx* c, int B, const qtt_tt* const* xs, double eps, int max_rank, qtt_round_info* infos,
+                    qtt_tt** ys);
+template <class R>
 int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* const* ops, const qtt_tt* const* xs,
                    const qtt_tt* S, double eps, int max_rank, qtt_round_info* info, qtt_tt** yout);
 template <class R>

@@ -98,6 +98,25 @@ int qtt_jacobi_cluster(const cplx<R>* G, R* sigma, cplx<R>* Vsorted, cplx<R>* Us
 // block-cyclic one-sided Jacobi over a cluster (columns split into blocks, linalg.cu); no rotations output
 template <class R>
 int qtt_jacobi_block_plan(int p, int q, int* bs_out);
+// batch: that many p x q matrices back to back (sigma q apart, Usorted p*q apart), one cluster each
 template <class R>
 int qtt_jacobi_block(const cplx<R>* G, R* sigma, cplx<R>* Usorted, int p, int q, int max_sweeps, int* sweeps,
-                     cudaStream_t s);
+                     cudaStream_t s, int batch = 1);
+// truncation rule for a batch of sorted singular-value vectors (q apart), delta per vector;
+// out[4b] = t, out[4b+1] = capped, out[4b+2..3] = discarded tail (double)
+template <class R>
+int qtt_trunc_rank_batch(const R* sigma, int q, const double* delta, int max_rank, int* out, int batch,
+                         cudaStream_t s);
+// ---- batched copies (elem.cu)
+// out[b*ob + i*ldo + j] = op(in[b*ib + rows(i) + cols(j)]), op = conj if conj_in
+template <class R>
+int qtt_copy_batch(const cplx<R>* in, int64_t ib, MIdx rows, MIdx cols, int64_t nrows, int64_t ncols, int conj_in,
+                   cplx<R>* out, int64_t ldo, int64_t ob, int batch, cudaStream_t s);
+// zero columns j >= t[b * tstride] of each rows x cols matrix (leading dimension ld, matrices bs apart)
+template <class R>
+int qtt_mask_cols_batch(cplx<R>* X, int64_t bs, int64_t rows, int64_t cols, int64_t ld, const int* t, int tstride,
+                        int batch, cudaStream_t s);
+// dst[b] (t0[b] x n x t1[b]) = src[b][:t0[b], :, :t1[b]] of the padded r0 x n x r1 cores (src cores sb apart)
+template <class R>
+int qtt_crop_batch(const cplx<R>* src, int64_t sb, int64_t r0, int64_t n, int64_t r1, cplx<R>* const* dst,
+                   const int* t0, const int* t1, int batch, cudaStream_t s);

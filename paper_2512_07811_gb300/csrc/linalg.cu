@@ -326,9 +326,8 @@ jacobi_kernel(cplx<R>* __restrict__ Gbase, cplx<R>* __restrict__ Vbase, R* __res
 // sqrt(sum_{j >= t} s_j^2) <= delta, then capped at max_rank.  Writes t and
 // whether the cap cut a rank the tolerance asked for, plus the discarded tail.
 template <class R>
-__global__ void trunc_rank_kernel(const R* __restrict__ s, int q, double delta, int max_rank,
-                                  int* __restrict__ out /* [t, capped] */, double* __restrict__ tail_out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void trunc_rank_body(const R* __restrict__ s, int q, double delta, int max_rank,
+                                int* __restrict__ out /* [t, capped] */, double* __restrict__ tail_out) {
   double tail2 = 0.0;
   int t = q;
   // walk from the end: tail2 after including s[j] is sum_{i >= j} s_i^2
@@ -353,6 +352,12 @@ __global__ void trunc_rank_kernel(const R* __restrict__ s, int q, double delta, 
   out[0] = t;
   out[1] = capped;
   if (tail_out) *tail_out = sqrt(tl);
+}
+
+template <class R>
+__global__ void trunc_rank_kernel(const R* __restrict__ s, int q, double delta, int max_rank,
+                                  int* __restrict__ out, double* __restrict__ tail_out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) trunc_rank_body<R>(s, q, delta, max_rank, out, tail_out);
 }
 
 // ------------------------------------------- one-sided Jacobi over many CTAs
@@ -1178,6 +1183,27 @@ int qtt_jacobi(cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, in
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
 
+// one block per matrix of a batch: sigma q apart, delta per matrix, out[4 b
+// .. 4 b + 3] = (t, capped, tail as a double)
+template <class R>
+__global__ void trunc_rank_batch_kernel(const R* __restrict__ s, int q, const double* __restrict__ delta,
+                                        int max_rank, int* __restrict__ out) {
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0)
+    trunc_rank_body<R>(s + (size_t)b * q, q, delta[b], max_rank, out + 4 * b,
+                       reinterpret_cast<double*>(out + 4 * b + 2));
+}
+
+template <class R>
+int qtt_trunc_rank_batch(const R* sigma, int q, const double* delta, int max_rank, int* out, int batch,
+                         cudaStream_t s) {
+  if (batch < 1) return QTT_OK;
+  trunc_rank_batch_kernel<R><<<batch, 32, 0, s>>>(sigma, q, delta, max_rank, out);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+template int qtt_trunc_rank_batch<double>(const double*, int, const double*, int, int*, int, cudaStream_t);
+template int qtt_trunc_rank_batch<float>(const float*, int, const double*, int, int*, int, cudaStream_t);
+
 template <class R>
 int qtt_trunc_rank(const R* sigma, int q, double delta, int max_rank, int* out, double* tail, cudaStream_t s) {
   trunc_rank_kernel<R><<<1, 32, 0, s>>>(sigma, q, delta, max_rank, out, tail);
@@ -1403,6 +1429,11 @@ jacobi_block_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out, 
   cg::cluster_group cluster = cg::this_cluster();
   constexpr int NB = 2 * NC;
   const int rank = (int)cluster.block_rank();
+  // one cluster per matrix of a batch (blockIdx.y): matrices p*q apart, sigma q apart
+  Gin += (size_t)blockIdx.y * p * q;
+  sigma_out += (size_t)blockIdx.y * q;
+  if (Us_out) Us_out += (size_t)blockIdx.y * p * q;
+  if (blockIdx.y != 0) sweeps_out = nullptr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>* slots = reinterpret_cast<cplx<R>*>(smem_raw);  // [4][bs][p]
   R* norms = reinterpret_cast<R*>(slots + (size_t)4 * bs * p);  // [NB * bs]
@@ -1534,11 +1565,12 @@ jacobi_block_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out, 
 
 template <class R, int NC, int RPL>
 static int launch_jacobi_block(const cplx<R>* G, R* sigma, cplx<R>* Us, int p, int q, int bs, int max_sweeps,
-                               int* sweeps, cudaStream_t s) {
+                               int* sweeps, cudaStream_t s, int batch) {
   const size_t sm = jacobi_block_bytes<R>(p, bs, NC);
   if (qtt_allow_max_smem((const void*)jacobi_block_kernel<R, NC, RPL>) != QTT_OK) return QTT_ERR_CUDA;
+  if (batch < 1 || batch > 65535) return QTT_ERR_ARG;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(NC, 1, 1);
+  cfg.gridDim = dim3(NC, (unsigned)batch, 1);
   cfg.blockDim = dim3(32 * bs, 1, 1);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = s;
@@ -1577,7 +1609,7 @@ int qtt_jacobi_block_plan(int p, int q, int* bs_out) {
 
 template <class R>
 int qtt_jacobi_block(const cplx<R>* G, R* sigma, cplx<R>* Usorted, int p, int q, int max_sweeps, int* sweeps,
-                     cudaStream_t s) {
+                     cudaStream_t s, int batch) {
   int bs = 0;
   const int nc = qtt_jacobi_block_plan<R>(p, q, &bs);
   if (!nc) return QTT_ERR_UNSUPPORTED;
@@ -1586,18 +1618,18 @@ int qtt_jacobi_block(const cplx<R>* G, R* sigma, cplx<R>* Usorted, int p, int q,
   int st;
   constexpr int RMAX = sizeof(R) == 8 ? 8 : 16;  // rows per lane: two columns of them live in registers
   if (nc == 8)
-    st = rpl == 4 ? launch_jacobi_block<R, 8, 4>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s)
-       : rpl == 8 ? launch_jacobi_block<R, 8, 8>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s)
-                  : launch_jacobi_block<R, 8, RMAX>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s);
+    st = rpl == 4 ? launch_jacobi_block<R, 8, 4>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s, batch)
+       : rpl == 8 ? launch_jacobi_block<R, 8, 8>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s, batch)
+                  : launch_jacobi_block<R, 8, RMAX>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s, batch);
   else
-    st = rpl == 4 ? launch_jacobi_block<R, 4, 4>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s)
-       : rpl == 8 ? launch_jacobi_block<R, 4, 8>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s)
-                  : launch_jacobi_block<R, 4, RMAX>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s);
+    st = rpl == 4 ? launch_jacobi_block<R, 4, 4>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s, batch)
+       : rpl == 8 ? launch_jacobi_block<R, 4, 8>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s, batch)
+                  : launch_jacobi_block<R, 4, RMAX>(G, sigma, Usorted, p, q, bs, max_sweeps, sweeps, s, batch);
   if (st != QTT_OK) return st;
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
 
 template int qtt_jacobi_block_plan<double>(int, int, int*);
 template int qtt_jacobi_block_plan<float>(int, int, int*);
-template int qtt_jacobi_block<double>(const zc*, double*, zc*, int, int, int, int*, cudaStream_t);
-template int qtt_jacobi_block<float>(const cc*, float*, cc*, int, int, int, int*, cudaStream_t);
+template int qtt_jacobi_block<double>(const zc*, double*, zc*, int, int, int, int*, cudaStream_t, int);
+template int qtt_jacobi_block<float>(const cc*, float*, cc*, int, int, int, int*, cudaStream_t, int);

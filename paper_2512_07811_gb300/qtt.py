@@ -111,6 +111,8 @@ _sig("tt_add", C.c_int, [_P, Complex, _P, Complex, _P, C.POINTER(_P)])
 _sig("tt_hadamard", C.c_int, [_P, _P, _P, C.POINTER(_P)])
 _sig("tt_mpo_apply", C.c_int, [_P, _P, _P, C.POINTER(_P)])
 _sig("tt_round", C.c_int, [_P, _P, C.c_double, C.c_int, C.c_int, C.POINTER(RoundInfo), C.POINTER(_P)])
+_sig("tt_round_batch", C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_double, C.c_int, C.c_int, C.POINTER(RoundInfo),
+                                 C.POINTER(_P)])
 _sig("tt_round_sketched", C.c_int, [_P, C.c_int, C.POINTER(Complex), C.POINTER(_P), C.POINTER(_P), _P,
                                     C.c_double, C.c_int, C.c_int, C.POINTER(RoundInfo), C.POINTER(_P)])
 _sig("tt_dot", C.c_int, [_P, _P, _P, C.POINTER(C.c_double)])
@@ -139,7 +141,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_tt_create", "qtt_tt_destroy", "qtt_tt_ncores", "qtt_tt_ranks", "qtt_tt_modes", "qtt_tt_dtype",
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
-            "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_sketched", "tt_dot", "tt_norm",
+            "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_norm",
             "tt_from_dense", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
             "ms_homogenize_batch", "qtt_cgemm", "qtt_cgemm_noalloc",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
@@ -341,6 +343,19 @@ def tt_round(ctx: Context, x: TT, eps: float, max_rank: int = 0, prec=None):
     info = RoundInfo()
     _check(_lib.tt_round(ctx.h, x.h, float(eps), int(max_rank), int(prec), C.byref(info), C.byref(h)), "tt_round")
     return TT(ctx, h), info
+
+
+def tt_round_batch(ctx: Context, xs, eps: float, max_rank: int = 0, prec=None):
+    """Round trains of one shape together; returns (list of TT, list of RoundInfo)."""
+    xs = list(xs)
+    if prec is None:
+        prec = PREC_F64 if xs[0].dtype == C128 else PREC_F32
+    B = len(xs)
+    hin = (_P * B)(*[x.h for x in xs])
+    hout = (_P * B)()
+    infos = (RoundInfo * B)()
+    _check(_lib.tt_round_batch(ctx.h, B, hin, float(eps), int(max_rank), int(prec), infos, hout), "tt_round_batch")
+    return [TT(ctx, _P(hout[b])) for b in range(B)], [infos[b] for b in range(B)]
 
 
 def tt_round_sketched(ctx: Context, terms, sketch: TT, eps: float, max_rank: int = 0, prec=None):

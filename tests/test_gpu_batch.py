@@ -47,3 +47,82 @@ def test_batch_equals_sequential_and_is_faster(Q):
         np.testing.assert_array_equal(a[:, :2], b[:, :2])
     assert all(r.iterations[0] == 6 for r in reps)
     assert t_bat < t_seq
+
+
+def _rank_limited(seed, d, n, K, k_true):
+    """A train of bond ranks K whose true ranks are min(K, k_true): the last
+    K - k_true slices of every inner bond are zero."""
+    rng = np.random.default_rng(seed)
+    ranks = [1] + [min(K, n ** min(k, d - k)) for k in range(1, d)] + [1]
+    cores = []
+    for k in range(d):
+        c = (rng.standard_normal((ranks[k], n, ranks[k + 1]))
+             + 1j * rng.standard_normal((ranks[k], n, ranks[k + 1]))) / np.sqrt(2 * K)
+        if k < d - 1 and ranks[k + 1] > k_true:
+            c[:, :, k_true:] = 0
+        cores.append(c)
+    return cores
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_round_batch_equals_one_by_one(Q, fp32):
+    """Trains of one shape but different true ranks (so the lockstep path pads
+    and crops) plus flat random trains truncated at 1e-3: every output has the
+    ranks of its own tt_round and agrees with it (1e-10 FP64, 1e-5 FP32) and
+    with the oracle's rounding."""
+    from oracle import tt as T
+    ctx = Q.Context(0)
+    dt = Q.C64 if fp32 else Q.C128
+    trains = []
+    for b, kt in enumerate([3, 9, 16, 16, 5, 12]):
+        base = _rank_limited(200 + b, 10, 2, 16, kt)
+        trains.append(T.tt_add(base, base, 1.0, 0.75))
+    rng_eps = 1e-6 if fp32 else 1e-10
+    xs = [Q.TT.from_cores(ctx, c, dt) for c in trains]
+    ys, infos = Q.tt_round_batch(ctx, xs, rng_eps)
+    for b, (x, y, inf) in enumerate(zip(xs, ys, infos)):
+        y1, inf1 = Q.tt_round(ctx, x, rng_eps)
+        assert y.ranks == y1.ranks, (b, y.ranks, y1.ranks)
+        assert abs(inf.norm - inf1.norm) <= 1e-12 * inf1.norm
+        ref, _ = T.tt_round(trains[b], rng_eps)
+        assert y.ranks == T.tt_ranks(ref)
+        tol = 1e-5 if fp32 else 1e-10
+        yc = [c.astype(np.complex128) for c in y.cores()]
+        d1 = T.tt_norm(T.tt_add(yc, [c.astype(np.complex128) for c in y1.cores()], 1.0, -1.0)) / inf1.norm
+        d2 = T.tt_norm(T.tt_add(yc, ref, 1.0, -1.0)) / T.tt_norm(ref)
+        assert d1 < tol and d2 < tol, (b, d1, d2)
+    # flat spectra, a real truncation at 1e-3: ranks may differ per train
+    flat = [I.random_tt_cores(12, 2, 24, seed=300 + b, dtype=np.complex128) for b in range(4)]
+    xs = [Q.TT.from_cores(ctx, c, dt) for c in flat]
+    ys, _ = Q.tt_round_batch(ctx, xs, 1e-3)
+    for x, y, c in zip(xs, ys, flat):
+        y1, _ = Q.tt_round(ctx, x, 1e-3)
+        assert y.ranks == y1.ranks
+        yc = [a.astype(np.complex128) for a in y.cores()]
+        assert T.tt_norm(T.tt_add(yc, c, 1.0, -1.0)) <= 1e-3 * T.tt_norm(c) * (1 + 1e-6)
+
+
+def test_round_batch_bench_shape(Q):
+    """The rank-128 sums of the TT-op workload (d = 30) in FP32, four at a
+    time.  Their flat spectra truncate nothing at 1e-6, so the rounded train
+    equals its input up to FP32 rounding: ranks of the one-by-one rounding,
+    and both results within 5e-5 of the input (the batched GEMMs take other
+    tiles and split-K than single ones, so the two FP32 results differ at
+    that level -- 3.5e-5 measured -- but neither is closer to the input)."""
+    from oracle import tt as T
+    ctx = Q.Context(0)
+    zs, zc = [], []
+    for b in range(4):
+        x = I.random_tt_cores(30, 2, 64, seed=400 + b, dtype=np.complex128)
+        y = I.random_tt_cores(30, 2, 64, seed=500 + b, dtype=np.complex128)
+        z = Q.tt_add(ctx, 1.0, Q.TT.from_cores(ctx, x, Q.C64), 1.0, Q.TT.from_cores(ctx, y, Q.C64))
+        zs.append(z)
+        zc.append([c.astype(np.complex128) for c in z.cores()])
+    ys, infos = Q.tt_round_batch(ctx, zs, 1e-6)
+    for z, c, y, inf in zip(zs, zc, ys, infos):
+        y1, inf1 = Q.tt_round(ctx, z, 1e-6)
+        assert y.ranks == y1.ranks
+        nz = T.tt_norm(c)
+        for out in (y, y1):
+            a = [t.astype(np.complex128) for t in out.cores()]
+            assert T.tt_norm(T.tt_add(a, c, 1.0, -1.0)) < 5e-5 * nz
