@@ -85,7 +85,7 @@ def tt_round_polar(x, eps: float):
     for k in range(d - 1, 0, -1):
         r0, n, r1 = cores[k].shape
         A = cores[k].reshape(r0, n * r1).conj().T           # (n r1) x r0: the bond r0 on the columns
-        F, G, l, tail = polar_truncate(A, delta / r0)
+        F, G, l, tail = polar_truncate(A, delta / min(A.shape))   # q: the number of singular values
         tails[k] = tail
         cores[k] = F.conj().T.reshape(l, n, r1)
         cores[k - 1] = np.tensordot(cores[k - 1], G.conj().T, axes=(2, 0))
