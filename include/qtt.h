@@ -156,6 +156,18 @@ QTT_API int tt_mpo_apply(qtt_ctx* ctx, const qtt_mpo* A, const qtt_tt* x, qtt_tt
 QTT_API int tt_round(qtt_ctx* ctx, const qtt_tt* x, double eps, int max_rank, qtt_prec prec, qtt_round_info* info,
              qtt_tt** y);
 
+/* Compression via polar decomposition (Sec. 2.2): the sweeps of tt_round
+ * with the truncated SVD of each centre replaced by its polar
+ * decomposition T = U H, the sign function of H - dt I (dt = delta / q, q the
+ * centre's number of singular values), the projector P+ = (I + sign) / 2,
+ * whose trace is the kept rank, and an orthonormal basis C+ of its range
+ * (subspace iteration): new core = (U C+)^H.  Computed by Newton-Schulz
+ * iterations, i.e. matrix products only (on the tensor cores under
+ * QTT_PREC_TC32).  The bound ||x - y|| <= eps ||x|| holds with ranks at
+ * least those of tt_round; no rank cap.  info->capped is 0. */
+QTT_API int tt_round_polar(qtt_ctx* ctx, const qtt_tt* x, double eps, qtt_prec prec, qtt_round_info* info,
+                           qtt_tt** y);
+
 /* Batched SVD-based rounding: count trains of one shape (equal modes, ranks
  * and dtype), each rounded exactly as tt_round would (its own ||x||, delta,
  * truncation ranks and cap), in lockstep: each step of either sweep is one

@@ -513,6 +513,14 @@ int tt_round(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, qtt_prec p, 
                               : round_det<float>(c, x, eps, max_rank, nullptr, info, y);
 }
 
+int tt_round_polar(qtt_ctx* c, const qtt_tt* x, double eps, qtt_prec p, qtt_round_info* info, qtt_tt** y) {
+  if (!c || !valid_tt(x) || !y || !(eps >= 0)) return QTT_ERR_ARG;
+  TRY(check_prec(x->dtype, p));
+  TcScope tc(c, p == QTT_PREC_TC32);
+  return x->dtype == QTT_C128 ? round_det<double>(c, x, eps, 0, nullptr, info, y, false, true)
+                              : round_det<float>(c, x, eps, 0, nullptr, info, y, false, true);
+}
+
 int tt_round_batch(qtt_ctx* c, int count, const qtt_tt* const* x, double eps, int max_rank, qtt_prec p,
                    qtt_round_info* info, qtt_tt** y) {
   if (!c || count < 1 || !x || !y || !(eps >= 0)) return QTT_ERR_ARG;

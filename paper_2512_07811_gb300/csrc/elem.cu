@@ -395,6 +395,45 @@ __global__ void crop_kernel(const cplx<R>* __restrict__ src, int64_t sb, int64_t
   }
 }
 
+// out = (H + H^H) / 2 - shift I (q x q, row-major), and the identity-plus
+// helpers of the polar compression
+template <class R>
+__global__ void herm_shift_kernel(const cplx<R>* __restrict__ H, int64_t q, double shift, cplx<R>* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < q * q; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / q, j = e - i * q;
+    const cplx<R> a = H[e], b = H[j * q + i];
+    cplx<R> v(R(0.5) * (a.re + b.re), R(0.5) * (a.im - b.im));
+    if (i == j) v.re -= (R)shift;
+    out[e] = v;
+  }
+}
+
+// P = (I + S) / 2 in place, and the real part of its trace into *tr
+template <class R>
+__global__ void half_identity_plus_kernel(cplx<R>* __restrict__ S, int64_t q, double* __restrict__ tr) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < q * q; e += blockDim.x) {
+    const int64_t i = e / q, j = e - i * q;
+    cplx<R> v = S[e];
+    v.re *= R(0.5);
+    v.im *= R(0.5);
+    if (i == j) {
+      v.re += R(0.5);
+      acc += (double)v.re;
+    }
+    S[e] = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *tr = t;
+  }
+}
+
 template <class R>
 int qtt_place_block(const cplx<R>* src, int64_t s0, int64_t n, int64_t s1, cplx<R>* dst, int64_t d1,
                     int64_t off0, int64_t off1, cplx<R> scale, cudaStream_t s) {
@@ -574,3 +613,20 @@ template int qtt_crop_batch<double>(const zc*, int64_t, int64_t, int64_t, int64_
                                     const int*, int, cudaStream_t);
 template int qtt_crop_batch<float>(const cc*, int64_t, int64_t, int64_t, int64_t, cc* const*, const int*, const int*,
                                    int, cudaStream_t);
+
+template <class R>
+int qtt_herm_shift(const cplx<R>* H, int64_t q, double shift, cplx<R>* out, cudaStream_t s) {
+  if (q <= 0) return QTT_OK;
+  herm_shift_kernel<R><<<grid_for(q * q), 256, 0, s>>>(H, q, shift, out);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+template <class R>
+int qtt_half_identity_plus(cplx<R>* S, int64_t q, double* tr, cudaStream_t s) {
+  if (q <= 0) return QTT_OK;
+  half_identity_plus_kernel<R><<<1, 1024, 0, s>>>(S, q, tr);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+template int qtt_herm_shift<double>(const zc*, int64_t, double, zc*, cudaStream_t);
+template int qtt_herm_shift<float>(const cc*, int64_t, double, cc*, cudaStream_t);
+template int qtt_half_identity_plus<double>(zc*, int64_t, double*, cudaStream_t);
+template int qtt_half_identity_plus<float>(cc*, int64_t, double*, cudaStream_t);

@@ -8,6 +8,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <float.h>
+
 #include <algorithm>
 #include <chrono>
 #include <new>
@@ -422,6 +424,139 @@ int left_svd(qtt_ctx* c, const cplx<R>* Cm, int64_t rows, int64_t cols, int64_t 
   return QTT_OK;
 }
 
+// ------------------------------------------------- polar-based truncation
+// Compression via polar decomposition (Sec. 2.2) of A (m x q, row-major):
+// the polar factor U of A by the Newton-Schulz iteration X <- X (3I - X^H X)/2
+// from X0 = A / ||A||_F; H = U^H A (Hermitian part); the sign function S of
+// H - dt I by the same iteration on S0 = (H - dt I) / ||.||_F; P+ = (I + S)/2
+// and l = round(tr P+); an orthonormal basis C+ of range P+ by two steps of
+// subspace iteration from a Gaussian block (Philox, seeded by `stream_id`),
+// each orthonormalised by Newton-Schulz; F = U C+ (m x l, orthonormal
+// columns).  Only GEMMs and elementwise kernels: under QTT_PREC_TC32 every
+// product runs on the tensor cores.  The iteration counts cover the dynamic
+// range min(||A|| / dt, 1 / machine epsilon) at a growth of 1.5 per step for
+// the smallest scaled values, plus 12 steps to finish (quadratic convergence).
+// tail = sqrt(||A||^2 - ||C+^H H||^2), the discarded mass.
+template <class R>
+static int ns_iterate(qtt_ctx* c, cplx<R>*& X, cplx<R>*& Xn, cplx<R>* G, int64_t m, int64_t q, int iters,
+                      bool hermitian) {
+  typedef cplx<R> C;
+  for (int it = 0; it < iters; ++it) {
+    // G = X^H X (or X X for a Hermitian X), Xn = 1.5 X - 0.5 X G
+    if (hermitian)
+      TRY(mm<R>(c, q, q, q, X, q, 1, 0, X, q, 1, 0, G, q, 1));
+    else
+      TRY(mm<R>(c, q, q, m, X, 1, q, 1, X, q, 1, 0, G, q, 1));
+    if (cudaMemcpyAsync(Xn, X, (size_t)m * q * sizeof(C), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      return QTT_ERR_CUDA;
+    TRY(mm<R>(c, m, q, q, X, q, 1, 0, G, q, 1, 0, Xn, q, 1, C(-0.5, 0), C(1.5, 0)));
+    std::swap(X, Xn);
+  }
+  return QTT_OK;
+}
+
+template <class R>
+static int polar_truncate_dev(qtt_ctx* c, const cplx<R>* A, int64_t m, int64_t q, double dt, uint64_t stream_id,
+                              DBuf* Fout, int64_t* l_out, double* tail_out) {
+  typedef cplx<R> C;
+  DBuf scal;
+  TRY(scal.alloc(c, 64));
+  double* ds = scal.as<double>();
+  double s2 = 0;
+  c->launches++;
+  TRY(qtt_sumsq<R>(A, m * q, ds, c->stream));
+  TRY(sync_read(c, &s2, ds, sizeof(double)));
+  const double an = sqrt(s2);
+  const double ueps = sizeof(R) == 8 ? DBL_EPSILON : FLT_EPSILON;
+  if (!(an > 0)) {
+    // zero centre: any unit vector spans the (empty) kept part
+    TRY(Fout->alloc(c, (size_t)m * sizeof(C)));
+    if (cudaMemsetAsync(Fout->p, 0, (size_t)m * sizeof(C), c->stream) != cudaSuccess) return QTT_ERR_CUDA;
+    const C one(1, 0);
+    if (cudaMemcpyAsync(Fout->p, &one, sizeof(C), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      return QTT_ERR_CUDA;
+    *l_out = 1;
+    *tail_out = 0;
+    return QTT_OK;
+  }
+  const double range = std::min(an / std::max(dt, 1e-300), 1.0 / ueps);
+  const int iters = std::max(12, std::min(120, (int)ceil(log(std::max(range, 1.0)) / log(1.5)) + 12));
+  // polar factor of A
+  DBuf Xa, Xb, G;
+  TRY(Xa.alloc(c, (size_t)m * q * sizeof(C)));
+  TRY(Xb.alloc(c, (size_t)m * q * sizeof(C)));
+  TRY(G.alloc(c, (size_t)q * q * sizeof(C)));
+  if (cudaMemcpyAsync(Xa.p, A, (size_t)m * q * sizeof(C), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+    return QTT_ERR_CUDA;
+  c->launches++;
+  TRY(qtt_scale<R>(Xa.as<C>(), m * q, C((R)(1.0 / an), 0), c->stream));
+  C* X = Xa.as<C>();
+  C* Xn = Xb.as<C>();
+  TRY(ns_iterate<R>(c, X, Xn, G.as<C>(), m, q, iters, false));
+  // H = U^H A (Hermitian part) and B = H - dt I, scaled
+  DBuf Hr, Hh, Sa, Sb, S2;
+  TRY(Hr.alloc(c, (size_t)q * q * sizeof(C)));
+  TRY(Hh.alloc(c, (size_t)q * q * sizeof(C)));
+  TRY(Sa.alloc(c, (size_t)q * q * sizeof(C)));
+  TRY(Sb.alloc(c, (size_t)q * q * sizeof(C)));
+  TRY(S2.alloc(c, (size_t)q * q * sizeof(C)));
+  TRY(mm<R>(c, q, q, m, X, 1, q, 1, A, q, 1, 0, Hr.as<C>(), q, 1));
+  c->launches += 2;
+  TRY(qtt_herm_shift<R>(Hr.as<C>(), q, 0.0, Hh.as<C>(), c->stream));
+  TRY(qtt_herm_shift<R>(Hr.as<C>(), q, dt, Sa.as<C>(), c->stream));
+  double b2 = 0;
+  c->launches++;
+  TRY(qtt_sumsq<R>(Sa.as<C>(), q * q, ds, c->stream));
+  TRY(sync_read(c, &b2, ds, sizeof(double)));
+  if (!(b2 > 0)) b2 = 1;
+  c->launches++;
+  TRY(qtt_scale<R>(Sa.as<C>(), q * q, C((R)(1.0 / sqrt(b2)), 0), c->stream));
+  // sign function, P+ = (I + S) / 2, l = round(tr P+)
+  C* S = Sa.as<C>();
+  C* Sn = Sb.as<C>();
+  TRY(ns_iterate<R>(c, S, Sn, S2.as<C>(), q, q, iters, true));
+  double tr = 0;
+  c->launches++;
+  TRY(qtt_half_identity_plus<R>(S, q, ds + 1, c->stream));
+  TRY(sync_read(c, &tr, ds + 1, sizeof(double)));
+  const int64_t l = std::max<int64_t>(1, std::min<int64_t>(std::min(m, q), (int64_t)llround(tr)));
+  // basis of range P+: two subspace-iteration steps, each orthonormalised
+  DBuf Om, Ya, Yb, Gl;
+  TRY(Om.alloc(c, (size_t)q * l * sizeof(C)));
+  TRY(Ya.alloc(c, (size_t)q * l * sizeof(C)));
+  TRY(Yb.alloc(c, (size_t)q * l * sizeof(C)));
+  TRY(Gl.alloc(c, (size_t)l * l * sizeof(C)));
+  c->launches++;
+  TRY(qtt_fill_gaussian<R>(Om.as<C>(), q * l, 0x706f6c6172ULL, stream_id, 1.0, c->stream));
+  C* Y = Ya.as<C>();
+  C* Yn = Yb.as<C>();
+  for (int pass = 0; pass < 2; ++pass) {
+    TRY(mm<R>(c, q, l, q, S, q, 1, 0, pass == 0 ? Om.as<C>() : Y, l, 1, 0, Yn, l, 1));
+    std::swap(Y, Yn);
+    double y2 = 0;
+    c->launches++;
+    TRY(qtt_sumsq<R>(Y, q * l, ds + 2, c->stream));
+    TRY(sync_read(c, &y2, ds + 2, sizeof(double)));
+    c->launches++;
+    TRY(qtt_scale<R>(Y, q * l, C((R)(1.0 / sqrt(std::max(y2, 1e-300))), 0), c->stream));
+    // the starting block's condition enters only the first pass; the second starts near orthonormal
+    TRY(ns_iterate<R>(c, Y, Yn, Gl.as<C>(), q, l, pass == 0 ? 40 : 16, false));
+  }
+  // F = U C+, tail from G = C+^H H
+  TRY(Fout->alloc(c, (size_t)m * l * sizeof(C)));
+  TRY(mm<R>(c, m, l, q, X, q, 1, 0, Y, l, 1, 0, Fout->as<C>(), l, 1));
+  DBuf Gm;
+  TRY(Gm.alloc(c, (size_t)l * q * sizeof(C)));
+  TRY(mm<R>(c, l, q, q, Y, 1, l, 1, Hh.as<C>(), q, 1, 0, Gm.as<C>(), q, 1));
+  double g2 = 0;
+  c->launches++;
+  TRY(qtt_sumsq<R>(Gm.as<C>(), l * q, ds + 3, c->stream));
+  TRY(sync_read(c, &g2, ds + 3, sizeof(double)));
+  *l_out = l;
+  *tail_out = sqrt(std::max(0.0, s2 - g2));
+  return QTT_OK;
+}
+
 // ------------------------------------------------------- deterministic round
 // R-only variant of the QR-then-SVD rounding (Sec. 2.2): the left sweep keeps
 // only the triangular factors R_k of R_{k-1} A_k; the right sweep factors
@@ -442,7 +577,7 @@ int left_svd(qtt_ctx* c, const cplx<R>* Cm, int64_t rows, int64_t cols, int64_t 
 // error in FP32).
 template <class R>
 int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* forced, qtt_round_info* info,
-              qtt_tt** yout, bool left_orth) {
+              qtt_tt** yout, bool left_orth, bool polar) {
   const int d = x->d;
   std::vector<int> n = x->n, r = x->r;
   auto A = [&](int k) { return reinterpret_cast<const cplx<R>*>(static_cast<const char*>(x->data) + x->off[k]); };
@@ -530,7 +665,7 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     // of C^H first pays for itself
     const int64_t jp = Tcols;
     int64_t jq = rk;
-    if (jp <= 4 * jq || jp * jq <= 4096) {
+    if (polar || jp <= 4 * jq || jp * jq <= 4096) {
       TRY(Cb.alloc(c, (size_t)rk * Tcols * sizeof(cplx<R>)));
       if (left_orth) {
         c->launches++;
@@ -542,7 +677,16 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
       TRY(dbg_finite<R>(c, Cb.as<cplx<R>>(), rk * Tcols, "round sweep2 G", k));
       // X (Tcols x jq): right singular vectors of C, columns by decreasing singular value
       DBuf X;
-      if (Tcols < rk) {
+      if (polar) {
+        // polar-based compression of the centre C^H at dt = delta / q, q its number of singular values
+        int64_t l = 0;
+        double tl = 0;
+        TRY(polar_truncate_dev<R>(c, Cb.as<cplx<R>>(), Tcols, rk, delta / (double)std::min(Tcols, rk),
+                                  (uint64_t)k, &X, &l, &tl));
+        jq = l;
+        nr[k] = (int)l;
+        tail2 += tl * tl;
+      } else if (Tcols < rk) {
         // C taller than wide (rank <= Tcols): C = Q_c R_c with R_c square
         // (R only), and Jacobi on R_c^H (Tcols x Tcols) gives the same right
         // vectors as normalised rotated columns, in Tcols - 1 rounds a sweep
@@ -570,22 +714,27 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
       }
       TRY(dbg_finite<R>(c, X.as<cplx<R>>(), Tcols * jq, "round sweep2 X", k));
       int t;
-      c->launches++;
-      if (forced) {
-        t = (int)std::min<int64_t>(forced[k], jq);
-        TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)jq, -1.0, t, dint, reinterpret_cast<double*>(dint + 2), c->stream));
+      if (polar) {
+        t = (int)jq;  // the rank polar_truncate_dev found; no cap in this variant
       } else {
-        TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)jq, delta, max_rank, dint, reinterpret_cast<double*>(dint + 2),
-                              c->stream));
+        c->launches++;
+        if (forced) {
+          t = (int)std::min<int64_t>(forced[k], jq);
+          TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)jq, -1.0, t, dint, reinterpret_cast<double*>(dint + 2),
+                                c->stream));
+        } else {
+          TRY(qtt_trunc_rank<R>(sig.as<R>(), (int)jq, delta, max_rank, dint, reinterpret_cast<double*>(dint + 2),
+                                c->stream));
+        }
+        int hv[4];
+        TRY(sync_read(c, hv, dint, sizeof(hv)));
+        double tl;
+        memcpy(&tl, hv + 2, sizeof(double));
+        t = hv[0];
+        if (!forced) capped |= hv[1];
+        tail2 += tl * tl;
+        nr[k] = t;
       }
-      int hv[4];
-      TRY(sync_read(c, hv, dint, sizeof(hv)));
-      double tl;
-      memcpy(&tl, hv + 2, sizeof(double));
-      t = hv[0];
-      if (!forced) capped |= hv[1];
-      tail2 += tl * tl;
-      nr[k] = t;
       // new core k = X[:, :t]^H (t x Tcols)
       TRY(newc[k].alloc(c, (size_t)t * Tcols * sizeof(cplx<R>)));
       cplx<R>* core = newc[k].as<cplx<R>>();
@@ -691,9 +840,9 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
 }
 
 template int round_det<double>(qtt_ctx*, const qtt_tt*, double, int, const int*, qtt_round_info*, qtt_tt**,
-                                bool);
+                                bool, bool);
 template int round_det<float>(qtt_ctx*, const qtt_tt*, double, int, const int*, qtt_round_info*, qtt_tt**,
-                               bool);
+                               bool, bool);
 
 // ------------------------------------------------ batched deterministic round
 // B trains of one shape (same modes and ranks) rounded in lockstep by the

@@ -94,7 +94,7 @@ void mpo_free(qtt_mpo* A);
 
 template <class R>
 int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* forced, qtt_round_info* info,
-              qtt_tt** yout, bool left_orth = false);
+              qtt_tt** yout, bool left_orth = false, bool polar = false);
 template <class R>
 int round_det_batch(qtt_ctx* c, int B, const qtt_tt* const* xs, double eps, int max_rank, qtt_round_info* infos,
                     qtt_tt** ys);

@@ -120,3 +120,8 @@ int qtt_mask_cols_batch(cplx<R>* X, int64_t bs, int64_t rows, int64_t cols, int6
 template <class R>
 int qtt_crop_batch(const cplx<R>* src, int64_t sb, int64_t r0, int64_t n, int64_t r1, cplx<R>* const* dst,
                    const int* t0, const int* t1, int batch, cudaStream_t s);
+// polar compression helpers (elem.cu): out = (H + H^H)/2 - shift I; S <- (I + S)/2 with Re tr into *tr
+template <class R>
+int qtt_herm_shift(const cplx<R>* H, int64_t q, double shift, cplx<R>* out, cudaStream_t s);
+template <class R>
+int qtt_half_identity_plus(cplx<R>* S, int64_t q, double* tr, cudaStream_t s);

@@ -111,6 +111,7 @@ _sig("tt_add", C.c_int, [_P, Complex, _P, Complex, _P, C.POINTER(_P)])
 _sig("tt_hadamard", C.c_int, [_P, _P, _P, C.POINTER(_P)])
 _sig("tt_mpo_apply", C.c_int, [_P, _P, _P, C.POINTER(_P)])
 _sig("tt_round", C.c_int, [_P, _P, C.c_double, C.c_int, C.c_int, C.POINTER(RoundInfo), C.POINTER(_P)])
+_sig("tt_round_polar", C.c_int, [_P, _P, C.c_double, C.c_int, C.POINTER(RoundInfo), C.POINTER(_P)])
 _sig("tt_round_batch", C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_double, C.c_int, C.c_int, C.POINTER(RoundInfo),
                                  C.POINTER(_P)])
 _sig("tt_round_sketched", C.c_int, [_P, C.c_int, C.POINTER(Complex), C.POINTER(_P), C.POINTER(_P), _P,
@@ -141,7 +142,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_tt_create", "qtt_tt_destroy", "qtt_tt_ncores", "qtt_tt_ranks", "qtt_tt_modes", "qtt_tt_dtype",
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
-            "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_norm",
+            "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_polar", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_norm",
             "tt_from_dense", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
             "ms_homogenize_batch", "qtt_cgemm", "qtt_cgemm_noalloc",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
@@ -342,6 +343,15 @@ def tt_round(ctx: Context, x: TT, eps: float, max_rank: int = 0, prec=None):
     h = _P()
     info = RoundInfo()
     _check(_lib.tt_round(ctx.h, x.h, float(eps), int(max_rank), int(prec), C.byref(info), C.byref(h)), "tt_round")
+    return TT(ctx, h), info
+
+
+def tt_round_polar(ctx: Context, x: TT, eps: float, prec=None):
+    if prec is None:
+        prec = PREC_F64 if x.dtype == C128 else PREC_F32
+    h = _P()
+    info = RoundInfo()
+    _check(_lib.tt_round_polar(ctx.h, x.h, float(eps), int(prec), C.byref(info), C.byref(h)), "tt_round_polar")
     return TT(ctx, h), info
 
 
