@@ -292,6 +292,7 @@ def run_ours(args, rank, world, local_rank):
     ctx.sync()
     ms64, flops64 = time_steps(torch, stream, slow, args.fp64_steps, flush)
 
+    polar = polar_vs_svd(Q, torch, ctx, stream, flush, fast)
     batched = None
     if args.batch > 0:
         batched = batched_rounding(Q, torch, ctx, stream, flush, r, args.batch, 2)
@@ -299,7 +300,8 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_ms:
         ms_part = ms_laminate(Q, ctx)
     return dict(ms=ms, flops=flops, prof=prof, ms_prof=ms_prof, launches=launches, clocks=clk, e2e_ms=e2e_ms,
-                e2e_flops=e2e_flops, h2d=h2d, d2h=d2h, ms64=ms64, flops64=flops64, ms_part=ms_part, batched=batched)
+                e2e_flops=e2e_flops, h2d=h2d, d2h=d2h, ms64=ms64, flops64=flops64, ms_part=ms_part, batched=batched,
+                polar=polar)
 
 
 def batched_rounding(Q, torch, ctx, stream, flush, r, count, steps):
@@ -332,6 +334,38 @@ def batched_rounding(Q, torch, ctx, stream, flush, r, count, steps):
                         % (count, D, r, 2 * r),
             "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_batch": ms / steps, "steps": steps,
             "roundings_per_s": count * steps / (ms * 1e-3)}
+
+
+def polar_vs_svd(Q, torch, ctx, stream, flush, step):
+    """SVD- vs polar-based compression (the paper's comparison, chi =
+    tau_polar / tau_SVD) on the step's first rounding: the rank-128 sum of the
+    two rank-64 trains, FP32 storage, SVD rounding vs polar rounding with
+    CUDA-core products (f32) and with the products on the tensor cores
+    (tc32).  One warm-up and one timed rounding each, L2 flushed first."""
+    z = Q.tt_add(ctx, 1.0, step.X, 1.0, step.Y)
+
+    def timed(fn):
+        fn()
+        ctx.sync()
+        with torch.cuda.stream(stream):
+            flush_l2(torch, flush)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y, _ = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), y.ranks
+
+    svd_ms, svd_r = timed(lambda: Q.tt_round(ctx, z, EPS, prec=Q.PREC_F32))
+    out = {"workload": "rounding of the rank-128 sum (d=30), eps %g, complex64" % EPS, "svd_ms": svd_ms}
+    for name, p in [("f32", Q.PREC_F32), ("tc32", Q.PREC_TC32)]:
+        ms, r = timed(lambda: Q.tt_round_polar(ctx, z, EPS, prec=p))
+        out["polar_ms_" + name] = ms
+        out["chi_" + name] = ms / svd_ms
+        out["ranks_equal_" + name] = r == svd_r
+    return out
 
 
 def ms_laminate(Q, ctx):
@@ -502,6 +536,8 @@ def main():
         line["ms_iteration"] = res["ms_part"]
     if res.get("batched") is not None:
         line["batched_rounding"] = res["batched"]
+    if res.get("polar") is not None:
+        line["polar_vs_svd"] = res["polar"]
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
