@@ -119,7 +119,30 @@ static inline MIdx B0() { return MIdx{1, 1, 0, 0}; }
 // Tensor-core route for one float contraction (batch handled by a loop);
 // returns QTT_ERR_UNSUPPORTED when the contraction is too small to pay for
 // the packing, so that the caller falls back to the CUDA-core kernel.
-static int tc_route(qtt_ctx* c, const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C) {
+// A batch whose A (or B) operand is the same for every entry (batch stride 0)
+// is one GEMM with the batch folded into N (or M) as the outer part of a
+// two-level index: C[:, (b, n)] = A B[:, (b, n)].
+static GemmDesc fold_shared_batch(const GemmDesc& g) {
+  GemmDesc f = g;
+  if (g.batch <= 1 || g.bA.n2 != 1 || g.bB.n2 != 1 || g.bC.n2 != 1) return f;
+  if (g.bA.s1 == 0 && g.nB.n2 == 1 && g.nC.n2 == 1) {
+    f.nB = MIdx{g.batch, g.N, g.bB.s1, g.nB.s1};
+    f.nC = MIdx{g.batch, g.N, g.bC.s1, g.nC.s1};
+    f.N = g.batch * g.N;
+  } else if (g.bB.s1 == 0 && g.mA.n2 == 1 && g.mC.n2 == 1) {
+    f.mA = MIdx{g.batch, g.M, g.bA.s1, g.mA.s1};
+    f.mC = MIdx{g.batch, g.M, g.bC.s1, g.mC.s1};
+    f.M = g.batch * g.M;
+  } else {
+    return f;
+  }
+  f.batch = 1;
+  f.bA = f.bB = f.bC = MIdx{1, 1, 0, 0};
+  return f;
+}
+
+static int tc_route(qtt_ctx* c, const GemmDesc& g0, cc alpha, cc beta, const cc* A, const cc* B, cc* C) {
+  const GemmDesc g = fold_shared_batch(g0);
   if (!c->tc || g.M < 64 || g.N < 16 || g.K < 32 || (double)g.M * g.N * g.K < 2.0e5) return QTT_ERR_UNSUPPORTED;
   if (!c->d_tcerr) {
     if (cudaMalloc(&c->d_tcerr, sizeof(int)) != cudaSuccess) return QTT_ERR_OOM;
