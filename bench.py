@@ -44,7 +44,7 @@ from paper_2512_07811_gb300.flops import round_flops  # noqa: E402
 D = 30
 EPS = 1e-6
 OVERSAMPLE = 8
-JACOBI_DRAM_BYTES_PER_LAUNCH = 128.5e3
+JACOBI_DRAM_BYTES_PER_LAUNCH = 144.5e3
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -498,9 +498,9 @@ def main():
                 "peak": fp32_peak, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
     # DRAM bytes per launch of the class (dram__bytes_read.sum + write.sum),
-    # mean over its launches in the ncu launch list of this workload
-    # (profiles/tt_ops_d30_r64_launches.md); valid while the kernels are those
-    # the list was taken on
+    # mean over its launches in an ncu capture of this workload
+    # (profiles/jacobi_block_kernel_f32_256x128.md); valid while the kernels are
+    # those the capture was taken on
     roof["traffic"] = JACOBI_DRAM_BYTES_PER_LAUNCH if dom == "jacobi" and args.prec == "f32" else None
     # the 256 x 128 factorisations run on one 8-CTA cluster: the same rate
     # against the FP32 peak of the SMs they occupy
