@@ -387,14 +387,36 @@ def ms_laminate(Q, ctx):
         it = rep.iterations[0]
         out[name] = {"iters_per_s": it / (rep.iterate_ms * 1e-3) if rep.iterate_ms > 0 else None, "eps": eps,
                      "setup_ms": rep.setup_ms, "k_eff_xx": C[0, 0], "iterations": it,
-                     "max_rank": rep.max_rank_seen}
+                     "max_rank": rep.max_rank_seen, "sketch_width_sum": rep.sketch_width_sum}
         if name == "fp64":
             C64 = C
         else:
             out[name]["rel_dev_from_fp64"] = float(abs(C[0, 0] - C64[0, 0]) / abs(C64[0, 0]))
+    # learned ranks: the MLP (trained here by the library's own kernels on the
+    # rank traces of 8^3 / 16^3 solves, outside the timed region) sizes each
+    # bond's sketch instead of the fixed width max_rank + oversampling
+    from paper_2512_07811_gb300 import predictor as PR
+    common = dict(kind="scalar", moduli=(1.0, 10.0), C0=5.5 * np.eye(3), tol=0.0, max_rank=64, max_iter=4,
+                  min_iter=4, prec=Q.PREC_F32, load_mask=1)
+    train = [dict(indicator=ind_t, eps=e, **common)
+             for ind_t in [I.laminate_indicator(8), I.laminate_indicator(16), I.box_indicator(8, 0.2)]
+             for e in (1e-6, 1e-4)]
+    X, t = PR.collect_traces(ctx, train)
+    net = Q.MLP(ctx, Q.MLP_FEATURES, seed=7)
+    PR.train(net, X, t, epochs=150, batch=512, lr=3e-3, alpha=4.0)
+    kw = dict(tol=0.0, max_rank=64, eps=1e-6, prec=Q.PREC_F32, load_mask=1, predictor=net)
+    Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=1, min_iter=1, **kw)
+    C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=5, min_iter=5, **kw)
+    it = rep.iterations[0]
+    out["fast_learned_rank"] = {
+        "iters_per_s": it / (rep.iterate_ms * 1e-3) if rep.iterate_ms > 0 else None, "eps": 1e-6,
+        "k_eff_xx": C[0, 0], "rel_dev_from_fp64": float(abs(C[0, 0] - C64[0, 0]) / abs(C64[0, 0])),
+        "sketch_width_sum": rep.sketch_width_sum, "fallbacks": rep.fallbacks, "training_rows": int(X.shape[0])}
     out["k_eff_xx_exact"] = 20.0 / 11.0
     if out["fast"]["iters_per_s"] and out["fp64"]["iters_per_s"]:
         out["speedup_fast_vs_fp64"] = out["fast"]["iters_per_s"] / out["fp64"]["iters_per_s"]
+        if out["fast_learned_rank"]["iters_per_s"]:
+            out["speedup_fast_learned_vs_fp64"] = out["fast_learned_rank"]["iters_per_s"] / out["fp64"]["iters_per_s"]
     return out
 
 

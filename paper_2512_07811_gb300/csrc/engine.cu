@@ -315,14 +315,13 @@ static int qr_launch(qtt_ctx* c, const cplx<R>* in, MIdx inB, MIdx rowI, MIdx co
 template <class R>
 static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<R>* Vsorted, int p, int q,
                          int max_sweeps, cplx<R>* Usorted = nullptr) {
-  // FP64 runs at a few flops per clock per SM on this part: spread every
-  // sizeable FP64 factorisation over all SMs; FP32 stays in one CTA up to
-  // q = 256, where one SM's FP32 rate beats a launch per round.
-  // FP32 matrices too large for one CTA's shared memory: a cluster of 4 or 8
-  // CTAs splitting the rows (a cluster barrier per round costs more than one
-  // SM's compute at the sizes that fit one CTA, so those stay single-CTA)
-  // Without rotations wanted (Vsorted null) and q >= 32: the block-cyclic
-  // cluster kernel, which needs a cluster barrier only per block exchange
+  // Routing.  Without rotations wanted (Vsorted null) and q >= 32: the
+  // block-cyclic cluster kernel (columns split over 4 or 8 CTAs, a cluster
+  // barrier only per block exchange), in FP32 and FP64 alike.  Otherwise:
+  // FP32 matrices too large for one CTA's shared memory go to the row-split
+  // cluster kernel; FP64 with q >= 32 and anything with q > 256 to the
+  // multi-launch kernel over all SMs (FP64 runs at 2 DFMA/clk/SM on this
+  // part); the rest to the single-CTA shared-memory kernel.
   int bs = 0;
   if (!Vsorted && qtt_jacobi_block_plan<R>(p, q, &bs)) {
     int idx;
