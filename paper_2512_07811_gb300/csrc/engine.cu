@@ -11,6 +11,8 @@
 #include <float.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <chrono>
 #include <new>
 #include <vector>
@@ -165,16 +167,98 @@ static int tc_route(qtt_ctx* c, const GemmDesc& g0, cc alpha, cc beta, const cc*
   return st;
 }
 
-// CUDA-core GEMM with the thin-tile / split-K choice of qtt_gemm_splits
+// ------------------------------------------------------ GEMM tile autotuner
+// The first CUDA-core GEMM of a shape (element size, M, N, K, batch and which
+// operand indices are contiguous) with enough work times the candidate tile
+// edges (32, 64) and split counts (1, the rule's, twice the rule's) once, with
+// CUDA events on the caller's stream into a scratch output, and caches the
+// fastest; later GEMMs of the shape use it.  The cache is process-wide, so
+// every context of a process takes the same choice (results do not depend on
+// which context, or thread, tuned a shape first).  GEMMs that accumulate
+// into C (beta != 0) or are too small to matter keep the rule's choice.
+struct TuneKey {
+  int64_t v[7];
+  bool operator<(const TuneKey& o) const { return std::lexicographical_compare(v, v + 7, o.v, o.v + 7); }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune;  // -> (tile, splits)
+
+static bool unit_inner(const MIdx& m) { return (m.n2 == 1 ? m.s1 : m.s2) == 1; }
+
+template <class R>
+static int tune_gemm(qtt_ctx* c, const GemmDesc& g, const cplx<R>* A, const cplx<R>* B, int* tile, int* splits) {
+  GemmDesc d = g;  // dense scratch output
+  d.bC = MIdx{g.batch, 1, g.M * g.N, 0};
+  d.mC = MIdx{g.M, 1, g.N, 0};
+  d.nC = MIdx{g.N, 1, 1, 0};
+  std::vector<std::pair<int, int>> cand;
+  for (int t : {32, 64}) {
+    const int s0 = qtt_gemm_splits_for(g, t);
+    for (int sp : {1, s0, 2 * s0})
+      if (sp >= 1 && sp <= 32 && (int64_t)g.batch * sp <= 65535 &&
+          std::find(cand.begin(), cand.end(), std::make_pair(t, sp)) == cand.end())
+        cand.emplace_back(t, sp);
+  }
+  int maxs = 1;
+  for (auto& cs : cand) maxs = std::max(maxs, cs.second);
+  void* buf = nullptr;
+  const size_t outb = (size_t)g.batch * g.M * g.N * sizeof(cplx<R>);
+  if (dalloc(c, &buf, outb * (1 + (maxs > 1 ? maxs : 0)))) return QTT_ERR_OOM;
+  cplx<R>* Cs = reinterpret_cast<cplx<R>*>(buf);
+  cplx<R>* Ps = Cs + (size_t)g.batch * g.M * g.N;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int st = QTT_OK;
+  for (auto& cs : cand) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && st == QTT_OK; ++rep) {  // first run warms up
+      cudaEventRecord(e0, c->stream);
+      st = qtt_gemm_ex<R>(d, cplx<R>(1, 0), cplx<R>(0, 0), A, B, Cs, cs.second, Ps, c->stream, cs.first);
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = QTT_ERR_CUDA;
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    c->launches += 2 * (cs.second > 1 ? 2 : 1);
+    if (st == QTT_OK && ms < best) {
+      best = ms;
+      *tile = cs.first;
+      *splits = cs.second;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dfree(c, buf);
+  return st;
+}
+
+// CUDA-core GEMM: tile edge and split-K from the tuner (or the rule)
 template <class R>
 static int simt_gemm(qtt_ctx* c, const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B,
                      cplx<R>* C) {
-  const int splits = qtt_gemm_splits(g);
+  int tile = 0, splits = qtt_gemm_splits(g);
+  const bool beta0 = beta.re == R(0) && beta.im == R(0);
+  if (beta0 && (double)g.M * g.N * g.K * g.batch >= 4.0e6) {
+    const bool a_kfast = unit_inner(g.kA) && !unit_inner(g.mA);
+    const bool b_kfast = unit_inner(g.kB) && !unit_inner(g.nB);
+    const TuneKey key{{(int64_t)sizeof(R), g.M, g.N, g.K, g.batch, (int64_t)a_kfast, (int64_t)b_kfast}};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) {
+      int t = qtt_gemm_tile_rule(g), sp = splits;
+      const int ts = tune_gemm<R>(c, g, A, B, &t, &sp);
+      if (ts != QTT_OK) return ts;
+      it = g_tune.emplace(key, std::make_pair(t, sp)).first;
+    }
+    tile = it->second.first;
+    splits = it->second.second;
+  }
   void* P = nullptr;
   if (splits > 1 && dalloc(c, &P, (size_t)splits * g.batch * g.M * g.N * sizeof(cplx<R>))) return QTT_ERR_OOM;
   c->launches += splits > 1 ? 2 : 1;
   cudaEvent_t ev = prof_begin(c);
-  int st = qtt_gemm_ex<R>(g, alpha, beta, A, B, C, splits, reinterpret_cast<cplx<R>*>(P), c->stream);
+  int st = qtt_gemm_ex<R>(g, alpha, beta, A, B, C, splits, reinterpret_cast<cplx<R>*>(P), c->stream, tile);
   prof_end(c, ev, PK_GEMM, 8.0 * g.M * g.N * g.K * g.batch,
            (double)(g.M * g.K + g.K * g.N + g.M * g.N) * g.batch * sizeof(cplx<R>));
   dfree(c, P);

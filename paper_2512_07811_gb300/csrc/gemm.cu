@@ -209,11 +209,11 @@ int qtt_gemm_splits(const GemmDesc& g) {
 
 template <class R>
 int qtt_gemm_ex(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B, cplx<R>* C,
-                int splits, cplx<R>* P, cudaStream_t s) {
+                int splits, cplx<R>* P, cudaStream_t s, int tile) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return QTT_OK;
   if (splits < 1 || (splits > 1 && !P)) return QTT_ERR_ARG;
   const int64_t kchunk = splits > 1 ? (g.K + splits - 1) / splits : std::max<int64_t>(g.K, 1);
-  const bool thin = gemm_tile(g) == 32;
+  const bool thin = (tile ? tile : gemm_tile(g)) == 32;
   constexpr int BK = sizeof(R) == 8 ? 8 : 16;
   const int64_t zdim = g.batch * splits;
   if (zdim > 65535) return QTT_ERR_ARG;
@@ -234,8 +234,17 @@ int qtt_gemm_ex(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
 
-template int qtt_gemm_ex<double>(const GemmDesc&, zc, zc, const zc*, const zc*, zc*, int, zc*, cudaStream_t);
-template int qtt_gemm_ex<float>(const GemmDesc&, cc, cc, const cc*, const cc*, cc*, int, cc*, cudaStream_t);
+template int qtt_gemm_ex<double>(const GemmDesc&, zc, zc, const zc*, const zc*, zc*, int, zc*, cudaStream_t, int);
+template int qtt_gemm_ex<float>(const GemmDesc&, cc, cc, const cc*, const cc*, cc*, int, cc*, cudaStream_t, int);
+
+// the rule's tile edge and the split count the rule would take with a given tile
+int qtt_gemm_tile_rule(const GemmDesc& g) { return (int)gemm_tile(g); }
+int qtt_gemm_splits_for(const GemmDesc& g, int tile) {
+  const int64_t tiles = ((g.M + tile - 1) / tile) * ((g.N + tile - 1) / tile) * g.batch;
+  if (tiles >= 76 || g.K < 128) return 1;
+  int64_t s = std::min<int64_t>((g.K + 63) / 64, std::max<int64_t>(1, 152 / tiles));
+  return (int)std::min<int64_t>(s, 32);
+}
 
 template <class R>
 int qtt_gemm(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A,

@@ -12,9 +12,12 @@ int qtt_gemm(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, c
 
 // split-K aware variant: `splits` K ranges, partials in P (splits x batch x M x N), see qtt_gemm_splits
 int qtt_gemm_splits(const GemmDesc& g);
+// tile: 0 = the rule (gemm_tile), else 32 or 64
 template <class R>
 int qtt_gemm_ex(const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B, cplx<R>* C,
-                int splits, cplx<R>* P, cudaStream_t s);
+                int splits, cplx<R>* P, cudaStream_t s, int tile = 0);
+int qtt_gemm_tile_rule(const GemmDesc& g);
+int qtt_gemm_splits_for(const GemmDesc& g, int tile);
 
 template <class R>
 int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
