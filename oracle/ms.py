@@ -25,7 +25,13 @@ Readings (the paper is silent or garbled on these):
   convention); conjugation is a no-op for the real, even Green operator;
 * the 3D SFFT is applied one dimension at a time (x, then y, then z), each
   operator application followed by a rounding; the inverse uses the adjoint
-  trains in the reverse order (z, y, x).
+  trains in the reverse order (z, y, x);
+* grids may have a different power of two per dimension, including 2^0 = 1:
+  a grid one voxel thick along z is the two-dimensional problem (for
+  conductivity exactly; for elasticity in plane strain), every field
+  uniform along z, xi_z = 0, and that dimension holds no QTT sites.
+  Interleaved order with unequal bit counts: level by level (the a-th bit of
+  x, then of y, then of z, skipping a dimension whose bits are used up).
 """
 from __future__ import annotations
 
@@ -57,7 +63,7 @@ def iso_voigt(lam: float, mu: float) -> np.ndarray:
 @dataclass
 class Problem:
     kind: str                    # "scalar" or "elastic"
-    indicator: np.ndarray        # (N, N, N) 0/1, 1 = phase 2
+    indicator: np.ndarray        # (Nx, Ny, Nz) 0/1, 1 = phase 2 (powers of two, Nz = 1 allowed)
     C1: np.ndarray               # phase-1 tensor (3x3 or 6x6)
     C2: np.ndarray               # phase-2 tensor
     C0: np.ndarray               # reference tensor
@@ -89,22 +95,34 @@ def elastic_problem(indicator, lam1, mu1, lam2, mu2) -> Problem:
 # ---------------------------------------------------- Green operators --
 
 def frequencies(N: int) -> np.ndarray:
+    """xi_k = k below the Nyquist index, else k - N (numpy.fft.fftfreq times N;
+    the single frequency of a one-voxel dimension is 0)."""
     k = np.arange(N)
-    return np.where(k < N // 2, k, k - N).astype(np.float64)
+    return np.where(k < (N + 1) // 2, k, k - N).astype(np.float64)
+
+
+def grid_shape(pb: Problem):
+    return tuple(pb.indicator.shape)
+
+
+def grid_bits(shape) -> tuple:
+    nb = tuple(int(round(math.log2(N))) for N in shape)
+    assert all(1 << b == N for b, N in zip(nb, shape)), shape
+    return nb
 
 
 def green_dense(pb: Problem) -> np.ndarray:
     """Dense Green operator G[I, J, kx, ky, kz] in the natural frequency order."""
-    N = pb.N
-    f = frequencies(N)
-    xi = [f[:, None, None] * np.ones((1, N, N)),
-          f[None, :, None] * np.ones((N, 1, N)),
-          f[None, None, :] * np.ones((N, N, 1))]
+    Nx, Ny, Nz = grid_shape(pb)
+    ones = np.ones((Nx, Ny, Nz))
+    xi = [frequencies(Nx)[:, None, None] * ones,
+          frequencies(Ny)[None, :, None] * ones,
+          frequencies(Nz)[None, None, :] * ones]
     q2 = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
     zero = q2 == 0
     q2s = np.where(zero, 1.0, q2)
     if pb.kind == "scalar":
-        G = np.zeros((3, 3, N, N, N))
+        G = np.zeros((3, 3, Nx, Ny, Nz))
         for i in range(3):
             for j in range(3):
                 G[i, j] = xi[i] * xi[j] / (pb.k0 * q2s)
@@ -113,7 +131,7 @@ def green_dense(pb: Problem) -> np.ndarray:
     lam0, mu0 = pb.lam0, pb.mu0
     coef = (lam0 + mu0) / (mu0 * (lam0 + 2 * mu0))
     d = np.eye(3)
-    G = np.zeros((6, 6, N, N, N))
+    G = np.zeros((6, 6, Nx, Ny, Nz))
     for I, (i, j) in enumerate(VOIGT):
         for J, (k, h) in enumerate(VOIGT):
             g = (d[k, i] * xi[h] * xi[j] + d[h, i] * xi[k] * xi[j]
@@ -155,12 +173,12 @@ def ms_dense(pb: Problem, E: np.ndarray, tol: float = 1e-10, max_iter: int = 100
              G: np.ndarray | None = None, keep_field: bool = False) -> MSResult:
     """Algorithm 1: tau = (C - C0) eps; tau^ = F[tau]; eps^ = G tau^;
     eps_{m+1} = E - F^{-1}[eps^]; stop when the relative change is < tol."""
-    N = pb.N
+    shape = grid_shape(pb)
     if G is None:
         G = green_dense(pb)
     E = np.asarray(E, dtype=np.complex128)
-    eps = np.broadcast_to(E[:, None, None, None], (pb.ncomp, N, N, N)).astype(np.complex128)
-    normE = float(np.linalg.norm(E)) * math.sqrt(N ** 3)
+    eps = np.broadcast_to(E[:, None, None, None], (pb.ncomp,) + shape).astype(np.complex128)
+    normE = float(np.linalg.norm(E)) * math.sqrt(float(np.prod(shape)))
     res = []
     it = 0
     for it in range(1, max_iter + 1):
@@ -193,68 +211,82 @@ def effective_tensor_dense(pb: Problem, tol=1e-10, max_iter=1000):
 
 # ---------------------------------------------- QTT representations --
 
-def site_permutation(n: int, ordering: str) -> list:
-    """Axis permutation from (x1..xn, y1..yn, z1..zn) to the chosen site order."""
+def _bits3(n) -> tuple:
+    """Bits per dimension: an int means a cube."""
+    return (n, n, n) if isinstance(n, (int, np.integer)) else tuple(n)
+
+
+def site_permutation(n, ordering: str) -> list:
+    """Axis permutation from (x bits, y bits, z bits) to the chosen site order;
+    n: bits per dimension (an int for a cube)."""
+    nb = _bits3(n)
+    start = [0, nb[0], nb[0] + nb[1]]
     if ordering == "grouped":
-        return list(range(3 * n))
+        return list(range(sum(nb)))
     if ordering == "interleaved":
         perm = []
-        for a in range(n):
-            perm += [a, n + a, 2 * n + a]
+        for a in range(max(nb)):
+            for dim in range(3):
+                if a < nb[dim]:
+                    perm.append(start[dim] + a)
         return perm
     raise ValueError(ordering)
 
 
-def dim_positions(n: int, ordering: str, dim: int) -> list:
+def dim_positions(n, ordering: str, dim: int) -> list:
     """Spatial site numbers (0-based, control site excluded) holding the bits of `dim`."""
-    perm = site_permutation(n, ordering)
-    return [s for s, ax in enumerate(perm) if dim * n <= ax < (dim + 1) * n]
+    nb = _bits3(n)
+    lo = sum(nb[:dim])
+    perm = site_permutation(nb, ordering)
+    return [s for s, ax in enumerate(perm) if lo <= ax < lo + nb[dim]]
 
 
-def spatial_to_sites(field: np.ndarray, n: int, ordering: str, momentum: bool = False,
+def spatial_to_sites(field: np.ndarray, n, ordering: str, momentum: bool = False,
                      lead: int = 0) -> np.ndarray:
-    """Reshape a field (..., N, N, N) with `lead` leading axes into one axis per
-    bit in site order.  Position space: MSB first; momentum space: the bits
-    of every dimension reversed (LSB first)."""
+    """Reshape a field (..., Nx, Ny, Nz) with `lead` leading axes into one axis
+    per bit in site order.  Position space: MSB first; momentum space: the
+    bits of every dimension reversed (LSB first)."""
+    nb = _bits3(n)
+    d = sum(nb)
     lead_shape = field.shape[:lead]
-    a = field.reshape(lead_shape + (2,) * (3 * n))
-    axes = list(range(3 * n))
+    a = field.reshape(lead_shape + (2,) * d)
+    axes = list(range(d))
     if momentum:
-        axes = [dim * n + (n - 1 - b) for dim in range(3) for b in range(n)]
+        start = [0, nb[0], nb[0] + nb[1]]
+        axes = [start[dim] + (nb[dim] - 1 - b) for dim in range(3) for b in range(nb[dim])]
     a = a.transpose(list(range(lead)) + [lead + ax for ax in axes])
-    perm = site_permutation(n, ordering)
+    perm = site_permutation(nb, ordering)
     return a.transpose(list(range(lead)) + [lead + p for p in perm])
 
 
-def sites_to_spatial(arr: np.ndarray, n: int, ordering: str, lead: int = 0) -> np.ndarray:
+def sites_to_spatial(arr: np.ndarray, n, ordering: str, lead: int = 0) -> np.ndarray:
     """Inverse of spatial_to_sites (position space)."""
-    perm = site_permutation(n, ordering)
+    nb = _bits3(n)
+    perm = site_permutation(nb, ordering)
     inv = np.argsort(perm)
     a = arr.transpose(list(range(lead)) + [lead + i for i in inv])
-    N = 1 << n
-    return a.reshape(arr.shape[:lead] + (N, N, N))
+    return a.reshape(arr.shape[:lead] + tuple(1 << b for b in nb))
 
 
 @dataclass
 class QTTOperators:
-    n: int
+    n: tuple                      # bits per dimension
     ordering: str
     ncomp: int
     chi: list                     # phase indicator TT (spatial sites only)
     dC: list                      # operator train of C(x) - C0 (control + spatial)
     gamma: list                   # Green operator train in momentum convention
-    qft: list                     # per-dimension forward SFFT trains [x, y, z]
+    qft: list                     # per-dimension forward SFFT trains [x, y, z] (None: no bits)
     qft_inv: list                 # adjoints
     ones: list                    # all-ones spatial TT
 
 
 def build_operators(pb: Problem, ordering: str = "interleaved", op_tol: float = 1e-10,
                     qft_tol: float = 1e-12) -> QTTOperators:
-    N = pb.N
-    n = int(round(math.log2(N)))
-    assert 1 << n == N
+    shape = grid_shape(pb)
+    n = grid_bits(shape)
     nc = pb.ncomp
-    d_sp = 3 * n
+    d_sp = sum(n)
     chi = T.tt_svd(spatial_to_sites(pb.indicator.astype(np.complex128), n, ordering), op_tol)
     ones = T.ones_tt([2] * d_sp)
     ctrl_a = (pb.C1 - pb.C0).astype(np.complex128).reshape(1, nc, nc, 1)
@@ -263,16 +295,20 @@ def build_operators(pb: Problem, ordering: str = "interleaved", op_tol: float = 
     part_b = [ctrl_b] + T.diag_mpo_from_tt(chi)
     dC = T.mpo_add(part_a, part_b)
     # Green operator: TT-SVD of G[(I J), bits...] in the momentum convention
-    G = green_dense(pb).reshape(nc * nc, N, N, N).astype(np.complex128)
+    G = green_dense(pb).reshape((nc * nc,) + shape).astype(np.complex128)
     Gs = spatial_to_sites(G, n, ordering, momentum=True, lead=1)
     g_tt = T.tt_svd(Gs, op_tol)
     c0 = g_tt[0]
     gamma = [c0.reshape(1, nc, nc, c0.shape[2])] + T.diag_mpo_from_tt(g_tt[1:])
     # SFFT, one dimension at a time, embedded with identities elsewhere
-    q1 = QF.qft_mpo(n, -1.0, qft_tol)
     dims = [nc] + [2] * d_sp
     qft, qinv = [], []
     for dim in range(3):
+        if n[dim] == 0:
+            qft.append(None)
+            qinv.append(None)
+            continue
+        q1 = QF.qft_mpo(n[dim], -1.0, qft_tol)
         pos = [1 + s for s in dim_positions(n, ordering, dim)]
         full = QF.embed_1d_mpo(q1, pos, 1 + d_sp, dims)
         qft.append(full)
@@ -289,7 +325,7 @@ def qtt_mean_stress(pb: Problem, ops: QTTOperators, eps_tt) -> np.ndarray:
     """sigma = C1 <eps> + (C2 - C1) <chi eps>, the means by inner products with
     e_I (x) ones and e_I (x) chi (Appendix A)."""
     nc = ops.ncomp
-    Nvox = float(2 ** (3 * ops.n))
+    Nvox = float(2 ** sum(ops.n))
     m1 = np.zeros(nc, dtype=np.complex128)
     m2 = np.zeros(nc, dtype=np.complex128)
     for I in range(nc):
@@ -309,7 +345,7 @@ def ms_qtt(pb: Problem, E, ops: QTTOperators | None = None, eps: float = 1e-8,
       stop when ||eps_{m+1} - eps_m|| / ||E 1|| < tol (after min_iter)."""
     if ops is None:
         ops = build_operators(pb, ordering)
-    d_sp = 3 * ops.n
+    d_sp = sum(ops.n)
     Et = e_tt(E, d_sp)
     normE = T.tt_norm(Et)
     x = [c.copy() for c in Et]
@@ -325,10 +361,12 @@ def ms_qtt(pb: Problem, E, ops: QTTOperators | None = None, eps: float = 1e-8,
         tau = rnd(T.tt_mpo_apply(ops.dC, x), "dC")
         h = tau
         for dim in range(3):
-            h = rnd(T.tt_mpo_apply(ops.qft[dim], h), "S%d" % dim)
+            if ops.qft[dim] is not None:
+                h = rnd(T.tt_mpo_apply(ops.qft[dim], h), "S%d" % dim)
         h = rnd(T.tt_mpo_apply(ops.gamma, h), "G")
         for dim in (2, 1, 0):
-            h = rnd(T.tt_mpo_apply(ops.qft_inv[dim], h), "Si%d" % dim)
+            if ops.qft_inv[dim] is not None:
+                h = rnd(T.tt_mpo_apply(ops.qft_inv[dim], h), "Si%d" % dim)
         x_new = rnd(T.tt_add(Et, h, 1.0, -1.0), "E")
         r = T.tt_norm(T.tt_add(x_new, x, 1.0, -1.0)) / normE
         res.append(r)

@@ -37,6 +37,59 @@ def laminate_indicator(N: int, axis: int = 0, fraction: float = 0.5) -> np.ndarr
     return np.broadcast_to(ind1d.reshape(shape), (N, N, N)).copy()
 
 
+def prism(ind2d: np.ndarray) -> np.ndarray:
+    """A two-dimensional phase image (Nx, Ny) as a grid one voxel thick along
+    z (Nx, Ny, 1): the plane problem in the three-dimensional solver."""
+    return np.ascontiguousarray(ind2d, dtype=np.float64)[:, :, None].copy()
+
+
+def laminate_indicator_2d(N: int, axis: int = 0, fraction: float = 0.5) -> np.ndarray:
+    """Plane laminate (N, N, 1): layers normal to `axis` (0 or 1)."""
+    c = voxel_centres(N)
+    ind1d = (c < fraction).astype(np.float64)
+    img = ind1d[:, None] * np.ones((1, N)) if axis == 0 else np.ones((N, 1)) * ind1d[None, :]
+    return prism(img)
+
+
+def box_indicator_2d(N: int, area_fraction: float = 0.2, centre=(0.5, 0.5)) -> np.ndarray:
+    """Square inclusion of the given area fraction in the plane (N, N, 1) --
+    the box geometry of the paper's Fig. 4."""
+    h = 0.5 * math.sqrt(area_fraction)
+    c = voxel_centres(N)
+    img = (np.abs(c - centre[0]) <= h)[:, None] & (np.abs(c - centre[1]) <= h)[None, :]
+    return prism(img.astype(np.float64))
+
+
+def multibox_indicator_2d(N: int, count: int = 8, area_fraction: float = 0.2, seed: int = 0) -> np.ndarray:
+    """`count` non-overlapping axis-aligned squares of random sizes and
+    positions (periodic minimum image) filling about `area_fraction` of the
+    plane (N, N, 1): a synthetic look-alike of the paper's multibox images."""
+    rng = np.random.default_rng(seed)
+    c = voxel_centres(N)
+    img = np.zeros((N, N), dtype=bool)
+    placed = []
+    target = area_fraction / count
+    tries = 0
+    while len(placed) < count and tries < 10000:
+        tries += 1
+        h = 0.5 * math.sqrt(target * rng.uniform(0.5, 1.5))
+        x0, y0 = rng.uniform(0, 1, 2)
+        ok = True
+        for (x1, y1, h1) in placed:
+            dx = abs((x0 - x1 + 0.5) % 1.0 - 0.5)
+            dy = abs((y0 - y1 + 0.5) % 1.0 - 0.5)
+            if dx < h + h1 + 1.0 / N and dy < h + h1 + 1.0 / N:
+                ok = False
+                break
+        if not ok:
+            continue
+        placed.append((x0, y0, h))
+        dxs = np.abs((c - x0 + 0.5) % 1.0 - 0.5)
+        dys = np.abs((c - y0 + 0.5) % 1.0 - 0.5)
+        img |= (dxs <= h)[:, None] & (dys <= h)[None, :]
+    return prism(img.astype(np.float64))
+
+
 def box_indicator(N: int, volume_fraction: float = 0.2, centre=(0.5, 0.5, 0.5)) -> np.ndarray:
     """Axis-aligned cubic inclusion of the given volume fraction (the 3D
     counterpart of the box geometry of the paper's Fig. 4)."""

@@ -187,3 +187,66 @@ def test_qtt_scalar_sphere_matches_dense():
     Cd, _ = MS.effective_tensor_dense(pb, tol=1e-10, max_iter=500)
     Cq = _qtt_effective(pb, "interleaved", 1e-10, max_iter=80, tol=1e-10)
     assert np.linalg.norm(Cq - Cd) / np.linalg.norm(Cd) < 1e-7
+
+
+# ------------------------------------------------------------ plane (2D) and anisotropic grids
+
+def test_plane_scalar_laminate_closed_form():
+    """32 x 32 x 1 laminate (15 bits in the plane, none along z): the QTT
+    solve gives the plane laminate's harmonic mean 20/11 across the layers
+    and the arithmetic mean 11/2 along them and along z, and agrees with the
+    dense solve."""
+    pb = MS.scalar_problem(I.laminate_indicator_2d(32), 1.0, 10.0)
+    ops = MS.build_operators(pb, "interleaved")
+    assert ops.n == (5, 5, 0) and len(ops.chi) == 10 and ops.qft[2] is None
+    expect = np.diag([20.0 / 11.0, 5.5, 5.5])
+    for k in range(3):
+        E = np.zeros(3)
+        E[k] = 1.0
+        r = MS.ms_qtt(pb, E, ops, eps=1e-8, max_rank=64, tol=1e-12, max_iter=4)
+        np.testing.assert_allclose(r.sigma.real, expect[:, k], atol=1e-10)
+    Cd, _ = MS.effective_tensor_dense(pb, tol=1e-12)
+    np.testing.assert_allclose(Cd.real, expect, atol=1e-10)
+
+
+def test_plane_elastic_laminate_backus():
+    """16 x 16 x 1 elastic laminate in plane strain (every field uniform along
+    z): the dense solve reproduces the Backus averages."""
+    lam1, mu1 = I.lame_from_young(1.0, 0.3)
+    lam2, mu2 = I.lame_from_young(10.0, 0.3)
+    pb = MS.elastic_problem(I.laminate_indicator_2d(16), lam1, mu1, lam2, mu2)
+    C, _ = MS.effective_tensor_dense(pb, tol=1e-12, max_iter=400)
+    ref = MS.elastic_laminate_ceff(np.array([lam1, lam2]), np.array([mu1, mu2]), np.array([0.5, 0.5]))
+    np.testing.assert_allclose(C.real, ref, atol=1e-9 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("ordering", ["interleaved", "grouped"])
+def test_plane_box_qtt_matches_dense(ordering):
+    pb = MS.scalar_problem(I.box_indicator_2d(8, 0.25), 1.0, 10.0)
+    Cd, _ = MS.effective_tensor_dense(pb, tol=1e-12)
+    ops = MS.build_operators(pb, ordering)
+    for k in range(2):
+        E = np.zeros(3)
+        E[k] = 1.0
+        r = MS.ms_qtt(pb, E, ops, eps=1e-12, tol=1e-12, max_iter=200)
+        np.testing.assert_allclose(r.sigma, Cd[:, k], atol=1e-8)
+
+
+def test_anisotropic_grid_qtt_matches_dense():
+    """8 x 4 x 2 grid (3 + 2 + 1 bits, interleaved level by level)."""
+    rng = np.random.default_rng(8)
+    ind = (rng.random((8, 4, 2)) < 0.3).astype(np.float64)
+    pb = MS.scalar_problem(ind, 1.0, 5.0)
+    Cd, _ = MS.effective_tensor_dense(pb, tol=1e-12)
+    for ordering in ("interleaved", "grouped"):
+        ops = MS.build_operators(pb, ordering)
+        assert ops.n == (3, 2, 1)
+        E = np.array([0.3, -1.0, 0.5])
+        r = MS.ms_qtt(pb, E, ops, eps=1e-12, tol=1e-12, max_iter=300)
+        np.testing.assert_allclose(r.sigma, Cd @ E, atol=1e-8)
+
+
+def test_multibox_plane_geometry():
+    img = I.multibox_indicator_2d(64, count=8, area_fraction=0.2, seed=3)
+    assert img.shape == (64, 64, 1)
+    assert 0.1 < img.mean() < 0.3
