@@ -262,11 +262,15 @@ QTT_API int qtt_mpo_convert(qtt_ctx* ctx, const qtt_mpo* A, qtt_dtype dtype, qtt
 /* ---------------------------------------------------- homogenisation */
 typedef struct {
   int32_t ncomp;        /* 3: scalar conductivity, 6: elasticity (Voigt 11,22,33,23,13,12) */
-  int32_t nbits;        /* N = 2^nbits voxels per side                                     */
-  const double* indicator; /* host, N^3 values 0/1 (1 = phase 2), x slowest                 */
+  int32_t nbits;        /* N = 2^nbits voxels per side (a cube; see nbits_dim)             */
+  const double* indicator; /* host, Nx*Ny*Nz values 0/1 (1 = phase 2), x slowest, z fastest */
   double k1, k2;        /* scalar: phase conductivities                                    */
   double lam1, mu1, lam2, mu2; /* elasticity: Lame constants of phases 1 and 2             */
-  int32_t interleaved;  /* site order: 1 = x1 y1 z1 x2 ..., 0 = grouped by dimension      */
+  int32_t interleaved;  /* site order: 1 = x1 y1 z1 x2 ... (level by level), 0 = grouped   */
+  int32_t nbits_dim[3]; /* if any is nonzero: 2^nbits_dim[a] voxels along x, y, z (0 to 15
+                         * each, 1 to 27 in all; nbits is then ignored).  A dimension of
+                         * 2^0 = 1 voxel has no sites: every field is uniform along it, the
+                         * plane problem (plane strain for elasticity) for nbits_dim[2] = 0. */
 } qtt_rve;
 
 /* Per-bond rank features of one rounding inside ms_homogenize (the rank

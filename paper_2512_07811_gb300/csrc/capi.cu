@@ -916,20 +916,52 @@ int ctrl_core(qtt_ctx* c, const double* Mh, int nc, zc* dst) {
   return upload(c, dst, h.data(), h.size() * sizeof(zc));
 }
 
-// site p (0-based, spatial) -> (dimension, bit position)
-void site_of(int p, int nbits, int interleaved, int* dim, int* pos) {
-  if (interleaved) {
-    *dim = p % 3;
-    *pos = p / 3;
+// Bits per dimension of an RVE (nbits_dim, or nbits for every dimension when
+// nbits_dim is all zero) and its spatial sites: grouped by dimension (x bits,
+// y bits, z bits) or interleaved level by level (bit a of x, y, z in turn,
+// skipping a dimension whose bits are used up).
+static void rve_bits(const qtt_rve* rve, int nb[3]) {
+  const bool per_dim = rve->nbits_dim[0] || rve->nbits_dim[1] || rve->nbits_dim[2];
+  for (int a = 0; a < 3; ++a) nb[a] = per_dim ? rve->nbits_dim[a] : rve->nbits;
+}
+
+// 0 to 15 bits per dimension, 1 to 27 in all (the operator setup fills the
+// Green operator densely: ncomp^2 * 2^bits complex doubles)
+static bool rve_bits_valid(const qtt_rve* rve) {
+  int nb[3];
+  rve_bits(rve, nb);
+  const int tot = nb[0] + nb[1] + nb[2];
+  for (int a = 0; a < 3; ++a)
+    if (nb[a] < 0 || nb[a] > 15) return false;
+  return tot >= 1 && tot <= 27;
+}
+
+static SiteMap site_map(const qtt_rve* rve) {
+  SiteMap m{};
+  rve_bits(rve, m.nb);
+  m.d = 0;
+  if (rve->interleaved) {
+    const int mx = std::max(m.nb[0], std::max(m.nb[1], m.nb[2]));
+    for (int a = 0; a < mx; ++a)
+      for (int dim = 0; dim < 3; ++dim)
+        if (a < m.nb[dim]) {
+          m.dim[m.d] = (signed char)dim;
+          m.pos[m.d++] = (signed char)a;
+        }
   } else {
-    *dim = p / nbits;
-    *pos = p % nbits;
+    for (int dim = 0; dim < 3; ++dim)
+      for (int a = 0; a < m.nb[dim]; ++a) {
+        m.dim[m.d] = (signed char)dim;
+        m.pos[m.d++] = (signed char)a;
+      }
   }
+  return m;
 }
 
 int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2, const double* C0, double op_tol,
               double k0, double lam0, double mu0, Ops* ops) {
-  const int nc = rve->ncomp, nb = rve->nbits, dsp = 3 * nb, d = dsp + 1;
+  const SiteMap sm = site_map(rve);
+  const int nc = rve->ncomp, dsp = sm.d, d = dsp + 1;
   const int64_t Nv = (int64_t)1 << dsp;
   // phase indicator train
   void *ind = nullptr, *dense = nullptr;
@@ -941,8 +973,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     return s;
   }
   c->launches++;
-  s = qtt_fill_indicator_sites<double>(reinterpret_cast<double*>(ind), nb, rve->interleaved,
-                                       reinterpret_cast<zc*>(dense), c->stream);
+  s = qtt_fill_indicator_sites<double>(reinterpret_cast<double*>(ind), sm, reinterpret_cast<zc*>(dense), c->stream);
   if (!s) s = tt_svd_dev<double>(c, dsp, std::vector<int>(dsp, 2), reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128,
                                  &ops->chi);
   dfree(c, ind);
@@ -952,7 +983,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
   }
   // Green operator train
   c->launches++;
-  s = qtt_fill_green_dense<double>(reinterpret_cast<zc*>(dense), nb, nc, rve->interleaved, k0, lam0, mu0, c->stream);
+  s = qtt_fill_green_dense<double>(reinterpret_cast<zc*>(dense), sm, nc, k0, lam0, mu0, c->stream);
   qtt_tt* g = nullptr;
   if (!s) {
     std::vector<int> modes(d, 2);
@@ -1001,17 +1032,18 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     TRY(qtt_diag_mpo_core<double>(core_ptr<zc>(ops->chi, k - 1), ops->chi->r[k - 1], 2, ops->chi->r[k],
                                   core_ptr<zc>(ops->dCb, k), c->stream));
   }
-  // superfast Fourier transform, one dimension at a time
-  qtt_mpo* q1 = nullptr;
-  TRY(qtt_qft_mpo(c, nb, -1, 1e-12, &q1));
+  // superfast Fourier transform, one dimension at a time (none for a
+  // dimension without bits)
   for (int dim = 0; dim < 3; ++dim) {
+    if (sm.nb[dim] == 0) continue;
+    qtt_mpo* q1 = nullptr;
+    TRY(qtt_qft_mpo(c, sm.nb[dim], -1, 1e-12, &q1));
     // the bond of the one-dimensional train is carried unchanged through the
     // sites of the other dimensions (identity cores)
     std::vector<int> gq(d + 1, 1);
     int cur = 1;
     for (int p = 0; p < dsp; ++p) {
-      int dm, pos;
-      site_of(p, nb, rve->interleaved, &dm, &pos);
+      const int dm = sm.dim[p], pos = sm.pos[p];
       if (dm == dim) cur = q1->g[pos + 1];
       gq[p + 2] = cur;
     }
@@ -1025,8 +1057,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     c->launches++;
     qtt_identity_core<double>(1, nc, core_ptr<zc>(Q, 0), c->stream);
     for (int p = 0; p < dsp; ++p) {
-      int dm, pos;
-      site_of(p, nb, rve->interleaved, &dm, &pos);
+      const int dm = sm.dim[p], pos = sm.pos[p];
       const int k = p + 1;
       if (dm == dim) {
         cudaMemcpyAsync(core_ptr<char>(Q, k), core_ptr<char>(q1, pos),
@@ -1042,8 +1073,8 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     }
     ops->q[dim] = Q;
     ops->qi[dim] = Qi;
+    mpo_free(q1);
   }
-  mpo_free(q1);
   return QTT_OK;
 }
 
@@ -1051,7 +1082,8 @@ template <class R>
 int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2h, Ops& O, double tol, int max_rank,
              const ms_opts& o, qtt_dtype dt, double* C_eff, ms_report* rep) {
   typedef cplx<R> C;
-  const int nc = rve->ncomp, nb = rve->nbits, dsp = 3 * nb, d = dsp + 1;
+  const SiteMap sm = site_map(rve);
+  const int nc = rve->ncomp, dsp = sm.d, d = dsp + 1;
   std::vector<int> modes(d, 2);
   modes[0] = nc;
   const int ell = max_rank + std::max(0, (int)o.oversample);
@@ -1092,6 +1124,8 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
   TRY(convert_mpo(c, O.dCb, dt, &dCb));
   TRY(convert_mpo(c, O.gamma, dt, &G));
   for (int i = 0; i < 3; ++i) {
+    Q[i] = Qi[i] = nullptr;
+    if (!O.q[i]) continue;  // a dimension without bits
     TRY(convert_mpo(c, O.q[i], dt, &Q[i]));
     TRY(convert_mpo(c, O.qi[i], dt, &Qi[i]));
   }
@@ -1239,6 +1273,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
       static const char* fwd[3] = {"S0", "S1", "S2"};
       static const char* inv[3] = {"Si0", "Si1", "Si2"};
       for (int dim = 0; dim < 3; ++dim) {
+        if (!Q[dim]) continue;
         stage = fwd[dim];
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {Q[dim]};
@@ -1259,6 +1294,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         h = hn;
       }
       for (int dim = 2; dim >= 0; --dim) {
+        if (!Qi[dim]) continue;
         stage = inv[dim];
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {Qi[dim]};
@@ -1344,8 +1380,7 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
 extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, double tol, int max_rank,
                              const ms_opts* o, double* C_eff, ms_report* rep) {
   if (!c || !rve || !C0 || !o || !C_eff || max_rank < 1) return QTT_ERR_ARG;
-  if ((rve->ncomp != 3 && rve->ncomp != 6) || rve->nbits < 1 || rve->nbits > 10 || !rve->indicator)
-    return QTT_ERR_ARG;
+  if ((rve->ncomp != 3 && rve->ncomp != 6) || !rve->indicator || !rve_bits_valid(rve)) return QTT_ERR_ARG;
   if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32) return QTT_ERR_ARG;
   const int nc = rve->ncomp;
   std::vector<double> C1(nc * nc, 0.0), C2(nc * nc, 0.0);
@@ -1424,7 +1459,7 @@ extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const
     if (nc != 3 && nc != 6) return QTT_ERR_ARG;
     off[i + 1] = off[i] + (int64_t)nc * nc;
     for (int lc = 0; lc < nc; ++lc)
-      if (o->load_mask & (1 << lc)) jobs.push_back(Job{i, lc, (int64_t)rves[i].nbits * 3 * nc});
+      if (o->load_mask & (1 << lc)) jobs.push_back(Job{i, lc, (int64_t)site_map(&rves[i]).d * nc});
   }
   std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.cost > b.cost; });
   for (int64_t i = 0; i < off[n]; ++i) C_effs[i] = 0.0;

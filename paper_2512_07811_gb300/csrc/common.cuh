@@ -70,6 +70,17 @@ QTT_HD int64_t midx_off(const MIdx& m, int64_t v) {
 }
 QTT_HD int64_t midx_size(const MIdx& m) { return m.n1 * m.n2; }
 
+// Spatial QTT sites of a grid with 2^nb[dim] voxels along dimension dim:
+// site p (0-based, control site excluded) holds bit pos[p] (0 = most
+// significant in position space) of dimension dim[p].  Passed to kernels by
+// value.
+struct SiteMap {
+  int d;                 // number of spatial sites, nb[0] + nb[1] + nb[2]
+  int nb[3];
+  signed char dim[64];
+  signed char pos[64];
+};
+
 // C[b][m][n] = alpha * sum_k opA(A)[b][m][k] * opB(B)[b][k][n] + beta * C[b][m][n]
 // with every one of b, m, n, k a two-level multi-index per operand.
 struct GemmDesc {

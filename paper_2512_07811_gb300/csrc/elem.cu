@@ -187,27 +187,15 @@ __global__ void qft_dense_kernel(cplx<R>* out, int n, double sign) {
   }
 }
 
-// weight of spatial site p (0-based) and its dimension, for the given ordering
-__device__ __forceinline__ void site_info(int p, int nbits, int interleaved, int* dim, int* pos) {
-  if (interleaved) {
-    *dim = p % 3;
-    *pos = p / 3;
-  } else {
-    *dim = p / nbits;
-    *pos = p % nbits;
-  }
-}
-
-// Dense Green operator in momentum site order: out[IJ * 2^(3n) + s], s the
-// site multi-index (site 0 slowest).  In momentum space site (dim, pos)
-// carries the bit of weight 2^pos of the frequency index k_dim (Sec. 3.2:
-// bits reversed per dimension).  Frequencies xi = k for k < N/2 else k - N.
+// Dense Green operator in momentum site order: out[IJ * 2^d + s], s the site
+// multi-index (site 0 slowest).  In momentum space site (dim, pos) carries
+// the bit of weight 2^pos of the frequency index k_dim (Sec. 3.2: bits
+// reversed per dimension).  Frequencies xi = k below the Nyquist index, else
+// k - N (a one-voxel dimension has the single frequency 0).
 template <class R>
-__global__ void green_dense_kernel(cplx<R>* out, int nbits, int ncomp, int interleaved, double k0,
-                                   double lam0, double mu0) {
-  const int d = 3 * nbits;
+__global__ void green_dense_kernel(cplx<R>* out, SiteMap m, int ncomp, double k0, double lam0, double mu0) {
+  const int d = m.d;
   const int64_t total = (int64_t)1 << d;
-  const int64_t N = (int64_t)1 << nbits;
   const int vi[6] = {0, 1, 2, 1, 0, 0};
   const int vj[6] = {0, 1, 2, 2, 2, 1};
   const double vw[6] = {1, 1, 1, 2, 2, 2};
@@ -215,13 +203,14 @@ __global__ void green_dense_kernel(cplx<R>* out, int nbits, int ncomp, int inter
        s += (int64_t)gridDim.x * blockDim.x) {
     int64_t k[3] = {0, 0, 0};
     for (int p = 0; p < d; ++p) {
-      int bit = (int)((s >> (d - 1 - p)) & 1);
-      int dim, pos;
-      site_info(p, nbits, interleaved, &dim, &pos);
-      k[dim] |= (int64_t)bit << pos;
+      const int bit = (int)((s >> (d - 1 - p)) & 1);
+      k[m.dim[p]] |= (int64_t)bit << m.pos[p];
     }
     double xi[3];
-    for (int a = 0; a < 3; ++a) xi[a] = (double)(k[a] < N / 2 ? k[a] : k[a] - N);
+    for (int a = 0; a < 3; ++a) {
+      const int64_t N = (int64_t)1 << m.nb[a];
+      xi[a] = (double)(k[a] < (N + 1) / 2 ? k[a] : k[a] - N);
+    }
     double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
     if (ncomp == 3) {
       for (int I = 0; I < 3; ++I)
@@ -250,23 +239,21 @@ __global__ void green_dense_kernel(cplx<R>* out, int nbits, int ncomp, int inter
   }
 }
 
-// Phase indicator (N^3 doubles, x slowest, MSB-first bits) to site order.
+// Phase indicator (Nx x Ny x Nz doubles, x slowest, MSB-first bits) to site order.
 template <class R>
-__global__ void indicator_sites_kernel(const double* __restrict__ ind, int nbits, int interleaved,
-                                       cplx<R>* __restrict__ out) {
-  const int d = 3 * nbits;
+__global__ void indicator_sites_kernel(const double* __restrict__ ind, SiteMap m, cplx<R>* __restrict__ out) {
+  const int d = m.d;
   const int64_t total = (int64_t)1 << d;
-  const int64_t N = (int64_t)1 << nbits;
+  const int64_t Ny = (int64_t)1 << m.nb[1], Nz = (int64_t)1 << m.nb[2];
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
        s += (int64_t)gridDim.x * blockDim.x) {
     int64_t x[3] = {0, 0, 0};
     for (int p = 0; p < d; ++p) {
-      int bit = (int)((s >> (d - 1 - p)) & 1);
-      int dim, pos;
-      site_info(p, nbits, interleaved, &dim, &pos);
-      x[dim] |= (int64_t)bit << (nbits - 1 - pos);
+      const int bit = (int)((s >> (d - 1 - p)) & 1);
+      const int dm = m.dim[p];
+      x[dm] |= (int64_t)bit << (m.nb[dm] - 1 - m.pos[p]);
     }
-    out[s] = cplx<R>((R)ind[(x[0] * N + x[1]) * N + x[2]], R(0));
+    out[s] = cplx<R>((R)ind[(x[0] * Ny + x[1]) * Nz + x[2]], R(0));
   }
 }
 
@@ -508,16 +495,16 @@ int qtt_fill_qft_dense(cplx<R>* out, int n, double sign, cudaStream_t s) {
   CHECK_LAUNCH();
 }
 template <class R>
-int qtt_fill_green_dense(cplx<R>* out, int nbits, int ncomp, int interleaved, double k0, double lam0,
-                         double mu0, cudaStream_t s) {
-  int64_t total = (int64_t)1 << (3 * nbits);
-  green_dense_kernel<R><<<nblocks(total), TPB, 0, s>>>(out, nbits, ncomp, interleaved, k0, lam0, mu0);
+int qtt_fill_green_dense(cplx<R>* out, const SiteMap& m, int ncomp, double k0, double lam0, double mu0,
+                         cudaStream_t s) {
+  const int64_t total = (int64_t)1 << m.d;
+  green_dense_kernel<R><<<nblocks(total), TPB, 0, s>>>(out, m, ncomp, k0, lam0, mu0);
   CHECK_LAUNCH();
 }
 template <class R>
-int qtt_fill_indicator_sites(const double* ind, int nbits, int interleaved, cplx<R>* out, cudaStream_t s) {
-  int64_t total = (int64_t)1 << (3 * nbits);
-  indicator_sites_kernel<R><<<nblocks(total), TPB, 0, s>>>(ind, nbits, interleaved, out);
+int qtt_fill_indicator_sites(const double* ind, const SiteMap& m, cplx<R>* out, cudaStream_t s) {
+  const int64_t total = (int64_t)1 << m.d;
+  indicator_sites_kernel<R><<<nblocks(total), TPB, 0, s>>>(ind, m, out);
   CHECK_LAUNCH();
 }
 
@@ -564,8 +551,8 @@ int qtt_adjoint_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64
   template int qtt_scale_rows<R>(cplx<R>*, int64_t, int64_t, int64_t, const R*, int, cudaStream_t);       \
   template int qtt_isfinite<R>(const cplx<R>*, int64_t, int*, cudaStream_t);                             \
   template int qtt_fill_qft_dense<R>(cplx<R>*, int, double, cudaStream_t);                               \
-  template int qtt_fill_green_dense<R>(cplx<R>*, int, int, int, double, double, double, cudaStream_t);   \
-  template int qtt_fill_indicator_sites<R>(const double*, int, int, cplx<R>*, cudaStream_t);                \
+  template int qtt_fill_green_dense<R>(cplx<R>*, const SiteMap&, int, double, double, double, cudaStream_t);   \
+  template int qtt_fill_indicator_sites<R>(const double*, const SiteMap&, cplx<R>*, cudaStream_t);              \
   template int qtt_fill_gaussian<R>(cplx<R>*, int64_t, uint64_t, uint64_t, double, cudaStream_t);          \
   template int qtt_diag_mpo_core<R>(const cplx<R>*, int64_t, int64_t, int64_t, cplx<R>*, cudaStream_t);    \
   template int qtt_identity_core<R>(int64_t, int64_t, cplx<R>*, cudaStream_t);                             \

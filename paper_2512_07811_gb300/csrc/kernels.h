@@ -72,10 +72,10 @@ int qtt_isfinite(const cplx<R>* x, int64_t count, int* flag, cudaStream_t s);
 template <class R>
 int qtt_fill_qft_dense(cplx<R>* out, int n, double sign, cudaStream_t s);
 template <class R>
-int qtt_fill_green_dense(cplx<R>* out, int nbits, int ncomp, int interleaved, double k0, double lam0,
-                         double mu0, cudaStream_t s);
+int qtt_fill_green_dense(cplx<R>* out, const SiteMap& m, int ncomp, double k0, double lam0, double mu0,
+                         cudaStream_t s);
 template <class R>
-int qtt_fill_indicator_sites(const double* ind, int nbits, int interleaved, cplx<R>* out, cudaStream_t s);
+int qtt_fill_indicator_sites(const double* ind, const SiteMap& m, cplx<R>* out, cudaStream_t s);
 template <class R>
 int qtt_fill_gaussian(cplx<R>* out, int64_t count, uint64_t seed, uint64_t stream, double scale, cudaStream_t s);
 template <class R>

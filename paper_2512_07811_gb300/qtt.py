@@ -52,7 +52,19 @@ class RoundInfo(C.Structure):
 class RVE(C.Structure):
     _fields_ = [("ncomp", C.c_int32), ("nbits", C.c_int32), ("indicator", C.POINTER(C.c_double)),
                 ("k1", C.c_double), ("k2", C.c_double), ("lam1", C.c_double), ("mu1", C.c_double),
-                ("lam2", C.c_double), ("mu2", C.c_double), ("interleaved", C.c_int32)]
+                ("lam2", C.c_double), ("mu2", C.c_double), ("interleaved", C.c_int32),
+                ("nbits_dim", C.c_int32 * 3)]
+
+
+def _grid_bits(ind):
+    """Bits per dimension of an (Nx, Ny, Nz) phase image (powers of two; a
+    dimension of one voxel has 0 bits: the plane problem)."""
+    if ind.ndim != 3:
+        raise ValueError("the phase indicator must be (Nx, Ny, Nz)")
+    nb = [int(round(np.log2(n))) for n in ind.shape]
+    if any((1 << b) != n for b, n in zip(nb, ind.shape)):
+        raise ValueError("grid sizes must be powers of two, got %s" % (ind.shape,))
+    return nb
 
 
 class MSOpts(C.Structure):
@@ -497,11 +509,10 @@ class MLP:
 
 def _rve(ind, kind, moduli, interleaved):
     ind = np.ascontiguousarray(ind, dtype=np.float64)
-    N = ind.shape[0]
-    nbits = int(round(np.log2(N)))
-    assert ind.shape == (N, N, N) and (1 << nbits) == N
+    nb = _grid_bits(ind)
     rve = RVE()
-    rve.nbits = nbits
+    rve.nbits = max(nb)
+    rve.nbits_dim[0], rve.nbits_dim[1], rve.nbits_dim[2] = nb
     rve.indicator = ind.ctypes.data_as(C.POINTER(C.c_double))
     rve.interleaved = 1 if interleaved else 0
     if kind == "scalar":
@@ -556,11 +567,10 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
     kind "scalar": moduli = (k1, k2), C0 = 3x3; kind "elastic": moduli =
     (lam1, mu1, lam2, mu2), C0 = Voigt 6x6.  Returns (C_eff, report)."""
     ind = np.ascontiguousarray(indicator, dtype=np.float64)
-    N = ind.shape[0]
-    nbits = int(round(np.log2(N)))
-    assert ind.shape == (N, N, N) and (1 << nbits) == N
+    nb = _grid_bits(ind)
     rve = RVE()
-    rve.nbits = nbits
+    rve.nbits = max(nb)
+    rve.nbits_dim[0], rve.nbits_dim[1], rve.nbits_dim[2] = nb
     rve.indicator = ind.ctypes.data_as(C.POINTER(C.c_double))
     rve.interleaved = 1 if interleaved else 0
     if kind == "scalar":

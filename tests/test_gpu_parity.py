@@ -264,6 +264,46 @@ def test_ms_scalar_sphere_matches_dense_oracle(Q, ctx):
     assert np.linalg.norm(C - Cd.real) / np.linalg.norm(Cd.real) < 1e-7
 
 
+def test_ms_plane_laminate_closed_form(Q, ctx):
+    """32 x 32 x 1 laminate (10 spatial sites, none along z): the plane
+    laminate's k_eff = diag(20/11, 11/2, 11/2) to 1e-10 in FP64."""
+    ind = I.laminate_indicator_2d(32)
+    C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), tol=1e-13, max_rank=32,
+                             eps=1e-10, max_iter=20, prec=Q.PREC_F64)
+    np.testing.assert_allclose(C, np.diag([20.0 / 11.0, 5.5, 5.5]), atol=1e-10)
+
+
+def test_ms_plane_elastic_laminate_backus(Q, ctx):
+    """16 x 16 x 1 elastic laminate in plane strain: the Backus averages."""
+    lam1, mu1 = I.lame_from_young(1.0, 0.3)
+    lam2, mu2 = I.lame_from_young(10.0, 0.3)
+    C0 = MS.iso_voigt(0.5 * (lam1 + lam2), 0.5 * (mu1 + mu2))
+    C, rep = Q.ms_homogenize(ctx, I.laminate_indicator_2d(16), "elastic", (lam1, mu1, lam2, mu2), C0, tol=1e-13,
+                             max_rank=32, eps=1e-12, max_iter=200, prec=Q.PREC_F64)
+    Cx = MS.elastic_laminate_ceff([lam2, lam1], [mu2, mu1], [0.5, 0.5])
+    np.testing.assert_allclose(C, Cx, atol=1e-9 * np.abs(Cx).max())
+
+
+def test_ms_plane_box_matches_dense_oracle(Q, ctx):
+    pb = MS.scalar_problem(I.box_indicator_2d(16, 0.25), 1.0, 10.0)
+    Cd, _ = MS.effective_tensor_dense(pb, tol=1e-11, max_iter=500)
+    C, rep = Q.ms_homogenize(ctx, pb.indicator, "scalar", (1.0, 10.0), pb.C0, tol=1e-11, max_rank=64,
+                             eps=1e-11, max_iter=300, oversample=16, prec=Q.PREC_F64)
+    assert np.linalg.norm(C - Cd.real) / np.linalg.norm(Cd.real) < 1e-7
+
+
+@pytest.mark.parametrize("interleaved", [True, False])
+def test_ms_anisotropic_grid_matches_dense_oracle(Q, ctx, interleaved):
+    """8 x 4 x 2 grid (3 + 2 + 1 bits): both site orders reach the dense result."""
+    rng = np.random.default_rng(8)
+    ind = (rng.random((8, 4, 2)) < 0.3).astype(np.float64)
+    pb = MS.scalar_problem(ind, 1.0, 5.0)
+    Cd, _ = MS.effective_tensor_dense(pb, tol=1e-12, max_iter=500)
+    C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 5.0), pb.C0, tol=1e-12, max_rank=64, eps=1e-12,
+                             max_iter=300, oversample=16, prec=Q.PREC_F64, interleaved=interleaved)
+    assert np.linalg.norm(C - Cd.real) / np.linalg.norm(Cd.real) < 1e-8
+
+
 def test_ms_fp32_laminate(Q, ctx):
     ind = I.laminate_indicator(16)
     C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), tol=1e-6, max_rank=32,
