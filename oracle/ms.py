@@ -111,18 +111,16 @@ def grid_bits(shape) -> tuple:
     return nb
 
 
-def green_dense(pb: Problem) -> np.ndarray:
-    """Dense Green operator G[I, J, kx, ky, kz] in the natural frequency order."""
-    Nx, Ny, Nz = grid_shape(pb)
-    ones = np.ones((Nx, Ny, Nz))
-    xi = [frequencies(Nx)[:, None, None] * ones,
-          frequencies(Ny)[None, :, None] * ones,
-          frequencies(Nz)[None, None, :] * ones]
+def green_components(pb: Problem, xi) -> np.ndarray:
+    """Green operator G[I, J, ...] at the frequency vectors xi = (xi_x, xi_y,
+    xi_z) (float arrays of one shape), G = 0 where xi = 0."""
+    xi = [np.asarray(x, dtype=np.float64) for x in xi]
     q2 = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
     zero = q2 == 0
     q2s = np.where(zero, 1.0, q2)
+    shape = q2.shape
     if pb.kind == "scalar":
-        G = np.zeros((3, 3, Nx, Ny, Nz))
+        G = np.zeros((3, 3) + shape)
         for i in range(3):
             for j in range(3):
                 G[i, j] = xi[i] * xi[j] / (pb.k0 * q2s)
@@ -131,7 +129,7 @@ def green_dense(pb: Problem) -> np.ndarray:
     lam0, mu0 = pb.lam0, pb.mu0
     coef = (lam0 + mu0) / (mu0 * (lam0 + 2 * mu0))
     d = np.eye(3)
-    G = np.zeros((6, 6, Nx, Ny, Nz))
+    G = np.zeros((6, 6) + shape)
     for I, (i, j) in enumerate(VOIGT):
         for J, (k, h) in enumerate(VOIGT):
             g = (d[k, i] * xi[h] * xi[j] + d[h, i] * xi[k] * xi[j]
@@ -141,6 +139,16 @@ def green_dense(pb: Problem) -> np.ndarray:
             G[I, J] = VOIGT_W[I] * VOIGT_W[J] * g
     G[:, :, zero] = 0.0
     return G
+
+
+def green_dense(pb: Problem) -> np.ndarray:
+    """Dense Green operator G[I, J, kx, ky, kz] in the natural frequency order."""
+    Nx, Ny, Nz = grid_shape(pb)
+    ones = np.ones((Nx, Ny, Nz))
+    xi = [frequencies(Nx)[:, None, None] * ones,
+          frequencies(Ny)[None, :, None] * ones,
+          frequencies(Nz)[None, None, :] * ones]
+    return green_components(pb, xi)
 
 
 # --------------------------------------------- Algorithm 1 (dense FFT) --

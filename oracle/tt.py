@@ -139,6 +139,16 @@ def mpo_adjoint(mpo):
     return [np.conj(D.transpose(0, 2, 1, 3)) for D in mpo]
 
 
+def tt_entries(cores, idx) -> np.ndarray:
+    """Entries of the train at the multi-indices idx (M x d): the product of
+    the core slices G_k[:, i_k, :]."""
+    idx = np.asarray(idx)
+    v = np.ones((idx.shape[0], 1), dtype=np.complex128)
+    for k, c in enumerate(cores):
+        v = np.einsum("ma,amb->mb", v, c[:, idx[:, k], :])
+    return v[:, 0]
+
+
 def tt_dot(x, y):
     """<x, y> = sum_i conj(x(i)) y(i) by the transfer-matrix chain
     W_k = sum_i A_k(i)^H W_{k-1} B_k(i)."""

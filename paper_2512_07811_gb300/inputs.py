@@ -60,13 +60,38 @@ def box_indicator_2d(N: int, area_fraction: float = 0.2, centre=(0.5, 0.5)) -> n
     return prism(img.astype(np.float64))
 
 
-def multibox_indicator_2d(N: int, count: int = 8, area_fraction: float = 0.2, seed: int = 0) -> np.ndarray:
+def boxes_value(boxes, ix, iy, iz, shape) -> np.ndarray:
+    """Phase value (0.0 / 1.0) at voxels (ix, iy, iz) (integer arrays of one
+    shape) of an (Nx, Ny, Nz) grid for a union of axis-aligned boxes, rows
+    (cx, cy, cz, hx, hy, hz) in unit-cell coordinates: a voxel is in phase 2
+    when, along every axis, the periodic (minimum image) distance
+    |((c - cx + 1/2) mod 1) - 1/2| of its centre c = (i + 1/2)/N from some
+    box centre is at most that box's half width."""
+    boxes = np.asarray(boxes, dtype=np.float64).reshape(-1, 6)
+    idx = [np.asarray(ix), np.asarray(iy), np.asarray(iz)]
+    cen = [(idx[a].astype(np.float64) + 0.5) / shape[a] for a in range(3)]
+    out = np.zeros(np.broadcast(*idx).shape, dtype=bool)
+    for b in boxes:
+        inside = np.ones_like(out)
+        for a in range(3):
+            inside &= np.abs((cen[a] - b[a] + 0.5) % 1.0 - 0.5) <= b[3 + a]
+        out |= inside
+    return out.astype(np.float64)
+
+
+def boxes_indicator(boxes, shape) -> np.ndarray:
+    """The union of boxes voxelised on the whole (Nx, Ny, Nz) grid (see boxes_value)."""
+    ix, iy, iz = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    return boxes_value(boxes, ix, iy, iz, shape)
+
+
+def multibox_boxes_2d(N: int, count: int = 8, area_fraction: float = 0.2, seed: int = 0) -> np.ndarray:
     """`count` non-overlapping axis-aligned squares of random sizes and
-    positions (periodic minimum image) filling about `area_fraction` of the
-    plane (N, N, 1): a synthetic look-alike of the paper's multibox images."""
+    positions (periodic minimum image, at least one voxel of an N x N grid
+    apart) filling about `area_fraction` of the plane, as box rows
+    (cx, cy, 1/2, h, h, 1/2) spanning the single voxel along z: a synthetic
+    look-alike of the paper's multibox images."""
     rng = np.random.default_rng(seed)
-    c = voxel_centres(N)
-    img = np.zeros((N, N), dtype=bool)
     placed = []
     target = area_fraction / count
     tries = 0
@@ -84,10 +109,18 @@ def multibox_indicator_2d(N: int, count: int = 8, area_fraction: float = 0.2, se
         if not ok:
             continue
         placed.append((x0, y0, h))
-        dxs = np.abs((c - x0 + 0.5) % 1.0 - 0.5)
-        dys = np.abs((c - y0 + 0.5) % 1.0 - 0.5)
-        img |= (dxs <= h)[:, None] & (dys <= h)[None, :]
-    return prism(img.astype(np.float64))
+    return np.array([[x0, y0, 0.5, h, h, 0.5] for (x0, y0, h) in placed], dtype=np.float64)
+
+
+def multibox_indicator_2d(N: int, count: int = 8, area_fraction: float = 0.2, seed: int = 0) -> np.ndarray:
+    """The multibox image of multibox_boxes_2d voxelised on (N, N, 1)."""
+    return boxes_indicator(multibox_boxes_2d(N, count, area_fraction, seed), (N, N, 1))
+
+
+def laminate_boxes_2d(fraction: float = 0.5) -> np.ndarray:
+    """The plane laminate of laminate_indicator_2d (axis 0) as one box: phase 2
+    where the x coordinate of the voxel centre is below `fraction`."""
+    return np.array([[0.5 * fraction, 0.5, 0.5, 0.5 * fraction, 0.5, 0.5]])
 
 
 def box_indicator(N: int, volume_fraction: float = 0.2, centre=(0.5, 0.5, 0.5)) -> np.ndarray:

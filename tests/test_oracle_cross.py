@@ -1,0 +1,142 @@
+"""Pins of the TT-cross oracle (Sec. 3, operator setup): maxvol against the
+volume bound of dominant submatrices (brute force over all row subsets),
+cross approximations of tensors with known exact QTT ranks (a separable
+product: rank 1; an exponential: rank 1; a sine: rank 2), and the sampled
+Green operator and box phase indicator against their dense definitions
+(the pointwise samplers are pinned to the dense arrays entry by entry)."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cross as X
+from oracle import ms as MS
+from oracle import tt as T
+from paper_2512_07811_gb300 import inputs as I
+
+
+def test_maxvol_finds_dominant_rows():
+    """Rows scaled by 100 dominate: maxvol returns them, B[rows] = I, |B| <= tol."""
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((20, 4))
+    big = [3, 7, 11, 15]
+    A[big] *= 100.0
+    rows, B = X.maxvol(A)
+    assert sorted(rows) == big
+    np.testing.assert_allclose(B[rows], np.eye(4), atol=1e-12)
+    np.testing.assert_allclose(B, A @ np.linalg.inv(A[rows]), atol=1e-12)
+    assert np.abs(B).max() <= 1.05
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_maxvol_volume_bound_brute_force(seed):
+    """A submatrix with |A A[rows]^-1| <= tol has volume at least
+    max volume / (tol sqrt(r))^r (Goreinov-Tyrtyshnikov): checked against all
+    C(8, 3) row subsets."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((8, 3)) + 1j * rng.standard_normal((8, 3))
+    rows, B = X.maxvol(A)
+    assert np.abs(B).max() <= 1.05 + 1e-12
+    vol = abs(np.linalg.det(A[rows]))
+    best = max(abs(np.linalg.det(A[list(s)])) for s in itertools.combinations(range(8), 3))
+    assert vol * (1.05 * math.sqrt(3)) ** 3 >= best
+    # dominance: no single row swap raises the volume by more than the tolerance
+    for j in range(3):
+        for i in range(8):
+            if i in rows:
+                continue
+            trial = list(rows)
+            trial[j] = i
+            assert abs(np.linalg.det(A[trial])) <= 1.05 * vol * (1 + 1e-12)
+
+
+def test_cross_separable_product_rank_one():
+    rng = np.random.default_rng(1)
+    modes = [3, 4, 2, 5, 3]
+    g = [rng.standard_normal(n) for n in modes]
+
+    def f(idx):
+        return np.prod([g[k][idx[:, k]] for k in range(len(modes))], axis=0)
+
+    cores, info = X.tt_cross(f, modes, 1e-12)
+    full = T.tt_full(cores).reshape(modes)
+    ref = np.einsum("a,b,c,d,e->abcde", *g)
+    assert np.abs(full - ref).max() < 1e-13 * np.abs(ref).max()
+    y, _ = T.tt_round(cores, 1e-12)
+    assert T.tt_ranks(y) == [1] * 6
+
+
+def _bits_value(idx, n):
+    return (idx * (1 << np.arange(n - 1, -1, -1))).sum(axis=1)
+
+
+@pytest.mark.parametrize("n", [10, 14])
+def test_cross_exponential_and_sine_qtt_ranks(n):
+    """exp(-3x) has QTT rank 1 and sin(6 pi x + 0.3) rank 2 (closed forms:
+    exp of a sum of bits is a product; sin(a + b) = sin a cos b + cos a sin b)."""
+    x = np.arange(1 << n) / (1 << n)
+    for fun, rank in [(lambda t: np.exp(-3.0 * t), 1), (lambda t: np.sin(6 * np.pi * t + 0.3), 2)]:
+        cores, info = X.tt_cross(lambda idx: fun(_bits_value(idx, n) / (1 << n)), [2] * n, 1e-12)
+        assert np.abs(T.tt_full(cores).reshape(-1) - fun(x)).max() < 1e-12
+        y, _ = T.tt_round(cores, 1e-12)
+        assert max(T.tt_ranks(y)) == rank
+
+
+@pytest.mark.parametrize("kind,nb,ordering", [("scalar", (3, 3, 0), "interleaved"),
+                                              ("scalar", (2, 3, 1), "grouped"),
+                                              ("elastic", (2, 2, 1), "interleaved")])
+def test_green_sampler_equals_dense_definition(kind, nb, ordering):
+    """Every entry of green_fn equals the dense Green operator in the
+    momentum site order (bits of each dimension reversed)."""
+    shape = tuple(1 << b for b in nb)
+    ind = np.zeros(shape)
+    pb = MS.scalar_problem(ind, 1.0, 10.0) if kind == "scalar" else MS.elastic_problem(ind, 1.0, 1.0, 10.0, 5.0)
+    nc = pb.ncomp
+    G = MS.green_dense(pb).reshape((nc * nc,) + shape)
+    Gs = MS.spatial_to_sites(G, nb, ordering, momentum=True, lead=1)
+    d = sum(nb)
+    idx = np.array(list(itertools.product(range(nc * nc), *[range(2)] * d)))
+    vals = X.green_fn(pb, nb, ordering)(idx)
+    np.testing.assert_array_equal(vals.reshape(Gs.shape), Gs)
+
+
+@pytest.mark.parametrize("nb,ordering", [((4, 3, 0), "interleaved"), ((2, 2, 3), "grouped")])
+def test_boxes_sampler_equals_voxelisation(nb, ordering):
+    shape = tuple(1 << b for b in nb)
+    boxes = np.array([[0.3, 0.6, 0.5, 0.2, 0.15, 0.5], [0.9, 0.1, 0.25, 0.12, 0.3, 0.2]])
+    ref = MS.spatial_to_sites(I.boxes_indicator(boxes, shape), nb, ordering)
+    d = sum(nb)
+    idx = np.array(list(itertools.product(*[range(2)] * d)))
+    vals = X.boxes_fn(boxes, nb, ordering)(idx)
+    np.testing.assert_array_equal(vals.reshape(ref.shape), ref)
+
+
+@pytest.mark.parametrize("kind,nb,ordering", [("scalar", (4, 4, 0), "interleaved"),
+                                              ("scalar", (3, 3, 3), "grouped"),
+                                              ("elastic", (3, 2, 2), "interleaved")])
+def test_cross_green_matches_dense(kind, nb, ordering):
+    shape = tuple(1 << b for b in nb)
+    ind = np.zeros(shape)
+    pb = MS.scalar_problem(ind, 1.0, 10.0) if kind == "scalar" else MS.elastic_problem(ind, 1.0, 1.0, 10.0, 5.0)
+    nc = pb.ncomp
+    Gs = MS.spatial_to_sites(MS.green_dense(pb).reshape((nc * nc,) + shape), nb, ordering, momentum=True, lead=1)
+    cores, info = X.tt_cross(X.green_fn(pb, nb, ordering), [nc * nc] + [2] * sum(nb), 1e-10)
+    full = T.tt_full(cores).reshape(Gs.shape)
+    assert np.linalg.norm(full - Gs) / np.linalg.norm(Gs) < 1e-9
+    # the interpolation needs no more rank than the dense TT-SVD at the same tolerance, up to the kick columns
+    y, _ = T.tt_round(cores, 1e-10)
+    assert max(T.tt_ranks(y)) <= max(T.tt_ranks(T.tt_svd(Gs.astype(np.complex128), 1e-10))) + 2
+
+
+@pytest.mark.parametrize("nb,ordering", [((5, 5, 0), "interleaved"), ((6, 6, 0), "grouped"),
+                                         ((3, 3, 3), "interleaved")])
+def test_cross_boxes_exact(nb, ordering):
+    shape = tuple(1 << b for b in nb)
+    if nb[2] == 0:
+        boxes = I.multibox_boxes_2d(shape[0], count=6, seed=3)
+    else:
+        boxes = np.array([[0.5, 0.5, 0.5, 0.3, 0.2, 0.25]])
+    ref = MS.spatial_to_sites(I.boxes_indicator(boxes, shape), nb, ordering)
+    cores, info = X.tt_cross(X.boxes_fn(boxes, nb, ordering), [2] * sum(nb), 1e-10, init_rank=8)
+    assert np.abs(T.tt_full(cores).reshape(ref.shape) - ref).max() < 1e-10
