@@ -299,6 +299,7 @@ def run_ours(args, rank, world, local_rank):
     ms_part = None
     if not args.no_ms:
         ms_part = ms_laminate(Q, ctx)
+        ms_part["plane"] = ms_plane(Q, ctx)
     return dict(ms=ms, flops=flops, prof=prof, ms_prof=ms_prof, launches=launches, clocks=clk, e2e_ms=e2e_ms,
                 e2e_flops=e2e_flops, h2d=h2d, d2h=d2h, ms64=ms64, flops64=flops64, ms_part=ms_part, batched=batched,
                 polar=polar)
@@ -417,6 +418,37 @@ def ms_laminate(Q, ctx):
         out["speedup_fast_vs_fp64"] = out["fast"]["iters_per_s"] / out["fp64"]["iters_per_s"]
         if out["fast_learned_rank"]["iters_per_s"]:
             out["speedup_fast_learned_vs_fp64"] = out["fast_learned_rank"]["iters_per_s"] / out["fp64"]["iters_per_s"]
+    return out
+
+
+def ms_plane(Q, ctx, N=256):
+    """Moulinec-Suquet iterations on a plane multibox image (N x N x 1: eight
+    square inclusions of random sizes filling 20 % of the plane, contrast 10;
+    a grid one voxel thick along z is the plane problem), load case E = e_x,
+    FP64 at 1e-8 and the fast path at 1e-6, max rank 64; one warm-up solve,
+    then five timed iterations.  The arithmetic and harmonic means of the
+    phase moduli bound k_eff_xx from above and below."""
+    ind = I.multibox_indicator_2d(N, count=8, area_fraction=0.2, seed=5)
+    f = float(ind.mean())
+    out = {"workload": f"{N}x{N}x1 scalar multibox (8 squares, area fraction {f:.3f}), "
+                       f"{2 * int(np.log2(N))} interleaved bit sites + control, contrast 10, max rank 64, "
+                       "E = e_x, 5 iterations; eps 1e-8 (FP64) / 1e-6 (fast)",
+           "k_bounds": [1.0 / ((1 - f) / 1.0 + f / 10.0), (1 - f) * 1.0 + f * 10.0]}
+    C64 = None
+    for name, prec, eps in [("fp64", Q.PREC_F64, 1e-8), ("fast", Q.PREC_F32, 1e-6)]:
+        kw = dict(tol=0.0, max_rank=64, eps=eps, prec=prec, load_mask=1)
+        Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=1, min_iter=1, **kw)
+        C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=5, min_iter=5, **kw)
+        it = rep.iterations[0]
+        out[name] = {"iters_per_s": it / (rep.iterate_ms * 1e-3) if rep.iterate_ms > 0 else None, "eps": eps,
+                     "setup_ms": rep.setup_ms, "k_eff_xx": C[0, 0], "iterations": it,
+                     "max_rank": rep.max_rank_seen}
+        if name == "fp64":
+            C64 = C
+        else:
+            out[name]["rel_dev_from_fp64"] = float(abs(C[0, 0] - C64[0, 0]) / abs(C64[0, 0]))
+    if out["fast"]["iters_per_s"] and out["fp64"]["iters_per_s"]:
+        out["speedup_fast_vs_fp64"] = out["fast"]["iters_per_s"] / out["fp64"]["iters_per_s"]
     return out
 
 

@@ -259,6 +259,58 @@ QTT_API int qtt_mpo_diag(qtt_ctx* ctx, const qtt_tt* x, qtt_mpo** out);
 /* B = A stored in another dtype. */
 QTT_API int qtt_mpo_convert(qtt_ctx* ctx, const qtt_mpo* A, qtt_dtype dtype, qtt_mpo** out);
 
+/* ------------------------------------------------------------ TT-cross */
+/* Functions the TT-cross samples (Sec. 3, operator setup: the discretised
+ * operands are separated into cores by the TT-cross approximation instead of
+ * a TT-SVD of the dense array, so the grid is never stored densely).
+ *  QTT_CROSS_GREEN: the Green operator train of the reference medium, modes
+ *    (ncomp^2, 2, ..., 2): site 0 the component I * ncomp + J, then the
+ *    spatial bits in the momentum convention (every dimension's bits least
+ *    significant first, Sec. 3.2); ncomp 3: xi_I xi_J / (k0 |xi|^2); ncomp 6:
+ *    the isotropic elastic operator of (lam0, mu0) in Voigt form on
+ *    engineering strains; 0 at xi = 0; frequencies xi = k below the Nyquist
+ *    index, else k - N.
+ *  QTT_CROSS_BOXES: the phase indicator of a union of axis-aligned boxes,
+ *    modes (2, ..., 2), position convention (most significant bit first); a
+ *    voxel is in phase 2 (value 1) when, on every axis, the periodic distance
+ *    |((c - cx + 1/2) mod 1) - 1/2| of its centre c = (x + 1/2) / N from some
+ *    box centre is at most that box's half width.
+ * The spatial sites are ordered as in qtt_rve (interleaved level by level,
+ * or grouped by dimension). */
+typedef enum { QTT_CROSS_GREEN = 1, QTT_CROSS_BOXES = 2 } qtt_cross_kind;
+typedef struct {
+  int32_t kind;          /* qtt_cross_kind                                                 */
+  int32_t nbits_dim[3];  /* 2^nbits_dim[a] voxels along x, y, z: 0 to 20 each, 1 to 60 in all */
+  int32_t interleaved;
+  int32_t ncomp;         /* GREEN: 3 or 6                                                  */
+  double k0, lam0, mu0;  /* GREEN: reference conductivity / Lame constants                 */
+  const double* boxes;   /* BOXES: host, nboxes rows (cx, cy, cz, hx, hy, hz)             */
+  int32_t nboxes;
+} qtt_cross_fn;
+
+typedef struct {
+  int32_t half_sweeps;   /* half-sweeps made                                               */
+  int64_t evaluations;   /* function samples taken                                         */
+  double rel_change;     /* ||x_h - x_{h-1}|| / ||x_h|| over the last half-sweep           */
+  int32_t max_rank;      /* largest bond rank before the final rounding                    */
+} qtt_cross_info;
+
+/* TT-cross approximation of the function `fn` (rank-adaptive two-site cross
+ * with maximum-volume index sets, Oseledets & Tyrtyshnikov; Savostyanov &
+ * Oseledets): half-sweeps alternate left to right and right to left; at
+ * every bond the sampled two-site superblock is truncated by SVD at
+ * eps ||S||_F / sqrt(d - 1) (at most max_rank singular vectors, 0 = no cap),
+ * `kick` Gaussian columns are appended so that the index sets keep
+ * exploring, and the maximum-volume rows (tolerance 1.05, at most 100 swaps)
+ * become the next index set.  The sweep stops once the train changes by at
+ * most 10 eps (relative) over a half-sweep, or after max_half_sweeps (at
+ * least 2); the result is then rounded at eps (FP64 SVD rounding).  Every
+ * step runs on the device; complex128 train.  seed: the initial index sets
+ * (8 random points) and the Gaussian columns.  QTT_ERR_ARG for an invalid
+ * description, QTT_ERR_RANK if a superblock's kept basis is rank deficient. */
+QTT_API int tt_cross(qtt_ctx* ctx, const qtt_cross_fn* fn, double eps, int32_t max_rank, int32_t kick,
+                     int32_t max_half_sweeps, uint64_t seed, qtt_tt** out, qtt_cross_info* info);
+
 /* ---------------------------------------------------- homogenisation */
 typedef struct {
   int32_t ncomp;        /* 3: scalar conductivity, 6: elasticity (Voigt 11,22,33,23,13,12) */
@@ -271,6 +323,14 @@ typedef struct {
                          * each, 1 to 27 in all; nbits is then ignored).  A dimension of
                          * 2^0 = 1 voxel has no sites: every field is uniform along it, the
                          * plane problem (plane strain for elasticity) for nbits_dim[2] = 0. */
+  const double* boxes;  /* host; used when indicator is NULL: nboxes rows (cx, cy, cz, hx,
+                         * hy, hz) of axis-aligned boxes in unit-cell coordinates (the
+                         * phase-2 region, see qtt_cross_fn), the phase train then built by
+                         * tt_cross; the grid may then have 0 to 20 bits per dimension and
+                         * 1 to 60 in all                                                   */
+  int32_t nboxes;
+  int32_t op_cross;     /* 1: build the Green operator train by tt_cross; 0: by a dense
+                         * TT-SVD up to 27 bits in all, by tt_cross above               */
 } qtt_rve;
 
 /* Per-bond rank features of one rounding inside ms_homogenize (the rank
@@ -312,6 +372,8 @@ typedef struct {
   int64_t trace_len;       /* rows written to opts->trace                                 */
   int64_t sketch_width_sum;/* sum over roundings and bonds of the sketch ranks used      */
   int32_t fallbacks;       /* sketched roundings redone at the full width                */
+  int32_t green_rank;      /* largest bond rank of the Green operator train              */
+  int32_t phase_rank;      /* largest bond rank of the phase indicator train             */
 } ms_report;
 
 /* Moulinec-Suquet homogenisation in QTT form (Sec. 3.2, Algorithm 2):

@@ -891,6 +891,7 @@ struct Ops {
   qtt_mpo* q[3] = {nullptr, nullptr, nullptr};
   qtt_mpo* qi[3] = {nullptr, nullptr, nullptr};
   qtt_tt* chi = nullptr;     // spatial sites only
+  int green_rank = 0, phase_rank = 0;
   void release() {
     mpo_free(dCa);
     mpo_free(dCb);
@@ -925,22 +926,29 @@ static void rve_bits(const qtt_rve* rve, int nb[3]) {
   for (int a = 0; a < 3; ++a) nb[a] = per_dim ? rve->nbits_dim[a] : rve->nbits;
 }
 
-// 0 to 15 bits per dimension, 1 to 27 in all (the operator setup fills the
-// Green operator densely: ncomp^2 * 2^bits complex doubles)
+// A dense phase image: 0 to 15 bits per dimension, 1 to 27 in all (the
+// indicator is uploaded and compressed by a dense TT-SVD).  A box geometry
+// (indicator NULL): 0 to 20 per dimension, 1 to 60 in all (sampled by
+// TT-cross, nothing stored densely).
 static bool rve_bits_valid(const qtt_rve* rve) {
   int nb[3];
   rve_bits(rve, nb);
   const int tot = nb[0] + nb[1] + nb[2];
+  const bool dense = rve->indicator != nullptr;
+  if (!dense && (rve->nboxes < 1 || !rve->boxes)) return false;
   for (int a = 0; a < 3; ++a)
-    if (nb[a] < 0 || nb[a] > 15) return false;
-  return tot >= 1 && tot <= 27;
+    if (nb[a] < 0 || nb[a] > (dense ? 15 : 20)) return false;
+  return tot >= 1 && tot <= (dense ? 27 : 60);
 }
 
-static SiteMap site_map(const qtt_rve* rve) {
+// Green operator by a dense fill + TT-SVD only while that array stays small
+static bool green_dense_ok(const qtt_rve* rve, int dsp) { return !rve->op_cross && dsp <= 27; }
+
+static SiteMap site_map_bits(const int nb[3], bool interleaved) {
   SiteMap m{};
-  rve_bits(rve, m.nb);
+  for (int a = 0; a < 3; ++a) m.nb[a] = nb[a];
   m.d = 0;
-  if (rve->interleaved) {
+  if (interleaved) {
     const int mx = std::max(m.nb[0], std::max(m.nb[1], m.nb[2]));
     for (int a = 0; a < mx; ++a)
       for (int dim = 0; dim < 3; ++dim)
@@ -958,40 +966,292 @@ static SiteMap site_map(const qtt_rve* rve) {
   return m;
 }
 
+static SiteMap site_map(const qtt_rve* rve) {
+  int nb[3];
+  rve_bits(rve, nb);
+  return site_map_bits(nb, rve->interleaved != 0);
+}
+
+// ------------------------------------------------------------ TT-cross
+// Rank-adaptive two-site TT-cross (Sec. 3 operator setup; Oseledets &
+// Tyrtyshnikov, two-site form of Savostyanov & Oseledets).  Index sets live
+// on the device as byte rows: I[k] holds rI[k] left rows of k site values
+// (sites 0..k-1), J[k] holds rJ[k] right rows of d-k values (sites k..d-1).
+// A forward half-sweep samples at bond k (sites k, k+1) the superblock
+// S = f(I[k], i, j, J[k+2]), keeps the leading left singular vectors whose
+// tail is at most eps ||S|| / sqrt(d-1), appends `kick` Gaussian columns,
+// picks their maximum-volume rows, which give I[k+1] and the interpolation
+// core A A[rows]^-1; at the last bond core d-1 is S[rows, :].  A backward
+// half-sweep does the same on S^H, giving J[k+1], the cores
+// (A A[rows]^-1)^H and at bond 0 core 0 = S[:, rows].
+struct CrossOut {
+  int half_sweeps = 0;
+  int64_t evaluations = 0;
+  double rel_change = 0.0;
+  int max_rank = 1;
+};
+
+static uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int cross_dev(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, double eps, int max_rank, int kick,
+              int max_half_sweeps, uint64_t seed, qtt_tt** out, CrossOut* st) {
+  const int d = (int)modes.size();
+  for (int k = 0; k < d; ++k)
+    if (modes[k] < 1 || modes[k] > 255) return QTT_ERR_ARG;
+  int s = 0;
+  if (d == 1) {
+    qtt_tt* y = tt_alloc(c, 1, modes, std::vector<int>{1, 1}, QTT_C128, &s);
+    if (!y) return s;
+    c->launches++;
+    s = qtt_cross_eval<double>(f, 1, 0, nullptr, 1, nullptr, 1, modes[0], 1, 0, core_ptr<zc>(y, 0), c->stream);
+    if (s) {
+      tt_free(y);
+      return s;
+    }
+    st->evaluations = modes[0];
+    *out = y;
+    return QTT_OK;
+  }
+  // initial right index sets: the suffixes of 8 random points, duplicates removed
+  const int npts = 8;
+  uint64_t rs = seed ^ 0x5DEECE66Dull;
+  std::vector<std::vector<uint8_t>> pts(npts, std::vector<uint8_t>(d));
+  for (auto& p : pts)
+    for (int k = 0; k < d; ++k) p[k] = (uint8_t)(splitmix64(rs) % (uint64_t)modes[k]);
+  std::vector<DBuf> I(d + 1), J(d + 1);
+  std::vector<int> rI(d + 1, 1), rJ(d + 1, 1);
+  for (int k = 1; k < d; ++k) {
+    std::vector<std::vector<uint8_t>> rows;
+    for (auto& p : pts) rows.emplace_back(p.begin() + k, p.end());
+    std::sort(rows.begin(), rows.end());
+    rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+    std::vector<uint8_t> flat;
+    for (auto& r : rows) flat.insert(flat.end(), r.begin(), r.end());
+    TRY(J[k].alloc(c, flat.size()));
+    TRY(upload(c, J[k].p, flat.data(), flat.size()));
+    rJ[k] = (int)rows.size();
+  }
+  DBuf scal, pivb, Zb;
+  TRY(scal.alloc(c, 64));
+  double* dscal = scal.as<double>();
+  int* dint = reinterpret_cast<int*>(dscal + 4);
+  std::vector<DBuf> cores(d);
+  struct Held {
+    qtt_tt* p = nullptr;
+    ~Held() {
+      if (p) tt_free(p);
+    }
+  } held;   // the train of the previous half-sweep
+  qtt_tt*& prev = held.p;
+  uint64_t gauss_stream = 1;
+  const double sq = sqrt((double)(d - 1));
+  int h = 0;
+  double rel = INFINITY;
+  for (h = 1; h <= std::max(2, max_half_sweeps); ++h) {
+    const bool fwd = (h & 1) == 1;
+    for (int step = 0; step < d - 1; ++step) {
+      const int k = fwd ? step : d - 2 - step;
+      const int rl = rI[k], rr = rJ[k + 2], n0 = modes[k], n1 = modes[k + 1];
+      const int64_t rows = (int64_t)rl * n0, cols = (int64_t)n1 * rr;
+      DBuf S;
+      TRY(S.alloc(c, (size_t)rows * cols * sizeof(zc)));
+      c->launches++;
+      TRY(qtt_cross_eval<double>(f, d, k, I[k].as<uint8_t>(), rl, J[k + 2].as<uint8_t>(), rr, n0, n1, fwd ? 0 : 1,
+                                 S.as<zc>(), c->stream));
+      st->evaluations += rows * cols;
+      // basis side: rows of S (forward) or of S^H (backward)
+      const int64_t M = fwd ? rows : cols, Nn = fwd ? cols : rows;
+      c->launches++;
+      TRY(qtt_sumsq<double>(S.as<zc>(), rows * cols, dscal, c->stream));
+      double n2 = 0;
+      TRY(sync_read(c, &n2, dscal, sizeof(double)));
+      int t = 0;
+      DBuf U, sig;
+      int64_t nsv = 0;
+      if (n2 > 0) {
+        const int64_t p = std::min(M, Nn);
+        TRY(U.alloc(c, (size_t)M * p * sizeof(zc)));
+        TRY(sig.alloc(c, (size_t)p * sizeof(double)));
+        TRY(left_svd<double>(c, S.as<zc>(), M, Nn, Nn, U.as<zc>(), sig.as<double>(), &nsv));
+        c->launches++;
+        TRY(qtt_trunc_rank<double>(sig.as<double>(), (int)nsv, eps * sqrt(n2) / sq, max_rank, dint,
+                                   dscal + 1, c->stream));
+        TRY(sync_read(c, &t, dint, sizeof(int)));
+      }
+      // a zero superblock keeps only random directions (exploration)
+      const int tk = (int)std::min<int64_t>(std::max(t + kick, 1), M);
+      DBuf A;
+      TRY(A.alloc(c, (size_t)M * tk * sizeof(zc)));
+      if (t > 0) {
+        c->launches++;
+        TRY(qtt_copy_strided<double>(U.as<zc>(), MIdx{M, 1, nsv, 0}, MIdx{t, 1, 1, 0}, M, t, 0, A.as<zc>(), tk,
+                                     c->stream));
+      }
+      if (tk > t) {
+        const int e = tk - t;
+        TRY(Zb.alloc(c, (size_t)M * e * sizeof(zc)));
+        c->launches += 2;
+        TRY(qtt_fill_gaussian<double>(Zb.as<zc>(), M * e, seed, gauss_stream++, 1.0, c->stream));
+        TRY(qtt_copy_strided<double>(Zb.as<zc>(), MIdx{M, 1, e, 0}, MIdx{e, 1, 1, 0}, M, e, 0, A.as<zc>() + t, tk,
+                                     c->stream));
+      }
+      TRY(pivb.alloc(c, (size_t)tk * sizeof(int)));
+      cudaMemsetAsync(dint + 2, 0, sizeof(int), c->stream);
+      c->launches++;
+      TRY(qtt_maxvol<double>(A.as<zc>(), (int)M, tk, pivb.as<int>(), 1.05, 100, dint + 2, c->stream));
+      int mvst = 0;
+      TRY(sync_read(c, &mvst, dint + 2, sizeof(int)));
+      if (mvst == 1) return QTT_ERR_RANK;
+      if (mvst < 2) return QTT_ERR_CUDA;
+      if (fwd) {
+        cores[k] = std::move(A);
+        DBuf In;
+        TRY(In.alloc(c, (size_t)tk * (k + 1)));
+        c->launches++;
+        TRY(qtt_cross_left_index(I[k].as<uint8_t>(), k, n0, pivb.as<int>(), tk, In.as<uint8_t>(), c->stream));
+        I[k + 1] = std::move(In);
+        rI[k + 1] = tk;
+        if (k == d - 2) {
+          TRY(cores[d - 1].alloc(c, (size_t)tk * cols * sizeof(zc)));
+          c->launches++;
+          TRY(qtt_cross_gather<double>(S.as<zc>(), cols, pivb.as<int>(), tk, cols, 0, cores[d - 1].as<zc>(),
+                                       c->stream));
+        }
+      } else {
+        DBuf Cn;
+        TRY(Cn.alloc(c, (size_t)tk * M * sizeof(zc)));
+        c->launches++;
+        TRY(qtt_copy_strided<double>(A.as<zc>(), MIdx{tk, 1, 1, 0}, MIdx{M, 1, tk, 0}, tk, M, 1, Cn.as<zc>(), M,
+                                     c->stream));
+        cores[k + 1] = std::move(Cn);
+        DBuf Jn;
+        TRY(Jn.alloc(c, (size_t)tk * (d - k - 1)));
+        c->launches++;
+        TRY(qtt_cross_right_index(J[k + 2].as<uint8_t>(), d - k - 2, rr, pivb.as<int>(), tk, Jn.as<uint8_t>(),
+                                  c->stream));
+        J[k + 1] = std::move(Jn);
+        rJ[k + 1] = tk;
+        if (k == 0) {
+          // core 0 (1, n0, tk): S[i, piv[a]] = conj(S^H[piv[a], i])
+          TRY(cores[0].alloc(c, (size_t)rows * tk * sizeof(zc)));
+          c->launches++;
+          TRY(qtt_cross_gather<double>(S.as<zc>(), rows, pivb.as<int>(), tk, rows, 1, cores[0].as<zc>(),
+                                       c->stream));
+        }
+      }
+    }
+    std::vector<int> r(d + 1, 1);
+    for (int k = 1; k < d; ++k) r[k] = fwd ? rI[k] : rJ[k];
+    qtt_tt* y = tt_alloc(c, d, modes, r, QTT_C128, &s);
+    if (!y) return s;
+    for (int k = 0; k < d; ++k)
+      cudaMemcpyAsync(core_ptr<char>(y, k), cores[k].p, (size_t)r[k] * modes[k] * r[k + 1] * sizeof(zc),
+                      cudaMemcpyDeviceToDevice, c->stream);
+    st->max_rank = *std::max_element(r.begin(), r.end());
+    st->half_sweeps = h;
+    if (prev) {
+      qtt_tt* diff = nullptr;
+      double nd = 0, ny = 0;
+      s = add_dev<double>(c, zc(1, 0), y, zc(-1, 0), prev, &diff);
+      if (!s) s = norm_dev<double>(c, diff, &nd);
+      if (diff) tt_free(diff);
+      if (!s) s = norm_dev<double>(c, y, &ny);
+      tt_free(prev);
+      prev = nullptr;
+      if (s) {
+        tt_free(y);
+        return s;
+      }
+      rel = ny > 0 ? nd / ny : 0.0;
+    }
+    prev = y;
+    st->rel_change = rel;
+    if (h >= 2 && rel <= 10.0 * eps) break;
+  }
+  *out = prev;
+  prev = nullptr;
+  return QTT_OK;
+}
+
+// TT-cross, then an FP64 SVD rounding at eps (the interpolation ranks carry
+// the kick columns and some redundancy).
+int cross_rounded(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, double eps, int max_rank, int kick,
+                  int max_half_sweeps, uint64_t seed, qtt_tt** out, CrossOut* st) {
+  qtt_tt* x = nullptr;
+  TRY(cross_dev(c, f, modes, eps, max_rank, kick, max_half_sweeps, seed, &x, st));
+  qtt_round_info ri;
+  int s = round_det<double>(c, x, eps, 0, nullptr, &ri, out);
+  tt_free(x);
+  return s;
+}
+
 int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2, const double* C0, double op_tol,
               double k0, double lam0, double mu0, Ops* ops) {
   const SiteMap sm = site_map(rve);
   const int nc = rve->ncomp, dsp = sm.d, d = dsp + 1;
   const int64_t Nv = (int64_t)1 << dsp;
+  const int cross_rank = 1024, cross_kick = 4, cross_sweeps = 16;
+  CrossFn cf{};
+  cf.m = sm;
+  cf.ncomp = nc;
+  cf.k0 = k0;
+  cf.lam0 = lam0;
+  cf.mu0 = mu0;
+  int s = 0;
   // phase indicator train
-  void *ind = nullptr, *dense = nullptr;
-  TRY(dalloc(c, &ind, Nv * sizeof(double)));
-  int s = upload(c, ind, rve->indicator, Nv * sizeof(double));
-  if (!s) s = dalloc(c, &dense, (size_t)Nv * nc * nc * sizeof(zc));
-  if (s) {
+  if (rve->indicator) {
+    void *ind = nullptr, *dense = nullptr;
+    TRY(dalloc(c, &ind, Nv * sizeof(double)));
+    s = upload(c, ind, rve->indicator, Nv * sizeof(double));
+    if (!s) s = dalloc(c, &dense, (size_t)Nv * sizeof(zc));
+    if (!s) {
+      c->launches++;
+      s = qtt_fill_indicator_sites<double>(reinterpret_cast<double*>(ind), sm, reinterpret_cast<zc*>(dense),
+                                           c->stream);
+    }
+    if (!s)
+      s = tt_svd_dev<double>(c, dsp, std::vector<int>(dsp, 2), reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128,
+                             &ops->chi);
     dfree(c, ind);
-    return s;
-  }
-  c->launches++;
-  s = qtt_fill_indicator_sites<double>(reinterpret_cast<double*>(ind), sm, reinterpret_cast<zc*>(dense), c->stream);
-  if (!s) s = tt_svd_dev<double>(c, dsp, std::vector<int>(dsp, 2), reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128,
-                                 &ops->chi);
-  dfree(c, ind);
-  if (s) {
     dfree(c, dense);
-    return s;
+    if (s) return s;
+  } else {
+    DBuf boxes;
+    TRY(boxes.alloc(c, (size_t)rve->nboxes * 6 * sizeof(double)));
+    TRY(upload(c, boxes.p, rve->boxes, (size_t)rve->nboxes * 6 * sizeof(double)));
+    CrossFn fb = cf;
+    fb.kind = CROSS_BOXES;
+    fb.boxes = boxes.as<double>();
+    fb.nboxes = rve->nboxes;
+    CrossOut co;
+    TRY(cross_rounded(c, fb, std::vector<int>(dsp, 2), op_tol, cross_rank, cross_kick, cross_sweeps, 0x9a5eull,
+                      &ops->chi, &co));
   }
-  // Green operator train
-  c->launches++;
-  s = qtt_fill_green_dense<double>(reinterpret_cast<zc*>(dense), sm, nc, k0, lam0, mu0, c->stream);
+  ops->phase_rank = *std::max_element(ops->chi->r.begin(), ops->chi->r.end());
+  // Green operator train: control core (ncomp^2) first, then the spatial sites
   qtt_tt* g = nullptr;
-  if (!s) {
-    std::vector<int> modes(d, 2);
-    modes[0] = nc * nc;
-    s = tt_svd_dev<double>(c, d, modes, reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128, &g);
+  std::vector<int> gmodes(d, 2);
+  gmodes[0] = nc * nc;
+  if (green_dense_ok(rve, dsp)) {
+    void* dense = nullptr;
+    TRY(dalloc(c, &dense, (size_t)Nv * nc * nc * sizeof(zc)));
+    c->launches++;
+    s = qtt_fill_green_dense<double>(reinterpret_cast<zc*>(dense), sm, nc, k0, lam0, mu0, c->stream);
+    if (!s) s = tt_svd_dev<double>(c, d, gmodes, reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128, &g);
+    dfree(c, dense);
+    if (s) return s;
+  } else {
+    CrossFn fg = cf;
+    fg.kind = CROSS_GREEN;
+    CrossOut co;
+    TRY(cross_rounded(c, fg, gmodes, op_tol, cross_rank, cross_kick, cross_sweeps, 0x6a3eull, &g, &co));
   }
-  dfree(c, dense);
-  if (s) return s;
+  ops->green_rank = *std::max_element(g->r.begin(), g->r.end());
   std::vector<int> mo(d, 2), g1(d + 1, 1);
   mo[0] = nc;
   // Gamma: control core reshaped, spatial cores diagonal
@@ -1377,10 +1637,63 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
 
 }  // namespace
 
+extern "C" int tt_cross(qtt_ctx* c, const qtt_cross_fn* fn, double eps, int32_t max_rank, int32_t kick,
+                        int32_t max_half_sweeps, uint64_t seed, qtt_tt** out, qtt_cross_info* info) {
+  if (!c || !fn || !out || !(eps > 0) || max_rank < 0 || kick < 0 || kick > 64 || max_half_sweeps < 2 ||
+      max_half_sweeps > 64)
+    return QTT_ERR_ARG;
+  int tot = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (fn->nbits_dim[a] < 0 || fn->nbits_dim[a] > 20) return QTT_ERR_ARG;
+    tot += fn->nbits_dim[a];
+  }
+  if (tot < 1 || tot > 60) return QTT_ERR_ARG;
+  CrossFn f{};
+  f.m = site_map_bits(fn->nbits_dim, fn->interleaved != 0);
+  std::vector<int> modes;
+  DBuf boxes;
+  if (fn->kind == QTT_CROSS_GREEN) {
+    if (fn->ncomp == 3) {
+      if (!(fn->k0 > 0)) return QTT_ERR_ARG;
+    } else if (fn->ncomp == 6) {
+      if (!(fn->mu0 > 0) || !(fn->lam0 + 2 * fn->mu0 > 0)) return QTT_ERR_ARG;
+    } else {
+      return QTT_ERR_ARG;
+    }
+    f.kind = CROSS_GREEN;
+    f.ncomp = fn->ncomp;
+    f.k0 = fn->k0;
+    f.lam0 = fn->lam0;
+    f.mu0 = fn->mu0;
+    modes.assign(tot + 1, 2);
+    modes[0] = fn->ncomp * fn->ncomp;
+  } else if (fn->kind == QTT_CROSS_BOXES) {
+    if (!fn->boxes || fn->nboxes < 1) return QTT_ERR_ARG;
+    TRY(boxes.alloc(c, (size_t)fn->nboxes * 6 * sizeof(double)));
+    TRY(upload(c, boxes.p, fn->boxes, (size_t)fn->nboxes * 6 * sizeof(double)));
+    f.kind = CROSS_BOXES;
+    f.boxes = boxes.as<double>();
+    f.nboxes = fn->nboxes;
+    modes.assign(tot, 2);
+  } else {
+    return QTT_ERR_ARG;
+  }
+  CrossOut co;
+  int s = cross_rounded(c, f, modes, eps, max_rank, kick, max_half_sweeps, seed, out, &co);
+  if (info) {
+    info->half_sweeps = co.half_sweeps;
+    info->evaluations = co.evaluations;
+    info->rel_change = co.rel_change;
+    info->max_rank = co.max_rank;
+  }
+  if (!s) s = cudaStreamSynchronize(c->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+  return s;
+}
+
 extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, double tol, int max_rank,
                              const ms_opts* o, double* C_eff, ms_report* rep) {
   if (!c || !rve || !C0 || !o || !C_eff || max_rank < 1) return QTT_ERR_ARG;
-  if ((rve->ncomp != 3 && rve->ncomp != 6) || !rve->indicator || !rve_bits_valid(rve)) return QTT_ERR_ARG;
+  if ((rve->ncomp != 3 && rve->ncomp != 6) || !rve_bits_valid(rve)) return QTT_ERR_ARG;
   if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32) return QTT_ERR_ARG;
   const int nc = rve->ncomp;
   std::vector<double> C1(nc * nc, 0.0), C2(nc * nc, 0.0);
@@ -1429,6 +1742,10 @@ extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, d
   }
   cudaStreamSynchronize(c->stream);
   auto t2 = std::chrono::steady_clock::now();
+  if (rep) {
+    rep->green_rank = O.green_rank;
+    rep->phase_rank = O.phase_rank;
+  }
   O.release();
   if (rep) {
     rep->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();

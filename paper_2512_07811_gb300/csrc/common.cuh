@@ -81,6 +81,48 @@ struct SiteMap {
   signed char pos[64];
 };
 
+// Green operator component (I, J) at the frequency vector xi (Sec. 3.1):
+// scalar conductivity (ncomp 3) xi_I xi_J / (k0 |xi|^2); isotropic elasticity
+// (ncomp 6, Voigt order 11, 22, 33, 23, 13, 12 on engineering strains) the
+// Moulinec-Suquet operator scaled by the Voigt weights of I and J; 0 at xi = 0.
+__device__ __forceinline__ double green_entry(const double xi[3], int I, int J, int ncomp, double k0, double lam0,
+                                              double mu0) {
+  const double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+  if (!(q2 > 0)) return 0.0;
+  if (ncomp == 3) return xi[I] * xi[J] / (k0 * q2);
+  const int vi[6] = {0, 1, 2, 1, 0, 0};
+  const int vj[6] = {0, 1, 2, 2, 2, 1};
+  const double vw[6] = {1, 1, 1, 2, 2, 2};
+  const double coef = (lam0 + mu0) / (mu0 * (lam0 + 2 * mu0));
+  const int i = vi[I], j = vj[I], kk = vi[J], h = vj[J];
+  double t = 0.0;
+  if (kk == i) t += xi[h] * xi[j];
+  if (h == i) t += xi[kk] * xi[j];
+  if (kk == j) t += xi[h] * xi[i];
+  if (h == j) t += xi[kk] * xi[i];
+  double g = t / (4.0 * mu0 * q2) - coef * xi[i] * xi[j] * xi[kk] * xi[h] / (q2 * q2);
+  return g * (vw[I] * vw[J]);
+}
+
+// A function sampled by the TT-cross (Sec. 3, operator setup).
+//  CROSS_GREEN: the Green operator train, site 0 the control index I*ncomp+J
+//    (ncomp^2 values), then the spatial sites of `m` in the momentum
+//    convention (site (dim, pos) holds the bit of weight 2^pos of k_dim);
+//  CROSS_BOXES: the phase indicator of a union of axis-aligned boxes (rows
+//    cx, cy, cz, hx, hy, hz of `boxes`, device memory), spatial sites only,
+//    position convention (site (dim, pos) holds bit nb[dim]-1-pos of x_dim);
+//    a voxel is inside a box when the periodic distance of its centre
+//    (x + 1/2)/N from the box centre is at most the half width on every axis.
+enum { CROSS_GREEN = 1, CROSS_BOXES = 2 };
+struct CrossFn {
+  int kind;
+  SiteMap m;
+  int ncomp;
+  double k0, lam0, mu0;
+  const double* boxes;
+  int nboxes;
+};
+
 // C[b][m][n] = alpha * sum_k opA(A)[b][m][k] * opB(B)[b][k][n] + beta * C[b][m][n]
 // with every one of b, m, n, k a two-level multi-index per operand.
 struct GemmDesc {

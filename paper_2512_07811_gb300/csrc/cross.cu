@@ -1,0 +1,347 @@
+// TT-cross on the device (Sec. 3, operator setup: the cores of the phase and
+// Green operator trains are separated by the TT-cross approximation of
+// Oseledets & Tyrtyshnikov, here in its rank-adaptive two-site form): the
+// superblock sampler, the maximum-volume row selection and the index-set
+// bookkeeping.  The sweep itself is driven from the host (capi.cu).
+#include <limits.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned nblocks(int64_t count) {
+  int64_t b = (count + TPB - 1) / TPB;
+  if (b > (int64_t)1 << 20) b = (int64_t)1 << 20;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+#define TRYK(e)                      \
+  do {                               \
+    int _s = (e);                    \
+    if (_s != QTT_OK) return _s;     \
+  } while (0)
+#define CHECK_LAUNCH() return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA
+
+// Coordinates of one multi-index, accumulated site by site.
+struct CrossAcc {
+  int ctrl;
+  int64_t v[3];
+};
+
+__device__ __forceinline__ void cross_put(const CrossFn& f, int site, int val, CrossAcc& a) {
+  if (f.kind == CROSS_GREEN) {
+    if (site == 0) {
+      a.ctrl = val;
+      return;
+    }
+    const int p = site - 1;
+    a.v[f.m.dim[p]] |= (int64_t)val << f.m.pos[p];
+  } else {
+    const int dm = f.m.dim[site];
+    a.v[dm] |= (int64_t)val << (f.m.nb[dm] - 1 - f.m.pos[site]);
+  }
+}
+
+__device__ double cross_value(const CrossFn& f, const CrossAcc& a) {
+  if (f.kind == CROSS_GREEN) {
+    double xi[3];
+    for (int d = 0; d < 3; ++d) {
+      const int64_t N = (int64_t)1 << f.m.nb[d];
+      xi[d] = (double)(a.v[d] < (N + 1) / 2 ? a.v[d] : a.v[d] - N);
+    }
+    return green_entry(xi, a.ctrl / f.ncomp, a.ctrl % f.ncomp, f.ncomp, f.k0, f.lam0, f.mu0);
+  }
+  double c[3];
+  for (int d = 0; d < 3; ++d) c[d] = ((double)a.v[d] + 0.5) / (double)((int64_t)1 << f.m.nb[d]);
+  for (int b = 0; b < f.nboxes; ++b) {
+    const double* B = f.boxes + 6 * b;
+    bool in = true;
+    for (int d = 0; d < 3 && in; ++d) {
+      // (c - centre + 1/2) mod 1, the result taking the sign of the divisor
+      double t = fmod(c[d] - B[d] + 0.5, 1.0);
+      if (t < 0) t += 1.0;
+      in = fabs(t - 0.5) <= B[3 + d];
+    }
+    if (in) return 1.0;
+  }
+  return 0.0;
+}
+
+// S[(a, i), (j, b)] = f(Il[a], i, j, Jr[b]) for the bond between sites k and
+// k+1: Il holds rl left rows of k site values, Jr rr right rows of d-k-2
+// values.  Row-major (rl n0) x (n1 rr), or its conjugate transpose (herm).
+// With k + 1 == d (a one-site train) n1 = rr = 1 and no second site.
+template <class R>
+__global__ void cross_eval_kernel(CrossFn f, int d, int k, const uint8_t* __restrict__ Il, int rl,
+                                  const uint8_t* __restrict__ Jr, int rr, int n0, int n1, int herm,
+                                  cplx<R>* __restrict__ out) {
+  const int64_t total = (int64_t)rl * n0 * n1 * rr;
+  const int nr = d - k - 2;
+  const int64_t rows = (int64_t)rl * n0, cols = (int64_t)n1 * rr;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = e;
+    const int b = (int)(t % rr);
+    t /= rr;
+    const int j = (int)(t % n1);
+    t /= n1;
+    const int i = (int)(t % n0);
+    const int a = (int)(t / n0);
+    CrossAcc acc{0, {0, 0, 0}};
+    for (int s = 0; s < k; ++s) cross_put(f, s, Il[(int64_t)a * k + s], acc);
+    cross_put(f, k, i, acc);
+    if (k + 1 < d) cross_put(f, k + 1, j, acc);
+    for (int s = 0; s < nr; ++s) cross_put(f, k + 2 + s, Jr[(int64_t)b * nr + s], acc);
+    const cplx<R> v((R)cross_value(f, acc), R(0));
+    const int64_t row = (int64_t)a * n0 + i, col = (int64_t)j * rr + b;
+    if (herm)
+      out[col * rows + row] = v;   // the values are real: conjugation is a no-op
+    else
+      out[row * cols + col] = v;
+  }
+}
+
+// Block-wide argmax of (value, index) pairs: the largest value, ties to the
+// smallest index.  Every thread receives the result.
+__device__ void block_argmax(double v, long long idx, double* sv, long long* si, double* out_v, long long* out_i) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, v, o);
+    const long long oi = __shfl_down_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+  if (lane == 0) {
+    sv[w] = v;
+    si[w] = idx;
+  }
+  __syncthreads();
+  if (w == 0) {
+    v = lane < nw ? sv[lane] : -1.0;
+    idx = lane < nw ? si[lane] : LLONG_MAX;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, v, o);
+      const long long oi = __shfl_down_sync(0xffffffffu, idx, o);
+      if (ov > v || (ov == v && oi < idx)) {
+        v = ov;
+        idx = oi;
+      }
+    }
+    if (lane == 0) {
+      sv[32] = v;
+      si[32] = idx;
+    }
+  }
+  __syncthreads();
+  *out_v = sv[32];
+  *out_i = si[32];
+  __syncthreads();
+}
+
+// Maximum-volume rows of the tall A (m x r, row-major, full column rank), in
+// place, one CTA.  Phase 1: Gauss-Jordan elimination by column operations
+// with partial pivoting over rows, which leaves A A[piv]^-1 (the pivot rows
+// become unit rows).  Phase 2: while the largest |B_ij| of B = A A[piv]^-1
+// exceeds sqrt(tol2), row i replaces piv[j] and B takes the rank-one update
+// B -= B[:, j] (B[i, :] - e_j) / B[i, j] (Sherman-Morrison), at most
+// max_iters times.  status: 1 if a pivot column was zero (rank deficient),
+// else the number of swaps + 2 (so that 0 means "not run").
+template <class R>
+__global__ void __launch_bounds__(1024) maxvol_kernel(cplx<R>* __restrict__ A, int m, int r, int* __restrict__ piv,
+                                                      double tol2, int max_iters, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char mv_smem[];
+  cplx<R>* rowv = reinterpret_cast<cplx<R>*>(mv_smem);
+  cplx<R>* colv = rowv + r;
+  unsigned char* chosen = reinterpret_cast<unsigned char*>(colv + m);
+  __shared__ double sv[33];
+  __shared__ long long si[33];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t mr = (int64_t)m * r;
+  for (int i = tid; i < m; i += nt) chosen[i] = 0;
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    double bv = -1.0;
+    long long bi = LLONG_MAX;
+    for (int i = tid; i < m; i += nt)
+      if (!chosen[i]) {
+        const double v = (double)abs2(A[(int64_t)i * r + j]);
+        if (v > bv) {
+          bv = v;
+          bi = i;
+        }
+      }
+    double best;
+    long long bidx;
+    block_argmax(bv, bi, sv, si, &best, &bidx);
+    if (!(best > 0.0)) {
+      if (tid == 0) *status = 1;
+      return;
+    }
+    const int p = (int)bidx;
+    for (int l = tid; l < r; l += nt) rowv[l] = A[(int64_t)p * r + l];
+    if (tid == 0) {
+      piv[j] = p;
+      chosen[p] = 1;
+    }
+    __syncthreads();
+    const cplx<R> pv = rowv[j];
+    const R den = pv.re * pv.re + pv.im * pv.im;
+    const cplx<R> inv(pv.re / den, -pv.im / den);
+    for (int i = tid; i < m; i += nt) {
+      const cplx<R> x = i == p ? cplx<R>(1, 0) : A[(int64_t)i * r + j] * inv;
+      colv[i] = x;
+      A[(int64_t)i * r + j] = x;
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < mr; e += nt) {
+      const int i = (int)(e / r), l = (int)(e - (int64_t)i * r);
+      if (l == j) continue;
+      if (i == p) {
+        A[e] = cplx<R>(0, 0);
+      } else {
+        cplx<R> x = A[e];
+        cfma(x, -rowv[l], colv[i]);
+        A[e] = x;
+      }
+    }
+    __syncthreads();
+  }
+  int swaps = 0;
+  for (int it = 0; it < max_iters; ++it) {
+    double bv = -1.0;
+    long long bi = LLONG_MAX;
+    for (int64_t e = tid; e < mr; e += nt) {
+      const double v = (double)abs2(A[e]);
+      if (v > bv) {
+        bv = v;
+        bi = e;
+      }
+    }
+    double best;
+    long long bidx;
+    block_argmax(bv, bi, sv, si, &best, &bidx);
+    if (!(best > tol2)) break;
+    const int i = (int)(bidx / r), j = (int)(bidx - (long long)i * r);
+    for (int l = tid; l < r; l += nt) {
+      cplx<R> x = A[(int64_t)i * r + l];
+      if (l == j) x.re -= R(1);
+      rowv[l] = x;
+    }
+    for (int q = tid; q < m; q += nt) colv[q] = A[(int64_t)q * r + j];
+    __syncthreads();
+    const cplx<R> pv = colv[i];
+    const R den = pv.re * pv.re + pv.im * pv.im;
+    const cplx<R> inv(pv.re / den, -pv.im / den);
+    for (int64_t e = tid; e < mr; e += nt) {
+      const int q = (int)(e / r), l = (int)(e - (int64_t)q * r);
+      cplx<R> x = A[e];
+      cfma(x, -(colv[q] * inv), rowv[l]);
+      A[e] = x;
+    }
+    if (tid == 0) piv[j] = i;
+    ++swaps;
+    __syncthreads();
+  }
+  if (tid == 0) *status = 2 + swaps;
+}
+
+// New left rows: row a extends Iprev[piv[a] / n0] (k values) by piv[a] % n0.
+__global__ void cross_left_index_kernel(const uint8_t* __restrict__ Iprev, int k, int n0, const int* __restrict__ piv,
+                                        int t, uint8_t* __restrict__ Inew) {
+  const int w = k + 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)t * w;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e / w), s = (int)(e - (int64_t)a * w);
+    const int p = piv[a];
+    Inew[e] = s < k ? Iprev[(int64_t)(p / n0) * k + s] : (uint8_t)(p % n0);
+  }
+}
+
+// New right rows: row a is piv[a] / rr followed by Jnext[piv[a] % rr] (nr values).
+__global__ void cross_right_index_kernel(const uint8_t* __restrict__ Jnext, int nr, int rr,
+                                         const int* __restrict__ piv, int t, uint8_t* __restrict__ Jnew) {
+  const int w = nr + 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)t * w;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e / w), s = (int)(e - (int64_t)a * w);
+    const int c = piv[a];
+    Jnew[e] = s == 0 ? (uint8_t)(c / rr) : Jnext[(int64_t)(c % rr) * nr + s - 1];
+  }
+}
+
+// Rows piv of S (ld columns, len copied): out[a, c] = S[piv[a], c], or the
+// conjugate transpose out[c, a] = conj(S[piv[a], c]).
+template <class R>
+__global__ void cross_gather_kernel(const cplx<R>* __restrict__ S, int64_t ld, const int* __restrict__ piv, int t,
+                                    int64_t len, int trans, cplx<R>* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)t * len;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e / len);
+    const int64_t c = e - (int64_t)a * len;
+    const cplx<R> v = S[(int64_t)piv[a] * ld + c];
+    if (trans)
+      out[c * t + a] = conjg(v);
+    else
+      out[e] = v;
+  }
+}
+
+}  // namespace
+
+template <class R>
+int qtt_cross_eval(const CrossFn& f, int d, int k, const uint8_t* Il, int rl, const uint8_t* Jr, int rr, int n0,
+                   int n1, int herm, cplx<R>* out, cudaStream_t s) {
+  const int64_t total = (int64_t)rl * n0 * n1 * rr;
+  if (total <= 0) return QTT_OK;
+  cross_eval_kernel<R><<<nblocks(total), TPB, 0, s>>>(f, d, k, Il, rl, Jr, rr, n0, n1, herm, out);
+  CHECK_LAUNCH();
+}
+
+template <class R>
+size_t qtt_maxvol_smem(int m, int r) {
+  return (size_t)(m + r) * sizeof(cplx<R>) + (size_t)m + 16;
+}
+
+template <class R>
+int qtt_maxvol(cplx<R>* A, int m, int r, int* piv, double tol, int max_iters, int* status, cudaStream_t s) {
+  if (r < 1 || m < r) return QTT_ERR_ARG;
+  const size_t smem = qtt_maxvol_smem<R>(m, r);
+  if (smem > 200 * 1024) return QTT_ERR_UNSUPPORTED;
+  if (smem > 48 * 1024) TRYK(qtt_allow_max_smem((const void*)maxvol_kernel<R>));
+  maxvol_kernel<R><<<1, 1024, smem, s>>>(A, m, r, piv, tol * tol, max_iters, status);
+  CHECK_LAUNCH();
+}
+
+int qtt_cross_left_index(const uint8_t* Iprev, int k, int n0, const int* piv, int t, uint8_t* Inew, cudaStream_t s) {
+  const int64_t total = (int64_t)t * (k + 1);
+  if (total <= 0) return QTT_OK;
+  cross_left_index_kernel<<<nblocks(total), TPB, 0, s>>>(Iprev, k, n0, piv, t, Inew);
+  CHECK_LAUNCH();
+}
+
+int qtt_cross_right_index(const uint8_t* Jnext, int nr, int rr, const int* piv, int t, uint8_t* Jnew, cudaStream_t s) {
+  const int64_t total = (int64_t)t * (nr + 1);
+  if (total <= 0) return QTT_OK;
+  cross_right_index_kernel<<<nblocks(total), TPB, 0, s>>>(Jnext, nr, rr, piv, t, Jnew);
+  CHECK_LAUNCH();
+}
+
+template <class R>
+int qtt_cross_gather(const cplx<R>* S, int64_t ld, const int* piv, int t, int64_t len, int trans, cplx<R>* out,
+                     cudaStream_t s) {
+  const int64_t total = (int64_t)t * len;
+  if (total <= 0) return QTT_OK;
+  cross_gather_kernel<R><<<nblocks(total), TPB, 0, s>>>(S, ld, piv, t, len, trans, out);
+  CHECK_LAUNCH();
+}
+
+template int qtt_cross_eval<double>(const CrossFn&, int, int, const uint8_t*, int, const uint8_t*, int, int, int, int,
+                                    zc*, cudaStream_t);
+template size_t qtt_maxvol_smem<double>(int, int);
+template int qtt_maxvol<double>(zc*, int, int, int*, double, int, int*, cudaStream_t);
+template int qtt_cross_gather<double>(const zc*, int64_t, const int*, int, int64_t, int, zc*, cudaStream_t);

@@ -196,9 +196,6 @@ template <class R>
 __global__ void green_dense_kernel(cplx<R>* out, SiteMap m, int ncomp, double k0, double lam0, double mu0) {
   const int d = m.d;
   const int64_t total = (int64_t)1 << d;
-  const int vi[6] = {0, 1, 2, 1, 0, 0};
-  const int vj[6] = {0, 1, 2, 2, 2, 1};
-  const double vw[6] = {1, 1, 1, 2, 2, 2};
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
        s += (int64_t)gridDim.x * blockDim.x) {
     int64_t k[3] = {0, 0, 0};
@@ -211,31 +208,9 @@ __global__ void green_dense_kernel(cplx<R>* out, SiteMap m, int ncomp, double k0
       const int64_t N = (int64_t)1 << m.nb[a];
       xi[a] = (double)(k[a] < (N + 1) / 2 ? k[a] : k[a] - N);
     }
-    double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
-    if (ncomp == 3) {
-      for (int I = 0; I < 3; ++I)
-        for (int J = 0; J < 3; ++J) {
-          double g = q2 > 0 ? xi[I] * xi[J] / (k0 * q2) : 0.0;
-          out[(int64_t)(I * 3 + J) * total + s] = cplx<R>((R)g, R(0));
-        }
-    } else {
-      double coef = (lam0 + mu0) / (mu0 * (lam0 + 2 * mu0));
-      for (int I = 0; I < 6; ++I)
-        for (int J = 0; J < 6; ++J) {
-          double g = 0.0;
-          if (q2 > 0) {
-            int i = vi[I], j = vj[I], kk = vi[J], h = vj[J];
-            double t = 0.0;
-            if (kk == i) t += xi[h] * xi[j];
-            if (h == i) t += xi[kk] * xi[j];
-            if (kk == j) t += xi[h] * xi[i];
-            if (h == j) t += xi[kk] * xi[i];
-            g = t / (4.0 * mu0 * q2) - coef * xi[i] * xi[j] * xi[kk] * xi[h] / (q2 * q2);
-            g *= vw[I] * vw[J];
-          }
-          out[(int64_t)(I * 6 + J) * total + s] = cplx<R>((R)g, R(0));
-        }
-    }
+    for (int I = 0; I < ncomp; ++I)
+      for (int J = 0; J < ncomp; ++J)
+        out[(int64_t)(I * ncomp + J) * total + s] = cplx<R>((R)green_entry(xi, I, J, ncomp, k0, lam0, mu0), R(0));
   }
 }
 

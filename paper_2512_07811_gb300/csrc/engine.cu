@@ -342,33 +342,6 @@ static int dbg_finite(qtt_ctx* c, const cplx<R>* p, int64_t count, const char* t
   return QTT_OK;
 }
 
-// RAII device buffer on the context stream
-struct DBuf {
-  qtt_ctx* c = nullptr;
-  void* p = nullptr;
-  DBuf() {}
-  DBuf(const DBuf&) = delete;
-  DBuf& operator=(const DBuf&) = delete;
-  DBuf(DBuf&& o) noexcept : c(o.c), p(o.p) { o.p = nullptr; }
-  DBuf& operator=(DBuf&& o) noexcept {
-    if (this != &o) {
-      dfree(c, p);
-      c = o.c;
-      p = o.p;
-      o.p = nullptr;
-    }
-    return *this;
-  }
-  ~DBuf() { dfree(c, p); }
-  int alloc(qtt_ctx* ctx, size_t bytes) {
-    dfree(c, p);
-    c = ctx;
-    return dalloc(ctx, &p, bytes);
-  }
-  template <class T>
-  T* as() const { return reinterpret_cast<T*>(p); }
-};
-
 // model flops of a complex Householder QR of an m x n panel (R only, or R and Q)
 static double qr_flops(double m, double n, bool with_q) {
   double k = m < n ? m : n;
@@ -1253,6 +1226,7 @@ int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* 
 }
 
 template int tt_svd_dev<double>(qtt_ctx*, int, const std::vector<int>&, const zc*, double, int, qtt_dtype, qtt_tt**);
+template int left_svd<double>(qtt_ctx*, const zc*, int64_t, int64_t, int64_t, zc*, double*, int64_t*);
 
 // ----------------------------------------------------------- inner product
 template <class R>

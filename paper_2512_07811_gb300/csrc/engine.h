@@ -109,6 +109,40 @@ int dot_dev(qtt_ctx* c, const qtt_tt* x, const qtt_tt* y, double out[2]);
 template <class R>
 int norm_dev(qtt_ctx* c, const qtt_tt* x, double* out);
 
+// RAII device buffer on the context stream
+struct DBuf {
+  qtt_ctx* c = nullptr;
+  void* p = nullptr;
+  DBuf() {}
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : c(o.c), p(o.p) { o.p = nullptr; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      dfree(c, p);
+      c = o.c;
+      p = o.p;
+      o.p = nullptr;
+    }
+    return *this;
+  }
+  ~DBuf() { dfree(c, p); }
+  int alloc(qtt_ctx* ctx, size_t bytes) {
+    dfree(c, p);
+    c = ctx;
+    return dalloc(ctx, &p, bytes);
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Left singular vectors (rows x min(rows, cols), row-major, by decreasing
+// singular value) and singular values of the row-major rows x cols C
+// (leading dimension ld); *nsv = min(rows, cols).
+template <class R>
+int left_svd(qtt_ctx* c, const cplx<R>* Cm, int64_t rows, int64_t cols, int64_t ld, cplx<R>* U, R* sigma,
+             int64_t* nsv);
+
 template <class T>
 inline T* core_ptr(const qtt_tt* x, int k) {
   return reinterpret_cast<T*>(static_cast<char*>(x->data) + x->off[k]);

@@ -128,3 +128,17 @@ template <class R>
 int qtt_herm_shift(const cplx<R>* H, int64_t q, double shift, cplx<R>* out, cudaStream_t s);
 template <class R>
 int qtt_half_identity_plus(cplx<R>* S, int64_t q, double* tr, cudaStream_t s);
+
+// TT-cross (cross.cu): superblock sampler, maximum-volume rows, index sets
+template <class R>
+int qtt_cross_eval(const CrossFn& f, int d, int k, const uint8_t* Il, int rl, const uint8_t* Jr, int rr, int n0,
+                   int n1, int herm, cplx<R>* out, cudaStream_t s);
+template <class R>
+size_t qtt_maxvol_smem(int m, int r);
+template <class R>
+int qtt_maxvol(cplx<R>* A, int m, int r, int* piv, double tol, int max_iters, int* status, cudaStream_t s);
+int qtt_cross_left_index(const uint8_t* Iprev, int k, int n0, const int* piv, int t, uint8_t* Inew, cudaStream_t s);
+int qtt_cross_right_index(const uint8_t* Jnext, int nr, int rr, const int* piv, int t, uint8_t* Jnew, cudaStream_t s);
+template <class R>
+int qtt_cross_gather(const cplx<R>* S, int64_t ld, const int* piv, int t, int64_t len, int trans, cplx<R>* out,
+                     cudaStream_t s);

@@ -53,7 +53,37 @@ class RVE(C.Structure):
     _fields_ = [("ncomp", C.c_int32), ("nbits", C.c_int32), ("indicator", C.POINTER(C.c_double)),
                 ("k1", C.c_double), ("k2", C.c_double), ("lam1", C.c_double), ("mu1", C.c_double),
                 ("lam2", C.c_double), ("mu2", C.c_double), ("interleaved", C.c_int32),
-                ("nbits_dim", C.c_int32 * 3)]
+                ("nbits_dim", C.c_int32 * 3), ("boxes", C.POINTER(C.c_double)), ("nboxes", C.c_int32),
+                ("op_cross", C.c_int32)]
+
+
+class CrossFn(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nbits_dim", C.c_int32 * 3), ("interleaved", C.c_int32),
+                ("ncomp", C.c_int32), ("k0", C.c_double), ("lam0", C.c_double), ("mu0", C.c_double),
+                ("boxes", C.POINTER(C.c_double)), ("nboxes", C.c_int32)]
+
+
+class CrossInfo(C.Structure):
+    _fields_ = [("half_sweeps", C.c_int32), ("evaluations", C.c_int64), ("rel_change", C.c_double),
+                ("max_rank", C.c_int32)]
+
+
+CROSS_GREEN, CROSS_BOXES = 1, 2
+
+
+class Boxes:
+    """A phase geometry without a dense image: a union of axis-aligned boxes
+    (rows cx, cy, cz, hx, hy, hz in unit-cell coordinates, periodic) on a grid
+    of `shape` = (Nx, Ny, Nz) voxels (powers of two).  The library samples it
+    by TT-cross, so the grid may go up to 2^20 voxels per side."""
+
+    def __init__(self, boxes, shape):
+        self.boxes = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 6))
+        self.shape = tuple(int(n) for n in shape)
+        nb = [int(round(np.log2(n))) for n in self.shape]
+        if len(nb) != 3 or any((1 << b) != n for b, n in zip(nb, self.shape)):
+            raise ValueError("grid sizes must be powers of two, got %s" % (self.shape,))
+        self.nbits = nb
 
 
 def _grid_bits(ind):
@@ -78,7 +108,7 @@ class MSReport(C.Structure):
     _fields_ = [("iterations", C.c_int32 * 6), ("residual", C.c_double * 6), ("sigma_imag_max", C.c_double),
                 ("max_rank_seen", C.c_int32), ("setup_ms", C.c_double), ("iterate_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("trace_len", C.c_int64), ("sketch_width_sum", C.c_int64),
-                ("fallbacks", C.c_int32)]
+                ("fallbacks", C.c_int32), ("green_rank", C.c_int32), ("phase_rank", C.c_int32)]
 
 
 MLP_FEATURES = 10
@@ -146,6 +176,8 @@ _sig("qtt_mlp_get_params", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64])
 _sig("qtt_mlp_forward", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_float)])
 _sig("qtt_mlp_train_step", C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64, C.c_float,
                                      C.c_float, C.POINTER(C.c_double), C.POINTER(C.c_float)])
+_sig("tt_cross", C.c_int, [_P, C.POINTER(CrossFn), C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+                          C.POINTER(_P), C.POINTER(CrossInfo)])
 _sig("ms_homogenize", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
                                 C.POINTER(MSOpts), C.POINTER(C.c_double), C.POINTER(MSReport)])
 
@@ -155,7 +187,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_polar", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_norm",
-            "tt_from_dense", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
+            "tt_from_dense", "tt_cross", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
             "ms_homogenize_batch", "qtt_cgemm", "qtt_cgemm_noalloc",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
             "qtt_mlp_get_params", "qtt_mlp_forward", "qtt_mlp_train_step"]
@@ -367,6 +399,31 @@ def tt_round_polar(ctx: Context, x: TT, eps: float, prec=None):
     return TT(ctx, h), info
 
 
+def tt_cross(ctx: Context, kind: str, nbits, eps: float, interleaved: bool = True, ncomp: int = 3,
+             k0: float = 1.0, lam0: float = 0.0, mu0: float = 0.0, boxes=None, max_rank: int = 0, kick: int = 4,
+             max_half_sweeps: int = 16, seed: int = 1):
+    """TT-cross of the Green operator train (kind "green": modes (ncomp^2,
+    2, ...), momentum convention) or of a box geometry's phase indicator
+    (kind "boxes": modes (2, ...), position convention) on a grid of
+    2^nbits[a] voxels per dimension.  Returns (TT, CrossInfo)."""
+    f = CrossFn()
+    f.kind = CROSS_GREEN if kind == "green" else CROSS_BOXES
+    for a in range(3):
+        f.nbits_dim[a] = int(nbits[a])
+    f.interleaved = 1 if interleaved else 0
+    f.ncomp, f.k0, f.lam0, f.mu0 = int(ncomp), float(k0), float(lam0), float(mu0)
+    keep = None
+    if boxes is not None:
+        keep = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 6))
+        f.boxes = keep.ctypes.data_as(C.POINTER(C.c_double))
+        f.nboxes = keep.shape[0]
+    h = _P()
+    info = CrossInfo()
+    _check(_lib.tt_cross(ctx.h, C.byref(f), float(eps), int(max_rank), int(kick), int(max_half_sweeps), int(seed),
+                         C.byref(h), C.byref(info)), "tt_cross")
+    return TT(ctx, h), info
+
+
 def tt_round_batch(ctx: Context, xs, eps: float, max_rank: int = 0, prec=None):
     """Round trains of one shape together; returns (list of TT, list of RoundInfo)."""
     xs = list(xs)
@@ -507,21 +564,30 @@ class MLP:
         return (loss.value, g) if want_grads else loss.value
 
 
-def _rve(ind, kind, moduli, interleaved):
-    ind = np.ascontiguousarray(ind, dtype=np.float64)
-    nb = _grid_bits(ind)
+def _rve(ind, kind, moduli, interleaved, op_cross=False):
+    """qtt_rve for a dense phase image (Nx, Ny, Nz) or a Boxes geometry;
+    returns (rve, arrays kept alive for the call)."""
     rve = RVE()
+    if isinstance(ind, Boxes):
+        nb = ind.nbits
+        keep = ind.boxes
+        rve.boxes = keep.ctypes.data_as(C.POINTER(C.c_double))
+        rve.nboxes = keep.shape[0]
+    else:
+        keep = np.ascontiguousarray(ind, dtype=np.float64)
+        nb = _grid_bits(keep)
+        rve.indicator = keep.ctypes.data_as(C.POINTER(C.c_double))
     rve.nbits = max(nb)
     rve.nbits_dim[0], rve.nbits_dim[1], rve.nbits_dim[2] = nb
-    rve.indicator = ind.ctypes.data_as(C.POINTER(C.c_double))
     rve.interleaved = 1 if interleaved else 0
+    rve.op_cross = 1 if op_cross else 0
     if kind == "scalar":
         rve.ncomp = 3
         rve.k1, rve.k2 = map(float, moduli)
     else:
         rve.ncomp = 6
         rve.lam1, rve.mu1, rve.lam2, rve.mu2 = map(float, moduli)
-    return rve, ind
+    return rve, keep
 
 
 def ms_homogenize_batch(ctx: Context, problems, tol: float, max_rank: int, workers: int = 8, eps: float = 1e-6,
@@ -561,24 +627,16 @@ def ms_homogenize_batch(ctx: Context, problems, tol: float, max_rank: int, worke
 def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, tol: float, max_rank: int,
                   eps: float = 1e-6, op_tol: float = 1e-10, prec: int = PREC_F64, max_iter: int = 100,
                   oversample: int = 8, load_mask: int | None = None, interleaved: bool = True,
-                  min_iter: int = 1, seed: int = 12345, predictor: "MLP | None" = None, trace_cap: int = 0):
+                  min_iter: int = 1, seed: int = 12345, predictor: "MLP | None" = None, trace_cap: int = 0,
+                  op_cross: bool = False):
     """Effective tensor of a two-phase RVE (phase 2 where indicator == 1).
 
     kind "scalar": moduli = (k1, k2), C0 = 3x3; kind "elastic": moduli =
-    (lam1, mu1, lam2, mu2), C0 = Voigt 6x6.  Returns (C_eff, report)."""
-    ind = np.ascontiguousarray(indicator, dtype=np.float64)
-    nb = _grid_bits(ind)
-    rve = RVE()
-    rve.nbits = max(nb)
-    rve.nbits_dim[0], rve.nbits_dim[1], rve.nbits_dim[2] = nb
-    rve.indicator = ind.ctypes.data_as(C.POINTER(C.c_double))
-    rve.interleaved = 1 if interleaved else 0
-    if kind == "scalar":
-        rve.ncomp = 3
-        rve.k1, rve.k2 = map(float, moduli)
-    else:
-        rve.ncomp = 6
-        rve.lam1, rve.mu1, rve.lam2, rve.mu2 = map(float, moduli)
+    (lam1, mu1, lam2, mu2), C0 = Voigt 6x6.  `indicator` is a dense
+    (Nx, Ny, Nz) image or a Boxes geometry (phase train by TT-cross);
+    op_cross builds the Green operator train by TT-cross at any size (it is
+    always so above 2^27 voxels).  Returns (C_eff, report)."""
+    rve, keep = _rve(indicator, kind, moduli, interleaved, op_cross)
     nc = rve.ncomp
     C0a = np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(nc, nc))
     o = MSOpts()
