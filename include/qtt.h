@@ -306,7 +306,9 @@ typedef struct {
  * most 10 eps (relative) over a half-sweep, or after max_half_sweeps (at
  * least 2); the result is then rounded at eps (FP64 SVD rounding).  Every
  * step runs on the device; complex128 train.  seed: the initial index sets
- * (8 random points) and the Gaussian columns.  QTT_ERR_ARG for an invalid
+ * (8 random points, plus the voxel of every box centre for a box geometry)
+ * and the Gaussian columns.  Inside ms_homogenize: kick 4 for the Green
+ * operator, 8 for a box geometry, at most 24 half-sweeps.  QTT_ERR_ARG for an invalid
  * description, QTT_ERR_RANK if a superblock's kept basis is rank deficient. */
 QTT_API int tt_cross(qtt_ctx* ctx, const qtt_cross_fn* fn, double eps, int32_t max_rank, int32_t kick,
                      int32_t max_half_sweeps, uint64_t seed, qtt_tt** out, qtt_cross_info* info);

@@ -28,7 +28,9 @@ of sampled two-site blocks:
   (relative, in the Frobenius norm) from one half-sweep to the next (two
   approximations that each meet the eps truncation rule differ by a few eps),
   or a sweep limit is met; the start is a right index set drawn from
-  `init_rank` random points.
+  `init_rank` random points and any given `init_points` (for a box geometry
+  the voxels holding the box centres, box_centre_points: points inside the
+  phase-2 region, which random points may all miss).
 
 maxvol (Goreinov, Oseledets, Savostyanov et al. 2010): start from the rows of
 Gaussian elimination with partial pivoting, then, while some entry of
@@ -90,7 +92,7 @@ def _kept(S, eps, d, max_rank, kick, rng, right: bool):
 
 
 def tt_cross(f, modes, eps: float, max_rank: int | None = None, kick: int = 2, max_half_sweeps: int = 12,
-             init_rank: int = 2, seed: int = 0):
+             init_rank: int = 2, seed: int = 0, init_points=None):
     """TT-cross approximation of the tensor with entries f(idx) (idx an
     integer array (M, d) of multi-indices, f returning M values) and mode
     sizes `modes`.  Returns (cores, info), info = dict(half_sweeps,
@@ -102,6 +104,8 @@ def tt_cross(f, modes, eps: float, max_rank: int | None = None, kick: int = 2, m
         return [np.asarray(f(idx), dtype=np.complex128).reshape(1, modes[0], 1)], \
             dict(half_sweeps=0, evaluations=modes[0], rel_change=0.0, ranks=[1, 1])
     pts = np.stack([rng.integers(0, n, size=init_rank) for n in modes], axis=1)
+    if init_points is not None:
+        pts = np.concatenate([pts, np.asarray(init_points, dtype=pts.dtype).reshape(-1, d)], axis=0)
     I = [np.zeros((1, 0), dtype=np.int64) for _ in range(d + 1)]
     J = [np.zeros((1, 0), dtype=np.int64) for _ in range(d + 1)]
     for k in range(1, d):
@@ -176,6 +180,19 @@ def green_fn(pb: MS.Problem, nb, ordering: str = "interleaved"):
         c = idx[:, 0]
         return G[c // nc, c % nc, np.arange(idx.shape[0])]
     return f
+
+
+def box_centre_points(boxes, nb, ordering: str = "interleaved") -> np.ndarray:
+    """Site values (position convention) of the voxel holding each box centre."""
+    boxes = np.asarray(boxes, dtype=np.float64).reshape(-1, 6)
+    pts = np.zeros((boxes.shape[0], sum(nb)), dtype=np.int64)
+    for i, b in enumerate(boxes):
+        for dim in range(3):
+            N = 1 << nb[dim]
+            x = min(int((b[dim] - math.floor(b[dim])) * N), N - 1)
+            for a, s in enumerate(MS.dim_positions(nb, ordering, dim)):
+                pts[i, s] = (x >> (nb[dim] - 1 - a)) & 1
+    return pts
 
 
 def boxes_fn(boxes, nb, ordering: str = "interleaved"):

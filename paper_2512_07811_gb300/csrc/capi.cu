@@ -998,8 +998,27 @@ static uint64_t splitmix64(uint64_t& s) {
   return z ^ (z >> 31);
 }
 
+// Site values (position convention) of the voxel holding each box centre:
+// starting points inside the phase-2 region, which random points may miss.
+static std::vector<std::vector<uint8_t>> box_seeds(const SiteMap& m, const double* boxes, int nboxes) {
+  std::vector<std::vector<uint8_t>> out;
+  for (int b = 0; b < nboxes; ++b) {
+    int64_t x[3];
+    for (int a = 0; a < 3; ++a) {
+      const int64_t N = (int64_t)1 << m.nb[a];
+      double cf = boxes[6 * b + a] - floor(boxes[6 * b + a]);
+      x[a] = std::min<int64_t>((int64_t)(cf * (double)N), N - 1);
+    }
+    std::vector<uint8_t> p(m.d);
+    for (int q = 0; q < m.d; ++q) p[q] = (uint8_t)((x[m.dim[q]] >> (m.nb[m.dim[q]] - 1 - m.pos[q])) & 1);
+    out.push_back(p);
+  }
+  return out;
+}
+
 int cross_dev(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, double eps, int max_rank, int kick,
-              int max_half_sweeps, uint64_t seed, qtt_tt** out, CrossOut* st) {
+              int max_half_sweeps, uint64_t seed, const std::vector<std::vector<uint8_t>>& seeds, qtt_tt** out,
+              CrossOut* st) {
   const int d = (int)modes.size();
   for (int k = 0; k < d; ++k)
     if (modes[k] < 1 || modes[k] > 255) return QTT_ERR_ARG;
@@ -1017,12 +1036,15 @@ int cross_dev(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, doubl
     *out = y;
     return QTT_OK;
   }
-  // initial right index sets: the suffixes of 8 random points, duplicates removed
+  // initial right index sets: the suffixes of 8 random points and of the
+  // caller's seed points, duplicates removed
   const int npts = 8;
   uint64_t rs = seed ^ 0x5DEECE66Dull;
   std::vector<std::vector<uint8_t>> pts(npts, std::vector<uint8_t>(d));
   for (auto& p : pts)
     for (int k = 0; k < d; ++k) p[k] = (uint8_t)(splitmix64(rs) % (uint64_t)modes[k]);
+  for (const auto& p : seeds)
+    if ((int)p.size() == d) pts.push_back(p);
   std::vector<DBuf> I(d + 1), J(d + 1);
   std::vector<int> rI(d + 1, 1), rJ(d + 1, 1);
   for (int k = 1; k < d; ++k) {
@@ -1181,9 +1203,10 @@ int cross_dev(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, doubl
 // TT-cross, then an FP64 SVD rounding at eps (the interpolation ranks carry
 // the kick columns and some redundancy).
 int cross_rounded(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, double eps, int max_rank, int kick,
-                  int max_half_sweeps, uint64_t seed, qtt_tt** out, CrossOut* st) {
+                  int max_half_sweeps, uint64_t seed, const std::vector<std::vector<uint8_t>>& seeds, qtt_tt** out,
+                  CrossOut* st) {
   qtt_tt* x = nullptr;
-  TRY(cross_dev(c, f, modes, eps, max_rank, kick, max_half_sweeps, seed, &x, st));
+  TRY(cross_dev(c, f, modes, eps, max_rank, kick, max_half_sweeps, seed, seeds, &x, st));
   qtt_round_info ri;
   int s = round_det<double>(c, x, eps, 0, nullptr, &ri, out);
   tt_free(x);
@@ -1195,7 +1218,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
   const SiteMap sm = site_map(rve);
   const int nc = rve->ncomp, dsp = sm.d, d = dsp + 1;
   const int64_t Nv = (int64_t)1 << dsp;
-  const int cross_rank = 1024, cross_kick = 4, cross_sweeps = 16;
+  const int cross_rank = 1024, cross_kick = 4, cross_sweeps = 24;
   CrossFn cf{};
   cf.m = sm;
   cf.ncomp = nc;
@@ -1229,8 +1252,8 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     fb.boxes = boxes.as<double>();
     fb.nboxes = rve->nboxes;
     CrossOut co;
-    TRY(cross_rounded(c, fb, std::vector<int>(dsp, 2), op_tol, cross_rank, cross_kick, cross_sweeps, 0x9a5eull,
-                      &ops->chi, &co));
+    TRY(cross_rounded(c, fb, std::vector<int>(dsp, 2), op_tol, cross_rank, 2 * cross_kick, cross_sweeps, 0x9a5eull,
+                      box_seeds(sm, rve->boxes, rve->nboxes), &ops->chi, &co));
   }
   ops->phase_rank = *std::max_element(ops->chi->r.begin(), ops->chi->r.end());
   // Green operator train: control core (ncomp^2) first, then the spatial sites
@@ -1249,7 +1272,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     CrossFn fg = cf;
     fg.kind = CROSS_GREEN;
     CrossOut co;
-    TRY(cross_rounded(c, fg, gmodes, op_tol, cross_rank, cross_kick, cross_sweeps, 0x6a3eull, &g, &co));
+    TRY(cross_rounded(c, fg, gmodes, op_tol, cross_rank, cross_kick, cross_sweeps, 0x6a3eull, {}, &g, &co));
   }
   ops->green_rank = *std::max_element(g->r.begin(), g->r.end());
   std::vector<int> mo(d, 2), g1(d + 1, 1);
@@ -1679,7 +1702,9 @@ extern "C" int tt_cross(qtt_ctx* c, const qtt_cross_fn* fn, double eps, int32_t 
     return QTT_ERR_ARG;
   }
   CrossOut co;
-  int s = cross_rounded(c, f, modes, eps, max_rank, kick, max_half_sweeps, seed, out, &co);
+  const auto seeds = f.kind == CROSS_BOXES ? box_seeds(f.m, fn->boxes, fn->nboxes)
+                                           : std::vector<std::vector<uint8_t>>();
+  int s = cross_rounded(c, f, modes, eps, max_rank, kick, max_half_sweeps, seed, seeds, out, &co);
   if (info) {
     info->half_sweeps = co.half_sweeps;
     info->evaluations = co.evaluations;

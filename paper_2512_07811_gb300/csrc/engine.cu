@@ -469,12 +469,16 @@ int tsqr_r(qtt_ctx* c, const cplx<R>* in, MIdx rowI, MIdx colI, int conj_in, int
   DBuf W, Rs;
   TRY(W.alloc(c, (size_t)nch * chunk * n * sizeof(cplx<R>)));
   TRY(Rs.alloc(c, (size_t)nch * n * n * sizeof(cplx<R>)));
-  // batch b reads rows [b*chunk, (b+1)*chunk): the batch stride is chunk rows
-  MIdx inB = L1(nch, rowI.n2 == 1 ? chunk * rowI.s1 : 0);
+  // batch b reads rows [b*chunk, (b+1)*chunk): the batch stride is chunk rows;
+  // at most 65535 batches per launch, so very tall inputs go in slabs
   if (rowI.n2 != 1) return QTT_ERR_UNSUPPORTED;
   MIdx rows = L1(chunk, rowI.s1);
-  TRY(qr_launch<R>(c, in, inB, rows, colI, conj_in, chunk, n, m, chunk, nch, W.as<cplx<R>>(), Rs.as<cplx<R>>(),
-                   n * n, n));
+  const int64_t max_batch = 65535;
+  for (int64_t b0 = 0; b0 < nch; b0 += max_batch) {
+    const int64_t nb = std::min(max_batch, nch - b0), r0 = b0 * chunk;
+    TRY(qr_launch<R>(c, in + r0 * rowI.s1, L1(nb, chunk * rowI.s1), rows, colI, conj_in, chunk, n, m - r0, chunk,
+                     nb, W.as<cplx<R>>() + b0 * chunk * n, Rs.as<cplx<R>>() + b0 * n * n, n * n, n));
+  }
   return tsqr_r<R>(c, Rs.as<cplx<R>>(), L1(nch * n, n), L1(n, 1), 0, nch * n, n, Rout, rows_out);
 }
 

@@ -400,12 +400,15 @@ def tt_round_polar(ctx: Context, x: TT, eps: float, prec=None):
 
 
 def tt_cross(ctx: Context, kind: str, nbits, eps: float, interleaved: bool = True, ncomp: int = 3,
-             k0: float = 1.0, lam0: float = 0.0, mu0: float = 0.0, boxes=None, max_rank: int = 0, kick: int = 4,
-             max_half_sweeps: int = 16, seed: int = 1):
+             k0: float = 1.0, lam0: float = 0.0, mu0: float = 0.0, boxes=None, max_rank: int = 0,
+             kick: int | None = None, max_half_sweeps: int = 24, seed: int = 1):
     """TT-cross of the Green operator train (kind "green": modes (ncomp^2,
     2, ...), momentum convention) or of a box geometry's phase indicator
     (kind "boxes": modes (2, ...), position convention) on a grid of
-    2^nbits[a] voxels per dimension.  Returns (TT, CrossInfo)."""
+    2^nbits[a] voxels per dimension; kick defaults to 4 (green) / 8 (boxes),
+    as inside ms_homogenize.  Returns (TT, CrossInfo)."""
+    if kick is None:
+        kick = 4 if kind == "green" else 8
     f = CrossFn()
     f.kind = CROSS_GREEN if kind == "green" else CROSS_BOXES
     for a in range(3):

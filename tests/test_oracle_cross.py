@@ -140,3 +140,26 @@ def test_cross_boxes_exact(nb, ordering):
     ref = MS.spatial_to_sites(I.boxes_indicator(boxes, shape), nb, ordering)
     cores, info = X.tt_cross(X.boxes_fn(boxes, nb, ordering), [2] * sum(nb), 1e-10, init_rank=8)
     assert np.abs(T.tt_full(cores).reshape(ref.shape) - ref).max() < 1e-10
+
+
+def test_box_centre_points_are_inside():
+    """The seed points of a box geometry lie in phase 2 (the centre voxel of
+    every box wider than a voxel)."""
+    nb = (7, 6, 0)
+    boxes = I.multibox_boxes_2d(128, count=8, seed=9)
+    for ordering in ["interleaved", "grouped"]:
+        pts = X.box_centre_points(boxes, nb, ordering)
+        assert np.all(X.boxes_fn(boxes, nb, ordering)(pts) == 1.0)
+
+
+def test_cross_boxes_fine_grid_with_seeds():
+    """2^14 x 2^14 multibox: with the centre seeds and kick 8 the cross reaches
+    the exact indicator (20000 random samples)."""
+    nb = (14, 14, 0)
+    boxes = I.multibox_boxes_2d(1 << 14, count=8, seed=5)
+    f = X.boxes_fn(boxes, nb)
+    cores, info = X.tt_cross(f, [2] * 28, 1e-10, kick=8, init_rank=8, max_half_sweeps=24,
+                             init_points=X.box_centre_points(boxes, nb))
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, 2, (20000, 28))
+    assert np.abs(T.tt_entries(cores, idx) - f(idx)).max() < 1e-10
