@@ -259,6 +259,29 @@ QTT_API int qtt_mpo_diag(qtt_ctx* ctx, const qtt_tt* x, qtt_mpo** out);
 /* B = A stored in another dtype. */
 QTT_API int qtt_mpo_convert(qtt_ctx* ctx, const qtt_mpo* A, qtt_dtype dtype, qtt_mpo** out);
 
+/* ---------------------------------------------------------------- AMEn */
+typedef struct {
+  int32_t sweeps;   /* sweeps made                                                     */
+  double dx;        /* largest relative change of a core in the last sweep             */
+} qtt_amen_info;
+
+/* y ~ A x by AMEn (Sec. 2.1, the optimisation-based product that the paper
+ * applies to the Green operator, Sec. 3.2; Dolgov & Savostyanov's
+ * alternating minimal energy with residual enrichment, matrix-vector form):
+ * sweeps over the cores replace each core of y by the projection of A x on
+ * the interfaces of the others (right-orthogonalised before every sweep),
+ * truncate it by SVD at eps ||y|| / sqrt(d - 1), and enrich its basis with
+ * the residual A x - y projected on a rank-`kick` residual train z, updated
+ * alongside; sweeps stop when no core changes by more than eps (relative),
+ * or after max_sweeps; the result is rounded at eps.  A x is never formed:
+ * every step contracts the cores of A and x with interfaces of rank
+ * (r_y, r_A, r_x).  y0: initial guess (NULL: a Gaussian train of rank 4
+ * drawn with `seed`), same modes as A's outputs and x's dtype.  A and x of
+ * one dtype (complex128: FP64 arithmetic; complex64: FP32).  QTT_ERR_ARG on
+ * mismatched shapes or dtypes. */
+QTT_API int tt_amen_mv(qtt_ctx* ctx, const qtt_mpo* A, const qtt_tt* x, const qtt_tt* y0, double eps, int32_t kick,
+                       int32_t max_sweeps, uint64_t seed, qtt_tt** y, qtt_amen_info* info);
+
 /* ------------------------------------------------------------ TT-cross */
 /* Functions the TT-cross samples (Sec. 3, operator setup: the discretised
  * operands are separated into cores by the TT-cross approximation instead of
@@ -362,6 +385,9 @@ typedef struct {
   float* trace;          /* NULL or host buffer receiving (features, target) rows of every
                             sketched rounding: QTT_MLP_FEATURES + 1 floats per bond          */
   int64_t trace_cap;     /* capacity of `trace` in rows                                     */
+  int32_t green_amen;    /* 1: the Green step eps^ = Gamma0 tau^ by AMEn (tt_amen_mv, kick 4,
+                            at most 12 sweeps, warm-started from the previous iteration's
+                            eps^) instead of the MPO x TT product with a sketched rounding  */
 } ms_opts;
 
 typedef struct {

@@ -127,11 +127,12 @@ def amen_mv(A, x, eps: float, y0=None, kick: int = 4, max_sweeps: int = 20, init
             # enrichment: (A x - y) on y's left and z's right interface
             Ek = _proj(phi, A[k], x[k], psiz[k + 1]) - np.einsum("aie,de->aid", Ycur.reshape(r0, n, r1),
                                                                   psizy[k + 1])
-            # orthonormal basis of [U_t, E_k]: its left singular vectors above
-            # 1e-14 of the largest (E_k may repeat directions of U_t)
+            # orthonormal basis of [U_t, E_k]: its left singular vectors, the
+            # discarded tail at most 100 u ||[U_t, E_k]|| (E_k may repeat
+            # directions of U_t)
             Uaug = np.hstack([U[:, :t], Ek.reshape(r0 * n, -1)])
             Qs, sq, _ = np.linalg.svd(Uaug, full_matrices=False)
-            keep = int(np.sum(sq > 1e-14 * sq[0]))
+            keep, _ = T.truncation_rank(sq, 100 * np.finfo(np.float64).eps * np.linalg.norm(Uaug))
             Q = Qs[:, :keep]
             carry = Q.conj().T @ Ycur                                  # keep x r1
             y[k] = Q.reshape(r0, n, keep)

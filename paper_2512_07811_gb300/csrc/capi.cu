@@ -521,6 +521,30 @@ int tt_round_polar(qtt_ctx* c, const qtt_tt* x, double eps, qtt_prec p, qtt_roun
                               : round_det<float>(c, x, eps, 0, nullptr, info, y, false, true);
 }
 
+int tt_amen_mv(qtt_ctx* c, const qtt_mpo* A, const qtt_tt* x, const qtt_tt* y0, double eps, int32_t kick,
+               int32_t max_sweeps, uint64_t seed, qtt_tt** y, qtt_amen_info* info) {
+  if (!c || !A || !valid_tt(x) || !y || !(eps > 0) || kick < 1 || kick > 64 || max_sweeps < 1 || max_sweeps > 100)
+    return QTT_ERR_ARG;
+  if (A->d != x->d || A->dtype != x->dtype || A->g.front() != 1 || A->g.back() != 1) return QTT_ERR_ARG;
+  for (int k = 0; k < x->d; ++k)
+    if (A->ni[k] != x->n[k]) return QTT_ERR_ARG;
+  if (y0) {
+    if (!valid_tt(y0) || y0->d != x->d || y0->dtype != x->dtype) return QTT_ERR_ARG;
+    for (int k = 0; k < x->d; ++k)
+      if (y0->n[k] != A->no[k]) return QTT_ERR_ARG;
+  }
+  int sw = 0;
+  double dx = 0;
+  int s = x->dtype == QTT_C128 ? amen_mv_dev<double>(c, A, x, y0, eps, kick, max_sweeps, seed, 0, y, &sw, &dx)
+                               : amen_mv_dev<float>(c, A, x, y0, eps, kick, max_sweeps, seed, 0, y, &sw, &dx);
+  if (info) {
+    info->sweeps = sw;
+    info->dx = dx;
+  }
+  if (!s && cudaStreamSynchronize(c->stream) != cudaSuccess) s = QTT_ERR_CUDA;
+  return s;
+}
+
 int tt_round_batch(qtt_ctx* c, int count, const qtt_tt* const* x, double eps, int max_rank, qtt_prec p,
                    qtt_round_info* info, qtt_tt** y) {
   if (!c || count < 1 || !x || !y || !(eps >= 0)) return QTT_ERR_ARG;
@@ -1535,6 +1559,13 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     const double normE = sqrt(Nvox);
     qtt_tt* x = nullptr;
     TRY(convert_tt(c, E, dt, &x));
+    struct Ghat {
+      qtt_tt* p = nullptr;
+      ~Ghat() {
+        if (p) tt_free(p);
+      }
+    } ghat_hold;   // the previous eps^ (AMEn's warm start)
+    qtt_tt*& ghat = ghat_hold.p;
     int it = 0;
     double res = 1.0;
     const qtt_complex one = {1.0, 0.0};
@@ -1569,9 +1600,24 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
       {
         stage = "Gamma";
         qtt_tt* hn = nullptr;
-        const qtt_mpo* A[1] = {G};
-        const qtt_tt* X[1] = {h};
-        int s = sk_round(1, &one, A, X, 4, &hn);
+        int s;
+        if (o.green_amen) {
+          // AMEn, warm-started from the previous iteration's eps^
+          int sw = 0;
+          double dxv = 0;
+          s = amen_mv_dev<R>(c, G, h, ghat, o.eps, 4, 12, o.seed + 7919ull * (uint64_t)it, max_rank, &hn, &sw,
+                             &dxv);
+          if (!s) {
+            if (ghat) tt_free(ghat);
+            ghat = nullptr;
+            s = convert_tt(c, hn, dt, &ghat);
+            if (rep) rep->max_rank_seen = std::max(rep->max_rank_seen, *std::max_element(hn->r.begin(), hn->r.end()));
+          }
+        } else {
+          const qtt_mpo* A[1] = {G};
+          const qtt_tt* X[1] = {h};
+          s = sk_round(1, &one, A, X, 4, &hn);
+        }
         tt_free(h);
         if (s) return s;
         h = hn;

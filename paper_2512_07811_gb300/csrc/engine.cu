@@ -298,6 +298,20 @@ int mm(qtt_ctx* c, int64_t M, int64_t N, int64_t K, const cplx<R>* A, int64_t sA
   return simt_gemm<R>(c, g, alpha, beta, A, B, C);
 }
 
+// C = alpha op(A) op(B) + beta C for a general descriptor
+template <class R>
+int gemm_ab(qtt_ctx* c, const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B,
+            cplx<R>* C) {
+  if (sizeof(R) == 4) {
+    int st = tc_route(c, g, cc((float)alpha.re, (float)alpha.im), cc((float)beta.re, (float)beta.im),
+                      reinterpret_cast<const cc*>(A), reinterpret_cast<const cc*>(B), reinterpret_cast<cc*>(C));
+    if (st != QTT_ERR_UNSUPPORTED) return st;
+  }
+  return simt_gemm<R>(c, g, alpha, beta, A, B, C);
+}
+template int gemm_ab<double>(qtt_ctx*, const GemmDesc&, zc, zc, const zc*, const zc*, zc*);
+template int gemm_ab<float>(qtt_ctx*, const GemmDesc&, cc, cc, const cc*, const cc*, cc*);
+
 template <class R>
 int gemm(qtt_ctx* c, const GemmDesc& g, const cplx<R>* A, const cplx<R>* B, cplx<R>* C) {
   if (sizeof(R) == 4) {
@@ -1231,6 +1245,7 @@ int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* 
 
 template int tt_svd_dev<double>(qtt_ctx*, int, const std::vector<int>&, const zc*, double, int, qtt_dtype, qtt_tt**);
 template int left_svd<double>(qtt_ctx*, const zc*, int64_t, int64_t, int64_t, zc*, double*, int64_t*);
+template int left_svd<float>(qtt_ctx*, const cc*, int64_t, int64_t, int64_t, cc*, float*, int64_t*);
 
 // ----------------------------------------------------------- inner product
 template <class R>

@@ -136,6 +136,16 @@ struct DBuf {
   T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// C = alpha op(A) op(B) + beta C for a general multi-index descriptor
+template <class R>
+int gemm_ab(qtt_ctx* c, const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B,
+            cplx<R>* C);
+
+// AMEn y ~ A x (amen.cu)
+template <class R>
+int amen_mv_dev(qtt_ctx* c, const qtt_mpo* A, const qtt_tt* x, const qtt_tt* y0, double eps, int kick,
+                int max_sweeps, uint64_t seed, int max_rank, qtt_tt** yout, int* sweeps_out, double* dx_out);
+
 // Left singular vectors (rows x min(rows, cols), row-major, by decreasing
 // singular value) and singular values of the row-major rows x cols C
 // (leading dimension ld); *nsv = min(rows, cols).

@@ -71,6 +71,10 @@ class CrossInfo(C.Structure):
 CROSS_GREEN, CROSS_BOXES = 1, 2
 
 
+class AmenInfo(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("dx", C.c_double)]
+
+
 class Boxes:
     """A phase geometry without a dense image: a union of axis-aligned boxes
     (rows cx, cy, cz, hx, hy, hz in unit-cell coordinates, periodic) on a grid
@@ -101,7 +105,7 @@ class MSOpts(C.Structure):
     _fields_ = [("prec", C.c_int), ("eps", C.c_double), ("op_tol", C.c_double), ("max_iter", C.c_int32),
                 ("oversample", C.c_int32), ("load_mask", C.c_int32), ("min_iter", C.c_int32),
                 ("seed", C.c_uint64), ("predictor", C.c_void_p), ("trace", C.POINTER(C.c_float)),
-                ("trace_cap", C.c_int64)]
+                ("trace_cap", C.c_int64), ("green_amen", C.c_int32)]
 
 
 class MSReport(C.Structure):
@@ -176,6 +180,8 @@ _sig("qtt_mlp_get_params", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64])
 _sig("qtt_mlp_forward", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_float)])
 _sig("qtt_mlp_train_step", C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64, C.c_float,
                                      C.c_float, C.POINTER(C.c_double), C.POINTER(C.c_float)])
+_sig("tt_amen_mv", C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_P),
+                            C.POINTER(AmenInfo)])
 _sig("tt_cross", C.c_int, [_P, C.POINTER(CrossFn), C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
                           C.POINTER(_P), C.POINTER(CrossInfo)])
 _sig("ms_homogenize", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
@@ -187,7 +193,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_polar", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_norm",
-            "tt_from_dense", "tt_cross", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
+            "tt_from_dense", "tt_cross", "tt_amen_mv", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
             "ms_homogenize_batch", "qtt_cgemm", "qtt_cgemm_noalloc",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
             "qtt_mlp_get_params", "qtt_mlp_forward", "qtt_mlp_train_step"]
@@ -379,6 +385,16 @@ def tt_mpo_apply(ctx: Context, A: MPO, x: TT) -> TT:
     h = _P()
     _check(_lib.tt_mpo_apply(ctx.h, A.h, x.h, C.byref(h)), "tt_mpo_apply")
     return TT(ctx, h)
+
+
+def tt_amen_mv(ctx: Context, A: MPO, x: TT, eps: float, y0: TT | None = None, kick: int = 4, max_sweeps: int = 20,
+               seed: int = 1):
+    """y ~ A x by AMEn (never forms A x); returns (TT, AmenInfo)."""
+    h = _P()
+    info = AmenInfo()
+    _check(_lib.tt_amen_mv(ctx.h, A.h, x.h, y0.h if y0 is not None else None, float(eps), int(kick),
+                           int(max_sweeps), int(seed), C.byref(h), C.byref(info)), "tt_amen_mv")
+    return TT(ctx, h), info
 
 
 def tt_round(ctx: Context, x: TT, eps: float, max_rank: int = 0, prec=None):
@@ -631,14 +647,15 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
                   eps: float = 1e-6, op_tol: float = 1e-10, prec: int = PREC_F64, max_iter: int = 100,
                   oversample: int = 8, load_mask: int | None = None, interleaved: bool = True,
                   min_iter: int = 1, seed: int = 12345, predictor: "MLP | None" = None, trace_cap: int = 0,
-                  op_cross: bool = False):
+                  op_cross: bool = False, green_amen: bool = False):
     """Effective tensor of a two-phase RVE (phase 2 where indicator == 1).
 
     kind "scalar": moduli = (k1, k2), C0 = 3x3; kind "elastic": moduli =
     (lam1, mu1, lam2, mu2), C0 = Voigt 6x6.  `indicator` is a dense
     (Nx, Ny, Nz) image or a Boxes geometry (phase train by TT-cross);
     op_cross builds the Green operator train by TT-cross at any size (it is
-    always so above 2^27 voxels).  Returns (C_eff, report)."""
+    always so above 2^27 voxels); green_amen applies it by AMEn.  Returns
+    (C_eff, report)."""
     rve, keep = _rve(indicator, kind, moduli, interleaved, op_cross)
     nc = rve.ncomp
     C0a = np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(nc, nc))
@@ -655,6 +672,7 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
     trace = np.zeros((max(trace_cap, 1), MLP_FEATURES + 1), dtype=np.float32)
     o.trace = _fptr(trace) if trace_cap > 0 else None
     o.trace_cap = int(trace_cap)
+    o.green_amen = 1 if green_amen else 0
     out = np.zeros((nc, nc), dtype=np.float64)
     rep = MSReport()
     _check(_lib.ms_homogenize(ctx.h, C.byref(rve), C0a.ctypes.data_as(C.POINTER(C.c_double)), float(tol),
