@@ -259,6 +259,15 @@ QTT_API int qtt_mpo_diag(qtt_ctx* ctx, const qtt_tt* x, qtt_mpo** out);
 /* B = A stored in another dtype. */
 QTT_API int qtt_mpo_convert(qtt_ctx* ctx, const qtt_mpo* A, qtt_dtype dtype, qtt_mpo** out);
 
+/* Algorithm 2's final contract(): the full tensor of x written as a voxel
+ * field.  x has the homogenisation's site convention: either a control core
+ * (ncomp components) followed by the spatial sites, or spatial sites only
+ * (ncomp = 1); nbits_dim and interleaved as in qtt_rve (position space, most
+ * significant bit first), 1 to 40 bits in all.  out: host, ncomp x Nx x Ny x
+ * Nz complex values of x's dtype, component slowest, z fastest. */
+QTT_API int tt_contract_voxels(qtt_ctx* ctx, const qtt_tt* x, const int32_t* nbits_dim, int32_t interleaved,
+                               void* out);
+
 /* ---------------------------------------------------------------- AMEn */
 typedef struct {
   int32_t sweeps;   /* sweeps made                                                     */
@@ -388,6 +397,10 @@ typedef struct {
   int32_t green_amen;    /* 1: the Green step eps^ = Gamma0 tau^ by AMEn (tt_amen_mv, kick 4,
                             at most 12 sweeps, warm-started from the previous iteration's
                             eps^) instead of the MPO x TT product with a sketched rounding  */
+  qtt_tt** strain;       /* NULL, or receives the converged strain train of the last solved
+                            load case (control core first, site order of the RVE, the
+                            iteration's dtype); *strain must be NULL or a train the call
+                            may destroy; ms_homogenize_batch ignores it                    */
 } ms_opts;
 
 typedef struct {

@@ -384,6 +384,16 @@ def ms_qtt(pb: Problem, E, ops: QTTOperators | None = None, eps: float = 1e-8,
     return MSResult(qtt_mean_stress(pb, ops, x), it, res, trace, x)
 
 
+def contract(x, n, ordering: str = "interleaved") -> np.ndarray:
+    """The local field of a strain train (Algorithm 2's final contract()):
+    the full tensor, control index first, in the position-space voxel order
+    (ncomp, Nx, Ny, Nz)."""
+    nb = _bits3(n)
+    full = T.tt_full(x)
+    nc = x[0].shape[1]
+    return sites_to_spatial(full.reshape((nc,) + (2,) * sum(nb)), nb, ordering, lead=1)
+
+
 # ------------------------------------------------------ closed forms --
 
 def scalar_laminate_keff(k1, k2, f2, axis=0):

@@ -1697,7 +1697,12 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
       rep->iterations[lc] = it;
       rep->residual[lc] = res;
     }
-    tt_free(x);
+    if (o.strain) {   // hand the converged strain of the last load case to the caller
+      if (*o.strain) tt_free(*o.strain);
+      *o.strain = x;
+    } else {
+      tt_free(x);
+    }
     tt_free(E);
   }
   if (rep) rep->sigma_imag_max = sig_im;
@@ -1705,6 +1710,77 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
 }
 
 }  // namespace
+
+// Full tensor of x as a row-major vector (site 0 slowest): a chain of GEMMs
+// V <- V (P x r_k) core_k (r_k x n_k r_{k+1}).
+template <class R>
+static int tt_full_dev(qtt_ctx* c, const qtt_tt* x, DBuf* out) {
+  typedef cplx<R> C;
+  int64_t P = x->n[0];
+  DBuf V;
+  TRY(V.alloc(c, (size_t)P * x->r[1] * sizeof(C)));
+  if (cudaMemcpyAsync(V.p, core_ptr<const C>(x, 0), (size_t)P * x->r[1] * sizeof(C), cudaMemcpyDeviceToDevice,
+                      c->stream) != cudaSuccess)
+    return QTT_ERR_CUDA;
+  for (int k = 1; k < x->d; ++k) {
+    const int64_t rk = x->r[k], nk = x->n[k], r1 = x->r[k + 1];
+    DBuf W;
+    TRY(W.alloc(c, (size_t)P * nk * r1 * sizeof(C)));
+    GemmDesc g;
+    g.bA = g.bB = g.bC = MIdx{1, 1, 0, 0};
+    g.M = P;
+    g.N = nk * r1;
+    g.K = rk;
+    g.batch = 1;
+    g.mA = MIdx{P, 1, rk, 0};
+    g.kA = MIdx{rk, 1, 1, 0};
+    g.kB = MIdx{rk, 1, nk * r1, 0};
+    g.nB = MIdx{nk * r1, 1, 1, 0};
+    g.mC = MIdx{P, 1, nk * r1, 0};
+    g.nC = MIdx{nk * r1, 1, 1, 0};
+    g.conjA = g.conjB = 0;
+    TRY(gemm_ab<R>(c, g, C(1, 0), C(0, 0), V.as<C>(), core_ptr<const C>(x, k), W.as<C>()));
+    V = std::move(W);
+    P *= nk;
+  }
+  *out = std::move(V);
+  return QTT_OK;
+}
+
+extern "C" int tt_contract_voxels(qtt_ctx* c, const qtt_tt* x, const int32_t* nbits_dim, int32_t interleaved,
+                                  void* out) {
+  if (!c || !valid_tt(x) || !nbits_dim || !out) return QTT_ERR_ARG;
+  int nb[3], tot = 0;
+  for (int a = 0; a < 3; ++a) {
+    nb[a] = nbits_dim[a];
+    if (nb[a] < 0 || nb[a] > 20) return QTT_ERR_ARG;
+    tot += nb[a];
+  }
+  if (tot < 1 || tot > 40) return QTT_ERR_ARG;
+  const bool ctrl = x->d == tot + 1;
+  if (!ctrl && x->d != tot) return QTT_ERR_ARG;
+  for (int k = ctrl ? 1 : 0; k < x->d; ++k)
+    if (x->n[k] != 2) return QTT_ERR_ARG;
+  const int ncomp = ctrl ? x->n[0] : 1;
+  const SiteMap m = site_map_bits(nb, interleaved != 0);
+  const size_t es = dtype_size(x->dtype);
+  const size_t count = ((size_t)1 << tot) * (size_t)ncomp;
+  DBuf full, vox;
+  int s = QTT_OK;
+  if (x->dtype == QTT_C128)
+    s = tt_full_dev<double>(c, x, &full);
+  else
+    s = tt_full_dev<float>(c, x, &full);
+  if (s) return s;
+  TRY(vox.alloc(c, count * es));
+  c->launches++;
+  if (x->dtype == QTT_C128)
+    s = qtt_sites_to_voxels<double>(full.as<zc>(), m, ncomp, vox.as<zc>(), c->stream);
+  else
+    s = qtt_sites_to_voxels<float>(full.as<cc>(), m, ncomp, vox.as<cc>(), c->stream);
+  if (s) return s;
+  return sync_read(c, out, vox.p, count * es);
+}
 
 extern "C" int tt_cross(qtt_ctx* c, const qtt_cross_fn* fn, double eps, int32_t max_rank, int32_t kick,
                         int32_t max_half_sweeps, uint64_t seed, qtt_tt** out, qtt_cross_info* info) {
@@ -1872,6 +1948,7 @@ extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const
       oj.load_mask = 1 << jb.lc;
       oj.trace = nullptr;
       oj.trace_cap = 0;
+      oj.strain = nullptr;
       std::vector<double> Cj(nc * nc, 0.0);
       ms_report rj;
       st = ms_homogenize(wc, &rves[jb.rve], C0s + (size_t)jb.rve * 36, tol, max_rank, &oj, Cj.data(), &rj);

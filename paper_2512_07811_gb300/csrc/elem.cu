@@ -232,6 +232,29 @@ __global__ void indicator_sites_kernel(const double* __restrict__ ind, SiteMap m
   }
 }
 
+// Full tensor of a train (control index c slowest, then the site multi-index
+// s with site 0 most significant) to the voxel field out[c][x][y][z]: site p
+// holds bit nb[dim[p]] - 1 - pos[p] of coordinate dim[p] (position space).
+template <class R>
+__global__ void sites_to_voxels_kernel(const cplx<R>* __restrict__ in, SiteMap m, int ncomp,
+                                       cplx<R>* __restrict__ out) {
+  const int d = m.d;
+  const int64_t nv = (int64_t)1 << d;
+  const int64_t total = nv * ncomp;
+  const int64_t Ny = (int64_t)1 << m.nb[1], Nz = (int64_t)1 << m.nb[2];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e >> d, s = e & (nv - 1);
+    int64_t x[3] = {0, 0, 0};
+    for (int p = 0; p < d; ++p) {
+      const int bit = (int)((s >> (d - 1 - p)) & 1);
+      const int dm = m.dim[p];
+      x[dm] |= (int64_t)bit << (m.nb[dm] - 1 - m.pos[p]);
+    }
+    out[c * nv + (x[0] * Ny + x[1]) * Nz + x[2]] = in[e];
+  }
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
 // as 1, 2, 3", SC'11): counter-based generator, 10 rounds with the published
 // multipliers and Weyl key increments.
@@ -484,6 +507,13 @@ int qtt_fill_indicator_sites(const double* ind, const SiteMap& m, cplx<R>* out, 
 }
 
 template <class R>
+int qtt_sites_to_voxels(const cplx<R>* in, const SiteMap& m, int ncomp, cplx<R>* out, cudaStream_t s) {
+  const int64_t total = ((int64_t)1 << m.d) * ncomp;
+  sites_to_voxels_kernel<R><<<nblocks(total), TPB, 0, s>>>(in, m, ncomp, out);
+  CHECK_LAUNCH();
+}
+
+template <class R>
 int qtt_fill_gaussian(cplx<R>* out, int64_t count, uint64_t seed, uint64_t stream, double scale, cudaStream_t s) {
   if (count <= 0) return QTT_OK;
   gaussian_kernel<R><<<nblocks(count), TPB, 0, s>>>(out, count, seed, stream, scale);
@@ -528,6 +558,7 @@ int qtt_adjoint_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64
   template int qtt_fill_qft_dense<R>(cplx<R>*, int, double, cudaStream_t);                               \
   template int qtt_fill_green_dense<R>(cplx<R>*, const SiteMap&, int, double, double, double, cudaStream_t);   \
   template int qtt_fill_indicator_sites<R>(const double*, const SiteMap&, cplx<R>*, cudaStream_t);              \
+  template int qtt_sites_to_voxels<R>(const cplx<R>*, const SiteMap&, int, cplx<R>*, cudaStream_t);            \
   template int qtt_fill_gaussian<R>(cplx<R>*, int64_t, uint64_t, uint64_t, double, cudaStream_t);          \
   template int qtt_diag_mpo_core<R>(const cplx<R>*, int64_t, int64_t, int64_t, cplx<R>*, cudaStream_t);    \
   template int qtt_identity_core<R>(int64_t, int64_t, cplx<R>*, cudaStream_t);                             \

@@ -142,3 +142,7 @@ int qtt_cross_right_index(const uint8_t* Jnext, int nr, int rr, const int* piv, 
 template <class R>
 int qtt_cross_gather(const cplx<R>* S, int64_t ld, const int* piv, int t, int64_t len, int trans, cplx<R>* out,
                      cudaStream_t s);
+
+// full tensor in site order (control first) -> voxel field (elem.cu)
+template <class R>
+int qtt_sites_to_voxels(const cplx<R>* in, const SiteMap& m, int ncomp, cplx<R>* out, cudaStream_t s);

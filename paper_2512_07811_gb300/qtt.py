@@ -105,7 +105,7 @@ class MSOpts(C.Structure):
     _fields_ = [("prec", C.c_int), ("eps", C.c_double), ("op_tol", C.c_double), ("max_iter", C.c_int32),
                 ("oversample", C.c_int32), ("load_mask", C.c_int32), ("min_iter", C.c_int32),
                 ("seed", C.c_uint64), ("predictor", C.c_void_p), ("trace", C.POINTER(C.c_float)),
-                ("trace_cap", C.c_int64), ("green_amen", C.c_int32)]
+                ("trace_cap", C.c_int64), ("green_amen", C.c_int32), ("strain", C.POINTER(C.c_void_p))]
 
 
 class MSReport(C.Structure):
@@ -180,6 +180,7 @@ _sig("qtt_mlp_get_params", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64])
 _sig("qtt_mlp_forward", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_float)])
 _sig("qtt_mlp_train_step", C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64, C.c_float,
                                      C.c_float, C.POINTER(C.c_double), C.POINTER(C.c_float)])
+_sig("tt_contract_voxels", C.c_int, [_P, _P, _I32P, C.c_int32, _P])
 _sig("tt_amen_mv", C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_P),
                             C.POINTER(AmenInfo)])
 _sig("tt_cross", C.c_int, [_P, C.POINTER(CrossFn), C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
@@ -193,7 +194,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_polar", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_norm",
-            "tt_from_dense", "tt_cross", "tt_amen_mv", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
+            "tt_from_dense", "tt_cross", "tt_amen_mv", "tt_contract_voxels", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
             "ms_homogenize_batch", "qtt_cgemm", "qtt_cgemm_noalloc",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
             "qtt_mlp_get_params", "qtt_mlp_forward", "qtt_mlp_train_step"]
@@ -385,6 +386,17 @@ def tt_mpo_apply(ctx: Context, A: MPO, x: TT) -> TT:
     h = _P()
     _check(_lib.tt_mpo_apply(ctx.h, A.h, x.h, C.byref(h)), "tt_mpo_apply")
     return TT(ctx, h)
+
+
+def contract_voxels(ctx: Context, x: TT, nbits, interleaved: bool = True) -> np.ndarray:
+    """Algorithm 2's contract(): the full tensor of x (control core first, or
+    spatial sites only) as a voxel field (ncomp, Nx, Ny, Nz)."""
+    nb = [int(b) for b in nbits]
+    ncomp = x.modes[0] if x.ncores == sum(nb) + 1 else 1
+    out = np.zeros((ncomp, 1 << nb[0], 1 << nb[1], 1 << nb[2]), dtype=_NP[x.dtype])
+    _check(_lib.tt_contract_voxels(ctx.h, x.h, _i32(nb), 1 if interleaved else 0, out.ctypes.data),
+           "tt_contract_voxels")
+    return out
 
 
 def tt_amen_mv(ctx: Context, A: MPO, x: TT, eps: float, y0: TT | None = None, kick: int = 4, max_sweeps: int = 20,
@@ -647,15 +659,16 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
                   eps: float = 1e-6, op_tol: float = 1e-10, prec: int = PREC_F64, max_iter: int = 100,
                   oversample: int = 8, load_mask: int | None = None, interleaved: bool = True,
                   min_iter: int = 1, seed: int = 12345, predictor: "MLP | None" = None, trace_cap: int = 0,
-                  op_cross: bool = False, green_amen: bool = False):
+                  op_cross: bool = False, green_amen: bool = False, return_strain: bool = False):
     """Effective tensor of a two-phase RVE (phase 2 where indicator == 1).
 
     kind "scalar": moduli = (k1, k2), C0 = 3x3; kind "elastic": moduli =
     (lam1, mu1, lam2, mu2), C0 = Voigt 6x6.  `indicator` is a dense
     (Nx, Ny, Nz) image or a Boxes geometry (phase train by TT-cross);
     op_cross builds the Green operator train by TT-cross at any size (it is
-    always so above 2^27 voxels); green_amen applies it by AMEn.  Returns
-    (C_eff, report)."""
+    always so above 2^27 voxels); green_amen applies it by AMEn;
+    return_strain puts the converged strain train of the last load case in
+    report.strain (see contract_voxels).  Returns (C_eff, report)."""
     rve, keep = _rve(indicator, kind, moduli, interleaved, op_cross)
     nc = rve.ncomp
     C0a = np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(nc, nc))
@@ -673,6 +686,8 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
     o.trace = _fptr(trace) if trace_cap > 0 else None
     o.trace_cap = int(trace_cap)
     o.green_amen = 1 if green_amen else 0
+    strain = _P()
+    o.strain = C.pointer(strain) if return_strain else None
     out = np.zeros((nc, nc), dtype=np.float64)
     rep = MSReport()
     _check(_lib.ms_homogenize(ctx.h, C.byref(rve), C0a.ctypes.data_as(C.POINTER(C.c_double)), float(tol),
@@ -680,4 +695,6 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
            "ms_homogenize")
     if trace_cap > 0:
         rep.trace_rows = trace[:rep.trace_len].copy()
+    if return_strain:
+        rep.strain = TT(ctx, strain) if strain.value else None
     return out, rep

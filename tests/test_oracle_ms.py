@@ -250,3 +250,31 @@ def test_multibox_plane_geometry():
     img = I.multibox_indicator_2d(64, count=8, area_fraction=0.2, seed=3)
     assert img.shape == (64, 64, 1)
     assert 0.1 < img.mean() < 0.3
+
+
+def test_contract_local_strain_laminate_closed_form():
+    """Algorithm 2's contract() on the 8^3 laminate, E = e_x: the local
+    gradient is 20/11 in phase 1 and 2/11 in phase 2 (constant flux 20/11),
+    zero across the layers."""
+    ind = I.laminate_indicator(8)
+    pb = MS.scalar_problem(ind, 1.0, 10.0)
+    res = MS.ms_qtt(pb, np.array([1.0, 0.0, 0.0]), eps=1e-12, tol=1e-13, max_iter=10)
+    loc = MS.contract(res.eps_field, (3, 3, 3))
+    want = np.where(ind == 1.0, 2.0 / 11.0, 20.0 / 11.0)
+    np.testing.assert_allclose(loc[0].real, want, atol=1e-10)
+    np.testing.assert_allclose(np.abs(loc[1:]), 0.0, atol=1e-10)
+
+
+@pytest.mark.parametrize("ordering", ["interleaved", "grouped"])
+def test_contract_equals_dense_local_field(ordering):
+    """8 x 8 x 2 random two-phase grid: the QTT local strain equals the dense
+    FFT solver's local field (Algorithm 1)."""
+    rng = np.random.default_rng(12)
+    ind = (rng.random((8, 8, 2)) < 0.3).astype(np.float64)
+    pb = MS.scalar_problem(ind, 1.0, 5.0)
+    E = np.array([1.0, 0.0, 0.0])
+    dense = MS.ms_dense(pb, E, tol=1e-12, max_iter=500, keep_field=True)
+    res = MS.ms_qtt(pb, E, ops=MS.build_operators(pb, ordering), eps=1e-12, tol=1e-12, max_iter=500,
+                    ordering=ordering)
+    loc = MS.contract(res.eps_field, (3, 3, 1), ordering)
+    np.testing.assert_allclose(loc, dense.eps_field, atol=1e-8)
