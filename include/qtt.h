@@ -173,7 +173,7 @@ QTT_API int tt_round_polar(qtt_ctx* ctx, const qtt_tt* x, double eps, qtt_prec p
  * truncation ranks and cap), in lockstep: each step of either sweep is one
  * launch per kernel for the whole batch (one QR block and one Jacobi
  * cluster per train), so many independent roundings share the device instead
- * of queueing.  A builder addition for many RVEs or load cases (the grouped
+ * of queueing.  An addition for many RVEs or load cases (the grouped
  * batching the paper lists as future work, Sec. 6); results agree with
  * tt_round to rounding error (the Jacobi sweeps may visit pairs in another
  * order).  x: count input handles; y: count outputs (new handles owned by
@@ -189,7 +189,7 @@ QTT_API int tt_round_batch(qtt_ctx* ctx, int count, const qtt_tt* const* x, doub
  * sketch are built term by term, then a left-to-right sweep of QR
  * factorisations of the sketched cores projects s onto rank l_k, and a
  * deterministic rounding (tt_round) of that projection applies eps and
- * max_rank.  A builder addition with no counterpart in the paper (Al Daas et
+ * max_rank.  Not in the paper (Al Daas et
  * al., SIAM J. Sci. Comput. 45, 2023).  All trains share one dtype. */
 QTT_API int tt_round_sketched(qtt_ctx* ctx, int nterms, const qtt_complex* coef, const qtt_mpo* const* ops,
                       const qtt_tt* const* xs, const qtt_tt* sketch, double eps, int max_rank, qtt_prec prec,
@@ -445,7 +445,7 @@ QTT_API int ms_homogenize_batch(qtt_ctx* ctx, int n, const qtt_rve* rves, const 
 /* A multilayer perceptron with three hidden layers of width 64 and ReLU, FP16
  * weights, FP32 accumulation, FP32 master weights and Adam moments; it maps
  * QTT_MLP_FEATURES (or any n_features <= 32) per-bond features to a predicted
- * log2 rank.  A builder addition with no counterpart in the paper (nearest
+ * log2 rank.  Not in the paper (nearest
  * relative: the coarse-grained ranks of Sec. 5.1).  Packed parameter order:
  * W0 (64 x F), b0 (64), W1 (64 x 64), b1, W2 (64 x 64), b2, W3 (64), b3 (1),
  * weights row-major (out, in).  Host buffers throughout; every call

@@ -16,6 +16,6 @@ ms      dense FFT Moulinec-Suquet (Algorithm 1) and QTT Moulinec-Suquet
         (Algorithm 2), Green operators, effective tensors, closed forms
 mlp     the per-bond rank predictor (3 hidden layers of width 64) with
         hand-written forward and backward passes
-randround  randomize-then-orthogonalize TT rounding (a builder addition; no
-        counterpart in the paper) used to judge the GPU sketch path
+randround  randomize-then-orthogonalize TT rounding (not in the
+        paper) used to check the GPU sketch path
 """

@@ -1,6 +1,6 @@
 """Per-bond rank predictor: a multilayer perceptron with three hidden layers of
 width 64 and ReLU, hand-written forward and backward passes in FP64, and an
-Adam update.  A builder addition (no counterpart in the paper; the nearest
+Adam update.  Not in the paper (the nearest
 relative is the coarse-grained rank of Sec. 5.1).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).

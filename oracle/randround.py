@@ -1,5 +1,5 @@
-"""Randomize-then-orthogonalize TT rounding (a builder addition; the paper has
-no counterpart).  TEST INFRASTRUCTURE ONLY (see the package docstring).
+"""Randomize-then-orthogonalize TT rounding (not in the
+paper).  TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 Published method: Al Daas, Ballard, Cazeaux, Hallman, Miedlar, Pasha, Reid,
 Saibaba, "Randomized algorithms for rounding in the tensor-train format",

@@ -1,7 +1,7 @@
 // Per-bond rank predictor: a multilayer perceptron with three hidden layers of
 // width 64 and ReLU, FP16 weights, FP32 biases, FP32 accumulation, FP32 master
-// weights and Adam moments for training (a builder addition with no
-// counterpart in the paper; its nearest relative is the coarse-grained rank
+// weights and Adam moments for training (not in the paper; its
+// nearest relative is the coarse-grained rank
 // of Sec. 5.1).
 //
 //   h1 = relu(W0 x + b0), h2 = relu(W1 h1 + b1), h3 = relu(W2 h2 + b2),
