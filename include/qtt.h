@@ -291,6 +291,17 @@ typedef struct {
 QTT_API int tt_amen_mv(qtt_ctx* ctx, const qtt_mpo* A, const qtt_tt* x, const qtt_tt* y0, double eps, int32_t kick,
                        int32_t max_sweeps, uint64_t seed, qtt_tt** y, qtt_amen_info* info);
 
+/* The spatial site order of a grid of 2^nbits_dim[a] voxels per dimension
+ * (the order every homogenisation train uses after its control site): for
+ * each site p (0-based), dim[p] the dimension and pos[p] the bit level it
+ * holds (0 = most significant in position space, least significant in
+ * momentum space).  interleaved: level by level (bit a of x, y, z in turn,
+ * skipping a dimension whose bits are used up), else grouped by dimension.
+ * Host only (no context, no device); dim and pos take at least
+ * nbits_dim[0] + nbits_dim[1] + nbits_dim[2] entries; returns that count,
+ * or QTT_ERR_ARG. */
+QTT_API int qtt_site_order(const int32_t* nbits_dim, int32_t interleaved, int32_t* dim, int32_t* pos);
+
 /* ------------------------------------------------------------ TT-cross */
 /* Functions the TT-cross samples (Sec. 3, operator setup: the discretised
  * operands are separated into cores by the TT-cross approximation instead of

@@ -1747,6 +1747,23 @@ static int tt_full_dev(qtt_ctx* c, const qtt_tt* x, DBuf* out) {
   return QTT_OK;
 }
 
+extern "C" int qtt_site_order(const int32_t* nbits_dim, int32_t interleaved, int32_t* dim, int32_t* pos) {
+  if (!nbits_dim || !dim || !pos) return QTT_ERR_ARG;
+  int nb[3], tot = 0;
+  for (int a = 0; a < 3; ++a) {
+    nb[a] = nbits_dim[a];
+    if (nb[a] < 0 || nb[a] > 20) return QTT_ERR_ARG;
+    tot += nb[a];
+  }
+  if (tot > 60) return QTT_ERR_ARG;
+  const SiteMap m = site_map_bits(nb, interleaved != 0);
+  for (int p = 0; p < m.d; ++p) {
+    dim[p] = m.dim[p];
+    pos[p] = m.pos[p];
+  }
+  return m.d;
+}
+
 extern "C" int tt_contract_voxels(qtt_ctx* c, const qtt_tt* x, const int32_t* nbits_dim, int32_t interleaved,
                                   void* out) {
   if (!c || !valid_tt(x) || !nbits_dim || !out) return QTT_ERR_ARG;

@@ -180,6 +180,7 @@ _sig("qtt_mlp_get_params", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64])
 _sig("qtt_mlp_forward", C.c_int, [_P, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_float)])
 _sig("qtt_mlp_train_step", C.c_int, [_P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64, C.c_float,
                                      C.c_float, C.POINTER(C.c_double), C.POINTER(C.c_float)])
+_sig("qtt_site_order", C.c_int, [_I32P, C.c_int32, _I32P, _I32P])
 _sig("tt_contract_voxels", C.c_int, [_P, _P, _I32P, C.c_int32, _P])
 _sig("tt_amen_mv", C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_P),
                             C.POINTER(AmenInfo)])
@@ -194,7 +195,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_polar", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_norm",
-            "tt_from_dense", "tt_cross", "tt_amen_mv", "tt_contract_voxels", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
+            "tt_from_dense", "tt_cross", "tt_amen_mv", "tt_contract_voxels", "qtt_site_order", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
             "ms_homogenize_batch", "qtt_cgemm", "qtt_cgemm_noalloc",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
             "qtt_mlp_get_params", "qtt_mlp_forward", "qtt_mlp_train_step"]
@@ -386,6 +387,18 @@ def tt_mpo_apply(ctx: Context, A: MPO, x: TT) -> TT:
     h = _P()
     _check(_lib.tt_mpo_apply(ctx.h, A.h, x.h, C.byref(h)), "tt_mpo_apply")
     return TT(ctx, h)
+
+
+def site_order(nbits, interleaved: bool = True):
+    """(dim, pos) of every spatial site of a 2^nbits grid (host only)."""
+    nb = [int(b) for b in nbits]
+    n = max(sum(nb), 1)
+    dim = (C.c_int32 * n)()
+    pos = (C.c_int32 * n)()
+    d = _lib.qtt_site_order(_i32(nb), 1 if interleaved else 0, dim, pos)
+    if d < 0:
+        _check(d, "qtt_site_order")
+    return list(dim[:d]), list(pos[:d])
 
 
 def contract_voxels(ctx: Context, x: TT, nbits, interleaved: bool = True) -> np.ndarray:
