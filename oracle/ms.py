@@ -290,22 +290,39 @@ class QTTOperators:
 
 
 def build_operators(pb: Problem, ordering: str = "interleaved", op_tol: float = 1e-10,
-                    qft_tol: float = 1e-12) -> QTTOperators:
+                    qft_tol: float = 1e-12, op_cross: bool = False, boxes=None) -> QTTOperators:
+    """The operator trains of Algorithm 2.  By default the phase indicator
+    and the Green operator are compressed from their dense arrays (TT-SVD);
+    op_cross samples the Green operator by TT-cross instead (Sec. 3), and a
+    box list (rows cx, cy, cz, hx, hy, hz) samples the phase indicator by
+    TT-cross; both crosses are rounded at op_tol."""
+    from . import cross as X
     shape = grid_shape(pb)
     n = grid_bits(shape)
     nc = pb.ncomp
     d_sp = sum(n)
-    chi = T.tt_svd(spatial_to_sites(pb.indicator.astype(np.complex128), n, ordering), op_tol)
+    if boxes is not None:
+        chi, _ = X.tt_cross(X.boxes_fn(boxes, n, ordering), [2] * d_sp, op_tol, kick=8, init_rank=8,
+                            max_half_sweeps=24, init_points=X.box_centre_points(boxes, n, ordering))
+        chi = T.tt_round(chi, op_tol)[0]
+    else:
+        chi = T.tt_svd(spatial_to_sites(pb.indicator.astype(np.complex128), n, ordering), op_tol)
     ones = T.ones_tt([2] * d_sp)
     ctrl_a = (pb.C1 - pb.C0).astype(np.complex128).reshape(1, nc, nc, 1)
     ctrl_b = (pb.C2 - pb.C1).astype(np.complex128).reshape(1, nc, nc, 1)
     part_a = [ctrl_a] + T.identity_mpo([2] * d_sp)
     part_b = [ctrl_b] + T.diag_mpo_from_tt(chi)
     dC = T.mpo_add(part_a, part_b)
-    # Green operator: TT-SVD of G[(I J), bits...] in the momentum convention
-    G = green_dense(pb).reshape((nc * nc,) + shape).astype(np.complex128)
-    Gs = spatial_to_sites(G, n, ordering, momentum=True, lead=1)
-    g_tt = T.tt_svd(Gs, op_tol)
+    # Green operator in the momentum convention: TT-SVD of G[(I J), bits...]
+    # or TT-cross of its entries
+    if op_cross:
+        g_tt, _ = X.tt_cross(X.green_fn(pb, n, ordering), [nc * nc] + [2] * d_sp, op_tol, kick=4,
+                             max_half_sweeps=24)
+        g_tt = T.tt_round(g_tt, op_tol)[0]
+    else:
+        G = green_dense(pb).reshape((nc * nc,) + shape).astype(np.complex128)
+        Gs = spatial_to_sites(G, n, ordering, momentum=True, lead=1)
+        g_tt = T.tt_svd(Gs, op_tol)
     c0 = g_tt[0]
     gamma = [c0.reshape(1, nc, nc, c0.shape[2])] + T.diag_mpo_from_tt(g_tt[1:])
     # SFFT, one dimension at a time, embedded with identities elsewhere

@@ -163,3 +163,18 @@ def test_cross_boxes_fine_grid_with_seeds():
     rng = np.random.default_rng(0)
     idx = rng.integers(0, 2, (20000, 28))
     assert np.abs(T.tt_entries(cores, idx) - f(idx)).max() < 1e-10
+
+
+@pytest.mark.parametrize("kind", ["scalar", "elastic"])
+def test_ms_with_cross_operators_equals_dense_operators(kind):
+    """16 x 16 plane box: the QTT solve with the phase and Green trains built
+    by TT-cross gives the effective-tensor column of the TT-SVD-built ones."""
+    boxes = np.array([[0.5, 0.5, 0.5, 0.25, 0.25, 0.5]])
+    ind = I.boxes_indicator(boxes, (16, 16, 1))
+    pb = MS.scalar_problem(ind, 1.0, 10.0) if kind == "scalar" else MS.elastic_problem(ind, 1.0, 1.0, 10.0, 5.0)
+    E = np.zeros(pb.ncomp)
+    E[0] = 1.0
+    dense = MS.ms_qtt(pb, E, ops=MS.build_operators(pb), eps=1e-10, tol=1e-10, max_iter=200)
+    cross = MS.ms_qtt(pb, E, ops=MS.build_operators(pb, op_cross=True, boxes=boxes), eps=1e-10, tol=1e-10,
+                      max_iter=200)
+    assert np.abs(cross.sigma - dense.sigma).max() < 1e-8 * np.abs(dense.sigma).max()
