@@ -363,10 +363,11 @@ def qtt_mean_stress(pb: Problem, ops: QTTOperators, eps_tt) -> np.ndarray:
 
 def ms_qtt(pb: Problem, E, ops: QTTOperators | None = None, eps: float = 1e-8,
            max_rank: int | None = None, tol: float = 1e-10, max_iter: int = 50,
-           ordering: str = "interleaved", min_iter: int = 1, r0: int = 1) -> MSResult:
+           ordering: str = "interleaved", min_iter: int = 1, r0: int = 1, green_amen: bool = False) -> MSResult:
     """Algorithm 2 with operator application + SVD rounding after every step:
       tau = round(dC eps);  tau^ = S tau (three applications, each rounded);
-      eps^ = round(Gamma tau^);  eps_{m+1} = round(E - S^{-1} eps^);
+      eps^ = round(Gamma tau^) (or AMEn(Gamma, tau^), warm-started from the
+      previous iteration's eps^, with green_amen);  eps_{m+1} = round(E - S^{-1} eps^);
       stop when ||eps_{m+1} - eps_m|| / ||E 1|| < tol (after min_iter)."""
     if ops is None:
         ops = build_operators(pb, ordering)
@@ -382,13 +383,19 @@ def ms_qtt(pb: Problem, E, ops: QTTOperators | None = None, eps: float = 1e-8,
         return z
 
     it = 0
+    ghat = None
     for it in range(1, max_iter + 1):
         tau = rnd(T.tt_mpo_apply(ops.dC, x), "dC")
         h = tau
         for dim in range(3):
             if ops.qft[dim] is not None:
                 h = rnd(T.tt_mpo_apply(ops.qft[dim], h), "S%d" % dim)
-        h = rnd(T.tt_mpo_apply(ops.gamma, h), "G")
+        if green_amen:
+            from . import amen as AM
+            h, _ = AM.amen_mv(ops.gamma, h, eps, y0=ghat, seed=it)
+            ghat = h
+        else:
+            h = rnd(T.tt_mpo_apply(ops.gamma, h), "G")
         for dim in (2, 1, 0):
             if ops.qft_inv[dim] is not None:
                 h = rnd(T.tt_mpo_apply(ops.qft_inv[dim], h), "Si%d" % dim)

@@ -65,3 +65,16 @@ def test_amen_green_operator_on_polarisation_field():
     exact = T.tt_mpo_apply(ops.gamma, tau)
     y, info = AM.amen_mv(ops.gamma, tau, 1e-10)
     assert _rel(y, T.tt_full(exact)) < 1e-10
+
+
+def test_ms_with_amen_green_step_equals_rounded_product():
+    """4 x 4 x 2 random grid: Algorithm 2 with the Green step by AMEn
+    reaches the effective-tensor column of the rounded-product version."""
+    rng = np.random.default_rng(21)
+    ind = (rng.random((4, 4, 2)) < 0.3).astype(np.float64)
+    pb = MS.scalar_problem(ind, 1.0, 5.0)
+    E = np.array([1.0, 0.0, 0.0])
+    ops = MS.build_operators(pb)
+    a = MS.ms_qtt(pb, E, ops=ops, eps=1e-11, tol=1e-10, max_iter=300)
+    b = MS.ms_qtt(pb, E, ops=ops, eps=1e-11, tol=1e-10, max_iter=300, green_amen=True)
+    assert np.abs(a.sigma - b.sigma).max() < 1e-8 * np.abs(a.sigma).max()
