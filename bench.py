@@ -555,11 +555,40 @@ def oracle_sample(r, repeats=1):
     return time.perf_counter() - t0, fl
 
 
-def cpu_baseline(r):
-    sec, fl = oracle_sample(r)
-    return {"value": fl / sec / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one tt_add + SVD rounding of the d=30, r=%d pair (the first of the step's three roundings), "
-                      "NumPy FP64 with its threaded BLAS" % r, "seconds": sec}
+def single_core_sample(r, budget_s=10.0):
+    """The same oracle sample with the BLAS pinned to one thread (a child
+    process, so the thread count is fixed before NumPy loads its BLAS):
+    returns (seconds, model flops, repetitions) or None."""
+    code = ("import sys, time, math; sys.path.insert(0, %r); import bench; "
+            "s, f = bench.oracle_sample(%d); n = max(1, int(math.ceil(%f / max(s, 1e-3)))); "
+            "s, f = bench.oracle_sample(%d, n); print(s, f, n)" % (ROOT, r, budget_s, r))
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=6 * budget_s + 60)
+        s, f, n = out.stdout.split()[-3:]
+        return float(s), float(f), int(n)
+    except Exception:  # noqa: BLE001
+        return None
+
+
+def cpu_baseline(r, budget_s=10.0):
+    """The oracle timed on the host cores: a calibration run, then as many
+    repetitions of the sample as fill about budget_s seconds; and the same
+    with one BLAS thread."""
+    s1, _ = oracle_sample(r)
+    reps = max(1, int(math.ceil(budget_s / max(s1, 1e-3))))
+    sec, fl = oracle_sample(r, reps)
+    out = {"value": fl / sec / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "%d repetitions of one tt_add + SVD rounding of the d=30, r=%d pair (the first of the "
+                     "step's three roundings), NumPy FP64 with its threaded BLAS" % (reps, r), "seconds": sec}
+    one = single_core_sample(r, budget_s)
+    if one is not None:
+        out["single_core"] = {"value": one[1] / one[0] / 1e12, "unit": "TFLOP/s", "cores": 1,
+                              "repetitions": one[2], "seconds": one[0]}
+    return out
 
 
 def aggregate(ms: float, flops: float):
