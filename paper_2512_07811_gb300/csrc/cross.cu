@@ -5,7 +5,13 @@
 // bookkeeping.  The sweep itself is driven from the host (capi.cu).
 #include <limits.h>
 
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
+#include "engine.h"
 #include "kernels.h"
 
 namespace {
@@ -345,3 +351,244 @@ template int qtt_cross_eval<double>(const CrossFn&, int, int, const uint8_t*, in
 template size_t qtt_maxvol_smem<double>(int, int);
 template int qtt_maxvol<double>(zc*, int, int, int*, double, int, int*, cudaStream_t);
 template int qtt_cross_gather<double>(const zc*, int64_t, const int*, int, int64_t, int, zc*, cudaStream_t);
+
+#define TRY(expr)                  \
+  do {                             \
+    int _st = (expr);              \
+    if (_st != QTT_OK) return _st; \
+  } while (0)
+
+// ------------------------------------------------------------ TT-cross
+// Rank-adaptive two-site TT-cross (Sec. 3 operator setup; Oseledets &
+// Tyrtyshnikov, two-site form of Savostyanov & Oseledets).  Index sets live
+// on the device as byte rows: I[k] holds rI[k] left rows of k site values
+// (sites 0..k-1), J[k] holds rJ[k] right rows of d-k values (sites k..d-1).
+// A forward half-sweep samples at bond k (sites k, k+1) the superblock
+// S = f(I[k], i, j, J[k+2]), keeps the leading left singular vectors whose
+// tail is at most eps ||S|| / sqrt(d-1), appends `kick` Gaussian columns,
+// picks their maximum-volume rows, which give I[k+1] and the interpolation
+// core A A[rows]^-1; at the last bond core d-1 is S[rows, :].  A backward
+// half-sweep does the same on S^H, giving J[k+1], the cores
+// (A A[rows]^-1)^H and at bond 0 core 0 = S[:, rows].
+static uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Site values (position convention) of the voxel holding each box centre:
+// starting points inside the phase-2 region, which random points may miss.
+std::vector<std::vector<uint8_t>> box_seeds(const SiteMap& m, const double* boxes, int nboxes) {
+  std::vector<std::vector<uint8_t>> out;
+  for (int b = 0; b < nboxes; ++b) {
+    int64_t x[3];
+    for (int a = 0; a < 3; ++a) {
+      const int64_t N = (int64_t)1 << m.nb[a];
+      double cf = boxes[6 * b + a] - floor(boxes[6 * b + a]);
+      x[a] = std::min<int64_t>((int64_t)(cf * (double)N), N - 1);
+    }
+    std::vector<uint8_t> p(m.d);
+    for (int q = 0; q < m.d; ++q) p[q] = (uint8_t)((x[m.dim[q]] >> (m.nb[m.dim[q]] - 1 - m.pos[q])) & 1);
+    out.push_back(p);
+  }
+  return out;
+}
+
+static int cross_dev(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, double eps, int max_rank, int kick,
+              int max_half_sweeps, uint64_t seed, const std::vector<std::vector<uint8_t>>& seeds, qtt_tt** out,
+              CrossOut* st) {
+  const int d = (int)modes.size();
+  for (int k = 0; k < d; ++k)
+    if (modes[k] < 1 || modes[k] > 255) return QTT_ERR_ARG;
+  int s = 0;
+  if (d == 1) {
+    qtt_tt* y = tt_alloc(c, 1, modes, std::vector<int>{1, 1}, QTT_C128, &s);
+    if (!y) return s;
+    c->launches++;
+    s = qtt_cross_eval<double>(f, 1, 0, nullptr, 1, nullptr, 1, modes[0], 1, 0, core_ptr<zc>(y, 0), c->stream);
+    if (s) {
+      tt_free(y);
+      return s;
+    }
+    st->evaluations = modes[0];
+    *out = y;
+    return QTT_OK;
+  }
+  // initial right index sets: the suffixes of 8 random points and of the
+  // caller's seed points, duplicates removed
+  const int npts = 8;
+  uint64_t rs = seed ^ 0x5DEECE66Dull;
+  std::vector<std::vector<uint8_t>> pts(npts, std::vector<uint8_t>(d));
+  for (auto& p : pts)
+    for (int k = 0; k < d; ++k) p[k] = (uint8_t)(splitmix64(rs) % (uint64_t)modes[k]);
+  for (const auto& p : seeds)
+    if ((int)p.size() == d) pts.push_back(p);
+  std::vector<DBuf> I(d + 1), J(d + 1);
+  std::vector<int> rI(d + 1, 1), rJ(d + 1, 1);
+  for (int k = 1; k < d; ++k) {
+    std::vector<std::vector<uint8_t>> rows;
+    for (auto& p : pts) rows.emplace_back(p.begin() + k, p.end());
+    std::sort(rows.begin(), rows.end());
+    rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+    std::vector<uint8_t> flat;
+    for (auto& r : rows) flat.insert(flat.end(), r.begin(), r.end());
+    TRY(J[k].alloc(c, flat.size()));
+    TRY(upload(c, J[k].p, flat.data(), flat.size()));
+    rJ[k] = (int)rows.size();
+  }
+  DBuf scal, pivb, Zb;
+  TRY(scal.alloc(c, 64));
+  double* dscal = scal.as<double>();
+  int* dint = reinterpret_cast<int*>(dscal + 4);
+  std::vector<DBuf> cores(d);
+  struct Held {
+    qtt_tt* p = nullptr;
+    ~Held() {
+      if (p) tt_free(p);
+    }
+  } held;   // the train of the previous half-sweep
+  qtt_tt*& prev = held.p;
+  uint64_t gauss_stream = 1;
+  const double sq = sqrt((double)(d - 1));
+  int h = 0;
+  double rel = INFINITY;
+  for (h = 1; h <= std::max(2, max_half_sweeps); ++h) {
+    const bool fwd = (h & 1) == 1;
+    for (int step = 0; step < d - 1; ++step) {
+      const int k = fwd ? step : d - 2 - step;
+      const int rl = rI[k], rr = rJ[k + 2], n0 = modes[k], n1 = modes[k + 1];
+      const int64_t rows = (int64_t)rl * n0, cols = (int64_t)n1 * rr;
+      DBuf S;
+      TRY(S.alloc(c, (size_t)rows * cols * sizeof(zc)));
+      c->launches++;
+      TRY(qtt_cross_eval<double>(f, d, k, I[k].as<uint8_t>(), rl, J[k + 2].as<uint8_t>(), rr, n0, n1, fwd ? 0 : 1,
+                                 S.as<zc>(), c->stream));
+      st->evaluations += rows * cols;
+      // basis side: rows of S (forward) or of S^H (backward)
+      const int64_t M = fwd ? rows : cols, Nn = fwd ? cols : rows;
+      c->launches++;
+      TRY(qtt_sumsq<double>(S.as<zc>(), rows * cols, dscal, c->stream));
+      double n2 = 0;
+      TRY(sync_read(c, &n2, dscal, sizeof(double)));
+      int t = 0;
+      DBuf U, sig;
+      int64_t nsv = 0;
+      if (n2 > 0) {
+        const int64_t p = std::min(M, Nn);
+        TRY(U.alloc(c, (size_t)M * p * sizeof(zc)));
+        TRY(sig.alloc(c, (size_t)p * sizeof(double)));
+        TRY(left_svd<double>(c, S.as<zc>(), M, Nn, Nn, U.as<zc>(), sig.as<double>(), &nsv));
+        c->launches++;
+        TRY(qtt_trunc_rank<double>(sig.as<double>(), (int)nsv, eps * sqrt(n2) / sq, max_rank, dint,
+                                   dscal + 1, c->stream));
+        TRY(sync_read(c, &t, dint, sizeof(int)));
+      }
+      // a zero superblock keeps only random directions (exploration)
+      const int tk = (int)std::min<int64_t>(std::max(t + kick, 1), M);
+      DBuf A;
+      TRY(A.alloc(c, (size_t)M * tk * sizeof(zc)));
+      if (t > 0) {
+        c->launches++;
+        TRY(qtt_copy_strided<double>(U.as<zc>(), MIdx{M, 1, nsv, 0}, MIdx{t, 1, 1, 0}, M, t, 0, A.as<zc>(), tk,
+                                     c->stream));
+      }
+      if (tk > t) {
+        const int e = tk - t;
+        TRY(Zb.alloc(c, (size_t)M * e * sizeof(zc)));
+        c->launches += 2;
+        TRY(qtt_fill_gaussian<double>(Zb.as<zc>(), M * e, seed, gauss_stream++, 1.0, c->stream));
+        TRY(qtt_copy_strided<double>(Zb.as<zc>(), MIdx{M, 1, e, 0}, MIdx{e, 1, 1, 0}, M, e, 0, A.as<zc>() + t, tk,
+                                     c->stream));
+      }
+      TRY(pivb.alloc(c, (size_t)tk * sizeof(int)));
+      cudaMemsetAsync(dint + 2, 0, sizeof(int), c->stream);
+      c->launches++;
+      TRY(qtt_maxvol<double>(A.as<zc>(), (int)M, tk, pivb.as<int>(), 1.05, 100, dint + 2, c->stream));
+      int mvst = 0;
+      TRY(sync_read(c, &mvst, dint + 2, sizeof(int)));
+      if (mvst == 1) return QTT_ERR_RANK;
+      if (mvst < 2) return QTT_ERR_CUDA;
+      if (fwd) {
+        cores[k] = std::move(A);
+        DBuf In;
+        TRY(In.alloc(c, (size_t)tk * (k + 1)));
+        c->launches++;
+        TRY(qtt_cross_left_index(I[k].as<uint8_t>(), k, n0, pivb.as<int>(), tk, In.as<uint8_t>(), c->stream));
+        I[k + 1] = std::move(In);
+        rI[k + 1] = tk;
+        if (k == d - 2) {
+          TRY(cores[d - 1].alloc(c, (size_t)tk * cols * sizeof(zc)));
+          c->launches++;
+          TRY(qtt_cross_gather<double>(S.as<zc>(), cols, pivb.as<int>(), tk, cols, 0, cores[d - 1].as<zc>(),
+                                       c->stream));
+        }
+      } else {
+        DBuf Cn;
+        TRY(Cn.alloc(c, (size_t)tk * M * sizeof(zc)));
+        c->launches++;
+        TRY(qtt_copy_strided<double>(A.as<zc>(), MIdx{tk, 1, 1, 0}, MIdx{M, 1, tk, 0}, tk, M, 1, Cn.as<zc>(), M,
+                                     c->stream));
+        cores[k + 1] = std::move(Cn);
+        DBuf Jn;
+        TRY(Jn.alloc(c, (size_t)tk * (d - k - 1)));
+        c->launches++;
+        TRY(qtt_cross_right_index(J[k + 2].as<uint8_t>(), d - k - 2, rr, pivb.as<int>(), tk, Jn.as<uint8_t>(),
+                                  c->stream));
+        J[k + 1] = std::move(Jn);
+        rJ[k + 1] = tk;
+        if (k == 0) {
+          // core 0 (1, n0, tk): S[i, piv[a]] = conj(S^H[piv[a], i])
+          TRY(cores[0].alloc(c, (size_t)rows * tk * sizeof(zc)));
+          c->launches++;
+          TRY(qtt_cross_gather<double>(S.as<zc>(), rows, pivb.as<int>(), tk, rows, 1, cores[0].as<zc>(),
+                                       c->stream));
+        }
+      }
+    }
+    std::vector<int> r(d + 1, 1);
+    for (int k = 1; k < d; ++k) r[k] = fwd ? rI[k] : rJ[k];
+    qtt_tt* y = tt_alloc(c, d, modes, r, QTT_C128, &s);
+    if (!y) return s;
+    for (int k = 0; k < d; ++k)
+      cudaMemcpyAsync(core_ptr<char>(y, k), cores[k].p, (size_t)r[k] * modes[k] * r[k + 1] * sizeof(zc),
+                      cudaMemcpyDeviceToDevice, c->stream);
+    st->max_rank = *std::max_element(r.begin(), r.end());
+    st->half_sweeps = h;
+    if (prev) {
+      qtt_tt* diff = nullptr;
+      double nd = 0, ny = 0;
+      s = add_dev<double>(c, zc(1, 0), y, zc(-1, 0), prev, &diff);
+      if (!s) s = norm_dev<double>(c, diff, &nd);
+      if (diff) tt_free(diff);
+      if (!s) s = norm_dev<double>(c, y, &ny);
+      tt_free(prev);
+      prev = nullptr;
+      if (s) {
+        tt_free(y);
+        return s;
+      }
+      rel = ny > 0 ? nd / ny : 0.0;
+    }
+    prev = y;
+    st->rel_change = rel;
+    if (h >= 2 && rel <= 10.0 * eps) break;
+  }
+  *out = prev;
+  prev = nullptr;
+  return QTT_OK;
+}
+
+// TT-cross, then an FP64 SVD rounding at eps (the interpolation ranks carry
+// the kick columns and some redundancy).
+int cross_rounded(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, double eps, int max_rank, int kick,
+                  int max_half_sweeps, uint64_t seed, const std::vector<std::vector<uint8_t>>& seeds, qtt_tt** out,
+                  CrossOut* st) {
+  qtt_tt* x = nullptr;
+  TRY(cross_dev(c, f, modes, eps, max_rank, kick, max_half_sweeps, seed, seeds, &x, st));
+  qtt_round_info ri;
+  int s = round_det<double>(c, x, eps, 0, nullptr, &ri, out);
+  tt_free(x);
+  return s;
+}
+

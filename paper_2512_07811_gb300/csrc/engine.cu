@@ -1182,6 +1182,85 @@ int round_det_batch(qtt_ctx* c, int B, const qtt_tt* const* xs, double eps, int 
 template int round_det_batch<double>(qtt_ctx*, int, const qtt_tt* const*, double, int, qtt_round_info*, qtt_tt**);
 template int round_det_batch<float>(qtt_ctx*, int, const qtt_tt* const*, double, int, qtt_round_info*, qtt_tt**);
 
+// -------------------------------------------------------------- TT sum
+// z = a x + b y: block-diagonal placement of the cores (ranks add; a and b
+// scale the first core's blocks).
+template <class R>
+int add_dev(qtt_ctx* c, cplx<R> a, const qtt_tt* x, cplx<R> b, const qtt_tt* y, qtt_tt** out) {
+  const int d = x->d;
+  std::vector<int> r(d + 1, 1);
+  for (int k = 1; k < d; ++k) r[k] = x->r[k] + y->r[k];
+  int st;
+  qtt_tt* z = tt_alloc(c, d, x->n, r, x->dtype, &st);
+  if (!z) return st;
+  cudaMemsetAsync(z->data, 0, z->bytes, c->stream);
+  typedef cplx<R> C;
+  const C one(1, 0);
+  for (int k = 0; k < d; ++k) {
+    const int64_t n = x->n[k];
+    const int64_t xa = x->r[k], xb = x->r[k + 1], ya = y->r[k], yb = y->r[k + 1];
+    C* Z = core_ptr<C>(z, k);
+    const int64_t zb = r[k + 1];
+    if (d == 1) {
+      // z = a x + b y elementwise (single core)
+      c->launches += 2;
+      int s1 = qtt_place_block<R>(core_ptr<C>(x, 0), 1, n, 1, Z, 1, 0, 0, a, c->stream);
+      if (s1) {
+        tt_free(z);
+        return s1;
+      }
+      // accumulate b*y with a rank-1 GEMM: Z (1 x n) += b * [1] (1 x 1) * y (1 x n)
+      void* onep;
+      if (dalloc(c, &onep, sizeof(C))) {
+        tt_free(z);
+        return QTT_ERR_OOM;
+      }
+      cudaMemcpyAsync(onep, &one, sizeof(C), cudaMemcpyHostToDevice, c->stream);
+      GemmDesc g;
+      g.bA = g.bB = g.bC = MIdx{1, 1, 0, 0};
+      g.M = 1;
+      g.N = n;
+      g.K = 1;
+      g.batch = 1;
+      g.mA = MIdx{1, 1, 1, 0};
+      g.kA = MIdx{1, 1, 1, 0};
+      g.kB = MIdx{1, 1, n, 0};
+      g.nB = MIdx{n, 1, 1, 0};
+      g.mC = MIdx{1, 1, n, 0};
+      g.nC = MIdx{n, 1, 1, 0};
+      g.conjA = g.conjB = 0;
+      int s2 = qtt_gemm<R>(g, b, one, reinterpret_cast<C*>(onep), core_ptr<C>(y, 0), Z, c->stream);
+      dfree(c, onep);
+      if (s2) {
+        tt_free(z);
+        return s2;
+      }
+      break;
+    }
+    const int64_t xoff0 = 0, xoff1 = 0;
+    const int64_t yoff0 = (k == 0) ? 0 : xa;
+    const int64_t yoff1 = (k == d - 1) ? 0 : xb;
+    c->launches += 2;
+    int s1 = qtt_place_block<R>(core_ptr<C>(x, k), xa, n, xb, Z, zb, xoff0, xoff1, k == 0 ? a : one, c->stream);
+    int s2 = qtt_place_block<R>(core_ptr<C>(y, k), ya, n, yb, Z, zb, yoff0, yoff1, k == 0 ? b : one, c->stream);
+    if (s1 || s2) {
+      tt_free(z);
+      return s1 ? s1 : s2;
+    }
+  }
+  *out = z;
+  return QTT_OK;
+}
+
+template int add_dev<double>(qtt_ctx*, zc, const qtt_tt*, zc, const qtt_tt*, qtt_tt**);
+template int add_dev<float>(qtt_ctx*, cc, const qtt_tt*, cc, const qtt_tt*, qtt_tt**);
+
+// host -> device copy on the context stream, then wait for it
+int upload(qtt_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return QTT_ERR_CUDA;
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
 // ------------------------------------------------------------------- TT-SVD
 template <class R>
 int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* dense, double eps, int max_rank,

@@ -141,6 +141,25 @@ template <class R>
 int gemm_ab(qtt_ctx* c, const GemmDesc& g, cplx<R> alpha, cplx<R> beta, const cplx<R>* A, const cplx<R>* B,
             cplx<R>* C);
 
+// z = a x + b y (ranks add) and a synchronous host -> device copy (engine.cu)
+template <class R>
+int add_dev(qtt_ctx* c, cplx<R> a, const qtt_tt* x, cplx<R> b, const qtt_tt* y, qtt_tt** out);
+int upload(qtt_ctx* c, void* dst, const void* src, size_t bytes);
+
+// TT-cross (cross.cu): the sweep with an FP64 rounding of the result at eps;
+// seeds are extra starting points (site values) for the right index sets
+struct CrossOut {
+  int half_sweeps = 0;
+  int64_t evaluations = 0;
+  double rel_change = 0.0;
+  int max_rank = 1;
+};
+int cross_rounded(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, double eps, int max_rank, int kick,
+                  int max_half_sweeps, uint64_t seed, const std::vector<std::vector<uint8_t>>& seeds, qtt_tt** out,
+                  CrossOut* st);
+// the voxel of every box centre as site values (position convention)
+std::vector<std::vector<uint8_t>> box_seeds(const SiteMap& m, const double* boxes, int nboxes);
+
 // AMEn y ~ A x (amen.cu)
 template <class R>
 int amen_mv_dev(qtt_ctx* c, const qtt_mpo* A, const qtt_tt* x, const qtt_tt* y0, double eps, int kick,
