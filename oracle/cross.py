@@ -32,6 +32,13 @@ of sampled two-site blocks:
   the voxels holding the box centres, box_centre_points: points inside the
   phase-2 region, which random points may all miss).
 
+The sampled operands: the Green operator train (momentum convention), the
+phase indicator of a union of axis-aligned boxes, and the phase indicator of
+a union of ellipsoids (spheres, random ellipsoids and aligned fibres, the
+geometries of the 3D workloads), each a pointwise function of the site
+values pinned entry by entry to the dense voxelisation of the input
+generators.
+
 maxvol (Goreinov, Oseledets, Savostyanov et al. 2010): start from the rows of
 Gaussian elimination with partial pivoting, then, while some entry of
 B = A A[rows]^-1 exceeds `tol` in modulus, replace the row of its column by
@@ -203,4 +210,30 @@ def boxes_fn(boxes, nb, ordering: str = "interleaved"):
     def f(idx):
         x = _site_bits(np.asarray(idx), nb, ordering, momentum=False)
         return IN.boxes_value(boxes, x[0], x[1], x[2], shape)
+    return f
+
+
+def ellipsoid_centre_points(rows, nb, ordering: str = "interleaved") -> np.ndarray:
+    """Site values (position convention) of the voxel holding each ellipsoid
+    centre (rows as in inputs.ellipsoids_value)."""
+    rows = np.asarray(rows, dtype=np.float64).reshape(-1, IN.ELLIPSOID_ROW)
+    pts = np.zeros((rows.shape[0], sum(nb)), dtype=np.int64)
+    for i, e in enumerate(rows):
+        for dim in range(3):
+            N = 1 << nb[dim]
+            x = min(int((e[dim] - math.floor(e[dim])) * N), N - 1)
+            for a, s in enumerate(MS.dim_positions(nb, ordering, dim)):
+                pts[i, s] = (x >> (nb[dim] - 1 - a)) & 1
+    return pts
+
+
+def ellipsoids_fn(rows, nb, ordering: str = "interleaved"):
+    """Entries of the phase indicator train of a union of ellipsoids (spheres,
+    random ellipsoids, fibres with an infinite semi-axis), position
+    convention, spatial sites only."""
+    shape = tuple(1 << b for b in nb)
+
+    def f(idx):
+        x = _site_bits(np.asarray(idx), nb, ordering, momentum=False)
+        return IN.ellipsoids_value(rows, x[0], x[1], x[2], shape)
     return f

@@ -290,12 +290,14 @@ class QTTOperators:
 
 
 def build_operators(pb: Problem, ordering: str = "interleaved", op_tol: float = 1e-10,
-                    qft_tol: float = 1e-12, op_cross: bool = False, boxes=None) -> QTTOperators:
+                    qft_tol: float = 1e-12, op_cross: bool = False, boxes=None,
+                    ellipsoids=None) -> QTTOperators:
     """The operator trains of Algorithm 2.  By default the phase indicator
     and the Green operator are compressed from their dense arrays (TT-SVD);
     op_cross samples the Green operator by TT-cross instead (Sec. 3), and a
-    box list (rows cx, cy, cz, hx, hy, hz) samples the phase indicator by
-    TT-cross; both crosses are rounded at op_tol."""
+    box list (rows cx, cy, cz, hx, hy, hz) or an ellipsoid list (rows as in
+    inputs.ellipsoids_value) samples the phase indicator by TT-cross; every
+    cross is rounded at op_tol."""
     from . import cross as X
     shape = grid_shape(pb)
     n = grid_bits(shape)
@@ -304,6 +306,10 @@ def build_operators(pb: Problem, ordering: str = "interleaved", op_tol: float = 
     if boxes is not None:
         chi, _ = X.tt_cross(X.boxes_fn(boxes, n, ordering), [2] * d_sp, op_tol, kick=8, init_rank=8,
                             max_half_sweeps=24, init_points=X.box_centre_points(boxes, n, ordering))
+        chi = T.tt_round(chi, op_tol)[0]
+    elif ellipsoids is not None:
+        chi, _ = X.tt_cross(X.ellipsoids_fn(ellipsoids, n, ordering), [2] * d_sp, op_tol, kick=8, init_rank=8,
+                            max_half_sweeps=24, init_points=X.ellipsoid_centre_points(ellipsoids, n, ordering))
         chi = T.tt_round(chi, op_tol)[0]
     else:
         chi = T.tt_svd(spatial_to_sites(pb.indicator.astype(np.complex128), n, ordering), op_tol)

@@ -150,6 +150,83 @@ def sphere_indicator(N: int, volume_fraction: float = 0.2,
     return ((dx * dx + dy * dy + dz * dz) <= R * R).astype(np.float64)
 
 
+# Ellipsoid rows: (cx, cy, cz, a0, a1, a2, R00, R01, R02, R10, R11, R12, R20,
+# R21, R22) -- centre, semi-axes and the rotation R (row-major) whose column i
+# is the direction of semi-axis i.  A semi-axis may be +inf (a cylinder along
+# that direction: a fibre).  Spheres, random ellipsoids and aligned fibres
+# all use this one description and the one voxelisation rule below.
+ELLIPSOID_ROW = 15
+
+
+def ellipsoids_value(rows, ix, iy, iz, shape) -> np.ndarray:
+    """Phase value (0.0 / 1.0) at voxels (ix, iy, iz) (integer arrays of one
+    shape) of an (Nx, Ny, Nz) grid for a union of ellipsoids (rows as above):
+    with the voxel centre c_j = (i_j + 1/2)/N_j, the periodic offsets
+    D_j = (c_j - centre_j) - round(c_j - centre_j) (round half to even), the
+    body-frame coordinates u_i = (R[0, i] D_0 + R[1, i] D_1) + R[2, i] D_2 and
+    t_i = u_i / a_i, a voxel is in phase 2 when
+    (t_0 t_0 + t_1 t_1) + t_2 t_2 <= 1 for some row.  Every operation is one
+    IEEE double operation in exactly this order (no fused multiply-add), so
+    any implementation that follows it voxelises bit for bit alike."""
+    rows = np.asarray(rows, dtype=np.float64).reshape(-1, ELLIPSOID_ROW)
+    idx = [np.asarray(ix), np.asarray(iy), np.asarray(iz)]
+    cen = [(idx[a].astype(np.float64) + 0.5) / shape[a] for a in range(3)]
+    out = np.zeros(np.broadcast(*idx).shape, dtype=bool)
+    for e in rows:
+        D = []
+        for a in range(3):
+            t = cen[a] - e[a]
+            D.append(t - np.round(t))
+        R = e[6:15].reshape(3, 3)
+        s = None
+        for i in range(3):
+            u = R[0, i] * D[0] + R[1, i] * D[1]
+            u = u + R[2, i] * D[2]
+            t = u / e[3 + i]
+            s = t * t if s is None else s + t * t
+        out |= s <= 1.0
+    return out.astype(np.float64)
+
+
+def ellipsoids_indicator(rows, shape) -> np.ndarray:
+    """The union of ellipsoids voxelised on the whole (Nx, Ny, Nz) grid (see ellipsoids_value)."""
+    ix, iy, iz = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    return ellipsoids_value(rows, ix, iy, iz, shape)
+
+
+def sphere_rows(volume_fraction: float = 0.2, centre=(0.5, 0.5, 0.5)) -> np.ndarray:
+    """One sphere of the given continuum volume fraction as an ellipsoid row."""
+    R = sphere_radius(volume_fraction)
+    return np.array([[centre[0], centre[1], centre[2], R, R, R, 1, 0, 0, 0, 1, 0, 0, 0, 1]], dtype=np.float64)
+
+
+def fibre_rows(rng: np.random.Generator, count: int = 32, fibre_fraction: float = 0.3,
+               max_tries: int = 100000) -> np.ndarray:
+    """`count` aligned cylindrical fibres (axis along z), non-overlapping under
+    the periodic minimum-image distance, radius sqrt(fraction / (count pi)) so
+    that they fill `fibre_fraction` of the cell, as ellipsoid rows with an
+    infinite third semi-axis."""
+    radius = math.sqrt(fibre_fraction / (count * math.pi))
+    centres = []
+    for _ in range(max_tries):
+        if len(centres) == count:
+            break
+        p = rng.uniform(0.0, 1.0, size=2)
+        ok = True
+        for q in centres:
+            d = p - q
+            d -= np.round(d)
+            if d @ d < (2.0 * radius) ** 2:
+                ok = False
+                break
+        if ok:
+            centres.append(p)
+    if len(centres) < count:
+        raise RuntimeError("fibre_rows: could not place all fibres")
+    return np.array([[p[0], p[1], 0.5, radius, radius, math.inf, 1, 0, 0, 0, 1, 0, 0, 0, 1] for p in centres],
+                    dtype=np.float64)
+
+
 def _random_rotation(rng: np.random.Generator) -> np.ndarray:
     """Uniform random rotation from a uniform unit quaternion."""
     q = rng.normal(size=4)
@@ -167,7 +244,7 @@ def _periodic_delta(c: np.ndarray, centre: float) -> np.ndarray:
     return d - np.round(d)
 
 
-def ellipsoid_rve(N: int, rng: np.random.Generator, max_tries: int = 400):
+def ellipsoid_rve_rows(N: int, rng: np.random.Generator, max_tries: int = 400):
     """Random RVE of 1..8 non-overlapping, randomly oriented ellipsoids.
 
     The count is drawn from 1..8, the semi-axes from U[0.05, 0.2] (units of
@@ -177,41 +254,43 @@ def ellipsoid_rve(N: int, rng: np.random.Generator, max_tries: int = 400):
     as specified, 1-8 such ellipsoids rarely reach the required fraction of
     0.1-0.3).  An ellipsoid that overlaps an earlier one on the voxel grid
     (periodic) is redrawn; the whole RVE is redrawn until the voxel phase
-    fraction lies in [0.1, 0.3].  Returns (indicator, contrast) with the
-    contrast log-uniform in [5, 100].
+    fraction lies in [0.1, 0.3].  Returns (rows, indicator, contrast): the
+    ellipsoid rows, their voxelisation on the N^3 grid (ellipsoids_value) and
+    the contrast, log-uniform in [5, 100].
     """
-    c = voxel_centres(N)
+    shape = (N, N, N)
+    ix, iy, iz = np.meshgrid(*[np.arange(N)] * 3, indexing="ij")
     for _ in range(max_tries):
         count = int(rng.integers(1, 9))
         f = rng.uniform(0.12, 0.28)
         axes_all = rng.uniform(0.05, 0.2, size=(count, 3))
         vol = float(np.sum(4.0 / 3.0 * math.pi * np.prod(axes_all, axis=1)))
         axes_all *= (f / vol) ** (1.0 / 3.0)
-        ind = np.zeros((N, N, N), dtype=bool)
-        placed = 0
+        ind = np.zeros(shape, dtype=bool)
+        rows = []
         for e in range(count):
             axes = axes_all[e]
             for _ in range(50):
                 rot = _random_rotation(rng)
                 ctr = rng.uniform(0.0, 1.0, size=3)
-                dx = _periodic_delta(c, ctr[0])[:, None, None]
-                dy = _periodic_delta(c, ctr[1])[None, :, None]
-                dz = _periodic_delta(c, ctr[2])[None, None, :]
-                # body-frame coordinates u = rot^T (x - c)
-                u0 = rot[0, 0] * dx + rot[1, 0] * dy + rot[2, 0] * dz
-                u1 = rot[0, 1] * dx + rot[1, 1] * dy + rot[2, 1] * dz
-                u2 = rot[0, 2] * dx + rot[1, 2] * dy + rot[2, 2] * dz
-                inside = (u0 / axes[0]) ** 2 + (u1 / axes[1]) ** 2 + (u2 / axes[2]) ** 2 <= 1.0
+                row = np.concatenate([ctr, axes, rot.reshape(-1)])
+                inside = ellipsoids_value(row, ix, iy, iz, shape) > 0
                 if np.any(inside & ind):
                     continue
                 ind |= inside
-                placed += 1
+                rows.append(row)
                 break
         frac = ind.mean()
-        if placed == count and 0.1 <= frac <= 0.3:
+        if len(rows) == count and 0.1 <= frac <= 0.3:
             contrast = float(np.exp(rng.uniform(np.log(5.0), np.log(100.0))))
-            return ind.astype(np.float64), contrast
+            return np.array(rows), ind.astype(np.float64), contrast
     raise RuntimeError("ellipsoid_rve: no admissible draw")
+
+
+def ellipsoid_rve(N: int, rng: np.random.Generator, max_tries: int = 400):
+    """The RVE of ellipsoid_rve_rows as (indicator, contrast)."""
+    _, ind, contrast = ellipsoid_rve_rows(N, rng, max_tries)
+    return ind, contrast
 
 
 def fibre_rve(N: int, rng: np.random.Generator, count: int = 32,

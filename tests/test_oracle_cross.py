@@ -178,3 +178,84 @@ def test_ms_with_cross_operators_equals_dense_operators(kind):
     cross = MS.ms_qtt(pb, E, ops=MS.build_operators(pb, op_cross=True, boxes=boxes), eps=1e-10, tol=1e-10,
                       max_iter=200)
     assert np.abs(cross.sigma - dense.sigma).max() < 1e-8 * np.abs(dense.sigma).max()
+
+
+def _ellipsoid_sets():
+    rows, _, _ = I.ellipsoid_rve_rows(16, np.random.default_rng(11))
+    return {"sphere": I.sphere_rows(0.2), "ellipsoids": rows,
+            "fibres": I.fibre_rows(np.random.default_rng(5), count=6, fibre_fraction=0.3)}
+
+
+@pytest.mark.parametrize("which", ["sphere", "ellipsoids", "fibres"])
+def test_ellipsoid_voxelisation_equals_quadratic_form(which):
+    """The ellipsoid rule (body-frame coordinates divided by the semi-axes)
+    against the quadratic form D^T R diag(1/a^2) R^T D <= 1 written out
+    independently, on every voxel not within rounding of the boundary; the
+    sphere and the fibres also against their plain distance tests."""
+    rows = _ellipsoid_sets()[which]
+    N = 32
+    shape = (N, N, N)
+    ind = I.ellipsoids_indicator(rows, shape)
+    c = (np.arange(N) + 0.5) / N
+    inside = np.zeros(shape, dtype=bool)
+    near = np.zeros(shape, dtype=bool)
+    for e in rows:
+        R = e[6:15].reshape(3, 3)
+        M = R @ np.diag(1.0 / e[3:6] ** 2) @ R.T
+        D = [c - e[a] for a in range(3)]
+        D = [t - np.round(t) for t in D]
+        g = np.stack(np.meshgrid(*D, indexing="ij"), axis=-1)
+        q = np.einsum("...i,ij,...j->...", g, M, g)
+        inside |= q <= 1.0
+        near |= np.abs(q - 1.0) < 1e-9
+    assert np.array_equal(ind[~near] > 0, inside[~near])
+    if which == "sphere":
+        np.testing.assert_array_equal(ind, I.sphere_indicator(N, 0.2))
+    if which == "fibres":
+        np.testing.assert_array_equal(ind, I.fibre_rve(N, np.random.default_rng(5), count=6, fibre_fraction=0.3))
+
+
+@pytest.mark.parametrize("nb,ordering", [((3, 2, 3), "interleaved"), ((2, 3, 3), "grouped")])
+@pytest.mark.parametrize("which", ["sphere", "ellipsoids", "fibres"])
+def test_ellipsoids_sampler_equals_voxelisation(nb, ordering, which):
+    rows = _ellipsoid_sets()[which]
+    shape = tuple(1 << b for b in nb)
+    ref = MS.spatial_to_sites(I.ellipsoids_indicator(rows, shape), nb, ordering)
+    idx = np.array(list(itertools.product(*[range(2)] * sum(nb))))
+    vals = X.ellipsoids_fn(rows, nb, ordering)(idx)
+    np.testing.assert_array_equal(vals.reshape(ref.shape), ref)
+
+
+@pytest.mark.parametrize("which,ordering", [("sphere", "interleaved"), ("sphere", "grouped"),
+                                            ("ellipsoids", "grouped"), ("fibres", "interleaved")])
+def test_cross_ellipsoids_exact(which, ordering):
+    """The cross of an ellipsoid geometry reaches the exact voxel indicator."""
+    rows = _ellipsoid_sets()[which]
+    nb = (4, 4, 3)
+    shape = tuple(1 << b for b in nb)
+    ref = MS.spatial_to_sites(I.ellipsoids_indicator(rows, shape), nb, ordering)
+    cores, info = X.tt_cross(X.ellipsoids_fn(rows, nb, ordering), [2] * sum(nb), 1e-10, kick=8, init_rank=8,
+                             max_half_sweeps=24, init_points=X.ellipsoid_centre_points(rows, nb, ordering))
+    assert np.abs(T.tt_full(cores).reshape(ref.shape) - ref).max() < 1e-10
+
+
+def test_ellipsoid_centre_points_are_inside():
+    rows = _ellipsoid_sets()["ellipsoids"]
+    nb = (5, 5, 5)
+    for ordering in ["interleaved", "grouped"]:
+        pts = X.ellipsoid_centre_points(rows, nb, ordering)
+        assert np.all(X.ellipsoids_fn(rows, nb, ordering)(pts) == 1.0)
+
+
+def test_ms_with_cross_sphere_equals_dense_operators():
+    """8^3 sphere (scalar): the QTT solve with the phase train sampled by
+    TT-cross from the ellipsoid description gives the effective-tensor column
+    of the TT-SVD of the dense image."""
+    rows = I.sphere_rows(0.2)
+    ind = I.ellipsoids_indicator(rows, (8, 8, 8))
+    pb = MS.scalar_problem(ind, 1.0, 10.0)
+    E = np.array([1.0, 0.0, 0.0])
+    dense = MS.ms_qtt(pb, E, ops=MS.build_operators(pb, ordering="grouped"), eps=1e-9, tol=1e-8, max_iter=200)
+    cross = MS.ms_qtt(pb, E, ops=MS.build_operators(pb, ordering="grouped", ellipsoids=rows), eps=1e-9,
+                      tol=1e-8, max_iter=200)
+    assert np.abs(cross.sigma - dense.sigma).max() < 1e-7 * np.abs(dense.sigma).max()
