@@ -103,6 +103,12 @@ QTT_API int qtt_ctx_profile(qtt_ctx* ctx, int enable);
  * kernel ran) and model bytes.  Synchronises the stream. */
 QTT_API int qtt_ctx_profile_read(qtt_ctx* ctx, int kclass, double* total_ms, int64_t* launches, double* flops,
                                  double* bytes);
+/* Failure injection for tests of the error paths (not in the paper): after
+ * `n` more successful device allocations of this context, every allocation
+ * fails as if the device were out of memory, so the call in progress
+ * returns QTT_ERR_OOM after releasing what it holds.  n < 0 switches the
+ * injection off again.  Host-side only: no kernel is affected. */
+QTT_API int qtt_ctx_fail_alloc_after(qtt_ctx* ctx, int64_t n);
 
 /* --------------------------------------------------------------- trains */
 /* New train with the given modes (d entries) and ranks (d + 1 entries,
@@ -318,9 +324,21 @@ QTT_API int qtt_site_order(const int32_t* nbits_dim, int32_t interleaved, int32_
  *    voxel is in phase 2 (value 1) when, on every axis, the periodic distance
  *    |((c - cx + 1/2) mod 1) - 1/2| of its centre c = (x + 1/2) / N from some
  *    box centre is at most that box's half width.
+ *  QTT_CROSS_ELLIPSOIDS: the phase indicator of a union of ellipsoids (the
+ *    spheres, random ellipsoids and aligned fibres of the 3D workloads),
+ *    modes (2, ..., 2), position convention; rows of 15 doubles (cx, cy, cz,
+ *    a0, a1, a2, R00, R01, R02, R10, R11, R12, R20, R21, R22): the centre,
+ *    the semi-axes (+inf allowed: a cylinder, i.e. a fibre) and the rotation
+ *    R (row-major) whose column i is the direction of semi-axis i.  With the
+ *    voxel centre c = (x + 1/2) / N, the periodic offsets
+ *    D_j = (c_j - centre_j) - rint(c_j - centre_j) (half to even), the
+ *    body-frame coordinates u_i = (R[0][i] D_0 + R[1][i] D_1) + R[2][i] D_2
+ *    and t_i = u_i / a_i, a voxel is in phase 2 when
+ *    (t_0 t_0 + t_1 t_1) + t_2 t_2 <= 1 for some row, each operation an IEEE
+ *    double operation in that order.
  * The spatial sites are ordered as in qtt_rve (interleaved level by level,
  * or grouped by dimension). */
-typedef enum { QTT_CROSS_GREEN = 1, QTT_CROSS_BOXES = 2 } qtt_cross_kind;
+typedef enum { QTT_CROSS_GREEN = 1, QTT_CROSS_BOXES = 2, QTT_CROSS_ELLIPSOIDS = 3 } qtt_cross_kind;
 typedef struct {
   int32_t kind;          /* qtt_cross_kind                                                 */
   int32_t nbits_dim[3];  /* 2^nbits_dim[a] voxels along x, y, z: 0 to 20 each, 1 to 60 in all */
@@ -329,6 +347,8 @@ typedef struct {
   double k0, lam0, mu0;  /* GREEN: reference conductivity / Lame constants                 */
   const double* boxes;   /* BOXES: host, nboxes rows (cx, cy, cz, hx, hy, hz)             */
   int32_t nboxes;
+  const double* ellipsoids; /* ELLIPSOIDS: host, nellipsoids rows of 15 (see above)        */
+  int32_t nellipsoids;
 } qtt_cross_fn;
 
 typedef struct {
@@ -376,6 +396,11 @@ typedef struct {
   int32_t nboxes;
   int32_t op_cross;     /* 1: build the Green operator train by tt_cross; 0: by a dense
                          * TT-SVD up to 27 bits in all, by tt_cross above               */
+  const double* ellipsoids; /* host; used when indicator and boxes are NULL: nellipsoids
+                         * rows of 15 (centre, semi-axes, rotation; see qtt_cross_fn) of
+                         * a union of ellipsoids, the phase train then built by tt_cross
+                         * (grids as for boxes)                                           */
+  int32_t nellipsoids;
 } qtt_rve;
 
 /* Per-bond rank features of one rounding inside ms_homogenize (the rank

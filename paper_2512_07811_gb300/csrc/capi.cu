@@ -285,6 +285,12 @@ int qtt_ctx_sync(qtt_ctx* c) {
 
 int64_t qtt_ctx_launch_count(const qtt_ctx* c) { return c ? c->launches : -1; }
 
+int qtt_ctx_fail_alloc_after(qtt_ctx* c, int64_t n) {
+  if (!c) return QTT_ERR_ARG;
+  c->fail_alloc_after = n < 0 ? -1 : n;
+  return QTT_OK;
+}
+
 int qtt_ctx_profile(qtt_ctx* c, int enable) {
   if (!c) return QTT_ERR_ARG;
   cudaStreamSynchronize(c->stream);
@@ -888,7 +894,7 @@ static bool rve_bits_valid(const qtt_rve* rve) {
   rve_bits(rve, nb);
   const int tot = nb[0] + nb[1] + nb[2];
   const bool dense = rve->indicator != nullptr;
-  if (!dense && (rve->nboxes < 1 || !rve->boxes)) return false;
+  if (!dense && (rve->nboxes < 1 || !rve->boxes) && (rve->nellipsoids < 1 || !rve->ellipsoids)) return false;
   for (int a = 0; a < 3; ++a)
     if (nb[a] < 0 || nb[a] > (dense ? 15 : 20)) return false;
   return tot >= 1 && tot <= (dense ? 27 : 60);
@@ -955,7 +961,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     dfree(c, ind);
     dfree(c, dense);
     if (s) return s;
-  } else {
+  } else if (rve->boxes && rve->nboxes > 0) {
     DBuf boxes;
     TRY(boxes.alloc(c, (size_t)rve->nboxes * 6 * sizeof(double)));
     TRY(upload(c, boxes.p, rve->boxes, (size_t)rve->nboxes * 6 * sizeof(double)));
@@ -965,7 +971,18 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     fb.nboxes = rve->nboxes;
     CrossOut co;
     TRY(cross_rounded(c, fb, std::vector<int>(dsp, 2), op_tol, cross_rank, 2 * cross_kick, cross_sweeps, 0x9a5eull,
-                      box_seeds(sm, rve->boxes, rve->nboxes), &ops->chi, &co));
+                      centre_seeds(sm, rve->boxes, rve->nboxes, 6), &ops->chi, &co));
+  } else {
+    DBuf ells;
+    TRY(ells.alloc(c, (size_t)rve->nellipsoids * 15 * sizeof(double)));
+    TRY(upload(c, ells.p, rve->ellipsoids, (size_t)rve->nellipsoids * 15 * sizeof(double)));
+    CrossFn fe = cf;
+    fe.kind = CROSS_ELLIPSOIDS;
+    fe.ells = ells.as<double>();
+    fe.nells = rve->nellipsoids;
+    CrossOut co;
+    TRY(cross_rounded(c, fe, std::vector<int>(dsp, 2), op_tol, cross_rank, 2 * cross_kick, cross_sweeps, 0xe111ull,
+                      centre_seeds(sm, rve->ellipsoids, rve->nellipsoids, 15), &ops->chi, &co));
   }
   ops->phase_rank = *std::max_element(ops->chi->r.begin(), ops->chi->r.end());
   // Green operator train: control core (ncomp^2) first, then the spatial sites
@@ -1340,11 +1357,22 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
           return QTT_ERR_NAN;
         }
       }
-      // relative change, on the difference train (orthogonalisation, no cancellation)
+      // relative change, on the difference train (orthogonalisation, no
+      // cancellation), always in FP64: on the float path the difference
+      // train's cores are widened exactly to complex128 first, so the
+      // residual that decides convergence carries no float rounding beyond
+      // that of the iterates themselves
       qtt_tt* diff = nullptr;
       TRY(add_dev<R>(c, C(1, 0), xn, C(-1, 0), x, &diff));
       double dn = 0;
-      s = norm_dev<R>(c, diff, &dn);
+      if (dt == QTT_C128) {
+        s = norm_dev<double>(c, diff, &dn);
+      } else {
+        qtt_tt* wide = nullptr;
+        s = convert_tt(c, diff, QTT_C128, &wide);
+        if (!s) s = norm_dev<double>(c, wide, &dn);
+        if (wide) tt_free(wide);
+      }
       tt_free(diff);
       if (s) return s;
       res = dn / normE;
@@ -1501,7 +1529,7 @@ extern "C" int tt_cross(qtt_ctx* c, const qtt_cross_fn* fn, double eps, int32_t 
   CrossFn f{};
   f.m = site_map_bits(fn->nbits_dim, fn->interleaved != 0);
   std::vector<int> modes;
-  DBuf boxes;
+  DBuf boxes, ells;
   if (fn->kind == QTT_CROSS_GREEN) {
     if (fn->ncomp == 3) {
       if (!(fn->k0 > 0)) return QTT_ERR_ARG;
@@ -1525,12 +1553,21 @@ extern "C" int tt_cross(qtt_ctx* c, const qtt_cross_fn* fn, double eps, int32_t 
     f.boxes = boxes.as<double>();
     f.nboxes = fn->nboxes;
     modes.assign(tot, 2);
+  } else if (fn->kind == QTT_CROSS_ELLIPSOIDS) {
+    if (!fn->ellipsoids || fn->nellipsoids < 1) return QTT_ERR_ARG;
+    TRY(ells.alloc(c, (size_t)fn->nellipsoids * 15 * sizeof(double)));
+    TRY(upload(c, ells.p, fn->ellipsoids, (size_t)fn->nellipsoids * 15 * sizeof(double)));
+    f.kind = CROSS_ELLIPSOIDS;
+    f.ells = ells.as<double>();
+    f.nells = fn->nellipsoids;
+    modes.assign(tot, 2);
   } else {
     return QTT_ERR_ARG;
   }
   CrossOut co;
-  const auto seeds = f.kind == CROSS_BOXES ? box_seeds(f.m, fn->boxes, fn->nboxes)
-                                           : std::vector<std::vector<uint8_t>>();
+  std::vector<std::vector<uint8_t>> seeds;
+  if (f.kind == CROSS_BOXES) seeds = centre_seeds(f.m, fn->boxes, fn->nboxes, 6);
+  if (f.kind == CROSS_ELLIPSOIDS) seeds = centre_seeds(f.m, fn->ellipsoids, fn->nellipsoids, 15);
   int s = cross_rounded(c, f, modes, eps, max_rank, kick, max_half_sweeps, seed, seeds, out, &co);
   if (info) {
     info->half_sweeps = co.half_sweeps;

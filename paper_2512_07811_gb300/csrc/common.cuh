@@ -113,7 +113,14 @@ __device__ __forceinline__ double green_entry(const double xi[3], int I, int J, 
 //    position convention (site (dim, pos) holds bit nb[dim]-1-pos of x_dim);
 //    a voxel is inside a box when the periodic distance of its centre
 //    (x + 1/2)/N from the box centre is at most the half width on every axis.
-enum { CROSS_GREEN = 1, CROSS_BOXES = 2 };
+//  CROSS_ELLIPSOIDS: the phase indicator of a union of ellipsoids (rows of
+//    15: centre, semi-axes a_i (may be +inf: a fibre), rotation R row-major,
+//    column i the direction of semi-axis i; device memory), spatial sites
+//    only, position convention: with the periodic offsets
+//    D_j = (c_j - centre_j) - rint(c_j - centre_j) of the voxel centre, the
+//    voxel is inside when sum_i (u_i / a_i)^2 <= 1, u_i = sum_j R[j][i] D_j,
+//    every operation rounded separately in that order (no fused multiply-add).
+enum { CROSS_GREEN = 1, CROSS_BOXES = 2, CROSS_ELLIPSOIDS = 3 };
 struct CrossFn {
   int kind;
   SiteMap m;
@@ -121,6 +128,8 @@ struct CrossFn {
   double k0, lam0, mu0;
   const double* boxes;
   int nboxes;
+  const double* ells;
+  int nells;
 };
 
 // C[b][m][n] = alpha * sum_k opA(A)[b][m][k] * opB(B)[b][k][n] + beta * C[b][m][n]

@@ -62,6 +62,25 @@ __device__ double cross_value(const CrossFn& f, const CrossAcc& a) {
   }
   double c[3];
   for (int d = 0; d < 3; ++d) c[d] = ((double)a.v[d] + 0.5) / (double)((int64_t)1 << f.m.nb[d]);
+  if (f.kind == CROSS_ELLIPSOIDS) {
+    for (int e = 0; e < f.nells; ++e) {
+      const double* E = f.ells + 15 * e;
+      double D[3];
+      for (int d = 0; d < 3; ++d) {
+        const double t = __dsub_rn(c[d], E[d]);
+        D[d] = __dsub_rn(t, rint(t));   // round half to even, as the host voxelisation
+      }
+      double q = 0.0;
+      for (int i = 0; i < 3; ++i) {
+        double u = __dadd_rn(__dmul_rn(E[6 + i], D[0]), __dmul_rn(E[9 + i], D[1]));
+        u = __dadd_rn(u, __dmul_rn(E[12 + i], D[2]));
+        const double t = __ddiv_rn(u, E[3 + i]);
+        q = i == 0 ? __dmul_rn(t, t) : __dadd_rn(q, __dmul_rn(t, t));
+      }
+      if (q <= 1.0) return 1.0;
+    }
+    return 0.0;
+  }
   for (int b = 0; b < f.nboxes; ++b) {
     const double* B = f.boxes + 6 * b;
     bool in = true;
@@ -377,15 +396,16 @@ static uint64_t splitmix64(uint64_t& s) {
   return z ^ (z >> 31);
 }
 
-// Site values (position convention) of the voxel holding each box centre:
-// starting points inside the phase-2 region, which random points may miss.
-std::vector<std::vector<uint8_t>> box_seeds(const SiteMap& m, const double* boxes, int nboxes) {
+// Site values (position convention) of the voxel holding each box (or
+// ellipsoid) centre: starting points inside the phase-2 region, which random
+// points may miss.  Rows of `stride` values, the centre first.
+std::vector<std::vector<uint8_t>> centre_seeds(const SiteMap& m, const double* rows, int nrows, int stride) {
   std::vector<std::vector<uint8_t>> out;
-  for (int b = 0; b < nboxes; ++b) {
+  for (int b = 0; b < nrows; ++b) {
     int64_t x[3];
     for (int a = 0; a < 3; ++a) {
       const int64_t N = (int64_t)1 << m.nb[a];
-      double cf = boxes[6 * b + a] - floor(boxes[6 * b + a]);
+      double cf = rows[stride * b + a] - floor(rows[stride * b + a]);
       x[a] = std::min<int64_t>((int64_t)(cf * (double)N), N - 1);
     }
     std::vector<uint8_t> p(m.d);

@@ -4,6 +4,8 @@
 // context's stream; the host only sizes buffers and reads back the ranks that
 // the truncations choose.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -29,6 +31,10 @@ size_t dtype_size(qtt_dtype t) { return t == QTT_C128 ? 16 : 8; }
 int dalloc(qtt_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return QTT_OK;
+  if (c->fail_alloc_after >= 0) {
+    if (c->fail_alloc_after == 0) return QTT_ERR_OOM;  // injected failure (qtt_ctx_fail_alloc_after)
+    --c->fail_alloc_after;
+  }
   if (cudaMallocAsync(p, bytes, c->stream) != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -743,6 +749,7 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
   }
   double nrm2 = 0;
   TRY(sync_read(c, &nrm2, dscal, sizeof(double)));
+  if (!std::isfinite(nrm2)) return QTT_ERR_NAN;  // a non-finite input: nothing to truncate
   const double nrm = sqrt(nrm2);
   const double delta = d > 1 ? eps * nrm / sqrt((double)(d - 1)) : 0.0;
   // ---- sweep 2
@@ -1275,6 +1282,7 @@ int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* 
   TRY(qtt_sumsq<R>(dense, total, dscal, c->stream));
   double n2 = 0;
   TRY(sync_read(c, &n2, dscal, sizeof(double)));
+  if (!std::isfinite(n2)) return QTT_ERR_NAN;
   const double delta = d > 1 ? eps * sqrt(n2) / sqrt((double)(d - 1)) : 0.0;
   std::vector<DBuf> cores(d);
   std::vector<int> ranks(d + 1, 1);

@@ -30,6 +30,7 @@ struct qtt_ctx {
   int sweeps_cap = 0, sweeps_used = 0;
   bool tc = false;           // route large float contractions to the tensor cores
   int* d_tcerr = nullptr;    // bounded-wait failure flag of the tensor-core GEMM
+  int64_t fail_alloc_after = -1;  // test hook: allocations left before dalloc fails (-1: off)
 };
 
 // Scoped switch of the tensor-core route for one ABI call.
@@ -157,8 +158,9 @@ struct CrossOut {
 int cross_rounded(qtt_ctx* c, const CrossFn& f, const std::vector<int>& modes, double eps, int max_rank, int kick,
                   int max_half_sweeps, uint64_t seed, const std::vector<std::vector<uint8_t>>& seeds, qtt_tt** out,
                   CrossOut* st);
-// the voxel of every box centre as site values (position convention)
-std::vector<std::vector<uint8_t>> box_seeds(const SiteMap& m, const double* boxes, int nboxes);
+// the voxel of every box (stride 6) or ellipsoid (stride 15) centre as site
+// values (position convention)
+std::vector<std::vector<uint8_t>> centre_seeds(const SiteMap& m, const double* rows, int nrows, int stride);
 
 // AMEn y ~ A x (amen.cu)
 template <class R>

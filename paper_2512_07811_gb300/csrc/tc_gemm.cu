@@ -118,10 +118,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes));
 }
-// bounded wait on the phase with the given parity; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait on the phase with the given parity; returns false on timeout,
+// or as soon as *stop (a CTA-wide abort flag, read through a volatile
+// pointer so every poll reloads it) is set, when stop is given
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* stop = nullptr) {
   const uint32_t a = smem_u32(bar);
   for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+    if (stop && *stop) return false;
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -194,33 +197,45 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
 
+  volatile int* abort_v = &abort_sh;
   if (warp == 0 && lane == 0) {
     // producer: TMA loads into the ring
+    int issued = 0;
     for (int kt = 0; kt < k_tiles; ++kt) {
       const int s = kt % STAGES;
       const uint32_t round = kt / STAGES;
       if (kt >= STAGES) {
-        if (!mbar_wait(&empty_bar[s], (round - 1) & 1)) {
+        if (!mbar_wait(&empty_bar[s], (round - 1) & 1, abort_v)) {
           atomicExch(err, 1);
-          abort_sh = 1;
+          atomicExch(&abort_sh, 1);
           break;
         }
       }
-      if (abort_sh) break;
+      if (*abort_v) break;
       unsigned char* a = smem + s * STAGE_BYTES;
       unsigned char* b = a + TILE_A_BYTES;
       mbar_expect_tx(&full_bar[s], STAGE_BYTES);
       tma_load_2d(&mapA, &full_bar[s], a, kt * TBK, m0);
       tma_load_2d(&mapB, &full_bar[s], b, kt * TBK, n0);
+      issued = kt + 1;
+    }
+    // Drain: every load this thread issued must have landed before the CTA
+    // may exit (normally the MMA issuer has consumed them already and these
+    // waits return at once).  A stage's latest issued load is the only one
+    // that can still be in flight (the stage was refilled only after its
+    // previous load was consumed), and a TMA load completes by itself, so
+    // these waits end; they are bounded all the same.
+    for (int kt = issued - 1; kt >= 0 && kt >= issued - STAGES; --kt) {
+      if (!mbar_wait(&full_bar[kt % STAGES], (kt / STAGES) & 1)) atomicExch(err, 4);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     const uint32_t idesc = idesc_tf32(TBM, TBN);
     for (int kt = 0; kt < k_tiles; ++kt) {
       const int s = kt % STAGES;
-      if (!mbar_wait(&full_bar[s], (kt / STAGES) & 1)) {
+      if (!mbar_wait(&full_bar[s], (kt / STAGES) & 1, abort_v)) {
         atomicExch(err, 2);
-        abort_sh = 1;
+        atomicExch(&abort_sh, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -242,6 +257,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&empty_bar[s])));
     }
+    // issued on every exit path, abort included: done_bar completes once
+    // every MMA this thread issued has finished, so the epilogue's wait also
+    // orders the tensor-memory release after the last MMA
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
         smem_u32(&done_bar)));
   }
@@ -385,6 +403,10 @@ int noalloc_scratch(void** out) {
 extern "C" int qtt_cgemm_noalloc(void* stream, int64_t M, int64_t N, int64_t K, const void* A, const void* B,
                                  void* C) {
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return QTT_ERR_ARG;
+  // no operand dimension of a problem that fits the array comes near 2^22;
+  // refusing larger ones first keeps the workspace arithmetic below from
+  // overflowing
+  if (M > (1 << 22) || N > (1 << 22) || K > (1 << 22)) return QTT_ERR_RANK;
   const size_t need = qtt_tc_gemm_workspace(M, N, K);
   if (need + 256 > QTT_NOALLOC_SCRATCH_BYTES) return QTT_ERR_RANK;
   void* base = nullptr;

@@ -54,13 +54,14 @@ class RVE(C.Structure):
                 ("k1", C.c_double), ("k2", C.c_double), ("lam1", C.c_double), ("mu1", C.c_double),
                 ("lam2", C.c_double), ("mu2", C.c_double), ("interleaved", C.c_int32),
                 ("nbits_dim", C.c_int32 * 3), ("boxes", C.POINTER(C.c_double)), ("nboxes", C.c_int32),
-                ("op_cross", C.c_int32)]
+                ("op_cross", C.c_int32), ("ellipsoids", C.POINTER(C.c_double)), ("nellipsoids", C.c_int32)]
 
 
 class CrossFn(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nbits_dim", C.c_int32 * 3), ("interleaved", C.c_int32),
                 ("ncomp", C.c_int32), ("k0", C.c_double), ("lam0", C.c_double), ("mu0", C.c_double),
-                ("boxes", C.POINTER(C.c_double)), ("nboxes", C.c_int32)]
+                ("boxes", C.POINTER(C.c_double)), ("nboxes", C.c_int32),
+                ("ellipsoids", C.POINTER(C.c_double)), ("nellipsoids", C.c_int32)]
 
 
 class CrossInfo(C.Structure):
@@ -68,7 +69,7 @@ class CrossInfo(C.Structure):
                 ("max_rank", C.c_int32)]
 
 
-CROSS_GREEN, CROSS_BOXES = 1, 2
+CROSS_GREEN, CROSS_BOXES, CROSS_ELLIPSOIDS = 1, 2, 3
 
 
 class AmenInfo(C.Structure):
@@ -83,6 +84,21 @@ class Boxes:
 
     def __init__(self, boxes, shape):
         self.boxes = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 6))
+        self.shape = tuple(int(n) for n in shape)
+        nb = [int(round(np.log2(n))) for n in self.shape]
+        if len(nb) != 3 or any((1 << b) != n for b, n in zip(nb, self.shape)):
+            raise ValueError("grid sizes must be powers of two, got %s" % (self.shape,))
+        self.nbits = nb
+
+
+class Ellipsoids:
+    """A phase geometry without a dense image: a union of ellipsoids (rows of
+    15: centre, semi-axes (+inf for a fibre), rotation row-major; see
+    inputs.ellipsoids_value) on a grid of `shape` = (Nx, Ny, Nz) voxels
+    (powers of two), sampled by TT-cross like Boxes."""
+
+    def __init__(self, rows, shape):
+        self.rows = np.ascontiguousarray(np.asarray(rows, dtype=np.float64).reshape(-1, 15))
         self.shape = tuple(int(n) for n in shape)
         nb = [int(round(np.log2(n))) for n in self.shape]
         if len(nb) != 3 or any((1 << b) != n for b, n in zip(nb, self.shape)):
@@ -134,6 +150,7 @@ _sig("qtt_ctx_create", C.c_int, [C.c_int, _P, C.POINTER(_P)])
 _sig("qtt_ctx_destroy", None, [_P])
 _sig("qtt_ctx_sync", C.c_int, [_P])
 _sig("qtt_ctx_launch_count", C.c_int64, [_P])
+_sig("qtt_ctx_fail_alloc_after", C.c_int, [_P, C.c_int64])
 _sig("qtt_ctx_profile", C.c_int, [_P, C.c_int])
 _sig("qtt_ctx_profile_read", C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)])
@@ -190,6 +207,7 @@ _sig("ms_homogenize", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_d
                                 C.POINTER(MSOpts), C.POINTER(C.c_double), C.POINTER(MSReport)])
 
 EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_sync", "qtt_ctx_launch_count",
+            "qtt_ctx_fail_alloc_after",
             "qtt_ctx_profile", "qtt_ctx_profile_read",
             "qtt_tt_create", "qtt_tt_destroy", "qtt_tt_ncores", "qtt_tt_ranks", "qtt_tt_modes", "qtt_tt_dtype",
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
@@ -240,6 +258,10 @@ class Context:
     @property
     def launches(self) -> int:
         return int(_lib.qtt_ctx_launch_count(self.h))
+
+    def fail_alloc_after(self, n: int):
+        """Test hook: the allocation after `n` more succeed fails (QTT_ERR_OOM); n < 0 turns it off."""
+        _check(_lib.qtt_ctx_fail_alloc_after(self.h, int(n)), "qtt_ctx_fail_alloc_after")
 
     KERNEL_CLASSES = {"gemm": 0, "qr": 1, "jacobi": 2, "elem": 3}
 
@@ -442,16 +464,17 @@ def tt_round_polar(ctx: Context, x: TT, eps: float, prec=None):
 
 def tt_cross(ctx: Context, kind: str, nbits, eps: float, interleaved: bool = True, ncomp: int = 3,
              k0: float = 1.0, lam0: float = 0.0, mu0: float = 0.0, boxes=None, max_rank: int = 0,
-             kick: int | None = None, max_half_sweeps: int = 24, seed: int = 1):
+             kick: int | None = None, max_half_sweeps: int = 24, seed: int = 1, ellipsoids=None):
     """TT-cross of the Green operator train (kind "green": modes (ncomp^2,
-    2, ...), momentum convention) or of a box geometry's phase indicator
-    (kind "boxes": modes (2, ...), position convention) on a grid of
-    2^nbits[a] voxels per dimension; kick defaults to 4 (green) / 8 (boxes),
-    as inside ms_homogenize.  Returns (TT, CrossInfo)."""
+    2, ...), momentum convention) or of a box / ellipsoid geometry's phase
+    indicator (kind "boxes" / "ellipsoids": modes (2, ...), position
+    convention) on a grid of 2^nbits[a] voxels per dimension; kick defaults
+    to 4 (green) / 8 (geometries), as inside ms_homogenize.  Returns
+    (TT, CrossInfo)."""
     if kick is None:
         kick = 4 if kind == "green" else 8
     f = CrossFn()
-    f.kind = CROSS_GREEN if kind == "green" else CROSS_BOXES
+    f.kind = {"green": CROSS_GREEN, "boxes": CROSS_BOXES, "ellipsoids": CROSS_ELLIPSOIDS}[kind]
     for a in range(3):
         f.nbits_dim[a] = int(nbits[a])
     f.interleaved = 1 if interleaved else 0
@@ -461,6 +484,10 @@ def tt_cross(ctx: Context, kind: str, nbits, eps: float, interleaved: bool = Tru
         keep = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 6))
         f.boxes = keep.ctypes.data_as(C.POINTER(C.c_double))
         f.nboxes = keep.shape[0]
+    if ellipsoids is not None:
+        keep = np.ascontiguousarray(np.asarray(ellipsoids, dtype=np.float64).reshape(-1, 15))
+        f.ellipsoids = keep.ctypes.data_as(C.POINTER(C.c_double))
+        f.nellipsoids = keep.shape[0]
     h = _P()
     info = CrossInfo()
     _check(_lib.tt_cross(ctx.h, C.byref(f), float(eps), int(max_rank), int(kick), int(max_half_sweeps), int(seed),
@@ -609,7 +636,7 @@ class MLP:
 
 
 def _rve(ind, kind, moduli, interleaved, op_cross=False):
-    """qtt_rve for a dense phase image (Nx, Ny, Nz) or a Boxes geometry;
+    """qtt_rve for a dense phase image (Nx, Ny, Nz), a Boxes or an Ellipsoids geometry;
     returns (rve, arrays kept alive for the call)."""
     rve = RVE()
     if isinstance(ind, Boxes):
@@ -617,6 +644,11 @@ def _rve(ind, kind, moduli, interleaved, op_cross=False):
         keep = ind.boxes
         rve.boxes = keep.ctypes.data_as(C.POINTER(C.c_double))
         rve.nboxes = keep.shape[0]
+    elif isinstance(ind, Ellipsoids):
+        nb = ind.nbits
+        keep = ind.rows
+        rve.ellipsoids = keep.ctypes.data_as(C.POINTER(C.c_double))
+        rve.nellipsoids = keep.shape[0]
     else:
         keep = np.ascontiguousarray(ind, dtype=np.float64)
         nb = _grid_bits(keep)
@@ -677,7 +709,7 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
 
     kind "scalar": moduli = (k1, k2), C0 = 3x3; kind "elastic": moduli =
     (lam1, mu1, lam2, mu2), C0 = Voigt 6x6.  `indicator` is a dense
-    (Nx, Ny, Nz) image or a Boxes geometry (phase train by TT-cross);
+    (Nx, Ny, Nz) image or a Boxes / Ellipsoids geometry (phase train by TT-cross);
     op_cross builds the Green operator train by TT-cross at any size (it is
     always so above 2^27 voxels); green_amen applies it by AMEn;
     return_strain puts the converged strain train of the last load case in

