@@ -74,15 +74,7 @@ def load_peaks():
 
 
 def sketch_cores(rng, d, modes, ell):
-    ranks = [1]
-    left = 1
-    for k in range(1, d):
-        left *= modes[k - 1]
-        right = int(np.prod(modes[k:], dtype=np.float64)) if d - k < 60 else 1 << 60
-        ranks.append(int(min(ell, left, right)))
-    ranks.append(1)
-    return [rng.standard_normal((ranks[k], modes[k], ranks[k + 1])) / math.sqrt(modes[k] * ranks[k + 1])
-            for k in range(d)], ranks
+    return I.sketch_cores(rng, d, modes, ell)
 
 
 # --------------------------------------------------------------- clocks

@@ -441,7 +441,8 @@ typedef struct {
 
 typedef struct {
   int32_t iterations[6];
-  double residual[6];      /* last relative change ||eps_{m+1} - eps_m|| / ||E 1||       */
+  double residual[6];      /* last relative change ||eps_{m+1} - eps_m|| / ||E 1|| (FP64
+                              whenever it ended the iteration)                             */
   double sigma_imag_max;   /* max |Im sigma_eff| (diagnostic)                             */
   int32_t max_rank_seen;
   double setup_ms, iterate_ms;
@@ -451,6 +452,8 @@ typedef struct {
   int32_t fallbacks;       /* sketched roundings redone at the full width                */
   int32_t green_rank;      /* largest bond rank of the Green operator train              */
   int32_t phase_rank;      /* largest bond rank of the phase indicator train             */
+  int32_t fp64_residuals;  /* float path: stop tests recomputed in FP64 (a stop is only
+                              decided on an FP64 residual; see ms_homogenize)              */
 } ms_report;
 
 /* Moulinec-Suquet homogenisation in QTT form (Sec. 3.2, Algorithm 2):
@@ -459,8 +462,15 @@ typedef struct {
  *   ||eps_{m+1} - eps_m||_F / ||E 1||_F < tol (Algorithm 2; Appendix A for the
  * effective tensor, sigma_eff = <C eps>).  C0 is the isotropic reference
  * (3x3 k0*I or Voigt 6x6, row-major).  Each rounding uses the sketched
- * rounding with width max_rank + oversample.  C_eff (ncomp x ncomp,
- * row-major, real part) receives the columns of the load cases in
+ * rounding with width max_rank + oversample.  S is applied one dimension at
+ * a time for interleaved sites, and as one operator train (the product of
+ * the three, whose bonds do not multiply) for sites grouped by dimension;
+ * the last inverse transform is applied inside the update's rounding,
+ * round(E - S^{-1} eps^) as one two-term sketched rounding.  The stop test
+ * is decided on an FP64 residual of the difference train on both paths
+ * (the float path screens iterates with a float residual first and
+ * recomputes it in FP64 once it comes within 10 tol).  C_eff (ncomp x
+ * ncomp, row-major, real part) receives the columns of the load cases in
  * opts->load_mask; `report` may be NULL. */
 QTT_API int ms_homogenize(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, double tol, int max_rank,
                   const ms_opts* opts, double* C_eff, ms_report* report);

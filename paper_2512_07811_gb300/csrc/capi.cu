@@ -136,7 +136,14 @@ int check_prec(qtt_dtype dt, qtt_prec p) {
   return QTT_ERR_ARG;
 }
 
-// sketch train: real Gaussian cores N(0, 1/(n_k l_k)), ranks min(l, prod left, prod right)
+// sketch train: ranks min(l, prod left, prod right); real Gaussian cores
+// N(0, 1/(n_k l_{k+1})), except where the rank is the full product of the
+// modes to the right (l_k = n_k l_{k+1}): there the core is the identity
+// unfolding (the M x M identity, M = n_k l_{k+1}), so the sketch of the sites
+// to the right of such a bond is exact and orthonormal.  A Gaussian sketch
+// there would be square, and the projection's rounding error grows with the
+// condition number of a square Gaussian matrix (no oversampling margin);
+// with the identity it is the rounding of an orthogonal factorisation.
 int make_sketch(qtt_ctx* c, const std::vector<int>& modes, const std::vector<int>& ell, qtt_dtype dt, uint64_t seed,
                 uint64_t stream_id, qtt_tt** out) {
   const int d = (int)modes.size();
@@ -154,10 +161,16 @@ int make_sketch(qtt_ctx* c, const std::vector<int>& modes, const std::vector<int
   for (int k = 0; k < d; ++k) {
     int64_t cnt = (int64_t)r[k] * modes[k] * r[k + 1];
     double scale = 1.0 / sqrt((double)modes[k] * r[k + 1]);
+    const int64_t M = (int64_t)modes[k] * r[k + 1];
     c->launches++;
-    int s = dt == QTT_C128
-                ? qtt_fill_gaussian<double>(core_ptr<zc>(S, k), cnt, seed, (stream_id << 8) + k, scale, c->stream)
-                : qtt_fill_gaussian<float>(core_ptr<cc>(S, k), cnt, seed, (stream_id << 8) + k, scale, c->stream);
+    int s;
+    if (k > 0 && r[k] == M)
+      s = dt == QTT_C128 ? qtt_identity_core<double>(1, M, core_ptr<zc>(S, k), c->stream)
+                         : qtt_identity_core<float>(1, M, core_ptr<cc>(S, k), c->stream);
+    else
+      s = dt == QTT_C128
+              ? qtt_fill_gaussian<double>(core_ptr<zc>(S, k), cnt, seed, (stream_id << 8) + k, scale, c->stream)
+              : qtt_fill_gaussian<float>(core_ptr<cc>(S, k), cnt, seed, (stream_id << 8) + k, scale, c->stream);
     if (s) {
       tt_free(S);
       return s;
@@ -1044,26 +1057,38 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     TRY(qtt_diag_mpo_core<double>(core_ptr<zc>(ops->chi, k - 1), ops->chi->r[k - 1], 2, ops->chi->r[k],
                                   core_ptr<zc>(ops->dCb, k), c->stream));
   }
-  // superfast Fourier transform, one dimension at a time (none for a
-  // dimension without bits)
+  // superfast Fourier transform (none for a dimension without bits).  Sites
+  // grouped by dimension (the paper's order): the three one-dimensional
+  // transforms act on disjoint runs of sites with bond 1 between the runs, so
+  // their product is ONE operator train whose core at a site is that site's
+  // one-dimensional core -- one application and one rounding per transform.
+  // Interleaved sites: one operator per dimension, its bond carried unchanged
+  // through the sites of the other dimensions (identity cores).
+  qtt_mpo* q1[3] = {nullptr, nullptr, nullptr};
+  struct FreeQ1 {
+    qtt_mpo** q;
+    ~FreeQ1() {
+      for (int i = 0; i < 3; ++i) mpo_free(q[i]);
+    }
+  } free_q1{q1};
+  for (int dim = 0; dim < 3; ++dim)
+    if (sm.nb[dim] > 0) TRY(qtt_qft_mpo(c, sm.nb[dim], -1, 1e-12, &q1[dim]));
+  const bool combined = !rve->interleaved;
   for (int dim = 0; dim < 3; ++dim) {
     if (sm.nb[dim] == 0) continue;
-    qtt_mpo* q1 = nullptr;
-    TRY(qtt_qft_mpo(c, sm.nb[dim], -1, 1e-12, &q1));
-    // the bond of the one-dimensional train is carried unchanged through the
-    // sites of the other dimensions (identity cores)
+    if (combined && ops->q[0]) break;   // the one combined operator is built
     std::vector<int> gq(d + 1, 1);
     int cur = 1;
     for (int p = 0; p < dsp; ++p) {
       const int dm = sm.dim[p], pos = sm.pos[p];
-      if (dm == dim) cur = q1->g[pos + 1];
+      if (combined) cur = q1[dm]->g[pos + 1];
+      else if (dm == dim) cur = q1[dim]->g[pos + 1];
       gq[p + 2] = cur;
     }
     qtt_mpo* Q = mpo_alloc(c, d, mo, mo, gq, QTT_C128, &s);
     qtt_mpo* Qi = Q ? mpo_alloc(c, d, mo, mo, gq, QTT_C128, &s) : nullptr;
     if (!Q || !Qi) {
       mpo_free(Q);
-      mpo_free(q1);
       return s;
     }
     c->launches++;
@@ -1071,9 +1096,10 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     for (int p = 0; p < dsp; ++p) {
       const int dm = sm.dim[p], pos = sm.pos[p];
       const int k = p + 1;
-      if (dm == dim) {
-        cudaMemcpyAsync(core_ptr<char>(Q, k), core_ptr<char>(q1, pos),
-                        (size_t)q1->g[pos] * 4 * q1->g[pos + 1] * sizeof(zc), cudaMemcpyDeviceToDevice, c->stream);
+      if (combined || dm == dim) {
+        const qtt_mpo* src = q1[dm];
+        cudaMemcpyAsync(core_ptr<char>(Q, k), core_ptr<char>(src, pos),
+                        (size_t)src->g[pos] * 4 * src->g[pos + 1] * sizeof(zc), cudaMemcpyDeviceToDevice, c->stream);
       } else {
         c->launches++;
         qtt_identity_core<double>(gq[k], 2, core_ptr<zc>(Q, k), c->stream);
@@ -1083,9 +1109,8 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
       c->launches++;
       qtt_adjoint_core<double>(core_ptr<zc>(Q, k), gq[k], mo[k], mo[k], gq[k + 1], core_ptr<zc>(Qi, k), c->stream);
     }
-    ops->q[dim] = Q;
-    ops->qi[dim] = Qi;
-    mpo_free(q1);
+    ops->q[combined ? 0 : dim] = Q;
+    ops->qi[combined ? 0 : dim] = Qi;
   }
   return QTT_OK;
 }
@@ -1327,7 +1352,14 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         if (s) return s;
         h = hn;
       }
-      for (int dim = 2; dim >= 0; --dim) {
+      // inverse SFFT in the order z, y, x: every operator but the last one
+      // applied and rounded on its own; the last one is applied inside the
+      // update's rounding, eps_{m+1} = round(E - S^{-1} eps^) as one
+      // two-term structured rounding (no separate rounding of S^{-1} eps^)
+      int last = -1;
+      for (int dim = 0; dim < 3 && last < 0; ++dim)
+        if (Qi[dim]) last = dim;
+      for (int dim = 2; dim > last; --dim) {
         if (!Qi[dim]) continue;
         stage = inv[dim];
         qtt_tt* hn = nullptr;
@@ -1338,15 +1370,16 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         if (s) return s;
         h = hn;
       }
-      // eps_{m+1} = round(E - S^{-1} eps^)
-      qtt_tt *sum = nullptr, *xn = nullptr;
-      int s = add_dev<R>(c, C(1, 0), E, C(-1, 0), h, &sum);
-      tt_free(h);
-      if (s) return s;
+      qtt_tt* xn = nullptr;
       stage = "update";
-      s = round_det<R>(c, sum, o.eps, max_rank, nullptr, nullptr, &xn);
-      tt_free(sum);
-      if (s) return s;
+      {
+        const qtt_complex cf[2] = {one, {-1.0, 0.0}};
+        const qtt_mpo* A[2] = {nullptr, Qi[last]};
+        const qtt_tt* X[2] = {E, h};
+        int s = sk_round(2, cf, A, X, 8, &xn);
+        tt_free(h);
+        if (s) return s;
+      }
       // the new iterate is always scanned: a non-finite strain ends the solve with QTT_ERR_NAN
       {
         int ok = 1;
@@ -1358,24 +1391,37 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         }
       }
       // relative change, on the difference train (orthogonalisation, no
-      // cancellation), always in FP64: on the float path the difference
-      // train's cores are widened exactly to complex128 first, so the
-      // residual that decides convergence carries no float rounding beyond
+      // cancellation).  The residual that decides convergence is always an
+      // FP64 one: on the float path the difference train's cores are widened
+      // exactly to complex128 first, so it carries no float rounding beyond
       // that of the iterates themselves
       qtt_tt* diff = nullptr;
       TRY(add_dev<R>(c, C(1, 0), xn, C(-1, 0), x, &diff));
       double dn = 0;
+      int s = QTT_OK;
       if (dt == QTT_C128) {
         s = norm_dev<double>(c, diff, &dn);
       } else {
-        qtt_tt* wide = nullptr;
-        s = convert_tt(c, diff, QTT_C128, &wide);
-        if (!s) s = norm_dev<double>(c, wide, &dn);
-        if (wide) tt_free(wide);
+        // float path: a float residual first, so an iterate that is
+        // clearly not converged costs no FP64 sweep; once it comes within
+        // 10 tol the residual is recomputed in FP64 and that one decides.
+        // A float residual overestimating the true one only delays the FP64
+        // check by an iteration; a stop is never decided in float
+        s = norm_dev<R>(c, diff, &dn);
+        if (!s && dn / normE < 10.0 * tol && it >= std::max(1, (int)o.min_iter)) {
+          qtt_tt* wide = nullptr;
+          s = convert_tt(c, diff, QTT_C128, &wide);
+          if (!s) s = norm_dev<double>(c, wide, &dn);
+          if (wide) tt_free(wide);
+          if (rep) rep->fp64_residuals++;
+        }
       }
       tt_free(diff);
       if (s) return s;
       res = dn / normE;
+      if (debug_checks())
+        fprintf(stderr, "qtt: lc %d it %d residual %.3e rank %d\n", lc, it, res,
+                *std::max_element(xn->r.begin(), xn->r.end()));
       tt_free(x);
       x = xn;
       if (res < tol && it >= std::max(1, (int)o.min_iter)) break;

@@ -378,6 +378,32 @@ def random_tt_cores(d: int, p: int, r: int, seed: int, dtype=np.float64,
     return cores
 
 
+def sketch_cores(rng: np.random.Generator, d: int, modes, ell: int):
+    """Sketch train of width `ell` for sketched rounding: ranks
+    l_k = min(ell, prod of the modes left of bond k, prod right of it); real
+    Gaussian cores N(0, 1/(n_k l_{k+1})), except cores whose left rank is the
+    full product of the modes to their right (l_k = n_k l_{k+1}), which are
+    the identity unfolding (the M x M identity, M = n_k l_{k+1}).  Returns
+    (cores, ranks)."""
+    ranks = [1]
+    left = 1
+    for k in range(1, d):
+        left = min(left * modes[k - 1], 1 << 60)
+        right = 1
+        for m in modes[k:]:
+            right = min(right * m, 1 << 60)
+        ranks.append(int(min(ell, left, right)))
+    ranks.append(1)
+    cores = []
+    for k in range(d):
+        M = modes[k] * ranks[k + 1]
+        if k > 0 and ranks[k] == M:
+            cores.append(np.eye(M).reshape(M, modes[k], ranks[k + 1]))
+        else:
+            cores.append(rng.standard_normal((ranks[k], modes[k], ranks[k + 1])) / math.sqrt(M))
+    return cores, ranks
+
+
 def random_mpo_cores(d: int, p: int, chi: int, seed: int, dtype=np.complex128) -> list[np.ndarray]:
     """Gaussian operator cores of shape (chi_{k-1}, p_out, p_in, chi_k)."""
     rng = np.random.default_rng(seed)

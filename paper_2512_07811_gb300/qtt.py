@@ -128,7 +128,8 @@ class MSReport(C.Structure):
     _fields_ = [("iterations", C.c_int32 * 6), ("residual", C.c_double * 6), ("sigma_imag_max", C.c_double),
                 ("max_rank_seen", C.c_int32), ("setup_ms", C.c_double), ("iterate_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("trace_len", C.c_int64), ("sketch_width_sum", C.c_int64),
-                ("fallbacks", C.c_int32), ("green_rank", C.c_int32), ("phase_rank", C.c_int32)]
+                ("fallbacks", C.c_int32), ("green_rank", C.c_int32), ("phase_rank", C.c_int32),
+                ("fp64_residuals", C.c_int32)]
 
 
 MLP_FEATURES = 10

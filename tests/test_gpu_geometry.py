@@ -87,14 +87,21 @@ def test_ms_elastic_sphere_fp64_matches_dense_oracle(Q, ctx):
     C, rep = Q.ms_homogenize(ctx, geo, "elastic", (LAM1, MU1, LAM2, MU2), pb.C0, tol=1e-10, max_rank=512,
                              eps=1e-11, max_iter=300, prec=Q.PREC_F64, load_mask=0b1001, interleaved=False)
     assert rep.max_rank_seen < 512
+    assert rep.iterations[0] < 300 and rep.iterations[3] < 300
     got = C[:, [0, 3]]
     assert np.linalg.norm(got - Cd) / np.linalg.norm(Cd) < 1e-7
 
 
 def _fast_vs_fp64(Q, ctx, geo, kind, moduli, C0, mask, interleaved):
-    kw = dict(load_mask=mask, interleaved=interleaved, max_iter=400, max_rank=512)
+    """C_eff columns of the FP64 path (eps 1e-9, converged to 1e-8) and of the
+    float path (eps 1e-6, converged to 5e-5: its residual settles at the
+    single-precision noise of the iterates, about 2e-5 on these grids)."""
+    kw = dict(load_mask=mask, interleaved=interleaved, max_iter=200, max_rank=512)
     C64, r64 = Q.ms_homogenize(ctx, geo, kind, moduli, C0, tol=1e-8, eps=1e-9, prec=Q.PREC_F64, **kw)
-    C32, r32 = Q.ms_homogenize(ctx, geo, kind, moduli, C0, tol=1e-6, eps=1e-6, prec=Q.PREC_F32, **kw)
+    C32, r32 = Q.ms_homogenize(ctx, geo, kind, moduli, C0, tol=5e-5, eps=1e-6, prec=Q.PREC_F32, **kw)
+    assert all(r64.iterations[k] < 200 for k in range(6) if mask >> k & 1)
+    assert all(r32.iterations[k] < 200 for k in range(6) if mask >> k & 1)
+    assert r32.fp64_residuals >= 1
     assert r64.max_rank_seen < 512 and r32.max_rank_seen < 512
     cols = [k for k in range(C64.shape[0]) if mask >> k & 1]
     a, b = C64[:, cols], C32[:, cols]

@@ -258,3 +258,39 @@ def test_rand_orth_is_projection_error_exact():
     lhs = np.linalg.norm(fx) ** 2
     rhs = np.linalg.norm(fy) ** 2 + np.linalg.norm(fx - fy) ** 2
     assert math.isclose(lhs, rhs, rel_tol=1e-11)
+
+
+def test_sketch_with_exact_right_part_is_stable_in_single_precision():
+    """A train at its full (mode-capped) ranks rounded by the randomized
+    projection in complex64: with Gaussian sketch cores on the bonds whose
+    width is capped by the product of the modes to the right, the projection
+    error grows with the condition number of square Gaussian matrices; with
+    the identity unfolding there (inputs.sketch_cores) it stays at the
+    single-precision level.  The projection runs in single precision by
+    casting the oracle's inputs."""
+    dims = [6] + [2] * 9
+    ranks = [1]
+    for k in range(1, 10):
+        ranks.append(min(int(np.prod(dims[:k])), int(np.prod(dims[k:]))))
+    ranks.append(1)
+    x = rand_tt(dims, ranks, 31)
+    fx = T.tt_full(x)
+    x32 = [c.astype(np.complex64) for c in x]
+    errs = {}
+    for kind in ["gaussian", "exact_right"]:
+        worst = 0.0
+        for seed in range(6):
+            rng = np.random.default_rng(100 + seed)
+            if kind == "exact_right":
+                R, _ = I.sketch_cores(rng, len(dims), dims, 56)
+            else:
+                rk = RR.sketch_ranks(len(dims), dims, 56)
+                R = [rng.standard_normal((rk[k], dims[k], rk[k + 1])) / math.sqrt(dims[k] * rk[k + 1])
+                     for k in range(len(dims))]
+            y = RR.rand_orth(x32, [c.astype(np.complex64) for c in R])
+            worst = max(worst, np.linalg.norm(T.tt_full([c.astype(np.complex128) for c in y]) - fx)
+                        / np.linalg.norm(fx))
+        errs[kind] = worst
+    print(errs)
+    assert errs["exact_right"] < 1e-5
+    assert errs["gaussian"] > 10 * errs["exact_right"]
