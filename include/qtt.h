@@ -96,7 +96,9 @@ QTT_API int64_t qtt_ctx_launch_count(const qtt_ctx* ctx);
 /* Built-in profiler: with `enable` != 0 every launch of the GEMM (class 0),
  * Householder QR (1), one-sided Jacobi (2) and elementwise (3) kernels is
  * bracketed by CUDA events on the context stream and its model flops and
- * bytes are recorded; enabling or disabling clears the records. */
+ * bytes are recorded; enabling or disabling clears the records.  enable = 2
+ * records inside ms_homogenize only the iterations of its timed region
+ * (report->timed_ms), including those of its load-case workers. */
 QTT_API int qtt_ctx_profile(qtt_ctx* ctx, int enable);
 /* Totals of one kernel class since profiling was enabled: summed event time
  * (ms), launches, model flops (Jacobi: per-sweep model times the sweeps the
@@ -109,6 +111,16 @@ QTT_API int qtt_ctx_profile_read(qtt_ctx* ctx, int kclass, double* total_ms, int
  * returns QTT_ERR_OOM after releasing what it holds.  n < 0 switches the
  * injection off again.  Host-side only: no kernel is affected. */
 QTT_API int qtt_ctx_fail_alloc_after(qtt_ctx* ctx, int64_t n);
+
+/* Arithmetic peak of the context's GPU in TFLOP/s, measured by the
+ * library's own kernel (not in the paper; the rooflines of the float and
+ * FP64 kernels are quoted against it): a full grid of independent
+ * fused-multiply-add chains (two flops each), best of five timed launches
+ * on the context stream.  which: QTT_PEAK_FP32_FMA or QTT_PEAK_FP64_FMA.
+ * Synchronises the stream; QTT_ERR_ARG for another `which`. */
+#define QTT_PEAK_FP32_FMA 0
+#define QTT_PEAK_FP64_FMA 1
+QTT_API int qtt_measure_peak(qtt_ctx* ctx, int which, double* tflops);
 
 /* --------------------------------------------------------------- trains */
 /* New train with the given modes (d entries) and ranks (d + 1 entries,
@@ -437,12 +449,15 @@ typedef struct {
                             load case (control core first, site order of the RVE, the
                             iteration's dtype); *strain must be NULL or a train the call
                             may destroy; ms_homogenize_batch ignores it                    */
+  int32_t lc_workers;    /* load cases solved at the same time, each on its own stream and
+                            host thread, all sharing the one set of operator trains (0 or 1:
+                            one after another; ignored when trace or strain is requested)  */
+  int32_t warm_iter;     /* iterations of every load case before report->timed_ms starts */
 } ms_opts;
 
 typedef struct {
   int32_t iterations[6];
-  double residual[6];      /* last relative change ||eps_{m+1} - eps_m|| / ||E 1|| (FP64
-                              whenever it ended the iteration)                             */
+  double residual[6];      /* last relative change ||eps_{m+1} - eps_m|| / ||E 1|| (FP64) */
   double sigma_imag_max;   /* max |Im sigma_eff| (diagnostic)                             */
   int32_t max_rank_seen;
   double setup_ms, iterate_ms;
@@ -452,8 +467,12 @@ typedef struct {
   int32_t fallbacks;       /* sketched roundings redone at the full width                */
   int32_t green_rank;      /* largest bond rank of the Green operator train              */
   int32_t phase_rank;      /* largest bond rank of the phase indicator train             */
-  int32_t fp64_residuals;  /* float path: stop tests recomputed in FP64 (a stop is only
-                              decided on an FP64 residual; see ms_homogenize)              */
+  int32_t fp64_residuals;  /* float path: stop tests evaluated from FP64 inner products  */
+  double timed_ms;         /* wall time from the moment every load case running at the
+                              start has made opts->warm_iter iterations (streams synchronised)
+                              until every load case has finished                          */
+  int32_t timed_iter;      /* iterations (summed over load cases) inside timed_ms          */
+  int64_t timed_launches;  /* kernel launches of those iterations                          */
 } ms_report;
 
 /* Moulinec-Suquet homogenisation in QTT form (Sec. 3.2, Algorithm 2):
@@ -467,13 +486,34 @@ typedef struct {
  * the three, whose bonds do not multiply) for sites grouped by dimension;
  * the last inverse transform is applied inside the update's rounding,
  * round(E - S^{-1} eps^) as one two-term sketched rounding.  The stop test
- * is decided on an FP64 residual of the difference train on both paths
- * (the float path screens iterates with a float residual first and
- * recomputes it in FP64 once it comes within 10 tol).  C_eff (ncomp x
+ * is evaluated in FP64 on both paths: by a QR sweep of the difference train
+ * on the FP64 path, and from FP64 inner products of the exactly widened
+ * iterates, <a,a> + <b,b> - 2 Re <a,b>, on the float path (absolute error
+ * about 1e-8 relative to ||E 1||, so float-path tolerances below 1e-6 are
+ * not meaningful; its iterates' own noise is larger).  C_eff (ncomp x
  * ncomp, row-major, real part) receives the columns of the load cases in
  * opts->load_mask; `report` may be NULL. */
 QTT_API int ms_homogenize(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, double tol, int max_rank,
                   const ms_opts* opts, double* C_eff, ms_report* report);
+
+/* The same solve in two parts, so that one RVE's operator trains serve many
+ * solves (precisions, tolerances, load cases):
+ *  ms_setup builds the trains of `rve` and C0 (what ms_homogenize does before
+ *  its iterations; op_tol as opts->op_tol), on ctx's stream, and returns a
+ *  handle owning them; the host arrays of `rve` are not kept.
+ *  ms_homogenize_ops runs the iterations of ms_homogenize on a handle, on
+ *  any context of the same device (the trains are only read);
+ *  report->setup_ms is 0 there.
+ *  ms_ops_destroy frees the trains on the stream of the setup's context,
+ *  which must still exist; ms_ops_ranks reports the largest bond ranks of
+ *  the Green operator and phase trains.  Not in the paper as an interface;
+ *  the paper builds the operators once per RVE as well (Sec. 3.2). */
+typedef struct ms_ops ms_ops;
+QTT_API int ms_setup(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, double op_tol, ms_ops** out);
+QTT_API int ms_homogenize_ops(qtt_ctx* ctx, const ms_ops* ops, double tol, int max_rank, const ms_opts* opts,
+                              double* C_eff, ms_report* report);
+QTT_API void ms_ops_destroy(ms_ops* ops);
+QTT_API int ms_ops_ranks(const ms_ops* ops, int32_t* green_rank, int32_t* phase_rank);
 
 QTT_API /* Many RVEs at once: the (RVE, load case) pairs of rves[0..n-1] (load cases
  * from opts->load_mask) are solved by `workers` host threads, each with its

@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 
 #include <atomic>
+#include <condition_variable>
 #include <mutex>
 #include <random>
 #include <thread>
@@ -233,6 +234,10 @@ static void prof_clear(qtt_ctx* c) {
   }
   c->recs.clear();
   c->sweeps_used = 0;
+  for (int k = 0; k < PK_N; ++k) {
+    c->ext_ms[k] = c->ext_flops[k] = c->ext_bytes[k] = 0.0;
+    c->ext_launches[k] = 0;
+  }
 }
 
 
@@ -316,7 +321,8 @@ int qtt_ctx_profile(qtt_ctx* c, int enable) {
       return QTT_ERR_OOM;
     }
   }
-  c->prof = enable != 0;
+  c->prof = enable == 1;
+  c->prof_mode = enable == 2 ? 2 : (enable ? 1 : 0);
   return QTT_OK;
 }
 
@@ -338,6 +344,10 @@ int qtt_ctx_profile_read(qtt_ctx* c, int kclass, double* total_ms, int64_t* laun
     fl += r.flops;
     if (r.sweep_idx >= 0) fl += r.per_sweep * std::max(1, sw[r.sweep_idx]);
   }
+  ms += c->ext_ms[kclass];
+  n += c->ext_launches[kclass];
+  fl += c->ext_flops[kclass];
+  by += c->ext_bytes[kclass];
   if (total_ms) *total_ms = ms;
   if (launches) *launches = n;
   if (flops) *flops = fl;
@@ -1115,9 +1125,33 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
   return QTT_OK;
 }
 
+// Start of the timed region of ms_homogenize: every load case of the first
+// wave arrives once (after its warm_iter-th iteration, its stream
+// synchronised, or when it ends earlier); the last arrival stamps the start
+// and releases the others.  Later load cases find it released.
+struct WarmGate {
+  std::mutex mu;
+  std::condition_variable cv;
+  int target = 1, count = 0;
+  std::atomic<bool> released{false};
+  std::chrono::steady_clock::time_point t0;
+  void arrive() {
+    std::unique_lock<std::mutex> lk(mu);
+    if (released) return;
+    if (++count >= target) {
+      t0 = std::chrono::steady_clock::now();
+      released = true;
+      cv.notify_all();
+      return;
+    }
+    cv.wait(lk, [&] { return released.load(); });
+  }
+};
+
 template <class R>
 int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2h, Ops& O, double tol, int max_rank,
-             const ms_opts& o, qtt_dtype dt, double* C_eff, ms_report* rep) {
+             const ms_opts& o, qtt_dtype dt, double* C_eff, ms_report* rep, WarmGate* gate = nullptr,
+             bool* arrived = nullptr) {
   typedef cplx<R> C;
   const SiteMap sm = site_map(rve);
   const int nc = rve->ncomp, dsp = sm.d, d = dsp + 1;
@@ -1298,11 +1332,20 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     qtt_tt*& ghat = ghat_hold.p;
     int it = 0;
     double res = 1.0;
+    double prev_norm2 = -1.0;   // float path: FP64 <x, x> of the current iterate, once known
     const qtt_complex one = {1.0, 0.0};
     cur_lc = lc;
     for (auto& v : prev) std::fill(v.begin(), v.end(), 0);
     call = 1;  // sketches depend only on the seed and the call order within one load case
+    if (gate && o.warm_iter <= 0 && !*arrived) {
+      cudaStreamSynchronize(c->stream);
+      *arrived = true;
+      gate->arrive();
+    }
     for (it = 1; it <= o.max_iter; ++it) {
+      const bool timed = gate && gate->released.load();   // inside the timed region from its start
+      const int64_t launches0 = c->launches;
+      if (c->prof_mode == 2) c->prof = timed;
       cur_it = it;
       cur_it_global = it;
       stage = "tau";
@@ -1390,33 +1433,42 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
           return QTT_ERR_NAN;
         }
       }
-      // relative change, on the difference train (orthogonalisation, no
-      // cancellation).  The residual that decides convergence is always an
-      // FP64 one: on the float path the difference train's cores are widened
-      // exactly to complex128 first, so it carries no float rounding beyond
-      // that of the iterates themselves
-      qtt_tt* diff = nullptr;
-      TRY(add_dev<R>(c, C(1, 0), xn, C(-1, 0), x, &diff));
+      // relative change ||eps_{m+1} - eps_m|| / ||E 1||, always evaluated in
+      // FP64.  FP64 path: on the difference train by orthogonalisation (a QR
+      // sweep; no cancellation, exact to FP64 rounding).  Float path: the
+      // iterates' cores are widened exactly to complex128 and
+      // ||a - b||^2 = <a,a> + <b,b> - 2 Re <a,b> is formed from FP64 inner
+      // products (transfer-matrix GEMMs spread over the whole GPU; <b,b> is
+      // the previous iteration's <a,a>).  Its cancellation leaves an absolute
+      // error of about 1e-8 ||a|| / ||E 1||, which is below 2% of every stop
+      // tolerance >= 1e-6 (the float path's iterates themselves carry
+      // single-precision noise of about 1e-5 at the grids measured), while a
+      // float QR sweep of the rank-2r difference train would cost a serial
+      // chain of one-CTA factorisations per iteration.
       double dn = 0;
       int s = QTT_OK;
       if (dt == QTT_C128) {
+        qtt_tt* diff = nullptr;
+        TRY(add_dev<R>(c, C(1, 0), xn, C(-1, 0), x, &diff));
         s = norm_dev<double>(c, diff, &dn);
+        tt_free(diff);
       } else {
-        // float path: a float residual first, so an iterate that is
-        // clearly not converged costs no FP64 sweep; once it comes within
-        // 10 tol the residual is recomputed in FP64 and that one decides.
-        // A float residual overestimating the true one only delays the FP64
-        // check by an iteration; a stop is never decided in float
-        s = norm_dev<R>(c, diff, &dn);
-        if (!s && dn / normE < 10.0 * tol && it >= std::max(1, (int)o.min_iter)) {
-          qtt_tt* wide = nullptr;
-          s = convert_tt(c, diff, QTT_C128, &wide);
-          if (!s) s = norm_dev<double>(c, wide, &dn);
-          if (wide) tt_free(wide);
-          if (rep) rep->fp64_residuals++;
+        qtt_tt *wa = nullptr, *wb = nullptr;
+        double aa[2] = {0, 0}, ab[2] = {0, 0}, bb[2] = {0, 0};
+        s = convert_tt(c, xn, QTT_C128, &wa);
+        if (!s) s = convert_tt(c, x, QTT_C128, &wb);
+        if (!s) s = dot_dev<double>(c, wa, wa, aa);
+        if (!s) s = dot_dev<double>(c, wa, wb, ab);
+        if (!s) {
+          if (prev_norm2 >= 0) bb[0] = prev_norm2;
+          else s = dot_dev<double>(c, wb, wb, bb);
         }
+        if (wa) tt_free(wa);
+        if (wb) tt_free(wb);
+        prev_norm2 = aa[0];
+        dn = sqrt(std::max(0.0, aa[0] + bb[0] - 2.0 * ab[0]));
+        if (rep) rep->fp64_residuals++;
       }
-      tt_free(diff);
       if (s) return s;
       res = dn / normE;
       if (debug_checks())
@@ -1424,8 +1476,20 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
                 *std::max_element(xn->r.begin(), xn->r.end()));
       tt_free(x);
       x = xn;
+      if (gate) {
+        if (timed && rep) {
+          rep->timed_iter++;
+          rep->timed_launches += c->launches - launches0;
+        }
+        if (it >= o.warm_iter && !*arrived) {
+          cudaStreamSynchronize(c->stream);
+          *arrived = true;
+          gate->arrive();
+        }
+      }
       if (res < tol && it >= std::max(1, (int)o.min_iter)) break;
     }
+    if (c->prof_mode == 2) c->prof = false;
     if (it > o.max_iter) it = o.max_iter;
     // sigma = C1 <eps> + (C2 - C1) <chi eps>
     std::vector<double> m1(2 * nc), m2(2 * nc);
@@ -1625,69 +1689,222 @@ extern "C" int tt_cross(qtt_ctx* c, const qtt_cross_fn* fn, double eps, int32_t 
   return s;
 }
 
-extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, double tol, int max_rank,
-                             const ms_opts* o, double* C_eff, ms_report* rep) {
-  if (!c || !rve || !C0 || !o || !C_eff || max_rank < 1) return QTT_ERR_ARG;
-  if ((rve->ncomp != 3 && rve->ncomp != 6) || !rve_bits_valid(rve)) return QTT_ERR_ARG;
-  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32) return QTT_ERR_ARG;
-  const int nc = rve->ncomp;
-  std::vector<double> C1(nc * nc, 0.0), C2(nc * nc, 0.0);
+// Operator trains of one RVE (phase indicator, stiffness contrasts, Green
+// operator, SFFT) with what the solve needs of the RVE description.
+struct ms_ops {
+  qtt_rve rve{};                  // scalars only: the host arrays are not kept
+  int nc = 0;
+  std::vector<double> C1, C2, C0;
   double k0 = 0, lam0 = 0, mu0 = 0;
+  Ops O;
+  double setup_ms = 0;
+  int64_t setup_launches = 0;
+};
+
+extern "C" int ms_setup(qtt_ctx* c, const qtt_rve* rve, const double* C0, double op_tol, ms_ops** out) {
+  if (!c || !rve || !C0 || !out) return QTT_ERR_ARG;
+  *out = nullptr;
+  if ((rve->ncomp != 3 && rve->ncomp != 6) || !rve_bits_valid(rve)) return QTT_ERR_ARG;
+  ms_ops* m = new (std::nothrow) ms_ops();
+  if (!m) return QTT_ERR_OOM;
+  const int nc = rve->ncomp;
+  m->nc = nc;
+  m->C1.assign(nc * nc, 0.0);
+  m->C2.assign(nc * nc, 0.0);
+  m->C0.assign(C0, C0 + nc * nc);
   if (nc == 3) {
     for (int i = 0; i < 3; ++i) {
-      C1[i * 3 + i] = rve->k1;
-      C2[i * 3 + i] = rve->k2;
+      m->C1[i * 3 + i] = rve->k1;
+      m->C2[i * 3 + i] = rve->k2;
     }
-    k0 = C0[0];
-    if (!(k0 > 0)) return QTT_ERR_ARG;
+    m->k0 = C0[0];
+    if (!(m->k0 > 0)) {
+      delete m;
+      return QTT_ERR_ARG;
+    }
   } else {
     auto iso = [](double lam, double mu, double* M) {
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) M[i * 6 + j] = lam + (i == j ? 2 * mu : 0.0);
       for (int i = 3; i < 6; ++i) M[i * 6 + i] = mu;
     };
-    iso(rve->lam1, rve->mu1, C1.data());
-    iso(rve->lam2, rve->mu2, C2.data());
-    lam0 = C0[1];
-    mu0 = C0[3 * 6 + 3];
-    if (!(mu0 > 0)) return QTT_ERR_ARG;
+    iso(rve->lam1, rve->mu1, m->C1.data());
+    iso(rve->lam2, rve->mu2, m->C2.data());
+    m->lam0 = C0[1];
+    m->mu0 = C0[3 * 6 + 3];
+    if (!(m->mu0 > 0)) {
+      delete m;
+      return QTT_ERR_ARG;
+    }
   }
+  const int64_t l0 = c->launches;
+  auto t0 = std::chrono::steady_clock::now();
+  int s = build_ops(c, rve, m->C1.data(), m->C2.data(), C0, op_tol > 0 ? op_tol : 1e-10, m->k0, m->lam0, m->mu0,
+                    &m->O);
+  if (!s && cudaStreamSynchronize(c->stream) != cudaSuccess) s = QTT_ERR_CUDA;
+  if (s) {
+    m->O.release();
+    delete m;
+    return s;
+  }
+  m->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  m->setup_launches = c->launches - l0;
+  m->rve = *rve;
+  m->rve.indicator = nullptr;
+  m->rve.boxes = nullptr;
+  m->rve.ellipsoids = nullptr;
+  *out = m;
+  return QTT_OK;
+}
+
+extern "C" void ms_ops_destroy(ms_ops* m) {
+  if (!m) return;
+  m->O.release();
+  delete m;
+}
+
+extern "C" int ms_ops_ranks(const ms_ops* m, int32_t* green_rank, int32_t* phase_rank) {
+  if (!m) return QTT_ERR_ARG;
+  if (green_rank) *green_rank = m->O.green_rank;
+  if (phase_rank) *phase_rank = m->O.phase_rank;
+  return QTT_OK;
+}
+
+extern "C" int ms_homogenize_ops(qtt_ctx* c, const ms_ops* m, double tol, int max_rank, const ms_opts* o,
+                                 double* C_eff, ms_report* rep) {
+  if (!c || !m || !o || !C_eff || max_rank < 1) return QTT_ERR_ARG;
+  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32) return QTT_ERR_ARG;
+  const int nc = m->nc;
+  const qtt_rve* rve = &m->rve;
+  Ops& O = const_cast<Ops&>(m->O);   // read only: every solve converts the trains to its own copies
+  const std::vector<double>& C1 = m->C1;
+  const std::vector<double>& C2 = m->C2;
   if (rep) memset(rep, 0, sizeof(*rep));
   for (int i = 0; i < nc * nc; ++i) C_eff[i] = 0.0;
   const int64_t l0 = c->launches;
-  auto t0 = std::chrono::steady_clock::now();
-  Ops O;
-  int s = build_ops(c, rve, C1.data(), C2.data(), C0, o->op_tol > 0 ? o->op_tol : 1e-10, k0, lam0, mu0, &O);
-  if (s) {
-    O.release();
-    return s;
-  }
-  cudaStreamSynchronize(c->stream);
+  int s = QTT_OK;
   auto t1 = std::chrono::steady_clock::now();
-  if (o->prec == QTT_PREC_F64) {
-    s = ms_solve<double>(c, rve, C1.data(), C2.data(), O, tol, max_rank, *o, QTT_C128, C_eff, rep);
+  std::vector<int> lcs;
+  for (int lc = 0; lc < nc; ++lc)
+    if (o->load_mask & (1 << lc)) lcs.push_back(lc);
+  const int nw = (o->trace || o->strain) ? 1 : std::max(1, std::min<int>(o->lc_workers, (int)lcs.size()));
+  WarmGate gate;
+  gate.target = nw;
+  // one solve of the load cases in opts->load_mask on context wc
+  auto solve_on = [&](qtt_ctx* wc, const ms_opts& oj, double* Cj, ms_report* rj, bool* arrived) -> int {
+    int st;
+    if (oj.prec == QTT_PREC_F64) {
+      st = ms_solve<double>(wc, rve, C1.data(), C2.data(), O, tol, max_rank, oj, QTT_C128, Cj, rj, &gate, arrived);
+    } else {
+      TcScope tc(wc, oj.prec == QTT_PREC_TC32);
+      st = ms_solve<float>(wc, rve, C1.data(), C2.data(), O, tol, max_rank, oj, QTT_C64, Cj, rj, &gate, arrived);
+    }
+    if (!st && wc->d_tcerr) {
+      int h = 0;
+      sync_read(wc, &h, wc->d_tcerr, sizeof(int));
+      if (h) st = QTT_ERR_TIMEOUT;
+    }
+    cudaStreamSynchronize(wc->stream);
+    return st;
+  };
+  if (nw <= 1) {
+    bool arrived = false;
+    s = solve_on(c, *o, C_eff, rep, &arrived);
+    if (!arrived) gate.arrive();
   } else {
-    TcScope tc(c, o->prec == QTT_PREC_TC32);
-    s = ms_solve<float>(c, rve, C1.data(), C2.data(), O, tol, max_rank, *o, QTT_C64, C_eff, rep);
-  }
-  if (!s && c->d_tcerr) {
-    int h = 0;
-    sync_read(c, &h, c->d_tcerr, sizeof(int));
-    if (h) s = QTT_ERR_TIMEOUT;
+    // load cases on worker contexts (own stream, own host thread), sharing
+    // the operator trains, which are complete on c's stream (synchronised
+    // above) and only read by the solves
+    std::atomic<size_t> next(0);
+    std::atomic<int> status(QTT_OK);
+    std::mutex mu;
+    auto work = [&]() {
+      qtt_ctx* wc = nullptr;
+      int st = qtt_ctx_create(c->device, nullptr, &wc);
+      if (st) {
+        status = st;
+        gate.arrive();
+        return;
+      }
+      if (c->prof_mode) qtt_ctx_profile(wc, c->prof_mode);
+      wc->fail_alloc_after = -1;
+      for (;;) {
+        const size_t j = next++;
+        if (j >= lcs.size()) break;
+        const int lc = lcs[j];
+        ms_opts oj = *o;
+        oj.load_mask = 1 << lc;
+        std::vector<double> Cj(nc * nc, 0.0);
+        ms_report rj;
+        memset(&rj, 0, sizeof(rj));
+        bool arrived = false;
+        st = status.load() == QTT_OK ? solve_on(wc, oj, Cj.data(), &rj, &arrived) : status.load();
+        if (!arrived) gate.arrive();
+        std::lock_guard<std::mutex> lock(mu);
+        if (st) {
+          status = st;
+          continue;
+        }
+        for (int I = 0; I < nc; ++I) C_eff[I * nc + lc] = Cj[I * nc + lc];
+        if (rep) {
+          rep->iterations[lc] = rj.iterations[lc];
+          rep->residual[lc] = rj.residual[lc];
+          rep->sigma_imag_max = std::max(rep->sigma_imag_max, rj.sigma_imag_max);
+          rep->max_rank_seen = std::max(rep->max_rank_seen, rj.max_rank_seen);
+          rep->sketch_width_sum += rj.sketch_width_sum;
+          rep->fallbacks += rj.fallbacks;
+          rep->fp64_residuals += rj.fp64_residuals;
+          rep->timed_iter += rj.timed_iter;
+          rep->timed_launches += rj.timed_launches;
+        }
+      }
+      std::lock_guard<std::mutex> lock(mu);
+      c->launches += wc->launches;
+      if (c->prof_mode) {
+        for (int k = 0; k < PK_N; ++k) {
+          double ms = 0, fl = 0, by = 0;
+          int64_t n = 0;
+          if (qtt_ctx_profile_read(wc, k, &ms, &n, &fl, &by) == QTT_OK) {
+            c->ext_ms[k] += ms;
+            c->ext_launches[k] += n;
+            c->ext_flops[k] += fl;
+            c->ext_bytes[k] += by;
+          }
+        }
+      }
+      qtt_ctx_destroy(wc);
+    };
+    std::vector<std::thread> th;
+    for (int w = 0; w < nw; ++w) th.emplace_back(work);
+    for (auto& t : th) t.join();
+    s = status.load();
   }
   cudaStreamSynchronize(c->stream);
   auto t2 = std::chrono::steady_clock::now();
   if (rep) {
+    rep->timed_ms = gate.released ? std::chrono::duration<double, std::milli>(t2 - gate.t0).count() : 0.0;
     rep->green_rank = O.green_rank;
     rep->phase_rank = O.phase_rank;
-  }
-  O.release();
-  if (rep) {
-    rep->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     rep->iterate_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
     rep->kernel_launches = c->launches - l0;
   }
   if (cudaGetLastError() != cudaSuccess) return QTT_ERR_CUDA;
+  return s;
+}
+
+extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, double tol, int max_rank,
+                             const ms_opts* o, double* C_eff, ms_report* rep) {
+  if (!c || !rve || !C0 || !o || !C_eff || max_rank < 1) return QTT_ERR_ARG;
+  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32) return QTT_ERR_ARG;
+  ms_ops* m = nullptr;
+  int s = ms_setup(c, rve, C0, o->op_tol, &m);
+  if (s) return s;
+  s = ms_homogenize_ops(c, m, tol, max_rank, o, C_eff, rep);
+  if (rep) {
+    rep->setup_ms = m->setup_ms;
+    rep->kernel_launches += m->setup_launches;
+  }
+  ms_ops_destroy(m);
   return s;
 }
 

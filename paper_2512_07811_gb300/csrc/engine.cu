@@ -769,7 +769,15 @@ int round_det(qtt_ctx* c, const qtt_tt* x, double eps, int max_rank, const int* 
     // of C^H first pays for itself
     const int64_t jp = Tcols;
     int64_t jq = rk;
-    if (polar || jp <= 4 * jq || jp * jq <= 4096) {
+    // Jacobi on C^H directly only where one of the fast single-launch
+    // kernels takes the (jp x jq) shape (the block-cyclic cluster kernel or
+    // the one-CTA shared-memory kernel; FP64 goes to the all-SM kernel
+    // anyway); otherwise, e.g. 512 x 256 in FP32, the QR first leaves a
+    // jq x jq factor that they do take
+    int bsd = 0;
+    const bool direct_fast = sizeof(R) == 8 || jq < 32 || qtt_jacobi_block_plan<R>((int)jp, (int)jq, &bsd) != 0 ||
+                             qtt_jacobi_smem_bytes<R>((int)jp, (int)jq) <= 200 * 1024;
+    if (polar || jp * jq <= 4096 || (jp <= 4 * jq && (jp < jq || direct_fast))) {
       TRY(Cb.alloc(c, (size_t)rk * Tcols * sizeof(cplx<R>)));
       if (left_orth) {
         c->launches++;

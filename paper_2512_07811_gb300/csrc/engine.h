@@ -25,12 +25,17 @@ struct qtt_ctx {
   bool own_stream = false;
   int64_t launches = 0;
   bool prof = false;
+  int prof_mode = 0;         // 0 off, 1 every launch, 2 timed iterations of ms_homogenize only
   std::vector<ProfRec> recs;
   int* d_sweeps = nullptr;   // device counters written by profiled Jacobi launches
   int sweeps_cap = 0, sweeps_used = 0;
   bool tc = false;           // route large float contractions to the tensor cores
   int* d_tcerr = nullptr;    // bounded-wait failure flag of the tensor-core GEMM
   int64_t fail_alloc_after = -1;  // test hook: allocations left before dalloc fails (-1: off)
+  // profiler totals handed over by contexts that worked for this one (the
+  // load-case workers of ms_homogenize), per kernel class
+  double ext_ms[PK_N] = {0, 0, 0, 0}, ext_flops[PK_N] = {0, 0, 0, 0}, ext_bytes[PK_N] = {0, 0, 0, 0};
+  int64_t ext_launches[PK_N] = {0, 0, 0, 0};
 };
 
 // Scoped switch of the tensor-core route for one ABI call.

@@ -121,7 +121,8 @@ class MSOpts(C.Structure):
     _fields_ = [("prec", C.c_int), ("eps", C.c_double), ("op_tol", C.c_double), ("max_iter", C.c_int32),
                 ("oversample", C.c_int32), ("load_mask", C.c_int32), ("min_iter", C.c_int32),
                 ("seed", C.c_uint64), ("predictor", C.c_void_p), ("trace", C.POINTER(C.c_float)),
-                ("trace_cap", C.c_int64), ("green_amen", C.c_int32), ("strain", C.POINTER(C.c_void_p))]
+                ("trace_cap", C.c_int64), ("green_amen", C.c_int32), ("strain", C.POINTER(C.c_void_p)),
+                ("lc_workers", C.c_int32), ("warm_iter", C.c_int32)]
 
 
 class MSReport(C.Structure):
@@ -129,7 +130,8 @@ class MSReport(C.Structure):
                 ("max_rank_seen", C.c_int32), ("setup_ms", C.c_double), ("iterate_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("trace_len", C.c_int64), ("sketch_width_sum", C.c_int64),
                 ("fallbacks", C.c_int32), ("green_rank", C.c_int32), ("phase_rank", C.c_int32),
-                ("fp64_residuals", C.c_int32)]
+                ("fp64_residuals", C.c_int32), ("timed_ms", C.c_double), ("timed_iter", C.c_int32),
+                ("timed_launches", C.c_int64)]
 
 
 MLP_FEATURES = 10
@@ -152,6 +154,7 @@ _sig("qtt_ctx_destroy", None, [_P])
 _sig("qtt_ctx_sync", C.c_int, [_P])
 _sig("qtt_ctx_launch_count", C.c_int64, [_P])
 _sig("qtt_ctx_fail_alloc_after", C.c_int, [_P, C.c_int64])
+_sig("qtt_measure_peak", C.c_int, [_P, C.c_int, C.POINTER(C.c_double)])
 _sig("qtt_ctx_profile", C.c_int, [_P, C.c_int])
 _sig("qtt_ctx_profile_read", C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)])
@@ -206,16 +209,22 @@ _sig("tt_cross", C.c_int, [_P, C.POINTER(CrossFn), C.c_double, C.c_int32, C.c_in
                           C.POINTER(_P), C.POINTER(CrossInfo)])
 _sig("ms_homogenize", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
                                 C.POINTER(MSOpts), C.POINTER(C.c_double), C.POINTER(MSReport)])
+_sig("ms_setup", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.POINTER(_P)])
+_sig("ms_homogenize_ops", C.c_int, [_P, _P, C.c_double, C.c_int, C.POINTER(MSOpts), C.POINTER(C.c_double),
+                                    C.POINTER(MSReport)])
+_sig("ms_ops_destroy", None, [_P])
+_sig("ms_ops_ranks", C.c_int, [_P, _I32P, _I32P])
 
 EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_sync", "qtt_ctx_launch_count",
-            "qtt_ctx_fail_alloc_after",
+            "qtt_ctx_fail_alloc_after", "qtt_measure_peak",
             "qtt_ctx_profile", "qtt_ctx_profile_read",
             "qtt_tt_create", "qtt_tt_destroy", "qtt_tt_ncores", "qtt_tt_ranks", "qtt_tt_modes", "qtt_tt_dtype",
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
             "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_polar", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_norm",
             "tt_from_dense", "tt_cross", "tt_amen_mv", "tt_contract_voxels", "qtt_site_order", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
-            "ms_homogenize_batch", "qtt_cgemm", "qtt_cgemm_noalloc",
+            "ms_homogenize_batch", "ms_setup", "ms_homogenize_ops", "ms_ops_destroy", "ms_ops_ranks",
+            "qtt_cgemm", "qtt_cgemm_noalloc",
             "qtt_mlp_create", "qtt_mlp_destroy", "qtt_mlp_param_count", "qtt_mlp_set_params",
             "qtt_mlp_get_params", "qtt_mlp_forward", "qtt_mlp_train_step"]
 
@@ -244,11 +253,31 @@ class Context:
                 stream = None
         _check(_lib.qtt_ctx_create(int(device), _P(stream) if stream else None, C.byref(h)), "qtt_ctx_create")
         self.h = h
+        # Trains, operators and predictors free their device memory on this
+        # context's stream, so the context is destroyed only after the last of
+        # them: a reference cycle collected in one pass may finalise the
+        # context before its children.
+        self._children = 0
+        self._close_pending = False
 
-    def close(self):
+    def _adopt(self):
+        self._children += 1
+
+    def _release(self):
+        self._children -= 1
+        if self._children <= 0 and self._close_pending:
+            self._destroy()
+
+    def _destroy(self):
         if getattr(self, "h", None) and _ALIVE[0]:
             _lib.qtt_ctx_destroy(self.h)
         self.h = None
+
+    def close(self):
+        if getattr(self, "_children", 0) > 0:
+            self._close_pending = True
+        else:
+            self._destroy()
 
     def __del__(self):
         self.close()
@@ -264,10 +293,19 @@ class Context:
         """Test hook: the allocation after `n` more succeed fails (QTT_ERR_OOM); n < 0 turns it off."""
         _check(_lib.qtt_ctx_fail_alloc_after(self.h, int(n)), "qtt_ctx_fail_alloc_after")
 
+    def measure_peak(self, which: str) -> float:
+        """FP32 ("fp32") or FP64 ("fp64") fused-multiply-add peak of this GPU in TFLOP/s."""
+        out = C.c_double()
+        _check(_lib.qtt_measure_peak(self.h, {"fp32": 0, "fp64": 1}[which], C.byref(out)), "qtt_measure_peak")
+        return float(out.value)
+
     KERNEL_CLASSES = {"gemm": 0, "qr": 1, "jacobi": 2, "elem": 3}
 
-    def profile(self, enable: bool):
-        _check(_lib.qtt_ctx_profile(self.h, 1 if enable else 0), "qtt_ctx_profile")
+    def profile(self, enable):
+        """True/1: record every launch; 2: only the timed iterations of
+        ms_homogenize (report.timed_ms); False/0: off."""
+        mode = 2 if enable == 2 else (1 if enable else 0)
+        _check(_lib.qtt_ctx_profile(self.h, mode), "qtt_ctx_profile")
 
     def profile_read(self, kclass: str):
         ms, fl, by = C.c_double(), C.c_double(), C.c_double()
@@ -283,6 +321,8 @@ class TT:
     def __init__(self, ctx: Context, handle):
         self.ctx = ctx
         self.h = handle
+        ctx._adopt()
+        self._adopted = True
 
     @classmethod
     def from_cores(cls, ctx: Context, cores, dtype=C128):
@@ -301,6 +341,9 @@ class TT:
         if getattr(self, "h", None) and _ALIVE[0]:
             _lib.qtt_tt_destroy(self.h)
         self.h = None
+        if getattr(self, "_adopted", False):
+            self._adopted = False
+            self.ctx._release()
 
     def __del__(self):
         self.close()
@@ -348,6 +391,8 @@ class MPO:
         self.ctx = ctx
         self.h = handle
         self.d = d
+        ctx._adopt()
+        self._adopted = True
 
     @classmethod
     def from_cores(cls, ctx: Context, cores, dtype=C128):
@@ -369,6 +414,9 @@ class MPO:
         if getattr(self, "h", None) and _ALIVE[0]:
             _lib.qtt_mpo_destroy(self.h)
         self.h = None
+        if getattr(self, "_adopted", False):
+            self._adopted = False
+            self.ctx._release()
 
     def __del__(self):
         self.close()
@@ -597,12 +645,17 @@ class MLP:
         h = _P()
         _check(_lib.qtt_mlp_create(ctx.h, int(n_features), int(seed), C.byref(h)), "qtt_mlp_create")
         self.h = h
+        ctx._adopt()
+        self._adopted = True
         self.n_features = n_features
 
     def close(self):
         if getattr(self, "h", None) and _ALIVE[0]:
             _lib.qtt_mlp_destroy(self.h)
         self.h = None
+        if getattr(self, "_adopted", False):
+            self._adopted = False
+            self.ctx._release()
 
     def __del__(self):
         self.close()
@@ -701,11 +754,56 @@ def ms_homogenize_batch(ctx: Context, problems, tol: float, max_rank: int, worke
     return res, [reps[i] for i in range(n)]
 
 
+class MSOps:
+    """The operator trains of one RVE (ms_setup), reusable by many solves."""
+
+    def __init__(self, ctx: Context, handle, ncomp: int, setup_ms: float):
+        self.ctx = ctx
+        self.h = handle
+        self.ncomp = ncomp
+        self.setup_ms = setup_ms
+        ctx._adopt()
+        self._adopted = True
+
+    @property
+    def ranks(self):
+        g, p = C.c_int32(), C.c_int32()
+        _check(_lib.ms_ops_ranks(self.h, C.byref(g), C.byref(p)), "ms_ops_ranks")
+        return int(g.value), int(p.value)
+
+    def close(self):
+        if getattr(self, "h", None) and _ALIVE[0]:
+            _lib.ms_ops_destroy(self.h)
+        self.h = None
+        if getattr(self, "_adopted", False):
+            self._adopted = False
+            self.ctx._release()
+
+    def __del__(self):
+        self.close()
+
+
+def ms_setup(ctx: Context, indicator, kind: str, moduli, C0, op_tol: float = 1e-10, interleaved: bool = True,
+             op_cross: bool = False) -> MSOps:
+    """Operator trains of an RVE (the setup of ms_homogenize) as a handle that
+    ms_homogenize(..., ops=handle) reuses; same arguments as ms_homogenize."""
+    import time as _time
+    rve, keep = _rve(indicator, kind, moduli, interleaved, op_cross)
+    nc = rve.ncomp
+    C0a = np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(nc, nc))
+    h = _P()
+    t0 = _time.perf_counter()
+    _check(_lib.ms_setup(ctx.h, C.byref(rve), C0a.ctypes.data_as(C.POINTER(C.c_double)), float(op_tol),
+                         C.byref(h)), "ms_setup")
+    return MSOps(ctx, h, nc, (_time.perf_counter() - t0) * 1e3)
+
+
 def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, tol: float, max_rank: int,
                   eps: float = 1e-6, op_tol: float = 1e-10, prec: int = PREC_F64, max_iter: int = 100,
                   oversample: int = 8, load_mask: int | None = None, interleaved: bool = True,
                   min_iter: int = 1, seed: int = 12345, predictor: "MLP | None" = None, trace_cap: int = 0,
-                  op_cross: bool = False, green_amen: bool = False, return_strain: bool = False):
+                  op_cross: bool = False, green_amen: bool = False, return_strain: bool = False,
+                  lc_workers: int = 1, warm_iter: int = 0, ops: "MSOps | None" = None):
     """Effective tensor of a two-phase RVE (phase 2 where indicator == 1).
 
     kind "scalar": moduli = (k1, k2), C0 = 3x3; kind "elastic": moduli =
@@ -714,10 +812,19 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
     op_cross builds the Green operator train by TT-cross at any size (it is
     always so above 2^27 voxels); green_amen applies it by AMEn;
     return_strain puts the converged strain train of the last load case in
-    report.strain (see contract_voxels).  Returns (C_eff, report)."""
-    rve, keep = _rve(indicator, kind, moduli, interleaved, op_cross)
-    nc = rve.ncomp
-    C0a = np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(nc, nc))
+    report.strain (see contract_voxels); lc_workers solves that many load
+    cases at the same time on their own streams (operators built once);
+    report.timed_ms times the iterations after the first warm_iter of every
+    load case; ops (from ms_setup) reuses operator trains built before, and
+    indicator, moduli, C0, op_tol, interleaved and op_cross are then those of
+    the setup.  Returns (C_eff, report)."""
+    if ops is not None:
+        nc = ops.ncomp
+        C0a = None
+    else:
+        rve, keep = _rve(indicator, kind, moduli, interleaved, op_cross)
+        nc = rve.ncomp
+        C0a = np.ascontiguousarray(np.asarray(C0, dtype=np.float64).reshape(nc, nc))
     o = MSOpts()
     o.prec = int(prec)
     o.eps = float(eps)
@@ -732,13 +839,19 @@ def ms_homogenize(ctx: Context, indicator: np.ndarray, kind: str, moduli, C0, to
     o.trace = _fptr(trace) if trace_cap > 0 else None
     o.trace_cap = int(trace_cap)
     o.green_amen = 1 if green_amen else 0
+    o.lc_workers = int(lc_workers)
+    o.warm_iter = int(warm_iter)
     strain = _P()
     o.strain = C.pointer(strain) if return_strain else None
     out = np.zeros((nc, nc), dtype=np.float64)
     rep = MSReport()
-    _check(_lib.ms_homogenize(ctx.h, C.byref(rve), C0a.ctypes.data_as(C.POINTER(C.c_double)), float(tol),
-                              int(max_rank), C.byref(o), out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep)),
-           "ms_homogenize")
+    if ops is not None:
+        _check(_lib.ms_homogenize_ops(ctx.h, ops.h, float(tol), int(max_rank), C.byref(o),
+                                      out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep)), "ms_homogenize_ops")
+    else:
+        _check(_lib.ms_homogenize(ctx.h, C.byref(rve), C0a.ctypes.data_as(C.POINTER(C.c_double)), float(tol),
+                                  int(max_rank), C.byref(o), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                  C.byref(rep)), "ms_homogenize")
     if trace_cap > 0:
         rep.trace_rows = trace[:rep.trace_len].copy()
     if return_strain:

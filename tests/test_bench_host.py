@@ -1,8 +1,11 @@
 """The bench's host-side legs work without a GPU: the CPU baseline (the
-oracle on the host cores, threaded and with one BLAS thread in a child
-process) returns a well-formed record."""
+dense FFT Moulinec-Suquet oracle on the host cores, on the bench's sphere
+RVE) returns a well-formed record, and the bounds the bench checks an
+effective tensor against hold for a tensor inside them and fail outside."""
 import os
 import sys
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -11,8 +14,22 @@ if ROOT not in sys.path:
 
 def test_cpu_baseline_record():
     import bench
-    rec = bench.cpu_baseline(16, budget_s=0.3)
-    assert rec["kind"] == "oracle" and rec["unit"] == "TFLOP/s" and rec["value"] > 0
-    assert rec["cores"] >= 1 and "repetitions" in rec["sample"]
-    one = rec["single_core"]
-    assert one["cores"] == 1 and one["value"] > 0 and one["repetitions"] >= 1
+    rec = bench.cpu_baseline(3, budget_s=0.3)
+    assert rec["kind"] == "oracle" and rec["unit"] == "iterations/s" and rec["value"] > 0
+    assert rec["cores"] >= 1 and "iterations" in rec["sample"]
+
+
+def test_bound_checks():
+    import bench
+    N, rows, moduli, C0 = bench.sphere_problem(3)
+    lam1, mu1, lam2, mu2 = moduli
+    f = 0.2
+    mid = 0.5 * ((1 - f) * bench.iso_voigt(lam1, mu1) + f * bench.iso_voigt(lam2, mu2)
+                 + np.linalg.inv((1 - f) * np.linalg.inv(bench.iso_voigt(lam1, mu1))
+                                 + f * np.linalg.inv(bench.iso_voigt(lam2, mu2))))
+    c = bench.checks(mid, moduli, f)
+    assert c["voigt_minus_C_min_eig"] > 0 and c["C_minus_reuss_min_eig"] > 0 and c["asymmetry"] < 1e-12
+    lo, hi = c["hs_bulk_bounds"]
+    assert lo < hi
+    c2 = bench.checks(2.0 * bench.iso_voigt(lam2, mu2), moduli, f)
+    assert c2["voigt_minus_C_min_eig"] < 0 and not c2["bulk_within_hs"]

@@ -125,3 +125,40 @@ def test_round_batch_bench_shape(Q):
         for out in (y, y1):
             a = [t.astype(np.complex128) for t in out.cores()]
             assert T.tt_norm(T.tt_add(a, c, 1.0, -1.0)) < 5e-5 * nz
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_concurrent_load_cases_equal_sequential(Q, prec):
+    """The six load cases of an 8^3 elastic sphere solved at the same time on
+    six streams (operators built once, shared read-only) give the same
+    effective tensor bit for bit as one after another, and the timed region
+    counts the iterations after the warm-up of every load case."""
+    ctx = Q.Context(0)
+    lam1, mu1 = I.lame_from_young(1.0, 0.3)
+    lam2, mu2 = I.lame_from_young(10.0, 0.3)
+    C0 = MS.iso_voigt(0.5 * (lam1 + lam2), 0.5 * (mu1 + mu2))
+    geo = Q.Ellipsoids(I.sphere_rows(0.2), (8, 8, 8))
+    p = Q.PREC_F64 if prec == "f64" else Q.PREC_F32
+    kw = dict(tol=0.0, max_rank=64, eps=1e-6, prec=p, max_iter=5, min_iter=5, interleaved=False, warm_iter=2)
+    Cs, rs = Q.ms_homogenize(ctx, geo, "elastic", (lam1, mu1, lam2, mu2), C0, lc_workers=1, **kw)
+    Cc, rc = Q.ms_homogenize(ctx, geo, "elastic", (lam1, mu1, lam2, mu2), C0, lc_workers=6, **kw)
+    np.testing.assert_array_equal(Cs, Cc)
+    assert rc.timed_iter == 6 * 3 and rc.timed_ms > 0 and rc.timed_launches > 0
+    assert list(rc.iterations) == [5] * 6
+
+
+def test_setup_handle_reused_equals_one_call(Q):
+    """Operator trains built once (ms_setup) and used by two solves of
+    different precisions give the effective tensors of two ms_homogenize
+    calls bit for bit."""
+    ctx = Q.Context(0)
+    geo = Q.Ellipsoids(I.sphere_rows(0.2), (8, 8, 8))
+    kw = dict(tol=1e-6, max_rank=64, eps=1e-6, max_iter=20, interleaved=False, load_mask=0b11)
+    ops = Q.ms_setup(ctx, geo, "scalar", (1.0, 10.0), 5.5 * np.eye(3), interleaved=False)
+    g, p = ops.ranks
+    assert g > 1 and p > 1
+    for prec in [Q.PREC_F64, Q.PREC_F32]:
+        Ca, ra = Q.ms_homogenize(ctx, geo, "scalar", (1.0, 10.0), 5.5 * np.eye(3), prec=prec, **kw)
+        Cb, rb = Q.ms_homogenize(ctx, None, "scalar", None, None, prec=prec, ops=ops, **kw)
+        np.testing.assert_array_equal(Ca, Cb)
+        assert rb.setup_ms == 0 and ra.green_rank == rb.green_rank == g

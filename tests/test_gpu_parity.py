@@ -132,14 +132,17 @@ def test_round_forced_by_max_rank(Q, ctx):
     assert rel_diff(y.cores(), ref) < 1e-10
 
 
-@pytest.mark.parametrize("k,n0,n1", [(17, 39, 100), (25, 55, 150), (50, 300, 300), (64, 140, 256), (100, 205, 500)])
+@pytest.mark.parametrize("k,n0,n1", [(17, 39, 100), (25, 55, 150), (50, 300, 300), (64, 140, 256), (100, 205, 500),
+                                     (128, 300, 512)])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_round_factorisation_shapes(Q, ctx, k, n0, n1, fp32):
     """Two cores (1, n0, 2k) and (2k, n1, 1) holding 1.75 x a rank-k train:
     the left sweep factors an n0 x 2k matrix, the truncation SVD a
     (n1 x 2k) C^H, so the cases reach the block-cyclic Jacobi with odd block
     widths and 4 or 8 CTAs, 8 and 16 rows per lane, the shared-memory limit
-    (2k = 200, 500 rows), and the panel QR beyond 256 rows.  The rank-k
+    (2k = 200, 500 rows), the panel QR beyond 256 rows, and a 512 x 256 C^H
+    that no single-launch Jacobi kernel takes (QR first, then Jacobi on the
+    256 x 256 factor).  The rank-k
     truncation is unique: ranks equal, 1e-12 (FP64) / 1e-5 (FP32) parity."""
     rng = np.random.default_rng(100 + k)
     a = (rng.standard_normal((1, n0, k)) + 1j * rng.standard_normal((1, n0, k))) / math.sqrt(2 * k)
