@@ -68,6 +68,9 @@ def parse():
     p.add_argument("--batch", type=int, default=32)
     p.add_argument("--prec", choices=["f32", "tc32"], default="f32",
                    help="fast path arithmetic: float CUDA cores, or tensor cores for the large contractions")
+    p.add_argument("--profile-region", action="store_true",
+                   help="only the fast solve of the headline, its iterations bracketed by cudaProfilerStart/Stop "
+                        "(for ncu --profile-from-start off); prints one line with the launch count")
     return p.parse_args()
 
 
@@ -424,6 +427,29 @@ def roofline(prof, repp, peaks, mpeaks):
     return roof
 
 
+def profile_region(args):
+    """The headline's fast solve alone for a profiler: operators built and one
+    warm-up solve outside the region, then `steps` iterations of all six load
+    cases between cudaProfilerStart and cudaProfilerStop."""
+    import torch
+    from paper_2512_07811_gb300 import qtt as Q
+    stream = torch.cuda.Stream()
+    ctx = Q.Context(0, stream.cuda_stream)
+    geo, moduli, C0 = sphere_geometry(Q, args.n)
+    ops = Q.ms_setup(ctx, geo, "elastic", moduli, C0, op_tol=1e-10, interleaved=False)
+    sphere_solve(Q, ctx, args.n, Q.PREC_F32, 1, 1, ops)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    C, rep, wall = sphere_solve(Q, ctx, args.n, Q.PREC_F32, 0, args.steps, ops)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"profile_region": "elastic sphere %d^3, %d iterations of 6 load cases" % (1 << args.n,
+                                                                                                 args.steps),
+                      "launches": int(rep.timed_launches), "timed_ms": rep.timed_ms}))
+    ops.close()
+    return 0
+
+
 # ------------------------------------------------------- CPU oracle arm
 def dense_oracle_sample(n, iters):
     """The dense FFT Moulinec-Suquet oracle (Algorithm 1, NumPy FP64) on the
@@ -502,6 +528,8 @@ def main():
         print(json.dumps(line))
         return 0
 
+    if args.profile_region:
+        return profile_region(args)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -206,6 +206,7 @@ int convert_mpo(qtt_ctx* c, const qtt_mpo* A, qtt_dtype dt, qtt_mpo** out) {
   int st;
   qtt_mpo* B = mpo_alloc(c, A->d, A->no, A->ni, A->g, dt, &st);
   if (!B) return st;
+  B->diag = A->diag;
   for (int k = 0; k < A->d; ++k) {
     int64_t cnt = (int64_t)A->g[k] * A->no[k] * A->ni[k] * A->g[k + 1];
     if (A->dtype == dt) {
@@ -744,6 +745,7 @@ int qtt_mpo_diag(qtt_ctx* c, const qtt_tt* x, qtt_mpo** out) {
       mpo_free(A);
       return s;
     }
+    A->diag[k] = 1;
   }
   *out = A;
   return QTT_OK;
@@ -1040,6 +1042,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
   for (int k = 1; k < d; ++k) {
     c->launches++;
     TRY(qtt_diag_mpo_core<double>(core_ptr<zc>(g, k), g->r[k], 2, g->r[k + 1], core_ptr<zc>(ops->gamma, k), c->stream));
+    ops->gamma->diag[k] = 1;
   }
   tt_free(g);
   // stiffness contrast operators
@@ -1054,6 +1057,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
   for (int k = 1; k < d; ++k) {
     c->launches++;
     TRY(qtt_identity_core<double>(1, 2, core_ptr<zc>(ops->dCa, k), c->stream));
+    ops->dCa->diag[k] = 1;
   }
   // bond k of the full operator sits between site k-1 and site k; spatial
   // site k holds phase core k-1, so bond k equals the phase train's bond k-1
@@ -1066,6 +1070,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     c->launches++;
     TRY(qtt_diag_mpo_core<double>(core_ptr<zc>(ops->chi, k - 1), ops->chi->r[k - 1], 2, ops->chi->r[k],
                                   core_ptr<zc>(ops->dCb, k), c->stream));
+    ops->dCb->diag[k] = 1;
   }
   // superfast Fourier transform (none for a dimension without bits).  Sites
   // grouped by dimension (the paper's order): the three one-dimensional
@@ -1103,6 +1108,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     }
     c->launches++;
     qtt_identity_core<double>(1, nc, core_ptr<zc>(Q, 0), c->stream);
+    Q->diag[0] = Qi->diag[0] = 1;
     for (int p = 0; p < dsp; ++p) {
       const int dm = sm.dim[p], pos = sm.pos[p];
       const int k = p + 1;
@@ -1113,6 +1119,7 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
       } else {
         c->launches++;
         qtt_identity_core<double>(gq[k], 2, core_ptr<zc>(Q, k), c->stream);
+        Q->diag[k] = Qi->diag[k] = 1;
       }
     }
     for (int k = 0; k < d; ++k) {

@@ -98,6 +98,7 @@ qtt_mpo* mpo_alloc(qtt_ctx* c, int d, const std::vector<int>& no, const std::vec
   A->no = no;
   A->ni = ni;
   A->g = g;
+  A->diag.assign(d, 0);
   A->dtype = dt;
   A->off.resize(d);
   size_t tot = 0;
@@ -1450,6 +1451,7 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
         c->launches++;
         TRY(qtt_identity_core<R>(1, xs[t]->n[k],
                                  reinterpret_cast<C*>(static_cast<char*>(own[t]->data) + own[t]->off[k]), c->stream));
+        own[t]->diag[k] = 1;
       }
       A[t] = own[t];
     }
@@ -1505,7 +1507,27 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
       TRY(dbg_finite<R>(c, U1.as<C>(), g1 * a1 * no * l0, "sketch U1", k));
       // U2[a1, g0, j, l0] = sum_{i, g1} D[g0, i, j, g1] U1[g1, a1, i, l0]   (batch a1)
       TRY(U2.alloc(c, (size_t)a1 * g0 * ni * l0 * sizeof(C)));
-      {
+      const bool dg = A[t]->diag[k] && ni == no;
+      if (dg) {
+        // diagonal core (D[g0, i, j, g1] = 0 for i != j): batch (a1, i),
+        // U2[a1, g0, i, l0] = sum_g1 D[g0, i, i, g1] U1[g1, a1, i, l0]
+        GemmDesc g;
+        g.M = g0;
+        g.N = l0;
+        g.K = g1;
+        g.batch = a1 * ni;
+        g.bA = L2(a1, 0, ni, (ni + 1) * g1);
+        g.mA = L1(g0, no * ni * g1);
+        g.kA = L1(g1, 1);
+        g.bB = L2(a1, no * l0, ni, l0);
+        g.kB = L1(g1, a1 * no * l0);
+        g.nB = L1(l0, 1);
+        g.bC = L2(a1, g0 * ni * l0, ni, l0);
+        g.mC = L1(g0, ni * l0);
+        g.nC = L1(l0, 1);
+        g.conjA = g.conjB = 0;
+        TRY(gemm<R>(c, g, Dk(t, k), U1.as<C>(), U2.as<C>()));
+      } else {
         GemmDesc g;
         g.M = g0 * ni;
         g.N = l0;
@@ -1586,7 +1608,25 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
       }
       TRY(dbg_finite<R>(c, T1.as<C>(), lk * g0 * ni * a1, "left T1", k));
       // Y[l, i, off' + g1 a1 + a1] = sum_{g0, j} D[g0, i, j, g1] T1[l, g0, j, a1]  (batch l)
-      {
+      if (A[t]->diag[k] && ni == no) {
+        // diagonal core: batch (l, i), sum over g0 only with j = i
+        GemmDesc g;
+        g.M = g1;
+        g.N = a1;
+        g.K = g0;
+        g.batch = lk * no;
+        g.bA = L2(lk, 0, no, (ni + 1) * g1);
+        g.mA = L1(g1, 1);
+        g.kA = L1(g0, no * ni * g1);
+        g.bB = L2(lk, g0 * ni * a1, no, a1);
+        g.kB = L1(g0, ni * a1);
+        g.nB = L1(a1, 1);
+        g.bC = L2(lk, no * Bn, no, Bn);
+        g.mC = L1(g1, a1);
+        g.nC = L1(a1, 1);
+        g.conjA = g.conjB = 0;
+        TRY(gemm<R>(c, g, Dk(t, k), T1.as<C>(), Y.as<C>() + boff[k + 1][t]));
+      } else {
         GemmDesc g;
         g.M = no * g1;
         g.N = a1;

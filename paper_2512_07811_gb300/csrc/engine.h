@@ -82,6 +82,8 @@ struct qtt_mpo {
   qtt_ctx* ctx = nullptr;
   int d = 0;
   std::vector<int> no, ni, g;     // output modes, input modes, bond ranks (d + 1)
+  std::vector<char> diag;         // per core: zero unless in == out index (a diagonal
+                                  // operator core; the contractions then skip the zeros)
   qtt_dtype dtype = QTT_C128;
   void* data = nullptr;
   std::vector<size_t> off;
