@@ -51,7 +51,11 @@ NLC = 6
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel class, from the one-kernel ncu captures summarised in
 # profiles/ (file named in the line); None where no current capture exists.
-TRAFFIC = {}
+TRAFFIC = {
+    "jacobi_block_kernel": {"bytes": 320.0e3, "profile": "profiles/jacobi_block_kernel_sphere32.md"},
+    "qr_panel_kernel": {"bytes": 400.128e3, "profile": "profiles/qr_panel_kernel_sphere32.md"},
+    "gemm_midx_kernel": {"bytes": 554.496e3, "profile": "profiles/gemm_midx_kernel_sphere32.md"},
+}
 
 
 def parse():
@@ -373,7 +377,9 @@ def run_ours(args, world, local_rank):
     # same number of iterations with the profiler on (kernel classes of the
     # timed iterations), whose effective tensor is compared with the FP64 one
     C64, rep64, _ = sphere_solve(Q, ctx, args.n, Q.PREC_F64, 1, args.fp64_steps, ops)
-    Cp, repp, _ = sphere_solve(Q, ctx, args.n, fast_prec, 1, args.fp64_steps, ops, profile=True)
+    # (one load case after another here, so that each launch's duration is
+    # its own and the class shares agree with a serialised ncu launch list)
+    Cp, repp, _ = sphere_solve(Q, ctx, args.n, fast_prec, 1, args.fp64_steps, ops, lc_workers=1, profile=True)
     prof = {k: ctx.profile_read(k) for k in ["gemm", "qr", "jacobi", "elem"]}
     ctx.profile(False)
     # end to end: the public call from host inputs (ellipsoid rows, C0) to the
@@ -404,11 +410,16 @@ def run_ours(args, world, local_rank):
                 green_rank=green_rank, phase_rank=phase_rank, setup_ms=setup_ms)
 
 
+SMS_USED = {"gemm": None, "qr": 1, "jacobi": 8}
+
+
 def roofline(prof, repp, peaks, mpeaks):
     """The dominant kernel class of the timed iterations by summed device time
-    (CUDA events around each launch on its own stream; the six load-case
-    streams run concurrently, so a launch's duration includes the sharing of
-    the GPU).  achieved = the class's model flops / summed duration."""
+    (CUDA events around each launch, load cases one after another so that no
+    launch shares the GPU with another solve's).  achieved = the class's
+    model flops / summed duration, against the measured FP32 FMA peak of the
+    whole GPU and of the SMs one launch occupies (one CTA per QR, one 8-CTA
+    cluster per Jacobi SVD)."""
     dom = max(["gemm", "qr", "jacobi"], key=lambda k: prof[k]["ms"])
     p = prof[dom]
     kernel = {"gemm": "gemm_midx_kernel", "qr": "qr_panel_kernel", "jacobi": "jacobi_block_kernel"}[dom]
@@ -418,8 +429,12 @@ def roofline(prof, repp, peaks, mpeaks):
             "peak_source": "measured FP32 FMA peak of this GPU (library microbenchmark qtt_measure_peak)",
             "launches": p["launches"], "kernel_ms_total": p["ms"],
             "flops_per_launch": p["flops"] / p["launches"] if p["launches"] else None,
-            "traffic": TRAFFIC.get(kernel)}
+            "traffic": TRAFFIC.get(kernel, {}).get("bytes"),
+            "traffic_source": TRAFFIC.get(kernel, {}).get("profile")}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+    if SMS_USED[dom]:
+        roof["sms_per_launch"] = SMS_USED[dom]
+        roof["frac_of_sms_used"] = roof["achieved"] / (roof["peak"] * SMS_USED[dom] / peaks["sms"])
     roof["classes"] = {k: {"ms": v["ms"], "launches": v["launches"], "model_flops": v["flops"],
                            "tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] else None}
                        for k, v in prof.items()}
