@@ -69,6 +69,9 @@ def parse():
     p.add_argument("--sweep-ranks", default="16,32,64,128,256")
     p.add_argument("--sweep-fp64-max-rank", type=int, default=64)
     p.add_argument("--no-secondary", action="store_true")
+    p.add_argument("--extras", action="store_true",
+                   help="also the f-row measurements: SVD vs polar compression, TT-cross operator setup on 2^18 x "
+                        "2^18 grids and the 65536^2 multibox, AMEn vs sketched Green step (several minutes more)")
     p.add_argument("--batch", type=int, default=32)
     p.add_argument("--prec", choices=["f32", "tc32"], default="f32",
                    help="fast path arithmetic: float CUDA cores, or tensor cores for the large contractions")
@@ -341,6 +344,118 @@ def batched_rounding(Q, torch, ctx, stream, flush, r, count, steps=2):
             "tflops": flops / (ms * 1e-3) / 1e12, "ms_per_batch": ms / steps}
 
 
+# ------------------------------------------ extras (--extras only)
+def polar_vs_svd(Q, torch, ctx, stream, flush, r=64):
+    """SVD- vs polar-based compression (the paper's comparison, chi =
+    tau_polar / tau_SVD) on the step's first rounding: the rank-128 sum of the
+    two rank-64 trains, FP32 storage, SVD rounding vs polar rounding with
+    CUDA-core products (f32) and with the products on the tensor cores
+    (tc32).  One warm-up and one timed rounding each, L2 flushed first."""
+    X = Q.TT.from_cores(ctx, I.random_tt_cores(D, 2, r, seed=1000 + r, dtype=np.complex128), Q.C64)
+    Y = Q.TT.from_cores(ctx, I.random_tt_cores(D, 2, r, seed=1001 + r, dtype=np.complex128), Q.C64)
+    z = Q.tt_add(ctx, 1.0, X, 1.0, Y)
+
+    def timed(fn):
+        fn()
+        ctx.sync()
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y, _ = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), y.ranks
+
+    svd_ms, svd_r = timed(lambda: Q.tt_round(ctx, z, EPS, prec=Q.PREC_F32))
+    out = {"workload": "rounding of the rank-128 sum (d=30), eps %g, complex64" % EPS, "svd_ms": svd_ms}
+    for name, p in [("f32", Q.PREC_F32), ("tc32", Q.PREC_TC32)]:
+        ms, r = timed(lambda: Q.tt_round_polar(ctx, z, EPS, prec=p))
+        out["polar_ms_" + name] = ms
+        out["chi_" + name] = ms / svd_ms
+        out["ranks_equal_" + name] = r == svd_r
+    return out
+
+
+def cross_setup(Q, ctx):
+    """Operator setup by TT-cross (Sec. 3) on the paper's largest plane grid
+    (2^18 x 2^18, 36 spatial sites): the Green operator train (scalar and
+    elastic) at 1e-10 and a multibox phase train; then, on a 4096 x 4096
+    multibox where both routes fit, the setup time of the homogenisation
+    with a dense image and dense Green TT-SVD against the box geometry with
+    both trains by TT-cross, and the 65536 x 65536 multibox solved on the
+    fast path (phase and Green trains by TT-cross, nothing dense)."""
+    import time
+    out = {}
+    for name, kw in [("green_scalar_2pow18_sq", dict(ncomp=3, k0=5.5)),
+                     ("green_elastic_2pow18_sq", dict(ncomp=6, lam0=3.0, mu0=2.0))]:
+        ctx.sync()
+        t0 = time.perf_counter()
+        y, info = Q.tt_cross(ctx, "green", (18, 18, 0), 1e-10, **kw)
+        ctx.sync()
+        ms = (time.perf_counter() - t0) * 1e3
+        out[name] = {"ms": ms, "evaluations": int(info.evaluations), "half_sweeps": int(info.half_sweeps),
+                     "rank_before_rounding": int(info.max_rank), "rank": max(y.ranks),
+                     "evaluations_per_s": info.evaluations / (ms * 1e-3)}
+    boxes = I.multibox_boxes_2d(1 << 18, count=8, area_fraction=0.2, seed=5)
+    ctx.sync()
+    t0 = time.perf_counter()
+    y, info = Q.tt_cross(ctx, "boxes", (18, 18, 0), 1e-10, boxes=boxes)
+    ctx.sync()
+    out["multibox_phase_2pow18_sq"] = {"ms": (time.perf_counter() - t0) * 1e3, "rank": max(y.ranks),
+                                       "evaluations": int(info.evaluations)}
+    # setup of one solve: dense image + dense Green TT-SVD vs box geometry + TT-cross
+    N = 4096
+    boxes = I.multibox_boxes_2d(N, count=8, area_fraction=0.2, seed=5)
+    ind = I.boxes_indicator(boxes, (N, N, 1))
+    kw = dict(tol=0.0, max_rank=64, eps=1e-6, prec=Q.PREC_F32, load_mask=1, max_iter=1, min_iter=1)
+    _, rd = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), **kw)
+    _, rx = Q.ms_homogenize(ctx, Q.Boxes(boxes, (N, N, 1)), "scalar", (1.0, 10.0), 5.5 * np.eye(3), op_cross=True,
+                            **kw)
+    out["ms_setup_4096_sq"] = {"dense_ms": rd.setup_ms, "cross_ms": rx.setup_ms,
+                               "green_rank_dense": rd.green_rank, "green_rank_cross": rx.green_rank,
+                               "phase_rank_dense": rd.phase_rank, "phase_rank_cross": rx.phase_rank}
+    # the paper-scale plane problem on the fast path
+    N = 1 << 16
+    geo = Q.Boxes(I.multibox_boxes_2d(N, count=8, area_fraction=0.2, seed=5), (N, N, 1))
+    kw = dict(tol=0.0, max_rank=64, eps=1e-6, prec=Q.PREC_F32, load_mask=1)
+    Q.ms_homogenize(ctx, geo, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=1, min_iter=1, **kw)
+    C, rep = Q.ms_homogenize(ctx, geo, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=5, min_iter=5, **kw)
+    f = 0.2
+    out["ms_multibox_65536_sq_fast"] = {
+        "workload": "65536 x 65536 x 1 scalar multibox (8 squares), 32 interleaved bit sites + control, "
+                    "contrast 10, max rank 64, eps 1e-6, E = e_x, 5 iterations",
+        "iters_per_s": rep.iterations[0] / (rep.iterate_ms * 1e-3) if rep.iterate_ms > 0 else None,
+        "setup_ms": rep.setup_ms, "k_eff_xx": C[0, 0], "max_rank": rep.max_rank_seen,
+        "green_rank": rep.green_rank, "phase_rank": rep.phase_rank}
+    return out
+
+
+def ms_green_amen(Q, ctx):
+    """The Green step eps^ = Gamma0 tau^ by AMEn (warm-started from the
+    previous iteration) against the MPO x TT product with a sketched
+    rounding, on the 32^3 scalar laminate and the 256^2 plane multibox, FP64
+    (eps 1e-8) and fast (eps 1e-6) paths, 5 timed iterations after one
+    warm-up solve each."""
+    out = {}
+    cases = [("laminate_32cube", I.laminate_indicator(32)),
+             ("multibox_256sq", I.multibox_indicator_2d(256, count=8, area_fraction=0.2, seed=5))]
+    for cname, ind in cases:
+        res = {}
+        for pname, prec, eps in [("fp64", Q.PREC_F64, 1e-8), ("fast", Q.PREC_F32, 1e-6)]:
+            for route in ["sketched", "amen"]:
+                kw = dict(tol=0.0, max_rank=64, eps=eps, prec=prec, load_mask=1, green_amen=route == "amen")
+                Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=1, min_iter=1, **kw)
+                C, rep = Q.ms_homogenize(ctx, ind, "scalar", (1.0, 10.0), 5.5 * np.eye(3), max_iter=5, min_iter=5,
+                                         **kw)
+                res[f"{pname}_{route}"] = {"iters_per_s": 5 / (rep.iterate_ms * 1e-3) if rep.iterate_ms > 0 else None,
+                                           "k_eff_xx": C[0, 0], "max_rank": rep.max_rank_seen}
+        out[cname] = res
+    return out
+
+
 # ------------------------------------------------------------ our arm
 def run_ours(args, world, local_rank):
     import torch
@@ -405,6 +520,10 @@ def run_ours(args, world, local_rank):
         sec("plane_multibox", ms_plane, Q, ctx, 128)
         if args.batch > 0:
             sec("batched_rounding", batched_rounding, Q, torch, ctx, stream, flush, 64, args.batch)
+        if args.extras:
+            sec("polar_vs_svd", polar_vs_svd, Q, torch, ctx, stream, flush)
+            sec("tt_cross", cross_setup, Q, ctx)
+            sec("green_amen", ms_green_amen, Q, ctx)
     return dict(C32=C32, rep32=rep32, ms=ms, steps_done=steps_done, clocks=clk, C64=C64, Cp=Cp, rep64=rep64,
                 prof=prof, repp=repp, peaks=peaks, secondary=secondary, wall_e2e=wall_e2e, repe=repe,
                 green_rank=green_rank, phase_rank=phase_rank, setup_ms=setup_ms)
