@@ -283,6 +283,44 @@ def converged_fast_vs_fp64(Q, ctx, N=16):
             "max_rank_fp64": int(r64.max_rank_seen), "max_rank_fast": int(r32.max_rank_seen)}
 
 
+def learned_ranks(Q, ctx, n, ops, fast_prec, iters=3):
+    """The rank predictor on the sphere RVE: trained (by the library's own
+    forward, backward and Adam kernels) on the rank traces of 16^3 and 32^3
+    sphere solves (elastic, load cases e_11 and e_23, eps 1e-6 and 1e-5),
+    then used on the headline's 2^n grid: iterations/s and sketch width
+    against the fixed width, C_eff deviation after the same iterations, and
+    how its roundings were judged (FP64 a-posteriori errors, fallbacks)."""
+    from paper_2512_07811_gb300 import predictor as PR
+    train = []
+    for m in (4, 5):
+        geo, moduli, C0 = sphere_geometry(Q, m)
+        for e in (1e-6, 1e-5):
+            train.append(dict(indicator=geo, kind="elastic", moduli=moduli, C0=C0, eps=e, tol=0.0, max_rank=MAX_RANK,
+                              max_iter=6, min_iter=6, prec=fast_prec, load_mask=0b1001, interleaved=False))
+    t0 = time.perf_counter()
+    X, t = PR.collect_traces(ctx, train)
+    net = Q.MLP(ctx, Q.MLP_FEATURES, seed=7)
+    hist = PR.train(net, X, t, epochs=100, batch=512, lr=3e-3, alpha=4.0)
+    train_s = time.perf_counter() - t0
+    geo, moduli, C0 = sphere_geometry(Q, n)
+    out = {"workload": "%d^3 elastic sphere, 6 load cases, 1 + %d iterations" % (1 << n, iters),
+           "training_rows": int(X.shape[0]), "training_s": train_s, "loss_first_last": [hist[0], hist[-1]]}
+    res = {}
+    for name, pred in [("fixed", None), ("learned", net)]:
+        C, rep = Q.ms_homogenize(ctx, geo, "elastic", moduli, C0, tol=0.0, max_rank=MAX_RANK, eps=EPS,
+                                 prec=fast_prec, max_iter=1 + iters, min_iter=1 + iters, warm_iter=1,
+                                 lc_workers=NLC, load_mask=(1 << NLC) - 1, interleaved=False, ops=ops,
+                                 predictor=pred)
+        res[name] = C
+        out[name] = {"iters_per_s": (rep.timed_iter / NLC) / (rep.timed_ms * 1e-3),
+                     "sketch_width_sum": int(rep.sketch_width_sum), "fallbacks": int(rep.fallbacks),
+                     "judged": int(rep.post_checks), "svd_fallbacks": int(rep.svd_fallbacks),
+                     "post_err_max": rep.post_err_max}
+    out["rel_dev_learned_vs_fixed"] = rel_frob(res["learned"], res["fixed"])
+    out["speedup"] = out["learned"]["iters_per_s"] / out["fixed"]["iters_per_s"]
+    return out
+
+
 def ms_laminate(Q, ctx):
     """Config 1: 32^3 scalar laminate (15 interleaved bit sites + control),
     load case e_x, 5 timed iterations after one warm-up solve; FP64 at eps
@@ -500,11 +538,19 @@ def run_ours(args, world, local_rank):
     # end to end: the public call from host inputs (ellipsoid rows, C0) to the
     # host effective tensor, operator setup included
     _, repe, wall_e2e = sphere_solve(Q, ctx, args.n, fast_prec, args.warmup, args.steps)
+    learned = None
+    if not args.no_secondary:
+        try:
+            learned = learned_ranks(Q, ctx, args.n, ops, fast_prec)
+        except Exception as exc:  # noqa: BLE001
+            learned = {"error": "%s: %s" % (type(exc).__name__, exc)}
     green_rank, phase_rank = ops.ranks
     setup_ms = ops.setup_ms
     ops.close()
 
     secondary = {}
+    if learned is not None:
+        secondary["learned_ranks"] = learned
     if not args.no_secondary:
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 

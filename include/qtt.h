@@ -213,6 +213,13 @@ QTT_API int tt_round_sketched(qtt_ctx* ctx, int nterms, const qtt_complex* coef,
                       const qtt_tt* const* xs, const qtt_tt* sketch, double eps, int max_rank, qtt_prec prec,
                       qtt_round_info* info, qtt_tt** y);
 
+/* <y, s> = sum_i conj(y(i)) s(i) for the structured sum s = sum_t coef_t A_t x_t
+ * (ops[t] NULL: the identity) without forming s (Sec. 2.1: operator-train
+ * application; the transfer products run core by core from the right).
+ * All trains and operators of one dtype; FP64 result; synchronises.  Used
+ * for the FP64 a-posteriori error of roundings with learned sketch widths. */
+QTT_API int tt_dot_structured(qtt_ctx* ctx, int nterms, const qtt_complex* coef, const qtt_mpo* const* ops,
+                              const qtt_tt* const* xs, const qtt_tt* y, double out[2]);
 /* out = <x, y> = sum_i conj(x(i)) y(i) through the transfer-matrix chain
  * W_k = sum_i A_k(i)^H W_{k-1} B_k(i); out[0] = real, out[1] = imaginary
  * part.  Accumulates in the storage precision; returns a double. */
@@ -437,8 +444,13 @@ typedef struct {
   int32_t min_iter;
   uint64_t seed;        /* counter-based generator seed for the sketches                 */
   const qtt_mlp* predictor; /* NULL: every sketch has width max_rank + oversample; else the
-                            per-bond widths are 1.25 * predicted rank + oversample, with a
-                            fallback to the full width when a bond's rank saturates its sketch */
+                            per-bond widths are 1.25 * predicted rank + oversample and the
+                            result is judged: the SFFT and update roundings by their FP64
+                            a-posteriori error ||s - y|| (exact, from FP64 inner products;
+                            above 2 eps ||s|| they are redone at the full width, then by the
+                            deterministic SVD rounding of the explicit sum when its rank is
+                            at most 4096), the contrast and Green roundings by saturation
+                            (a bond whose rank reaches its narrowed width is widened)      */
   float* trace;          /* NULL or host buffer receiving (features, target) rows of every
                             sketched rounding: QTT_MLP_FEATURES + 1 floats per bond          */
   int64_t trace_cap;     /* capacity of `trace` in rows                                     */
@@ -473,6 +485,11 @@ typedef struct {
                               until every load case has finished                          */
   int32_t timed_iter;      /* iterations (summed over load cases) inside timed_ms          */
   int64_t timed_launches;  /* kernel launches of those iterations                          */
+  int32_t post_checks;     /* learned widths: roundings judged by their FP64 a-posteriori
+                              error (the SFFT steps and the update)                        */
+  int32_t svd_fallbacks;   /* judged roundings redone by deterministic SVD rounding of the
+                              explicit sum (the full-width sketch still above the bound)   */
+  double post_err_max;     /* largest a-posteriori error / ||s|| of the judged roundings    */
 } ms_report;
 
 /* Moulinec-Suquet homogenisation in QTT form (Sec. 3.2, Algorithm 2):

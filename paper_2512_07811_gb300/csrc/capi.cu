@@ -550,6 +550,18 @@ int tt_round_sketched(qtt_ctx* c, int nterms, const qtt_complex* coef, const qtt
              : round_sketched<float>(c, nterms, coef, ops, xs, sketch, eps, max_rank, info, y);
 }
 
+int tt_dot_structured(qtt_ctx* c, int nterms, const qtt_complex* coef, const qtt_mpo* const* ops,
+                      const qtt_tt* const* xs, const qtt_tt* y, double out[2]) {
+  if (!c || nterms < 1 || !coef || !xs || !valid_tt(y) || !out) return QTT_ERR_ARG;
+  for (int t = 0; t < nterms; ++t) {
+    if (!valid_tt(xs[t]) || xs[t]->dtype != y->dtype || xs[t]->d != y->d) return QTT_ERR_ARG;
+    if (ops && ops[t] && (ops[t]->dtype != y->dtype || ops[t]->d != y->d)) return QTT_ERR_ARG;
+    if (!(ops && ops[t]) && xs[t]->n != y->n) return QTT_ERR_ARG;
+  }
+  return y->dtype == QTT_C128 ? structured_dot<double>(c, nterms, coef, ops, xs, y, out)
+                              : structured_dot<float>(c, nterms, coef, ops, xs, y, out);
+}
+
 int tt_dot(qtt_ctx* c, const qtt_tt* x, const qtt_tt* y, double out[2]) {
   if (!c || !valid_tt(x) || !valid_tt(y) || !out || !same_modes(x, y) || x->dtype != y->dtype) return QTT_ERR_ARG;
   return x->dtype == QTT_C128 ? dot_dev<double>(c, x, y, out) : dot_dev<float>(c, x, y, out);
@@ -1261,8 +1273,54 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
       f[9] = (float)(side[k] / 20.0);
     }
   };
+  // FP64 a-posteriori error ||s - y|| of a rounding y of the structured sum
+  // s = sum_t cf_t A_t X_t where every A_t is unitary or the identity (the
+  // SFFT steps and the update E - S^{-1} eps^): ||s||^2 from the terms'
+  // norms and their cross inner products, <y, s> by the right partial
+  // contractions with y in place of the sketch, all on cores widened exactly
+  // to complex128 and with the complex128 operator trains A64.
+  auto post_error = [&](int T, const qtt_complex* cf, const qtt_mpo* const* A64, const qtt_tt* const* X,
+                        const qtt_tt* y, double* err, double* snorm) -> int {
+    std::vector<qtt_tt*> wx(T, nullptr);
+    qtt_tt* wy = nullptr;
+    struct FreeAll {
+      std::vector<qtt_tt*>& v;
+      qtt_tt*& y;
+      ~FreeAll() {
+        for (auto* p : v) tt_free(p);
+        tt_free(y);
+      }
+    } fa{wx, wy};
+    for (int t = 0; t < T; ++t) TRY(convert_tt(c, X[t], QTT_C128, &wx[t]));
+    TRY(convert_tt(c, y, QTT_C128, &wy));
+    double s2 = 0;
+    for (int t = 0; t < T; ++t) {
+      double n2[2];
+      TRY(dot_dev<double>(c, wx[t], wx[t], n2));
+      s2 += (cf[t].re * cf[t].re + cf[t].im * cf[t].im) * n2[0];
+      for (int u = t + 1; u < T; ++u) {
+        // <A_t x_t, A_u x_u> with A_t the identity (the update's E term)
+        if (A64[t]) return QTT_ERR_UNSUPPORTED;
+        const qtt_complex one1 = {1.0, 0.0};
+        const qtt_mpo* Au[1] = {A64[u]};
+        const qtt_tt* Xu[1] = {wx[u]};
+        double cr[2];
+        TRY(structured_dot<double>(c, 1, &one1, Au, Xu, wx[t], cr));
+        // 2 Re(conj(c_t) c_u <x_t, A_u x_u>)
+        const double pr = cf[t].re * cf[u].re + cf[t].im * cf[u].im, pi = cf[t].re * cf[u].im - cf[t].im * cf[u].re;
+        s2 += 2.0 * (pr * cr[0] - pi * cr[1]);
+      }
+    }
+    double yy[2], ys[2];
+    TRY(dot_dev<double>(c, wy, wy, yy));
+    std::vector<const qtt_tt*> wxc(wx.begin(), wx.end());
+    TRY(structured_dot<double>(c, T, cf, A64, wxc.data(), wy, ys));
+    *snorm = sqrt(std::max(0.0, s2));
+    *err = sqrt(std::max(0.0, yy[0] + s2 - 2.0 * ys[0]));
+    return QTT_OK;
+  };
   auto sk_round = [&](int T, const qtt_complex* cf, const qtt_mpo* const* A, const qtt_tt* const* X, int opid,
-                      qtt_tt** out) -> int {
+                      qtt_tt** out, const qtt_mpo* const* A64 = nullptr) -> int {
     std::vector<float> F;
     features(T, A, X, opid, F);
     std::vector<int> full(d + 1, ell), w(d + 1, ell);
@@ -1277,7 +1335,41 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     qtt_round_info info;
     int s = QTT_OK;
     std::vector<int> width = w;
-    for (int attempt = 0; attempt < 2; ++attempt) {
+    // With learned widths the result is judged: by its FP64 a-posteriori
+    // error where that is affordable (A64 given), else by sketch saturation.
+    // A failed judgement widens the sketch to the full width; a judged step
+    // that still exceeds the bound falls back to the deterministic SVD
+    // rounding of the explicit sum.
+    const double bound = 2.0 * o.eps;   // sketch error allowed beside the truncation's eps
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      if (attempt == 2) {
+        // deterministic SVD rounding of the explicit sum
+        qtt_tt* acc = nullptr;
+        for (int t = 0; t < T && !s; ++t) {
+          qtt_tt* term = nullptr;
+          if (A[t]) s = mpo_apply_dev<R>(c, A[t], X[t], &term);
+          else s = convert_tt(c, X[t], dt, &term);
+          if (s) break;
+          const C ct((R)cf[t].re, (R)cf[t].im);
+          if (!acc) {
+            // acc = c_t term: the coefficient scales the first core
+            c->launches++;
+            s = qtt_scale<R>(core_ptr<C>(term, 0), (int64_t)term->r[0] * term->n[0] * term->r[1], ct, c->stream);
+            acc = term;
+          } else {
+            qtt_tt* z = nullptr;
+            s = add_dev<R>(c, C(1, 0), acc, ct, term, &z);
+            tt_free(term);
+            tt_free(acc);
+            acc = z;
+          }
+        }
+        if (!s) s = round_det<R>(c, acc, o.eps, max_rank, nullptr, &info, out);
+        if (acc) tt_free(acc);
+        if (s) return s;
+        if (rep) rep->svd_fallbacks++;
+        break;
+      }
       qtt_tt* S = nullptr;
       TRY(make_sketch(c, modes, width, dt, o.seed, call++, &S));
       if (rep)
@@ -1286,20 +1378,44 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
       std::vector<int> sr = S->r;
       tt_free(S);
       if (s) return s;
-      if (!pred || attempt == 1) break;
-      // a bond whose rank reaches its narrowed sketch width may have been cut
-      // by the sketch rather than by the tolerance: widen those bonds to the
-      // full width (mode-product caps apply to both) and redo the rounding
-      bool saturated = false;
-      for (int k = 1; k < d; ++k) {
-        const int cap = (int)std::min<double>(full[k], exp2(side[k]));
-        if (sr[k] < cap && (*out)->r[k] >= sr[k]) {
-          saturated = true;
-          width[k] = full[k];
+      if (!pred) break;
+      bool redo = false;
+      if (A64) {
+        double err = 0, sn = 0;
+        TRY(post_error(T, cf, A64, X, *out, &err, &sn));
+        const double rel = sn > 0 ? err / sn : 0.0;
+        if (rep) {
+          rep->post_checks++;
+          rep->post_err_max = std::max(rep->post_err_max, rel);
+        }
+        redo = rel > bound && !info.capped;
+        if (redo)
+          for (int k = 1; k < d; ++k) width[k] = full[k];
+      } else if (attempt == 0) {
+        // a bond whose rank reaches its narrowed sketch width may have been
+        // cut by the sketch rather than by the tolerance: widen those bonds
+        // to the full width (mode-product caps apply to both)
+        for (int k = 1; k < d; ++k) {
+          const int cap = (int)std::min<double>(full[k], exp2(side[k]));
+          if (sr[k] < cap && (*out)->r[k] >= sr[k]) {
+            redo = true;
+            width[k] = full[k];
+          }
         }
       }
-      if (!saturated) break;
-      if (rep) rep->fallbacks++;
+      if (!redo) break;
+      if (attempt == 1) {
+        // the full width still misses the bound: the explicit sum, if its
+        // rank stays within 4096, else keep the full-width result
+        int64_t rk = 0;
+        for (int t = 0; t < T; ++t) {
+          int64_t m = 0;
+          for (int k = 1; k < d; ++k) m = std::max<int64_t>(m, (int64_t)(A[t] ? A[t]->g[k] : 1) * X[t]->r[k]);
+          rk += m;
+        }
+        if (!A64 || rk > 4096) break;
+      }
+      if (rep && attempt == 0) rep->fallbacks++;
       tt_free(*out);
       *out = nullptr;
     }
@@ -1371,8 +1487,9 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         stage = fwd[dim];
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {Q[dim]};
+        const qtt_mpo* A64[1] = {O.q[dim]};
         const qtt_tt* X[1] = {h};
-        int s = sk_round(1, &one, A, X, 1 + dim, &hn);
+        int s = sk_round(1, &one, A, X, 1 + dim, &hn, A64);
         tt_free(h);
         if (s) return s;
         h = hn;
@@ -1414,8 +1531,9 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         stage = inv[dim];
         qtt_tt* hn = nullptr;
         const qtt_mpo* A[1] = {Qi[dim]};
+        const qtt_mpo* A64[1] = {O.qi[dim]};
         const qtt_tt* X[1] = {h};
-        int s = sk_round(1, &one, A, X, 7 - dim, &hn);
+        int s = sk_round(1, &one, A, X, 7 - dim, &hn, A64);
         tt_free(h);
         if (s) return s;
         h = hn;
@@ -1425,8 +1543,9 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
       {
         const qtt_complex cf[2] = {one, {-1.0, 0.0}};
         const qtt_mpo* A[2] = {nullptr, Qi[last]};
+        const qtt_mpo* A64[2] = {nullptr, O.qi[last]};
         const qtt_tt* X[2] = {E, h};
-        int s = sk_round(2, cf, A, X, 8, &xn);
+        int s = sk_round(2, cf, A, X, 8, &xn, A64);
         tt_free(h);
         if (s) return s;
       }
@@ -1863,6 +1982,9 @@ extern "C" int ms_homogenize_ops(qtt_ctx* c, const ms_ops* m, double tol, int ma
           rep->fp64_residuals += rj.fp64_residuals;
           rep->timed_iter += rj.timed_iter;
           rep->timed_launches += rj.timed_launches;
+          rep->post_checks += rj.post_checks;
+          rep->svd_fallbacks += rj.svd_fallbacks;
+          rep->post_err_max = std::max(rep->post_err_max, rj.post_err_max);
         }
       }
       std::lock_guard<std::mutex> lock(mu);
@@ -1981,6 +2103,9 @@ extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const
         R.kernel_launches += rj.kernel_launches;
         R.sketch_width_sum += rj.sketch_width_sum;
         R.fallbacks += rj.fallbacks;
+        R.post_checks += rj.post_checks;
+        R.svd_fallbacks += rj.svd_fallbacks;
+        R.post_err_max = std::max(R.post_err_max, rj.post_err_max);
       }
     }
     {

@@ -1423,9 +1423,13 @@ template int norm_dev<float>(qtt_ctx*, const qtt_tt*, double*);
 
 // ------------------------------------------------------- sketched rounding
 // Randomize-then-orthogonalize for s = sum_t coef_t A_t x_t (A_t may be NULL).
+// With dot_out set, only the right partial contractions are run, down to the
+// first core, and the bilinear form sum_i S(i) s(i) is returned in dot_out
+// (no projection, no rounding).
 template <class R>
-int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* const* ops, const qtt_tt* const* xs,
-                   const qtt_tt* S, double eps, int max_rank, qtt_round_info* info, qtt_tt** yout) {
+static int sketch_core(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* const* ops,
+                       const qtt_tt* const* xs, const qtt_tt* S, double eps, int max_rank, qtt_round_info* info,
+                       qtt_tt** yout, double* dot_out) {
   const int d = S->d;
   typedef cplx<R> C;
   // identity operators for terms without one
@@ -1478,7 +1482,7 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
     std::vector<C> ones(T, C(1, 0));
     cudaMemcpyAsync(W[d].p, ones.data(), T * sizeof(C), cudaMemcpyHostToDevice, c->stream);
   }
-  for (int k = d - 1; k >= 1; --k) {
+  for (int k = d - 1; k >= (dot_out ? 0 : 1); --k) {
     const int64_t l0 = S->r[k], l1 = S->r[k + 1], no = S->n[k];
     TRY(W[k].alloc(c, (size_t)Bt(k) * l0 * sizeof(C)));
     for (int t = 0; t < T; ++t) {
@@ -1567,6 +1571,19 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
       }
     }
     TRY(dbg_finite<R>(c, W[k].as<C>(), Bt(k) * l0, "sketch W", k));
+  }
+  if (dot_out) {
+    // W_0 holds one entry per term (bond 0 has rank 1 for every term)
+    std::vector<C> w0(T);
+    TRY(sync_read(c, w0.data(), W[0].p, (size_t)T * sizeof(C)));
+    double re = 0, im = 0;
+    for (int t = 0; t < T; ++t) {
+      re += coef[t].re * (double)w0[t].re - coef[t].im * (double)w0[t].im;
+      im += coef[t].re * (double)w0[t].im + coef[t].im * (double)w0[t].re;
+    }
+    dot_out[0] = re;
+    dot_out[1] = im;
+    return QTT_OK;
   }
   // ---- left-to-right projection
   std::vector<DBuf> outc(d);
@@ -1686,6 +1703,40 @@ int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* co
   return rs;
 }
 
+template <class R>
+int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* const* ops, const qtt_tt* const* xs,
+                   const qtt_tt* S, double eps, int max_rank, qtt_round_info* info, qtt_tt** yout) {
+  return sketch_core<R>(c, T, coef, ops, xs, S, eps, max_rank, info, yout, nullptr);
+}
+
+// <y, s> = sum_i conj(y(i)) s(i) for the structured sum s = sum_t coef_t A_t x_t,
+// by the right partial contractions of the sketched rounding with the
+// conjugated train of y in the place of the sketch.
+template <class R>
+int structured_dot(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* const* ops, const qtt_tt* const* xs,
+                   const qtt_tt* y, double out[2]) {
+  int st;
+  qtt_tt* yc = tt_alloc(c, y->d, y->n, y->r, y->dtype, &st);
+  if (!yc) return st;
+  for (int k = 0; k < y->d; ++k) {
+    const int64_t rows = (int64_t)y->r[k] * y->n[k], cols = y->r[k + 1];
+    c->launches++;
+    st = qtt_copy_strided<R>(core_ptr<cplx<R>>(y, k), L1(rows, cols), L1(cols, 1), rows, cols, 1,
+                             core_ptr<cplx<R>>(yc, k), cols, c->stream);
+    if (st) {
+      tt_free(yc);
+      return st;
+    }
+  }
+  st = sketch_core<R>(c, T, coef, ops, xs, yc, 0.0, 0, nullptr, nullptr, out);
+  tt_free(yc);
+  return st;
+}
+
+template int structured_dot<double>(qtt_ctx*, int, const qtt_complex*, const qtt_mpo* const*, const qtt_tt* const*,
+                                    const qtt_tt*, double*);
+template int structured_dot<float>(qtt_ctx*, int, const qtt_complex*, const qtt_mpo* const*, const qtt_tt* const*,
+                                   const qtt_tt*, double*);
 template int round_sketched<double>(qtt_ctx*, int, const qtt_complex*, const qtt_mpo* const*, const qtt_tt* const*,
                                     const qtt_tt*, double, int, qtt_round_info*, qtt_tt**);
 template int round_sketched<float>(qtt_ctx*, int, const qtt_complex*, const qtt_mpo* const*, const qtt_tt* const*,

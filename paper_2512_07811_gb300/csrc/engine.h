@@ -109,6 +109,10 @@ int round_det_batch(qtt_ctx* c, int B, const qtt_tt* const* xs, double eps, int 
 template <class R>
 int round_sketched(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* const* ops, const qtt_tt* const* xs,
                    const qtt_tt* S, double eps, int max_rank, qtt_round_info* info, qtt_tt** yout);
+// <y, s> for s = sum_t coef_t A_t x_t (A_t may be NULL), without forming s
+template <class R>
+int structured_dot(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo* const* ops, const qtt_tt* const* xs,
+                   const qtt_tt* y, double out[2]);
 template <class R>
 int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* dense, double eps, int max_rank,
                qtt_dtype dt, qtt_tt** out);

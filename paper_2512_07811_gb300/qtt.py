@@ -131,7 +131,8 @@ class MSReport(C.Structure):
                 ("kernel_launches", C.c_int64), ("trace_len", C.c_int64), ("sketch_width_sum", C.c_int64),
                 ("fallbacks", C.c_int32), ("green_rank", C.c_int32), ("phase_rank", C.c_int32),
                 ("fp64_residuals", C.c_int32), ("timed_ms", C.c_double), ("timed_iter", C.c_int32),
-                ("timed_launches", C.c_int64)]
+                ("timed_launches", C.c_int64), ("post_checks", C.c_int32), ("svd_fallbacks", C.c_int32),
+                ("post_err_max", C.c_double)]
 
 
 MLP_FEATURES = 10
@@ -184,6 +185,8 @@ _sig("tt_round_batch", C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_double, C.c_int
 _sig("tt_round_sketched", C.c_int, [_P, C.c_int, C.POINTER(Complex), C.POINTER(_P), C.POINTER(_P), _P,
                                     C.c_double, C.c_int, C.c_int, C.POINTER(RoundInfo), C.POINTER(_P)])
 _sig("tt_dot", C.c_int, [_P, _P, _P, C.POINTER(C.c_double)])
+_sig("tt_dot_structured", C.c_int, [_P, C.c_int, C.POINTER(Complex), C.POINTER(_P), C.POINTER(_P), _P,
+                                    C.POINTER(C.c_double)])
 _sig("tt_norm", C.c_int, [_P, _P, C.POINTER(C.c_double)])
 _sig("tt_from_dense", C.c_int, [_P, C.c_int, _I32P, _P, C.c_double, C.c_int, C.POINTER(_P)])
 _sig("qtt_qft_mpo", C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.POINTER(_P)])
@@ -221,7 +224,7 @@ EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_s
             "qtt_tt_create", "qtt_tt_destroy", "qtt_tt_ncores", "qtt_tt_ranks", "qtt_tt_modes", "qtt_tt_dtype",
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
-            "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_polar", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_norm",
+            "tt_add", "tt_hadamard", "tt_mpo_apply", "tt_round", "tt_round_polar", "tt_round_batch", "tt_round_sketched", "tt_dot", "tt_dot_structured", "tt_norm",
             "tt_from_dense", "tt_cross", "tt_amen_mv", "tt_contract_voxels", "qtt_site_order", "qtt_qft_mpo", "qtt_mpo_diag", "qtt_mpo_convert", "ms_homogenize",
             "ms_homogenize_batch", "ms_setup", "ms_homogenize_ops", "ms_ops_destroy", "ms_ops_ranks",
             "qtt_cgemm", "qtt_cgemm_noalloc",
@@ -575,6 +578,17 @@ def tt_round_sketched(ctx: Context, terms, sketch: TT, eps: float, max_rank: int
 def tt_dot(ctx: Context, x: TT, y: TT) -> complex:
     out = (C.c_double * 2)()
     _check(_lib.tt_dot(ctx.h, x.h, y.h, out), "tt_dot")
+    return complex(out[0], out[1])
+
+
+def tt_dot_structured(ctx: Context, terms, y: TT) -> complex:
+    """<y, sum_t c_t A_t x_t> for terms (c_t, MPO or None, TT), without forming the sum."""
+    T = len(terms)
+    coefs = (Complex * T)(*[_cx(c) for c, _, _ in terms])
+    ops = (_P * T)(*[(A.h if A is not None else None) for _, A, _ in terms])
+    xs = (_P * T)(*[x.h for _, _, x in terms])
+    out = (C.c_double * 2)()
+    _check(_lib.tt_dot_structured(ctx.h, T, coefs, ops, xs, y.h, out), "tt_dot_structured")
     return complex(out[0], out[1])
 
 

@@ -112,3 +112,26 @@ def test_predictor_gain_over_fixed_width(Q, ctx):
     assert rep_pred.sketch_width_sum < 0.4 * rep_full.sketch_width_sum
     assert abs(C_pred[0, 0] - 20.0 / 11.0) < 1e-5 * 20.0 / 11.0
     assert abs(C_full[0, 0] - 20.0 / 11.0) < 1e-5 * 20.0 / 11.0
+
+
+def test_underpredicted_widths_fall_back(Q, ctx):
+    """A predictor that always answers rank 1 (all parameters zero: sketch
+    width 1.25 + oversample) under-sizes every sketch of a 16^3 elastic
+    sphere solve: the SFFT and update roundings are judged by their FP64
+    a-posteriori error and redone, the others widened on saturation, and the
+    effective tensor equals the solve without a predictor to 1e-5."""
+    lam1, mu1 = I.lame_from_young(1.0, 0.3)
+    lam2, mu2 = I.lame_from_young(10.0, 0.3)
+    C0 = MS.iso_voigt(0.5 * (lam1 + lam2), 0.5 * (mu1 + mu2))
+    geo = Q.Ellipsoids(I.sphere_rows(0.2), (16, 16, 16))
+    net = Q.MLP(ctx, Q.MLP_FEATURES, seed=1)
+    net.set_params(np.zeros(net.param_count, dtype=np.float32))
+    kw = dict(tol=5e-5, max_rank=128, eps=1e-6, prec=Q.PREC_F32, load_mask=1, max_iter=80, interleaved=False)
+    C_ref, r_ref = Q.ms_homogenize(ctx, geo, "elastic", (lam1, mu1, lam2, mu2), C0, **kw)
+    C_pred, r_pred = Q.ms_homogenize(ctx, geo, "elastic", (lam1, mu1, lam2, mu2), C0, predictor=net, **kw)
+    print("\nfallbacks %d, judged %d, SVD fallbacks %d, max a-posteriori error %.2e"
+          % (r_pred.fallbacks, r_pred.post_checks, r_pred.svd_fallbacks, r_pred.post_err_max))
+    assert r_pred.fallbacks > 0 and r_pred.post_checks > 0
+    assert r_pred.post_err_max > 1e-3          # the narrowed sketches were caught
+    col_ref, col = C_ref[:, 0], C_pred[:, 0]
+    assert np.linalg.norm(col - col_ref) / np.linalg.norm(col_ref) < 1e-5

@@ -336,3 +336,21 @@ def test_mpo_diag_is_hadamard(Q, ctx):
     gx, gy = Q.TT.from_cores(ctx, x), Q.TT.from_cores(ctx, y)
     z = Q.tt_mpo_apply(ctx, Q.qtt_mpo_diag(ctx, gx), gy)
     assert rel_diff(z.cores(), T.tt_hadamard(x, y)) < 1e-13
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_dot_structured_matches_oracle(Q, ctx, fp32):
+    """<y, 0.7 A x1 + (-0.3 + 0.2i) x2> without forming the sum equals the
+    dense inner product of the oracle's explicit sum."""
+    d = 8
+    x1 = cplx_tt([2] * d, I.capped_ranks(d, 2, 5), 41)
+    x2 = cplx_tt([2] * d, I.capped_ranks(d, 2, 3), 42)
+    y = cplx_tt([2] * d, I.capped_ranks(d, 2, 4), 43)
+    A = I.random_mpo_cores(d, 2, 3, seed=44)
+    c1, c2 = 0.7, -0.3 + 0.2j
+    s = c1 * T.tt_full(T.tt_mpo_apply(A, x1)) + c2 * T.tt_full(x2)
+    ref = np.vdot(T.tt_full(y), s)
+    dt = Q.C64 if fp32 else Q.C128
+    got = Q.tt_dot_structured(ctx, [(c1, Q.MPO.from_cores(ctx, A, dt), Q.TT.from_cores(ctx, x1, dt)),
+                                    (c2, None, Q.TT.from_cores(ctx, x2, dt))], Q.TT.from_cores(ctx, y, dt))
+    assert abs(got - ref) <= (2e-5 if fp32 else 1e-12) * np.linalg.norm(s) * np.linalg.norm(T.tt_full(y))
