@@ -447,10 +447,11 @@ typedef struct {
                             per-bond widths are 1.25 * predicted rank + oversample and the
                             result is judged: the SFFT and update roundings by their FP64
                             a-posteriori error ||s - y|| (exact, from FP64 inner products;
-                            above 2 eps ||s|| they are redone at the full width, then by the
-                            deterministic SVD rounding of the explicit sum when its rank is
-                            at most 4096), the contrast and Green roundings by saturation
-                            (a bond whose rank reaches its narrowed width is widened)      */
+                            above (2 eps + 1e-5 on the float path) ||s|| they are redone at
+                            the full width, then by the deterministic SVD rounding of the
+                            explicit sum when its rank is at most 4096), the contrast and
+                            Green roundings by saturation (a bond whose rank comes within the
+                            oversampling of its narrowed width is widened)                 */
   float* trace;          /* NULL or host buffer receiving (features, target) rows of every
                             sketched rounding: QTT_MLP_FEATURES + 1 floats per bond          */
   int64_t trace_cap;     /* capacity of `trace` in rows                                     */

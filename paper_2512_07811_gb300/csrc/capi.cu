@@ -1340,7 +1340,10 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
     // A failed judgement widens the sketch to the full width; a judged step
     // that still exceeds the bound falls back to the deterministic SVD
     // rounding of the explicit sum.
-    const double bound = 2.0 * o.eps;   // sketch error allowed beside the truncation's eps
+    // error allowed: the truncation's eps, as much again for the sketch, and
+    // on the float path the single-precision arithmetic of the rounding
+    // itself (about 1e-6 of ||s|| measured against the FP64 error)
+    const double bound = 2.0 * o.eps + (sizeof(R) == 4 ? 1e-5 : 0.0);
     for (int attempt = 0; attempt < 3; ++attempt) {
       if (attempt == 2) {
         // deterministic SVD rounding of the explicit sum
@@ -1392,12 +1395,13 @@ int ms_solve(qtt_ctx* c, const qtt_rve* rve, const double* C1h, const double* C2
         if (redo)
           for (int k = 1; k < d; ++k) width[k] = full[k];
       } else if (attempt == 0) {
-        // a bond whose rank reaches its narrowed sketch width may have been
-        // cut by the sketch rather than by the tolerance: widen those bonds
+        // a bond whose rank comes within the oversampling of its narrowed
+        // sketch width may have been cut by the sketch rather than by the
+        // tolerance (a randomized range needs that margin): widen those bonds
         // to the full width (mode-product caps apply to both)
         for (int k = 1; k < d; ++k) {
           const int cap = (int)std::min<double>(full[k], exp2(side[k]));
-          if (sr[k] < cap && (*out)->r[k] >= sr[k]) {
+          if (sr[k] < cap && (*out)->r[k] + std::max(1, (int)o.oversample) > sr[k]) {
             redo = true;
             width[k] = full[k];
           }
