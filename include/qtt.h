@@ -533,10 +533,11 @@ QTT_API int ms_homogenize_ops(qtt_ctx* ctx, const ms_ops* ops, double tol, int m
 QTT_API void ms_ops_destroy(ms_ops* ops);
 QTT_API int ms_ops_ranks(const ms_ops* ops, int32_t* green_rank, int32_t* phase_rank);
 
-QTT_API /* Many RVEs at once: the (RVE, load case) pairs of rves[0..n-1] (load cases
- * from opts->load_mask) are solved by `workers` host threads, each with its
- * own context and stream, largest RVE first, so that independent rounding
- * chains run concurrently on different SMs.  C0s holds n reference tensors
+QTT_API /* Many RVEs at once: the operator trains of every RVE are built once
+ * (ms_setup, RVEs spread over the workers), then the (RVE, load case) pairs
+ * of rves[0..n-1] (load cases from opts->load_mask) are solved by `workers`
+ * host threads, each with its own context and stream, largest RVE first, so
+ * that independent rounding chains run concurrently on different SMs.  C0s holds n reference tensors
  * at a stride of 36 doubles (3x3 or 6x6 row-major at the start of each
  * slot); C_effs receives the effective tensors back to back (ncomp^2 each);
  * reports (nullable) one report per RVE.  Every pair gives the same result

@@ -2041,12 +2041,14 @@ extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, d
   return s;
 }
 
-// Many independent solves at once: the (RVE, load case) pairs form a work
-// queue, largest RVE first; `workers` host threads each own a context on a
-// stream of their own, so that the latency-bound rounding chains of
-// different solves run concurrently on different SMs.  Results are the same
-// as solving each pair with ms_homogenize (the sketches depend only on the
-// seed and the call order within one solve).
+// Many independent solves at once.  Phase 1: the operator trains of every
+// RVE, built once each (ms_setup), RVEs spread over the workers.  Phase 2:
+// the (RVE, load case) pairs form a work queue, largest RVE first, solved by
+// ms_homogenize_ops.  `workers` host threads each own a context on a stream
+// of their own, so that the latency-bound rounding chains of different
+// solves run concurrently on different SMs.  Results are the same as solving
+// each pair with ms_homogenize (the sketches depend only on the seed and the
+// call order within one solve).
 extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const double* C0s, double tol, int max_rank,
                                    const ms_opts* o, int workers, double* C_effs, ms_report* reports) {
   if (!c || n < 0 || (n > 0 && (!rves || !C0s || !C_effs)) || !o || workers < 1) return QTT_ERR_ARG;
@@ -2067,18 +2069,38 @@ extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const
   for (int64_t i = 0; i < off[n]; ++i) C_effs[i] = 0.0;
   if (reports)
     for (int i = 0; i < n; ++i) memset(&reports[i], 0, sizeof(ms_report));
+  const int nw = std::max(1, std::min<int>(workers, (int)std::max<size_t>(1, std::max<size_t>(jobs.size(), n))));
+  std::vector<qtt_ctx*> wcs(nw, nullptr);
+  for (int w = 0; w < nw; ++w) {
+    int st = qtt_ctx_create(c->device, nullptr, &wcs[w]);
+    if (st) {
+      for (auto* x : wcs) qtt_ctx_destroy(x);
+      return st;
+    }
+  }
+  std::vector<ms_ops*> ops(n, nullptr);
   std::atomic<size_t> next(0);
   std::atomic<int> status(QTT_OK);
   std::mutex mu;
-  auto work = [&]() {
-    qtt_ctx* wc = nullptr;
-    int st = qtt_ctx_create(c->device, nullptr, &wc);
-    if (st) {
-      status = st;
-      return;
-    }
+  // phase 1: operators
+  auto setup_work = [&](int w) {
     for (;;) {
-      size_t j = next++;
+      const size_t i = next++;
+      if (i >= (size_t)n || status.load() != QTT_OK) break;
+      int st = ms_setup(wcs[w], &rves[i], C0s + i * 36, o->op_tol, &ops[i]);
+      if (st) status = st;
+    }
+  };
+  {
+    std::vector<std::thread> th;
+    for (int w = 0; w < nw; ++w) th.emplace_back(setup_work, w);
+    for (auto& t : th) t.join();
+  }
+  // phase 2: the (RVE, load case) pairs
+  next = 0;
+  auto solve_work = [&](int w) {
+    for (;;) {
+      const size_t j = next++;
       if (j >= jobs.size() || status.load() != QTT_OK) break;
       const Job jb = jobs[j];
       const int nc = rves[jb.rve].ncomp;
@@ -2087,9 +2109,10 @@ extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const
       oj.trace = nullptr;
       oj.trace_cap = 0;
       oj.strain = nullptr;
+      oj.lc_workers = 1;
       std::vector<double> Cj(nc * nc, 0.0);
       ms_report rj;
-      st = ms_homogenize(wc, &rves[jb.rve], C0s + (size_t)jb.rve * 36, tol, max_rank, &oj, Cj.data(), &rj);
+      int st = ms_homogenize_ops(wcs[w], ops[jb.rve], tol, max_rank, &oj, Cj.data(), &rj);
       if (st) {
         status = st;
         break;
@@ -2102,7 +2125,6 @@ extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const
         R.residual[jb.lc] = rj.residual[jb.lc];
         R.sigma_imag_max = std::max(R.sigma_imag_max, rj.sigma_imag_max);
         R.max_rank_seen = std::max(R.max_rank_seen, rj.max_rank_seen);
-        R.setup_ms += rj.setup_ms;
         R.iterate_ms += rj.iterate_ms;
         R.kernel_launches += rj.kernel_launches;
         R.sketch_width_sum += rj.sketch_width_sum;
@@ -2110,17 +2132,27 @@ extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const
         R.post_checks += rj.post_checks;
         R.svd_fallbacks += rj.svd_fallbacks;
         R.post_err_max = std::max(R.post_err_max, rj.post_err_max);
+        R.fp64_residuals += rj.fp64_residuals;
       }
     }
-    {
-      std::lock_guard<std::mutex> lock(mu);
-      c->launches += wc->launches;
-    }
-    qtt_ctx_destroy(wc);
   };
-  std::vector<std::thread> th;
-  const int nw = std::min<int>(workers, (int)std::max<size_t>(1, jobs.size()));
-  for (int w = 0; w < nw; ++w) th.emplace_back(work);
-  for (auto& t : th) t.join();
+  if (status.load() == QTT_OK) {
+    std::vector<std::thread> th;
+    for (int w = 0; w < nw; ++w) th.emplace_back(solve_work, w);
+    for (auto& t : th) t.join();
+  }
+  for (int i = 0; i < n; ++i) {
+    if (ops[i] && reports) {
+      reports[i].setup_ms = ops[i]->setup_ms;
+      reports[i].kernel_launches += ops[i]->setup_launches;
+      reports[i].green_rank = ops[i]->O.green_rank;
+      reports[i].phase_rank = ops[i]->O.phase_rank;
+    }
+    ms_ops_destroy(ops[i]);
+  }
+  for (auto* x : wcs) {
+    c->launches += x->launches;
+    qtt_ctx_destroy(x);
+  }
   return status.load();
 }
