@@ -48,6 +48,7 @@ OVERSAMPLE = 8
 MAX_RANK = 128
 L2_BYTES = 129 * 1024 * 1024
 NLC = 6
+E2E_ITERS = 30
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel class, from the one-kernel ncu captures summarised in
 # profiles/ (file named in the line); None where no current capture exists.
@@ -340,16 +341,18 @@ def batched_rves(Q, ctx, count=16, log2_min=4, log2_max=5, workers=8):
         fracs.append(float(ind.mean()))
     t0 = time.perf_counter()
     Cs, reps = Q.ms_homogenize_batch(ctx, probs, tol=5e-5, max_rank=MAX_RANK, workers=workers, eps=EPS,
-                                     prec=Q.PREC_F32, max_iter=150, interleaved=False)
+                                     prec=Q.PREC_F32, max_iter=60, interleaved=False)
     wall = time.perf_counter() - t0
     ok = 0
     for C, (g, _, moduli, _), f in zip(Cs, probs, fracs):
         c = checks(C, moduli, f)
         ok += c["voigt_minus_C_min_eig"] > -1e-6 and c["C_minus_reuss_min_eig"] > -1e-6
     iters = [int(r.iterations[k]) for r in reps for k in range(NLC)]
-    return {"workload": "%d ellipsoid RVEs, sides 2^%d..2^%d, 6 load cases each, fast path" % (count, log2_min,
-                                                                                               log2_max),
+    return {"workload": "%d ellipsoid RVEs, sides 2^%d..2^%d, 6 load cases each, fast path, at most 60 "
+                        "iterations" % (count, log2_min, log2_max),
             "wall_s": wall, "rve_solves_per_s": count / wall, "load_case_solves": count * NLC,
+            "load_case_iterations_per_s": sum(iters) / wall,
+            "converged": sum(1 for r in reps for k in range(NLC) if r.residual[k] < 5e-5),
             "iterations_mean": statistics.mean(iters), "iterations_max": max(iters),
             "setup_s_sum": sum(r.setup_ms for r in reps) / 1e3, "within_voigt_reuss": ok,
             "max_rank": max(int(r.max_rank_seen) for r in reps)}
@@ -569,13 +572,14 @@ def run_ours(args, world, local_rank):
     Cp, repp, _ = sphere_solve(Q, ctx, args.n, fast_prec, 1, args.fp64_steps, ops, lc_workers=1, profile=True)
     prof = {k: ctx.profile_read(k) for k in ["gemm", "qr", "jacobi", "elem"]}
     ctx.profile(False)
-    # end to end: one converged solve through the public call, from host
-    # inputs (ellipsoid rows, C0) to the host effective tensor, operator
-    # setup included (tolerance 5e-5, the float path's working tolerance)
+    # end to end: one solve of E2E_ITERS iterations through the public call,
+    # from host inputs (ellipsoid rows, C0) to the host effective tensor,
+    # operator setup included (at this grid the rank cap holds the residual
+    # near 4e-2, so the solve runs a fixed number of iterations)
     geo_e, moduli_e, C0_e = sphere_geometry(Q, args.n)
     t0 = time.perf_counter()
     Ce, repe = Q.ms_homogenize(ctx, geo_e, "elastic", moduli_e, C0_e, tol=5e-5, max_rank=MAX_RANK, eps=EPS,
-                               prec=fast_prec, max_iter=200, lc_workers=NLC, load_mask=(1 << NLC) - 1,
+                               prec=fast_prec, max_iter=E2E_ITERS, lc_workers=NLC, load_mask=(1 << NLC) - 1,
                                interleaved=False)
     wall_e2e = time.perf_counter() - t0
     learned = None
@@ -606,7 +610,7 @@ def run_ours(args, world, local_rank):
         sec("plane_multibox", ms_plane, Q, ctx, 128)
         if args.batch > 0:
             sec("batched_rounding", batched_rounding, Q, torch, ctx, stream, flush, 64, args.batch)
-            sec("batched_rves", batched_rves, Q, ctx)
+            sec("batched_rves", batched_rves, Q, ctx, 8, 4, 4)
         if args.extras:
             sec("polar_vs_svd", polar_vs_svd, Q, torch, ctx, stream, flush)
             sec("tt_cross", cross_setup, Q, ctx)
@@ -779,8 +783,9 @@ def main():
                 "h2d_bytes_per_step": (rows.nbytes + C0.nbytes) / e2e_iters,
                 "d2h_bytes_per_step": (36 * 8) / e2e_iters,
                 "setup_ms": res["repe"].setup_ms, "wall_s": res["wall_e2e"], "iterations": e2e_iters,
-                "workload": "one converged solve (tolerance 5e-5) of the 6 load cases through ms_homogenize, "
-                            "operator setup included",
+                "workload": "one solve of %d iterations of the 6 load cases through ms_homogenize (stop "
+                            "tolerance 5e-5 not reached: the rank cap holds the residual), operator setup "
+                            "included" % E2E_ITERS,
                 "residuals": [float(res["repe"].residual[k]) for k in range(NLC)]},
         "gpu_launches": int(rep32.timed_launches),
         "clocks": res["clocks"],
