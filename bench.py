@@ -74,8 +74,9 @@ def parse():
                    help="also the f-row measurements: SVD vs polar compression, TT-cross operator setup on 2^18 x "
                         "2^18 grids and the 65536^2 multibox, AMEn vs sketched Green step (several minutes more)")
     p.add_argument("--batch", type=int, default=32)
-    p.add_argument("--prec", choices=["f32", "tc32"], default="f32",
-                   help="fast path arithmetic: float CUDA cores, or tensor cores for the large contractions")
+    p.add_argument("--prec", choices=["f32", "tc32", "tf32s"], default="f32",
+                   help="fast path arithmetic: float CUDA cores; tensor cores (3 TF32 passes) for the large "
+                        "contractions; or the sketch contractions on the tensor cores in one TF32 pass")
     p.add_argument("--profile-region", action="store_true",
                    help="only the fast solve of the headline, its iterations bracketed by cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off); prints one line with the launch count")
@@ -540,7 +541,7 @@ def run_ours(args, world, local_rank):
     stream = torch.cuda.Stream(device=local_rank)
     ctx = Q.Context(local_rank, stream.cuda_stream)
     props = torch.cuda.get_device_properties(local_rank)
-    fast_prec = Q.PREC_TC32 if args.prec == "tc32" else Q.PREC_F32
+    fast_prec = {"f32": Q.PREC_F32, "tc32": Q.PREC_TC32, "tf32s": Q.PREC_TF32S}[args.prec]
     peaks = {"fp32_tflops": ctx.measure_peak("fp32"), "fp64_tflops": ctx.measure_peak("fp64"),
              "sms": props.multi_processor_count}
 
@@ -583,11 +584,27 @@ def run_ours(args, world, local_rank):
                                interleaved=False)
     wall_e2e = time.perf_counter() - t0
     learned = None
+    tc_sketch = None
     if not args.no_secondary:
         try:
             learned = learned_ranks(Q, ctx, args.n, ops, fast_prec)
         except Exception as exc:  # noqa: BLE001
             learned = {"error": "%s: %s" % (type(exc).__name__, exc)}
+        try:
+            # the other float arithmetic on the same solve: the sketch
+            # contractions on the tensor cores in one TF32 pass (or back on
+            # the CUDA cores when that is the headline's), same iterations
+            # as the headline and as the FP64 comparison
+            other = Q.PREC_F32 if fast_prec == Q.PREC_TF32S else Q.PREC_TF32S
+            sphere_solve(Q, ctx, args.n, other, 1, 1, ops)
+            Co, repo, _ = sphere_solve(Q, ctx, args.n, other, args.warmup, args.steps, ops)
+            Co2, _, _ = sphere_solve(Q, ctx, args.n, other, 1, args.fp64_steps, ops)
+            tc_sketch = {"prec": "tf32s" if other == Q.PREC_TF32S else "f32",
+                         "iters_per_s": (repo.timed_iter / NLC) / (repo.timed_ms * 1e-3),
+                         "rel_dev_vs_fp64_same_iterations": rel_frob(Co2, C64),
+                         "rel_dev_vs_headline": rel_frob(Co, C32)}
+        except Exception as exc:  # noqa: BLE001
+            tc_sketch = {"error": "%s: %s" % (type(exc).__name__, exc)}
     green_rank, phase_rank = ops.ranks
     setup_ms = ops.setup_ms
     ops.close()
@@ -595,6 +612,8 @@ def run_ours(args, world, local_rank):
     secondary = {}
     if learned is not None:
         secondary["learned_ranks"] = learned
+    if tc_sketch is not None:
+        secondary["other_float_arithmetic"] = tc_sketch
     if not args.no_secondary:
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 

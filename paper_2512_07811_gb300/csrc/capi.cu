@@ -133,7 +133,7 @@ bool debug_checks() {
 
 int check_prec(qtt_dtype dt, qtt_prec p) {
   if (dt == QTT_C128 && p == QTT_PREC_F64) return QTT_OK;
-  if (dt == QTT_C64 && (p == QTT_PREC_F32 || p == QTT_PREC_TC32)) return QTT_OK;
+  if (dt == QTT_C64 && (p == QTT_PREC_F32 || p == QTT_PREC_TC32 || p == QTT_PREC_TF32S)) return QTT_OK;
   return QTT_ERR_ARG;
 }
 
@@ -545,6 +545,7 @@ int tt_round_sketched(qtt_ctx* c, int nterms, const qtt_complex* coef, const qtt
   }
   TRY(check_prec(sketch->dtype, p));
   TcScope tc(c, p == QTT_PREC_TC32);
+  TcSketchScope tcs(c, p == QTT_PREC_TF32S);
   return sketch->dtype == QTT_C128
              ? round_sketched<double>(c, nterms, coef, ops, xs, sketch, eps, max_rank, info, y)
              : round_sketched<float>(c, nterms, coef, ops, xs, sketch, eps, max_rank, info, y);
@@ -1903,7 +1904,8 @@ extern "C" int ms_ops_ranks(const ms_ops* m, int32_t* green_rank, int32_t* phase
 extern "C" int ms_homogenize_ops(qtt_ctx* c, const ms_ops* m, double tol, int max_rank, const ms_opts* o,
                                  double* C_eff, ms_report* rep) {
   if (!c || !m || !o || !C_eff || max_rank < 1) return QTT_ERR_ARG;
-  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32) return QTT_ERR_ARG;
+  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32 && o->prec != QTT_PREC_TF32S)
+    return QTT_ERR_ARG;
   const int nc = m->nc;
   const qtt_rve* rve = &m->rve;
   Ops& O = const_cast<Ops&>(m->O);   // read only: every solve converts the trains to its own copies
@@ -1927,6 +1929,7 @@ extern "C" int ms_homogenize_ops(qtt_ctx* c, const ms_ops* m, double tol, int ma
       st = ms_solve<double>(wc, rve, C1.data(), C2.data(), O, tol, max_rank, oj, QTT_C128, Cj, rj, &gate, arrived);
     } else {
       TcScope tc(wc, oj.prec == QTT_PREC_TC32);
+      TcSketchScope tcs(wc, oj.prec == QTT_PREC_TF32S);
       st = ms_solve<float>(wc, rve, C1.data(), C2.data(), O, tol, max_rank, oj, QTT_C64, Cj, rj, &gate, arrived);
     }
     if (!st && wc->d_tcerr) {
@@ -2028,7 +2031,8 @@ extern "C" int ms_homogenize_ops(qtt_ctx* c, const ms_ops* m, double tol, int ma
 extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, double tol, int max_rank,
                              const ms_opts* o, double* C_eff, ms_report* rep) {
   if (!c || !rve || !C0 || !o || !C_eff || max_rank < 1) return QTT_ERR_ARG;
-  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32) return QTT_ERR_ARG;
+  if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32 && o->prec != QTT_PREC_TF32S)
+    return QTT_ERR_ARG;
   ms_ops* m = nullptr;
   int s = ms_setup(c, rve, C0, o->op_tol, &m);
   if (s) return s;

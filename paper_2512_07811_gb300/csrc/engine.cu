@@ -13,6 +13,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <numeric>
 #include <map>
 #include <mutex>
 #include <chrono>
@@ -151,24 +152,36 @@ static GemmDesc fold_shared_batch(const GemmDesc& g) {
 }
 
 static int tc_route(qtt_ctx* c, const GemmDesc& g0, cc alpha, cc beta, const cc* A, const cc* B, cc* C) {
+  const bool single = c->tc_sketch && c->in_sketch && !c->tc;
+  if (!c->tc && !single) return QTT_ERR_UNSUPPORTED;
   const GemmDesc g = fold_shared_batch(g0);
-  if (!c->tc || g.M < 64 || g.N < 16 || g.K < 32 || (double)g.M * g.N * g.K < 2.0e5) return QTT_ERR_UNSUPPORTED;
+  if (g.M < 64 || g.N < 16 || g.K < 32 || (double)g.M * g.N * g.K * g.batch < 2.0e5) return QTT_ERR_UNSUPPORTED;
   if (!c->d_tcerr) {
     if (cudaMalloc(&c->d_tcerr, sizeof(int)) != cudaSuccess) return QTT_ERR_OOM;
     cudaMemsetAsync(c->d_tcerr, 0, sizeof(int), c->stream);
   }
+  const int passes = single ? 1 : 3;
+  // batched in one launch per chunk of entries (the packed operands of a
+  // chunk stay within about 1 GiB)
+  const size_t per = qtt_tc_gemm_workspace_ex(g.M, g.N, g.K, 1, passes);
+  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(g.batch, ((int64_t)1 << 30) / (int64_t)per));
+  // a chunk starts at a multiple of every two-level batch index's inner
+  // size, so that the offsets of its entries are those of a batch from 0
+  const int64_t inner = std::lcm(std::lcm(std::max<int64_t>(1, g.bA.n2), std::max<int64_t>(1, g.bB.n2)),
+                                 std::max<int64_t>(1, g.bC.n2));
+  if (chunk < g.batch) chunk = std::max<int64_t>(inner, chunk / inner * inner);
   void* ws = nullptr;
-  if (dalloc(c, &ws, qtt_tc_gemm_workspace(g.M, g.N, g.K))) return QTT_ERR_OOM;
-  GemmDesc one = g;
-  one.batch = 1;
-  one.bA = one.bB = one.bC = MIdx{1, 1, 0, 0};
+  if (dalloc(c, &ws, qtt_tc_gemm_workspace_ex(g.M, g.N, g.K, chunk, passes))) return QTT_ERR_OOM;
   int st = QTT_OK;
-  for (int64_t b = 0; b < g.batch && !st; ++b) {
+  for (int64_t b0 = 0; b0 < g.batch && !st; b0 += chunk) {
+    GemmDesc part = g;
+    part.batch = std::min<int64_t>(chunk, g.batch - b0);
     c->launches += 4;
     cudaEvent_t ev = prof_begin(c);
-    st = qtt_tc_gemm(one, alpha, beta, A + midx_off(g.bA, b), B + midx_off(g.bB, b), C + midx_off(g.bC, b), ws,
-                     c->d_tcerr, c->stream);
-    prof_end(c, ev, PK_GEMM, 8.0 * g.M * g.N * g.K, (double)(g.M * g.K + g.K * g.N + g.M * g.N) * sizeof(cc));
+    st = qtt_tc_gemm_ex(part, alpha, beta, A + midx_off(g.bA, b0), B + midx_off(g.bB, b0), C + midx_off(g.bC, b0),
+                        ws, c->d_tcerr, c->stream, passes);
+    prof_end(c, ev, PK_GEMM, 8.0 * g.M * g.N * g.K * part.batch,
+             (double)(g.M * g.K + g.K * g.N + g.M * g.N) * part.batch * sizeof(cc));
   }
   dfree(c, ws);
   return st;
@@ -1485,6 +1498,10 @@ static int sketch_core(qtt_ctx* c, int T, const qtt_complex* coef, const qtt_mpo
   for (int k = d - 1; k >= (dot_out ? 0 : 1); --k) {
     const int64_t l0 = S->r[k], l1 = S->r[k + 1], no = S->n[k];
     TRY(W[k].alloc(c, (size_t)Bt(k) * l0 * sizeof(C)));
+    // the sketch side: under QTT_PREC_TF32S these contractions may take one
+    // TF32 pass on the tensor cores (never for an exact inner product)
+    InSketch in_sketch(c);
+    if (dot_out) c->in_sketch = false;
     for (int t = 0; t < T; ++t) {
       const int64_t g0 = A[t]->g[k], g1 = A[t]->g[k + 1], ni = A[t]->ni[k];
       const int64_t a0 = xs[t]->r[k], a1 = xs[t]->r[k + 1];

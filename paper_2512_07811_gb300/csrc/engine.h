@@ -29,13 +29,29 @@ struct qtt_ctx {
   std::vector<ProfRec> recs;
   int* d_sweeps = nullptr;   // device counters written by profiled Jacobi launches
   int sweeps_cap = 0, sweeps_used = 0;
-  bool tc = false;           // route large float contractions to the tensor cores
+  bool tc = false;           // route large float contractions to the tensor cores (3 TF32 passes)
+  bool tc_sketch = false;    // the sketch contractions of sketched roundings on the tensor cores, 1 pass
+  bool in_sketch = false;    // set while those contractions are issued
   int* d_tcerr = nullptr;    // bounded-wait failure flag of the tensor-core GEMM
   int64_t fail_alloc_after = -1;  // test hook: allocations left before dalloc fails (-1: off)
   // profiler totals handed over by contexts that worked for this one (the
   // load-case workers of ms_homogenize), per kernel class
   double ext_ms[PK_N] = {0, 0, 0, 0}, ext_flops[PK_N] = {0, 0, 0, 0}, ext_bytes[PK_N] = {0, 0, 0, 0};
   int64_t ext_launches[PK_N] = {0, 0, 0, 0};
+};
+
+// Scoped switch of the single-pass tensor-core route of the sketch contractions.
+struct TcSketchScope {
+  qtt_ctx* c;
+  bool old;
+  TcSketchScope(qtt_ctx* ctx, bool on) : c(ctx), old(ctx->tc_sketch) { ctx->tc_sketch = on; }
+  ~TcSketchScope() { c->tc_sketch = old; }
+};
+struct InSketch {
+  qtt_ctx* c;
+  bool old;
+  explicit InSketch(qtt_ctx* ctx) : c(ctx), old(ctx->in_sketch) { ctx->in_sketch = true; }
+  ~InSketch() { c->in_sketch = old; }
 };
 
 // Scoped switch of the tensor-core route for one ABI call.

@@ -88,6 +88,9 @@ int qtt_adjoint_core(const cplx<R>* D, int64_t g0, int64_t no, int64_t ni, int64
 
 // tensor-core complex64 GEMM (tc_gemm.cu), batch 1
 size_t qtt_tc_gemm_workspace(int64_t M, int64_t N, int64_t K);
+size_t qtt_tc_gemm_workspace_ex(int64_t M, int64_t N, int64_t K, int64_t batch, int passes);
+int qtt_tc_gemm_ex(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C, void* ws, int* err,
+                   cudaStream_t s, int passes);
 int qtt_tc_gemm(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C, void* ws, int* err,
                 cudaStream_t s);
 

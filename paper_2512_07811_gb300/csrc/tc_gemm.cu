@@ -8,7 +8,12 @@
 //   B2 = [[Br^T | -Bi^T]; [Bi^T | Br^T]] (2N x 2K)   =>  A2 B2^T = [Cr | Ci]
 // and, for FP32-level accuracy, the split x = hi + lo with hi = tf32(x),
 // lo = tf32(x - hi): A3 = [A2hi | A2hi | A2lo], B3 = [B2hi | B2lo | B2hi]
-// (K3 = 6K, padded to 32), so A3 B3^T = A2hi B2hi^T + A2hi B2lo^T + A2lo B2hi^T.
+// (K3 = 6K, padded to 32), so A3 B3^T = A2hi B2hi^T + A2hi B2lo^T + A2lo B2hi^T
+// (three passes); or the single pass A3 = A2hi, B3 = B2hi (K3 = 2K), TF32's
+// 11-bit significand, for contractions whose errors the method tolerates.
+// A batch of such products runs as one launch: the packed operands are
+// stacked [batch][rows][K3] and read through 3D tensor maps, blockIdx.z
+// being the batch entry.
 //
 // The tensor-core kernel: one CTA (128 threads) per 128 x 128 tile of C3;
 // TMA (128-byte swizzle, 32 fp32 of K per row) fills a 4-stage ring of A and
@@ -51,17 +56,19 @@ __device__ __forceinline__ float split_part(float x) {
   return PART_LO ? to_tf32(x - hi) : hi;
 }
 
-__global__ void pack_a_kernel(const cc* __restrict__ A, GemmDesc g, int64_t K3p, float* __restrict__ A3, int64_t Mp) {
+__global__ void pack_a_kernel(const cc* __restrict__ A, GemmDesc g, int64_t K3p, float* __restrict__ A3, int64_t Mp,
+                              int passes) {
   const int64_t K = g.K;
-  const int64_t total = Mp * K3p;
+  const int64_t per = Mp * K3p, total = per * g.batch;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t m = e / K3p, col = e - m * K3p;
+    const int64_t b = e / per, r = e - b * per;
+    int64_t m = r / K3p, col = r - m * K3p;
     float v = 0.f;
-    if (m < g.M && col < 6 * K) {
+    if (m < g.M && col < (passes == 3 ? 6 : 2) * K) {
       int part = (int)(col / (2 * K));
       int64_t c = col - part * 2 * K;
       int64_t k = c < K ? c : c - K;
-      cc a = A[midx_off(g.mA, m) + midx_off(g.kA, k)];
+      cc a = A[midx_off(g.bA, b) + midx_off(g.mA, m) + midx_off(g.kA, k)];
       if (g.conjA) a.im = -a.im;
       float x = c < K ? a.re : a.im;
       v = part == 2 ? split_part<1>(x) : split_part<0>(x);
@@ -71,18 +78,20 @@ __global__ void pack_a_kernel(const cc* __restrict__ A, GemmDesc g, int64_t K3p,
 }
 
 // B3 row j (j < Np): n = j mod N, half = j / N; K-columns as for A with parts (hi, lo, hi)
-__global__ void pack_b_kernel(const cc* __restrict__ B, GemmDesc g, int64_t K3p, float* __restrict__ B3, int64_t Np) {
+__global__ void pack_b_kernel(const cc* __restrict__ B, GemmDesc g, int64_t K3p, float* __restrict__ B3, int64_t Np,
+                              int passes) {
   const int64_t K = g.K, N = g.N;
-  const int64_t total = Np * K3p;
+  const int64_t per = Np * K3p, total = per * g.batch;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t j = e / K3p, col = e - j * K3p;
+    const int64_t bt = e / per, r = e - bt * per;
+    int64_t j = r / K3p, col = r - j * K3p;
     float v = 0.f;
-    if (j < 2 * N && col < 6 * K) {
+    if (j < 2 * N && col < (passes == 3 ? 6 : 2) * K) {
       int part = (int)(col / (2 * K));
       int64_t c = col - part * 2 * K;
       int64_t n = j < N ? j : j - N;
       int64_t k = c < K ? c : c - K;
-      cc b = B[midx_off(g.kB, k) + midx_off(g.nB, n)];
+      cc b = B[midx_off(g.bB, bt) + midx_off(g.kB, k) + midx_off(g.nB, n)];
       if (g.conjB) b.im = -b.im;
       float x;
       if (j < N) x = c < K ? b.re : -b.im;  // row n:   [Br | -Bi]
@@ -93,15 +102,18 @@ __global__ void pack_b_kernel(const cc* __restrict__ B, GemmDesc g, int64_t K3p,
   }
 }
 
-// C[m, n] = alpha (C3[m, n] + i C3[m, N + n]) + beta C[m, n]
-__global__ void unpack_c_kernel(const float* __restrict__ C3, int64_t ldc3, GemmDesc g, cc alpha, cc beta,
-                                cc* __restrict__ C) {
-  const int64_t total = g.M * g.N;
+// C[m, n] = alpha (C3[m, n] + i C3[m, N + n]) + beta C[m, n], batch entry by
+// batch entry (C3 entries at a stride of c3_batch floats)
+__global__ void unpack_c_kernel(const float* __restrict__ C3, int64_t ldc3, int64_t c3_batch, GemmDesc g, cc alpha,
+                                cc beta, cc* __restrict__ C) {
+  const int64_t per = g.M * g.N, total = per * g.batch;
   const bool use_beta = beta.re != 0.f || beta.im != 0.f;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t m = e / g.N, n = e - m * g.N;
-    cc v(C3[m * ldc3 + n], C3[m * ldc3 + g.N + n]);
-    int64_t o = midx_off(g.mC, m) + midx_off(g.nC, n);
+    const int64_t b = e / per, rr = e - b * per;
+    int64_t m = rr / g.N, n = rr - m * g.N;
+    const float* c3 = C3 + b * c3_batch;
+    cc v(c3[m * ldc3 + n], c3[m * ldc3 + g.N + n]);
+    int64_t o = midx_off(g.bC, b) + midx_off(g.mC, m) + midx_off(g.nC, n);
     cc r = alpha * v;
     if (use_beta) r = r + beta * C[o];
     C[o] = r;
@@ -137,11 +149,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
   }
   return false;
 }
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+// tile (x, y) of batch entry z of a 3D tensor map (x innermost)
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
           smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
 // shared-memory matrix descriptor (K-major, 128-byte swizzle): start >> 4,
@@ -167,7 +180,7 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 
 __global__ void __launch_bounds__(128, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float* __restrict__ C3,
-               int64_t ldc3, int k_tiles, int* __restrict__ err) {
+               int64_t ldc3, int64_t c3_batch, int k_tiles, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -215,8 +228,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       unsigned char* a = smem + s * STAGE_BYTES;
       unsigned char* b = a + TILE_A_BYTES;
       mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-      tma_load_2d(&mapA, &full_bar[s], a, kt * TBK, m0);
-      tma_load_2d(&mapB, &full_bar[s], b, kt * TBK, n0);
+      tma_load_3d(&mapA, &full_bar[s], a, kt * TBK, m0, (int)blockIdx.z);
+      tma_load_3d(&mapB, &full_bar[s], b, kt * TBK, n0, (int)blockIdx.z);
       issued = kt + 1;
     }
     // Drain: every load this thread issued must have landed before the CTA
@@ -270,7 +283,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
     const int row = m0 + warp * 32 + lane;
-    float* crow = C3 + (int64_t)row * ldc3 + n0;
+    float* crow = C3 + (int64_t)blockIdx.z * c3_batch + (int64_t)row * ldc3 + n0;
 #pragma unroll 1
     for (int c0 = 0; c0 < TBN; c0 += 16) {
       uint32_t v[16];
@@ -311,15 +324,16 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// rows x cols fp32, row-major (cols contiguous), box 32 (cols) x 128 (rows), 128-byte swizzle
-bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols) {
+// batch x rows x cols fp32, row-major (cols contiguous), box 32 (cols) x 128
+// (rows) x 1, 128-byte swizzle
+bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t batch) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)TBM};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)cols * sizeof(float), (cuuint64_t)(rows * cols) * sizeof(float)};
+  cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)TBM, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -328,40 +342,52 @@ inline unsigned grid1d(int64_t n) { return (unsigned)std::min<int64_t>((n + 255)
 
 }  // namespace
 
-// Workspace bytes for one call with the given sizes.
-size_t qtt_tc_gemm_workspace(int64_t M, int64_t N, int64_t K) {
+static int64_t k3_pad(int64_t K, int passes) { return ((passes == 3 ? 6 : 2) * K + TBK - 1) / TBK * TBK; }
+
+// Workspace bytes for a batched call (passes 1 or 3).
+size_t qtt_tc_gemm_workspace_ex(int64_t M, int64_t N, int64_t K, int64_t batch, int passes) {
   const int64_t Mp = (M + TBM - 1) / TBM * TBM;
   const int64_t Np = (2 * N + TBN - 1) / TBN * TBN;
-  const int64_t K3p = (6 * K + TBK - 1) / TBK * TBK;
-  return (size_t)(Mp * K3p + Np * K3p + Mp * Np) * sizeof(float) + 3 * 1024 + 16;
+  const int64_t K3p = k3_pad(K, passes);
+  return (size_t)batch * (Mp * K3p + Np * K3p + Mp * Np) * sizeof(float) + 3 * 1024 + 16;
 }
 
-// Single-batch complex64 GEMM through the tensor cores.  `ws` needs
-// qtt_tc_gemm_workspace(M, N, K) bytes (device), `err` one device int
-// (set non-zero when a bounded wait gave up).
+// Workspace bytes for one call with the given sizes.
+size_t qtt_tc_gemm_workspace(int64_t M, int64_t N, int64_t K) { return qtt_tc_gemm_workspace_ex(M, N, K, 1, 3); }
+
+// Batched complex64 GEMM through the tensor cores, every batch entry of g in
+// one launch, 1 or 3 TF32 passes.  `ws` needs qtt_tc_gemm_workspace_ex bytes
+// (device), `err` one device int (set non-zero when a bounded wait gave up).
+int qtt_tc_gemm_ex(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C, void* ws, int* err,
+                   cudaStream_t s, int passes) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0 || g.batch > 65535) return QTT_ERR_ARG;
+  if (passes != 1 && passes != 3) return QTT_ERR_ARG;
+  const int64_t Mp = (g.M + TBM - 1) / TBM * TBM;
+  const int64_t Np = (2 * g.N + TBN - 1) / TBN * TBN;
+  const int64_t K3p = k3_pad(g.K, passes);
+  uintptr_t p = (reinterpret_cast<uintptr_t>(ws) + 1023) & ~(uintptr_t)1023;
+  float* A3 = reinterpret_cast<float*>(p);
+  p = (reinterpret_cast<uintptr_t>(A3 + g.batch * Mp * K3p) + 1023) & ~(uintptr_t)1023;
+  float* B3 = reinterpret_cast<float*>(p);
+  p = (reinterpret_cast<uintptr_t>(B3 + g.batch * Np * K3p) + 1023) & ~(uintptr_t)1023;
+  float* C3 = reinterpret_cast<float*>(p);
+  pack_a_kernel<<<grid1d(g.batch * Mp * K3p), 256, 0, s>>>(A, g, K3p, A3, Mp, passes);
+  pack_b_kernel<<<grid1d(g.batch * Np * K3p), 256, 0, s>>>(B, g, K3p, B3, Np, passes);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A3, Mp, K3p, g.batch) || !make_map(&mb, B3, Np, K3p, g.batch)) return QTT_ERR_CUDA;
+  const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
+  if (qtt_allow_max_smem((const void*)tc_gemm_kernel) != QTT_OK) return QTT_ERR_CUDA;
+  dim3 grid((unsigned)(Np / TBN), (unsigned)(Mp / TBM), (unsigned)g.batch);
+  tc_gemm_kernel<<<grid, 128, smem, s>>>(ma, mb, C3, Np, Mp * Np, (int)(K3p / TBK), err);
+  unpack_c_kernel<<<grid1d(g.batch * g.M * g.N), 256, 0, s>>>(C3, Np, Mp * Np, g, alpha, beta, C);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
+// Single-batch complex64 GEMM through the tensor cores, three TF32 passes.
 int qtt_tc_gemm(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C, void* ws, int* err,
                 cudaStream_t s) {
   if (g.batch != 1) return QTT_ERR_UNSUPPORTED;
-  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return QTT_ERR_ARG;
-  const int64_t Mp = (g.M + TBM - 1) / TBM * TBM;
-  const int64_t Np = (2 * g.N + TBN - 1) / TBN * TBN;
-  const int64_t K3p = (6 * g.K + TBK - 1) / TBK * TBK;
-  uintptr_t p = (reinterpret_cast<uintptr_t>(ws) + 1023) & ~(uintptr_t)1023;
-  float* A3 = reinterpret_cast<float*>(p);
-  p = (reinterpret_cast<uintptr_t>(A3 + Mp * K3p) + 1023) & ~(uintptr_t)1023;
-  float* B3 = reinterpret_cast<float*>(p);
-  p = (reinterpret_cast<uintptr_t>(B3 + Np * K3p) + 1023) & ~(uintptr_t)1023;
-  float* C3 = reinterpret_cast<float*>(p);
-  pack_a_kernel<<<grid1d(Mp * K3p), 256, 0, s>>>(A, g, K3p, A3, Mp);
-  pack_b_kernel<<<grid1d(Np * K3p), 256, 0, s>>>(B, g, K3p, B3, Np);
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, A3, Mp, K3p) || !make_map(&mb, B3, Np, K3p)) return QTT_ERR_CUDA;
-  const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
-  if (qtt_allow_max_smem((const void*)tc_gemm_kernel) != QTT_OK) return QTT_ERR_CUDA;
-  dim3 grid((unsigned)(Np / TBN), (unsigned)(Mp / TBM), 1);
-  tc_gemm_kernel<<<grid, 128, smem, s>>>(ma, mb, C3, Np, (int)(K3p / TBK), err);
-  unpack_c_kernel<<<grid1d(g.M * g.N), 256, 0, s>>>(C3, Np, g, alpha, beta, C);
-  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+  return qtt_tc_gemm_ex(g, alpha, beta, A, B, C, ws, err, s, 3);
 }
 
 // --------------------------------------------- allocation-free entry point

@@ -29,7 +29,7 @@ _ALIVE = [True]
 atexit.register(lambda: _ALIVE.__setitem__(0, False))
 
 C128, C64 = 0, 1
-PREC_F64, PREC_F32, PREC_TC32 = 0, 1, 2
+PREC_F64, PREC_F32, PREC_TC32, PREC_TF32S = 0, 1, 2, 3
 _NP = {C128: np.complex128, C64: np.complex64}
 
 
