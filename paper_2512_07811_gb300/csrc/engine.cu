@@ -169,6 +169,7 @@ static int tc_route(qtt_ctx* c, const GemmDesc& g0, cc alpha, cc beta, const cc*
   // size, so that the offsets of its entries are those of a batch from 0
   const int64_t inner = std::lcm(std::lcm(std::max<int64_t>(1, g.bA.n2), std::max<int64_t>(1, g.bB.n2)),
                                  std::max<int64_t>(1, g.bC.n2));
+  chunk = std::min<int64_t>(chunk, 65535 / inner * inner);   // grid z limit
   if (chunk < g.batch) chunk = std::max<int64_t>(inner, chunk / inner * inner);
   void* ws = nullptr;
   if (dalloc(c, &ws, qtt_tc_gemm_workspace_ex(g.M, g.N, g.K, chunk, passes))) return QTT_ERR_OOM;
