@@ -63,26 +63,27 @@ def test_tc32_rounding_and_solver():
 def test_sketched_rounding_with_single_pass_tensor_core_sketch():
     """QTT_PREC_TF32S: the right partial contractions of the sketch (batched,
     one TF32 pass on the tensor cores) perturb only the random test matrix;
-    the rounded Hadamard product keeps the float path's accuracy against the
-    exact product."""
-    import math
+    the rounded Hadamard product (rank 128, inside the sketch width 144)
+    keeps the float path's accuracy against the exact product, and differs
+    from the float-sketch result (the tensor-core route did run)."""
     from oracle import tt as T
     from paper_2512_07811_gb300 import inputs as I
     from paper_2512_07811_gb300 import qtt as Q
     ctx = Q.Context(0)
-    d = 10
-    x = I.random_tt_cores(d, 2, 32, seed=61, dtype=np.complex128)
-    y = I.random_tt_cores(d, 2, 32, seed=62, dtype=np.complex128)
+    d = 12
+    x = I.random_tt_cores(d, 2, 8, seed=61, dtype=np.complex128)
+    y = I.random_tt_cores(d, 2, 16, seed=62, dtype=np.complex128)
     exact = T.tt_full(T.tt_hadamard(x, y))
-    sk, _ = I.sketch_cores(np.random.default_rng(63), d, [2] * d, 48)
+    sk, _ = I.sketch_cores(np.random.default_rng(63), d, [2] * d, 144)
     X = Q.TT.from_cores(ctx, x, Q.C64)
     Y = Q.TT.from_cores(ctx, y, Q.C64)
     S = Q.TT.from_cores(ctx, sk, Q.C64)
     DX = Q.qtt_mpo_diag(ctx, X)
-    errs = {}
+    errs, fulls = {}, {}
     for name, p in [("f32", Q.PREC_F32), ("tf32s", Q.PREC_TF32S)]:
-        z, info = Q.tt_round_sketched(ctx, [(1.0, DX, Y)], S, 1e-5, 0, prec=p)
-        full = T.tt_full([c.astype(np.complex128) for c in z.cores()])
-        errs[name] = np.linalg.norm(full - exact) / np.linalg.norm(exact)
+        z, info = Q.tt_round_sketched(ctx, [(1.0, DX, Y)], S, 1e-6, 0, prec=p)
+        fulls[name] = T.tt_full([c.astype(np.complex128) for c in z.cores()])
+        errs[name] = np.linalg.norm(fulls[name] - exact) / np.linalg.norm(exact)
     print("\nrelative error: float sketch %.2e, single-pass TF32 sketch %.2e" % (errs["f32"], errs["tf32s"]))
-    assert errs["f32"] < 5e-5 and errs["tf32s"] < 5e-5
+    assert errs["f32"] < 2e-5 and errs["tf32s"] < 2e-5
+    assert np.abs(fulls["f32"] - fulls["tf32s"]).max() > 0
