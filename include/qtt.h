@@ -69,11 +69,10 @@ typedef enum { QTT_C128 = 0, QTT_C64 = 1 } qtt_dtype;
  * (tcgen05.mma kind::tf32, three-term TF32 split, FP32 accumulation in
  * tensor memory): about 1e-5 relative per contraction at K ~ 10^3.
  * QTT_PREC_TF32S (QTT_C64 storage) is QTT_PREC_F32 with the sketch
- * contractions of the sketched roundings -- the right partial contractions
- * of the random sketch with the structured sum, whose errors only perturb
- * the random test matrix (the projection onto its range stays exact in
- * float) -- on the tensor cores in one TF32 pass, every batch entry in one
- * launch; all other contractions stay in float. */
+ * contractions of the sketched roundings (the right partial contractions of
+ * the random sketch with the structured sum) on the tensor cores, three-term
+ * TF32 split, every batch entry of a contraction in one launch; all other
+ * contractions stay on the CUDA cores. */
 typedef enum { QTT_PREC_F64 = 0, QTT_PREC_F32 = 1, QTT_PREC_TC32 = 2, QTT_PREC_TF32S = 3 } qtt_prec;
 
 typedef struct {

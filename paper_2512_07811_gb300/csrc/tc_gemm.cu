@@ -10,7 +10,8 @@
 // lo = tf32(x - hi): A3 = [A2hi | A2hi | A2lo], B3 = [B2hi | B2lo | B2hi]
 // (K3 = 6K, padded to 32), so A3 B3^T = A2hi B2hi^T + A2hi B2lo^T + A2lo B2hi^T
 // (three passes); or the single pass A3 = A2hi, B3 = B2hi (K3 = 2K), TF32's
-// 11-bit significand, for contractions whose errors the method tolerates.
+// 11-bit significand (available to callers; the library's own routes use
+// three passes).
 // A batch of such products runs as one launch: the packed operands are
 // stacked [batch][rows][K3] and read through 3D tensor maps, blockIdx.z
 // being the batch entry.

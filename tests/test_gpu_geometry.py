@@ -133,7 +133,8 @@ def test_fast_path_plane_multibox_within_1e4_of_fp64(Q, ctx):
 
 def test_tf32_sketch_path_elastic_sphere_within_1e4_of_fp64(Q, ctx):
     """The same 16^3 sphere with the sketch contractions on the tensor cores
-    in one TF32 pass (QTT_PREC_TF32S): C_eff within 1e-4 of the FP64 path."""
+    (QTT_PREC_TF32S, batched, three-term TF32 split): C_eff within 1e-4 of
+    the FP64 path."""
     N = 16
     rows = I.sphere_rows(0.2)
     C0 = MS.iso_voigt(0.5 * (LAM1 + LAM2), 0.5 * (MU1 + MU2))
@@ -144,5 +145,5 @@ def test_tf32_sketch_path_elastic_sphere_within_1e4_of_fp64(Q, ctx):
     Ct, rt = Q.ms_homogenize(ctx, geo, "elastic", (LAM1, MU1, LAM2, MU2), C0, tol=5e-5, eps=1e-6,
                              prec=Q.PREC_TF32S, **kw)
     rel = np.linalg.norm(Ct[:, 0] - C64[:, 0]) / np.linalg.norm(C64[:, 0])
-    print("\nelastic sphere 16^3: TF32-sketch path vs FP64 %.2e (%d iterations)" % (rel, rt.iterations[0]))
+    print("\nelastic sphere 16^3: tensor-core sketch path vs FP64 %.2e (%d iterations)" % (rel, rt.iterations[0]))
     assert rt.iterations[0] < 200 and rel < 1e-4

@@ -61,11 +61,11 @@ def test_tc32_rounding_and_solver():
 
 
 def test_sketched_rounding_with_single_pass_tensor_core_sketch():
-    """QTT_PREC_TF32S: the right partial contractions of the sketch (batched,
-    one TF32 pass on the tensor cores) perturb only the random test matrix;
-    the rounded Hadamard product (rank 128, inside the sketch width 144)
-    keeps the float path's accuracy against the exact product, and differs
-    from the float-sketch result (the tensor-core route did run)."""
+    """QTT_PREC_TF32S: the right partial contractions of the sketch on the
+    tensor cores (batched, three-term TF32 split): the rounded Hadamard
+    product (rank 128, inside the sketch width 144) keeps the float path's
+    accuracy against the exact product, and differs from the float-sketch
+    result in the last bits (the tensor-core route did run)."""
     from oracle import tt as T
     from paper_2512_07811_gb300 import inputs as I
     from paper_2512_07811_gb300 import qtt as Q
@@ -84,6 +84,6 @@ def test_sketched_rounding_with_single_pass_tensor_core_sketch():
         z, info = Q.tt_round_sketched(ctx, [(1.0, DX, Y)], S, 1e-6, 0, prec=p)
         fulls[name] = T.tt_full([c.astype(np.complex128) for c in z.cores()])
         errs[name] = np.linalg.norm(fulls[name] - exact) / np.linalg.norm(exact)
-    print("\nrelative error: float sketch %.2e, single-pass TF32 sketch %.2e" % (errs["f32"], errs["tf32s"]))
+    print("\nrelative error: float sketch %.2e, tensor-core sketch %.2e" % (errs["f32"], errs["tf32s"]))
     assert errs["f32"] < 2e-5 and errs["tf32s"] < 2e-5
     assert np.abs(fulls["f32"] - fulls["tf32s"]).max() > 0
