@@ -193,13 +193,13 @@ static int tc_route(qtt_ctx* c, const GemmDesc& g0, cc alpha, cc beta, const cc*
 
 // ------------------------------------------------------ GEMM tile autotuner
 // The first CUDA-core GEMM of a shape (element size, M, N, K, batch and which
-// operand indices are contiguous) with enough work times the candidate tile
-// edges (32, 64) and split counts (1, the rule's, twice the rule's) once, with
-// CUDA events on the caller's stream into a scratch output, and caches the
-// fastest; later GEMMs of the shape use it.  The cache is process-wide, so
-// every context of a process takes the same choice (results do not depend on
-// which context, or thread, tuned a shape first).  GEMMs that accumulate
-// into C (beta != 0) or are too small to matter keep the rule's choice.
+// operand indices are contiguous) with enough work times the two tile edges
+// (32, 64) once, at the split count the rule gives the shape, with CUDA
+// events on the caller's stream into a scratch output, and caches the
+// faster; later GEMMs of the shape use it.  The choice only changes speed:
+// both edges give the same result bit for bit, so results are reproducible
+// across contexts, threads and processes.  GEMMs that accumulate into C
+// (beta != 0) or are too small to matter keep the rule's choice.
 struct TuneKey {
   int64_t v[7];
   bool operator<(const TuneKey& o) const { return std::lexicographical_compare(v, v + 7, o.v, o.v + 7); }
@@ -215,14 +215,14 @@ static int tune_gemm(qtt_ctx* c, const GemmDesc& g, const cplx<R>* A, const cplx
   d.bC = MIdx{g.batch, 1, g.M * g.N, 0};
   d.mC = MIdx{g.M, 1, g.N, 0};
   d.nC = MIdx{g.N, 1, 1, 0};
+  // The split count is fixed by the shape (the rule at tile edge 64), only
+  // the tile edge is timed: both edges sum every element over K in the same
+  // order (K tiles of the same depth, then the fixed-order split reduction),
+  // so whichever edge a process picks, the results are the same bit for bit
+  // in every process.
   std::vector<std::pair<int, int>> cand;
-  for (int t : {32, 64}) {
-    const int s0 = qtt_gemm_splits_for(g, t);
-    for (int sp : {1, s0, 2 * s0})
-      if (sp >= 1 && sp <= 32 && (int64_t)g.batch * sp <= 65535 &&
-          std::find(cand.begin(), cand.end(), std::make_pair(t, sp)) == cand.end())
-        cand.emplace_back(t, sp);
-  }
+  const int s0 = std::min(qtt_gemm_splits_for(g, 64), (int)std::max<int64_t>(1, 65535 / std::max<int64_t>(1, g.batch)));
+  for (int t : {32, 64}) cand.emplace_back(t, s0);
   int maxs = 1;
   for (auto& cs : cand) maxs = std::max(maxs, cs.second);
   void* buf = nullptr;

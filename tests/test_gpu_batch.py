@@ -162,3 +162,27 @@ def test_setup_handle_reused_equals_one_call(Q):
         Cb, rb = Q.ms_homogenize(ctx, None, "scalar", None, None, prec=prec, ops=ops, **kw)
         np.testing.assert_array_equal(Ca, Cb)
         assert rb.setup_ms == 0 and ra.green_rank == rb.green_rank == g
+
+
+def test_results_identical_across_processes():
+    """The same solve in two fresh processes gives the same effective tensor
+    bit for bit: the GEMM tile tuner, which each process runs by timing,
+    chooses only between tile edges that sum in the same order."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import numpy as np\n"
+        "from paper_2512_07811_gb300 import qtt as Q, inputs as I\n"
+        "ctx = Q.Context(0)\n"
+        "geo = Q.Ellipsoids(I.sphere_rows(0.2), (16, 16, 16))\n"
+        "C, rep = Q.ms_homogenize(ctx, geo, 'scalar', (1.0, 10.0), 5.5 * np.eye(3), tol=0.0, max_rank=64,\n"
+        "                         eps=1e-6, prec=Q.PREC_F32, max_iter=4, min_iter=4, interleaved=False)\n"
+        "print(' '.join(float(v).hex() for v in C.ravel()))\n" % root)
+    outs = [subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+            for _ in range(2)]
+    for o in outs:
+        assert o.returncode == 0, o.stderr[-2000:]
+    assert outs[0].stdout.strip().splitlines()[-1] == outs[1].stdout.strip().splitlines()[-1]
