@@ -442,7 +442,8 @@ typedef struct {
 typedef struct {
   qtt_prec prec;        /* arithmetic of the iteration                                    */
   double eps;           /* rounding tolerance of every step                               */
-  double op_tol;        /* tolerance of the operator trains (phase, Green)               */
+  double op_tol;        /* tolerance of the operator trains (phase, Green); float paths
+                           with op_tol >= 1e-7 build them in float (ms_setup)             */
   int32_t max_iter;
   int32_t oversample;   /* sketch width = max_rank + oversample                           */
   int32_t load_mask;    /* bit k set: solve load case E = e_k (column k of C_eff)        */
@@ -523,7 +524,11 @@ QTT_API int ms_homogenize(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, do
  * solves (precisions, tolerances, load cases):
  *  ms_setup builds the trains of `rve` and C0 (what ms_homogenize does before
  *  its iterations; op_tol as opts->op_tol), on ctx's stream, and returns a
- *  handle owning them; the host arrays of `rve` are not kept.
+ *  handle owning them; the host arrays of `rve` are not kept.  op_prec
+ *  QTT_PREC_F64: every factorisation in FP64; QTT_PREC_F32 (op_tol >= 1e-7
+ *  only, else QTT_ERR_ARG): the dense TT-SVDs (phase image, Green
+ *  operator) in complex64, the TT-cross samplings in FP64.  ms_homogenize
+ *  itself takes QTT_PREC_F32 for the float paths when opts->op_tol >= 1e-7.
  *  ms_homogenize_ops runs the iterations of ms_homogenize on a handle, on
  *  any context of the same device (the trains are only read);
  *  report->setup_ms is 0 there.
@@ -532,7 +537,8 @@ QTT_API int ms_homogenize(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, do
  *  the Green operator and phase trains.  Not in the paper as an interface;
  *  the paper builds the operators once per RVE as well (Sec. 3.2). */
 typedef struct ms_ops ms_ops;
-QTT_API int ms_setup(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, double op_tol, ms_ops** out);
+QTT_API int ms_setup(qtt_ctx* ctx, const qtt_rve* rve, const double* C0, double op_tol, qtt_prec op_prec,
+                     ms_ops** out);
 QTT_API int ms_homogenize_ops(qtt_ctx* ctx, const ms_ops* ops, double tol, int max_rank, const ms_opts* opts,
                               double* C_eff, ms_report* report);
 QTT_API void ms_ops_destroy(ms_ops* ops);

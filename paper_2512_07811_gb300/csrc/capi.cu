@@ -969,8 +969,11 @@ static SiteMap site_map(const qtt_rve* rve) {
   return site_map_bits(nb, rve->interleaved != 0);
 }
 
+// f32: the dense TT-SVDs (phase image, Green operator) in complex64 (the
+// trains are then stored widened to complex128 like the others); the
+// TT-cross and the SFFT stay in FP64.
 int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2, const double* C0, double op_tol,
-              double k0, double lam0, double mu0, Ops* ops) {
+              double k0, double lam0, double mu0, Ops* ops, bool f32 = false) {
   const SiteMap sm = site_map(rve);
   const int nc = rve->ncomp, dsp = sm.d, d = dsp + 1;
   const int64_t Nv = (int64_t)1 << dsp;
@@ -987,15 +990,26 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
     void *ind = nullptr, *dense = nullptr;
     TRY(dalloc(c, &ind, Nv * sizeof(double)));
     s = upload(c, ind, rve->indicator, Nv * sizeof(double));
-    if (!s) s = dalloc(c, &dense, (size_t)Nv * sizeof(zc));
+    if (!s) s = dalloc(c, &dense, (size_t)Nv * (f32 ? sizeof(cc) : sizeof(zc)));
     if (!s) {
       c->launches++;
-      s = qtt_fill_indicator_sites<double>(reinterpret_cast<double*>(ind), sm, reinterpret_cast<zc*>(dense),
-                                           c->stream);
+      s = f32 ? qtt_fill_indicator_sites<float>(reinterpret_cast<double*>(ind), sm, reinterpret_cast<cc*>(dense),
+                                                c->stream)
+              : qtt_fill_indicator_sites<double>(reinterpret_cast<double*>(ind), sm, reinterpret_cast<zc*>(dense),
+                                                 c->stream);
     }
-    if (!s)
-      s = tt_svd_dev<double>(c, dsp, std::vector<int>(dsp, 2), reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128,
-                             &ops->chi);
+    if (!s) {
+      if (f32) {
+        qtt_tt* chi32 = nullptr;
+        s = tt_svd_dev<float>(c, dsp, std::vector<int>(dsp, 2), reinterpret_cast<cc*>(dense), op_tol, 0, QTT_C64,
+                              &chi32);
+        if (!s) s = convert_tt(c, chi32, QTT_C128, &ops->chi);
+        tt_free(chi32);
+      } else {
+        s = tt_svd_dev<double>(c, dsp, std::vector<int>(dsp, 2), reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128,
+                               &ops->chi);
+      }
+    }
     dfree(c, ind);
     dfree(c, dense);
     if (s) return s;
@@ -1029,10 +1043,18 @@ int build_ops(qtt_ctx* c, const qtt_rve* rve, const double* C1, const double* C2
   gmodes[0] = nc * nc;
   if (green_dense_ok(rve, dsp)) {
     void* dense = nullptr;
-    TRY(dalloc(c, &dense, (size_t)Nv * nc * nc * sizeof(zc)));
+    TRY(dalloc(c, &dense, (size_t)Nv * nc * nc * (f32 ? sizeof(cc) : sizeof(zc))));
     c->launches++;
-    s = qtt_fill_green_dense<double>(reinterpret_cast<zc*>(dense), sm, nc, k0, lam0, mu0, c->stream);
-    if (!s) s = tt_svd_dev<double>(c, d, gmodes, reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128, &g);
+    if (f32) {
+      s = qtt_fill_green_dense<float>(reinterpret_cast<cc*>(dense), sm, nc, k0, lam0, mu0, c->stream);
+      qtt_tt* g32 = nullptr;
+      if (!s) s = tt_svd_dev<float>(c, d, gmodes, reinterpret_cast<cc*>(dense), op_tol, 0, QTT_C64, &g32);
+      if (!s) s = convert_tt(c, g32, QTT_C128, &g);
+      tt_free(g32);
+    } else {
+      s = qtt_fill_green_dense<double>(reinterpret_cast<zc*>(dense), sm, nc, k0, lam0, mu0, c->stream);
+      if (!s) s = tt_svd_dev<double>(c, d, gmodes, reinterpret_cast<zc*>(dense), op_tol, 0, QTT_C128, &g);
+    }
     dfree(c, dense);
     if (s) return s;
   } else {
@@ -1832,8 +1854,11 @@ struct ms_ops {
   int64_t setup_launches = 0;
 };
 
-extern "C" int ms_setup(qtt_ctx* c, const qtt_rve* rve, const double* C0, double op_tol, ms_ops** out) {
+extern "C" int ms_setup(qtt_ctx* c, const qtt_rve* rve, const double* C0, double op_tol, qtt_prec op_prec,
+                        ms_ops** out) {
   if (!c || !rve || !C0 || !out) return QTT_ERR_ARG;
+  if (op_prec != QTT_PREC_F64 && op_prec != QTT_PREC_F32) return QTT_ERR_ARG;
+  if (op_prec == QTT_PREC_F32 && !(op_tol >= 1e-7)) return QTT_ERR_ARG;
   *out = nullptr;
   if ((rve->ncomp != 3 && rve->ncomp != 6) || !rve_bits_valid(rve)) return QTT_ERR_ARG;
   ms_ops* m = new (std::nothrow) ms_ops();
@@ -1871,7 +1896,7 @@ extern "C" int ms_setup(qtt_ctx* c, const qtt_rve* rve, const double* C0, double
   const int64_t l0 = c->launches;
   auto t0 = std::chrono::steady_clock::now();
   int s = build_ops(c, rve, m->C1.data(), m->C2.data(), C0, op_tol > 0 ? op_tol : 1e-10, m->k0, m->lam0, m->mu0,
-                    &m->O);
+                    &m->O, op_prec == QTT_PREC_F32);
   if (!s && cudaStreamSynchronize(c->stream) != cudaSuccess) s = QTT_ERR_CUDA;
   if (s) {
     m->O.release();
@@ -2034,7 +2059,10 @@ extern "C" int ms_homogenize(qtt_ctx* c, const qtt_rve* rve, const double* C0, d
   if (o->prec != QTT_PREC_F64 && o->prec != QTT_PREC_F32 && o->prec != QTT_PREC_TC32 && o->prec != QTT_PREC_TF32S)
     return QTT_ERR_ARG;
   ms_ops* m = nullptr;
-  int s = ms_setup(c, rve, C0, o->op_tol, &m);
+  // the float paths build their operator trains in float when the operator
+  // tolerance is one float can represent
+  const qtt_prec op_prec = o->prec != QTT_PREC_F64 && o->op_tol >= 1e-7 ? QTT_PREC_F32 : QTT_PREC_F64;
+  int s = ms_setup(c, rve, C0, o->op_tol, op_prec, &m);
   if (s) return s;
   s = ms_homogenize_ops(c, m, tol, max_rank, o, C_eff, rep);
   if (rep) {
@@ -2091,7 +2119,8 @@ extern "C" int ms_homogenize_batch(qtt_ctx* c, int n, const qtt_rve* rves, const
     for (;;) {
       const size_t i = next++;
       if (i >= (size_t)n || status.load() != QTT_OK) break;
-      int st = ms_setup(wcs[w], &rves[i], C0s + i * 36, o->op_tol, &ops[i]);
+      const qtt_prec op_prec = o->prec != QTT_PREC_F64 && o->op_tol >= 1e-7 ? QTT_PREC_F32 : QTT_PREC_F64;
+      int st = ms_setup(wcs[w], &rves[i], C0s + i * 36, o->op_tol, op_prec, &ops[i]);
       if (st) status = st;
     }
   };

@@ -1357,6 +1357,7 @@ int tt_svd_dev(qtt_ctx* c, int d, const std::vector<int>& modes, const cplx<R>* 
 }
 
 template int tt_svd_dev<double>(qtt_ctx*, int, const std::vector<int>&, const zc*, double, int, qtt_dtype, qtt_tt**);
+template int tt_svd_dev<float>(qtt_ctx*, int, const std::vector<int>&, const cc*, double, int, qtt_dtype, qtt_tt**);
 template int left_svd<double>(qtt_ctx*, const zc*, int64_t, int64_t, int64_t, zc*, double*, int64_t*);
 template int left_svd<float>(qtt_ctx*, const cc*, int64_t, int64_t, int64_t, cc*, float*, int64_t*);
 

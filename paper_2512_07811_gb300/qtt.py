@@ -212,7 +212,7 @@ _sig("tt_cross", C.c_int, [_P, C.POINTER(CrossFn), C.c_double, C.c_int32, C.c_in
                           C.POINTER(_P), C.POINTER(CrossInfo)])
 _sig("ms_homogenize", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int,
                                 C.POINTER(MSOpts), C.POINTER(C.c_double), C.POINTER(MSReport)])
-_sig("ms_setup", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.POINTER(_P)])
+_sig("ms_setup", C.c_int, [_P, C.POINTER(RVE), C.POINTER(C.c_double), C.c_double, C.c_int, C.POINTER(_P)])
 _sig("ms_homogenize_ops", C.c_int, [_P, _P, C.c_double, C.c_int, C.POINTER(MSOpts), C.POINTER(C.c_double),
                                     C.POINTER(MSReport)])
 _sig("ms_ops_destroy", None, [_P])
@@ -798,9 +798,10 @@ class MSOps:
 
 
 def ms_setup(ctx: Context, indicator, kind: str, moduli, C0, op_tol: float = 1e-10, interleaved: bool = True,
-             op_cross: bool = False) -> MSOps:
+             op_cross: bool = False, op_prec: int = PREC_F64) -> MSOps:
     """Operator trains of an RVE (the setup of ms_homogenize) as a handle that
-    ms_homogenize(..., ops=handle) reuses; same arguments as ms_homogenize."""
+    ms_homogenize(..., ops=handle) reuses; same arguments as ms_homogenize,
+    op_prec PREC_F32 (op_tol >= 1e-7) for the dense TT-SVDs in float."""
     import time as _time
     rve, keep = _rve(indicator, kind, moduli, interleaved, op_cross)
     nc = rve.ncomp
@@ -808,7 +809,7 @@ def ms_setup(ctx: Context, indicator, kind: str, moduli, C0, op_tol: float = 1e-
     h = _P()
     t0 = _time.perf_counter()
     _check(_lib.ms_setup(ctx.h, C.byref(rve), C0a.ctypes.data_as(C.POINTER(C.c_double)), float(op_tol),
-                         C.byref(h)), "ms_setup")
+                         int(op_prec), C.byref(h)), "ms_setup")
     return MSOps(ctx, h, nc, (_time.perf_counter() - t0) * 1e3)
 
 

@@ -147,3 +147,20 @@ def test_tf32_sketch_path_elastic_sphere_within_1e4_of_fp64(Q, ctx):
     rel = np.linalg.norm(Ct[:, 0] - C64[:, 0]) / np.linalg.norm(C64[:, 0])
     print("\nelastic sphere 16^3: tensor-core sketch path vs FP64 %.2e (%d iterations)" % (rel, rt.iterations[0]))
     assert rt.iterations[0] < 200 and rel < 1e-4
+
+
+def test_float_setup_elastic_sphere_within_1e4_of_fp64(Q, ctx):
+    """The float path with its operator trains built in float (operator
+    tolerance 1e-6: the dense Green-operator TT-SVD in complex64): C_eff of
+    the 16^3 sphere within 1e-4 of the FP64 path with FP64 operators."""
+    N = 16
+    C0 = MS.iso_voigt(0.5 * (LAM1 + LAM2), 0.5 * (MU1 + MU2))
+    geo = Q.Ellipsoids(I.sphere_rows(0.2), (N, N, N))
+    kw = dict(load_mask=0b1, interleaved=False, max_iter=200, max_rank=512)
+    C64, _ = Q.ms_homogenize(ctx, geo, "elastic", (LAM1, MU1, LAM2, MU2), C0, tol=1e-8, eps=1e-9,
+                             prec=Q.PREC_F64, **kw)
+    Cf, rf = Q.ms_homogenize(ctx, geo, "elastic", (LAM1, MU1, LAM2, MU2), C0, tol=5e-5, eps=1e-6,
+                             op_tol=1e-6, prec=Q.PREC_F32, **kw)
+    rel = np.linalg.norm(Cf[:, 0] - C64[:, 0]) / np.linalg.norm(C64[:, 0])
+    print("\nelastic sphere 16^3, float operators: vs FP64 %.2e (setup %.0f ms)" % (rel, rf.setup_ms))
+    assert rf.iterations[0] < 200 and rel < 1e-4
