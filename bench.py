@@ -544,6 +544,7 @@ def run_ours(args, world, local_rank):
     props = torch.cuda.get_device_properties(local_rank)
     fast_prec = {"f32": Q.PREC_F32, "tc32": Q.PREC_TC32, "tf32s": Q.PREC_TF32S}[args.prec]
     peaks = {"fp32_tflops": ctx.measure_peak("fp32"), "fp64_tflops": ctx.measure_peak("fp64"),
+             "tf32_mma_tflops": ctx.measure_peak("tf32"), "bf16_mma_tflops": ctx.measure_peak("bf16"),
              "sms": props.multi_processor_count}
 
     # the operator trains once (ms_setup); a warm-up solve (GEMM tile tuning,
@@ -682,10 +683,11 @@ def profile_region(args):
     ctx = Q.Context(0, stream.cuda_stream)
     geo, moduli, C0 = sphere_geometry(Q, args.n)
     ops = Q.ms_setup(ctx, geo, "elastic", moduli, C0, op_tol=1e-10, interleaved=False)
-    sphere_solve(Q, ctx, args.n, Q.PREC_F32, 1, 1, ops)
+    prec = {"f32": Q.PREC_F32, "tc32": Q.PREC_TC32, "tf32s": Q.PREC_TF32S}[args.prec]
+    sphere_solve(Q, ctx, args.n, prec, 1, 1, ops)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStart()
-    C, rep, wall = sphere_solve(Q, ctx, args.n, Q.PREC_F32, 0, args.steps, ops)
+    C, rep, wall = sphere_solve(Q, ctx, args.n, prec, 0, args.steps, ops)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
     print(json.dumps({"profile_region": "elastic sphere %d^3, %d iterations of 6 load cases" % (1 << args.n,

@@ -118,13 +118,18 @@ QTT_API int qtt_ctx_profile_read(qtt_ctx* ctx, int kclass, double* total_ms, int
 QTT_API int qtt_ctx_fail_alloc_after(qtt_ctx* ctx, int64_t n);
 
 /* Arithmetic peak of the context's GPU in TFLOP/s, measured by the
- * library's own kernel (not in the paper; the rooflines of the float and
- * FP64 kernels are quoted against it): a full grid of independent
- * fused-multiply-add chains (two flops each), best of five timed launches
- * on the context stream.  which: QTT_PEAK_FP32_FMA or QTT_PEAK_FP64_FMA.
- * Synchronises the stream; QTT_ERR_ARG for another `which`. */
+ * library's own kernels (not in the paper; the rooflines are quoted against
+ * them): QTT_PEAK_FP32_FMA / QTT_PEAK_FP64_FMA, a full grid of independent
+ * fused-multiply-add chains (two flops each), best of five timed launches;
+ * QTT_PEAK_TF32_MMA / QTT_PEAK_BF16_MMA, one CTA per SM issuing tcgen05.mma
+ * (M 128, N 256, FP32 accumulation in tensor memory) from operand tiles held
+ * in shared memory, best of three, no loads (the tensor pipe's issue rate).
+ * Synchronises the stream; QTT_ERR_ARG for another `which`, QTT_ERR_TIMEOUT
+ * if a bounded wait gave up. */
 #define QTT_PEAK_FP32_FMA 0
 #define QTT_PEAK_FP64_FMA 1
+#define QTT_PEAK_TF32_MMA 2
+#define QTT_PEAK_BF16_MMA 3
 QTT_API int qtt_measure_peak(qtt_ctx* ctx, int which, double* tflops);
 
 /* --------------------------------------------------------------- trains */

@@ -297,9 +297,11 @@ class Context:
         _check(_lib.qtt_ctx_fail_alloc_after(self.h, int(n)), "qtt_ctx_fail_alloc_after")
 
     def measure_peak(self, which: str) -> float:
-        """FP32 ("fp32") or FP64 ("fp64") fused-multiply-add peak of this GPU in TFLOP/s."""
+        """Peak of this GPU in TFLOP/s: FMA chains ("fp32", "fp64") or tcgen05
+        MMAs from shared memory ("tf32", "bf16")."""
         out = C.c_double()
-        _check(_lib.qtt_measure_peak(self.h, {"fp32": 0, "fp64": 1}[which], C.byref(out)), "qtt_measure_peak")
+        _check(_lib.qtt_measure_peak(self.h, {"fp32": 0, "fp64": 1, "tf32": 2, "bf16": 3}[which], C.byref(out)),
+               "qtt_measure_peak")
         return float(out.value)
 
     KERNEL_CLASSES = {"gemm": 0, "qr": 1, "jacobi": 2, "elem": 3}
