@@ -216,12 +216,18 @@ def tt_ops_sweep(Q, torch, ctx, stream, flush, ranks, fp64_max_rank, prec32):
     before every timed call, one warm-up call, then 3 timed calls (2 for
     r >= 128): add + SVD rounding, Hadamard + sketched rounding (width
     r + 8, cap r), 30-bit SFFT application + sketched rounding, inner
-    product.  "tt_round TFLOP/s" = the shared flop model / time."""
+    product.  "tt_round TFLOP/s" = the shared flop model / time.  Arithmetic:
+    float CUDA cores (fp32), FP64 up to fp64_max_rank, and from r = 64 the
+    float path with every large contraction on the tensor cores (tc32:
+    tcgen05 kind::tf32, three-term split; single-pass TF32 and BF16 are not
+    accurate enough for roundings at eps 1e-6)."""
     out = {}
     qft = Q.qtt_qft_mpo(ctx, D, -1, 1e-12)
     for r in ranks:
-        for name, dt, prec in [("fp32", Q.C64, prec32), ("fp64", Q.C128, Q.PREC_F64)]:
+        for name, dt, prec in [("fp32", Q.C64, prec32), ("fp64", Q.C128, Q.PREC_F64), ("tc32", Q.C64, Q.PREC_TC32)]:
             if name == "fp64" and r > fp64_max_rank:
+                continue
+            if name == "tc32" and r < 64:
                 continue
             xc = I.random_tt_cores(D, 2, r, seed=1000 + r, dtype=np.complex128)
             yc = I.random_tt_cores(D, 2, r, seed=1001 + r, dtype=np.complex128)
