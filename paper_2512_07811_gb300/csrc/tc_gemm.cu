@@ -57,67 +57,113 @@ __device__ __forceinline__ float split_part(float x) {
   return PART_LO ? to_tf32(x - hi) : hi;
 }
 
-__global__ void pack_a_kernel(const cc* __restrict__ A, GemmDesc g, int64_t K3p, float* __restrict__ A3, int64_t Mp,
-                              int passes) {
-  const int64_t K = g.K;
-  const int64_t per = Mp * K3p, total = per * g.batch;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / per, r = e - b * per;
-    int64_t m = r / K3p, col = r - m * K3p;
-    float v = 0.f;
-    if (m < g.M && col < (passes == 3 ? 6 : 2) * K) {
-      int part = (int)(col / (2 * K));
-      int64_t c = col - part * 2 * K;
-      int64_t k = c < K ? c : c - K;
-      cc a = A[midx_off(g.bA, b) + midx_off(g.mA, m) + midx_off(g.kA, k)];
-      if (g.conjA) a.im = -a.im;
-      float x = c < K ? a.re : a.im;
-      v = part == 2 ? split_part<1>(x) : split_part<0>(x);
+// Packing and unpacking move one 32 x 32 tile of complex values per CTA
+// (32 x 8 threads) through shared memory: the reads run along whichever index
+// of the source is contiguous, the writes along the packed rows, so both are
+// coalesced; the element offsets of the tile's 32 rows and 32 K values are
+// computed once per CTA.  The packed buffers are zeroed beforehand, so only
+// the valid entries are written.
+constexpr int PT = 32;
+
+// A3 row m of batch entry b: [part 0: Re | Im (hi)] [part 1: the same] [part 2: Re | Im (lo)]
+// (passes 3; passes 1: part 0 only), each half K wide.  B3 rows n and N + n:
+// [Br | -Bi] and [Bi | Br] with parts (hi, lo, hi).
+template <int IS_B>
+__global__ void __launch_bounds__(256) pack_tile_kernel(const cc* __restrict__ src, MIdx bI, MIdx rI, MIdx kI,
+                                                         int conj, int64_t R, int64_t K, int64_t rows_out,
+                                                         int64_t K3p, int passes, int r_contig,
+                                                         float* __restrict__ out) {
+  __shared__ cc tile[PT][PT + 1];
+  __shared__ int64_t roff[PT], koff[PT];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * PT + tx;
+  const int64_t k0 = (int64_t)blockIdx.x * PT, b = blockIdx.z, base = midx_off(bI, b);
+  if (tid < PT) koff[tid] = k0 + tid < K ? midx_off(kI, k0 + tid) : -1;
+  // row tiles grid-stride over y (the loop bounds are the same for the whole CTA)
+  for (int64_t r0 = (int64_t)blockIdx.y * PT; r0 < R; r0 += (int64_t)gridDim.y * PT) {
+    __syncthreads();
+    if (tid >= PT && tid < 2 * PT) roff[tid - PT] = r0 + tid - PT < R ? midx_off(rI, r0 + tid - PT) : -1;
+    __syncthreads();
+    for (int i = ty; i < PT; i += 8) {
+      const int rr = r_contig ? tx : i, kk = r_contig ? i : tx;
+      cc v(0.f, 0.f);
+      if (roff[rr] >= 0 && koff[kk] >= 0) {
+        v = src[base + roff[rr] + koff[kk]];
+        if (conj) v.im = -v.im;
+      }
+      tile[rr][kk] = v;
     }
-    A3[e] = v;
+    __syncthreads();
+    const int64_t k = k0 + tx;
+    if (k >= K) continue;
+    for (int i = ty; i < PT; i += 8) {
+      const int64_t r = r0 + i;
+      if (r >= R) break;
+      const cc v = tile[i][tx];
+      if (!IS_B) {
+        float* row = out + (b * rows_out + r) * K3p;
+        const float hr = split_part<0>(v.re), hi = split_part<0>(v.im);
+        row[k] = hr;
+        row[K + k] = hi;
+        if (passes == 3) {
+          row[2 * K + k] = hr;
+          row[3 * K + k] = hi;
+          row[4 * K + k] = split_part<1>(v.re);
+          row[5 * K + k] = split_part<1>(v.im);
+        }
+      } else {
+        float* rn = out + (b * rows_out + r) * K3p;      // [Br | -Bi]
+        float* rm = out + (b * rows_out + R + r) * K3p;  // [Bi |  Br]
+        const float hr = split_part<0>(v.re), hi = split_part<0>(v.im), hmi = split_part<0>(-v.im);
+        rn[k] = hr;
+        rn[K + k] = hmi;
+        rm[k] = hi;
+        rm[K + k] = hr;
+        if (passes == 3) {
+          const float lr = split_part<1>(v.re), li = split_part<1>(v.im), lmi = split_part<1>(-v.im);
+          rn[2 * K + k] = lr;
+          rn[3 * K + k] = lmi;
+          rm[2 * K + k] = li;
+          rm[3 * K + k] = lr;
+          rn[4 * K + k] = hr;
+          rn[5 * K + k] = hmi;
+          rm[4 * K + k] = hi;
+          rm[5 * K + k] = hr;
+        }
+      }
+    }
   }
 }
 
-// B3 row j (j < Np): n = j mod N, half = j / N; K-columns as for A with parts (hi, lo, hi)
-__global__ void pack_b_kernel(const cc* __restrict__ B, GemmDesc g, int64_t K3p, float* __restrict__ B3, int64_t Np,
-                              int passes) {
-  const int64_t K = g.K, N = g.N;
-  const int64_t per = Np * K3p, total = per * g.batch;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t bt = e / per, r = e - bt * per;
-    int64_t j = r / K3p, col = r - j * K3p;
-    float v = 0.f;
-    if (j < 2 * N && col < (passes == 3 ? 6 : 2) * K) {
-      int part = (int)(col / (2 * K));
-      int64_t c = col - part * 2 * K;
-      int64_t n = j < N ? j : j - N;
-      int64_t k = c < K ? c : c - K;
-      cc b = B[midx_off(g.bB, bt) + midx_off(g.kB, k) + midx_off(g.nB, n)];
-      if (g.conjB) b.im = -b.im;
-      float x;
-      if (j < N) x = c < K ? b.re : -b.im;  // row n:   [Br | -Bi]
-      else x = c < K ? b.im : b.re;         // row N+n: [Bi |  Br]
-      v = part == 1 ? split_part<1>(x) : split_part<0>(x);
-    }
-    B3[e] = v;
-  }
-}
-
-// C[m, n] = alpha (C3[m, n] + i C3[m, N + n]) + beta C[m, n], batch entry by
-// batch entry (C3 entries at a stride of c3_batch floats)
-__global__ void unpack_c_kernel(const float* __restrict__ C3, int64_t ldc3, int64_t c3_batch, GemmDesc g, cc alpha,
-                                cc beta, cc* __restrict__ C) {
-  const int64_t per = g.M * g.N, total = per * g.batch;
+// C[m, n] = alpha (C3[m, n] + i C3[m, N + n]) + beta C[m, n], one 32 x 32
+// tile per CTA step: C3 read along n, C written along its contiguous index
+__global__ void __launch_bounds__(256) unpack_tile_kernel(const float* __restrict__ C3, int64_t ldc3,
+                                                           int64_t c3_batch, GemmDesc g, cc alpha, cc beta,
+                                                           int m_contig, cc* __restrict__ C) {
+  __shared__ cc tile[PT][PT + 1];
+  __shared__ int64_t moff[PT], noff[PT];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * PT + tx;
+  const int64_t n0 = (int64_t)blockIdx.x * PT, b = blockIdx.z, base = midx_off(g.bC, b);
+  if (tid < PT) noff[tid] = n0 + tid < g.N ? midx_off(g.nC, n0 + tid) : -1;
+  const float* c3 = C3 + b * c3_batch;
   const bool use_beta = beta.re != 0.f || beta.im != 0.f;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / per, rr = e - b * per;
-    int64_t m = rr / g.N, n = rr - m * g.N;
-    const float* c3 = C3 + b * c3_batch;
-    cc v(c3[m * ldc3 + n], c3[m * ldc3 + g.N + n]);
-    int64_t o = midx_off(g.bC, b) + midx_off(g.mC, m) + midx_off(g.nC, n);
-    cc r = alpha * v;
-    if (use_beta) r = r + beta * C[o];
-    C[o] = r;
+  for (int64_t m0 = (int64_t)blockIdx.y * PT; m0 < g.M; m0 += (int64_t)gridDim.y * PT) {
+    __syncthreads();
+    if (tid >= PT && tid < 2 * PT) moff[tid - PT] = m0 + tid - PT < g.M ? midx_off(g.mC, m0 + tid - PT) : -1;
+    for (int i = ty; i < PT; i += 8) {
+      const int64_t m = m0 + i, n = n0 + tx;
+      cc v(0.f, 0.f);
+      if (m < g.M && n < g.N) v = cc(c3[m * ldc3 + n], c3[m * ldc3 + g.N + n]);
+      tile[i][tx] = v;
+    }
+    __syncthreads();
+    for (int i = ty; i < PT; i += 8) {
+      const int mm = m_contig ? tx : i, nn = m_contig ? i : tx;
+      if (moff[mm] < 0 || noff[nn] < 0) continue;
+      const int64_t o = base + moff[mm] + noff[nn];
+      cc r = alpha * tile[mm][nn];
+      if (use_beta) r = r + beta * C[o];
+      C[o] = r;
+    }
   }
 }
 
@@ -339,7 +385,8 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-inline unsigned grid1d(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 65535 * 8); }
+// grid.y of the tile kernels: one CTA per 32 rows, at most 65535 (the kernels loop over the rest)
+inline unsigned tiles_y(int64_t rows) { return (unsigned)std::min<int64_t>((rows + PT - 1) / PT, 65535); }
 
 }  // namespace
 
@@ -362,6 +409,7 @@ size_t qtt_tc_gemm_workspace(int64_t M, int64_t N, int64_t K) { return qtt_tc_ge
 int qtt_tc_gemm_ex(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* B, cc* C, void* ws, int* err,
                    cudaStream_t s, int passes) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0 || g.batch > 65535) return QTT_ERR_ARG;
+  if ((g.M + TBM - 1) / TBM > 65535 || (g.K + PT - 1) / PT > INT32_MAX) return QTT_ERR_ARG;
   if (passes != 1 && passes != 3) return QTT_ERR_ARG;
   const int64_t Mp = (g.M + TBM - 1) / TBM * TBM;
   const int64_t Np = (2 * g.N + TBN - 1) / TBN * TBN;
@@ -372,15 +420,30 @@ int qtt_tc_gemm_ex(const GemmDesc& g, cc alpha, cc beta, const cc* A, const cc* 
   float* B3 = reinterpret_cast<float*>(p);
   p = (reinterpret_cast<uintptr_t>(B3 + g.batch * Np * K3p) + 1023) & ~(uintptr_t)1023;
   float* C3 = reinterpret_cast<float*>(p);
-  pack_a_kernel<<<grid1d(g.batch * Mp * K3p), 256, 0, s>>>(A, g, K3p, A3, Mp, passes);
-  pack_b_kernel<<<grid1d(g.batch * Np * K3p), 256, 0, s>>>(B, g, K3p, B3, Np, passes);
+  if (cudaMemsetAsync(A3, 0, (size_t)g.batch * Mp * K3p * sizeof(float), s) != cudaSuccess ||
+      cudaMemsetAsync(B3, 0, (size_t)g.batch * Np * K3p * sizeof(float), s) != cudaSuccess)
+    return QTT_ERR_CUDA;
+  const auto unit = [](const MIdx& m) { return (m.n2 == 1 ? m.s1 : m.s2) == 1; };
+  {
+    dim3 blk(PT, 8), grd((unsigned)((g.K + PT - 1) / PT), tiles_y(g.M), (unsigned)g.batch);
+    pack_tile_kernel<0><<<grd, blk, 0, s>>>(A, g.bA, g.mA, g.kA, g.conjA, g.M, g.K, Mp, K3p, passes,
+                                            unit(g.mA) && !unit(g.kA) ? 1 : 0, A3);
+  }
+  {
+    dim3 blk(PT, 8), grd((unsigned)((g.K + PT - 1) / PT), tiles_y(g.N), (unsigned)g.batch);
+    pack_tile_kernel<1><<<grd, blk, 0, s>>>(B, g.bB, g.nB, g.kB, g.conjB, g.N, g.K, Np, K3p, passes,
+                                            unit(g.nB) && !unit(g.kB) ? 1 : 0, B3);
+  }
   CUtensorMap ma, mb;
   if (!make_map(&ma, A3, Mp, K3p, g.batch) || !make_map(&mb, B3, Np, K3p, g.batch)) return QTT_ERR_CUDA;
   const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
   if (qtt_allow_max_smem((const void*)tc_gemm_kernel) != QTT_OK) return QTT_ERR_CUDA;
   dim3 grid((unsigned)(Np / TBN), (unsigned)(Mp / TBM), (unsigned)g.batch);
   tc_gemm_kernel<<<grid, 128, smem, s>>>(ma, mb, C3, Np, Mp * Np, (int)(K3p / TBK), err);
-  unpack_c_kernel<<<grid1d(g.batch * g.M * g.N), 256, 0, s>>>(C3, Np, Mp * Np, g, alpha, beta, C);
+  {
+    dim3 blk(PT, 8), grd((unsigned)((g.N + PT - 1) / PT), tiles_y(g.M), (unsigned)g.batch);
+    unpack_tile_kernel<<<grd, blk, 0, s>>>(C3, Np, Mp * Np, g, alpha, beta, unit(g.mC) && !unit(g.nC) ? 1 : 0, C);
+  }
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
 
