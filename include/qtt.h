@@ -110,6 +110,18 @@ QTT_API int qtt_ctx_profile(qtt_ctx* ctx, int enable);
  * kernel ran) and model bytes.  Synchronises the stream. */
 QTT_API int qtt_ctx_profile_read(qtt_ctx* ctx, int kclass, double* total_ms, int64_t* launches, double* flops,
                                  double* bytes);
+/* The same records of one kernel class grouped by launch shape, this
+ * context's own launches only (not those of ms_homogenize's load-case
+ * workers: profile a solve with lc_workers = 1 to see its shapes).  Writes up
+ * to `max_rows` rows of 8 doubles to `rows` (host, caller-owned, 8 *
+ * max_rows), by decreasing total time: d0, d1, d2, batch, variant, launches,
+ * total ms, model flops -- GEMM: M, N, K, batch and variant = tile edge x 100
+ * + split-K count (tile edge 128: the tensor-core kernel, + its TF32
+ * passes); QR: m, n, 0, batch, variant 1 when the explicit Q was formed;
+ * Jacobi: rows p, columns q, 0, batch, 0.  *n_rows = the number of distinct
+ * shapes (may exceed max_rows).  Synchronises the stream.  QTT_ERR_ARG on a
+ * bad class or null pointers. */
+QTT_API int qtt_ctx_profile_shapes(qtt_ctx* ctx, int kclass, double* rows, int64_t max_rows, int64_t* n_rows);
 /* Failure injection for tests of the error paths (not in the paper): after
  * `n` more successful device allocations of this context, every allocation
  * fails as if the device were out of memory, so the call in progress

@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <chrono>
 #include <vector>
 
@@ -353,6 +355,39 @@ int qtt_ctx_profile_read(qtt_ctx* c, int kclass, double* total_ms, int64_t* laun
   if (launches) *launches = n;
   if (flops) *flops = fl;
   if (bytes) *bytes = by;
+  return QTT_OK;
+}
+
+int qtt_ctx_profile_shapes(qtt_ctx* c, int kclass, double* rows, int64_t max_rows, int64_t* n_rows) {
+  if (!c || kclass < 0 || kclass >= PK_N || max_rows < 0 || (max_rows > 0 && !rows) || !n_rows) return QTT_ERR_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return QTT_ERR_CUDA;
+  std::vector<int> sw(c->sweeps_used, 0);
+  if (c->sweeps_used)
+    cudaMemcpy(sw.data(), c->d_sweeps, c->sweeps_used * sizeof(int), cudaMemcpyDeviceToHost);
+  struct Agg {
+    int64_t launches = 0;
+    double ms = 0, flops = 0;
+  };
+  std::map<std::array<int64_t, 5>, Agg> agg;
+  for (auto& r : c->recs) {
+    if (r.cls != kclass) continue;
+    float e = 0;
+    cudaEventElapsedTime(&e, r.a, r.b);
+    Agg& a = agg[{r.shape[0], r.shape[1], r.shape[2], r.shape[3], (int64_t)r.variant}];
+    a.launches++;
+    a.ms += e;
+    a.flops += r.flops + (r.sweep_idx >= 0 ? r.per_sweep * std::max(1, sw[r.sweep_idx]) : 0.0);
+  }
+  std::vector<std::pair<std::array<int64_t, 5>, Agg>> v(agg.begin(), agg.end());
+  std::stable_sort(v.begin(), v.end(), [](const auto& x, const auto& y) { return x.second.ms > y.second.ms; });
+  *n_rows = (int64_t)v.size();
+  for (int64_t i = 0; i < std::min<int64_t>(max_rows, (int64_t)v.size()); ++i) {
+    double* o = rows + 8 * i;
+    for (int j = 0; j < 5; ++j) o[j] = (double)v[i].first[j];
+    o[5] = (double)v[i].second.launches;
+    o[6] = v[i].second.ms;
+    o[7] = v[i].second.flops;
+  }
   return QTT_OK;
 }
 

@@ -186,6 +186,7 @@ static int tc_route(qtt_ctx* c, const GemmDesc& g0, cc alpha, cc beta, const cc*
                         ws, c->d_tcerr, c->stream, passes);
     prof_end(c, ev, PK_GEMM, 8.0 * g.M * g.N * g.K * part.batch,
              (double)(g.M * g.K + g.K * g.N + g.M * g.N) * part.batch * sizeof(cc));
+    prof_shape(c, ev, g.M, g.N, g.K, part.batch, 128 * 100 + passes);
   }
   dfree(c, ws);
   return st;
@@ -285,6 +286,7 @@ static int simt_gemm(qtt_ctx* c, const GemmDesc& g, cplx<R> alpha, cplx<R> beta,
   int st = qtt_gemm_ex<R>(g, alpha, beta, A, B, C, splits, reinterpret_cast<cplx<R>*>(P), c->stream, tile);
   prof_end(c, ev, PK_GEMM, 8.0 * g.M * g.N * g.K * g.batch,
            (double)(g.M * g.K + g.K * g.N + g.M * g.N) * g.batch * sizeof(cplx<R>));
+  prof_shape(c, ev, g.M, g.N, g.K, g.batch, (tile ? tile : qtt_gemm_tile_rule(g)) * 100 + splits);
   dfree(c, P);
   return st;
 }
@@ -404,6 +406,7 @@ static int qr_launch(qtt_ctx* c, const cplx<R>* in, MIdx inB, MIdx rowI, MIdx co
   dfree(c, qws);
   prof_end(c, ev, PK_QR, batch * qr_flops((double)m, (double)n, Qout != nullptr),
            (double)batch * m * n * sizeof(cplx<R>) * 2.0);
+  prof_shape(c, ev, m, n, 0, batch, Qout ? 1 : 0);
   return st;
 }
 
@@ -425,6 +428,7 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
     cudaEvent_t ev = prof_begin(c);
     int st = qtt_jacobi_block<R>(G, sigma, Usorted, p, q, max_sweeps, slot, c->stream);
     prof_end(c, ev, PK_JACOBI, 0.0, (double)p * q * sizeof(cplx<R>) * 2.0, idx, jacobi_sweep_flops(p, q));
+    prof_shape(c, ev, p, q, 0, 1);
     return st;
   }
   // Vsorted may be null (rotations not wanted): the single-CTA, cluster and
@@ -449,6 +453,7 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
       cudaEvent_t ev = prof_begin(c);
       int st = qtt_jacobi_cluster<R>(G, sigma, Vsorted, Usorted, p, q, nc, max_sweeps, slot, c->stream);
       prof_end(c, ev, PK_JACOBI, 0.0, (double)(p + 2.0 * q) * q * sizeof(cplx<R>), idx, jacobi_sweep_flops(p, q));
+      prof_shape(c, ev, p, q, 0, 1);
       (void)Vwork;
       return st;
     }
@@ -460,6 +465,7 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
     cudaEvent_t ev = prof_begin(c);
     int st = qtt_jacobi_smem<R>(G, Vwork, sigma, Vsorted, Usorted, p, q, max_sweeps, slot, c->stream);
     prof_end(c, ev, PK_JACOBI, 0.0, (double)(p + 2.0 * q) * q * sizeof(cplx<R>), idx, jacobi_sweep_flops(p, q));
+    prof_shape(c, ev, p, q, 0, 1);
     return st;
   }
   if (wide) {
@@ -474,6 +480,7 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
     int st = qtt_jacobi_wide<R>(G, Gw, Vw, sigma, Vsorted, Usorted, p, q, max_sweeps, flag, &sweeps, &c->launches,
                                 c->stream);
     prof_end(c, ev, PK_JACOBI, jacobi_sweep_flops(p, q) * std::max(1, sweeps), (double)(p + 2.0 * q) * q * sizeof(cplx<R>));
+    prof_shape(c, ev, p, q, 0, 1);
     dfree(c, buf);
     (void)Vwork;
     return st;
@@ -484,6 +491,7 @@ static int jacobi_launch(qtt_ctx* c, cplx<R>* G, cplx<R>* Vwork, R* sigma, cplx<
   cudaEvent_t ev = prof_begin(c);
   int st = qtt_jacobi<R>(G, Vwork, sigma, Vsorted, p, q, 1, max_sweeps, slot, c->stream, Usorted);
   prof_end(c, ev, PK_JACOBI, 0.0, (double)(p + 2.0 * q) * q * sizeof(cplx<R>), idx, jacobi_sweep_flops(p, q));
+  prof_shape(c, ev, p, q, 0, 1);
   return st;
 }
 
@@ -1123,6 +1131,7 @@ int round_det_batch(qtt_ctx* c, int B, const qtt_tt* const* xs, double eps, int 
       TRY(qtt_jacobi_block<R>(G, sig.as<R>(), X.as<C>(), (int)Tcols, (int)jq, 60, slot, c->stream, B));
       prof_end(c, ev, PK_JACOBI, 0.0, (double)B * Tcols * jq * sizeof(C) * 2.0, idx,
                B * jacobi_sweep_flops((double)Tcols, (double)jq));
+      prof_shape(c, ev, Tcols, jq, 0, B);
     } else {
       for (int b = 0; b < B; ++b)
         TRY(jacobi_launch<R>(c, G + (size_t)b * Tcols * jq, nullptr, sig.as<R>() + (size_t)b * jq, nullptr,

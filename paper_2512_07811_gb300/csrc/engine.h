@@ -17,6 +17,8 @@ struct ProfRec {
   double flops, bytes;
   int sweep_idx;         // Jacobi: index of the device sweep counter, else -1
   double per_sweep;      // Jacobi: model flops of one sweep
+  int64_t shape[4];      // GEMM: M, N, K, batch; QR: m, n, 0, batch; Jacobi: p, q, 0, batch
+  int variant;           // GEMM: tile edge (32, 64; 128 = tensor cores) x 100 + split-K; else 0
 };
 
 struct qtt_ctx {
@@ -75,7 +77,18 @@ inline void prof_end(qtt_ctx* c, cudaEvent_t a, int cls, double flops, double by
   cudaEvent_t b;
   cudaEventCreate(&b);
   cudaEventRecord(b, c->stream);
-  c->recs.push_back(ProfRec{cls, a, b, flops, bytes, sweep_idx, per_sweep});
+  c->recs.push_back(ProfRec{cls, a, b, flops, bytes, sweep_idx, per_sweep, {0, 0, 0, 0}, 0});
+}
+// Shape of the launch that the last prof_end(c, a, ...) recorded (a = its start event).
+inline void prof_shape(qtt_ctx* c, cudaEvent_t a, int64_t d0, int64_t d1, int64_t d2, int64_t batch,
+                       int variant = 0) {
+  if (!c->prof || !a || c->recs.empty() || c->recs.back().a != a) return;
+  ProfRec& r = c->recs.back();
+  r.shape[0] = d0;
+  r.shape[1] = d1;
+  r.shape[2] = d2;
+  r.shape[3] = batch;
+  r.variant = variant;
 }
 inline int* prof_sweep_slot(qtt_ctx* c, int* idx) {
   *idx = -1;

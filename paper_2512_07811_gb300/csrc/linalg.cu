@@ -981,11 +981,14 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
       S[e] = s_taus[j] != R(0) ? v : cplx<R>(0, 0);
     }
   };
-  // x <- (I - tau v v^H) x for a register column and a scaled reflector in shared memory
-  auto reflect = [&](cplx<R>(&x)[RPL], const cplx<R>* v, R tau) {
+  // x <- (I - tau v v^H) x for a register column and the scaled reflector j
+  // in shared memory; v is zero above row j and below row m, so only the
+  // 32-row slices that meet rows j .. m-1 are touched (a warp-uniform test)
+  auto reflect = [&](cplx<R>(&x)[RPL], const cplx<R>* v, R tau, int j) {
     cplx<R> w(0, 0), w1(0, 0);
 #pragma unroll
     for (int u = 0; u < RPL; ++u) {
+      if (32 * u + 31 < j || 32 * u >= m) continue;
       if (u & 1) cfma_conj(w1, v[lane + 32 * u], x[u]); else cfma_conj(w, v[lane + 32 * u], x[u]);
     }
     w = w + w1;
@@ -993,7 +996,10 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
     w.im = warp_sum(w.im);
     w = tau * w;
 #pragma unroll
-    for (int u = 0; u < RPL; ++u) x[u] = x[u] - v[lane + 32 * u] * w;
+    for (int u = 0; u < RPL; ++u) {
+      if (32 * u + 31 < j || 32 * u >= m) continue;
+      x[u] = x[u] - v[lane + 32 * u] * w;
+    }
   };
   for (int p0 = 0; p0 < n; p0 += NW) {
     const int pcols = min(NW, n - p0);
@@ -1019,7 +1025,7 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
       if (warp < pcols)
         for (int jj = 0; jj < qn; ++jj) {
           const R tau = s_taus[q0 + jj];
-          if (tau != R(0)) reflect(x, S + (size_t)jj * MP, tau);
+          if (tau != R(0)) reflect(x, S + (size_t)jj * MP, tau, q0 + jj);
         }
       __syncthreads();
     }
@@ -1057,7 +1063,7 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
           xr[u] = i < m ? colc[i] : cplx<R>(0, 0);
         }
         if (tau != R(0)) {
-          reflect(xr, Vc + (j & 1) * MP, tau);
+          reflect(xr, Vc + (j & 1) * MP, tau, j);
 #pragma unroll
           for (int u = 0; u < RPL; ++u) {
             const int i = lane + 32 * u;
@@ -1111,7 +1117,7 @@ qr_panel_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, 
           for (int jj = qn - 1; jj >= 0; --jj) {
             const int j = q0 + jj;
             const R tau = s_taus[j];
-            if (j <= c && tau != R(0)) reflect(x, S + (size_t)jj * MP, tau);
+            if (j <= c && tau != R(0)) reflect(x, S + (size_t)jj * MP, tau, j);
           }
       }
       if (c < kmax) {
@@ -1363,16 +1369,18 @@ template int qtt_jacobi_cluster<float>(const cc*, float*, cc*, cc*, int, int, in
 // other kernels).  Outputs: sigma sorted decreasingly and the normalised
 // rotated columns (row-major p x q) in the same order.
 template <class R, int RPL>
-__device__ __forceinline__ bool warp_pair_rotate(cplx<R> (&x)[RPL], cplx<R> (&y)[RPL], R tol2) {
-  // two independent accumulator sets (even / odd rows) halve the FMA chains
+__device__ __forceinline__ bool warp_pair_rotate(cplx<R> (&x)[RPL], cplx<R> (&y)[RPL], R tol2, int p) {
+  // two independent accumulator sets (even / odd rows) halve the FMA chains;
+  // 32-row slices at or below row p hold zeros and are skipped (warp-uniform)
   R al = 0, be = 0, al1 = 0, be1 = 0;
   cplx<R> g(0, 0), g1(0, 0);
 #pragma unroll
   for (int u = 0; u < RPL; u += 2) {
+    if (32 * u >= p) break;
     al += abs2(x[u]);
     be += abs2(y[u]);
     cfma_conj(g, x[u], y[u]);
-    if (u + 1 < RPL) {
+    if (u + 1 < RPL && 32 * (u + 1) < p) {
       al1 += abs2(x[u + 1]);
       be1 += abs2(y[u + 1]);
       cfma_conj(g1, x[u + 1], y[u + 1]);
@@ -1390,6 +1398,7 @@ __device__ __forceinline__ bool warp_pair_rotate(cplx<R> (&x)[RPL], cplx<R> (&y)
   if (!jacobi_rotation(al, be, g, tol2, cs, f1, f2)) return false;
 #pragma unroll
   for (int u = 0; u < RPL; ++u) {
+    if (32 * u >= p) break;
     const cplx<R> a = x[u], b = y[u];
     x[u] = cs * a - f1 * b;
     y[u] = f2 * a + cs * b;
@@ -1468,7 +1477,7 @@ jacobi_block_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out, 
           cplx<R> x[RPL], y[RPL];
           col_load(x, col(slot, a), p, lane);
           col_load(y, col(slot, c), p, lane);
-          if (warp_pair_rotate(x, y, tol2)) {
+          if (warp_pair_rotate(x, y, tol2, p)) {
             col_store(x, col(slot, a), p, lane);
             col_store(y, col(slot, c), p, lane);
             if (lane == 0) s_rot = 1;
@@ -1484,7 +1493,7 @@ jacobi_block_kernel(const cplx<R>* __restrict__ Gin, R* __restrict__ sigma_out, 
         const int c = (w + s) % bs;
         cplx<R> y[RPL];
         col_load(y, col(bot, c), p, lane);
-        if (warp_pair_rotate(x, y, tol2)) {
+        if (warp_pair_rotate(x, y, tol2, p)) {
           col_store(y, col(bot, c), p, lane);
           xr = true;
         }

@@ -159,6 +159,7 @@ _sig("qtt_measure_peak", C.c_int, [_P, C.c_int, C.POINTER(C.c_double)])
 _sig("qtt_ctx_profile", C.c_int, [_P, C.c_int])
 _sig("qtt_ctx_profile_read", C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)])
+_sig("qtt_ctx_profile_shapes", C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int64)])
 _sig("qtt_tt_create", C.c_int, [_P, C.c_int, _I32P, _I32P, C.c_int, C.POINTER(_P)])
 _sig("qtt_tt_destroy", None, [_P])
 _sig("qtt_tt_ncores", C.c_int, [_P])
@@ -220,7 +221,7 @@ _sig("ms_ops_ranks", C.c_int, [_P, _I32P, _I32P])
 
 EXPORTED = ["qtt_status_string", "qtt_ctx_create", "qtt_ctx_destroy", "qtt_ctx_sync", "qtt_ctx_launch_count",
             "qtt_ctx_fail_alloc_after", "qtt_measure_peak",
-            "qtt_ctx_profile", "qtt_ctx_profile_read",
+            "qtt_ctx_profile", "qtt_ctx_profile_read", "qtt_ctx_profile_shapes",
             "qtt_tt_create", "qtt_tt_destroy", "qtt_tt_ncores", "qtt_tt_ranks", "qtt_tt_modes", "qtt_tt_dtype",
             "qtt_tt_core_ptr", "qtt_tt_from_host", "qtt_tt_to_host", "qtt_tt_from_device", "qtt_tt_convert",
             "qtt_mpo_create", "qtt_mpo_destroy", "qtt_mpo_ranks", "qtt_mpo_from_host", "qtt_mpo_to_host",
@@ -318,6 +319,21 @@ class Context:
         _check(_lib.qtt_ctx_profile_read(self.h, self.KERNEL_CLASSES[kclass], C.byref(ms), C.byref(n), C.byref(fl),
                                          C.byref(by)), "qtt_ctx_profile_read")
         return {"ms": ms.value, "launches": int(n.value), "flops": fl.value, "bytes": by.value}
+
+    def profile_shapes(self, kclass: str, max_rows: int = 64):
+        """This context's records of one class grouped by launch shape, by
+        decreasing total time: dicts with dims (GEMM M, N, K; QR m, n, 0;
+        Jacobi p, q, 0), batch, variant, launches, ms and flops."""
+        n = C.c_int64()
+        rows = np.zeros((max_rows, 8), dtype=np.float64)
+        _check(_lib.qtt_ctx_profile_shapes(self.h, self.KERNEL_CLASSES[kclass],
+                                           rows.ctypes.data_as(C.POINTER(C.c_double)), max_rows, C.byref(n)),
+               "qtt_ctx_profile_shapes")
+        out = []
+        for r in rows[:min(max_rows, int(n.value))]:
+            out.append({"dims": tuple(int(v) for v in r[:3]), "batch": int(r[3]), "variant": int(r[4]),
+                        "launches": int(r[5]), "ms": float(r[6]), "flops": float(r[7])})
+        return out
 
 
 class TT:

@@ -354,3 +354,26 @@ def test_dot_structured_matches_oracle(Q, ctx, fp32):
     got = Q.tt_dot_structured(ctx, [(c1, Q.MPO.from_cores(ctx, A, dt), Q.TT.from_cores(ctx, x1, dt)),
                                     (c2, None, Q.TT.from_cores(ctx, x2, dt))], Q.TT.from_cores(ctx, y, dt))
     assert abs(got - ref) <= (2e-5 if fp32 else 1e-12) * np.linalg.norm(s) * np.linalg.norm(T.tt_full(y))
+
+
+def test_profile_shapes_sum_to_class_totals(Q, ctx):
+    """The per-shape profiler rows of each kernel class add up to the class
+    totals (launches, time, model flops), and every GEMM row names a shape."""
+    x = Q.TT.from_cores(ctx, I.random_tt_cores(12, 2, 24, seed=71, dtype=np.complex128), Q.C64)
+    y = Q.TT.from_cores(ctx, I.random_tt_cores(12, 2, 24, seed=72, dtype=np.complex128), Q.C64)
+    ctx.profile(True)
+    try:
+        z = Q.tt_add(ctx, 1.0, x, 0.5, y)
+        Q.tt_round(ctx, z, 1e-6)
+        for cls in ["gemm", "qr", "jacobi"]:
+            tot = ctx.profile_read(cls)
+            rows = ctx.profile_shapes(cls, 4096)
+            assert sum(r["launches"] for r in rows) == tot["launches"]
+            assert abs(sum(r["ms"] for r in rows) - tot["ms"]) <= 1e-9 * max(1.0, tot["ms"])
+            assert abs(sum(r["flops"] for r in rows) - tot["flops"]) <= 1e-9 * max(1.0, tot["flops"])
+            assert all(r["ms"] >= rows[i + 1]["ms"] for i, r in enumerate(rows[:-1]))
+            if cls == "gemm":
+                assert tot["launches"] > 0
+                assert all(min(r["dims"]) > 0 and r["batch"] > 0 and r["variant"] >= 3200 for r in rows)
+    finally:
+        ctx.profile(False)
