@@ -1148,6 +1148,353 @@ static int launch_qr_panel(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, in
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
 
+// ------------------------------------------------ blocked left-looking QR
+// Householder QR, one CTA of 16 warps per matrix, m <= 32 * RPL rows, in
+// panels of QB = 16 columns with the compact WY form of each panel's
+// reflectors: H_{p0} ... H_{p0+15} = I - V T V^H, T upper triangular
+// (T_kk = tau_k, T_{0:k,k} = -tau_k T_{0:k,0:k} V_{:,0:k}^H v_k).
+//   * A panel (all m rows, in shared memory) first receives every earlier
+//     panel q as one block update P <- P - V_q (T_q^H (V_q^H P)): the
+//     reflectors of q staged from the workspace W, T_q kept in shared memory;
+//     three small products instead of sixteen rank-1 updates with a warp
+//     reduction each.
+//   * The panel is then factored in shared memory column by column (every
+//     warp applies reflector j to one later panel column, the warp holding
+//     column j + 1 forms reflector j + 1; one barrier per column), written
+//     back to W (R above, reflectors below the diagonal), and T of the panel
+//     built from the Gram matrix of its reflectors.
+//   * The explicit Q is formed backwards from [I; 0]: for the panels from the
+//     last to the first, Q[p0:, c0:c0+16] <- X - V (T (V^H X)) for every
+//     16-column chunk c0 >= p0 (read from and written to Qout).
+// Same inputs, outputs, reflector format (W, 1/v0 and tau per column) and
+// zero-column rule as qr_panel_kernel.
+constexpr int QB = 16;
+
+template <class R, int RPL>
+static size_t qr_blocked_bytes(int m, int n) {
+  const int kmax = m < n ? m : n, npan = (kmax + QB - 1) / QB, ldp = m | 1;
+  return ((size_t)2 * QB * ldp + (size_t)npan * QB * QB + (size_t)2 * QB * QB + 2 * 32 * RPL + kmax) *
+             sizeof(cplx<R>) + (size_t)kmax * sizeof(R) + 16;
+}
+
+template <class R, int RPL>
+__global__ void __launch_bounds__(32 * QB, 1)
+qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int m, int n,
+                  int64_t rows_total, int64_t rows_per_batch, cplx<R>* __restrict__ Wbase, cplx<R>* __restrict__ out,
+                  int64_t out_bstride, int64_t ldr, cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout,
+                  int64_t q_bstride, int64_t ldq) {
+  constexpr int MP = 32 * RPL;  // rows padded to whole warps (the panel factorisation's registers)
+  constexpr int NT = 32 * QB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int kmax = m < n ? m : n;
+  const int npan = (kmax + QB - 1) / QB;
+  const int ldp = m | 1;  // odd column stride: lanes on different columns of one row hit different banks
+  cplx<R>* P = reinterpret_cast<cplx<R>*>(smem_raw);  // QB columns of ldp: the panel, or a chunk of Q
+  cplx<R>* S = P + (size_t)QB * ldp;                   // QB staged scaled reflectors
+  cplx<R>* Tall = S + (size_t)QB * ldp;                // npan x QB x QB, T_q[l][k] row-major
+  cplx<R>* Yb = Tall + (size_t)npan * QB * QB;         // QB x QB: V^H X
+  cplx<R>* Zb = Yb + QB * QB;                          // QB x QB
+  cplx<R>* Vc = Zb + QB * QB;                          // 2 x MP reflector being applied in the panel
+  cplx<R>* s_ivs = Vc + 2 * MP;                        // 1/v0 per reflector
+  R* s_taus = reinterpret_cast<R*>(s_ivs + kmax);      // tau per reflector
+  __shared__ R red[32];
+  const int64_t b = blockIdx.x;
+  cplx<R>* W = Wbase + b * (int64_t)m * n;
+  cplx<R>* tw = tauws ? tauws + b * 2 * n : nullptr;
+  const int64_t row0 = b * rows_per_batch;
+  int64_t valid = rows_total - row0;
+  if (valid > m) valid = m;
+  const int64_t ib = midx_off(inB, b);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  R part = 0;
+  for (int c = warp; c < n; c += QB)
+    for (int i = lane; i < valid; i += 32) part += abs2(in[ib + midx_off(rowI, i) + midx_off(colI, c)]);
+  const R anorm2 = block_sum(part, red);
+  const R eps = sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON);
+  const R zero_thresh2 = eps * eps * anorm2;
+  // S <- the scaled reflectors q0 .. q0+qn-1 (column k: 0 above row q0+k, 1
+  // there, x_i / v0 below; zero for tau = 0 and for k >= qn), whose unscaled
+  // entries are column k of src (stride ld)
+  auto stage = [&](const cplx<R>* src, int ld, int q0, int qn) {
+    for (int e = tid; e < QB * m; e += NT) {
+      const int k = e / m, i = e - k * m, j = q0 + k;
+      cplx<R> v(0, 0);
+      if (k < qn && s_taus[j] != R(0))
+        v = i > j ? src[(size_t)k * ld + i] * s_ivs[j] : cplx<R>(i == j ? R(1) : R(0), R(0));
+      S[(size_t)k * ldp + i] = v;
+    }
+  };
+  // Yb[k][c] = sum over rows i >= r0 of conj(S[k][i]) X[c][i]: each thread
+  // sums the outputs (k, c), (k, c+8), (k+8, c), (k+8, c+8) over every
+  // eighth row, the eight row groups of an output being adjacent lanes
+  // (reduced by shuffles)
+  auto vhx = [&](const cplx<R>* X, int r0) {
+    const int g = tid & 7, q = tid >> 3, kq = q >> 3, cq = q & 7;
+    const cplx<R>* s0 = S + (size_t)kq * ldp;
+    const cplx<R>* s1 = S + (size_t)(kq + 8) * ldp;
+    const cplx<R>* x0 = X + (size_t)cq * ldp;
+    const cplx<R>* x1 = X + (size_t)(cq + 8) * ldp;
+    cplx<R> a00(0, 0), a01(0, 0), a10(0, 0), a11(0, 0);
+    for (int i = r0 + g; i < m; i += 8) {
+      const cplx<R> u0 = s0[i], u1 = s1[i], y0 = x0[i], y1 = x1[i];
+      cfma_conj(a00, u0, y0);
+      cfma_conj(a01, u0, y1);
+      cfma_conj(a10, u1, y0);
+      cfma_conj(a11, u1, y1);
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      a00.re += __shfl_xor_sync(0xffffffffu, a00.re, o);
+      a00.im += __shfl_xor_sync(0xffffffffu, a00.im, o);
+      a01.re += __shfl_xor_sync(0xffffffffu, a01.re, o);
+      a01.im += __shfl_xor_sync(0xffffffffu, a01.im, o);
+      a10.re += __shfl_xor_sync(0xffffffffu, a10.re, o);
+      a10.im += __shfl_xor_sync(0xffffffffu, a10.im, o);
+      a11.re += __shfl_xor_sync(0xffffffffu, a11.re, o);
+      a11.im += __shfl_xor_sync(0xffffffffu, a11.im, o);
+    }
+    if (g == 0) {
+      Yb[kq * QB + cq] = a00;
+      Yb[kq * QB + cq + 8] = a01;
+      Yb[(kq + 8) * QB + cq] = a10;
+      Yb[(kq + 8) * QB + cq + 8] = a11;
+    }
+  };
+  // X[c][i] -= sum_k S[k][i] Zb[k][c] for rows i >= r0 and columns c < ncols,
+  // one row per thread (its QB reflector entries in registers, Zb broadcast)
+  auto update = [&](cplx<R>* X, int r0, int ncols) {
+    for (int i = r0 + tid; i < m; i += NT) {
+      cplx<R> sv[QB];
+#pragma unroll
+      for (int kk = 0; kk < QB; ++kk) sv[kk] = S[(size_t)kk * ldp + i];
+#pragma unroll
+      for (int c = 0; c < QB; ++c) {
+        if (c >= ncols) break;
+        cplx<R> acc(0, 0);
+#pragma unroll
+        for (int kk = 0; kk < QB; ++kk) cfma(acc, sv[kk], Zb[kk * QB + c]);
+        X[(size_t)c * ldp + i] = X[(size_t)c * ldp + i] - acc;
+      }
+    }
+  };
+  // x <- (I - tau v v^H) x for a register column and the scaled reflector in
+  // shared memory (zero above its diagonal row and from row m; the row count
+  // is padded only to whole warps, so every slice is processed -- measured
+  // faster than testing which slices meet the nonzero rows)
+  auto reflect = [&](cplx<R>(&x)[RPL], const cplx<R>* v, R tau) {
+    cplx<R> w(0, 0), w1(0, 0);
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      if (u & 1) cfma_conj(w1, v[lane + 32 * u], x[u]); else cfma_conj(w, v[lane + 32 * u], x[u]);
+    }
+    w = w + w1;
+    w.re = warp_sum(w.re);
+    w.im = warp_sum(w.im);
+    w = tau * w;
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) x[u] = x[u] - v[lane + 32 * u] * w;
+  };
+  // ---------------- R
+  for (int p0 = 0, pi = 0; p0 < n; p0 += QB, ++pi) {
+    const int pcols = min(QB, n - p0);
+    const int pw = max(0, min(QB, kmax - p0));  // reflectors formed in this panel
+    __syncthreads();  // the previous panel's reads of P are done
+    for (int e = tid; e < pcols * m; e += NT) {
+      const int c = e / m, i = e - c * m;
+      cplx<R> v(0, 0);
+      if (i < valid) {
+        v = in[ib + midx_off(rowI, i) + midx_off(colI, p0 + c)];
+        if (conj_in) v.im = -v.im;
+      }
+      P[(size_t)c * ldp + i] = v;
+    }
+    // every earlier panel as one block update: P <- P - V (T^H (V^H P))
+    for (int q0 = 0, qi = 0; q0 < p0 && q0 < kmax; q0 += QB, ++qi) {
+      const int qn = min(QB, kmax - q0);
+      __syncthreads();
+      stage(W + (size_t)q0 * m, m, q0, qn);
+      __syncthreads();
+      vhx(P, q0);
+      __syncthreads();
+      if (tid < QB * QB) {
+        const int k = tid / QB, c = tid - k * QB;
+        const cplx<R>* T = Tall + (size_t)qi * QB * QB;
+        cplx<R> z(0, 0);
+        for (int l = 0; l <= k; ++l) cfma_conj(z, T[l * QB + k], Yb[l * QB + c]);
+        Zb[tid] = z;
+      }
+      __syncthreads();
+      update(P, q0, pcols);
+    }
+    __syncthreads();
+    // factor the panel: warp w keeps panel column w in registers (rows on
+    // lanes).  Step jj: warp jj forms reflector p0 + jj from its column (norm
+    // below the diagonal, scalars in every lane), writes the finished column
+    // to P and the scaled reflector to Vc; after the barrier the warps of the
+    // later columns apply it.  The warp that forms the next reflector thus
+    // goes straight from applying this one to forming its own.
+    cplx<R> xr[RPL];
+    {
+      const cplx<R>* col = P + (size_t)warp * ldp;
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        const int i = lane + 32 * u;
+        xr[u] = warp < pcols && i < m ? col[i] : cplx<R>(0, 0);
+      }
+    }
+    for (int jj = 0; jj < pw; ++jj) {
+      const int j = p0 + jj;
+      if (warp == jj) {
+        R hi = 0, lo = 0;
+        cplx<R> x0(0, 0);
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const int i = lane + 32 * u;
+          if (i > j && i < m) two_sum_acc(hi, lo, abs2(xr[u]));
+          if (i == j) x0 = xr[u];
+        }
+        const R below = warp_sum_compensated(hi, lo);
+        x0.re = warp_sum(x0.re);  // one lane holds row j, the others add zeros
+        x0.im = warp_sum(x0.im);
+        const R ax2 = abs2(x0), nrm2 = below + ax2;
+        const bool zero = nrm2 <= zero_thresh2 || below <= zero_thresh2;
+        R tau = R(0);
+        cplx<R> iv(0, 0), diag = nrm2 <= zero_thresh2 ? cplx<R>(0, 0) : x0;
+        if (!zero) {
+          const R ax0 = sqrt(ax2), nrm = sqrt(nrm2);
+          const R phr = ax0 > R(0) ? x0.re / ax0 : R(1), phi = ax0 > R(0) ? x0.im / ax0 : R(0);
+          const R s0 = ax0 + nrm;
+          const R v02 = s0 * s0;
+          tau = R(2) * v02 / (below + v02);
+          iv = cplx<R>(phr / s0, -phi / s0);
+          diag = cplx<R>(-phr * nrm, -phi * nrm);
+        }
+        cplx<R>* col = P + (size_t)jj * ldp;
+        cplx<R>* vs = Vc + (j & 1) * MP;
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const int i = lane + 32 * u;
+          if (32 * u >= m) {
+            vs[i] = cplx<R>(0, 0);
+            continue;
+          }
+          const cplx<R> x = i == j ? diag : (i > j && zero ? cplx<R>(0, 0) : xr[u]);
+          if (i < m) col[i] = x;
+          vs[i] = i > j && i < m ? x * iv : cplx<R>(i == j ? R(1) : R(0), R(0));
+        }
+        if (lane == 0) {
+          s_taus[j] = tau;
+          s_ivs[j] = iv;
+          if (tw) {
+            tw[2 * j] = iv;
+            tw[2 * j + 1] = cplx<R>(tau, R(0));
+          }
+        }
+      }
+      __syncthreads();
+      if (warp > jj && warp < pcols) {
+        const R tau = s_taus[j];
+        if (tau != R(0)) reflect(xr, Vc + (j & 1) * MP, tau);
+      }
+    }
+    // columns past the last reflector (n > m) go back as they are
+    if (warp >= pw && warp < pcols) {
+      cplx<R>* col = P + (size_t)warp * ldp;
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        const int i = lane + 32 * u;
+        if (i < m) col[i] = xr[u];
+      }
+    }
+    __syncthreads();
+    // panel back to W; T of the panel from the Gram matrix of its reflectors
+    for (int e = tid; e < pcols * m; e += NT) {
+      const int c = e / m, i = e - c * m;
+      W[(size_t)(p0 + c) * m + i] = P[(size_t)c * ldp + i];
+    }
+    if (pw > 0) {
+      stage(P, ldp, p0, pw);
+      __syncthreads();
+      vhx(S, p0);
+      cplx<R>* T = Tall + (size_t)pi * QB * QB;
+      if (tid < QB * QB) {
+        const int l = tid / QB, k = tid - l * QB;
+        T[tid] = l == k && k < pw ? cplx<R>(s_taus[p0 + k], R(0)) : cplx<R>(0, 0);
+      }
+      __syncthreads();
+      for (int k = 1; k < pw; ++k) {
+        if (tid < k) {
+          const int l = tid;
+          cplx<R> acc(0, 0);
+          for (int jx = l; jx < k; ++jx) cfma(acc, T[l * QB + jx], Yb[jx * QB + k]);
+          const R tk = s_taus[p0 + k];
+          T[l * QB + k] = cplx<R>(-tk * acc.re, -tk * acc.im);
+        }
+        __syncthreads();
+      }
+    }
+  }
+  __syncthreads();
+  if (out) {
+    cplx<R>* Rb = out + b * out_bstride;
+    for (int64_t e = tid; e < (int64_t)kmax * n; e += NT) {
+      const int64_t i = e / n, c = e - i * n;
+      Rb[i * ldr + c] = (c >= i) ? W[c * m + i] : cplx<R>(0, 0);
+    }
+  }
+  if (!Qout) return;
+  // ---------------- explicit Q, backwards from [I; 0]
+  cplx<R>* Q = Qout + b * q_bstride;
+  for (int64_t e = tid; e < (int64_t)m * kmax; e += NT) {
+    const int64_t i = e / kmax, c = e - i * kmax;
+    Q[i * ldq + c] = cplx<R>(i == c ? R(1) : R(0), R(0));
+  }
+  for (int pi = npan - 1; pi >= 0; --pi) {
+    const int p0 = pi * QB, qn = min(QB, kmax - p0);
+    __syncthreads();
+    stage(W + (size_t)p0 * m, m, p0, qn);
+    const cplx<R>* T = Tall + (size_t)pi * QB * QB;
+    for (int c0 = p0; c0 < kmax; c0 += QB) {
+      const int ncols = min(QB, kmax - c0);
+      __syncthreads();
+      for (int e = tid; e < (m - p0) * QB; e += NT) {
+        const int i = p0 + (e >> 4), c = e & (QB - 1);
+        P[(size_t)c * ldp + i] = c < ncols ? Q[(int64_t)i * ldq + c0 + c] : cplx<R>(0, 0);
+      }
+      __syncthreads();
+      vhx(P, p0);
+      __syncthreads();
+      if (tid < QB * QB) {
+        const int k = tid / QB, c = tid - k * QB;
+        cplx<R> z(0, 0);
+        for (int l = k; l < QB; ++l) cfma(z, T[k * QB + l], Yb[l * QB + c]);
+        Zb[tid] = z;
+      }
+      __syncthreads();
+      update(P, p0, ncols);
+      __syncthreads();
+      for (int e = tid; e < (m - p0) * QB; e += NT) {
+        const int i = p0 + (e >> 4), c = e & (QB - 1);
+        if (c < ncols) Q[(int64_t)i * ldq + c0 + c] = P[(size_t)c * ldp + i];
+      }
+    }
+  }
+}
+
+template <class R, int RPL>
+static int launch_qr_blocked(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
+                             int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
+                             int64_t out_bstride, int64_t ldr, cplx<R>* tauws, cplx<R>* Qout, int64_t q_bstride,
+                             int64_t ldq, cudaStream_t s) {
+  const size_t sm = qr_blocked_bytes<R, RPL>((int)m, (int)n);
+  if (sm > 200 * 1024) return QTT_ERR_UNSUPPORTED;
+  if (qtt_allow_max_smem((const void*)qr_blocked_kernel<R, RPL>) != QTT_OK) return QTT_ERR_CUDA;
+  qr_blocked_kernel<R, RPL><<<(unsigned)batch, 32 * QB, sm, s>>>(in, inB, rowI, colI, conj_in, (int)m, (int)n,
+                                                                  rows_total, rows_per_batch, W, out, out_bstride,
+                                                                  ldr, tauws, Qout, q_bstride, ldq);
+  return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
+}
+
 template <class R>
 int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
              int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
@@ -1155,7 +1502,24 @@ int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int
              int64_t q_bstride, int64_t ldq, cplx<R>* Qws) {
   if (batch <= 0 || m <= 0 || n <= 0) return QTT_OK;
   if (batch > 65535 || m > INT32_MAX || n > INT32_MAX) return QTT_ERR_ARG;
-  // panel kernel for up to 512 rows (256 in FP64), else the workspace kernel
+  // FP32: the blocked kernel where its shared memory fits; else the panel
+  // kernel for up to 512 rows (256 in FP64); else the workspace kernel
+  if constexpr (sizeof(R) == 4) {
+    int st = QTT_ERR_UNSUPPORTED;
+    if (m <= 128)
+      st = launch_qr_blocked<R, 4>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
+                                   out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+    else if (m <= 256)
+      st = launch_qr_blocked<R, 8>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
+                                   out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+    else if (m <= 288)  // 2 x 136 rows: the projection QR of sketch width 136
+      st = launch_qr_blocked<R, 9>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
+                                   out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+    else if (m <= 512)
+      st = launch_qr_blocked<R, 16>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
+                                    out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+    if (st != QTT_ERR_UNSUPPORTED) return st;
+  }
   {
     int st = QTT_ERR_UNSUPPORTED;
     if (m <= 128)
