@@ -1170,6 +1170,81 @@ static int launch_qr_panel(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, in
 // zero-column rule as qr_panel_kernel.
 constexpr int QB = 16;
 
+// Building blocks of the blocked QR kernels (512 threads; S, X: QB columns of
+// ldp complex values in shared memory, column-major).
+//
+// S <- the scaled reflectors q0 .. q0+qn-1 (column k: 0 above row q0+k, 1
+// there, x_i / v0 below; zero for tau = 0 and for k >= qn), whose unscaled
+// entries are column k of src (stride ld); taus / ivs indexed by reflector.
+template <class R>
+__device__ __forceinline__ void qb_stage(cplx<R>* S, int ldp, const cplx<R>* src, int ld, int q0, int qn, int m,
+                                         const R* taus, const cplx<R>* ivs) {
+  for (int e = threadIdx.x; e < QB * m; e += blockDim.x) {
+    const int k = e / m, i = e - k * m, j = q0 + k;
+    cplx<R> v(0, 0);
+    if (k < qn && taus[j] != R(0))
+      v = i > j ? src[(size_t)k * ld + i] * ivs[j] : cplx<R>(i == j ? R(1) : R(0), R(0));
+    S[(size_t)k * ldp + i] = v;
+  }
+}
+
+// Yb[k][c] = sum over rows i >= r0 of conj(S[k][i]) X[c][i]: each thread sums
+// the outputs (k, c), (k, c+8), (k+8, c), (k+8, c+8) over every eighth row,
+// the eight row groups of an output being adjacent lanes (reduced by shuffles)
+template <class R>
+__device__ __forceinline__ void qb_vhx(const cplx<R>* S, const cplx<R>* X, int ldp, int r0, int m, cplx<R>* Yb) {
+  const int tid = threadIdx.x, g = tid & 7, q = tid >> 3, kq = q >> 3, cq = q & 7;
+  const cplx<R>* s0 = S + (size_t)kq * ldp;
+  const cplx<R>* s1 = S + (size_t)(kq + 8) * ldp;
+  const cplx<R>* x0 = X + (size_t)cq * ldp;
+  const cplx<R>* x1 = X + (size_t)(cq + 8) * ldp;
+  cplx<R> a00(0, 0), a01(0, 0), a10(0, 0), a11(0, 0);
+  for (int i = r0 + g; i < m; i += 8) {
+    const cplx<R> u0 = s0[i], u1 = s1[i], y0 = x0[i], y1 = x1[i];
+    cfma_conj(a00, u0, y0);
+    cfma_conj(a01, u0, y1);
+    cfma_conj(a10, u1, y0);
+    cfma_conj(a11, u1, y1);
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    a00.re += __shfl_xor_sync(0xffffffffu, a00.re, o);
+    a00.im += __shfl_xor_sync(0xffffffffu, a00.im, o);
+    a01.re += __shfl_xor_sync(0xffffffffu, a01.re, o);
+    a01.im += __shfl_xor_sync(0xffffffffu, a01.im, o);
+    a10.re += __shfl_xor_sync(0xffffffffu, a10.re, o);
+    a10.im += __shfl_xor_sync(0xffffffffu, a10.im, o);
+    a11.re += __shfl_xor_sync(0xffffffffu, a11.re, o);
+    a11.im += __shfl_xor_sync(0xffffffffu, a11.im, o);
+  }
+  if (g == 0) {
+    Yb[kq * QB + cq] = a00;
+    Yb[kq * QB + cq + 8] = a01;
+    Yb[(kq + 8) * QB + cq] = a10;
+    Yb[(kq + 8) * QB + cq + 8] = a11;
+  }
+}
+
+// X[c][i] -= sum_k S[k][i] Zb[k][c] for rows i >= r0 and columns c < ncols,
+// one row per thread (its QB reflector entries in registers, Zb broadcast)
+template <class R>
+__device__ __forceinline__ void qb_update(const cplx<R>* S, const cplx<R>* Zb, cplx<R>* X, int ldp, int r0, int m,
+                                          int ncols) {
+  for (int i = r0 + threadIdx.x; i < m; i += blockDim.x) {
+    cplx<R> sv[QB];
+#pragma unroll
+    for (int kk = 0; kk < QB; ++kk) sv[kk] = S[(size_t)kk * ldp + i];
+#pragma unroll
+    for (int c = 0; c < QB; ++c) {
+      if (c >= ncols) break;
+      cplx<R> acc(0, 0);
+#pragma unroll
+      for (int kk = 0; kk < QB; ++kk) cfma(acc, sv[kk], Zb[kk * QB + c]);
+      X[(size_t)c * ldp + i] = X[(size_t)c * ldp + i] - acc;
+    }
+  }
+}
+
 template <class R, int RPL>
 static size_t qr_blocked_bytes(int m, int n) {
   const int kmax = m < n ? m : n, npan = (kmax + QB - 1) / QB, ldp = m | 1;
@@ -1182,7 +1257,7 @@ __global__ void __launch_bounds__(32 * QB, 1)
 qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int m, int n,
                   int64_t rows_total, int64_t rows_per_batch, cplx<R>* __restrict__ Wbase, cplx<R>* __restrict__ out,
                   int64_t out_bstride, int64_t ldr, cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout,
-                  int64_t q_bstride, int64_t ldq) {
+                  int64_t q_bstride, int64_t ldq, cplx<R>* __restrict__ Tg) {
   constexpr int MP = 32 * RPL;  // rows padded to whole warps (the panel factorisation's registers)
   constexpr int NT = 32 * QB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1212,71 +1287,6 @@ qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI
   const R anorm2 = block_sum(part, red);
   const R eps = sizeof(R) == 8 ? R(DBL_EPSILON) : R(FLT_EPSILON);
   const R zero_thresh2 = eps * eps * anorm2;
-  // S <- the scaled reflectors q0 .. q0+qn-1 (column k: 0 above row q0+k, 1
-  // there, x_i / v0 below; zero for tau = 0 and for k >= qn), whose unscaled
-  // entries are column k of src (stride ld)
-  auto stage = [&](const cplx<R>* src, int ld, int q0, int qn) {
-    for (int e = tid; e < QB * m; e += NT) {
-      const int k = e / m, i = e - k * m, j = q0 + k;
-      cplx<R> v(0, 0);
-      if (k < qn && s_taus[j] != R(0))
-        v = i > j ? src[(size_t)k * ld + i] * s_ivs[j] : cplx<R>(i == j ? R(1) : R(0), R(0));
-      S[(size_t)k * ldp + i] = v;
-    }
-  };
-  // Yb[k][c] = sum over rows i >= r0 of conj(S[k][i]) X[c][i]: each thread
-  // sums the outputs (k, c), (k, c+8), (k+8, c), (k+8, c+8) over every
-  // eighth row, the eight row groups of an output being adjacent lanes
-  // (reduced by shuffles)
-  auto vhx = [&](const cplx<R>* X, int r0) {
-    const int g = tid & 7, q = tid >> 3, kq = q >> 3, cq = q & 7;
-    const cplx<R>* s0 = S + (size_t)kq * ldp;
-    const cplx<R>* s1 = S + (size_t)(kq + 8) * ldp;
-    const cplx<R>* x0 = X + (size_t)cq * ldp;
-    const cplx<R>* x1 = X + (size_t)(cq + 8) * ldp;
-    cplx<R> a00(0, 0), a01(0, 0), a10(0, 0), a11(0, 0);
-    for (int i = r0 + g; i < m; i += 8) {
-      const cplx<R> u0 = s0[i], u1 = s1[i], y0 = x0[i], y1 = x1[i];
-      cfma_conj(a00, u0, y0);
-      cfma_conj(a01, u0, y1);
-      cfma_conj(a10, u1, y0);
-      cfma_conj(a11, u1, y1);
-    }
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      a00.re += __shfl_xor_sync(0xffffffffu, a00.re, o);
-      a00.im += __shfl_xor_sync(0xffffffffu, a00.im, o);
-      a01.re += __shfl_xor_sync(0xffffffffu, a01.re, o);
-      a01.im += __shfl_xor_sync(0xffffffffu, a01.im, o);
-      a10.re += __shfl_xor_sync(0xffffffffu, a10.re, o);
-      a10.im += __shfl_xor_sync(0xffffffffu, a10.im, o);
-      a11.re += __shfl_xor_sync(0xffffffffu, a11.re, o);
-      a11.im += __shfl_xor_sync(0xffffffffu, a11.im, o);
-    }
-    if (g == 0) {
-      Yb[kq * QB + cq] = a00;
-      Yb[kq * QB + cq + 8] = a01;
-      Yb[(kq + 8) * QB + cq] = a10;
-      Yb[(kq + 8) * QB + cq + 8] = a11;
-    }
-  };
-  // X[c][i] -= sum_k S[k][i] Zb[k][c] for rows i >= r0 and columns c < ncols,
-  // one row per thread (its QB reflector entries in registers, Zb broadcast)
-  auto update = [&](cplx<R>* X, int r0, int ncols) {
-    for (int i = r0 + tid; i < m; i += NT) {
-      cplx<R> sv[QB];
-#pragma unroll
-      for (int kk = 0; kk < QB; ++kk) sv[kk] = S[(size_t)kk * ldp + i];
-#pragma unroll
-      for (int c = 0; c < QB; ++c) {
-        if (c >= ncols) break;
-        cplx<R> acc(0, 0);
-#pragma unroll
-        for (int kk = 0; kk < QB; ++kk) cfma(acc, sv[kk], Zb[kk * QB + c]);
-        X[(size_t)c * ldp + i] = X[(size_t)c * ldp + i] - acc;
-      }
-    }
-  };
   // x <- (I - tau v v^H) x for a register column and the scaled reflector in
   // shared memory (zero above its diagonal row and from row m; the row count
   // is padded only to whole warps, so every slice is processed -- measured
@@ -1312,9 +1322,9 @@ qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI
     for (int q0 = 0, qi = 0; q0 < p0 && q0 < kmax; q0 += QB, ++qi) {
       const int qn = min(QB, kmax - q0);
       __syncthreads();
-      stage(W + (size_t)q0 * m, m, q0, qn);
+      qb_stage(S, ldp, W + (size_t)q0 * m, m, q0, qn, m, s_taus, s_ivs);
       __syncthreads();
-      vhx(P, q0);
+      qb_vhx(S, P, ldp, q0, m, Yb);
       __syncthreads();
       if (tid < QB * QB) {
         const int k = tid / QB, c = tid - k * QB;
@@ -1324,7 +1334,7 @@ qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI
         Zb[tid] = z;
       }
       __syncthreads();
-      update(P, q0, pcols);
+      qb_update(S, Zb, P, ldp, q0, m, pcols);
     }
     __syncthreads();
     // factor the panel: warp w keeps panel column w in registers (rows on
@@ -1413,9 +1423,9 @@ qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI
       W[(size_t)(p0 + c) * m + i] = P[(size_t)c * ldp + i];
     }
     if (pw > 0) {
-      stage(P, ldp, p0, pw);
+      qb_stage(S, ldp, P, ldp, p0, pw, m, s_taus, s_ivs);
       __syncthreads();
-      vhx(S, p0);
+      qb_vhx(S, S, ldp, p0, m, Yb);
       cplx<R>* T = Tall + (size_t)pi * QB * QB;
       if (tid < QB * QB) {
         const int l = tid / QB, k = tid - l * QB;
@@ -1443,6 +1453,12 @@ qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI
     }
   }
   if (!Qout) return;
+  if (Tg) {
+    // Q is formed by qr_form_q_kernel, one CTA per 16-column chunk: hand the T factors over
+    cplx<R>* Tb = Tg + b * (int64_t)npan * QB * QB;
+    for (int e = tid; e < npan * QB * QB; e += NT) Tb[e] = Tall[e];
+    return;
+  }
   // ---------------- explicit Q, backwards from [I; 0]
   cplx<R>* Q = Qout + b * q_bstride;
   for (int64_t e = tid; e < (int64_t)m * kmax; e += NT) {
@@ -1452,7 +1468,7 @@ qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI
   for (int pi = npan - 1; pi >= 0; --pi) {
     const int p0 = pi * QB, qn = min(QB, kmax - p0);
     __syncthreads();
-    stage(W + (size_t)p0 * m, m, p0, qn);
+    qb_stage(S, ldp, W + (size_t)p0 * m, m, p0, qn, m, s_taus, s_ivs);
     const cplx<R>* T = Tall + (size_t)pi * QB * QB;
     for (int c0 = p0; c0 < kmax; c0 += QB) {
       const int ncols = min(QB, kmax - c0);
@@ -1462,7 +1478,7 @@ qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI
         P[(size_t)c * ldp + i] = c < ncols ? Q[(int64_t)i * ldq + c0 + c] : cplx<R>(0, 0);
       }
       __syncthreads();
-      vhx(P, p0);
+      qb_vhx(S, P, ldp, p0, m, Yb);
       __syncthreads();
       if (tid < QB * QB) {
         const int k = tid / QB, c = tid - k * QB;
@@ -1471,7 +1487,7 @@ qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI
         Zb[tid] = z;
       }
       __syncthreads();
-      update(P, p0, ncols);
+      qb_update(S, Zb, P, ldp, p0, m, ncols);
       __syncthreads();
       for (int e = tid; e < (m - p0) * QB; e += NT) {
         const int i = p0 + (e >> 4), c = e & (QB - 1);
@@ -1481,17 +1497,92 @@ qr_blocked_kernel(const cplx<R>* __restrict__ in, MIdx inB, MIdx rowI, MIdx colI
   }
 }
 
+// Explicit Q of the blocked QR, m x min(m, n): CTA ci forms columns 16 ci ..
+// 16 ci + 15 in shared memory, starting from the identity columns and
+// applying the block reflectors of panels ci, ci - 1, ..., 0 in that order
+// (X <- X - V_p (T_p (V_p^H X)) on rows >= 16 p).  The chunks are independent,
+// so the backward accumulation runs on as many SMs as there are panels.
+// Reads the reflectors (W), the (1/v0, tau) pairs (tauws) and the T factors
+// (Tg, npan x 16 x 16 per matrix) that qr_blocked_kernel left.
+template <class R>
+__global__ void __launch_bounds__(32 * QB, 1)
+qr_form_q_kernel(const cplx<R>* __restrict__ Wbase, int m, int n, const cplx<R>* __restrict__ Tg,
+                 const cplx<R>* __restrict__ tauws, cplx<R>* __restrict__ Qout, int64_t q_bstride, int64_t ldq) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int kmax = m < n ? m : n, npan = (kmax + QB - 1) / QB, ldp = m | 1;
+  const int tid = threadIdx.x, ci = blockIdx.x, c0 = ci * QB, ncols = min(QB, kmax - c0);
+  const int64_t b = blockIdx.y;
+  cplx<R>* X = reinterpret_cast<cplx<R>*>(smem_raw);  // QB x ldp
+  cplx<R>* S = X + (size_t)QB * ldp;                   // QB x ldp
+  cplx<R>* Yb = S + (size_t)QB * ldp;
+  cplx<R>* Zb = Yb + QB * QB;
+  cplx<R>* T = Zb + QB * QB;
+  cplx<R>* ivs = T + QB * QB;                          // kmax
+  R* taus = reinterpret_cast<R*>(ivs + kmax);          // kmax
+  const cplx<R>* W = Wbase + b * (int64_t)m * n;
+  const cplx<R>* tw = tauws + b * 2 * n;
+  const cplx<R>* Tb = Tg + b * (int64_t)npan * QB * QB;
+  for (int j = tid; j < kmax; j += blockDim.x) {
+    ivs[j] = tw[2 * j];
+    taus[j] = tw[2 * j + 1].re;
+  }
+  for (int e = tid; e < QB * m; e += blockDim.x) {
+    const int c = e / m, i = e - c * m;
+    X[(size_t)c * ldp + i] = cplx<R>(c < ncols && i == c0 + c ? R(1) : R(0), R(0));
+  }
+  for (int p = ci; p >= 0; --p) {
+    const int p0 = p * QB, qn = min(QB, kmax - p0);
+    __syncthreads();
+    qb_stage(S, ldp, W + (size_t)p0 * m, m, p0, qn, m, taus, ivs);
+    for (int e = tid; e < QB * QB; e += blockDim.x) T[e] = Tb[(size_t)p * QB * QB + e];
+    __syncthreads();
+    qb_vhx(S, X, ldp, p0, m, Yb);
+    __syncthreads();
+    if (tid < QB * QB) {
+      const int k = tid / QB, c = tid - k * QB;
+      cplx<R> z(0, 0);
+      for (int l = k; l < QB; ++l) cfma(z, T[k * QB + l], Yb[l * QB + c]);
+      Zb[tid] = z;
+    }
+    __syncthreads();
+    qb_update(S, Zb, X, ldp, p0, m, ncols);
+  }
+  __syncthreads();
+  cplx<R>* Q = Qout + b * q_bstride;
+  for (int e = tid; e < m * QB; e += blockDim.x) {
+    const int i = e / QB, c = e - i * QB;
+    if (c < ncols) Q[(int64_t)i * ldq + c0 + c] = X[(size_t)c * ldp + i];
+  }
+}
+
+template <class R>
+static size_t qr_form_q_bytes(int m, int n) {
+  const int kmax = m < n ? m : n, ldp = m | 1;
+  return ((size_t)2 * QB * ldp + (size_t)3 * QB * QB + kmax) * sizeof(cplx<R>) + (size_t)kmax * sizeof(R) + 16;
+}
+
 template <class R, int RPL>
 static int launch_qr_blocked(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int64_t m, int64_t n,
                              int64_t rows_total, int64_t rows_per_batch, int64_t batch, cplx<R>* W, cplx<R>* out,
                              int64_t out_bstride, int64_t ldr, cplx<R>* tauws, cplx<R>* Qout, int64_t q_bstride,
-                             int64_t ldq, cudaStream_t s) {
+                             int64_t ldq, cplx<R>* Qws, cudaStream_t s) {
   const size_t sm = qr_blocked_bytes<R, RPL>((int)m, (int)n);
   if (sm > 200 * 1024) return QTT_ERR_UNSUPPORTED;
+  const int64_t kmax = std::min(m, n), npan = (kmax + QB - 1) / QB;
+  // the explicit Q by the chunk-parallel kernel where the workspace can hold
+  // the T factors and the (1/v0, tau) pairs are kept
+  const bool split_q = Qout && tauws && Qws && npan * QB * QB <= m * kmax &&
+                       qr_form_q_bytes<R>((int)m, (int)n) <= 200 * 1024;
   if (qtt_allow_max_smem((const void*)qr_blocked_kernel<R, RPL>) != QTT_OK) return QTT_ERR_CUDA;
   qr_blocked_kernel<R, RPL><<<(unsigned)batch, 32 * QB, sm, s>>>(in, inB, rowI, colI, conj_in, (int)m, (int)n,
                                                                   rows_total, rows_per_batch, W, out, out_bstride,
-                                                                  ldr, tauws, Qout, q_bstride, ldq);
+                                                                  ldr, tauws, Qout, q_bstride, ldq,
+                                                                  split_q ? Qws : nullptr);
+  if (split_q) {
+    if (qtt_allow_max_smem((const void*)qr_form_q_kernel<R>) != QTT_OK) return QTT_ERR_CUDA;
+    qr_form_q_kernel<R><<<dim3((unsigned)npan, (unsigned)batch), 32 * QB, qr_form_q_bytes<R>((int)m, (int)n), s>>>(
+        W, (int)m, (int)n, Qws, tauws, Qout, q_bstride, ldq);
+  }
   return cudaGetLastError() == cudaSuccess ? QTT_OK : QTT_ERR_CUDA;
 }
 
@@ -1508,16 +1599,16 @@ int qtt_qr_r(const cplx<R>* in, MIdx inB, MIdx rowI, MIdx colI, int conj_in, int
     int st = QTT_ERR_UNSUPPORTED;
     if (m <= 128)
       st = launch_qr_blocked<R, 4>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
-                                   out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+                                   out_bstride, ldr, tauws, Qout, q_bstride, ldq, Qws, s);
     else if (m <= 256)
       st = launch_qr_blocked<R, 8>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
-                                   out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+                                   out_bstride, ldr, tauws, Qout, q_bstride, ldq, Qws, s);
     else if (m <= 288)  // 2 x 136 rows: the projection QR of sketch width 136
       st = launch_qr_blocked<R, 9>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
-                                   out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+                                   out_bstride, ldr, tauws, Qout, q_bstride, ldq, Qws, s);
     else if (m <= 512)
       st = launch_qr_blocked<R, 16>(in, inB, rowI, colI, conj_in, m, n, rows_total, rows_per_batch, batch, W, out,
-                                    out_bstride, ldr, tauws, Qout, q_bstride, ldq, s);
+                                    out_bstride, ldr, tauws, Qout, q_bstride, ldq, Qws, s);
     if (st != QTT_ERR_UNSUPPORTED) return st;
   }
   {
