@@ -55,7 +55,7 @@ E2E_OP_TOL = 1e-6   # the float path's operators in float (ms_setup)
 # profiles/ (file named in the line); None where no current capture exists.
 TRAFFIC = {
     "jacobi_block_kernel": {"bytes": 320.0e3, "profile": "profiles/jacobi_block_kernel_sphere32.md"},
-    "qr_panel_kernel": {"bytes": 400.128e3, "profile": "profiles/qr_panel_kernel_sphere32.md"},
+    "qr_blocked_kernel": {"bytes": None, "profile": None},
     "gemm_midx_kernel": {"bytes": 554.496e3, "profile": "profiles/gemm_midx_kernel_sphere32.md"},
 }
 
@@ -659,7 +659,7 @@ def roofline(prof, repp, peaks, mpeaks):
     cluster per Jacobi SVD)."""
     dom = max(["gemm", "qr", "jacobi"], key=lambda k: prof[k]["ms"])
     p = prof[dom]
-    kernel = {"gemm": "gemm_midx_kernel", "qr": "qr_panel_kernel", "jacobi": "jacobi_block_kernel"}[dom]
+    kernel = {"gemm": "gemm_midx_kernel", "qr": "qr_blocked_kernel", "jacobi": "jacobi_block_kernel"}[dom]
     roof = {"bound": "alu", "kernel": kernel, "unit": "TFLOP/s",
             "achieved": p["flops"] / (p["ms"] * 1e-3) / 1e12 if p["ms"] else 0.0,
             "peak": peaks["fp32_tflops"],
